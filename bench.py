@@ -1,0 +1,338 @@
+"""Benchmark: space-time unknowns per second of MGWR solves on GB300.
+
+Workload (one "step" = one complete solve): 2-D plain MGWR, 255 x 255 interior
+grid, M = 1024 time steps on (0, 1], alpha = 0.5, exact solution
+u = t^2 sin(pi x) sin(pi y) (f from D^a t^2 = 2 t^(2-a) / Gamma(3-a)),
+5-point Laplacian, V(1,1) red-black cycles from u = 0 until the relative
+infinity-norm defect is below 1e-10, FP64.  6.66e7 space-time unknowns; each
+FP64 field is 533 MB, larger than the 129 MB L2, so no flush is needed
+between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+  python bench.py --impl reference ...   (the CPU oracle on the host cores)
+
+Prints one JSON line.  Multi-GPU runs (torchrun, one rank per GPU) are
+independent replicas of the same solve (weak scaling, no collective on the data
+path); value = all ranks' unknowns / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+D, NPTS, M, T, ALPHA, TOL = 2, 255, 1024, 1.0, 0.5, 1e-10
+NU1, NU2, CYCLE = 1, 1, 1
+METRIC = "space-time unknowns/s to rel-res 1e-10 (FP64 vs mixed)"
+UNIT = "unknowns/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP64 issue rate of a GB300 SM: 2 FP64 FMA per clock (measured with an FMA
+# chain: 1.20 TFLOP/s at 1995 MHz on 152 SMs); peak at the maximum clock.
+FP64_FMA_PER_CLK_PER_SM = 2
+SMS = 152
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    p.add_argument("--alpha", type=float, default=ALPHA)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.path = None
+        self.proc = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 7:
+                    continue
+                try:
+                    sm.append(float(parts[0]))
+                    mx.append(float(parts[1]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[3:7]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        finally:
+            os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def sweep_flops_per_line(d: int, Mv: int) -> float:
+    """Algorithmic FP64 flops of one smoothed time line: half a line pair's
+    complex FFT convolution of length L = 2M (5 L log2 L per transform, forward
+    and inverse, plus 6 L for the spectrum product) and the stencil gather
+    (2d adds, one multiply, one add per time value)."""
+    L = 2 * Mv
+    return 0.5 * (2 * 5 * L * math.log2(L) + 6 * L) + (2 * d + 2) * Mv
+
+
+def defect_flops_per_line(d: int, Mv: int) -> float:
+    L = 2 * Mv
+    return 0.5 * (2 * 5 * L * math.log2(L) + 6 * L) + (2 * d + 4) * Mv
+
+
+def roofline_from_profile(prof: dict, prec: str, pk: dict) -> dict:
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    p = prof[dom]
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    if dom in ("sweep64", "defect64"):
+        per_line = sweep_flops_per_line(D, M) if dom == "sweep64" else defect_flops_per_line(D, M)
+        flops = p["lines"] * per_line
+        achieved = flops / (p["ms"] * 1e-3) / 1e12
+        peak = SMS * FP64_FMA_PER_CLK_PER_SM * 2 * sm_max * 1e6 / 1e12
+        word = 8
+        bytes_alg = p["lines"] * 3 * word * M  # f, one line of the other colour, the output
+        hbm = bytes_alg / (p["ms"] * 1e-3) / 1e9
+        return {"kernel": f"k_sweep<double>" if dom == "sweep64" else "k_defect<double>",
+                "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x max SM clock",
+                "launches": p["launches"], "avg_launch_ms": p["ms"] / max(p["launches"], 1),
+                "hbm_view": {"achieved_gbs": hbm, "peak_gbs": pk.get("hbm_gbs"),
+                             "frac": hbm / pk["hbm_gbs"] if pk.get("hbm_gbs") else None}}
+    word = 4
+    bytes_per_line = 3 * word * M
+    bytes_alg = p["lines"] * bytes_per_line
+    achieved = bytes_alg / (p["ms"] * 1e-3) / 1e9
+    peak = float(pk.get("hbm_gbs", 6800.0))
+    return {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None, "launches": p["launches"],
+            "avg_launch_ms": p["ms"] / max(p["launches"], 1)}
+
+
+def cpu_oracle_sample(steps_in_time: int = 256):
+    """The CPU oracle (direct L1 time stepping) on the full grid for the first
+    `steps_in_time` of the M time levels."""
+    from oracle import direct
+    from paper_1608_05400_gb300 import inputs
+
+    prob = inputs.Problem(D, NPTS, M, T, ALPHA, "t2")
+    f = prob.rhs()
+    t0 = time.perf_counter()
+    direct.time_stepping(D, NPTS, M, T, ALPHA, f, steps=steps_in_time)
+    dt = time.perf_counter() - t0
+    unknowns = prob.N * steps_in_time
+    return {"value": unknowns / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"direct L1 time stepping (sparse LU per step + history sums) on the full "
+                      f"{NPTS}x{NPTS} grid, first {steps_in_time} of {M} time levels "
+                      f"({dt:.1f} s; later levels cost more: the history sum grows with the step)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    base = {"impl": "reference", "metric": METRIC, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True}
+    for _ in range(args.warmup):
+        cpu_oracle_sample(16)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_oracle_sample(32))
+    dt = time.perf_counter() - t0
+    v = statistics.median(x["value"] for x in vals)
+    out = dict(base, value=v, ms_per_step=1e3 * dt / args.steps, scaling="weak", vs_baseline=None,
+               dtype="f64", data="synthetic",
+               config={"workload": f"2-D MGWR {NPTS}x{NPTS}, M={M}, alpha={ALPHA}, V(1,1), rel-res {TOL}",
+                       "parallelism": "replicas"},
+               cpu_baseline=dict(vals[0], value=v),
+               e2e={"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0})
+    print(json.dumps(out))
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+
+    from paper_1608_05400_gb300 import inputs, mgwr
+
+    alpha = args.alpha
+    prob = inputs.Problem(D, NPTS, M, T, alpha, "t2")
+    f_host = prob.rhs()
+    f_dev = torch.from_numpy(f_host).cuda()
+    stream = torch.cuda.Stream()
+    s = mgwr.Solver(D, NPTS, M, T, alpha)
+    s.set_stream(stream.cuda_stream)
+    if args.precision == "mixed":
+        s.set_precision(mgwr.MGWR_MIXED)
+
+    def step():
+        s.set_rhs_dev(f_dev.data_ptr())
+        return s.solve(CYCLE, NU1, NU2, TOL, 100)
+
+    for _ in range(max(args.warmup, 3) if args.warmup >= 3 else args.warmup):
+        st = step()
+    barrier = (lambda: torch.distributed.barrier()) if world > 1 else (lambda: None)
+
+    l0 = mgwr.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+        stats = []
+        for _ in range(args.steps):
+            stats.append(step())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    launches = mgwr.launch_count() - l0
+    ms = e0.elapsed_time(e1)
+    t_max = ms
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = world * prob.unknowns * args.steps / (t_max * 1e-3)
+
+    # accuracy of the last solve against the exact discrete solution (separable form)
+    u = s.solution()
+    if rank == 0:
+        from oracle import separable  # test infrastructure: accuracy report only
+        ref = separable.solution(D, NPTS, M, T, alpha, prob.rhs_profile(), inputs.phi(D, NPTS))
+        err = float(np.abs(u - ref).max() / np.abs(ref).max())
+    # per-kernel-class times from one profiled solve (outside the timed region)
+    s.profile(True)
+    step()
+    prof = s.profile_read()
+    s.profile(False)
+
+    e2e = None
+    if not args.no_e2e:
+        pin_f = torch.from_numpy(f_host).pin_memory()
+        pin_u = torch.empty_like(pin_f).pin_memory()
+        fp = pin_f.numpy()
+        up = pin_u.numpy()
+        ee0, ee1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        torch.cuda.synchronize()
+        ee0.record(stream)
+        for _ in range(args.steps):
+            s.set_rhs(fp)
+            s.solve(CYCLE, NU1, NU2, TOL, 100)
+            s.lib.mgwr_get_solution(s.h, up.ctypes.data_as(mgwr._dp))
+        ee1.record(stream)
+        torch.cuda.synchronize()
+        ems = ee0.elapsed_time(ee1)
+        if world > 1:
+            t = torch.tensor([ems], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ems = float(t.item())
+        nbytes = prob.unknowns * 8
+        e2e = {"value": world * prob.unknowns * args.steps / (ems * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+    s.close()
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+    pk = peaks()
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32 cycles + f64 defect/update",
+        "data": "synthetic",
+        "config": {"workload": f"2-D plain MGWR {NPTS}x{NPTS} interior, M={M} on (0,1], alpha={alpha}, "
+                               f"u=t^2 sin(pi x) sin(pi y), V({NU1},{NU2}) red-black, rel-res {TOL}",
+                   "precision": args.precision, "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (533 MB per FP64 field)"},
+        "solve": {"cycles": stats[-1].cycles, "outer": stats[-1].outer, "relres": stats[-1].relres,
+                  "factor": stats[-1].factor, "rel_err_vs_exact_discrete": err},
+        "gpu_launches": launches,
+        "roofline": roofline_from_profile(prof, args.precision, pk),
+        "kernel_classes": {k: v for k, v in prof.items() if v["launches"]},
+        "clocks": clk.summary(),
+        "e2e": e2e,
+    }
+    if not args.no_cpu and world == 1:
+        out["cpu_baseline"] = cpu_oracle_sample()
+    print(json.dumps(out))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,199 @@
+/*
+ * mgwr.h -- C ABI of the GB300 multigrid waveform relaxation (MGWR) solver for
+ * the time-fractional heat equation
+ *
+ *     D_t^alpha u - Laplace u = f   on (0,1)^d x (0,T],  d in {1,2},  0 < alpha <= 1,
+ *     u = 0 on the boundary,        u(x,0) = g(x),
+ *
+ * discretised as in the paper: the L1 scheme in time (Sec. 2, Eq. L1_scheme2;
+ * Sec. 6, Eq. L1_scheme_2d) and the 3-point / 5-point Laplacian in space
+ * (Sec. 2, Eq. discrete_model_IVP_1; Sec. 6, Eq. discrete_model_IVP_2d_1), on
+ * n^d interior points (n = 2^k - 1, h = 1/(n+1)) and M uniform time steps
+ * (tau = T/M).  The solver is Algorithm 1 (WRMG): red-black waveform
+ * relaxation smoother (Sec. 3 Eq. red-black; Sec. 6 Eq. red-black_2d), defect
+ * (Algorithm 1), full-weighting restriction and linear / bilinear
+ * interpolation of whole time lines, coarsening in space down to one point.
+ * All time-line operators are applied as FFT convolutions (Sec. 5).
+ *
+ * Data layout (every field, host or device): N = n^d time lines of M values,
+ * index p*M + m, p = i (1-D) or p = i + n*j (2-D, i along x), m = 0..M-1 at
+ * time t_{m+1} = (m+1) tau.  Values are IEEE double.
+ *
+ * Ownership: the caller owns every pointer it passes; the library copies in
+ * and out.  The library owns all device memory it allocates (cudaMalloc) and
+ * frees it in mgwr_destroy.  Device pointers ("_dev" calls) must be
+ * cudaMalloc'd memory on the handle's device, 16-byte aligned.
+ *
+ * Errors: every call returns MGWR_OK (0) or a negative MGWR_E_* code;
+ * mgwr_last_error(h) gives a message for the last failing call on h (static
+ * text for a NULL handle).  No call aborts the process or faults the device on
+ * invalid arguments: they are checked on the host first.
+ *
+ * Threads: a handle is not thread-safe; use one handle per host thread.  All
+ * device work of a handle runs on its stream (mgwr_set_stream, default: a
+ * stream the handle creates).
+ */
+#ifndef MGWR_H
+#define MGWR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define MGWR_OK 0
+#define MGWR_E_INVAL (-1)   /* invalid argument                              */
+#define MGWR_E_NOMEM (-2)   /* device or host allocation failed              */
+#define MGWR_E_TOOBIG (-3)  /* request larger than a configured budget        */
+#define MGWR_E_NOCONV (-4)  /* max_cycles reached before the tolerance        */
+#define MGWR_E_NUMERIC (-5) /* non-finite residual norm                       */
+#define MGWR_E_AGAIN (-6)   /* not ready / queue full; retry                  */
+#define MGWR_E_TIMEOUT (-7) /* bounded wait ended                             */
+#define MGWR_E_CUDA (-8)    /* CUDA runtime error (message in last_error)     */
+#define MGWR_E_STATE (-9)   /* call not valid in the handle's current state   */
+
+/* arithmetic of a solve (mgwr_set_precision) */
+#define MGWR_FP64 0  /* every kernel in IEEE double                          */
+#define MGWR_MIXED 1 /* FP32 V-cycles on the defect, FP64 defect + update     */
+
+/* which hierarchy a component call addresses */
+#define MGWR_H64 64  /* the double-precision hierarchy                         */
+#define MGWR_H32 32  /* the single-precision hierarchy (MGWR_MIXED only)       */
+
+/* fields of a level */
+#define MGWR_U 0 /* iterate (finest) or coarse correction e (coarser levels)  */
+#define MGWR_F 1 /* right-hand side (finest) or restricted defect              */
+#define MGWR_R 2 /* defect work field                                           */
+
+/* smoother colours and colour orders */
+#define MGWR_RED 0   /* the colour visited first                              */
+#define MGWR_BLACK 1 /* the colour visited second                             */
+#define MGWR_ORDER_TEXT 0  /* 1-D: even mesh index n first (0-based odd i)   */
+#define MGWR_ORDER_TABLE 1 /* 1-D: odd mesh index n first (0-based even i)   */
+/* In 2-D both orders visit even n+l (0-based even i+j) first.  The text of
+ * Sec. 3 (below Eq. red-black) says even n first; the 1-D iteration counts of
+ * Table table_it_1d are reproduced with the odd-n-first order. */
+
+typedef struct mgwr_handle* mgwr_t;
+
+typedef struct {
+  int cycles;       /* WRMG cycles done (MGWR_MIXED: inner FP32 cycles)        */
+  int outer;        /* FP64 defect evaluations after the initial one           */
+  double relres;    /* ||f - A u||_inf / ||f - A u0||_inf at return            */
+  double factor;    /* mean convergence factor relres^(1/cycles)               */
+  double seconds;   /* device time of the solve (CUDA events)                  */
+} mgwr_stats;
+
+/* ---- lifecycle --------------------------------------------------------- */
+
+/* Create a solver for (d, n, M, T, alpha).  d in {1,2}; n = 2^k - 1 with
+ * 1 <= k <= 15 (1-D) or 1 <= k <= 12 (2-D); M = 2^j with 4 <= M <= 4096;
+ * T > 0 finite; 0 < alpha <= 1.  Allocates the double-precision hierarchy
+ * and computes on the GPU, in FP64: the L1 Toeplitz column r_1..r_M
+ * (Sec. 5 Eq. Toeplitz_matrix), the first column of (T_M + 2d/h_l^2 I)^{-1}
+ * for every level l by divide and conquer (Sec. 5, smoothing procedure), and
+ * their length-2M spectra (Sec. 5, circulant embedding).  Returns MGWR_E_INVAL
+ * for bad arguments, MGWR_E_NOMEM if device memory runs out. */
+int mgwr_create(int d, int n, int M, double T, double alpha, mgwr_t* out);
+int mgwr_destroy(mgwr_t h);
+const char* mgwr_last_error(mgwr_t h);
+const char* mgwr_status_string(int status);
+
+/* MGWR_FP64 (default) or MGWR_MIXED (allocates the FP32 hierarchy). */
+int mgwr_set_precision(mgwr_t h, int precision);
+/* MGWR_ORDER_TEXT (default) or MGWR_ORDER_TABLE. */
+int mgwr_set_order(mgwr_t h, int order);
+/* cudaStream_t to run on (NULL: the handle's own stream). */
+int mgwr_set_stream(mgwr_t h, void* stream);
+/* Inner FP32 cycles per FP64 defect in MGWR_MIXED (1..16, default 2). */
+int mgwr_set_inner_cycles(mgwr_t h, int cycles);
+
+/* ---- problem data -------------------------------------------------------- */
+
+/* Right-hand side f (N*M doubles, host) and initial values g (N doubles, host,
+ * NULL = 0).  g enters as + c d_m g in the right-hand side (Sec. 2
+ * Eq. L1_scheme2, c = tau^-alpha / Gamma(2-alpha)) and as the initial
+ * iterate u^0(t) = g (Sec. 3, below Eq. GS_ODEs).  Resets the iterate. */
+int mgwr_set_rhs(mgwr_t h, const double* f, const double* g);
+/* Same with device pointers; the copies run on the handle's stream. */
+int mgwr_set_rhs_dev(mgwr_t h, const double* f_dev, const double* g_dev);
+/* Overwrite the iterate (N*M doubles, host). */
+int mgwr_set_initial(mgwr_t h, const double* u0);
+
+/* ---- solve --------------------------------------------------------------- */
+
+/* Run WRMG cycles (cycle = 1: V, 2: W; nu1 pre- and nu2 post-smoothing steps,
+ * each one red and one black half-sweep) from the current iterate until
+ * ||f - A u||_inf <= tol * ||f - A u0||_inf or max_cycles cycles.  A is the
+ * whole space-time operator T_M (x) I + A_h (Sec. 5).  Returns MGWR_OK,
+ * MGWR_E_NOCONV (stats still filled) or MGWR_E_NUMERIC (non-finite norm).
+ * stats may be NULL. */
+int mgwr_solve(mgwr_t h, int cycle, int nu1, int nu2, double tol, int max_cycles,
+               mgwr_stats* stats);
+/* Defect of the current iterate in FP64: *relres = ||f - A u||_inf /
+ * ||f - A u0||_inf (u0 the iterate at set_rhs / set_initial), optional copy of
+ * the defect to r_host (N*M doubles). */
+int mgwr_residual(mgwr_t h, double* relres, double* r_host);
+int mgwr_get_solution(mgwr_t h, double* u_host);
+int mgwr_get_solution_dev(mgwr_t h, double* u_dev);
+
+/* ---- components (one step of Algorithm 1 on one level) ------------------ */
+/* hier is MGWR_H64 or MGWR_H32; level 0 is the one-point grid, level
+ * num_levels-1 the finest.  Fields are exchanged as doubles in both
+ * hierarchies (rounded to float on the way into MGWR_H32). */
+int mgwr_num_levels(mgwr_t h, int* levels);
+int mgwr_level_n(mgwr_t h, int level, int* n_level);
+int mgwr_field_set(mgwr_t h, int hier, int level, int which, const double* host);
+int mgwr_field_get(mgwr_t h, int hier, int level, int which, double* host);
+/* One colour half-sweep of the waveform smoother at `level`: every point p of
+ * the colour solves (T_M + 2d/h^2 I) u_p = f_p + h^-2 sum_{q~p} u_q
+ * (Sec. 3 Eq. red-black; Sec. 6 Eq. red-black_2d) by convolving with the
+ * precomputed inverse column (Sec. 5). */
+int mgwr_smooth(mgwr_t h, int hier, int level, int colour);
+/* r = f - (T_M (x) I + A_h) u at `level` (Algorithm 1, defect; Sec. 5
+ * circulant-embedding matvec); *norm_inf = max |r| (may be NULL). */
+int mgwr_defect(mgwr_t h, int hier, int level, double* norm_inf);
+/* f_{level-1} = full weighting of r_level; u_{level-1} = 0 (Algorithm 1). */
+int mgwr_restrict(mgwr_t h, int hier, int level);
+/* u_level += linear / bilinear interpolation of u_{level-1} (Algorithm 1). */
+int mgwr_prolong(mgwr_t h, int hier, int level);
+/* Exact solve on the one-point grid: u_0 = (T_M + 2d/h_0^2 I)^{-1} f_0. */
+int mgwr_coarsest(mgwr_t h, int hier);
+/* One WRMG cycle at the finest level of `hier` (no convergence test). */
+int mgwr_cycle(mgwr_t h, int hier, int cycle, int nu1, int nu2);
+
+/* ---- setup results (FP64, computed on the GPU at mgwr_create) ----------- */
+int mgwr_toeplitz_column(mgwr_t h, double* r_host);            /* r_1..r_M   */
+int mgwr_inverse_column(mgwr_t h, int level, double* k_host);  /* k_1..k_M   */
+
+/* Number of CUDA kernel launches issued through the library so far
+ * (process-wide; h may be NULL). */
+int mgwr_launch_count(mgwr_t h, long long* count);
+
+/* ---- per-kernel-class timing ------------------------------------------- */
+/* Kernel classes for mgwr_profile_read. */
+#define MGWR_K_SWEEP64 0    /* FP64 colour half-sweeps (levels >= 1)          */
+#define MGWR_K_SWEEP32 1    /* FP32 colour half-sweeps                         */
+#define MGWR_K_DEFECT64 2   /* FP64 defects (incl. the convergence test)       */
+#define MGWR_K_DEFECT32 3   /* FP32 defects                                    */
+#define MGWR_K_RESTRICT 4   /* full weighting                                   */
+#define MGWR_K_PROLONG 5    /* interpolation + correction                       */
+#define MGWR_K_COARSEST 6   /* one-point solves                                 */
+#define MGWR_K_REFINE 7     /* mixed-precision update u64 += e32                */
+#define MGWR_NUM_KERNEL_CLASSES 8
+/* enable != 0: from now on every launch of the solver is bracketed by CUDA
+ * events on the handle's stream (clears the totals).  Adds event records
+ * between launches; meant for a measurement run, not for timed runs. */
+int mgwr_profile(mgwr_t h, int enable);
+/* Totals since mgwr_profile: launches, summed device milliseconds, and the
+ * number of time lines the launches processed (points swept / defect points /
+ * coarse points restricted / fine points corrected). */
+int mgwr_profile_read(mgwr_t h, int kernel_class, long long* launches, double* ms, double* lines);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MGWR_H */

@@ -1,0 +1,772 @@
+// Host side of the MGWR library: handle, level hierarchy, Algorithm 1 driver,
+// FP64 / mixed-precision solve loops and the C ABI of include/mgwr.h.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/mgwr.h"
+#include "mgwr_internal.h"
+
+using mgwr::Cx;
+
+namespace {
+
+template <class R>
+struct Hier {
+  std::vector<R*> u, f, r;        // per level, N_l * M values each
+  Cx<R>* spec = nullptr;          // nlev * L: spectra of the inverse columns
+  Cx<R>* tspec = nullptr;         // L: spectrum of the Toeplitz column
+  Cx<R>* tw = nullptr;            // L twiddles
+  bool ready = false;
+};
+
+}  // namespace
+
+struct mgwr_handle {
+  int d = 1, n = 1, M = 4, L = 8, nlev = 1;
+  double T = 1.0, alpha = 0.5, c = 1.0;
+  int precision = MGWR_FP64, order = MGWR_ORDER_TEXT, inner = 2;
+  std::vector<int> nl;          // interior points per dimension, level 0 = 1
+  std::vector<double> hinv2;    // 1/h_l^2
+  std::vector<double> sigma;    // 2d/h_l^2
+  cudaStream_t stream = nullptr;
+  cudaStream_t own_stream = nullptr;
+  double* r = nullptr;          // r_1..r_M
+  double* dk = nullptr;         // d_0..d_M
+  double* kcol = nullptr;       // nlev * M inverse columns
+  Hier<double> h64;
+  Hier<float> h32;
+  unsigned long long* norm_bits = nullptr;  // device scalar
+  unsigned long long* norm_host = nullptr;  // pinned
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  double r0 = 0.0;
+  bool r0_valid = false;
+  std::vector<void*> allocs;
+  std::string err;
+  // per-kernel-class timing (mgwr_profile): event pairs around each launch
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  struct Mark { int cls; int ev; double lines; };
+  std::vector<Mark> marks;
+  long long prof_launches[MGWR_NUM_KERNEL_CLASSES] = {};
+  double prof_ms[MGWR_NUM_KERNEL_CLASSES] = {};
+  double prof_lines[MGWR_NUM_KERNEL_CLASSES] = {};
+};
+
+namespace {
+
+const char* kNullHandleMsg = "null handle";
+
+int fail(mgwr_t h, int code, const std::string& msg) {
+  if (h != nullptr) h->err = msg;
+  return code;
+}
+
+#define MGWR_CK(h, call)                                                                  \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail((h), MGWR_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define MGWR_TRY(call)        \
+  do {                        \
+    int s_ = (call);          \
+    if (s_ != MGWR_OK) return s_; \
+  } while (0)
+
+template <class P>
+int dev_alloc(mgwr_t h, P** p, size_t bytes) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, bytes < 16 ? 16 : bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, MGWR_E_NOMEM, std::string("cudaMalloc(") + std::to_string(bytes) + "): " +
+                                     cudaGetErrorString(e));
+  }
+  h->allocs.push_back(q);
+  *p = static_cast<P*>(q);
+  return MGWR_OK;
+}
+
+bool is_pow2(long long x) { return x > 0 && (x & (x - 1)) == 0; }
+
+size_t points(const mgwr_handle* h, int l) {
+  return h->d == 1 ? (size_t)h->nl[l] : (size_t)h->nl[l] * h->nl[l];
+}
+
+int parity(const mgwr_handle* h, int colour) {
+  int red_par;
+  if (h->d == 1)
+    red_par = h->order == MGWR_ORDER_TEXT ? 1 : 0;
+  else
+    red_par = 0;
+  return colour == MGWR_RED ? red_par : red_par ^ 1;
+}
+
+template <class R>
+int alloc_fields(mgwr_t h, Hier<R>& H) {
+  H.u.assign(h->nlev, nullptr);
+  H.f.assign(h->nlev, nullptr);
+  H.r.assign(h->nlev, nullptr);
+  for (int l = 0; l < h->nlev; ++l) {
+    const size_t bytes = points(h, l) * h->M * sizeof(R);
+    MGWR_TRY(dev_alloc(h, &H.u[l], bytes));
+    MGWR_TRY(dev_alloc(h, &H.f[l], bytes));
+    MGWR_TRY(dev_alloc(h, &H.r[l], bytes));
+    MGWR_CK(h, cudaMemsetAsync(H.u[l], 0, bytes, h->stream));
+    MGWR_CK(h, cudaMemsetAsync(H.f[l], 0, bytes, h->stream));
+    MGWR_CK(h, cudaMemsetAsync(H.r[l], 0, bytes, h->stream));
+  }
+  return MGWR_OK;
+}
+
+int ensure_h32(mgwr_t h) {
+  if (h->h32.ready) return MGWR_OK;
+  Hier<float>& H = h->h32;
+  MGWR_TRY(alloc_fields(h, H));
+  MGWR_TRY(dev_alloc(h, &H.spec, sizeof(Cx<float>) * (size_t)h->nlev * h->L));
+  MGWR_TRY(dev_alloc(h, &H.tspec, sizeof(Cx<float>) * (size_t)h->L));
+  MGWR_TRY(dev_alloc(h, &H.tw, sizeof(Cx<float>) * (size_t)h->L));
+  MGWR_CK(h, mgwr::launch_round_cx(H.spec, h->h64.spec, (size_t)h->nlev * h->L, h->stream));
+  MGWR_CK(h, mgwr::launch_round_cx(H.tspec, h->h64.tspec, (size_t)h->L, h->stream));
+  MGWR_CK(h, mgwr::launch_round_cx(H.tw, h->h64.tw, (size_t)h->L, h->stream));
+  MGWR_CK(h, cudaStreamSynchronize(h->stream));
+  H.ready = true;
+  return MGWR_OK;
+}
+
+// ---- per-class timing ----------------------------------------------------------
+
+// Records an event before a launch of class `cls` covering `lines` time lines;
+// returns the index to close with prof_end (or -1 when profiling is off).
+int prof_begin(mgwr_t h, int cls, double lines) {
+  if (!h->profiling) return -1;
+  const int idx = (int)h->marks.size();
+  const int ev = 2 * idx;
+  while ((int)h->ev_pool.size() < ev + 2) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return -1;
+    h->ev_pool.push_back(e);
+  }
+  cudaEventRecord(h->ev_pool[ev], h->stream);
+  h->marks.push_back({cls, ev, lines});
+  return idx;
+}
+
+void prof_end(mgwr_t h, int idx) {
+  if (idx < 0) return;
+  cudaEventRecord(h->ev_pool[h->marks[idx].ev + 1], h->stream);
+}
+
+// Folds all recorded launch times into the per-class totals (synchronises).
+void prof_collect(mgwr_t h) {
+  if (h->marks.empty()) return;
+  cudaStreamSynchronize(h->stream);
+  for (const auto& mk : h->marks) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->ev_pool[mk.ev], h->ev_pool[mk.ev + 1]) == cudaSuccess) {
+      h->prof_launches[mk.cls] += 1;
+      h->prof_ms[mk.cls] += ms;
+      h->prof_lines[mk.cls] += mk.lines;
+    }
+  }
+  h->marks.clear();
+}
+
+// ---- Algorithm 1 components ------------------------------------------------------
+
+template <class R>
+int coarsest(mgwr_t h, Hier<R>& H);
+
+template <class R>
+int smooth_colour(mgwr_t h, Hier<R>& H, int l, int colour) {
+  if (l == 0) return coarsest(h, H);  // one point: its half-sweep is the exact solve
+  const int par = parity(h, colour);
+  const size_t N = points(h, l);
+  const double lines = (double)(par == 0 ? (N + 1) / 2 : N / 2);
+  const int pm = prof_begin(h, sizeof(R) == 8 ? MGWR_K_SWEEP64 : MGWR_K_SWEEP32, lines);
+  MGWR_CK(h, mgwr::launch_sweep<R>(H.f[l], H.u[l], H.spec + (size_t)l * h->L, H.tw, h->d,
+                                    h->nl[l], h->M, par, false, R(h->hinv2[l]), h->stream));
+  prof_end(h, pm);
+  return MGWR_OK;
+}
+
+template <class R>
+int smooth(mgwr_t h, Hier<R>& H, int l, int steps) {
+  for (int s = 0; s < steps; ++s) {
+    MGWR_TRY(smooth_colour(h, H, l, MGWR_RED));
+    MGWR_TRY(smooth_colour(h, H, l, MGWR_BLACK));
+  }
+  return MGWR_OK;
+}
+
+template <class R>
+int defect(mgwr_t h, Hier<R>& H, int l, unsigned long long* norm_bits) {
+  const int pm = prof_begin(h, sizeof(R) == 8 ? MGWR_K_DEFECT64 : MGWR_K_DEFECT32, (double)points(h, l));
+  MGWR_CK(h, (mgwr::launch_defect<R, R>(H.u[l], H.f[l], H.r[l], H.tspec, H.tw, h->d, h->nl[l],
+                                         h->M, R(h->hinv2[l]), norm_bits, h->stream)));
+  prof_end(h, pm);
+  return MGWR_OK;
+}
+
+template <class R>
+int coarsest(mgwr_t h, Hier<R>& H) {
+  const int pm = prof_begin(h, MGWR_K_COARSEST, 1.0);
+  MGWR_CK(h, mgwr::launch_sweep<R>(H.f[0], H.u[0], H.spec, H.tw, h->d, 1, h->M, 0, true, R(0),
+                                    h->stream));
+  prof_end(h, pm);
+  return MGWR_OK;
+}
+
+template <class R>
+int cycle(mgwr_t h, Hier<R>& H, int l, int gamma, int nu1, int nu2) {
+  if (l == 0) return coarsest(h, H);
+  MGWR_TRY(smooth(h, H, l, nu1));
+  MGWR_TRY(defect(h, H, l, nullptr));
+  int pm = prof_begin(h, MGWR_K_RESTRICT, (double)points(h, l - 1));
+  MGWR_CK(h, mgwr::launch_restrict<R>(H.r[l], H.f[l - 1], H.u[l - 1], h->d, h->nl[l], h->M,
+                                       h->stream));
+  prof_end(h, pm);
+  for (int g = 0; g < gamma; ++g) MGWR_TRY(cycle(h, H, l - 1, gamma, nu1, nu2));
+  pm = prof_begin(h, MGWR_K_PROLONG, (double)points(h, l));
+  MGWR_CK(h, mgwr::launch_prolong<R>(H.u[l], H.u[l - 1], h->d, h->nl[l], h->M, h->stream));
+  prof_end(h, pm);
+  MGWR_TRY(smooth(h, H, l, nu2));
+  return MGWR_OK;
+}
+
+// Reads the device norm accumulator (cleared before the producing kernel).
+int read_norm(mgwr_t h, double* out) {
+  MGWR_CK(h, cudaMemcpyAsync(h->norm_host, h->norm_bits, sizeof(unsigned long long),
+                             cudaMemcpyDeviceToHost, h->stream));
+  MGWR_CK(h, cudaStreamSynchronize(h->stream));
+  unsigned long long bits = *h->norm_host;
+  double v;
+  std::memcpy(&v, &bits, sizeof v);
+  *out = v;
+  return MGWR_OK;
+}
+
+// FP64 defect of the finest iterate with its infinity norm.  In mixed mode the
+// defect is written, rounded, as the right-hand side of the FP32 hierarchy.
+int finest_defect_norm(mgwr_t h, double* norm, bool to_h32) {
+  const int L = h->nlev - 1;
+  MGWR_CK(h, cudaMemsetAsync(h->norm_bits, 0, sizeof(unsigned long long), h->stream));
+  const int pm = prof_begin(h, MGWR_K_DEFECT64, (double)points(h, L));
+  struct Closer { mgwr_t h; int pm; ~Closer() { prof_end(h, pm); } } closer{h, pm};
+  if (to_h32) {
+    MGWR_CK(h, (mgwr::launch_defect<double, float>(h->h64.u[L], h->h64.f[L], h->h32.f[L],
+                                                    h->h64.tspec, h->h64.tw, h->d, h->nl[L], h->M,
+                                                    h->hinv2[L], h->norm_bits, h->stream)));
+  } else {
+    MGWR_CK(h, (mgwr::launch_defect<double, double>(h->h64.u[L], h->h64.f[L], h->h64.r[L],
+                                                     h->h64.tspec, h->h64.tw, h->d, h->nl[L], h->M,
+                                                     h->hinv2[L], h->norm_bits, h->stream)));
+  }
+  return read_norm(h, norm);
+}
+
+int check_level(mgwr_t h, int hierarchy, int level) {
+  if (hierarchy != MGWR_H64 && hierarchy != MGWR_H32)
+    return fail(h, MGWR_E_INVAL, "hierarchy must be MGWR_H64 or MGWR_H32");
+  if (level < 0 || level >= h->nlev) return fail(h, MGWR_E_INVAL, "level out of range");
+  if (hierarchy == MGWR_H32 && !h->h32.ready)
+    return fail(h, MGWR_E_STATE, "the FP32 hierarchy exists only after mgwr_set_precision(MGWR_MIXED)");
+  return MGWR_OK;
+}
+
+int check_cycle_args(mgwr_t h, int cyc, int nu1, int nu2) {
+  if (cyc != 1 && cyc != 2) return fail(h, MGWR_E_INVAL, "cycle must be 1 (V) or 2 (W)");
+  if (nu1 < 0 || nu2 < 0 || nu1 > 16 || nu2 > 16 || nu1 + nu2 == 0)
+    return fail(h, MGWR_E_INVAL, "need 0 <= nu1, nu2 <= 16 and nu1 + nu2 >= 1");
+  return MGWR_OK;
+}
+
+}  // namespace
+
+// =================================================================================
+// C ABI
+// =================================================================================
+
+extern "C" {
+
+const char* mgwr_status_string(int s) {
+  switch (s) {
+    case MGWR_OK: return "ok";
+    case MGWR_E_INVAL: return "invalid argument";
+    case MGWR_E_NOMEM: return "out of memory";
+    case MGWR_E_TOOBIG: return "request exceeds budget";
+    case MGWR_E_NOCONV: return "not converged";
+    case MGWR_E_NUMERIC: return "non-finite residual";
+    case MGWR_E_AGAIN: return "try again";
+    case MGWR_E_TIMEOUT: return "timed out";
+    case MGWR_E_CUDA: return "CUDA error";
+    case MGWR_E_STATE: return "invalid state";
+    default: return "unknown status";
+  }
+}
+
+const char* mgwr_last_error(mgwr_t h) { return h == nullptr ? kNullHandleMsg : h->err.c_str(); }
+
+int mgwr_destroy(mgwr_t h) {
+  if (h == nullptr) return MGWR_OK;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->norm_host) cudaFreeHost(h->norm_host);
+  if (h->ev0) cudaEventDestroy(h->ev0);
+  if (h->ev1) cudaEventDestroy(h->ev1);
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  if (h->own_stream) cudaStreamDestroy(h->own_stream);
+  delete h;
+  return MGWR_OK;
+}
+
+int mgwr_create(int d, int n, int M, double T, double alpha, mgwr_t* out) {
+  if (out == nullptr) return MGWR_E_INVAL;
+  *out = nullptr;
+  if (d != 1 && d != 2) return MGWR_E_INVAL;
+  if (n < 1 || !is_pow2((long long)n + 1)) return MGWR_E_INVAL;
+  if ((d == 1 && n > 32767) || (d == 2 && n > 4095)) return MGWR_E_INVAL;
+  if (!is_pow2(M) || M < 4 || M > 4096) return MGWR_E_INVAL;
+  if (!(T > 0.0) || !std::isfinite(T)) return MGWR_E_INVAL;
+  if (!(alpha > 0.0) || !(alpha <= 1.0)) return MGWR_E_INVAL;
+
+  mgwr_t h = new (std::nothrow) mgwr_handle;
+  if (h == nullptr) return MGWR_E_NOMEM;
+  h->d = d;
+  h->n = n;
+  h->M = M;
+  h->L = 2 * M;
+  h->T = T;
+  h->alpha = alpha;
+  const double tau = T / M;
+  h->c = std::pow(tau, -alpha) / std::tgamma(2.0 - alpha);
+  // level sizes, coarsest first
+  std::vector<int> sizes{n};
+  while (sizes.back() > 1) sizes.push_back((sizes.back() - 1) / 2);
+  h->nl.assign(sizes.rbegin(), sizes.rend());
+  h->nlev = (int)h->nl.size();
+  for (int l = 0; l < h->nlev; ++l) {
+    const double hl = 1.0 / (h->nl[l] + 1);
+    h->hinv2.push_back(1.0 / (hl * hl));
+    h->sigma.push_back(2.0 * d / (hl * hl));
+  }
+
+  auto bail = [&](int code) {
+    mgwr_destroy(h);
+    return code;
+  };
+  if (cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(MGWR_E_CUDA);
+  }
+  h->stream = h->own_stream;
+  if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess ||
+      cudaMallocHost(&h->norm_host, sizeof(unsigned long long)) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(MGWR_E_CUDA);
+  }
+  int s;
+  double* sig_dev = nullptr;
+  Cx<double>* work = nullptr;
+  if ((s = dev_alloc(h, &h->norm_bits, sizeof(unsigned long long))) != MGWR_OK) return bail(s);
+  if ((s = dev_alloc(h, &h->r, sizeof(double) * M)) != MGWR_OK) return bail(s);
+  if ((s = dev_alloc(h, &h->dk, sizeof(double) * (M + 1))) != MGWR_OK) return bail(s);
+  if ((s = dev_alloc(h, &h->kcol, sizeof(double) * (size_t)h->nlev * M)) != MGWR_OK) return bail(s);
+  if ((s = dev_alloc(h, &sig_dev, sizeof(double) * h->nlev)) != MGWR_OK) return bail(s);
+  if ((s = dev_alloc(h, &work, sizeof(Cx<double>) * (size_t)h->nlev * 3 * M)) != MGWR_OK) return bail(s);
+  if ((s = dev_alloc(h, &h->h64.spec, sizeof(Cx<double>) * (size_t)h->nlev * h->L)) != MGWR_OK) return bail(s);
+  if ((s = dev_alloc(h, &h->h64.tspec, sizeof(Cx<double>) * (size_t)h->L)) != MGWR_OK) return bail(s);
+  if ((s = dev_alloc(h, &h->h64.tw, sizeof(Cx<double>) * (size_t)h->L)) != MGWR_OK) return bail(s);
+
+  cudaError_t e = cudaMemcpyAsync(sig_dev, h->sigma.data(), sizeof(double) * h->nlev,
+                                  cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = mgwr::launch_coefficients(h->r, h->dk, M, alpha, h->c, h->stream);
+  if (e == cudaSuccess)
+    e = mgwr::launch_inverse_columns(h->kcol, h->r, sig_dev, h->nlev, M, work, h->stream);
+  if (e == cudaSuccess) e = mgwr::launch_twiddles(h->h64.tw, h->L, h->stream);
+  if (e == cudaSuccess)
+    e = mgwr::launch_spectra(h->h64.spec, h->kcol, h->nlev, M, h->h64.tw, h->stream);
+  if (e == cudaSuccess) e = mgwr::launch_spectra(h->h64.tspec, h->r, 1, M, h->h64.tw, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return bail(MGWR_E_CUDA);
+  }
+  if ((s = alloc_fields(h, h->h64)) != MGWR_OK) return bail(s);
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(MGWR_E_CUDA);
+  }
+  h->h64.ready = true;
+  *out = h;
+  return MGWR_OK;
+}
+
+int mgwr_set_precision(mgwr_t h, int precision) {
+  if (h == nullptr) return MGWR_E_INVAL;
+  if (precision != MGWR_FP64 && precision != MGWR_MIXED)
+    return fail(h, MGWR_E_INVAL, "precision must be MGWR_FP64 or MGWR_MIXED");
+  if (precision == MGWR_MIXED) MGWR_TRY(ensure_h32(h));
+  h->precision = precision;
+  return MGWR_OK;
+}
+
+int mgwr_set_order(mgwr_t h, int order) {
+  if (h == nullptr) return MGWR_E_INVAL;
+  if (order != MGWR_ORDER_TEXT && order != MGWR_ORDER_TABLE)
+    return fail(h, MGWR_E_INVAL, "order must be MGWR_ORDER_TEXT or MGWR_ORDER_TABLE");
+  h->order = order;
+  return MGWR_OK;
+}
+
+int mgwr_set_stream(mgwr_t h, void* stream) {
+  if (h == nullptr) return MGWR_E_INVAL;
+  MGWR_CK(h, cudaStreamSynchronize(h->stream));
+  h->stream = stream != nullptr ? static_cast<cudaStream_t>(stream) : h->own_stream;
+  return MGWR_OK;
+}
+
+int mgwr_set_inner_cycles(mgwr_t h, int cycles) {
+  if (h == nullptr) return MGWR_E_INVAL;
+  if (cycles < 1 || cycles > 16) return fail(h, MGWR_E_INVAL, "inner cycles must be in 1..16");
+  h->inner = cycles;
+  return MGWR_OK;
+}
+
+static int set_rhs_impl(mgwr_t h, const double* f, const double* g, cudaMemcpyKind kind) {
+  if (h == nullptr) return MGWR_E_INVAL;
+  if (f == nullptr) return fail(h, MGWR_E_INVAL, "f must not be null");
+  const int L = h->nlev - 1;
+  const size_t N = points(h, L);
+  const size_t bytes = N * h->M * sizeof(double);
+  MGWR_CK(h, cudaMemcpyAsync(h->h64.f[L], f, bytes, kind, h->stream));
+  if (g != nullptr) {
+    double* g_dev = nullptr;
+    MGWR_TRY(dev_alloc(h, &g_dev, N * sizeof(double)));
+    MGWR_CK(h, cudaMemcpyAsync(g_dev, g, N * sizeof(double), kind, h->stream));
+    MGWR_CK(h, mgwr::launch_initial(h->h64.u[L], h->h64.f[L], g_dev, h->dk, h->c, (int)N, h->M,
+                                     h->stream));
+    MGWR_CK(h, cudaStreamSynchronize(h->stream));
+    cudaFree(g_dev);
+    h->allocs.pop_back();
+  } else {
+    MGWR_CK(h, cudaMemsetAsync(h->h64.u[L], 0, bytes, h->stream));
+    MGWR_CK(h, cudaStreamSynchronize(h->stream));
+  }
+  h->r0_valid = false;
+  return MGWR_OK;
+}
+
+int mgwr_set_rhs(mgwr_t h, const double* f, const double* g) {
+  return set_rhs_impl(h, f, g, cudaMemcpyHostToDevice);
+}
+
+int mgwr_set_rhs_dev(mgwr_t h, const double* f_dev, const double* g_dev) {
+  return set_rhs_impl(h, f_dev, g_dev, cudaMemcpyDeviceToDevice);
+}
+
+int mgwr_set_initial(mgwr_t h, const double* u0) {
+  if (h == nullptr) return MGWR_E_INVAL;
+  if (u0 == nullptr) return fail(h, MGWR_E_INVAL, "u0 must not be null");
+  const int L = h->nlev - 1;
+  MGWR_CK(h, cudaMemcpyAsync(h->h64.u[L], u0, points(h, L) * h->M * sizeof(double),
+                             cudaMemcpyHostToDevice, h->stream));
+  MGWR_CK(h, cudaStreamSynchronize(h->stream));
+  h->r0_valid = false;
+  return MGWR_OK;
+}
+
+int mgwr_solve(mgwr_t h, int cyc, int nu1, int nu2, double tol, int max_cycles, mgwr_stats* st) {
+  if (h == nullptr) return MGWR_E_INVAL;
+  MGWR_TRY(check_cycle_args(h, cyc, nu1, nu2));
+  if (!(tol >= 0.0) || max_cycles < 1) return fail(h, MGWR_E_INVAL, "need tol >= 0, max_cycles >= 1");
+  const bool mixed = h->precision == MGWR_MIXED;
+  const int L = h->nlev - 1;
+  mgwr_stats local{};
+  MGWR_CK(h, cudaEventRecord(h->ev0, h->stream));
+  double norm = 0.0;
+  MGWR_TRY(finest_defect_norm(h, &norm, mixed));
+  if (!h->r0_valid) {
+    h->r0 = norm;
+    h->r0_valid = true;
+  }
+  const double r0 = h->r0;
+  double rel = r0 > 0.0 ? norm / r0 : 0.0;
+  int status = MGWR_OK;
+  int cycles = 0, outer = 0;
+  while (rel > tol) {
+    if (!std::isfinite(rel)) {
+      status = MGWR_E_NUMERIC;
+      break;
+    }
+    if ((mixed ? outer : cycles) >= max_cycles) {
+      status = MGWR_E_NOCONV;
+      break;
+    }
+    if (!mixed) {
+      MGWR_TRY(cycle(h, h->h64, L, cyc, nu1, nu2));
+      ++cycles;
+      MGWR_TRY(finest_defect_norm(h, &norm, false));
+    } else {
+      const size_t cnt = points(h, L) * h->M;
+      MGWR_CK(h, cudaMemsetAsync(h->h32.u[L], 0, cnt * sizeof(float), h->stream));
+      for (int k = 0; k < h->inner; ++k) {
+        MGWR_TRY(cycle(h, h->h32, L, cyc, nu1, nu2));
+        ++cycles;
+      }
+      const int pm = prof_begin(h, MGWR_K_REFINE, (double)points(h, L));
+      MGWR_CK(h, mgwr::launch_refine(h->h64.u[L], h->h32.u[L], cnt, h->stream));
+      prof_end(h, pm);
+      MGWR_TRY(finest_defect_norm(h, &norm, true));
+    }
+    ++outer;
+    rel = r0 > 0.0 ? norm / r0 : 0.0;
+  }
+  if (!std::isfinite(rel)) status = MGWR_E_NUMERIC;
+  MGWR_CK(h, cudaEventRecord(h->ev1, h->stream));
+  MGWR_CK(h, cudaEventSynchronize(h->ev1));
+  prof_collect(h);
+  float ms = 0.f;
+  MGWR_CK(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+  local.cycles = cycles;
+  local.outer = outer;
+  local.relres = rel;
+  local.factor = cycles > 0 && rel > 0.0 ? std::pow(rel, 1.0 / cycles) : 0.0;
+  local.seconds = ms * 1e-3;
+  if (st != nullptr) *st = local;
+  if (status == MGWR_E_NOCONV) h->err = "max_cycles reached before the tolerance";
+  if (status == MGWR_E_NUMERIC) h->err = "non-finite residual norm";
+  return status;
+}
+
+int mgwr_residual(mgwr_t h, double* relres, double* r_host) {
+  if (h == nullptr) return MGWR_E_INVAL;
+  double norm = 0.0;
+  MGWR_TRY(finest_defect_norm(h, &norm, false));
+  if (!h->r0_valid) {
+    h->r0 = norm;
+    h->r0_valid = true;
+  }
+  if (relres != nullptr) *relres = h->r0 > 0.0 ? norm / h->r0 : 0.0;
+  if (r_host != nullptr) {
+    const int L = h->nlev - 1;
+    MGWR_CK(h, cudaMemcpyAsync(r_host, h->h64.r[L], points(h, L) * h->M * sizeof(double),
+                               cudaMemcpyDeviceToHost, h->stream));
+    MGWR_CK(h, cudaStreamSynchronize(h->stream));
+  }
+  return MGWR_OK;
+}
+
+int mgwr_get_solution(mgwr_t h, double* u_host) {
+  if (h == nullptr) return MGWR_E_INVAL;
+  if (u_host == nullptr) return fail(h, MGWR_E_INVAL, "u must not be null");
+  const int L = h->nlev - 1;
+  MGWR_CK(h, cudaMemcpyAsync(u_host, h->h64.u[L], points(h, L) * h->M * sizeof(double),
+                             cudaMemcpyDeviceToHost, h->stream));
+  MGWR_CK(h, cudaStreamSynchronize(h->stream));
+  return MGWR_OK;
+}
+
+int mgwr_get_solution_dev(mgwr_t h, double* u_dev) {
+  if (h == nullptr) return MGWR_E_INVAL;
+  if (u_dev == nullptr) return fail(h, MGWR_E_INVAL, "u must not be null");
+  const int L = h->nlev - 1;
+  MGWR_CK(h, cudaMemcpyAsync(u_dev, h->h64.u[L], points(h, L) * h->M * sizeof(double),
+                             cudaMemcpyDeviceToDevice, h->stream));
+  return MGWR_OK;
+}
+
+int mgwr_num_levels(mgwr_t h, int* levels) {
+  if (h == nullptr || levels == nullptr) return MGWR_E_INVAL;
+  *levels = h->nlev;
+  return MGWR_OK;
+}
+
+int mgwr_level_n(mgwr_t h, int level, int* n_level) {
+  if (h == nullptr || n_level == nullptr) return MGWR_E_INVAL;
+  if (level < 0 || level >= h->nlev) return fail(h, MGWR_E_INVAL, "level out of range");
+  *n_level = h->nl[level];
+  return MGWR_OK;
+}
+
+static void* field_ptr(mgwr_t h, int hierarchy, int level, int which) {
+  if (hierarchy == MGWR_H64) {
+    Hier<double>& H = h->h64;
+    return which == MGWR_U ? (void*)H.u[level] : which == MGWR_F ? (void*)H.f[level] : (void*)H.r[level];
+  }
+  Hier<float>& H = h->h32;
+  return which == MGWR_U ? (void*)H.u[level] : which == MGWR_F ? (void*)H.f[level] : (void*)H.r[level];
+}
+
+int mgwr_field_set(mgwr_t h, int hierarchy, int level, int which, const double* host) {
+  if (h == nullptr) return MGWR_E_INVAL;
+  MGWR_TRY(check_level(h, hierarchy, level));
+  if (which < MGWR_U || which > MGWR_R || host == nullptr)
+    return fail(h, MGWR_E_INVAL, "bad field or null pointer");
+  const size_t cnt = points(h, level) * h->M;
+  void* dst = field_ptr(h, hierarchy, level, which);
+  if (hierarchy == MGWR_H64) {
+    MGWR_CK(h, cudaMemcpyAsync(dst, host, cnt * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  } else {
+    std::vector<float> tmp(cnt);
+    for (size_t i = 0; i < cnt; ++i) tmp[i] = (float)host[i];
+    MGWR_CK(h, cudaMemcpyAsync(dst, tmp.data(), cnt * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+    MGWR_CK(h, cudaStreamSynchronize(h->stream));
+  }
+  MGWR_CK(h, cudaStreamSynchronize(h->stream));
+  if (hierarchy == MGWR_H64 && level == h->nlev - 1) h->r0_valid = false;
+  return MGWR_OK;
+}
+
+int mgwr_field_get(mgwr_t h, int hierarchy, int level, int which, double* host) {
+  if (h == nullptr) return MGWR_E_INVAL;
+  MGWR_TRY(check_level(h, hierarchy, level));
+  if (which < MGWR_U || which > MGWR_R || host == nullptr)
+    return fail(h, MGWR_E_INVAL, "bad field or null pointer");
+  const size_t cnt = points(h, level) * h->M;
+  const void* src = field_ptr(h, hierarchy, level, which);
+  if (hierarchy == MGWR_H64) {
+    MGWR_CK(h, cudaMemcpyAsync(host, src, cnt * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    MGWR_CK(h, cudaStreamSynchronize(h->stream));
+  } else {
+    std::vector<float> tmp(cnt);
+    MGWR_CK(h, cudaMemcpyAsync(tmp.data(), src, cnt * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    MGWR_CK(h, cudaStreamSynchronize(h->stream));
+    for (size_t i = 0; i < cnt; ++i) host[i] = (double)tmp[i];
+  }
+  return MGWR_OK;
+}
+
+int mgwr_smooth(mgwr_t h, int hierarchy, int level, int colour) {
+  if (h == nullptr) return MGWR_E_INVAL;
+  MGWR_TRY(check_level(h, hierarchy, level));
+  if (colour != MGWR_RED && colour != MGWR_BLACK) return fail(h, MGWR_E_INVAL, "bad colour");
+  if (hierarchy == MGWR_H64)
+    MGWR_TRY(smooth_colour(h, h->h64, level, colour));
+  else
+    MGWR_TRY(smooth_colour(h, h->h32, level, colour));
+  MGWR_CK(h, cudaStreamSynchronize(h->stream));
+  return MGWR_OK;
+}
+
+int mgwr_defect(mgwr_t h, int hierarchy, int level, double* norm_inf) {
+  if (h == nullptr) return MGWR_E_INVAL;
+  MGWR_TRY(check_level(h, hierarchy, level));
+  MGWR_CK(h, cudaMemsetAsync(h->norm_bits, 0, sizeof(unsigned long long), h->stream));
+  if (hierarchy == MGWR_H64)
+    MGWR_TRY(defect(h, h->h64, level, h->norm_bits));
+  else
+    MGWR_TRY(defect(h, h->h32, level, h->norm_bits));
+  double nrm = 0.0;
+  MGWR_TRY(read_norm(h, &nrm));
+  if (norm_inf != nullptr) *norm_inf = nrm;
+  return MGWR_OK;
+}
+
+int mgwr_restrict(mgwr_t h, int hierarchy, int level) {
+  if (h == nullptr) return MGWR_E_INVAL;
+  MGWR_TRY(check_level(h, hierarchy, level));
+  if (level == 0) return fail(h, MGWR_E_INVAL, "level 0 has no coarser level");
+  if (hierarchy == MGWR_H64) {
+    MGWR_CK(h, mgwr::launch_restrict<double>(h->h64.r[level], h->h64.f[level - 1],
+                                              h->h64.u[level - 1], h->d, h->nl[level], h->M, h->stream));
+  } else {
+    MGWR_CK(h, mgwr::launch_restrict<float>(h->h32.r[level], h->h32.f[level - 1],
+                                             h->h32.u[level - 1], h->d, h->nl[level], h->M, h->stream));
+  }
+  MGWR_CK(h, cudaStreamSynchronize(h->stream));
+  return MGWR_OK;
+}
+
+int mgwr_prolong(mgwr_t h, int hierarchy, int level) {
+  if (h == nullptr) return MGWR_E_INVAL;
+  MGWR_TRY(check_level(h, hierarchy, level));
+  if (level == 0) return fail(h, MGWR_E_INVAL, "level 0 has no coarser level");
+  if (hierarchy == MGWR_H64) {
+    MGWR_CK(h, mgwr::launch_prolong<double>(h->h64.u[level], h->h64.u[level - 1], h->d, h->nl[level],
+                                             h->M, h->stream));
+  } else {
+    MGWR_CK(h, mgwr::launch_prolong<float>(h->h32.u[level], h->h32.u[level - 1], h->d, h->nl[level],
+                                            h->M, h->stream));
+  }
+  MGWR_CK(h, cudaStreamSynchronize(h->stream));
+  return MGWR_OK;
+}
+
+int mgwr_coarsest(mgwr_t h, int hierarchy) {
+  if (h == nullptr) return MGWR_E_INVAL;
+  MGWR_TRY(check_level(h, hierarchy, 0));
+  if (hierarchy == MGWR_H64)
+    MGWR_TRY(coarsest(h, h->h64));
+  else
+    MGWR_TRY(coarsest(h, h->h32));
+  MGWR_CK(h, cudaStreamSynchronize(h->stream));
+  return MGWR_OK;
+}
+
+int mgwr_cycle(mgwr_t h, int hierarchy, int cyc, int nu1, int nu2) {
+  if (h == nullptr) return MGWR_E_INVAL;
+  MGWR_TRY(check_level(h, hierarchy, h->nlev - 1));
+  MGWR_TRY(check_cycle_args(h, cyc, nu1, nu2));
+  if (hierarchy == MGWR_H64)
+    MGWR_TRY(cycle(h, h->h64, h->nlev - 1, cyc, nu1, nu2));
+  else
+    MGWR_TRY(cycle(h, h->h32, h->nlev - 1, cyc, nu1, nu2));
+  MGWR_CK(h, cudaStreamSynchronize(h->stream));
+  return MGWR_OK;
+}
+
+int mgwr_toeplitz_column(mgwr_t h, double* r_host) {
+  if (h == nullptr || r_host == nullptr) return MGWR_E_INVAL;
+  MGWR_CK(h, cudaMemcpyAsync(r_host, h->r, sizeof(double) * h->M, cudaMemcpyDeviceToHost, h->stream));
+  MGWR_CK(h, cudaStreamSynchronize(h->stream));
+  return MGWR_OK;
+}
+
+int mgwr_inverse_column(mgwr_t h, int level, double* k_host) {
+  if (h == nullptr || k_host == nullptr) return MGWR_E_INVAL;
+  if (level < 0 || level >= h->nlev) return fail(h, MGWR_E_INVAL, "level out of range");
+  MGWR_CK(h, cudaMemcpyAsync(k_host, h->kcol + (size_t)level * h->M, sizeof(double) * h->M,
+                             cudaMemcpyDeviceToHost, h->stream));
+  MGWR_CK(h, cudaStreamSynchronize(h->stream));
+  return MGWR_OK;
+}
+
+int mgwr_profile(mgwr_t h, int enable) {
+  if (h == nullptr) return MGWR_E_INVAL;
+  prof_collect(h);
+  h->profiling = enable != 0;
+  for (int k = 0; k < MGWR_NUM_KERNEL_CLASSES; ++k) {
+    h->prof_launches[k] = 0;
+    h->prof_ms[k] = 0.0;
+    h->prof_lines[k] = 0.0;
+  }
+  return MGWR_OK;
+}
+
+int mgwr_profile_read(mgwr_t h, int kernel_class, long long* launches, double* ms, double* lines) {
+  if (h == nullptr) return MGWR_E_INVAL;
+  if (kernel_class < 0 || kernel_class >= MGWR_NUM_KERNEL_CLASSES)
+    return fail(h, MGWR_E_INVAL, "bad kernel class");
+  prof_collect(h);
+  if (launches) *launches = h->prof_launches[kernel_class];
+  if (ms) *ms = h->prof_ms[kernel_class];
+  if (lines) *lines = h->prof_lines[kernel_class];
+  return MGWR_OK;
+}
+
+int mgwr_launch_count(mgwr_t h, long long* count) {
+  (void)h;
+  if (count == nullptr) return MGWR_E_INVAL;
+  *count = mgwr::launch_counter();
+  return MGWR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,206 @@
+// Shared-memory FFT engine for causal time-line convolutions (Sec. 5).
+//
+// Every time-line operator of the method is a lower-triangular Toeplitz matrix
+// (T_M for the defect, the inverse (T_M + sigma I)^{-1} for the smoother).  Its
+// product with a line x is the first M entries of the cyclic convolution of the
+// zero-padded length-L = 2M sequences (Sec. 5, circulant embedding C_2M).  Two
+// real lines are packed as the real and imaginary parts of one complex line, so
+// one complex transform serves two spatial points.
+//
+// One thread group of L/8 threads owns one line pair.  Forward transform:
+// decimation in frequency, radix-8 stages (the first one reads the input from
+// global memory and skips the zero upper half), a last stage of radix 8, 4 or
+// 2 whose butterflies each thread does on 8 contiguous values.  The spectrum
+// product is applied in registers right there, followed by the matching
+// inverse stage, so the result never needs reordering: the inverse cascade
+// runs the forward one backwards with conjugate twiddles and writes only the
+// first M outputs.
+#pragma once
+
+#include "mgwr_internal.h"
+
+namespace mgwr {
+
+template <class R>
+__device__ __forceinline__ Cx<R> cadd(Cx<R> a, Cx<R> b) { return {a.x + b.x, a.y + b.y}; }
+template <class R>
+__device__ __forceinline__ Cx<R> csub(Cx<R> a, Cx<R> b) { return {a.x - b.x, a.y - b.y}; }
+template <class R>
+__device__ __forceinline__ Cx<R> cmul(Cx<R> a, Cx<R> b) {
+  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+// a * conj(b)
+template <class R>
+__device__ __forceinline__ Cx<R> cmulc(Cx<R> a, Cx<R> b) {
+  return {a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y};
+}
+
+// Multiplication by powers of w8 = exp(-+2 pi i / 8) (INV: the + sign).
+template <bool INV, class R>
+__device__ __forceinline__ Cx<R> mul_w1(Cx<R> a) {
+  const R s = R(0.70710678118654752440);
+  return INV ? Cx<R>{(a.x - a.y) * s, (a.x + a.y) * s} : Cx<R>{(a.x + a.y) * s, (a.y - a.x) * s};
+}
+template <bool INV, class R>
+__device__ __forceinline__ Cx<R> mul_w2(Cx<R> a) {
+  return INV ? Cx<R>{-a.y, a.x} : Cx<R>{a.y, -a.x};
+}
+template <bool INV, class R>
+__device__ __forceinline__ Cx<R> mul_w3(Cx<R> a) {
+  const R s = R(0.70710678118654752440);
+  return INV ? Cx<R>{-(a.x + a.y) * s, (a.x - a.y) * s} : Cx<R>{(a.y - a.x) * s, -(a.x + a.y) * s};
+}
+
+// Length-4 DFT, natural order in and out.
+template <bool INV, class R>
+__device__ __forceinline__ void dft4(Cx<R>& a0, Cx<R>& a1, Cx<R>& a2, Cx<R>& a3) {
+  const Cx<R> c0 = cadd(a0, a2), d0 = csub(a0, a2);
+  const Cx<R> c1 = cadd(a1, a3), d1 = mul_w2<INV>(csub(a1, a3));
+  a0 = cadd(c0, c1);
+  a2 = csub(c0, c1);
+  a1 = cadd(d0, d1);
+  a3 = csub(d0, d1);
+}
+
+template <class R>
+__device__ __forceinline__ void dft2(Cx<R>& a0, Cx<R>& a1) {
+  const Cx<R> s = cadd(a0, a1);
+  a1 = csub(a0, a1);
+  a0 = s;
+}
+
+// Length-8 DFT (one radix-2 layer, then two length-4 DFTs), natural order.
+template <bool INV, class R>
+__device__ __forceinline__ void dft8(Cx<R> (&v)[8]) {
+  Cx<R> a0 = cadd(v[0], v[4]), a1 = cadd(v[1], v[5]), a2 = cadd(v[2], v[6]), a3 = cadd(v[3], v[7]);
+  Cx<R> b0 = csub(v[0], v[4]), b1 = mul_w1<INV>(csub(v[1], v[5]));
+  Cx<R> b2 = mul_w2<INV>(csub(v[2], v[6])), b3 = mul_w3<INV>(csub(v[3], v[7]));
+  dft4<INV>(a0, a1, a2, a3);
+  dft4<INV>(b0, b1, b2, b3);
+  v[0] = a0; v[2] = a1; v[4] = a2; v[6] = a3;
+  v[1] = b0; v[3] = b1; v[5] = b2; v[7] = b3;
+}
+
+// Forward length-8 DFT of (v0, v1, v2, v3, 0, 0, 0, 0).
+template <class R>
+__device__ __forceinline__ void dft8_half_input(Cx<R> (&v)[8]) {
+  Cx<R> a0 = v[0], a1 = v[1], a2 = v[2], a3 = v[3];
+  Cx<R> b0 = v[0], b1 = mul_w1<false>(v[1]), b2 = mul_w2<false>(v[2]), b3 = mul_w3<false>(v[3]);
+  dft4<false>(a0, a1, a2, a3);
+  dft4<false>(b0, b1, b2, b3);
+  v[0] = a0; v[2] = a1; v[4] = a2; v[6] = a3;
+  v[1] = b0; v[3] = b1; v[5] = b2; v[7] = b3;
+}
+
+// Shared-memory index with one pad slot per 8 elements (bank-conflict free for
+// the strided and the contiguous access patterns of the stages below).
+__device__ __forceinline__ int pad8(int x) { return x + (x >> 3); }
+__host__ __device__ __forceinline__ int padded_len(int L) { return L + (L >> 3); }
+
+// Last-stage butterflies on the 8 contiguous values a thread owns.
+template <bool INV, class R>
+__device__ __forceinline__ void last_stage(Cx<R> (&v)[8], int rlast) {
+  if (rlast == 8) {
+    dft8<INV>(v);
+  } else if (rlast == 4) {
+    dft4<INV>(v[0], v[1], v[2], v[3]);
+    dft4<INV>(v[4], v[5], v[6], v[7]);
+  } else {
+    dft2(v[0], v[1]);
+    dft2(v[2], v[3]);
+    dft2(v[4], v[5]);
+    dft2(v[6], v[7]);
+  }
+}
+
+struct FftShape {
+  int L, logL, L8, rlast, kmid_end;
+  __device__ __forceinline__ explicit FftShape(int logL_) : L(1 << logL_), logL(logL_) {
+    L8 = L >> 3;
+    const int rem = logL % 3;
+    rlast = rem == 0 ? 8 : (1 << rem);
+    const int s8 = logL / 3;
+    kmid_end = rem == 0 ? s8 - 1 : s8;  // radix-8 stages 1 .. kmid_end-1 are "middle"
+  }
+};
+
+// Radix-8 middle stage k (span L >> 3(k+1)), forward or inverse, in shared memory.
+template <bool INV, class R>
+__device__ __forceinline__ void middle_stage(Cx<R>* buf, int t, const FftShape& sh, int k,
+                                             const Cx<R>* __restrict__ tw) {
+  const int shift = 3 * (k + 1);
+  const int s = sh.L >> shift;
+  const int j = t & (s - 1);
+  const int base = ((t - j) << 3) + j;
+  const int tws = 3 * k;
+  Cx<R> v[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) v[q] = buf[pad8(base + q * s)];
+  if (!INV) {
+    dft8<false>(v);
+#pragma unroll
+    for (int q = 1; q < 8; ++q) v[q] = cmul(v[q], tw[(j * q) << tws]);
+  } else {
+#pragma unroll
+    for (int q = 1; q < 8; ++q) v[q] = cmulc(v[q], tw[(j * q) << tws]);
+    dft8<true>(v);
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) buf[pad8(base + q * s)] = v[q];
+}
+
+// Forward transform of one zero-padded line pair.  `load(m)` returns the pair's
+// input at time index m < M (called for m = t + q L/8, q < 4).  On return the
+// thread holds, in v, the transform values at spectral positions 8t .. 8t+7.
+// Every thread of the block must call this (it synchronises the block).
+template <class R, class Load>
+__device__ __forceinline__ void fft_forward(Cx<R>* buf, int t, const FftShape& sh,
+                                            const Cx<R>* __restrict__ tw, Load load, Cx<R> (&v)[8]) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) v[q] = load(t + q * sh.L8);
+  dft8_half_input(v);
+  if (sh.logL == 3) return;  // single stage: thread 0 holds positions 0..7
+#pragma unroll
+  for (int q = 1; q < 8; ++q) v[q] = cmul(v[q], tw[t * q]);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) buf[pad8(t + q * sh.L8)] = v[q];
+  __syncthreads();
+  for (int k = 1; k < sh.kmid_end; ++k) {
+    middle_stage<false>(buf, t, sh, k, tw);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) v[q] = buf[pad8(8 * t + q)];
+  last_stage<false>(v, sh.rlast);
+}
+
+// Inverse transform starting from the spectral values in v (positions 8t..8t+7,
+// already multiplied).  `store(m, value)` receives the outputs for m < M.
+template <class R, class Store>
+__device__ __forceinline__ void fft_inverse(Cx<R>* buf, int t, const FftShape& sh,
+                                            const Cx<R>* __restrict__ tw, Cx<R> (&v)[8], Store store) {
+  if (sh.logL == 3) {
+    dft8<true>(v);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) store(q, v[q]);
+    return;
+  }
+  last_stage<true>(v, sh.rlast);
+  // each thread rewrites only the 8 positions it read in fft_forward
+#pragma unroll
+  for (int q = 0; q < 8; ++q) buf[pad8(8 * t + q)] = v[q];
+  __syncthreads();
+  for (int k = sh.kmid_end - 1; k >= 1; --k) {
+    middle_stage<true>(buf, t, sh, k, tw);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) v[q] = buf[pad8(t + q * sh.L8)];
+#pragma unroll
+  for (int q = 1; q < 8; ++q) v[q] = cmulc(v[q], tw[t * q]);
+  dft8<true>(v);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) store(t + q * sh.L8, v[q]);
+}
+
+}  // namespace mgwr

@@ -1,0 +1,687 @@
+// CUDA kernels of the MGWR solver (sm_103a).  See mgwr_fft.cuh for the FFT
+// engine shared by the smoother and the defect.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+
+#include "mgwr_fft.cuh"
+#include "mgwr_internal.h"
+
+namespace mgwr {
+
+namespace {
+std::atomic<long long> g_launches{0};
+
+inline cudaError_t counted(cudaError_t e) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return e;
+}
+
+// Threads per line pair: L/8.  Blocks hold 256 threads (several pairs) up to
+// L = 2048 and one pair of L/8 threads beyond.
+inline int block_threads(int L) { return L / 8 > 256 ? L / 8 : 256; }
+
+inline int ilog2(int x) {
+  int l = 0;
+  while ((1 << l) < x) ++l;
+  return l;
+}
+}  // namespace
+
+long long launch_counter() { return g_launches.load(); }
+
+// ---------------------------------------------------------------------------------
+// point enumeration
+// ---------------------------------------------------------------------------------
+
+// Number of points of parity `par`: (i & 1) == par in 1-D, ((i + j) & 1) == par in 2-D.
+__host__ __device__ __forceinline__ int colour_count(int d, int n, int par) {
+  if (d == 1) return (n - par + 1) / 2;
+  return ((n - 1) / 2) * n + (n - par + 1) / 2;
+}
+
+// k-th point of parity `par` in row-major order (p = i + n*j).
+__device__ __forceinline__ int colour_point(int k, int d, int n, int par, int& i, int& j) {
+  if (d == 1) {
+    i = par + 2 * k;
+    j = 0;
+    return i;
+  }
+  const int a = k / n;
+  const int rem = k - a * n;
+  const int c0 = (n - par + 1) / 2;  // points in row 2a (first i = par)
+  if (rem < c0) {
+    j = 2 * a;
+    i = par + 2 * rem;
+  } else {
+    j = 2 * a + 1;
+    i = (par ^ 1) + 2 * (rem - c0);
+  }
+  return i + n * j;
+}
+
+// Sum of the neighbour lines of point (i, j) at time m (zero Dirichlet values).
+template <class R>
+__device__ __forceinline__ R neighbour_sum(const R* __restrict__ u, int d, int n, int i, int j,
+                                           size_t pM, int M, int m) {
+  R s = R(0);
+  if (i > 0) s += u[pM - M + m];
+  if (i < n - 1) s += u[pM + M + m];
+  if (d == 2) {
+    const size_t nM = (size_t)n * M;
+    if (j > 0) s += u[pM - nM + m];
+    if (j < n - 1) s += u[pM + nM + m];
+  }
+  return s;
+}
+
+// ---------------------------------------------------------------------------------
+// smoother: one colour half-sweep (Sec. 3 Eq. red-black, Sec. 6 Eq. red-black_2d)
+// ---------------------------------------------------------------------------------
+
+template <class R, int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+    k_sweep(const R* __restrict__ f, R* __restrict__ u, const Cx<R>* __restrict__ spec,
+            const Cx<R>* __restrict__ tw, int d, int n, int M, int logL, int par, int all_points,
+            R hinv2, int npts, int npairs) {
+  extern __shared__ unsigned char smem_raw[];
+  Cx<R>* smem = reinterpret_cast<Cx<R>*>(smem_raw);
+  const FftShape sh(logL);
+  const int TL = sh.L8;
+  const int g = threadIdx.x / TL;
+  const int t = threadIdx.x - g * TL;
+  const int groups = BLOCK / TL;
+  const int pair = blockIdx.x * groups + g;
+  Cx<R>* buf = smem + g * padded_len(sh.L);
+
+  const bool valid = pair < npairs;
+  const int kA = 2 * pair, kB = 2 * pair + 1;
+  const bool hasB = valid && kB < npts;
+  int iA = 0, jA = 0, iB = 0, jB = 0, pA = 0, pB = 0;
+  if (valid) {
+    if (all_points) {
+      pA = kA;
+      pB = kB;
+    } else {
+      pA = colour_point(kA, d, n, par, iA, jA);
+      if (hasB) pB = colour_point(kB, d, n, par, iB, jB);
+    }
+  }
+  const size_t pAM = (size_t)pA * M, pBM = (size_t)pB * M;
+
+  auto load = [&](int m) -> Cx<R> {
+    Cx<R> b{R(0), R(0)};
+    if (valid) {
+      b.x = f[pAM + m];
+      if (!all_points) b.x += hinv2 * neighbour_sum(u, d, n, iA, jA, pAM, M, m);
+      if (hasB) {
+        b.y = f[pBM + m];
+        if (!all_points) b.y += hinv2 * neighbour_sum(u, d, n, iB, jB, pBM, M, m);
+      }
+    }
+    return b;
+  };
+  Cx<R> v[8];
+  fft_forward(buf, t, sh, tw, load, v);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) v[q] = cmul(v[q], spec[8 * t + q]);
+  auto store = [&](int m, Cx<R> y) {
+    if (valid) {
+      u[pAM + m] = y.x;
+      if (hasB) u[pBM + m] = y.y;
+    }
+  };
+  fft_inverse(buf, t, sh, tw, v, store);
+}
+
+// ---------------------------------------------------------------------------------
+// defect r = f - (T_M (x) I + A_h) u  (Algorithm 1; Sec. 5 circulant-embedding matvec)
+// ---------------------------------------------------------------------------------
+
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long* bits, double v) {
+  // non-negative doubles order like their bit patterns; NaN (all exponent bits
+  // set, non-zero mantissa) compares above +inf and so propagates
+  atomicMax(bits, (unsigned long long)__double_as_longlong(v));
+}
+
+template <class R>
+__device__ __forceinline__ R absmax_nan(R a, R b) {
+  // max that lets NaN win
+  return (a != a || a > b) ? a : b;
+}
+
+template <class R, class RO, int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+    k_defect(const R* __restrict__ u, const R* __restrict__ f, RO* __restrict__ r,
+             const Cx<R>* __restrict__ tspec, const Cx<R>* __restrict__ tw, int d, int n, int M,
+             int logL, R hinv2, int npts, int npairs, unsigned long long* __restrict__ norm_bits) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ double red[BLOCK / 32];
+  Cx<R>* smem = reinterpret_cast<Cx<R>*>(smem_raw);
+  const FftShape sh(logL);
+  const int TL = sh.L8;
+  const int g = threadIdx.x / TL;
+  const int t = threadIdx.x - g * TL;
+  const int groups = BLOCK / TL;
+  const int pair = blockIdx.x * groups + g;
+  Cx<R>* buf = smem + g * padded_len(sh.L);
+
+  const bool valid = pair < npairs;
+  const int pA = 2 * pair, pB = 2 * pair + 1;
+  const bool hasB = valid && pB < npts;
+  const size_t pAM = (size_t)pA * M, pBM = (size_t)pB * M;
+  const int iA = d == 1 ? pA : pA % n, jA = d == 1 ? 0 : pA / n;
+  const int iB = d == 1 ? pB : pB % n, jB = d == 1 ? 0 : pB / n;
+  const R diag = R(2 * d) * hinv2;
+
+  auto load = [&](int m) -> Cx<R> {
+    Cx<R> x{R(0), R(0)};
+    if (valid) {
+      x.x = u[pAM + m];
+      if (hasB) x.y = u[pBM + m];
+    }
+    return x;
+  };
+  Cx<R> v[8];
+  fft_forward(buf, t, sh, tw, load, v);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) v[q] = cmul(v[q], tspec[8 * t + q]);
+  R amax = R(0);
+  auto store = [&](int m, Cx<R> y) {
+    if (valid) {
+      const R ra = f[pAM + m] - y.x - (diag * u[pAM + m] - hinv2 * neighbour_sum(u, d, n, iA, jA, pAM, M, m));
+      r[pAM + m] = RO(ra);
+      amax = absmax_nan(fabs(ra), amax);
+      if (hasB) {
+        const R rb = f[pBM + m] - y.y - (diag * u[pBM + m] - hinv2 * neighbour_sum(u, d, n, iB, jB, pBM, M, m));
+        r[pBM + m] = RO(rb);
+        amax = absmax_nan(fabs(rb), amax);
+      }
+    }
+  };
+  fft_inverse(buf, t, sh, tw, v, store);
+
+  if (norm_bits != nullptr) {
+    double a = (double)amax;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a = absmax_nan(__shfl_xor_sync(0xffffffffu, a, o), a);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      a = threadIdx.x < BLOCK / 32 ? red[threadIdx.x] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) a = absmax_nan(__shfl_xor_sync(0xffffffffu, a, o), a);
+      if (threadIdx.x == 0) atomic_max_nonneg(norm_bits, a);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// grid transfers on whole time lines (Algorithm 1; Sec. 3 and Sec. 6)
+// ---------------------------------------------------------------------------------
+
+// Full weighting, (1/4)[1 2 1] per dimension; also clears the coarse correction.
+template <class R>
+__global__ void k_restrict(const R* __restrict__ r, R* __restrict__ fc, R* __restrict__ uc, int d,
+                           int n, int M, size_t total) {
+  const int nc = (n - 1) / 2;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t P = idx / M;
+    const int m = (int)(idx - P * M);
+    R acc;
+    if (d == 1) {
+      const size_t c = (2 * P + 1) * (size_t)M + m;
+      acc = R(0.25) * (r[c - M] + R(2) * r[c] + r[c + M]);
+    } else {
+      const int I = (int)(P % nc), J = (int)(P / nc);
+      const size_t c = ((size_t)(2 * I + 1) + (size_t)(2 * J + 1) * n) * M + m;
+      const size_t nM = (size_t)n * M;
+      const R row_m = r[c - nM - M] + R(2) * r[c - nM] + r[c - nM + M];
+      const R row_0 = r[c - M] + R(2) * r[c] + r[c + M];
+      const R row_p = r[c + nM - M] + R(2) * r[c + nM] + r[c + nM + M];
+      acc = R(0.0625) * (row_m + R(2) * row_0 + row_p);
+    }
+    fc[idx] = acc;
+    uc[idx] = R(0);
+  }
+}
+
+// 1-D interpolation weights of fine index i from coarse indices (zero outside).
+__device__ __forceinline__ int interp_taps(int i, int nc, int* idx, float* w) {
+  if (i & 1) {  // fine 2J+1 coincides with coarse J
+    idx[0] = (i - 1) >> 1;
+    w[0] = 1.f;
+    return 1;
+  }
+  int k = 0;
+  const int J = i >> 1;  // fine 2J: mean of coarse J-1 and J
+  if (J - 1 >= 0) { idx[k] = J - 1; w[k] = 0.5f; ++k; }
+  if (J < nc) { idx[k] = J; w[k] = 0.5f; ++k; }
+  return k;
+}
+
+template <class R>
+__global__ void k_prolong(R* __restrict__ u, const R* __restrict__ uc, int d, int n, int M,
+                          size_t total) {
+  const int nc = (n - 1) / 2;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t p = idx / M;
+    const int m = (int)(idx - p * M);
+    int ix[2], jy[2];
+    float wx[2], wy[2];
+    R acc = R(0);
+    if (d == 1) {
+      const int kx = interp_taps((int)p, nc, ix, wx);
+      for (int a = 0; a < kx; ++a) acc += R(wx[a]) * uc[(size_t)ix[a] * M + m];
+    } else {
+      const int i = (int)(p % n), j = (int)(p / n);
+      const int kx = interp_taps(i, nc, ix, wx);
+      const int ky = interp_taps(j, nc, jy, wy);
+      for (int b = 0; b < ky; ++b)
+        for (int a = 0; a < kx; ++a)
+          acc += R(wx[a] * wy[b]) * uc[((size_t)ix[a] + (size_t)jy[b] * nc) * M + m];
+    }
+    u[idx] += acc;
+  }
+}
+
+__global__ void k_refine(double* __restrict__ u, const float* __restrict__ e, size_t count) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
+       i += (size_t)gridDim.x * blockDim.x)
+    u[i] += (double)e[i];
+}
+
+__global__ void k_round(float* __restrict__ dst, const double* __restrict__ src, size_t count) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
+       i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = (float)src[i];
+}
+
+__global__ void k_initial(double* __restrict__ u, double* __restrict__ f,
+                          const double* __restrict__ g, const double* __restrict__ dk, double c,
+                          int N, int M) {
+  const size_t total = (size_t)N * M;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const size_t p = i / M;
+    const int m = (int)(i - p * M);
+    u[i] = g[p];
+    f[i] += c * dk[m + 1] * g[p];
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// setup, FP64: L1 coefficients, inverse columns, twiddles, spectra
+// ---------------------------------------------------------------------------------
+
+// r_1 = c; r_2 = c (2^beta - 2); for i >= 3 the second difference
+//   i^b - 2(i-1)^b + (i-2)^b = (i-1)^b [(1+y)^b + (1-y)^b - 2],  y = 1/(i-1),
+// is summed as its binomial series 2 sum_{k>=1} C(b, 2k) y^{2k}, whose terms all
+// have the sign of C(b, 2) < 0, so no cancellation occurs.  d_m (for the
+// initial-value term) is accumulated by the telescoping sum d_m = sum r_i / c.
+__global__ void k_coefficients(double* __restrict__ r, int M, double alpha, double c) {
+  const double b = 1.0 - alpha;
+  for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < M; i0 += gridDim.x * blockDim.x) {
+    const int i = i0 + 1;
+    double val;
+    if (i == 1) {
+      val = 1.0;
+    } else if (i == 2) {
+      val = exp2(b) - 2.0;
+    } else {
+      const double y = 1.0 / (double)(i - 1);
+      const double y2 = y * y;
+      double term = 0.5 * b * (b - 1.0) * y2;  // C(b,2) y^2
+      double sum = term;
+      for (int k = 1; k < 200; ++k) {
+        // C(b,2k+2)/C(b,2k) = (b-2k)(b-2k-1) / ((2k+1)(2k+2))
+        term *= (b - 2.0 * k) * (b - 2.0 * k - 1.0) / ((2.0 * k + 1.0) * (2.0 * k + 2.0)) * y2;
+        sum += term;
+        if (fabs(term) <= 1e-18 * fabs(sum)) break;
+      }
+      val = 2.0 * sum * pow((double)(i - 1), b);
+    }
+    r[i0] = c * val;
+  }
+}
+
+// d_0 = 0, d_m = d_{m-1} + r_m / c (sequential; setup only).
+__global__ void k_weights_from_column(double* __restrict__ dk, const double* __restrict__ r, int M,
+                                      double c) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    double acc = 0.0;
+    dk[0] = 0.0;
+    for (int m = 1; m <= M; ++m) {
+      acc += r[m - 1] / c;
+      dk[m] = acc;
+    }
+  }
+}
+
+// In-place radix-2 FFT of length N = 2^logN in global memory by one block
+// (bit reversal, then decimation-in-time passes); twiddles from sincospi.
+__device__ void block_fft_radix2(Cx<double>* x, int N, int logN, bool inv) {
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const int rr = (int)(__brev((unsigned)i) >> (32 - logN));
+    if (rr > i) {
+      const Cx<double> tmp = x[i];
+      x[i] = x[rr];
+      x[rr] = tmp;
+    }
+  }
+  __syncthreads();
+  for (int len = 2; len <= N; len <<= 1) {
+    const int half = len >> 1;
+    for (int bidx = threadIdx.x; bidx < N / 2; bidx += blockDim.x) {
+      const int grp = bidx / half, jj = bidx - grp * half;
+      const int i0 = grp * len + jj, i1 = i0 + half;
+      double s, co;
+      sincospi((inv ? 2.0 : -2.0) * (double)jj / (double)len, &s, &co);
+      const Cx<double> w{co, s};
+      const Cx<double> a = x[i0], bb = cmul(x[i1], w);
+      x[i0] = cadd(a, bb);
+      x[i1] = csub(a, bb);
+    }
+    __syncthreads();
+  }
+}
+
+// One block per level.  First column k of (T_M + sigma I)^{-1} by divide and
+// conquer (Sec. 5, smoothing procedure): with a = (r_1 + sigma, r_2, ...),
+// T_{2n}^{-1} = [T_n^{-1} 0; -T_n^{-1} P_n T_n^{-1}  T_n^{-1}], so the new half
+// of the column is k[n..2n) = -(k_n * c)[0..n) with c = (a * k_n)[n..2n), both
+// causal products done as cyclic convolutions of length 2n.  The first
+// 2^p0 = 16 entries come from forward substitution.
+__global__ void k_inverse_columns(double* __restrict__ kcol, const double* __restrict__ r,
+                                  const double* __restrict__ sigma, int M,
+                                  Cx<double>* __restrict__ work) {
+  const int l = blockIdx.x;
+  double* k = kcol + (size_t)l * M;
+  Cx<double>* X = work + (size_t)l * 3 * M;
+  Cx<double>* Y = X + M;
+  Cx<double>* Z = Y + M;
+  const double a0 = r[0] + sigma[l];
+  const int n0 = M < 16 ? M : 16;
+  if (threadIdx.x == 0) {
+    k[0] = 1.0 / a0;
+    for (int m = 1; m < n0; ++m) {
+      double s = 0.0;
+      for (int j = 0; j < m; ++j) s += r[m - j] * k[j];
+      k[m] = -s / a0;
+    }
+  }
+  __syncthreads();
+  for (int nn = n0; nn < M; nn *= 2) {
+    const int N2 = 2 * nn;
+    int logN = 0;
+    while ((1 << logN) < N2) ++logN;
+    const double inv = 1.0 / (double)N2;
+    for (int i = threadIdx.x; i < N2; i += blockDim.x) {
+      X[i] = Cx<double>{i == 0 ? a0 : r[i], 0.0};
+      Y[i] = Cx<double>{i < nn ? k[i] : 0.0, 0.0};
+    }
+    __syncthreads();
+    block_fft_radix2(X, N2, logN, false);
+    block_fft_radix2(Y, N2, logN, false);
+    for (int i = threadIdx.x; i < N2; i += blockDim.x) Z[i] = cmul(X[i], Y[i]);
+    __syncthreads();
+    block_fft_radix2(Z, N2, logN, true);
+    // c = (a * k_n)[n..2n): entries n.. of the cyclic product (no wrap for those)
+    for (int i = threadIdx.x; i < N2; i += blockDim.x)
+      X[i] = Cx<double>{i < nn ? Z[nn + i].x * inv : 0.0, 0.0};
+    __syncthreads();
+    block_fft_radix2(X, N2, logN, false);
+    for (int i = threadIdx.x; i < N2; i += blockDim.x) Z[i] = cmul(X[i], Y[i]);
+    __syncthreads();
+    block_fft_radix2(Z, N2, logN, true);
+    for (int i = threadIdx.x; i < nn; i += blockDim.x) k[nn + i] = -Z[i].x * inv;
+    __syncthreads();
+  }
+}
+
+__global__ void k_twiddles(Cx<double>* __restrict__ tw, int L) {
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < L; m += gridDim.x * blockDim.x) {
+    double s, c;
+    sincospi(-2.0 * (double)m / (double)L, &s, &c);
+    tw[m] = Cx<double>{c, s};
+  }
+}
+
+// Spectrum of one real line per thread group, in the engine's spectral order,
+// scaled by 1/L.
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+    k_spectra(Cx<double>* __restrict__ spec, const double* __restrict__ lines, int count, int M,
+              int logL, const Cx<double>* __restrict__ tw) {
+  extern __shared__ unsigned char smem_raw[];
+  Cx<double>* smem = reinterpret_cast<Cx<double>*>(smem_raw);
+  const FftShape sh(logL);
+  const int TL = sh.L8;
+  const int g = threadIdx.x / TL;
+  const int t = threadIdx.x - g * TL;
+  const int groups = BLOCK / TL;
+  const int line = blockIdx.x * groups + g;
+  const bool valid = line < count;
+  Cx<double>* buf = smem + g * padded_len(sh.L);
+  const double* x = lines + (size_t)(valid ? line : 0) * M;
+  auto load = [&](int m) -> Cx<double> { return Cx<double>{valid ? x[m] : 0.0, 0.0}; };
+  Cx<double> v[8];
+  fft_forward(buf, t, sh, tw, load, v);
+  const double inv = 1.0 / (double)sh.L;
+  if (valid) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      spec[(size_t)line * sh.L + 8 * t + q] = Cx<double>{v[q].x * inv, v[q].y * inv};
+  }
+}
+
+__global__ void k_round_cx(Cx<float>* __restrict__ dst, const Cx<double>* __restrict__ src,
+                           size_t count) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
+       i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = Cx<float>{(float)src[i].x, (float)src[i].y};
+}
+
+// ---------------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------------
+
+namespace {
+
+template <class K>
+cudaError_t prepare_smem(K kernel, size_t smem) {
+  if (smem > 48 * 1024) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  }
+  return cudaSuccess;
+}
+
+inline unsigned elementwise_grid(size_t total) {
+  size_t blocks = (total + 255) / 256;
+  const size_t cap = 152 * 16;
+  return (unsigned)(blocks < 1 ? 1 : (blocks > cap ? cap : blocks));
+}
+
+}  // namespace
+
+template <class R>
+cudaError_t launch_sweep(const R* f, R* u, const Cx<R>* spec, const Cx<R>* tw, int d, int n,
+                         int M, int par, bool all_points, R hinv2, cudaStream_t s) {
+  const int L = 2 * M, logL = ilog2(L);
+  const int npts = all_points ? (d == 1 ? n : n * n) : colour_count(d, n, par);
+  const int npairs = (npts + 1) / 2;
+  if (npairs == 0) return cudaSuccess;
+  const int block = block_threads(L);
+  const int groups = block / (L / 8);
+  const size_t smem = (size_t)groups * padded_len(L) * sizeof(Cx<R>);
+  const unsigned grid = (unsigned)((npairs + groups - 1) / groups);
+  cudaError_t e;
+  switch (block) {
+    case 256:
+      e = prepare_smem(k_sweep<R, 256>, smem);
+      if (e != cudaSuccess) return e;
+      k_sweep<R, 256><<<grid, 256, smem, s>>>(f, u, spec, tw, d, n, M, logL, par, all_points,
+                                              hinv2, npts, npairs);
+      break;
+    case 512:
+      e = prepare_smem(k_sweep<R, 512>, smem);
+      if (e != cudaSuccess) return e;
+      k_sweep<R, 512><<<grid, 512, smem, s>>>(f, u, spec, tw, d, n, M, logL, par, all_points,
+                                              hinv2, npts, npairs);
+      break;
+    default:
+      e = prepare_smem(k_sweep<R, 1024>, smem);
+      if (e != cudaSuccess) return e;
+      k_sweep<R, 1024><<<grid, 1024, smem, s>>>(f, u, spec, tw, d, n, M, logL, par, all_points,
+                                                hinv2, npts, npairs);
+      break;
+  }
+  return counted(cudaGetLastError());
+}
+
+template <class R, class RO>
+cudaError_t launch_defect(const R* u, const R* f, RO* r, const Cx<R>* tspec, const Cx<R>* tw,
+                          int d, int n, int M, R hinv2, unsigned long long* norm_bits,
+                          cudaStream_t s) {
+  const int L = 2 * M, logL = ilog2(L);
+  const int npts = d == 1 ? n : n * n;
+  const int npairs = (npts + 1) / 2;
+  const int block = block_threads(L);
+  const int groups = block / (L / 8);
+  const size_t smem = (size_t)groups * padded_len(L) * sizeof(Cx<R>);
+  const unsigned grid = (unsigned)((npairs + groups - 1) / groups);
+  cudaError_t e;
+  switch (block) {
+    case 256:
+      e = prepare_smem(k_defect<R, RO, 256>, smem);
+      if (e != cudaSuccess) return e;
+      k_defect<R, RO, 256><<<grid, 256, smem, s>>>(u, f, r, tspec, tw, d, n, M, logL, hinv2, npts,
+                                                   npairs, norm_bits);
+      break;
+    case 512:
+      e = prepare_smem(k_defect<R, RO, 512>, smem);
+      if (e != cudaSuccess) return e;
+      k_defect<R, RO, 512><<<grid, 512, smem, s>>>(u, f, r, tspec, tw, d, n, M, logL, hinv2, npts,
+                                                   npairs, norm_bits);
+      break;
+    default:
+      e = prepare_smem(k_defect<R, RO, 1024>, smem);
+      if (e != cudaSuccess) return e;
+      k_defect<R, RO, 1024><<<grid, 1024, smem, s>>>(u, f, r, tspec, tw, d, n, M, logL, hinv2,
+                                                     npts, npairs, norm_bits);
+      break;
+  }
+  return counted(cudaGetLastError());
+}
+
+template <class R>
+cudaError_t launch_restrict(const R* r, R* fc, R* uc, int d, int n, int M, cudaStream_t s) {
+  const int nc = (n - 1) / 2;
+  const size_t total = (size_t)(d == 1 ? nc : nc * nc) * M;
+  if (total == 0) return cudaSuccess;
+  k_restrict<R><<<elementwise_grid(total), 256, 0, s>>>(r, fc, uc, d, n, M, total);
+  return counted(cudaGetLastError());
+}
+
+template <class R>
+cudaError_t launch_prolong(R* u, const R* uc, int d, int n, int M, cudaStream_t s) {
+  const size_t total = (size_t)(d == 1 ? n : n * n) * M;
+  k_prolong<R><<<elementwise_grid(total), 256, 0, s>>>(u, uc, d, n, M, total);
+  return counted(cudaGetLastError());
+}
+
+cudaError_t launch_refine(double* u, const float* e, size_t count, cudaStream_t s) {
+  k_refine<<<elementwise_grid(count), 256, 0, s>>>(u, e, count);
+  return counted(cudaGetLastError());
+}
+
+cudaError_t launch_round(float* dst, const double* src, size_t count, cudaStream_t s) {
+  k_round<<<elementwise_grid(count), 256, 0, s>>>(dst, src, count);
+  return counted(cudaGetLastError());
+}
+
+cudaError_t launch_initial(double* u, double* f, const double* g, const double* dk, double c,
+                           int N, int M, cudaStream_t s) {
+  k_initial<<<elementwise_grid((size_t)N * M), 256, 0, s>>>(u, f, g, dk, c, N, M);
+  return counted(cudaGetLastError());
+}
+
+cudaError_t launch_coefficients(double* r, double* dk, int M, double alpha, double c,
+                                cudaStream_t s) {
+  k_coefficients<<<(M + 255) / 256, 256, 0, s>>>(r, M, alpha, c);
+  cudaError_t e = counted(cudaGetLastError());
+  if (e != cudaSuccess) return e;
+  k_weights_from_column<<<1, 32, 0, s>>>(dk, r, M, c);
+  return counted(cudaGetLastError());
+}
+
+cudaError_t launch_inverse_columns(double* kcol, const double* r, const double* sigma, int nlev,
+                                   int M, Cx<double>* work, cudaStream_t s) {
+  k_inverse_columns<<<nlev, 512, 0, s>>>(kcol, r, sigma, M, work);
+  return counted(cudaGetLastError());
+}
+
+cudaError_t launch_twiddles(Cx<double>* tw, int L, cudaStream_t s) {
+  k_twiddles<<<(L + 255) / 256, 256, 0, s>>>(tw, L);
+  return counted(cudaGetLastError());
+}
+
+cudaError_t launch_spectra(Cx<double>* spec, const double* lines, int count, int M,
+                           const Cx<double>* tw, cudaStream_t s) {
+  const int L = 2 * M, logL = ilog2(L);
+  const int block = block_threads(L);
+  const int groups = block / (L / 8);
+  const size_t smem = (size_t)groups * padded_len(L) * sizeof(Cx<double>);
+  const unsigned grid = (unsigned)((count + groups - 1) / groups);
+  cudaError_t e;
+  switch (block) {
+    case 256:
+      e = prepare_smem(k_spectra<256>, smem);
+      if (e != cudaSuccess) return e;
+      k_spectra<256><<<grid, 256, smem, s>>>(spec, lines, count, M, logL, tw);
+      break;
+    case 512:
+      e = prepare_smem(k_spectra<512>, smem);
+      if (e != cudaSuccess) return e;
+      k_spectra<512><<<grid, 512, smem, s>>>(spec, lines, count, M, logL, tw);
+      break;
+    default:
+      e = prepare_smem(k_spectra<1024>, smem);
+      if (e != cudaSuccess) return e;
+      k_spectra<1024><<<grid, 1024, smem, s>>>(spec, lines, count, M, logL, tw);
+      break;
+  }
+  return counted(cudaGetLastError());
+}
+
+cudaError_t launch_round_cx(Cx<float>* dst, const Cx<double>* src, size_t count, cudaStream_t s) {
+  k_round_cx<<<elementwise_grid(count), 256, 0, s>>>(dst, src, count);
+  return counted(cudaGetLastError());
+}
+
+// explicit instantiations
+template cudaError_t launch_sweep<double>(const double*, double*, const Cx<double>*,
+                                          const Cx<double>*, int, int, int, int, bool, double,
+                                          cudaStream_t);
+template cudaError_t launch_sweep<float>(const float*, float*, const Cx<float>*, const Cx<float>*,
+                                         int, int, int, int, bool, float, cudaStream_t);
+template cudaError_t launch_defect<double, double>(const double*, const double*, double*,
+                                                   const Cx<double>*, const Cx<double>*, int, int,
+                                                   int, double, unsigned long long*, cudaStream_t);
+template cudaError_t launch_defect<double, float>(const double*, const double*, float*,
+                                                  const Cx<double>*, const Cx<double>*, int, int,
+                                                  int, double, unsigned long long*, cudaStream_t);
+template cudaError_t launch_defect<float, float>(const float*, const float*, float*,
+                                                 const Cx<float>*, const Cx<float>*, int, int, int,
+                                                 float, unsigned long long*, cudaStream_t);
+template cudaError_t launch_restrict<double>(const double*, double*, double*, int, int, int,
+                                             cudaStream_t);
+template cudaError_t launch_restrict<float>(const float*, float*, float*, int, int, int,
+                                            cudaStream_t);
+template cudaError_t launch_prolong<double>(double*, const double*, int, int, int, cudaStream_t);
+template cudaError_t launch_prolong<float>(float*, const float*, int, int, int, cudaStream_t);
+
+}  // namespace mgwr

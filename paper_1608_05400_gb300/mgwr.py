@@ -1,0 +1,283 @@
+"""ctypes binding of the MGWR C ABI (include/mgwr.h).
+
+Argument marshalling only: every numerical step runs in the CUDA library
+``libmgwr.so`` built in-tree by ``paper_1608_05400_gb300._build``.  There is
+no fallback: if the library is missing or cannot be loaded, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libmgwr.so")
+
+MGWR_OK = 0
+MGWR_E_INVAL = -1
+MGWR_E_NOMEM = -2
+MGWR_E_TOOBIG = -3
+MGWR_E_NOCONV = -4
+MGWR_E_NUMERIC = -5
+MGWR_E_AGAIN = -6
+MGWR_E_TIMEOUT = -7
+MGWR_E_CUDA = -8
+MGWR_E_STATE = -9
+
+MGWR_FP64, MGWR_MIXED = 0, 1
+MGWR_H64, MGWR_H32 = 64, 32
+MGWR_U, MGWR_F, MGWR_R = 0, 1, 2
+MGWR_RED, MGWR_BLACK = 0, 1
+MGWR_ORDER_TEXT, MGWR_ORDER_TABLE = 0, 1
+
+
+class mgwr_stats(C.Structure):
+    _fields_ = [("cycles", C.c_int), ("outer", C.c_int), ("relres", C.c_double),
+                ("factor", C.c_double), ("seconds", C.c_double)]
+
+
+_h = C.c_void_p
+_dp = C.POINTER(C.c_double)
+_SIGS = {
+    "mgwr_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.POINTER(_h)]),
+    "mgwr_destroy": (C.c_int, [_h]),
+    "mgwr_last_error": (C.c_char_p, [_h]),
+    "mgwr_status_string": (C.c_char_p, [C.c_int]),
+    "mgwr_set_precision": (C.c_int, [_h, C.c_int]),
+    "mgwr_set_order": (C.c_int, [_h, C.c_int]),
+    "mgwr_set_stream": (C.c_int, [_h, C.c_void_p]),
+    "mgwr_set_inner_cycles": (C.c_int, [_h, C.c_int]),
+    "mgwr_set_rhs": (C.c_int, [_h, _dp, _dp]),
+    "mgwr_set_rhs_dev": (C.c_int, [_h, C.c_void_p, C.c_void_p]),
+    "mgwr_set_initial": (C.c_int, [_h, _dp]),
+    "mgwr_solve": (C.c_int, [_h, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, C.POINTER(mgwr_stats)]),
+    "mgwr_residual": (C.c_int, [_h, _dp, _dp]),
+    "mgwr_get_solution": (C.c_int, [_h, _dp]),
+    "mgwr_get_solution_dev": (C.c_int, [_h, C.c_void_p]),
+    "mgwr_num_levels": (C.c_int, [_h, C.POINTER(C.c_int)]),
+    "mgwr_level_n": (C.c_int, [_h, C.c_int, C.POINTER(C.c_int)]),
+    "mgwr_field_set": (C.c_int, [_h, C.c_int, C.c_int, C.c_int, _dp]),
+    "mgwr_field_get": (C.c_int, [_h, C.c_int, C.c_int, C.c_int, _dp]),
+    "mgwr_smooth": (C.c_int, [_h, C.c_int, C.c_int, C.c_int]),
+    "mgwr_defect": (C.c_int, [_h, C.c_int, C.c_int, _dp]),
+    "mgwr_restrict": (C.c_int, [_h, C.c_int, C.c_int]),
+    "mgwr_prolong": (C.c_int, [_h, C.c_int, C.c_int]),
+    "mgwr_coarsest": (C.c_int, [_h, C.c_int]),
+    "mgwr_cycle": (C.c_int, [_h, C.c_int, C.c_int, C.c_int, C.c_int]),
+    "mgwr_toeplitz_column": (C.c_int, [_h, _dp]),
+    "mgwr_inverse_column": (C.c_int, [_h, C.c_int, _dp]),
+    "mgwr_launch_count": (C.c_int, [_h, C.POINTER(C.c_longlong)]),
+    "mgwr_profile": (C.c_int, [_h, C.c_int]),
+    "mgwr_profile_read": (C.c_int, [_h, C.c_int, C.POINTER(C.c_longlong), _dp, _dp]),
+}
+
+KERNEL_CLASSES = ("sweep64", "sweep32", "defect64", "defect32", "restrict", "prolong",
+                  "coarsest", "refine")
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    """Load libmgwr.so (raises OSError / RuntimeError if it is absent)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library not built: {path} (run paper_1608_05400_gb300._build)")
+        lib = C.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def exported_symbols() -> list[str]:
+    return list(_SIGS)
+
+
+class MGWRError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+def _ptr(a: np.ndarray | None):
+    if a is None:
+        return None
+    return a.ctypes.data_as(_dp)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+@dataclass
+class Stats:
+    cycles: int
+    outer: int
+    relres: float
+    factor: float
+    seconds: float
+    status: int
+
+
+class Solver:
+    """One MGWR problem (d, n, M, T, alpha) living on the current CUDA device."""
+
+    def __init__(self, d: int, n: int, M: int, T: float, alpha: float):
+        self.lib = load()
+        self.d, self.n, self.M, self.T, self.alpha = d, n, M, T, alpha
+        self.N = n ** d
+        h = _h()
+        st = self.lib.mgwr_create(d, n, M, T, alpha, C.byref(h))
+        if st != MGWR_OK:
+            raise MGWRError(st, f"mgwr_create({d}, {n}, {M}, {T}, {alpha}) failed: "
+                            + self.lib.mgwr_status_string(st).decode())
+        self.h = h
+
+    # -- plumbing --
+    def _check(self, st: int, what: str, ok=(MGWR_OK,)):
+        if st not in ok:
+            raise MGWRError(st, f"{what}: {self.lib.mgwr_last_error(self.h).decode()}")
+        return st
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mgwr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- configuration --
+    def set_precision(self, prec: int):
+        self._check(self.lib.mgwr_set_precision(self.h, prec), "mgwr_set_precision")
+
+    def set_order(self, order: int):
+        self._check(self.lib.mgwr_set_order(self.h, order), "mgwr_set_order")
+
+    def set_stream(self, stream_ptr: int | None):
+        self._check(self.lib.mgwr_set_stream(self.h, C.c_void_p(stream_ptr or 0)), "mgwr_set_stream")
+
+    def set_inner_cycles(self, k: int):
+        self._check(self.lib.mgwr_set_inner_cycles(self.h, k), "mgwr_set_inner_cycles")
+
+    # -- data --
+    def set_rhs(self, f: np.ndarray, g: np.ndarray | None = None):
+        f = _f64(f)
+        assert f.shape == (self.N, self.M), f.shape
+        g = None if g is None else _f64(g).reshape(self.N)
+        self._check(self.lib.mgwr_set_rhs(self.h, _ptr(f), _ptr(g)), "mgwr_set_rhs")
+
+    def set_rhs_dev(self, f_ptr: int, g_ptr: int | None = None):
+        self._check(self.lib.mgwr_set_rhs_dev(self.h, C.c_void_p(f_ptr), C.c_void_p(g_ptr or 0)),
+                    "mgwr_set_rhs_dev")
+
+    def set_initial(self, u0: np.ndarray):
+        u0 = _f64(u0)
+        assert u0.shape == (self.N, self.M)
+        self._check(self.lib.mgwr_set_initial(self.h, _ptr(u0)), "mgwr_set_initial")
+
+    def solve(self, cycle=1, nu1=1, nu2=1, tol=1e-10, max_cycles=100, allow_noconv=False) -> Stats:
+        st = mgwr_stats()
+        ok = (MGWR_OK, MGWR_E_NOCONV) if allow_noconv else (MGWR_OK,)
+        s = self._check(self.lib.mgwr_solve(self.h, cycle, nu1, nu2, tol, max_cycles, C.byref(st)),
+                        "mgwr_solve", ok)
+        return Stats(st.cycles, st.outer, st.relres, st.factor, st.seconds, s)
+
+    def residual(self, want_field=False):
+        rel = C.c_double()
+        r = np.empty((self.N, self.M)) if want_field else None
+        self._check(self.lib.mgwr_residual(self.h, C.byref(rel), _ptr(r)), "mgwr_residual")
+        return (rel.value, r) if want_field else rel.value
+
+    def solution(self) -> np.ndarray:
+        u = np.empty((self.N, self.M))
+        self._check(self.lib.mgwr_get_solution(self.h, _ptr(u)), "mgwr_get_solution")
+        return u
+
+    def solution_dev(self, u_ptr: int):
+        self._check(self.lib.mgwr_get_solution_dev(self.h, C.c_void_p(u_ptr)), "mgwr_get_solution_dev")
+
+    # -- components --
+    def num_levels(self) -> int:
+        v = C.c_int()
+        self._check(self.lib.mgwr_num_levels(self.h, C.byref(v)), "mgwr_num_levels")
+        return v.value
+
+    def level_n(self, level: int) -> int:
+        v = C.c_int()
+        self._check(self.lib.mgwr_level_n(self.h, level, C.byref(v)), "mgwr_level_n")
+        return v.value
+
+    def field_set(self, hier: int, level: int, which: int, a: np.ndarray):
+        a = _f64(a)
+        nl = self.level_n(level)
+        assert a.shape == (nl ** self.d, self.M), a.shape
+        self._check(self.lib.mgwr_field_set(self.h, hier, level, which, _ptr(a)), "mgwr_field_set")
+
+    def field_get(self, hier: int, level: int, which: int) -> np.ndarray:
+        nl = self.level_n(level)
+        a = np.empty((nl ** self.d, self.M))
+        self._check(self.lib.mgwr_field_get(self.h, hier, level, which, _ptr(a)), "mgwr_field_get")
+        return a
+
+    def smooth(self, hier: int, level: int, colour: int):
+        self._check(self.lib.mgwr_smooth(self.h, hier, level, colour), "mgwr_smooth")
+
+    def defect(self, hier: int, level: int) -> float:
+        v = C.c_double()
+        self._check(self.lib.mgwr_defect(self.h, hier, level, C.byref(v)), "mgwr_defect")
+        return v.value
+
+    def restrict(self, hier: int, level: int):
+        self._check(self.lib.mgwr_restrict(self.h, hier, level), "mgwr_restrict")
+
+    def prolong(self, hier: int, level: int):
+        self._check(self.lib.mgwr_prolong(self.h, hier, level), "mgwr_prolong")
+
+    def coarsest(self, hier: int):
+        self._check(self.lib.mgwr_coarsest(self.h, hier), "mgwr_coarsest")
+
+    def cycle(self, hier: int, cycle=1, nu1=1, nu2=1):
+        self._check(self.lib.mgwr_cycle(self.h, hier, cycle, nu1, nu2), "mgwr_cycle")
+
+    def profile(self, enable: bool):
+        self._check(self.lib.mgwr_profile(self.h, int(enable)), "mgwr_profile")
+
+    def profile_read(self) -> dict:
+        out = {}
+        for k, name in enumerate(KERNEL_CLASSES):
+            n, ms, lines = C.c_longlong(), C.c_double(), C.c_double()
+            self._check(self.lib.mgwr_profile_read(self.h, k, C.byref(n), C.byref(ms), C.byref(lines)),
+                        "mgwr_profile_read")
+            out[name] = dict(launches=n.value, ms=ms.value, lines=lines.value)
+        return out
+
+    def toeplitz_column(self) -> np.ndarray:
+        r = np.empty(self.M)
+        self._check(self.lib.mgwr_toeplitz_column(self.h, _ptr(r)), "mgwr_toeplitz_column")
+        return r
+
+    def inverse_column(self, level: int) -> np.ndarray:
+        k = np.empty(self.M)
+        self._check(self.lib.mgwr_inverse_column(self.h, level, _ptr(k)), "mgwr_inverse_column")
+        return k
+
+
+def launch_count() -> int:
+    v = C.c_longlong()
+    load().mgwr_launch_count(None, C.byref(v))
+    return v.value

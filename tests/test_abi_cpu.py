@@ -1,0 +1,72 @@
+"""CPU-side checks of the C ABI: the library builds, loads, exports every
+function include/mgwr.h declares, and rejects invalid arguments on the host
+(no CUDA work is issued by any call made here)."""
+import ctypes as C
+import os
+import re
+import shutil
+
+import pytest
+
+from paper_1608_05400_gb300 import mgwr
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "mgwr.h")
+
+
+def header_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(mgwr_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(mgwr.LIB_PATH):
+        if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+            pytest.skip("nvcc not available to build the library")
+        from paper_1608_05400_gb300 import _build
+        _build.build()
+    return mgwr.load()
+
+
+def test_library_exports_every_declared_function(lib):
+    declared = header_functions()
+    assert len(declared) >= 25
+    for name in declared:
+        assert hasattr(lib, name), name
+    # the binding wraps exactly the declared set
+    assert sorted(mgwr.exported_symbols()) == declared
+
+
+@pytest.mark.parametrize("args", [
+    (3, 63, 64, 1.0, 0.5),      # d
+    (1, 62, 64, 1.0, 0.5),      # n not 2^k - 1
+    (1, 0, 64, 1.0, 0.5),
+    (2, 8191, 64, 1.0, 0.5),    # n too large in 2-D
+    (1, 63, 48, 1.0, 0.5),      # M not a power of two
+    (1, 63, 2, 1.0, 0.5),       # M too small
+    (1, 63, 8192, 1.0, 0.5),    # M too large
+    (1, 63, 64, 0.0, 0.5),      # T
+    (1, 63, 64, float("inf"), 0.5),
+    (1, 63, 64, 1.0, 0.0),      # alpha
+    (1, 63, 64, 1.0, 1.5),
+    (1, 63, 64, 1.0, float("nan")),
+])
+def test_create_rejects_invalid_arguments_on_host(lib, args):
+    h = C.c_void_p()
+    assert lib.mgwr_create(*args, C.byref(h)) == mgwr.MGWR_E_INVAL
+    assert not h.value
+
+
+def test_null_handle_calls_are_rejected(lib):
+    assert lib.mgwr_solve(None, 1, 1, 1, 1e-10, 10, None) == mgwr.MGWR_E_INVAL
+    assert lib.mgwr_set_precision(None, 0) == mgwr.MGWR_E_INVAL
+    assert lib.mgwr_destroy(None) == mgwr.MGWR_OK
+    assert lib.mgwr_last_error(None) == b"null handle"
+    assert lib.mgwr_create(1, 63, 64, 1.0, 0.5, None) == mgwr.MGWR_E_INVAL
+
+
+def test_status_strings(lib):
+    for code in range(-9, 1):
+        assert lib.mgwr_status_string(code) not in (None, b"unknown status")

@@ -169,6 +169,25 @@ int mgwr_cycle(mgwr_t h, int hier, int cycle, int nu1, int nu2);
 int mgwr_toeplitz_column(mgwr_t h, double* r_host);            /* r_1..r_M   */
 int mgwr_inverse_column(mgwr_t h, int level, double* k_host);  /* k_1..k_M   */
 
+/* Allocation-free variant of the inverse-column setup (the paper has no
+ * counterpart; it serves callers that cannot allocate device memory while
+ * they run, e.g. services that reserve their whole GPU budget at start-up or
+ * forbid allocation after initialisation).  Computes k_1..k_M, the first
+ * column of (T + sigma I)^{-1} for the lower-triangular Toeplitz T with first
+ * column r_1..r_M, by the same divide-and-conquer kernel as mgwr_create, on
+ * `stream` (a cudaStream_t, NULL = legacy default stream).  r_dev and k_dev
+ * are device pointers (M doubles each, caller-owned).  The kernel's scratch
+ * (sigma plus 3*M complex values) is a fixed 196,640-byte array compiled into
+ * the library, which every GPU that loads the library keeps until the process
+ * exits; so M is limited to 4096: larger M returns MGWR_E_TOOBIG, and a bad
+ * pointer, M not a power of two >= 4 or sigma < 0 returns MGWR_E_INVAL.
+ * Nothing is allocated.  The first call on each device looks up the array's
+ * device address (do it before any stream capture).  All calls share the one
+ * array: calls whose work overlaps on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller. */
+int mgwr_inverse_column_noalloc(const double* r_dev, int M, double sigma, double* k_dev,
+                                void* stream);
+
 /* Number of CUDA kernel launches issued through the library so far
  * (process-wide; h may be NULL). */
 int mgwr_launch_count(mgwr_t h, long long* count);

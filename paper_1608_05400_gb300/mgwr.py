@@ -69,6 +69,7 @@ _SIGS = {
     "mgwr_toeplitz_column": (C.c_int, [_h, _dp]),
     "mgwr_inverse_column": (C.c_int, [_h, C.c_int, _dp]),
     "mgwr_launch_count": (C.c_int, [_h, C.POINTER(C.c_longlong)]),
+    "mgwr_inverse_column_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p]),
     "mgwr_profile": (C.c_int, [_h, C.c_int]),
     "mgwr_profile_read": (C.c_int, [_h, C.c_int, C.POINTER(C.c_longlong), _dp, _dp]),
 }

@@ -156,6 +156,13 @@ int mgwr_smooth(mgwr_t h, int hier, int level, int colour);
 /* r = f - (T_M (x) I + A_h) u at `level` (Algorithm 1, defect; Sec. 5
  * circulant-embedding matvec); *norm_inf = max |r| (may be NULL). */
 int mgwr_defect(mgwr_t h, int hier, int level, double* norm_inf);
+/* One smoothing step (red then black half-sweep) at level >= 1, then the
+ * defect of the result into field R without a convolution: the black
+ * half-sweep leaves each black point's equation satisfied, so the defect is 0
+ * there and h^-2 * (sum over the black neighbours of their change) at red
+ * points.  Equal to mgwr_defect after mgwr_smooth(RED), mgwr_smooth(BLACK) up
+ * to rounding; the solver uses it for every defect that follows smoothing. */
+int mgwr_smooth_defect(mgwr_t h, int hier, int level, double* norm_inf);
 /* f_{level-1} = full weighting of r_level; u_{level-1} = 0 (Algorithm 1). */
 int mgwr_restrict(mgwr_t h, int hier, int level);
 /* u_level += linear / bilinear interpolation of u_{level-1} (Algorithm 1). */
@@ -202,7 +209,8 @@ int mgwr_launch_count(mgwr_t h, long long* count);
 #define MGWR_K_PROLONG 5    /* interpolation + correction                       */
 #define MGWR_K_COARSEST 6   /* one-point solves                                 */
 #define MGWR_K_REFINE 7     /* mixed-precision update u64 += e32                */
-#define MGWR_NUM_KERNEL_CLASSES 8
+#define MGWR_K_DEFECT_DELTA 8 /* defect after a smoothing step, no convolution  */
+#define MGWR_NUM_KERNEL_CLASSES 9
 /* enable != 0: from now on every launch of the solver is bracketed by CUDA
  * events on the handle's stream (clears the totals).  Adds event records
  * between launches; meant for a measurement run, not for timed runs. */

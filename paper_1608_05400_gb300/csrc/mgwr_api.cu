@@ -16,9 +16,19 @@ using mgwr::Cx;
 
 namespace {
 
+// What the defect work field r_l of a level currently stands for.
+enum RState {
+  R_STALE = 0,    // nothing known: the defect needs the full (convolution) form
+  R_ZERO_U = 1,   // u_l = 0 (just restricted into): the defect is f_l itself
+  R_DELTA = 2,    // last op was a complete red-black step: defect from its delta
+  R_CURRENT = 3,  // r_l holds the defect of the current (u_l, f_l)
+};
+
 template <class R>
 struct Hier {
   std::vector<R*> u, f, r;        // per level, N_l * M values each
+  std::vector<R*> dl;             // per level: black-point changes of the last step
+  std::vector<int> rs;            // per level: RState of r
   Cx<R>* spec = nullptr;          // nlev * L: spectra of the inverse columns
   Cx<R>* tspec = nullptr;         // L: spectrum of the Toeplitz column
   Cx<R>* tw = nullptr;            // L twiddles
@@ -114,11 +124,19 @@ int alloc_fields(mgwr_t h, Hier<R>& H) {
   H.u.assign(h->nlev, nullptr);
   H.f.assign(h->nlev, nullptr);
   H.r.assign(h->nlev, nullptr);
+  H.dl.assign(h->nlev, nullptr);
+  H.rs.assign(h->nlev, R_STALE);
   for (int l = 0; l < h->nlev; ++l) {
     const size_t bytes = points(h, l) * h->M * sizeof(R);
     MGWR_TRY(dev_alloc(h, &H.u[l], bytes));
     MGWR_TRY(dev_alloc(h, &H.f[l], bytes));
     MGWR_TRY(dev_alloc(h, &H.r[l], bytes));
+    if (l > 0) {
+      // zero-filled once: lines that are never swept black stay finite, so the
+      // zero-weight boundary reads of the defect-from-changes kernel are safe
+      MGWR_TRY(dev_alloc(h, &H.dl[l], bytes));
+      MGWR_CK(h, cudaMemsetAsync(H.dl[l], 0, bytes, h->stream));
+    }
     MGWR_CK(h, cudaMemsetAsync(H.u[l], 0, bytes, h->stream));
     MGWR_CK(h, cudaMemsetAsync(H.f[l], 0, bytes, h->stream));
     MGWR_CK(h, cudaMemsetAsync(H.r[l], 0, bytes, h->stream));
@@ -184,43 +202,91 @@ void prof_collect(mgwr_t h) {
 template <class R>
 int coarsest(mgwr_t h, Hier<R>& H);
 
+// One colour half-sweep at level l >= 1; delta != null also records the change of
+// every swept line (used by the black half-sweep ending a smoothing step).
 template <class R>
-int smooth_colour(mgwr_t h, Hier<R>& H, int l, int colour) {
-  if (l == 0) return coarsest(h, H);  // one point: its half-sweep is the exact solve
+int sweep_colour(mgwr_t h, Hier<R>& H, int l, int colour, R* delta) {
   const int par = parity(h, colour);
   const size_t N = points(h, l);
   const double lines = (double)(par == 0 ? (N + 1) / 2 : N / 2);
   const int pm = prof_begin(h, sizeof(R) == 8 ? MGWR_K_SWEEP64 : MGWR_K_SWEEP32, lines);
-  MGWR_CK(h, mgwr::launch_sweep<R>(H.f[l], H.u[l], H.spec + (size_t)l * h->L, H.tw, h->d,
+  MGWR_CK(h, mgwr::launch_sweep<R>(H.f[l], H.u[l], delta, H.spec + (size_t)l * h->L, H.tw, h->d,
                                     h->nl[l], h->M, par, false, R(h->hinv2[l]), h->stream));
   prof_end(h, pm);
   return MGWR_OK;
 }
 
 template <class R>
-int smooth(mgwr_t h, Hier<R>& H, int l, int steps) {
-  for (int s = 0; s < steps; ++s) {
-    MGWR_TRY(smooth_colour(h, H, l, MGWR_RED));
-    MGWR_TRY(smooth_colour(h, H, l, MGWR_BLACK));
-  }
+int smooth_colour(mgwr_t h, Hier<R>& H, int l, int colour) {
+  if (l == 0) return coarsest(h, H);  // one point: its half-sweep is the exact solve
+  MGWR_TRY(sweep_colour(h, H, l, colour, (R*)nullptr));
+  H.rs[l] = R_STALE;
   return MGWR_OK;
 }
 
+// `steps` red-black smoothing steps; the last black half-sweep records its
+// changes so that the defect that follows needs no convolution.
+template <class R>
+int smooth(mgwr_t h, Hier<R>& H, int l, int steps) {
+  for (int s = 0; s < steps; ++s) {
+    MGWR_TRY(sweep_colour(h, H, l, MGWR_RED, (R*)nullptr));
+    MGWR_TRY(sweep_colour(h, H, l, MGWR_BLACK, s == steps - 1 ? H.dl[l] : (R*)nullptr));
+  }
+  if (steps > 0) H.rs[l] = R_DELTA;
+  return MGWR_OK;
+}
+
+// Full defect r = f - (T_M (x) I + A_h) u with one FFT convolution per line.
 template <class R>
 int defect(mgwr_t h, Hier<R>& H, int l, unsigned long long* norm_bits) {
   const int pm = prof_begin(h, sizeof(R) == 8 ? MGWR_K_DEFECT64 : MGWR_K_DEFECT32, (double)points(h, l));
   MGWR_CK(h, (mgwr::launch_defect<R, R>(H.u[l], H.f[l], H.r[l], H.tspec, H.tw, h->d, h->nl[l],
                                          h->M, R(h->hinv2[l]), norm_bits, h->stream)));
   prof_end(h, pm);
+  H.rs[l] = R_CURRENT;
+  return MGWR_OK;
+}
+
+// Defect of level l from the last smoothing step's changes (no convolution).
+template <class R>
+int defect_from_delta(mgwr_t h, Hier<R>& H, int l, unsigned long long* norm_bits) {
+  const int pm = prof_begin(h, MGWR_K_DEFECT_DELTA, (double)points(h, l));
+  MGWR_CK(h, mgwr::launch_defect_from_delta<R>(H.dl[l], H.r[l], h->d, h->nl[l], h->M,
+                                                parity(h, MGWR_RED), R(h->hinv2[l]), norm_bits,
+                                                h->stream));
+  prof_end(h, pm);
+  H.rs[l] = R_CURRENT;
+  return MGWR_OK;
+}
+
+// Pointer to the defect of level l for the restriction, produced the cheapest
+// way the level's state allows (Algorithm 1, "compute the defect").
+template <class R>
+int current_defect(mgwr_t h, Hier<R>& H, int l, const R** out) {
+  switch (H.rs[l]) {
+    case R_ZERO_U:
+      *out = H.f[l];
+      return MGWR_OK;
+    case R_DELTA:
+      MGWR_TRY(defect_from_delta(h, H, l, nullptr));
+      break;
+    case R_CURRENT:
+      break;
+    default:
+      MGWR_TRY(defect(h, H, l, nullptr));
+      break;
+  }
+  *out = H.r[l];
   return MGWR_OK;
 }
 
 template <class R>
 int coarsest(mgwr_t h, Hier<R>& H) {
   const int pm = prof_begin(h, MGWR_K_COARSEST, 1.0);
-  MGWR_CK(h, mgwr::launch_sweep<R>(H.f[0], H.u[0], H.spec, H.tw, h->d, 1, h->M, 0, true, R(0),
-                                    h->stream));
+  MGWR_CK(h, mgwr::launch_sweep<R>(H.f[0], H.u[0], (R*)nullptr, H.spec, H.tw, h->d, 1, h->M, 0,
+                                    true, R(0), h->stream));
   prof_end(h, pm);
+  H.rs[0] = R_STALE;
   return MGWR_OK;
 }
 
@@ -228,15 +294,18 @@ template <class R>
 int cycle(mgwr_t h, Hier<R>& H, int l, int gamma, int nu1, int nu2) {
   if (l == 0) return coarsest(h, H);
   MGWR_TRY(smooth(h, H, l, nu1));
-  MGWR_TRY(defect(h, H, l, nullptr));
+  const R* r = nullptr;
+  MGWR_TRY(current_defect(h, H, l, &r));
   int pm = prof_begin(h, MGWR_K_RESTRICT, (double)points(h, l - 1));
-  MGWR_CK(h, mgwr::launch_restrict<R>(H.r[l], H.f[l - 1], H.u[l - 1], h->d, h->nl[l], h->M,
+  MGWR_CK(h, mgwr::launch_restrict<R>(r, H.f[l - 1], H.u[l - 1], h->d, h->nl[l], h->M,
                                        h->stream));
   prof_end(h, pm);
+  H.rs[l - 1] = R_ZERO_U;
   for (int g = 0; g < gamma; ++g) MGWR_TRY(cycle(h, H, l - 1, gamma, nu1, nu2));
   pm = prof_begin(h, MGWR_K_PROLONG, (double)points(h, l));
   MGWR_CK(h, mgwr::launch_prolong<R>(H.u[l], H.u[l - 1], h->d, h->nl[l], h->M, h->stream));
   prof_end(h, pm);
+  H.rs[l] = R_STALE;
   MGWR_TRY(smooth(h, H, l, nu2));
   return MGWR_OK;
 }
@@ -264,11 +333,27 @@ int finest_defect_norm(mgwr_t h, double* norm, bool to_h32) {
     MGWR_CK(h, (mgwr::launch_defect<double, float>(h->h64.u[L], h->h64.f[L], h->h32.f[L],
                                                     h->h64.tspec, h->h64.tw, h->d, h->nl[L], h->M,
                                                     h->hinv2[L], h->norm_bits, h->stream)));
+    h->h32.rs[L] = R_STALE;
   } else {
     MGWR_CK(h, (mgwr::launch_defect<double, double>(h->h64.u[L], h->h64.f[L], h->h64.r[L],
                                                      h->h64.tspec, h->h64.tw, h->d, h->nl[L], h->M,
                                                      h->hinv2[L], h->norm_bits, h->stream)));
+    h->h64.rs[L] = R_CURRENT;
   }
+  return read_norm(h, norm);
+}
+
+// FP64 defect norm of the finest level after a cycle: from the last smoothing
+// step's changes when the cycle ended with one, else the full form.
+int finest_cycle_norm(mgwr_t h, double* norm, bool* exact) {
+  const int L = h->nlev - 1;
+  if (h->h64.rs[L] != R_DELTA) {
+    *exact = true;
+    return finest_defect_norm(h, norm, false);
+  }
+  *exact = false;
+  MGWR_CK(h, cudaMemsetAsync(h->norm_bits, 0, sizeof(unsigned long long), h->stream));
+  MGWR_TRY(defect_from_delta(h, h->h64, L, h->norm_bits));
   return read_norm(h, norm);
 }
 
@@ -461,6 +546,7 @@ static int set_rhs_impl(mgwr_t h, const double* f, const double* g, cudaMemcpyKi
     MGWR_CK(h, cudaStreamSynchronize(h->stream));
   }
   h->r0_valid = false;
+  h->h64.rs[L] = R_STALE;
   return MGWR_OK;
 }
 
@@ -480,6 +566,7 @@ int mgwr_set_initial(mgwr_t h, const double* u0) {
                              cudaMemcpyHostToDevice, h->stream));
   MGWR_CK(h, cudaStreamSynchronize(h->stream));
   h->r0_valid = false;
+  h->h64.rs[L] = R_STALE;
   return MGWR_OK;
 }
 
@@ -501,6 +588,7 @@ int mgwr_solve(mgwr_t h, int cyc, int nu1, int nu2, double tol, int max_cycles, 
   double rel = r0 > 0.0 ? norm / r0 : 0.0;
   int status = MGWR_OK;
   int cycles = 0, outer = 0;
+  bool rel_exact = true;  // rel comes from the full defect (not from smoothing changes)
   while (rel > tol) {
     if (!std::isfinite(rel)) {
       status = MGWR_E_NUMERIC;
@@ -513,10 +601,18 @@ int mgwr_solve(mgwr_t h, int cyc, int nu1, int nu2, double tol, int max_cycles, 
     if (!mixed) {
       MGWR_TRY(cycle(h, h->h64, L, cyc, nu1, nu2));
       ++cycles;
-      MGWR_TRY(finest_defect_norm(h, &norm, false));
+      bool exact = false;
+      MGWR_TRY(finest_cycle_norm(h, &norm, &exact));
+      // the stopping decision is always taken on the full defect
+      if (!exact && r0 > 0.0 && norm / r0 <= tol) {
+        MGWR_TRY(finest_defect_norm(h, &norm, false));
+        exact = true;
+      }
+      rel_exact = exact;
     } else {
       const size_t cnt = points(h, L) * h->M;
       MGWR_CK(h, cudaMemsetAsync(h->h32.u[L], 0, cnt * sizeof(float), h->stream));
+      h->h32.rs[L] = R_ZERO_U;  // f32 holds the FP64 defect, e32 = 0
       for (int k = 0; k < h->inner; ++k) {
         MGWR_TRY(cycle(h, h->h32, L, cyc, nu1, nu2));
         ++cycles;
@@ -527,6 +623,10 @@ int mgwr_solve(mgwr_t h, int cyc, int nu1, int nu2, double tol, int max_cycles, 
       MGWR_TRY(finest_defect_norm(h, &norm, true));
     }
     ++outer;
+    rel = r0 > 0.0 ? norm / r0 : 0.0;
+  }
+  if (!rel_exact) {  // report the full defect also when stopping on max_cycles
+    MGWR_TRY(finest_defect_norm(h, &norm, false));
     rel = r0 > 0.0 ? norm / r0 : 0.0;
   }
   if (!std::isfinite(rel)) status = MGWR_E_NUMERIC;
@@ -622,6 +722,10 @@ int mgwr_field_set(mgwr_t h, int hierarchy, int level, int which, const double* 
   }
   MGWR_CK(h, cudaStreamSynchronize(h->stream));
   if (hierarchy == MGWR_H64 && level == h->nlev - 1) h->r0_valid = false;
+  if (hierarchy == MGWR_H64)
+    h->h64.rs[level] = R_STALE;
+  else
+    h->h32.rs[level] = R_STALE;
   return MGWR_OK;
 }
 
@@ -656,6 +760,24 @@ int mgwr_smooth(mgwr_t h, int hierarchy, int level, int colour) {
   return MGWR_OK;
 }
 
+int mgwr_smooth_defect(mgwr_t h, int hierarchy, int level, double* norm_inf) {
+  if (h == nullptr) return MGWR_E_INVAL;
+  MGWR_TRY(check_level(h, hierarchy, level));
+  if (level == 0) return fail(h, MGWR_E_INVAL, "level 0 has a direct solve, not a smoother");
+  MGWR_CK(h, cudaMemsetAsync(h->norm_bits, 0, sizeof(unsigned long long), h->stream));
+  if (hierarchy == MGWR_H64) {
+    MGWR_TRY(smooth(h, h->h64, level, 1));
+    MGWR_TRY(defect_from_delta(h, h->h64, level, h->norm_bits));
+  } else {
+    MGWR_TRY(smooth(h, h->h32, level, 1));
+    MGWR_TRY(defect_from_delta(h, h->h32, level, h->norm_bits));
+  }
+  double nrm = 0.0;
+  MGWR_TRY(read_norm(h, &nrm));
+  if (norm_inf != nullptr) *norm_inf = nrm;
+  return MGWR_OK;
+}
+
 int mgwr_defect(mgwr_t h, int hierarchy, int level, double* norm_inf) {
   if (h == nullptr) return MGWR_E_INVAL;
   MGWR_TRY(check_level(h, hierarchy, level));
@@ -677,9 +799,11 @@ int mgwr_restrict(mgwr_t h, int hierarchy, int level) {
   if (hierarchy == MGWR_H64) {
     MGWR_CK(h, mgwr::launch_restrict<double>(h->h64.r[level], h->h64.f[level - 1],
                                               h->h64.u[level - 1], h->d, h->nl[level], h->M, h->stream));
+    h->h64.rs[level - 1] = R_ZERO_U;
   } else {
     MGWR_CK(h, mgwr::launch_restrict<float>(h->h32.r[level], h->h32.f[level - 1],
                                              h->h32.u[level - 1], h->d, h->nl[level], h->M, h->stream));
+    h->h32.rs[level - 1] = R_ZERO_U;
   }
   MGWR_CK(h, cudaStreamSynchronize(h->stream));
   return MGWR_OK;
@@ -692,9 +816,11 @@ int mgwr_prolong(mgwr_t h, int hierarchy, int level) {
   if (hierarchy == MGWR_H64) {
     MGWR_CK(h, mgwr::launch_prolong<double>(h->h64.u[level], h->h64.u[level - 1], h->d, h->nl[level],
                                              h->M, h->stream));
+    h->h64.rs[level] = R_STALE;
   } else {
     MGWR_CK(h, mgwr::launch_prolong<float>(h->h32.u[level], h->h32.u[level - 1], h->d, h->nl[level],
                                             h->M, h->stream));
+    h->h32.rs[level] = R_STALE;
   }
   MGWR_CK(h, cudaStreamSynchronize(h->stream));
   return MGWR_OK;

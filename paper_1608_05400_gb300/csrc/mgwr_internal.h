@@ -25,10 +25,18 @@ struct alignas(2 * sizeof(R)) Cx {
 // One colour half-sweep (Sec. 3 Eq. red-black, Sec. 6 Eq. red-black_2d): for
 // each point p of parity `par`, u_p = k * (f_p + hinv2 * sum of neighbour
 // lines), k the inverse column whose spectrum is `spec`.  all_points: every
-// point, no neighbour term (one-point coarsest solve).
+// point, no neighbour term (one-point coarsest solve).  delta != null: also
+// delta_p = u_p(new) - u_p(old) on the swept lines.
 template <class R>
-cudaError_t launch_sweep(const R* f, R* u, const Cx<R>* spec, const Cx<R>* tw, int d, int n,
-                         int M, int par, bool all_points, R hinv2, cudaStream_t s);
+cudaError_t launch_sweep(const R* f, R* u, R* delta, const Cx<R>* spec, const Cx<R>* tw, int d,
+                         int n, int M, int par, bool all_points, R hinv2, cudaStream_t s);
+
+// Defect after a red-black step from the black half-sweep's delta: r = 0 on the
+// black points, r = hinv2 * sum of neighbour deltas on the red points
+// (parity red_par); |r|_inf folded into *norm_bits when non-null.
+template <class R>
+cudaError_t launch_defect_from_delta(const R* delta, R* r, int d, int n, int M, int red_par,
+                                     R hinv2, unsigned long long* norm_bits, cudaStream_t s);
 
 // r = f - T_M u - A_h u for all points; |r|_inf folded into *norm_bits
 // (bit pattern of a non-negative double, atomicMax) when norm_bits != null.

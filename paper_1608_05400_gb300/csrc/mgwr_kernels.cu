@@ -76,15 +76,27 @@ __device__ __forceinline__ R neighbour_sum(const R* __restrict__ u, int d, int n
   return s;
 }
 
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long* bits, double v) {
+  // non-negative doubles order like their bit patterns; NaN (all exponent bits
+  // set, non-zero mantissa) compares above +inf and so propagates
+  atomicMax(bits, (unsigned long long)__double_as_longlong(v));
+}
+
+template <class R>
+__device__ __forceinline__ R absmax_nan(R a, R b) {
+  // max that lets NaN win
+  return (a != a || a > b) ? a : b;
+}
+
 // ---------------------------------------------------------------------------------
 // smoother: one colour half-sweep (Sec. 3 Eq. red-black, Sec. 6 Eq. red-black_2d)
 // ---------------------------------------------------------------------------------
 
 template <class R, int BLOCK>
 __global__ void __launch_bounds__(BLOCK)
-    k_sweep(const R* __restrict__ f, R* __restrict__ u, const Cx<R>* __restrict__ spec,
-            const Cx<R>* __restrict__ tw, int d, int n, int M, int logL, int par, int all_points,
-            R hinv2, int npts, int npairs) {
+    k_sweep(const R* __restrict__ f, R* __restrict__ u, R* __restrict__ delta,
+            const Cx<R>* __restrict__ spec, const Cx<R>* __restrict__ tw, int d, int n, int M,
+            int logL, int par, int all_points, R hinv2, int npts, int npairs) {
   extern __shared__ unsigned char smem_raw[];
   Cx<R>* smem = reinterpret_cast<Cx<R>*>(smem_raw);
   const FftShape sh(logL);
@@ -128,28 +140,90 @@ __global__ void __launch_bounds__(BLOCK)
   for (int q = 0; q < 8; ++q) v[q] = cmul(v[q], spec[8 * t + q]);
   auto store = [&](int m, Cx<R> y) {
     if (valid) {
+      if (delta != nullptr) delta[pAM + m] = y.x - u[pAM + m];
       u[pAM + m] = y.x;
-      if (hasB) u[pBM + m] = y.y;
+      if (hasB) {
+        if (delta != nullptr) delta[pBM + m] = y.y - u[pBM + m];
+        u[pBM + m] = y.y;
+      }
     }
   };
   fft_inverse(buf, t, sh, tw, v, store);
 }
 
+// Line-wise kernels: a group of TPL threads owns one time line (TPL = min(128,
+// M/2), 128 / TPL lines per 128-thread block); each thread handles two
+// consecutive time values per step.  Index arithmetic is done once per line.
+struct LineMap {
+  int line, m0, step;
+  __device__ __forceinline__ LineMap(int log_tpl) {
+    const int tpl = 1 << log_tpl;
+    line = blockIdx.x * (128 >> log_tpl) + (threadIdx.x >> log_tpl);
+    m0 = 2 * (threadIdx.x & (tpl - 1));
+    step = 2 * tpl;
+  }
+};
+
+template <class R>
+__device__ __forceinline__ void block_absmax(double amax, unsigned long long* norm_bits) {
+  __shared__ double red[4];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) amax = absmax_nan(__shfl_xor_sync(0xffffffffu, amax, o), amax);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = amax;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    amax = absmax_nan(absmax_nan(red[0], red[1]), absmax_nan(red[2], red[3]));
+    atomic_max_nonneg(norm_bits, amax);
+  }
+}
+
+// Defect right after a complete red-black smoothing step, without a
+// convolution.  The second (black) half-sweep left every black point solving
+// its own equation exactly, so the defect is 0 there; at a red point the
+// equation was solved with the old black neighbours, so its defect is
+// h^-2 * sum over its black neighbours of (new - old) = h^-2 sum delta.
+template <class R>
+__global__ void __launch_bounds__(128)
+    k_defect_from_delta(const R* __restrict__ delta, R* __restrict__ r, int d, int n, int M,
+                        int log_tpl, int npts, int red_par, R hinv2,
+                        unsigned long long* __restrict__ norm_bits) {
+  const LineMap lm(log_tpl);
+  double amax = 0.0;
+  if (lm.line < npts) {
+    const int p = lm.line;
+    const int i = d == 1 ? p : p % n, j = d == 1 ? 0 : p / n;
+    const int par = d == 1 ? (i & 1) : ((i + j) & 1);
+    R* rp = r + (size_t)p * M;
+    if (par != red_par) {
+      for (int m = lm.m0; m < M; m += lm.step) {
+        rp[m] = R(0);
+        rp[m + 1] = R(0);
+      }
+    } else {
+      // neighbour lines; out-of-grid neighbours read the line itself with weight 0
+      const size_t pM = (size_t)p * M, nM = (size_t)n * M;
+      const R* w = delta + (i > 0 ? pM - M : pM);
+      const R* e = delta + (i < n - 1 ? pM + M : pM);
+      const R* so = delta + (d == 2 && j > 0 ? pM - nM : pM);
+      const R* no = delta + (d == 2 && j < n - 1 ? pM + nM : pM);
+      const R cw = i > 0 ? hinv2 : R(0), ce = i < n - 1 ? hinv2 : R(0);
+      const R cs = d == 2 && j > 0 ? hinv2 : R(0), cn = d == 2 && j < n - 1 ? hinv2 : R(0);
+      for (int m = lm.m0; m < M; m += lm.step) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const R v = cw * w[m + k] + ce * e[m + k] + cs * so[m + k] + cn * no[m + k];
+          rp[m + k] = v;
+          amax = absmax_nan((double)fabs(v), amax);
+        }
+      }
+    }
+  }
+  if (norm_bits != nullptr) block_absmax<R>(amax, norm_bits);
+}
+
 // ---------------------------------------------------------------------------------
 // defect r = f - (T_M (x) I + A_h) u  (Algorithm 1; Sec. 5 circulant-embedding matvec)
 // ---------------------------------------------------------------------------------
-
-__device__ __forceinline__ void atomic_max_nonneg(unsigned long long* bits, double v) {
-  // non-negative doubles order like their bit patterns; NaN (all exponent bits
-  // set, non-zero mantissa) compares above +inf and so propagates
-  atomicMax(bits, (unsigned long long)__double_as_longlong(v));
-}
-
-template <class R>
-__device__ __forceinline__ R absmax_nan(R a, R b) {
-  // max that lets NaN win
-  return (a != a || a > b) ? a : b;
-}
 
 template <class R, class RO, int BLOCK>
 __global__ void __launch_bounds__(BLOCK)
@@ -223,68 +297,96 @@ __global__ void __launch_bounds__(BLOCK)
 
 // Full weighting, (1/4)[1 2 1] per dimension; also clears the coarse correction.
 template <class R>
-__global__ void k_restrict(const R* __restrict__ r, R* __restrict__ fc, R* __restrict__ uc, int d,
-                           int n, int M, size_t total) {
+__global__ void __launch_bounds__(128)
+    k_restrict(const R* __restrict__ r, R* __restrict__ fc, R* __restrict__ uc, int d, int n, int M,
+               int log_tpl, int ncpts) {
+  const LineMap lm(log_tpl);
+  if (lm.line >= ncpts) return;
   const int nc = (n - 1) / 2;
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (size_t)gridDim.x * blockDim.x) {
-    const size_t P = idx / M;
-    const int m = (int)(idx - P * M);
-    R acc;
-    if (d == 1) {
-      const size_t c = (2 * P + 1) * (size_t)M + m;
-      acc = R(0.25) * (r[c - M] + R(2) * r[c] + r[c + M]);
-    } else {
-      const int I = (int)(P % nc), J = (int)(P / nc);
-      const size_t c = ((size_t)(2 * I + 1) + (size_t)(2 * J + 1) * n) * M + m;
-      const size_t nM = (size_t)n * M;
-      const R row_m = r[c - nM - M] + R(2) * r[c - nM] + r[c - nM + M];
-      const R row_0 = r[c - M] + R(2) * r[c] + r[c + M];
-      const R row_p = r[c + nM - M] + R(2) * r[c + nM] + r[c + nM + M];
-      acc = R(0.0625) * (row_m + R(2) * row_0 + row_p);
+  const int P = lm.line;
+  R* fo = fc + (size_t)P * M;
+  R* uo = uc + (size_t)P * M;
+  if (d == 1) {
+    const R* c = r + (size_t)(2 * P + 1) * M;
+    for (int m = lm.m0; m < M; m += lm.step) {
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        fo[m + k] = R(0.25) * (c[m + k - M] + R(2) * c[m + k] + c[m + k + M]);
+        uo[m + k] = R(0);
+      }
     }
-    fc[idx] = acc;
-    uc[idx] = R(0);
+  } else {
+    const int I = P % nc, J = P / nc;
+    const size_t nM = (size_t)n * M;
+    // centre line of the 3 x 3 fine stencil and the rows below / above it
+    const R* c = r + ((size_t)(2 * I + 1) + (size_t)(2 * J + 1) * n) * M;
+    const R* cs = c - nM;
+    const R* cn = c + nM;
+    for (int m = lm.m0; m < M; m += lm.step) {
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int q = m + k;
+        const R row_m = cs[q - M] + R(2) * cs[q] + cs[q + M];
+        const R row_0 = c[q - M] + R(2) * c[q] + c[q + M];
+        const R row_p = cn[q - M] + R(2) * cn[q] + cn[q + M];
+        fo[q] = R(0.0625) * (row_m + R(2) * row_0 + row_p);
+        uo[q] = R(0);
+      }
+    }
   }
 }
 
-// 1-D interpolation weights of fine index i from coarse indices (zero outside).
-__device__ __forceinline__ int interp_taps(int i, int nc, int* idx, float* w) {
-  if (i & 1) {  // fine 2J+1 coincides with coarse J
-    idx[0] = (i - 1) >> 1;
-    w[0] = 1.f;
-    return 1;
+// 1-D interpolation taps of fine index i from the coarse grid (nc points):
+// fine 2J+1 takes coarse J; fine 2J takes the mean of coarse J-1 and J; coarse
+// indices outside the grid get weight 0 (and point at a valid line).
+struct Taps {
+  int i0, i1;
+  float w0, w1;
+  __device__ __forceinline__ Taps(int i, int nc) {
+    if (i & 1) {
+      i0 = i1 = (i - 1) >> 1;
+      w0 = 1.f;
+      w1 = 0.f;
+    } else {
+      const int J = i >> 1;
+      i0 = J - 1 >= 0 ? J - 1 : 0;
+      w0 = J - 1 >= 0 ? 0.5f : 0.f;
+      i1 = J < nc ? J : nc - 1;
+      w1 = J < nc ? 0.5f : 0.f;
+    }
   }
-  int k = 0;
-  const int J = i >> 1;  // fine 2J: mean of coarse J-1 and J
-  if (J - 1 >= 0) { idx[k] = J - 1; w[k] = 0.5f; ++k; }
-  if (J < nc) { idx[k] = J; w[k] = 0.5f; ++k; }
-  return k;
-}
+};
 
 template <class R>
-__global__ void k_prolong(R* __restrict__ u, const R* __restrict__ uc, int d, int n, int M,
-                          size_t total) {
+__global__ void __launch_bounds__(128)
+    k_prolong(R* __restrict__ u, const R* __restrict__ uc, int d, int n, int M, int log_tpl,
+              int npts) {
+  const LineMap lm(log_tpl);
+  if (lm.line >= npts) return;
   const int nc = (n - 1) / 2;
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (size_t)gridDim.x * blockDim.x) {
-    const size_t p = idx / M;
-    const int m = (int)(idx - p * M);
-    int ix[2], jy[2];
-    float wx[2], wy[2];
-    R acc = R(0);
-    if (d == 1) {
-      const int kx = interp_taps((int)p, nc, ix, wx);
-      for (int a = 0; a < kx; ++a) acc += R(wx[a]) * uc[(size_t)ix[a] * M + m];
-    } else {
-      const int i = (int)(p % n), j = (int)(p / n);
-      const int kx = interp_taps(i, nc, ix, wx);
-      const int ky = interp_taps(j, nc, jy, wy);
-      for (int b = 0; b < ky; ++b)
-        for (int a = 0; a < kx; ++a)
-          acc += R(wx[a] * wy[b]) * uc[((size_t)ix[a] + (size_t)jy[b] * nc) * M + m];
+  const int p = lm.line;
+  R* up = u + (size_t)p * M;
+  if (d == 1) {
+    const Taps tx(p, nc);
+    const R* a = uc + (size_t)tx.i0 * M;
+    const R* b = uc + (size_t)tx.i1 * M;
+    const R wa = R(tx.w0), wb = R(tx.w1);
+    for (int m = lm.m0; m < M; m += lm.step) {
+#pragma unroll
+      for (int k = 0; k < 2; ++k) up[m + k] += wa * a[m + k] + wb * b[m + k];
     }
-    u[idx] += acc;
+  } else {
+    const Taps tx(p % n, nc), ty(p / n, nc);
+    const R* a = uc + ((size_t)tx.i0 + (size_t)ty.i0 * nc) * M;
+    const R* b = uc + ((size_t)tx.i1 + (size_t)ty.i0 * nc) * M;
+    const R* c = uc + ((size_t)tx.i0 + (size_t)ty.i1 * nc) * M;
+    const R* e = uc + ((size_t)tx.i1 + (size_t)ty.i1 * nc) * M;
+    const R wa = R(tx.w0 * ty.w0), wb = R(tx.w1 * ty.w0), wc = R(tx.w0 * ty.w1), we = R(tx.w1 * ty.w1);
+    for (int m = lm.m0; m < M; m += lm.step) {
+#pragma unroll
+      for (int k = 0; k < 2; ++k)
+        up[m + k] += wa * a[m + k] + wb * b[m + k] + wc * c[m + k] + we * e[m + k];
+    }
   }
 }
 
@@ -508,8 +610,8 @@ inline unsigned elementwise_grid(size_t total) {
 }  // namespace
 
 template <class R>
-cudaError_t launch_sweep(const R* f, R* u, const Cx<R>* spec, const Cx<R>* tw, int d, int n,
-                         int M, int par, bool all_points, R hinv2, cudaStream_t s) {
+cudaError_t launch_sweep(const R* f, R* u, R* delta, const Cx<R>* spec, const Cx<R>* tw, int d,
+                         int n, int M, int par, bool all_points, R hinv2, cudaStream_t s) {
   const int L = 2 * M, logL = ilog2(L);
   const int npts = all_points ? (d == 1 ? n : n * n) : colour_count(d, n, par);
   const int npairs = (npts + 1) / 2;
@@ -523,19 +625,19 @@ cudaError_t launch_sweep(const R* f, R* u, const Cx<R>* spec, const Cx<R>* tw, i
     case 256:
       e = prepare_smem(k_sweep<R, 256>, smem);
       if (e != cudaSuccess) return e;
-      k_sweep<R, 256><<<grid, 256, smem, s>>>(f, u, spec, tw, d, n, M, logL, par, all_points,
+      k_sweep<R, 256><<<grid, 256, smem, s>>>(f, u, delta, spec, tw, d, n, M, logL, par, all_points,
                                               hinv2, npts, npairs);
       break;
     case 512:
       e = prepare_smem(k_sweep<R, 512>, smem);
       if (e != cudaSuccess) return e;
-      k_sweep<R, 512><<<grid, 512, smem, s>>>(f, u, spec, tw, d, n, M, logL, par, all_points,
+      k_sweep<R, 512><<<grid, 512, smem, s>>>(f, u, delta, spec, tw, d, n, M, logL, par, all_points,
                                               hinv2, npts, npairs);
       break;
     default:
       e = prepare_smem(k_sweep<R, 1024>, smem);
       if (e != cudaSuccess) return e;
-      k_sweep<R, 1024><<<grid, 1024, smem, s>>>(f, u, spec, tw, d, n, M, logL, par, all_points,
+      k_sweep<R, 1024><<<grid, 1024, smem, s>>>(f, u, delta, spec, tw, d, n, M, logL, par, all_points,
                                                 hinv2, npts, npairs);
       break;
   }
@@ -577,19 +679,46 @@ cudaError_t launch_defect(const R* u, const R* f, RO* r, const Cx<R>* tspec, con
   return counted(cudaGetLastError());
 }
 
+// Launch geometry of the line-wise kernels: log2 of the threads per line and
+// the number of 128-thread blocks for `lines` lines.
+inline void line_grid(int M, int lines, int* log_tpl, unsigned* blocks) {
+  const int tpl = M / 2 < 128 ? M / 2 : 128;
+  *log_tpl = ilog2(tpl);
+  const int lpb = 128 / tpl;
+  *blocks = (unsigned)((lines + lpb - 1) / lpb);
+}
+
+template <class R>
+cudaError_t launch_defect_from_delta(const R* delta, R* r, int d, int n, int M, int red_par, R hinv2,
+                                     unsigned long long* norm_bits, cudaStream_t s) {
+  const int npts = d == 1 ? n : n * n;
+  int log_tpl;
+  unsigned blocks;
+  line_grid(M, npts, &log_tpl, &blocks);
+  k_defect_from_delta<R><<<blocks, 128, 0, s>>>(delta, r, d, n, M, log_tpl, npts, red_par, hinv2,
+                                                norm_bits);
+  return counted(cudaGetLastError());
+}
+
 template <class R>
 cudaError_t launch_restrict(const R* r, R* fc, R* uc, int d, int n, int M, cudaStream_t s) {
   const int nc = (n - 1) / 2;
-  const size_t total = (size_t)(d == 1 ? nc : nc * nc) * M;
-  if (total == 0) return cudaSuccess;
-  k_restrict<R><<<elementwise_grid(total), 256, 0, s>>>(r, fc, uc, d, n, M, total);
+  const int ncpts = d == 1 ? nc : nc * nc;
+  if (ncpts == 0) return cudaSuccess;
+  int log_tpl;
+  unsigned blocks;
+  line_grid(M, ncpts, &log_tpl, &blocks);
+  k_restrict<R><<<blocks, 128, 0, s>>>(r, fc, uc, d, n, M, log_tpl, ncpts);
   return counted(cudaGetLastError());
 }
 
 template <class R>
 cudaError_t launch_prolong(R* u, const R* uc, int d, int n, int M, cudaStream_t s) {
-  const size_t total = (size_t)(d == 1 ? n : n * n) * M;
-  k_prolong<R><<<elementwise_grid(total), 256, 0, s>>>(u, uc, d, n, M, total);
+  const int npts = d == 1 ? n : n * n;
+  int log_tpl;
+  unsigned blocks;
+  line_grid(M, npts, &log_tpl, &blocks);
+  k_prolong<R><<<blocks, 128, 0, s>>>(u, uc, d, n, M, log_tpl, npts);
   return counted(cudaGetLastError());
 }
 
@@ -663,11 +792,16 @@ cudaError_t launch_round_cx(Cx<float>* dst, const Cx<double>* src, size_t count,
 }
 
 // explicit instantiations
-template cudaError_t launch_sweep<double>(const double*, double*, const Cx<double>*,
+template cudaError_t launch_sweep<double>(const double*, double*, double*, const Cx<double>*,
                                           const Cx<double>*, int, int, int, int, bool, double,
                                           cudaStream_t);
-template cudaError_t launch_sweep<float>(const float*, float*, const Cx<float>*, const Cx<float>*,
-                                         int, int, int, int, bool, float, cudaStream_t);
+template cudaError_t launch_sweep<float>(const float*, float*, float*, const Cx<float>*,
+                                         const Cx<float>*, int, int, int, int, bool, float,
+                                         cudaStream_t);
+template cudaError_t launch_defect_from_delta<double>(const double*, double*, int, int, int, int,
+                                                      double, unsigned long long*, cudaStream_t);
+template cudaError_t launch_defect_from_delta<float>(const float*, float*, int, int, int, int, float,
+                                                     unsigned long long*, cudaStream_t);
 template cudaError_t launch_defect<double, double>(const double*, const double*, double*,
                                                    const Cx<double>*, const Cx<double>*, int, int,
                                                    int, double, unsigned long long*, cudaStream_t);

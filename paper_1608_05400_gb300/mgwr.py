@@ -62,6 +62,7 @@ _SIGS = {
     "mgwr_field_get": (C.c_int, [_h, C.c_int, C.c_int, C.c_int, _dp]),
     "mgwr_smooth": (C.c_int, [_h, C.c_int, C.c_int, C.c_int]),
     "mgwr_defect": (C.c_int, [_h, C.c_int, C.c_int, _dp]),
+    "mgwr_smooth_defect": (C.c_int, [_h, C.c_int, C.c_int, _dp]),
     "mgwr_restrict": (C.c_int, [_h, C.c_int, C.c_int]),
     "mgwr_prolong": (C.c_int, [_h, C.c_int, C.c_int]),
     "mgwr_coarsest": (C.c_int, [_h, C.c_int]),
@@ -75,7 +76,7 @@ _SIGS = {
 }
 
 KERNEL_CLASSES = ("sweep64", "sweep32", "defect64", "defect32", "restrict", "prolong",
-                  "coarsest", "refine")
+                  "coarsest", "refine", "defect_delta")
 
 _lib = None
 
@@ -241,6 +242,11 @@ class Solver:
     def defect(self, hier: int, level: int) -> float:
         v = C.c_double()
         self._check(self.lib.mgwr_defect(self.h, hier, level, C.byref(v)), "mgwr_defect")
+        return v.value
+
+    def smooth_defect(self, hier: int, level: int) -> float:
+        v = C.c_double()
+        self._check(self.lib.mgwr_smooth_defect(self.h, hier, level, C.byref(v)), "mgwr_smooth_defect")
         return v.value
 
     def restrict(self, hier: int, level: int):

@@ -123,6 +123,33 @@ def test_defect(hier, d, n, M):
 
 
 @pytest.mark.parametrize("hier", [G.MGWR_H64, G.MGWR_H32])
+@pytest.mark.parametrize("d,n,M", [(1, 63, 64), (2, 31, 256), (2, 15, 8), (1, 7, 4096)])
+@pytest.mark.parametrize("order", [G.MGWR_ORDER_TEXT, G.MGWR_ORDER_TABLE])
+def test_defect_after_smoothing_step_without_convolution(hier, d, n, M, order):
+    # one red-black step, then the defect from the black changes, against the oracle's
+    # two half-sweeps followed by its direct-sum defect
+    s, W = _setup(d, n, M, hier=hier, order=order)
+    with s:
+        for l in range(1, s.num_levels()):
+            N = s.level_n(l) ** d
+            u = inputs.random_field(N, M, seed=80 + l)
+            f = inputs.random_field(N, M, seed=90 + l, scale=W.levels[l].sigma)
+            s.field_set(hier, l, G.MGWR_U, u)
+            s.field_set(hier, l, G.MGWR_F, f)
+            nrm = s.smooth_defect(hier, l)
+            ref_u = u.copy()
+            W.smooth(l, ref_u, f, 1)
+            ref_r = W.defect(l, ref_u, f)
+            got = s.field_get(hier, l, G.MGWR_R)
+            scale = np.abs(f).max() + W.levels[l].sigma * 2 * np.abs(ref_u).max()
+            tol = TOL64 if hier == G.MGWR_H64 else TOL32
+            assert np.abs(got - ref_r).max() <= tol * scale, (l, np.abs(got - ref_r).max() / scale)
+            assert rel(s.field_get(hier, l, G.MGWR_U), ref_u) <= tol
+            if hier == G.MGWR_H64:
+                assert nrm == np.abs(got).max()
+
+
+@pytest.mark.parametrize("hier", [G.MGWR_H64, G.MGWR_H32])
 @pytest.mark.parametrize("d,n,M", [(1, 63, 64), (2, 31, 32), (2, 15, 4)])
 def test_restrict_and_prolong(hier, d, n, M):
     s, W = _setup(d, n, M, hier=hier)

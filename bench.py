@@ -1,14 +1,18 @@
 """Benchmark: space-time unknowns per second of MGWR solves on GB300.
 
-Workload (one "step" = one complete solve): 2-D plain MGWR, 255 x 255 interior
-grid, M = 1024 time steps on (0, 1], alpha = 0.5, exact solution
+Default workload (one "step" = one complete solve): 2-D plain MGWR, 255 x 255
+interior grid, M = 1024 time steps on (0, 1], alpha = 0.5, exact solution
 u = t^2 sin(pi x) sin(pi y) (f from D^a t^2 = 2 t^(2-a) / Gamma(3-a)),
 5-point Laplacian, V(1,1) red-black cycles from u = 0 until the relative
 infinity-norm defect is below 1e-10, FP64.  6.66e7 space-time unknowns; each
 FP64 field is 533 MB, larger than the 129 MB L2, so no flush is needed
-between steps.
+between steps.  Other workloads (--workload): c1 (1-D 63 points, M = 64),
+c3 (2-D 511 x 511, M = 4096, u = t^alpha sin sin, mixed to 1e-8) and c5a
+(4096 independent 2-D 63 x 63, M = 256 solves with alpha ~ U[0.1, 0.9] in one
+batched handle, mixed to 1e-8).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+                  [--workload c2|c1|c3|c5a]
   python bench.py --impl reference ...   (the CPU oracle on the host cores)
 
 Prints one JSON line.  Multi-GPU runs (torchrun, one rank per GPU) are
@@ -35,6 +39,16 @@ import numpy as np  # noqa: E402
 D, NPTS, M, T, ALPHA, TOL = 2, 255, 1024, 1.0, 0.5, 1e-10
 NU1, NU2, CYCLE = 1, 1, 1
 METRIC = "space-time unknowns/s to rel-res 1e-10 (FP64 vs mixed)"
+# workload name -> (d, n, M, batch, exact solution, tolerance, default precision, description)
+WORKLOADS = {
+    "c2": (2, 255, 1024, 1, "t2", 1e-10, "fp64",
+           "2-D plain MGWR 255x255 interior, M=1024 on (0,1], u=t^2 sin(pi x) sin(pi y)"),
+    "c1": (1, 63, 64, 1, "t2", 1e-10, "fp64", "1-D plain MGWR 63 interior points, M=64, u=t^2 sin(pi x)"),
+    "c3": (2, 511, 4096, 1, "talpha", 1e-8, "mixed",
+           "2-D MGWR 511x511 interior, M=4096, u=t^alpha sin(pi x) sin(pi y)"),
+    "c5a": (2, 63, 256, 4096, "t2", 1e-8, "mixed",
+            "4096 independent 2-D 63x63, M=256 solves, alpha~U[0.1,0.9] (seed 1608), one batched handle"),
+}
 UNIT = "unknowns/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP64 issue rate of a GB300 SM: 2 FP64 FMA per clock (measured with an FMA
@@ -49,7 +63,8 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    p.add_argument("--precision", default=None, choices=["fp64", "mixed"])
+    p.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     p.add_argument("--alpha", type=float, default=ALPHA)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
@@ -141,12 +156,12 @@ def defect_flops_per_line(d: int, Mv: int) -> float:
     return 0.5 * (2 * 5 * L * math.log2(L) + 6 * L) + (2 * d + 4) * Mv
 
 
-def roofline_from_profile(prof: dict, prec: str, pk: dict) -> dict:
+def roofline_from_profile(prof: dict, d: int, M: int, pk: dict) -> dict:
     dom = max(prof, key=lambda k: prof[k]["ms"])
     p = prof[dom]
     sm_max = float(pk.get("sm_max_mhz", 2070.0))
     if dom in ("sweep64", "defect64"):
-        per_line = sweep_flops_per_line(D, M) if dom == "sweep64" else defect_flops_per_line(D, M)
+        per_line = sweep_flops_per_line(d, M) if dom == "sweep64" else defect_flops_per_line(d, M)
         flops = p["lines"] * per_line
         achieved = flops / (p["ms"] * 1e-3) / 1e12
         peak = SMS * FP64_FMA_PER_CLK_PER_SM * 2 * sm_max * 1e6 / 1e12
@@ -239,19 +254,32 @@ def main():
 
     from paper_1608_05400_gb300 import inputs, mgwr
 
+    d, n, Mw, batch, kind, tol, prec_default, desc = WORKLOADS[args.workload]
+    precision = args.precision or prec_default
     alpha = args.alpha
-    prob = inputs.Problem(D, NPTS, M, T, alpha, "t2")
-    f_host = prob.rhs()
-    f_dev = torch.from_numpy(f_host).cuda()
+    if batch == 1:
+        prob = inputs.Problem(d, n, Mw, T, alpha, kind)
+        f_host = prob.rhs()
+        f_dev = torch.from_numpy(f_host).cuda()
+        s = mgwr.Solver(d, n, Mw, T, alpha)
+        unknowns = prob.unknowns
+    else:
+        # per-instance sources built on the device: f_b = F_b(t) phi(x)
+        alphas = inputs.random_alphas(batch, seed=1608)
+        F = np.stack([inputs.Problem(d, n, Mw, T, float(a), kind).rhs_profile() for a in alphas])
+        ph = torch.from_numpy(inputs.phi(d, n)).cuda()
+        f_dev = ph[None, :, None] * torch.from_numpy(F).cuda()[:, None, :]
+        f_host = None
+        s = mgwr.Solver(d, n, Mw, T, alphas)
+        unknowns = batch * n ** d * Mw
     stream = torch.cuda.Stream()
-    s = mgwr.Solver(D, NPTS, M, T, alpha)
     s.set_stream(stream.cuda_stream)
-    if args.precision == "mixed":
+    if precision == "mixed":
         s.set_precision(mgwr.MGWR_MIXED)
 
     def step():
         s.set_rhs_dev(f_dev.data_ptr())
-        return s.solve(CYCLE, NU1, NU2, TOL, 100)
+        return s.solve(CYCLE, NU1, NU2, tol, 100)
 
     for _ in range(max(args.warmup, 3) if args.warmup >= 3 else args.warmup):
         st = step()
@@ -277,9 +305,9 @@ def main():
         t = torch.tensor([ms], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         t_max = float(t.item())
-    value = world * prob.unknowns * args.steps / (t_max * 1e-3)
+    value = world * unknowns * args.steps / (t_max * 1e-3)
 
-    u = s.solution()
+    u = s.solution() if batch == 1 else None
     # per-kernel-class times from one profiled solve (outside the timed region)
     s.profile(True)
     step()
@@ -287,7 +315,7 @@ def main():
     s.profile(False)
 
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and f_host is not None:
         pin_f = torch.from_numpy(f_host).pin_memory()
         pin_u = torch.empty_like(pin_f).pin_memory()
         fp = pin_f.numpy()
@@ -298,7 +326,7 @@ def main():
         ee0.record(stream)
         for _ in range(args.steps):
             s.set_rhs(fp)
-            s.solve(CYCLE, NU1, NU2, TOL, 100)
+            s.solve(CYCLE, NU1, NU2, tol, 100)
             s.lib.mgwr_get_solution(s.h, up.ctypes.data_as(mgwr._dp))
         ee1.record(stream)
         torch.cuda.synchronize()
@@ -307,8 +335,8 @@ def main():
             t = torch.tensor([ems], device="cuda")
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             ems = float(t.item())
-        nbytes = prob.unknowns * 8
-        e2e = {"value": world * prob.unknowns * args.steps / (ems * 1e-3), "unit": UNIT,
+        nbytes = unknowns * 8
+        e2e = {"value": world * unknowns * args.steps / (ems * 1e-3), "unit": UNIT,
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
     s.close()
     if rank != 0:
@@ -320,21 +348,22 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.precision == "fp64" else "f32 cycles + f64 defect/update",
+        "dtype": "f64" if precision == "fp64" else "f32 cycles + f64 defect/update",
         "data": "synthetic",
-        "config": {"workload": f"2-D plain MGWR {NPTS}x{NPTS} interior, M={M} on (0,1], alpha={alpha}, "
-                               f"u=t^2 sin(pi x) sin(pi y), V({NU1},{NU2}) red-black, rel-res {TOL}",
-                   "precision": args.precision, "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "inputs larger than L2 (533 MB per FP64 field)"},
+        "config": {"workload": f"{desc}, " + (f"alpha={alpha}, " if batch == 1 else "")
+                               + f"V({NU1},{NU2}) red-black, rel-res {tol}",
+                   "name": args.workload, "precision": precision,
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": f"inputs larger than L2 ({unknowns * 8 / 1e6:.0f} MB per FP64 field)"},
         "solve": {"cycles": stats[-1].cycles, "outer": stats[-1].outer, "relres": stats[-1].relres,
                   "factor": stats[-1].factor},
         "gpu_launches": launches,
-        "roofline": roofline_from_profile(prof, args.precision, pk),
+        "roofline": roofline_from_profile(prof, d, Mw, pk),
         "kernel_classes": {k: v for k, v in prof.items() if v["launches"]},
         "clocks": clk.summary(),
         "e2e": e2e,
     }
-    if not args.no_cpu and world == 1:
+    if not args.no_cpu and world == 1 and args.workload == "c2":
         out["cpu_baseline"], out["solve"]["rel_err_vs_oracle"] = cpu_baseline_leg(u, alpha)
     print(json.dumps(out))
     if world > 1:

@@ -17,7 +17,10 @@
  *
  * Data layout (every field, host or device): N = n^d time lines of M values,
  * index p*M + m, p = i (1-D) or p = i + n*j (2-D, i along x), m = 0..M-1 at
- * time t_{m+1} = (m+1) tau.  Values are IEEE double.
+ * time t_{m+1} = (m+1) tau.  Values are IEEE double.  A handle holds a batch of
+ * `batch` instances of the same (d, n, M) with their own T and alpha
+ * (mgwr_create_batch; mgwr_create makes a batch of one); every field then
+ * holds the instances one after another: instance b at offset b*N*M.
  *
  * Ownership: the caller owns every pointer it passes; the library copies in
  * and out.  The library owns all device memory it allocates (cudaMalloc) and
@@ -98,6 +101,17 @@ typedef struct {
  * their length-2M spectra (Sec. 5, circulant embedding).  Returns MGWR_E_INVAL
  * for bad arguments, MGWR_E_NOMEM if device memory runs out. */
 int mgwr_create(int d, int n, int M, double T, double alpha, mgwr_t* out);
+/* A batch of `batch` (1..65535) independent problems of the same (d, n, M),
+ * instance b with final time T[b] and order alpha[b] (host arrays).  Every
+ * kernel launch serves all instances (one launch per step of the cycle, the
+ * instance index in the grid's second dimension); setup is done for each
+ * instance as in mgwr_create.  Sizes and layout: see the data-layout note. */
+int mgwr_create_batch(int d, int n, int M, const double* T, const double* alpha, int batch,
+                      mgwr_t* out);
+int mgwr_batch_size(mgwr_t h, int* batch);
+/* Per-instance relative defect ||f_b - A u_b||_inf / ||f_b - A u0_b||_inf after
+ * the last mgwr_solve / mgwr_residual (batch doubles). */
+int mgwr_instance_relres(mgwr_t h, double* relres);
 int mgwr_destroy(mgwr_t h);
 const char* mgwr_last_error(mgwr_t h);
 const char* mgwr_status_string(int status);
@@ -127,7 +141,8 @@ int mgwr_set_initial(mgwr_t h, const double* u0);
 
 /* Run WRMG cycles (cycle = 1: V, 2: W; nu1 pre- and nu2 post-smoothing steps,
  * each one red and one black half-sweep) from the current iterate until
- * ||f - A u||_inf <= tol * ||f - A u0||_inf or max_cycles cycles.  A is the
+ * ||f - A u||_inf <= tol * ||f - A u0||_inf for every instance of the batch, or
+ * max_cycles cycles (MGWR_MIXED: max_cycles FP64 defect evaluations).  A is the
  * whole space-time operator T_M (x) I + A_h (Sec. 5).  Returns MGWR_OK,
  * MGWR_E_NOCONV (stats still filled) or MGWR_E_NUMERIC (non-finite norm).
  * stats may be NULL. */
@@ -173,8 +188,8 @@ int mgwr_coarsest(mgwr_t h, int hier);
 int mgwr_cycle(mgwr_t h, int hier, int cycle, int nu1, int nu2);
 
 /* ---- setup results (FP64, computed on the GPU at mgwr_create) ----------- */
-int mgwr_toeplitz_column(mgwr_t h, double* r_host);            /* r_1..r_M   */
-int mgwr_inverse_column(mgwr_t h, int level, double* k_host);  /* k_1..k_M   */
+int mgwr_toeplitz_column(mgwr_t h, double* r_host);            /* batch x (r_1..r_M) */
+int mgwr_inverse_column(mgwr_t h, int level, double* k_host);  /* batch x (k_1..k_M) */
 
 /* Allocation-free variant of the inverse-column setup (the paper has no
  * counterpart; it serves callers that cannot allocate device memory while

@@ -1,7 +1,9 @@
-// Host side of the MGWR library: handle, level hierarchy, Algorithm 1 driver,
-// FP64 / mixed-precision solve loops and the C ABI of include/mgwr.h.
+// Host side of the MGWR library: handle (a batch of same-shape instances),
+// level hierarchy, Algorithm 1 driver, FP64 / mixed-precision solve loops and
+// the C ABI of include/mgwr.h.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -13,10 +15,12 @@
 #include "mgwr_internal.h"
 
 using mgwr::Cx;
+using mgwr::LevelShape;
 
 namespace {
 
-// What the defect work field r_l of a level currently stands for.
+// What the defect work field r_l of a level currently stands for (all
+// instances of a batch are always in the same state).
 enum RState {
   R_STALE = 0,    // nothing known: the defect needs the full (convolution) form
   R_ZERO_U = 1,   // u_l = 0 (just restricted into): the defect is f_l itself
@@ -26,35 +30,37 @@ enum RState {
 
 template <class R>
 struct Hier {
-  std::vector<R*> u, f, r;        // per level, N_l * M values each
+  std::vector<R*> u, f, r;        // per level: batch * N_l * M values each
   std::vector<R*> dl;             // per level: black-point changes of the last step
   std::vector<int> rs;            // per level: RState of r
-  Cx<R>* spec = nullptr;          // nlev * L: spectra of the inverse columns
-  Cx<R>* tspec = nullptr;         // L: spectrum of the Toeplitz column
+  Cx<R>* spec = nullptr;          // batch * nlev * L: spectra of the inverse columns
+  Cx<R>* tspec = nullptr;         // batch * L: spectra of the Toeplitz columns
   Cx<R>* tw = nullptr;            // L twiddles
-  bool ready = false;
+  bool ready = false;             // spectra present
+  bool full = false;              // every level's u, f, r, dl allocated
 };
 
 }  // namespace
 
 struct mgwr_handle {
-  int d = 1, n = 1, M = 4, L = 8, nlev = 1;
-  double T = 1.0, alpha = 0.5, c = 1.0;
+  int d = 1, n = 1, M = 4, L = 8, nlev = 1, B = 1;
+  std::vector<double> alpha, T, c;  // per instance; c = tau^-alpha / Gamma(2 - alpha)
   int precision = MGWR_FP64, order = MGWR_ORDER_TEXT, inner = 2;
   std::vector<int> nl;          // interior points per dimension, level 0 = 1
   std::vector<double> hinv2;    // 1/h_l^2
   std::vector<double> sigma;    // 2d/h_l^2
   cudaStream_t stream = nullptr;
   cudaStream_t own_stream = nullptr;
-  double* r = nullptr;          // r_1..r_M
-  double* dk = nullptr;         // d_0..d_M
-  double* kcol = nullptr;       // nlev * M inverse columns
+  double* r = nullptr;          // batch * M: r_1..r_M
+  double* dk = nullptr;         // batch * (M+1): d_0..d_M
+  double* kcol = nullptr;       // batch * nlev * M inverse columns
+  double* c_dev = nullptr;      // batch
   Hier<double> h64;
   Hier<float> h32;
-  unsigned long long* norm_bits = nullptr;  // device scalar
-  unsigned long long* norm_host = nullptr;  // pinned
+  unsigned long long* norm_bits = nullptr;  // device, one per instance
+  unsigned long long* norm_host = nullptr;  // pinned, one per instance
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  double r0 = 0.0;
+  std::vector<double> r0, relres;  // per instance
   bool r0_valid = false;
   std::vector<void*> allocs;
   std::string err;
@@ -84,9 +90,9 @@ int fail(mgwr_t h, int code, const std::string& msg) {
       return fail((h), MGWR_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
-#define MGWR_TRY(call)        \
-  do {                        \
-    int s_ = (call);          \
+#define MGWR_TRY(call)            \
+  do {                            \
+    int s_ = (call);              \
     if (s_ != MGWR_OK) return s_; \
   } while (0)
 
@@ -104,11 +110,25 @@ int dev_alloc(mgwr_t h, P** p, size_t bytes) {
   return MGWR_OK;
 }
 
+// Allocates a zero-filled field once.
+template <class R>
+int ensure_field(mgwr_t h, R** p, size_t count) {
+  if (*p != nullptr) return MGWR_OK;
+  MGWR_TRY(dev_alloc(h, p, count * sizeof(R)));
+  MGWR_CK(h, cudaMemsetAsync(*p, 0, count * sizeof(R), h->stream));
+  return MGWR_OK;
+}
+
 bool is_pow2(long long x) { return x > 0 && (x & (x - 1)) == 0; }
 
 size_t points(const mgwr_handle* h, int l) {
   return h->d == 1 ? (size_t)h->nl[l] : (size_t)h->nl[l] * h->nl[l];
 }
+
+// values of one level field over the whole batch
+size_t level_count(const mgwr_handle* h, int l) { return points(h, l) * h->M * h->B; }
+
+LevelShape shape(const mgwr_handle* h, int l) { return LevelShape{h->d, h->nl[l], h->M, h->B}; }
 
 int parity(const mgwr_handle* h, int colour) {
   int red_par;
@@ -119,40 +139,42 @@ int parity(const mgwr_handle* h, int colour) {
   return colour == MGWR_RED ? red_par : red_par ^ 1;
 }
 
+// Every field of every level (u, f, r, dl) of a hierarchy.  The black-change
+// field dl is zero-filled once, so lines that are never swept black stay finite
+// and the zero-weight boundary reads of the defect-from-changes kernel are safe.
 template <class R>
-int alloc_fields(mgwr_t h, Hier<R>& H) {
+int ensure_full(mgwr_t h, Hier<R>& H) {
+  if (H.full) return MGWR_OK;
+  for (int l = 0; l < h->nlev; ++l) {
+    const size_t cnt = level_count(h, l);
+    MGWR_TRY(ensure_field(h, &H.u[l], cnt));
+    MGWR_TRY(ensure_field(h, &H.f[l], cnt));
+    MGWR_TRY(ensure_field(h, &H.r[l], cnt));
+    if (l > 0) MGWR_TRY(ensure_field(h, &H.dl[l], cnt));
+  }
+  H.full = true;
+  return MGWR_OK;
+}
+
+template <class R>
+void init_hier(mgwr_t h, Hier<R>& H) {
   H.u.assign(h->nlev, nullptr);
   H.f.assign(h->nlev, nullptr);
   H.r.assign(h->nlev, nullptr);
   H.dl.assign(h->nlev, nullptr);
   H.rs.assign(h->nlev, R_STALE);
-  for (int l = 0; l < h->nlev; ++l) {
-    const size_t bytes = points(h, l) * h->M * sizeof(R);
-    MGWR_TRY(dev_alloc(h, &H.u[l], bytes));
-    MGWR_TRY(dev_alloc(h, &H.f[l], bytes));
-    MGWR_TRY(dev_alloc(h, &H.r[l], bytes));
-    if (l > 0) {
-      // zero-filled once: lines that are never swept black stay finite, so the
-      // zero-weight boundary reads of the defect-from-changes kernel are safe
-      MGWR_TRY(dev_alloc(h, &H.dl[l], bytes));
-      MGWR_CK(h, cudaMemsetAsync(H.dl[l], 0, bytes, h->stream));
-    }
-    MGWR_CK(h, cudaMemsetAsync(H.u[l], 0, bytes, h->stream));
-    MGWR_CK(h, cudaMemsetAsync(H.f[l], 0, bytes, h->stream));
-    MGWR_CK(h, cudaMemsetAsync(H.r[l], 0, bytes, h->stream));
-  }
-  return MGWR_OK;
 }
 
 int ensure_h32(mgwr_t h) {
   if (h->h32.ready) return MGWR_OK;
   Hier<float>& H = h->h32;
-  MGWR_TRY(alloc_fields(h, H));
-  MGWR_TRY(dev_alloc(h, &H.spec, sizeof(Cx<float>) * (size_t)h->nlev * h->L));
-  MGWR_TRY(dev_alloc(h, &H.tspec, sizeof(Cx<float>) * (size_t)h->L));
+  MGWR_TRY(ensure_full(h, H));
+  const size_t nspec = (size_t)h->B * h->nlev * h->L;
+  MGWR_TRY(dev_alloc(h, &H.spec, sizeof(Cx<float>) * nspec));
+  MGWR_TRY(dev_alloc(h, &H.tspec, sizeof(Cx<float>) * (size_t)h->B * h->L));
   MGWR_TRY(dev_alloc(h, &H.tw, sizeof(Cx<float>) * (size_t)h->L));
-  MGWR_CK(h, mgwr::launch_round_cx(H.spec, h->h64.spec, (size_t)h->nlev * h->L, h->stream));
-  MGWR_CK(h, mgwr::launch_round_cx(H.tspec, h->h64.tspec, (size_t)h->L, h->stream));
+  MGWR_CK(h, mgwr::launch_round_cx(H.spec, h->h64.spec, nspec, h->stream));
+  MGWR_CK(h, mgwr::launch_round_cx(H.tspec, h->h64.tspec, (size_t)h->B * h->L, h->stream));
   MGWR_CK(h, mgwr::launch_round_cx(H.tw, h->h64.tw, (size_t)h->L, h->stream));
   MGWR_CK(h, cudaStreamSynchronize(h->stream));
   H.ready = true;
@@ -200,7 +222,14 @@ void prof_collect(mgwr_t h) {
 // ---- Algorithm 1 components ------------------------------------------------------
 
 template <class R>
-int coarsest(mgwr_t h, Hier<R>& H);
+int coarsest(mgwr_t h, Hier<R>& H) {
+  const int pm = prof_begin(h, MGWR_K_COARSEST, (double)h->B);
+  MGWR_CK(h, mgwr::launch_sweep<R>(H.f[0], H.u[0], (R*)nullptr, H.spec, (size_t)h->nlev * h->L,
+                                    H.tw, shape(h, 0), 0, true, R(0), h->stream));
+  prof_end(h, pm);
+  H.rs[0] = R_STALE;
+  return MGWR_OK;
+}
 
 // One colour half-sweep at level l >= 1; delta != null also records the change of
 // every swept line (used by the black half-sweep ending a smoothing step).
@@ -208,10 +237,11 @@ template <class R>
 int sweep_colour(mgwr_t h, Hier<R>& H, int l, int colour, R* delta) {
   const int par = parity(h, colour);
   const size_t N = points(h, l);
-  const double lines = (double)(par == 0 ? (N + 1) / 2 : N / 2);
+  const double lines = (double)h->B * (double)(par == 0 ? (N + 1) / 2 : N / 2);
   const int pm = prof_begin(h, sizeof(R) == 8 ? MGWR_K_SWEEP64 : MGWR_K_SWEEP32, lines);
-  MGWR_CK(h, mgwr::launch_sweep<R>(H.f[l], H.u[l], delta, H.spec + (size_t)l * h->L, H.tw, h->d,
-                                    h->nl[l], h->M, par, false, R(h->hinv2[l]), h->stream));
+  MGWR_CK(h, mgwr::launch_sweep<R>(H.f[l], H.u[l], delta, H.spec + (size_t)l * h->L,
+                                    (size_t)h->nlev * h->L, H.tw, shape(h, l), par, false,
+                                    R(h->hinv2[l]), h->stream));
   prof_end(h, pm);
   return MGWR_OK;
 }
@@ -239,9 +269,10 @@ int smooth(mgwr_t h, Hier<R>& H, int l, int steps) {
 // Full defect r = f - (T_M (x) I + A_h) u with one FFT convolution per line.
 template <class R>
 int defect(mgwr_t h, Hier<R>& H, int l, unsigned long long* norm_bits) {
-  const int pm = prof_begin(h, sizeof(R) == 8 ? MGWR_K_DEFECT64 : MGWR_K_DEFECT32, (double)points(h, l));
-  MGWR_CK(h, (mgwr::launch_defect<R, R>(H.u[l], H.f[l], H.r[l], H.tspec, H.tw, h->d, h->nl[l],
-                                         h->M, R(h->hinv2[l]), norm_bits, h->stream)));
+  const int pm = prof_begin(h, sizeof(R) == 8 ? MGWR_K_DEFECT64 : MGWR_K_DEFECT32,
+                            (double)(points(h, l) * h->B));
+  MGWR_CK(h, (mgwr::launch_defect<R, R>(H.u[l], H.f[l], H.r[l], H.tspec, (size_t)h->L, H.tw,
+                                         shape(h, l), R(h->hinv2[l]), norm_bits, h->stream)));
   prof_end(h, pm);
   H.rs[l] = R_CURRENT;
   return MGWR_OK;
@@ -250,10 +281,9 @@ int defect(mgwr_t h, Hier<R>& H, int l, unsigned long long* norm_bits) {
 // Defect of level l from the last smoothing step's changes (no convolution).
 template <class R>
 int defect_from_delta(mgwr_t h, Hier<R>& H, int l, unsigned long long* norm_bits) {
-  const int pm = prof_begin(h, MGWR_K_DEFECT_DELTA, (double)points(h, l));
-  MGWR_CK(h, mgwr::launch_defect_from_delta<R>(H.dl[l], H.r[l], h->d, h->nl[l], h->M,
-                                                parity(h, MGWR_RED), R(h->hinv2[l]), norm_bits,
-                                                h->stream));
+  const int pm = prof_begin(h, MGWR_K_DEFECT_DELTA, (double)(points(h, l) * h->B));
+  MGWR_CK(h, mgwr::launch_defect_from_delta<R>(H.dl[l], H.r[l], shape(h, l), parity(h, MGWR_RED),
+                                                R(h->hinv2[l]), norm_bits, h->stream));
   prof_end(h, pm);
   H.rs[l] = R_CURRENT;
   return MGWR_OK;
@@ -281,12 +311,20 @@ int current_defect(mgwr_t h, Hier<R>& H, int l, const R** out) {
 }
 
 template <class R>
-int coarsest(mgwr_t h, Hier<R>& H) {
-  const int pm = prof_begin(h, MGWR_K_COARSEST, 1.0);
-  MGWR_CK(h, mgwr::launch_sweep<R>(H.f[0], H.u[0], (R*)nullptr, H.spec, H.tw, h->d, 1, h->M, 0,
-                                    true, R(0), h->stream));
+int restrict_into(mgwr_t h, Hier<R>& H, int l, const R* r) {
+  const int pm = prof_begin(h, MGWR_K_RESTRICT, (double)(points(h, l - 1) * h->B));
+  MGWR_CK(h, mgwr::launch_restrict<R>(r, H.f[l - 1], H.u[l - 1], shape(h, l), h->stream));
   prof_end(h, pm);
-  H.rs[0] = R_STALE;
+  H.rs[l - 1] = R_ZERO_U;
+  return MGWR_OK;
+}
+
+template <class R>
+int prolong_into(mgwr_t h, Hier<R>& H, int l) {
+  const int pm = prof_begin(h, MGWR_K_PROLONG, (double)(points(h, l) * h->B));
+  MGWR_CK(h, mgwr::launch_prolong<R>(H.u[l], H.u[l - 1], shape(h, l), h->stream));
+  prof_end(h, pm);
+  H.rs[l] = R_STALE;
   return MGWR_OK;
 }
 
@@ -296,65 +334,77 @@ int cycle(mgwr_t h, Hier<R>& H, int l, int gamma, int nu1, int nu2) {
   MGWR_TRY(smooth(h, H, l, nu1));
   const R* r = nullptr;
   MGWR_TRY(current_defect(h, H, l, &r));
-  int pm = prof_begin(h, MGWR_K_RESTRICT, (double)points(h, l - 1));
-  MGWR_CK(h, mgwr::launch_restrict<R>(r, H.f[l - 1], H.u[l - 1], h->d, h->nl[l], h->M,
-                                       h->stream));
-  prof_end(h, pm);
-  H.rs[l - 1] = R_ZERO_U;
+  MGWR_TRY(restrict_into(h, H, l, r));
   for (int g = 0; g < gamma; ++g) MGWR_TRY(cycle(h, H, l - 1, gamma, nu1, nu2));
-  pm = prof_begin(h, MGWR_K_PROLONG, (double)points(h, l));
-  MGWR_CK(h, mgwr::launch_prolong<R>(H.u[l], H.u[l - 1], h->d, h->nl[l], h->M, h->stream));
-  prof_end(h, pm);
-  H.rs[l] = R_STALE;
+  MGWR_TRY(prolong_into(h, H, l));
   MGWR_TRY(smooth(h, H, l, nu2));
   return MGWR_OK;
 }
 
-// Reads the device norm accumulator (cleared before the producing kernel).
-int read_norm(mgwr_t h, double* out) {
-  MGWR_CK(h, cudaMemcpyAsync(h->norm_host, h->norm_bits, sizeof(unsigned long long),
-                             cudaMemcpyDeviceToHost, h->stream));
-  MGWR_CK(h, cudaStreamSynchronize(h->stream));
-  unsigned long long bits = *h->norm_host;
-  double v;
-  std::memcpy(&v, &bits, sizeof v);
-  *out = v;
+int clear_norms(mgwr_t h) {
+  MGWR_CK(h, cudaMemsetAsync(h->norm_bits, 0, sizeof(unsigned long long) * h->B, h->stream));
   return MGWR_OK;
 }
 
-// FP64 defect of the finest iterate with its infinity norm.  In mixed mode the
-// defect is written, rounded, as the right-hand side of the FP32 hierarchy.
-int finest_defect_norm(mgwr_t h, double* norm, bool to_h32) {
-  const int L = h->nlev - 1;
-  MGWR_CK(h, cudaMemsetAsync(h->norm_bits, 0, sizeof(unsigned long long), h->stream));
-  const int pm = prof_begin(h, MGWR_K_DEFECT64, (double)points(h, L));
-  struct Closer { mgwr_t h; int pm; ~Closer() { prof_end(h, pm); } } closer{h, pm};
-  if (to_h32) {
-    MGWR_CK(h, (mgwr::launch_defect<double, float>(h->h64.u[L], h->h64.f[L], h->h32.f[L],
-                                                    h->h64.tspec, h->h64.tw, h->d, h->nl[L], h->M,
-                                                    h->hinv2[L], h->norm_bits, h->stream)));
-    h->h32.rs[L] = R_STALE;
-  } else {
-    MGWR_CK(h, (mgwr::launch_defect<double, double>(h->h64.u[L], h->h64.f[L], h->h64.r[L],
-                                                     h->h64.tspec, h->h64.tw, h->d, h->nl[L], h->M,
-                                                     h->hinv2[L], h->norm_bits, h->stream)));
-    h->h64.rs[L] = R_CURRENT;
-  }
-  return read_norm(h, norm);
+// Reads the per-instance norm accumulators (cleared before the producing kernel).
+int read_norms(mgwr_t h, std::vector<double>& out) {
+  MGWR_CK(h, cudaMemcpyAsync(h->norm_host, h->norm_bits, sizeof(unsigned long long) * h->B,
+                             cudaMemcpyDeviceToHost, h->stream));
+  MGWR_CK(h, cudaStreamSynchronize(h->stream));
+  out.resize(h->B);
+  for (int b = 0; b < h->B; ++b) std::memcpy(&out[b], &h->norm_host[b], sizeof(double));
+  return MGWR_OK;
 }
 
-// FP64 defect norm of the finest level after a cycle: from the last smoothing
-// step's changes when the cycle ended with one, else the full form.
-int finest_cycle_norm(mgwr_t h, double* norm, bool* exact) {
+// FP64 defect of the finest iterate with its per-instance infinity norms.  In
+// mixed mode the defect is written, rounded, as the FP32 right-hand side.
+int finest_defect_norms(mgwr_t h, std::vector<double>& norms, bool to_h32) {
+  const int L = h->nlev - 1;
+  MGWR_TRY(clear_norms(h));
+  const int pm = prof_begin(h, MGWR_K_DEFECT64, (double)(points(h, L) * h->B));
+  if (to_h32) {
+    MGWR_CK(h, (mgwr::launch_defect<double, float>(h->h64.u[L], h->h64.f[L], h->h32.f[L],
+                                                    h->h64.tspec, (size_t)h->L, h->h64.tw,
+                                                    shape(h, L), h->hinv2[L], h->norm_bits,
+                                                    h->stream)));
+    h->h32.rs[L] = R_STALE;
+  } else {
+    MGWR_TRY(ensure_field(h, &h->h64.r[L], level_count(h, L)));
+    MGWR_CK(h, (mgwr::launch_defect<double, double>(h->h64.u[L], h->h64.f[L], h->h64.r[L],
+                                                     h->h64.tspec, (size_t)h->L, h->h64.tw,
+                                                     shape(h, L), h->hinv2[L], h->norm_bits,
+                                                     h->stream)));
+    h->h64.rs[L] = R_CURRENT;
+  }
+  prof_end(h, pm);
+  return read_norms(h, norms);
+}
+
+// Finest-level defect norms after an FP64 cycle: from the last smoothing
+// step's changes when the cycle ended with one (*exact = false), else the
+// full form.
+int finest_cycle_norms(mgwr_t h, std::vector<double>& norms, bool* exact) {
   const int L = h->nlev - 1;
   if (h->h64.rs[L] != R_DELTA) {
     *exact = true;
-    return finest_defect_norm(h, norm, false);
+    return finest_defect_norms(h, norms, false);
   }
   *exact = false;
-  MGWR_CK(h, cudaMemsetAsync(h->norm_bits, 0, sizeof(unsigned long long), h->stream));
+  MGWR_TRY(clear_norms(h));
   MGWR_TRY(defect_from_delta(h, h->h64, L, h->norm_bits));
-  return read_norm(h, norm);
+  return read_norms(h, norms);
+}
+
+// Relative defects from norms; returns the largest, NaN if any is not finite.
+double relative(mgwr_t h, const std::vector<double>& norms, std::vector<double>& rel) {
+  rel.resize(h->B);
+  double worst = 0.0;
+  for (int b = 0; b < h->B; ++b) {
+    rel[b] = h->r0[b] > 0.0 ? norms[b] / h->r0[b] : (norms[b] == 0.0 ? 0.0 : norms[b]);
+    if (!std::isfinite(rel[b])) worst = NAN;
+    if (worst == worst) worst = std::max(worst, rel[b]);
+  }
+  return worst;
 }
 
 int check_level(mgwr_t h, int hierarchy, int level) {
@@ -363,6 +413,7 @@ int check_level(mgwr_t h, int hierarchy, int level) {
   if (level < 0 || level >= h->nlev) return fail(h, MGWR_E_INVAL, "level out of range");
   if (hierarchy == MGWR_H32 && !h->h32.ready)
     return fail(h, MGWR_E_STATE, "the FP32 hierarchy exists only after mgwr_set_precision(MGWR_MIXED)");
+  if (hierarchy == MGWR_H64) MGWR_TRY(ensure_full(h, h->h64));
   return MGWR_OK;
 }
 
@@ -370,6 +421,115 @@ int check_cycle_args(mgwr_t h, int cyc, int nu1, int nu2) {
   if (cyc != 1 && cyc != 2) return fail(h, MGWR_E_INVAL, "cycle must be 1 (V) or 2 (W)");
   if (nu1 < 0 || nu2 < 0 || nu1 > 16 || nu2 > 16 || nu1 + nu2 == 0)
     return fail(h, MGWR_E_INVAL, "need 0 <= nu1, nu2 <= 16 and nu1 + nu2 >= 1");
+  return MGWR_OK;
+}
+
+int create_impl(int d, int n, int M, const double* T, const double* alpha, int batch,
+                mgwr_t* out) {
+  if (out == nullptr) return MGWR_E_INVAL;
+  *out = nullptr;
+  if (d != 1 && d != 2) return MGWR_E_INVAL;
+  if (n < 1 || !is_pow2((long long)n + 1)) return MGWR_E_INVAL;
+  if ((d == 1 && n > 32767) || (d == 2 && n > 4095)) return MGWR_E_INVAL;
+  if (!is_pow2(M) || M < 4 || M > 4096) return MGWR_E_INVAL;
+  if (batch < 1 || batch > 65535 || T == nullptr || alpha == nullptr) return MGWR_E_INVAL;
+  for (int b = 0; b < batch; ++b) {
+    if (!(T[b] > 0.0) || !std::isfinite(T[b])) return MGWR_E_INVAL;
+    if (!(alpha[b] > 0.0) || !(alpha[b] <= 1.0)) return MGWR_E_INVAL;
+  }
+
+  mgwr_t h = new (std::nothrow) mgwr_handle;
+  if (h == nullptr) return MGWR_E_NOMEM;
+  h->d = d;
+  h->n = n;
+  h->M = M;
+  h->L = 2 * M;
+  h->B = batch;
+  h->alpha.assign(alpha, alpha + batch);
+  h->T.assign(T, T + batch);
+  for (int b = 0; b < batch; ++b) {
+    const double tau = T[b] / M;
+    h->c.push_back(std::pow(tau, -alpha[b]) / std::tgamma(2.0 - alpha[b]));
+  }
+  h->r0.assign(batch, 0.0);
+  h->relres.assign(batch, 0.0);
+  std::vector<int> sizes{n};
+  while (sizes.back() > 1) sizes.push_back((sizes.back() - 1) / 2);
+  h->nl.assign(sizes.rbegin(), sizes.rend());
+  h->nlev = (int)h->nl.size();
+  for (int l = 0; l < h->nlev; ++l) {
+    const double hl = 1.0 / (h->nl[l] + 1);
+    h->hinv2.push_back(1.0 / (hl * hl));
+    h->sigma.push_back(2.0 * d / (hl * hl));
+  }
+  init_hier(h, h->h64);
+  init_hier(h, h->h32);
+
+  auto bail = [&](int code) {
+    mgwr_destroy(h);
+    return code;
+  };
+  if (cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(MGWR_E_CUDA);
+  }
+  h->stream = h->own_stream;
+  if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess ||
+      cudaMallocHost(&h->norm_host, sizeof(unsigned long long) * batch) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(MGWR_E_CUDA);
+  }
+  const size_t B = batch;
+  int s;
+  double *sig_dev = nullptr, *alpha_dev = nullptr;
+  Cx<double>* work = nullptr;
+  if ((s = dev_alloc(h, &h->norm_bits, sizeof(unsigned long long) * B)) != MGWR_OK) return bail(s);
+  if ((s = dev_alloc(h, &h->r, sizeof(double) * B * M)) != MGWR_OK) return bail(s);
+  if ((s = dev_alloc(h, &h->dk, sizeof(double) * B * (M + 1))) != MGWR_OK) return bail(s);
+  if ((s = dev_alloc(h, &h->kcol, sizeof(double) * B * h->nlev * M)) != MGWR_OK) return bail(s);
+  if ((s = dev_alloc(h, &h->c_dev, sizeof(double) * B)) != MGWR_OK) return bail(s);
+  if ((s = dev_alloc(h, &alpha_dev, sizeof(double) * B)) != MGWR_OK) return bail(s);
+  if ((s = dev_alloc(h, &sig_dev, sizeof(double) * h->nlev)) != MGWR_OK) return bail(s);
+  if ((s = dev_alloc(h, &work, sizeof(Cx<double>) * B * h->nlev * 3 * M)) != MGWR_OK) return bail(s);
+  if ((s = dev_alloc(h, &h->h64.spec, sizeof(Cx<double>) * B * h->nlev * h->L)) != MGWR_OK)
+    return bail(s);
+  if ((s = dev_alloc(h, &h->h64.tspec, sizeof(Cx<double>) * B * h->L)) != MGWR_OK) return bail(s);
+  if ((s = dev_alloc(h, &h->h64.tw, sizeof(Cx<double>) * (size_t)h->L)) != MGWR_OK) return bail(s);
+
+  cudaError_t e = cudaMemcpyAsync(sig_dev, h->sigma.data(), sizeof(double) * h->nlev,
+                                  cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->c_dev, h->c.data(), sizeof(double) * B, cudaMemcpyHostToDevice,
+                        h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(alpha_dev, h->alpha.data(), sizeof(double) * B, cudaMemcpyHostToDevice,
+                        h->stream);
+  if (e == cudaSuccess)
+    e = mgwr::launch_coefficients(h->r, h->dk, M, alpha_dev, h->c_dev, batch, h->stream);
+  if (e == cudaSuccess)
+    e = mgwr::launch_inverse_columns(h->kcol, h->r, sig_dev, h->nlev, M, batch, work, h->stream);
+  if (e == cudaSuccess) e = mgwr::launch_twiddles(h->h64.tw, h->L, h->stream);
+  if (e == cudaSuccess)
+    e = mgwr::launch_spectra(h->h64.spec, h->kcol, batch * h->nlev, M, h->h64.tw, h->stream);
+  if (e == cudaSuccess) e = mgwr::launch_spectra(h->h64.tspec, h->r, batch, M, h->h64.tw, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return bail(MGWR_E_CUDA);
+  }
+  // the divide-and-conquer work area is no longer needed
+  cudaFree(work);
+  h->allocs.erase(std::find(h->allocs.begin(), h->allocs.end(), (void*)work));
+  h->h64.ready = true;
+  // the finest iterate and right-hand side always exist; the rest on demand
+  const int Lf = h->nlev - 1;
+  if ((s = ensure_field(h, &h->h64.u[Lf], level_count(h, Lf))) != MGWR_OK) return bail(s);
+  if ((s = ensure_field(h, &h->h64.f[Lf], level_count(h, Lf))) != MGWR_OK) return bail(s);
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(MGWR_E_CUDA);
+  }
+  *out = h;
   return MGWR_OK;
 }
 
@@ -413,84 +573,23 @@ int mgwr_destroy(mgwr_t h) {
 }
 
 int mgwr_create(int d, int n, int M, double T, double alpha, mgwr_t* out) {
-  if (out == nullptr) return MGWR_E_INVAL;
-  *out = nullptr;
-  if (d != 1 && d != 2) return MGWR_E_INVAL;
-  if (n < 1 || !is_pow2((long long)n + 1)) return MGWR_E_INVAL;
-  if ((d == 1 && n > 32767) || (d == 2 && n > 4095)) return MGWR_E_INVAL;
-  if (!is_pow2(M) || M < 4 || M > 4096) return MGWR_E_INVAL;
-  if (!(T > 0.0) || !std::isfinite(T)) return MGWR_E_INVAL;
-  if (!(alpha > 0.0) || !(alpha <= 1.0)) return MGWR_E_INVAL;
+  return create_impl(d, n, M, &T, &alpha, 1, out);
+}
 
-  mgwr_t h = new (std::nothrow) mgwr_handle;
-  if (h == nullptr) return MGWR_E_NOMEM;
-  h->d = d;
-  h->n = n;
-  h->M = M;
-  h->L = 2 * M;
-  h->T = T;
-  h->alpha = alpha;
-  const double tau = T / M;
-  h->c = std::pow(tau, -alpha) / std::tgamma(2.0 - alpha);
-  // level sizes, coarsest first
-  std::vector<int> sizes{n};
-  while (sizes.back() > 1) sizes.push_back((sizes.back() - 1) / 2);
-  h->nl.assign(sizes.rbegin(), sizes.rend());
-  h->nlev = (int)h->nl.size();
-  for (int l = 0; l < h->nlev; ++l) {
-    const double hl = 1.0 / (h->nl[l] + 1);
-    h->hinv2.push_back(1.0 / (hl * hl));
-    h->sigma.push_back(2.0 * d / (hl * hl));
-  }
+int mgwr_create_batch(int d, int n, int M, const double* T, const double* alpha, int batch,
+                      mgwr_t* out) {
+  return create_impl(d, n, M, T, alpha, batch, out);
+}
 
-  auto bail = [&](int code) {
-    mgwr_destroy(h);
-    return code;
-  };
-  if (cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
-    cudaGetLastError();
-    return bail(MGWR_E_CUDA);
-  }
-  h->stream = h->own_stream;
-  if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess ||
-      cudaMallocHost(&h->norm_host, sizeof(unsigned long long)) != cudaSuccess) {
-    cudaGetLastError();
-    return bail(MGWR_E_CUDA);
-  }
-  int s;
-  double* sig_dev = nullptr;
-  Cx<double>* work = nullptr;
-  if ((s = dev_alloc(h, &h->norm_bits, sizeof(unsigned long long))) != MGWR_OK) return bail(s);
-  if ((s = dev_alloc(h, &h->r, sizeof(double) * M)) != MGWR_OK) return bail(s);
-  if ((s = dev_alloc(h, &h->dk, sizeof(double) * (M + 1))) != MGWR_OK) return bail(s);
-  if ((s = dev_alloc(h, &h->kcol, sizeof(double) * (size_t)h->nlev * M)) != MGWR_OK) return bail(s);
-  if ((s = dev_alloc(h, &sig_dev, sizeof(double) * h->nlev)) != MGWR_OK) return bail(s);
-  if ((s = dev_alloc(h, &work, sizeof(Cx<double>) * (size_t)h->nlev * 3 * M)) != MGWR_OK) return bail(s);
-  if ((s = dev_alloc(h, &h->h64.spec, sizeof(Cx<double>) * (size_t)h->nlev * h->L)) != MGWR_OK) return bail(s);
-  if ((s = dev_alloc(h, &h->h64.tspec, sizeof(Cx<double>) * (size_t)h->L)) != MGWR_OK) return bail(s);
-  if ((s = dev_alloc(h, &h->h64.tw, sizeof(Cx<double>) * (size_t)h->L)) != MGWR_OK) return bail(s);
+int mgwr_batch_size(mgwr_t h, int* batch) {
+  if (h == nullptr || batch == nullptr) return MGWR_E_INVAL;
+  *batch = h->B;
+  return MGWR_OK;
+}
 
-  cudaError_t e = cudaMemcpyAsync(sig_dev, h->sigma.data(), sizeof(double) * h->nlev,
-                                  cudaMemcpyHostToDevice, h->stream);
-  if (e == cudaSuccess) e = mgwr::launch_coefficients(h->r, h->dk, M, alpha, h->c, h->stream);
-  if (e == cudaSuccess)
-    e = mgwr::launch_inverse_columns(h->kcol, h->r, sig_dev, h->nlev, M, work, h->stream);
-  if (e == cudaSuccess) e = mgwr::launch_twiddles(h->h64.tw, h->L, h->stream);
-  if (e == cudaSuccess)
-    e = mgwr::launch_spectra(h->h64.spec, h->kcol, h->nlev, M, h->h64.tw, h->stream);
-  if (e == cudaSuccess) e = mgwr::launch_spectra(h->h64.tspec, h->r, 1, M, h->h64.tw, h->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return bail(MGWR_E_CUDA);
-  }
-  if ((s = alloc_fields(h, h->h64)) != MGWR_OK) return bail(s);
-  if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
-    cudaGetLastError();
-    return bail(MGWR_E_CUDA);
-  }
-  h->h64.ready = true;
-  *out = h;
+int mgwr_instance_relres(mgwr_t h, double* relres) {
+  if (h == nullptr || relres == nullptr) return MGWR_E_INVAL;
+  std::copy(h->relres.begin(), h->relres.end(), relres);
   return MGWR_OK;
 }
 
@@ -530,14 +629,14 @@ static int set_rhs_impl(mgwr_t h, const double* f, const double* g, cudaMemcpyKi
   if (f == nullptr) return fail(h, MGWR_E_INVAL, "f must not be null");
   const int L = h->nlev - 1;
   const size_t N = points(h, L);
-  const size_t bytes = N * h->M * sizeof(double);
+  const size_t bytes = level_count(h, L) * sizeof(double);
   MGWR_CK(h, cudaMemcpyAsync(h->h64.f[L], f, bytes, kind, h->stream));
   if (g != nullptr) {
     double* g_dev = nullptr;
-    MGWR_TRY(dev_alloc(h, &g_dev, N * sizeof(double)));
-    MGWR_CK(h, cudaMemcpyAsync(g_dev, g, N * sizeof(double), kind, h->stream));
-    MGWR_CK(h, mgwr::launch_initial(h->h64.u[L], h->h64.f[L], g_dev, h->dk, h->c, (int)N, h->M,
-                                     h->stream));
+    MGWR_TRY(dev_alloc(h, &g_dev, N * h->B * sizeof(double)));
+    MGWR_CK(h, cudaMemcpyAsync(g_dev, g, N * h->B * sizeof(double), kind, h->stream));
+    MGWR_CK(h, mgwr::launch_initial(h->h64.u[L], h->h64.f[L], g_dev, h->dk, h->c_dev, (int)N, h->M,
+                                     h->B, h->stream));
     MGWR_CK(h, cudaStreamSynchronize(h->stream));
     cudaFree(g_dev);
     h->allocs.pop_back();
@@ -562,7 +661,7 @@ int mgwr_set_initial(mgwr_t h, const double* u0) {
   if (h == nullptr) return MGWR_E_INVAL;
   if (u0 == nullptr) return fail(h, MGWR_E_INVAL, "u0 must not be null");
   const int L = h->nlev - 1;
-  MGWR_CK(h, cudaMemcpyAsync(h->h64.u[L], u0, points(h, L) * h->M * sizeof(double),
+  MGWR_CK(h, cudaMemcpyAsync(h->h64.u[L], u0, level_count(h, L) * sizeof(double),
                              cudaMemcpyHostToDevice, h->stream));
   MGWR_CK(h, cudaStreamSynchronize(h->stream));
   h->r0_valid = false;
@@ -575,21 +674,21 @@ int mgwr_solve(mgwr_t h, int cyc, int nu1, int nu2, double tol, int max_cycles, 
   MGWR_TRY(check_cycle_args(h, cyc, nu1, nu2));
   if (!(tol >= 0.0) || max_cycles < 1) return fail(h, MGWR_E_INVAL, "need tol >= 0, max_cycles >= 1");
   const bool mixed = h->precision == MGWR_MIXED;
+  if (!mixed) MGWR_TRY(ensure_full(h, h->h64));
   const int L = h->nlev - 1;
   mgwr_stats local{};
   MGWR_CK(h, cudaEventRecord(h->ev0, h->stream));
-  double norm = 0.0;
-  MGWR_TRY(finest_defect_norm(h, &norm, mixed));
+  std::vector<double> norms;
+  MGWR_TRY(finest_defect_norms(h, norms, mixed));
   if (!h->r0_valid) {
-    h->r0 = norm;
+    h->r0 = norms;
     h->r0_valid = true;
   }
-  const double r0 = h->r0;
-  double rel = r0 > 0.0 ? norm / r0 : 0.0;
+  double rel = relative(h, norms, h->relres);
   int status = MGWR_OK;
   int cycles = 0, outer = 0;
   bool rel_exact = true;  // rel comes from the full defect (not from smoothing changes)
-  while (rel > tol) {
+  while (!(rel <= tol)) {
     if (!std::isfinite(rel)) {
       status = MGWR_E_NUMERIC;
       break;
@@ -602,32 +701,34 @@ int mgwr_solve(mgwr_t h, int cyc, int nu1, int nu2, double tol, int max_cycles, 
       MGWR_TRY(cycle(h, h->h64, L, cyc, nu1, nu2));
       ++cycles;
       bool exact = false;
-      MGWR_TRY(finest_cycle_norm(h, &norm, &exact));
+      MGWR_TRY(finest_cycle_norms(h, norms, &exact));
+      rel = relative(h, norms, h->relres);
       // the stopping decision is always taken on the full defect
-      if (!exact && r0 > 0.0 && norm / r0 <= tol) {
-        MGWR_TRY(finest_defect_norm(h, &norm, false));
+      if (!exact && rel <= tol) {
+        MGWR_TRY(finest_defect_norms(h, norms, false));
+        rel = relative(h, norms, h->relres);
         exact = true;
       }
       rel_exact = exact;
     } else {
-      const size_t cnt = points(h, L) * h->M;
+      const size_t cnt = level_count(h, L);
       MGWR_CK(h, cudaMemsetAsync(h->h32.u[L], 0, cnt * sizeof(float), h->stream));
       h->h32.rs[L] = R_ZERO_U;  // f32 holds the FP64 defect, e32 = 0
       for (int k = 0; k < h->inner; ++k) {
         MGWR_TRY(cycle(h, h->h32, L, cyc, nu1, nu2));
         ++cycles;
       }
-      const int pm = prof_begin(h, MGWR_K_REFINE, (double)points(h, L));
+      const int pm = prof_begin(h, MGWR_K_REFINE, (double)(points(h, L) * h->B));
       MGWR_CK(h, mgwr::launch_refine(h->h64.u[L], h->h32.u[L], cnt, h->stream));
       prof_end(h, pm);
-      MGWR_TRY(finest_defect_norm(h, &norm, true));
+      MGWR_TRY(finest_defect_norms(h, norms, true));
+      rel = relative(h, norms, h->relres);
     }
     ++outer;
-    rel = r0 > 0.0 ? norm / r0 : 0.0;
   }
   if (!rel_exact) {  // report the full defect also when stopping on max_cycles
-    MGWR_TRY(finest_defect_norm(h, &norm, false));
-    rel = r0 > 0.0 ? norm / r0 : 0.0;
+    MGWR_TRY(finest_defect_norms(h, norms, false));
+    rel = relative(h, norms, h->relres);
   }
   if (!std::isfinite(rel)) status = MGWR_E_NUMERIC;
   MGWR_CK(h, cudaEventRecord(h->ev1, h->stream));
@@ -648,16 +749,17 @@ int mgwr_solve(mgwr_t h, int cyc, int nu1, int nu2, double tol, int max_cycles, 
 
 int mgwr_residual(mgwr_t h, double* relres, double* r_host) {
   if (h == nullptr) return MGWR_E_INVAL;
-  double norm = 0.0;
-  MGWR_TRY(finest_defect_norm(h, &norm, false));
+  std::vector<double> norms;
+  MGWR_TRY(finest_defect_norms(h, norms, false));
   if (!h->r0_valid) {
-    h->r0 = norm;
+    h->r0 = norms;
     h->r0_valid = true;
   }
-  if (relres != nullptr) *relres = h->r0 > 0.0 ? norm / h->r0 : 0.0;
+  const double rel = relative(h, norms, h->relres);
+  if (relres != nullptr) *relres = rel;
   if (r_host != nullptr) {
     const int L = h->nlev - 1;
-    MGWR_CK(h, cudaMemcpyAsync(r_host, h->h64.r[L], points(h, L) * h->M * sizeof(double),
+    MGWR_CK(h, cudaMemcpyAsync(r_host, h->h64.r[L], level_count(h, L) * sizeof(double),
                                cudaMemcpyDeviceToHost, h->stream));
     MGWR_CK(h, cudaStreamSynchronize(h->stream));
   }
@@ -668,7 +770,7 @@ int mgwr_get_solution(mgwr_t h, double* u_host) {
   if (h == nullptr) return MGWR_E_INVAL;
   if (u_host == nullptr) return fail(h, MGWR_E_INVAL, "u must not be null");
   const int L = h->nlev - 1;
-  MGWR_CK(h, cudaMemcpyAsync(u_host, h->h64.u[L], points(h, L) * h->M * sizeof(double),
+  MGWR_CK(h, cudaMemcpyAsync(u_host, h->h64.u[L], level_count(h, L) * sizeof(double),
                              cudaMemcpyDeviceToHost, h->stream));
   MGWR_CK(h, cudaStreamSynchronize(h->stream));
   return MGWR_OK;
@@ -678,7 +780,7 @@ int mgwr_get_solution_dev(mgwr_t h, double* u_dev) {
   if (h == nullptr) return MGWR_E_INVAL;
   if (u_dev == nullptr) return fail(h, MGWR_E_INVAL, "u must not be null");
   const int L = h->nlev - 1;
-  MGWR_CK(h, cudaMemcpyAsync(u_dev, h->h64.u[L], points(h, L) * h->M * sizeof(double),
+  MGWR_CK(h, cudaMemcpyAsync(u_dev, h->h64.u[L], level_count(h, L) * sizeof(double),
                              cudaMemcpyDeviceToDevice, h->stream));
   return MGWR_OK;
 }
@@ -710,7 +812,7 @@ int mgwr_field_set(mgwr_t h, int hierarchy, int level, int which, const double* 
   MGWR_TRY(check_level(h, hierarchy, level));
   if (which < MGWR_U || which > MGWR_R || host == nullptr)
     return fail(h, MGWR_E_INVAL, "bad field or null pointer");
-  const size_t cnt = points(h, level) * h->M;
+  const size_t cnt = level_count(h, level);
   void* dst = field_ptr(h, hierarchy, level, which);
   if (hierarchy == MGWR_H64) {
     MGWR_CK(h, cudaMemcpyAsync(dst, host, cnt * sizeof(double), cudaMemcpyHostToDevice, h->stream));
@@ -734,7 +836,7 @@ int mgwr_field_get(mgwr_t h, int hierarchy, int level, int which, double* host) 
   MGWR_TRY(check_level(h, hierarchy, level));
   if (which < MGWR_U || which > MGWR_R || host == nullptr)
     return fail(h, MGWR_E_INVAL, "bad field or null pointer");
-  const size_t cnt = points(h, level) * h->M;
+  const size_t cnt = level_count(h, level);
   const void* src = field_ptr(h, hierarchy, level, which);
   if (hierarchy == MGWR_H64) {
     MGWR_CK(h, cudaMemcpyAsync(host, src, cnt * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -760,11 +862,19 @@ int mgwr_smooth(mgwr_t h, int hierarchy, int level, int colour) {
   return MGWR_OK;
 }
 
+// largest per-instance norm of the last reduction
+static double max_norm(mgwr_t h, const std::vector<double>& norms) {
+  double m = 0.0;
+  for (double v : norms) m = (v != v || v > m) ? v : m;
+  (void)h;
+  return m;
+}
+
 int mgwr_smooth_defect(mgwr_t h, int hierarchy, int level, double* norm_inf) {
   if (h == nullptr) return MGWR_E_INVAL;
   MGWR_TRY(check_level(h, hierarchy, level));
   if (level == 0) return fail(h, MGWR_E_INVAL, "level 0 has a direct solve, not a smoother");
-  MGWR_CK(h, cudaMemsetAsync(h->norm_bits, 0, sizeof(unsigned long long), h->stream));
+  MGWR_TRY(clear_norms(h));
   if (hierarchy == MGWR_H64) {
     MGWR_TRY(smooth(h, h->h64, level, 1));
     MGWR_TRY(defect_from_delta(h, h->h64, level, h->norm_bits));
@@ -772,23 +882,23 @@ int mgwr_smooth_defect(mgwr_t h, int hierarchy, int level, double* norm_inf) {
     MGWR_TRY(smooth(h, h->h32, level, 1));
     MGWR_TRY(defect_from_delta(h, h->h32, level, h->norm_bits));
   }
-  double nrm = 0.0;
-  MGWR_TRY(read_norm(h, &nrm));
-  if (norm_inf != nullptr) *norm_inf = nrm;
+  std::vector<double> norms;
+  MGWR_TRY(read_norms(h, norms));
+  if (norm_inf != nullptr) *norm_inf = max_norm(h, norms);
   return MGWR_OK;
 }
 
 int mgwr_defect(mgwr_t h, int hierarchy, int level, double* norm_inf) {
   if (h == nullptr) return MGWR_E_INVAL;
   MGWR_TRY(check_level(h, hierarchy, level));
-  MGWR_CK(h, cudaMemsetAsync(h->norm_bits, 0, sizeof(unsigned long long), h->stream));
+  MGWR_TRY(clear_norms(h));
   if (hierarchy == MGWR_H64)
     MGWR_TRY(defect(h, h->h64, level, h->norm_bits));
   else
     MGWR_TRY(defect(h, h->h32, level, h->norm_bits));
-  double nrm = 0.0;
-  MGWR_TRY(read_norm(h, &nrm));
-  if (norm_inf != nullptr) *norm_inf = nrm;
+  std::vector<double> norms;
+  MGWR_TRY(read_norms(h, norms));
+  if (norm_inf != nullptr) *norm_inf = max_norm(h, norms);
   return MGWR_OK;
 }
 
@@ -796,15 +906,10 @@ int mgwr_restrict(mgwr_t h, int hierarchy, int level) {
   if (h == nullptr) return MGWR_E_INVAL;
   MGWR_TRY(check_level(h, hierarchy, level));
   if (level == 0) return fail(h, MGWR_E_INVAL, "level 0 has no coarser level");
-  if (hierarchy == MGWR_H64) {
-    MGWR_CK(h, mgwr::launch_restrict<double>(h->h64.r[level], h->h64.f[level - 1],
-                                              h->h64.u[level - 1], h->d, h->nl[level], h->M, h->stream));
-    h->h64.rs[level - 1] = R_ZERO_U;
-  } else {
-    MGWR_CK(h, mgwr::launch_restrict<float>(h->h32.r[level], h->h32.f[level - 1],
-                                             h->h32.u[level - 1], h->d, h->nl[level], h->M, h->stream));
-    h->h32.rs[level - 1] = R_ZERO_U;
-  }
+  if (hierarchy == MGWR_H64)
+    MGWR_TRY(restrict_into(h, h->h64, level, h->h64.r[level]));
+  else
+    MGWR_TRY(restrict_into(h, h->h32, level, h->h32.r[level]));
   MGWR_CK(h, cudaStreamSynchronize(h->stream));
   return MGWR_OK;
 }
@@ -813,15 +918,10 @@ int mgwr_prolong(mgwr_t h, int hierarchy, int level) {
   if (h == nullptr) return MGWR_E_INVAL;
   MGWR_TRY(check_level(h, hierarchy, level));
   if (level == 0) return fail(h, MGWR_E_INVAL, "level 0 has no coarser level");
-  if (hierarchy == MGWR_H64) {
-    MGWR_CK(h, mgwr::launch_prolong<double>(h->h64.u[level], h->h64.u[level - 1], h->d, h->nl[level],
-                                             h->M, h->stream));
-    h->h64.rs[level] = R_STALE;
-  } else {
-    MGWR_CK(h, mgwr::launch_prolong<float>(h->h32.u[level], h->h32.u[level - 1], h->d, h->nl[level],
-                                            h->M, h->stream));
-    h->h32.rs[level] = R_STALE;
-  }
+  if (hierarchy == MGWR_H64)
+    MGWR_TRY(prolong_into(h, h->h64, level));
+  else
+    MGWR_TRY(prolong_into(h, h->h32, level));
   MGWR_CK(h, cudaStreamSynchronize(h->stream));
   return MGWR_OK;
 }
@@ -851,7 +951,8 @@ int mgwr_cycle(mgwr_t h, int hierarchy, int cyc, int nu1, int nu2) {
 
 int mgwr_toeplitz_column(mgwr_t h, double* r_host) {
   if (h == nullptr || r_host == nullptr) return MGWR_E_INVAL;
-  MGWR_CK(h, cudaMemcpyAsync(r_host, h->r, sizeof(double) * h->M, cudaMemcpyDeviceToHost, h->stream));
+  MGWR_CK(h, cudaMemcpyAsync(r_host, h->r, sizeof(double) * h->M * h->B, cudaMemcpyDeviceToHost,
+                             h->stream));
   MGWR_CK(h, cudaStreamSynchronize(h->stream));
   return MGWR_OK;
 }
@@ -859,8 +960,10 @@ int mgwr_toeplitz_column(mgwr_t h, double* r_host) {
 int mgwr_inverse_column(mgwr_t h, int level, double* k_host) {
   if (h == nullptr || k_host == nullptr) return MGWR_E_INVAL;
   if (level < 0 || level >= h->nlev) return fail(h, MGWR_E_INVAL, "level out of range");
-  MGWR_CK(h, cudaMemcpyAsync(k_host, h->kcol + (size_t)level * h->M, sizeof(double) * h->M,
-                             cudaMemcpyDeviceToHost, h->stream));
+  for (int b = 0; b < h->B; ++b)
+    MGWR_CK(h, cudaMemcpyAsync(k_host + (size_t)b * h->M,
+                               h->kcol + ((size_t)b * h->nlev + level) * h->M,
+                               sizeof(double) * h->M, cudaMemcpyDeviceToHost, h->stream));
   MGWR_CK(h, cudaStreamSynchronize(h->stream));
   return MGWR_OK;
 }

@@ -20,55 +20,67 @@ struct alignas(2 * sizeof(R)) Cx {
 // in that order, pre-scaled by 1/L, and the inverse cascade consumes it.  Only
 // products of two such spectra are ever formed, so the order never matters.
 
+// Shape of one level of a batch of same-shape instances: n^d lines of M
+// values per instance, instances stored one after another.
+struct LevelShape {
+  int d, n, M, batch;
+  size_t field_stride() const { return (size_t)(d == 1 ? n : n * n) * M; }
+};
+
 // ---- launchers (kernels in mgwr_kernels.cu); all return the launch status ----
+// Every launcher covers all `batch` instances (blockIdx.y = instance).
 
 // One colour half-sweep (Sec. 3 Eq. red-black, Sec. 6 Eq. red-black_2d): for
 // each point p of parity `par`, u_p = k * (f_p + hinv2 * sum of neighbour
-// lines), k the inverse column whose spectrum is `spec`.  all_points: every
-// point, no neighbour term (one-point coarsest solve).  delta != null: also
-// delta_p = u_p(new) - u_p(old) on the swept lines.
+// lines), k the inverse column whose spectrum is `spec` (instance b's at
+// spec + b * spec_stride).  all_points: every point, no neighbour term
+// (one-point coarsest solve).  delta != null: also delta_p = u_p(new) -
+// u_p(old) on the swept lines.
 template <class R>
-cudaError_t launch_sweep(const R* f, R* u, R* delta, const Cx<R>* spec, const Cx<R>* tw, int d,
-                         int n, int M, int par, bool all_points, R hinv2, cudaStream_t s);
+cudaError_t launch_sweep(const R* f, R* u, R* delta, const Cx<R>* spec, size_t spec_stride,
+                         const Cx<R>* tw, const LevelShape& ls, int par, bool all_points, R hinv2,
+                         cudaStream_t s);
 
 // Defect after a red-black step from the black half-sweep's delta: r = 0 on the
 // black points, r = hinv2 * sum of neighbour deltas on the red points
-// (parity red_par); |r|_inf folded into *norm_bits when non-null.
+// (parity red_par); |r|_inf of instance b folded into norm_bits[b].
 template <class R>
-cudaError_t launch_defect_from_delta(const R* delta, R* r, int d, int n, int M, int red_par,
+cudaError_t launch_defect_from_delta(const R* delta, R* r, const LevelShape& ls, int red_par,
                                      R hinv2, unsigned long long* norm_bits, cudaStream_t s);
 
-// r = f - T_M u - A_h u for all points; |r|_inf folded into *norm_bits
-// (bit pattern of a non-negative double, atomicMax) when norm_bits != null.
+// r = f - T_M u - A_h u for all points; |r|_inf of instance b folded into
+// norm_bits[b] (bit pattern of a non-negative double, atomicMax) when non-null.
 template <class R, class RO>
-cudaError_t launch_defect(const R* u, const R* f, RO* r, const Cx<R>* tspec, const Cx<R>* tw,
-                          int d, int n, int M, R hinv2, unsigned long long* norm_bits,
-                          cudaStream_t s);
+cudaError_t launch_defect(const R* u, const R* f, RO* r, const Cx<R>* tspec, size_t spec_stride,
+                          const Cx<R>* tw, const LevelShape& ls, R hinv2,
+                          unsigned long long* norm_bits, cudaStream_t s);
 
 // fc = full weighting of r (fine n -> coarse (n-1)/2), uc = 0.
 template <class R>
-cudaError_t launch_restrict(const R* r, R* fc, R* uc, int d, int n, int M, cudaStream_t s);
+cudaError_t launch_restrict(const R* r, R* fc, R* uc, const LevelShape& fine, cudaStream_t s);
 
 // u (fine, n) += linear / bilinear interpolation of uc (coarse (n-1)/2).
 template <class R>
-cudaError_t launch_prolong(R* u, const R* uc, int d, int n, int M, cudaStream_t s);
+cudaError_t launch_prolong(R* u, const R* uc, const LevelShape& fine, cudaStream_t s);
 
 // u += (double) e, elementwise.
 cudaError_t launch_refine(double* u, const float* e, size_t count, cudaStream_t s);
 // dst = (float) src.
 cudaError_t launch_round(float* dst, const double* src, size_t count, cudaStream_t s);
-// u = broadcast of g along time (initial iterate u^0(t) = g); f += c d_m g.
-cudaError_t launch_initial(double* u, double* f, const double* g, const double* dk, double c,
-                           int N, int M, cudaStream_t s);
+// Per instance b: u = broadcast of g_b along time (initial iterate u^0(t) = g);
+// f += c_b d_{b,m} g_b.  g: batch * N, dk: batch * (M+1), c: batch (device).
+cudaError_t launch_initial(double* u, double* f, const double* g, const double* dk, const double* c,
+                           int N, int M, int batch, cudaStream_t s);
 
 // ---- setup (FP64) ----
-// r[i] = r_{i+1}, i < M; dk[m] = d_m, m <= M (L1 weights, d_0 = 0).
-cudaError_t launch_coefficients(double* r, double* dk, int M, double alpha, double c,
-                                cudaStream_t s);
-// For each level l < nlev: kcol[l*M ..] = first column of (T_M + sigma[l] I)^{-1}
-// by divide and conquer with FFT convolutions; work: 3*M complex per level.
-cudaError_t launch_inverse_columns(double* kcol, const double* r, const double* sigma,
-                                   int nlev, int M, Cx<double>* work, cudaStream_t s);
+// Per instance b: r[b*M + i] = r_{i+1}, dk[b*(M+1) + m] = d_m (d_0 = 0), from
+// alphas[b] and cs[b] = tau_b^-alpha_b / Gamma(2 - alpha_b) (device arrays).
+cudaError_t launch_coefficients(double* r, double* dk, int M, const double* alphas,
+                                const double* cs, int batch, cudaStream_t s);
+// kcol[(b*nlev + l)*M ..] = first column of (T_{M,b} + sigma[l] I)^{-1} by
+// divide and conquer with FFT convolutions; work: 3*M complex per (b, l).
+cudaError_t launch_inverse_columns(double* kcol, const double* r, const double* sigma, int nlev,
+                                   int M, int batch, Cx<double>* work, cudaStream_t s);
 // tw[m] = exp(-2 pi i m / L), m < L.
 cudaError_t launch_twiddles(Cx<double>* tw, int L, cudaStream_t s);
 // spec[k*L ..] = FFT_L(pad(lines[k*M ..])) / L in the library's spectral order.

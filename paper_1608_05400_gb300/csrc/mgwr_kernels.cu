@@ -96,8 +96,14 @@ template <class R, int BLOCK>
 __global__ void __launch_bounds__(BLOCK)
     k_sweep(const R* __restrict__ f, R* __restrict__ u, R* __restrict__ delta,
             const Cx<R>* __restrict__ spec, const Cx<R>* __restrict__ tw, int d, int n, int M,
-            int logL, int par, int all_points, R hinv2, int npts, int npairs) {
+            int logL, int par, int all_points, R hinv2, int npts, int npairs, size_t fstride,
+            size_t sstride) {
   extern __shared__ unsigned char smem_raw[];
+  // instance of a batch: blockIdx.y
+  f += blockIdx.y * fstride;
+  u += blockIdx.y * fstride;
+  if (delta != nullptr) delta += blockIdx.y * fstride;
+  spec += blockIdx.y * sstride;
   Cx<R>* smem = reinterpret_cast<Cx<R>*>(smem_raw);
   const FftShape sh(logL);
   const int TL = sh.L8;
@@ -186,8 +192,11 @@ template <class R>
 __global__ void __launch_bounds__(128)
     k_defect_from_delta(const R* __restrict__ delta, R* __restrict__ r, int d, int n, int M,
                         int log_tpl, int npts, int red_par, R hinv2,
-                        unsigned long long* __restrict__ norm_bits) {
+                        unsigned long long* __restrict__ norm_bits, size_t fstride) {
   const LineMap lm(log_tpl);
+  delta += blockIdx.y * fstride;
+  r += blockIdx.y * fstride;
+  if (norm_bits != nullptr) norm_bits += blockIdx.y;
   double amax = 0.0;
   if (lm.line < npts) {
     const int p = lm.line;
@@ -229,8 +238,14 @@ template <class R, class RO, int BLOCK>
 __global__ void __launch_bounds__(BLOCK)
     k_defect(const R* __restrict__ u, const R* __restrict__ f, RO* __restrict__ r,
              const Cx<R>* __restrict__ tspec, const Cx<R>* __restrict__ tw, int d, int n, int M,
-             int logL, R hinv2, int npts, int npairs, unsigned long long* __restrict__ norm_bits) {
+             int logL, R hinv2, int npts, int npairs, unsigned long long* __restrict__ norm_bits,
+             size_t fstride, size_t sstride) {
   extern __shared__ unsigned char smem_raw[];
+  u += blockIdx.y * fstride;
+  f += blockIdx.y * fstride;
+  r += blockIdx.y * fstride;
+  tspec += blockIdx.y * sstride;
+  if (norm_bits != nullptr) norm_bits += blockIdx.y;
   __shared__ double red[BLOCK / 32];
   Cx<R>* smem = reinterpret_cast<Cx<R>*>(smem_raw);
   const FftShape sh(logL);
@@ -299,8 +314,11 @@ __global__ void __launch_bounds__(BLOCK)
 template <class R>
 __global__ void __launch_bounds__(128)
     k_restrict(const R* __restrict__ r, R* __restrict__ fc, R* __restrict__ uc, int d, int n, int M,
-               int log_tpl, int ncpts) {
+               int log_tpl, int ncpts, size_t fstride, size_t cstride) {
   const LineMap lm(log_tpl);
+  r += blockIdx.y * fstride;
+  fc += blockIdx.y * cstride;
+  uc += blockIdx.y * cstride;
   if (lm.line >= ncpts) return;
   const int nc = (n - 1) / 2;
   const int P = lm.line;
@@ -360,8 +378,10 @@ struct Taps {
 template <class R>
 __global__ void __launch_bounds__(128)
     k_prolong(R* __restrict__ u, const R* __restrict__ uc, int d, int n, int M, int log_tpl,
-              int npts) {
+              int npts, size_t fstride, size_t cstride) {
   const LineMap lm(log_tpl);
+  u += blockIdx.y * fstride;
+  uc += blockIdx.y * cstride;
   if (lm.line >= npts) return;
   const int nc = (n - 1) / 2;
   const int p = lm.line;
@@ -402,16 +422,23 @@ __global__ void k_round(float* __restrict__ dst, const double* __restrict__ src,
     dst[i] = (float)src[i];
 }
 
+// Initial value g of every instance (blockIdx.y): u = g along time (initial
+// iterate u^0(t) = g) and f += c d_m g (the u_0 term of the L1 scheme).
 __global__ void k_initial(double* __restrict__ u, double* __restrict__ f,
-                          const double* __restrict__ g, const double* __restrict__ dk, double c,
-                          int N, int M) {
-  const size_t total = (size_t)N * M;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
-       i += (size_t)gridDim.x * blockDim.x) {
-    const size_t p = i / M;
-    const int m = (int)(i - p * M);
-    u[i] = g[p];
-    f[i] += c * dk[m + 1] * g[p];
+                          const double* __restrict__ g, const double* __restrict__ dk,
+                          const double* __restrict__ c, int N, int M) {
+  const size_t stride = (size_t)N * M;
+  u += blockIdx.y * stride;
+  f += blockIdx.y * stride;
+  g += (size_t)blockIdx.y * N;
+  dk += (size_t)blockIdx.y * (M + 1);
+  const double cb = c[blockIdx.y];
+  for (int p = blockIdx.x; p < N; p += gridDim.x) {
+    const double gp = g[p];
+    for (int m = threadIdx.x; m < M; m += blockDim.x) {
+      u[(size_t)p * M + m] = gp;
+      f[(size_t)p * M + m] += cb * dk[m + 1] * gp;
+    }
   }
 }
 
@@ -424,8 +451,11 @@ __global__ void k_initial(double* __restrict__ u, double* __restrict__ f,
 // is summed as its binomial series 2 sum_{k>=1} C(b, 2k) y^{2k}, whose terms all
 // have the sign of C(b, 2) < 0, so no cancellation occurs.  d_m (for the
 // initial-value term) is accumulated by the telescoping sum d_m = sum r_i / c.
-__global__ void k_coefficients(double* __restrict__ r, int M, double alpha, double c) {
-  const double b = 1.0 - alpha;
+__global__ void k_coefficients(double* __restrict__ r, int M, const double* __restrict__ alphas,
+                               const double* __restrict__ cs) {
+  r += (size_t)blockIdx.y * M;
+  const double b = 1.0 - alphas[blockIdx.y];
+  const double c = cs[blockIdx.y];
   for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < M; i0 += gridDim.x * blockDim.x) {
     const int i = i0 + 1;
     double val;
@@ -452,8 +482,12 @@ __global__ void k_coefficients(double* __restrict__ r, int M, double alpha, doub
 
 // d_0 = 0, d_m = d_{m-1} + r_m / c (sequential; setup only).
 __global__ void k_weights_from_column(double* __restrict__ dk, const double* __restrict__ r, int M,
-                                      double c) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+                                      const double* __restrict__ cs, int batch) {
+  const int inst = blockIdx.x * blockDim.x + threadIdx.x;
+  if (inst < batch) {
+    dk += (size_t)inst * (M + 1);
+    r += (size_t)inst * M;
+    const double c = cs[inst];
     double acc = 0.0;
     dk[0] = 0.0;
     for (int m = 1; m <= M; ++m) {
@@ -500,9 +534,12 @@ __device__ void block_fft_radix2(Cx<double>* x, int N, int logN, bool inv) {
 __global__ void k_inverse_columns(double* __restrict__ kcol, const double* __restrict__ r,
                                   const double* __restrict__ sigma, int M,
                                   Cx<double>* __restrict__ work) {
+  // block (l, b): level l of instance b; columns and work are instance-major
   const int l = blockIdx.x;
-  double* k = kcol + (size_t)l * M;
-  Cx<double>* X = work + (size_t)l * 3 * M;
+  const size_t slot = (size_t)blockIdx.y * gridDim.x + l;
+  r += (size_t)blockIdx.y * M;
+  double* k = kcol + slot * M;
+  Cx<double>* X = work + slot * 3 * M;
   Cx<double>* Y = X + M;
   Cx<double>* Z = Y + M;
   const double a0 = r[0] + sigma[l];
@@ -610,70 +647,77 @@ inline unsigned elementwise_grid(size_t total) {
 }  // namespace
 
 template <class R>
-cudaError_t launch_sweep(const R* f, R* u, R* delta, const Cx<R>* spec, const Cx<R>* tw, int d,
-                         int n, int M, int par, bool all_points, R hinv2, cudaStream_t s) {
+cudaError_t launch_sweep(const R* f, R* u, R* delta, const Cx<R>* spec, size_t spec_stride,
+                         const Cx<R>* tw, const LevelShape& ls, int par, bool all_points, R hinv2,
+                         cudaStream_t s) {
+  const int d = ls.d, n = ls.n, M = ls.M;
   const int L = 2 * M, logL = ilog2(L);
   const int npts = all_points ? (d == 1 ? n : n * n) : colour_count(d, n, par);
   const int npairs = (npts + 1) / 2;
-  if (npairs == 0) return cudaSuccess;
+  if (npairs == 0 || ls.batch == 0) return cudaSuccess;
+  const size_t fstride = ls.field_stride();
   const int block = block_threads(L);
   const int groups = block / (L / 8);
   const size_t smem = (size_t)groups * padded_len(L) * sizeof(Cx<R>);
-  const unsigned grid = (unsigned)((npairs + groups - 1) / groups);
+  const dim3 grid((unsigned)((npairs + groups - 1) / groups), (unsigned)ls.batch);
   cudaError_t e;
   switch (block) {
     case 256:
       e = prepare_smem(k_sweep<R, 256>, smem);
       if (e != cudaSuccess) return e;
       k_sweep<R, 256><<<grid, 256, smem, s>>>(f, u, delta, spec, tw, d, n, M, logL, par, all_points,
-                                              hinv2, npts, npairs);
+                                              hinv2, npts, npairs, fstride, spec_stride);
       break;
     case 512:
       e = prepare_smem(k_sweep<R, 512>, smem);
       if (e != cudaSuccess) return e;
       k_sweep<R, 512><<<grid, 512, smem, s>>>(f, u, delta, spec, tw, d, n, M, logL, par, all_points,
-                                              hinv2, npts, npairs);
+                                              hinv2, npts, npairs, fstride, spec_stride);
       break;
     default:
       e = prepare_smem(k_sweep<R, 1024>, smem);
       if (e != cudaSuccess) return e;
-      k_sweep<R, 1024><<<grid, 1024, smem, s>>>(f, u, delta, spec, tw, d, n, M, logL, par, all_points,
-                                                hinv2, npts, npairs);
+      k_sweep<R, 1024><<<grid, 1024, smem, s>>>(f, u, delta, spec, tw, d, n, M, logL, par,
+                                                all_points, hinv2, npts, npairs, fstride,
+                                                spec_stride);
       break;
   }
   return counted(cudaGetLastError());
 }
 
 template <class R, class RO>
-cudaError_t launch_defect(const R* u, const R* f, RO* r, const Cx<R>* tspec, const Cx<R>* tw,
-                          int d, int n, int M, R hinv2, unsigned long long* norm_bits,
-                          cudaStream_t s) {
+cudaError_t launch_defect(const R* u, const R* f, RO* r, const Cx<R>* tspec, size_t spec_stride,
+                          const Cx<R>* tw, const LevelShape& ls, R hinv2,
+                          unsigned long long* norm_bits, cudaStream_t s) {
+  const int d = ls.d, n = ls.n, M = ls.M;
   const int L = 2 * M, logL = ilog2(L);
   const int npts = d == 1 ? n : n * n;
   const int npairs = (npts + 1) / 2;
+  if (ls.batch == 0) return cudaSuccess;
+  const size_t fstride = ls.field_stride();
   const int block = block_threads(L);
   const int groups = block / (L / 8);
   const size_t smem = (size_t)groups * padded_len(L) * sizeof(Cx<R>);
-  const unsigned grid = (unsigned)((npairs + groups - 1) / groups);
+  const dim3 grid((unsigned)((npairs + groups - 1) / groups), (unsigned)ls.batch);
   cudaError_t e;
   switch (block) {
     case 256:
       e = prepare_smem(k_defect<R, RO, 256>, smem);
       if (e != cudaSuccess) return e;
       k_defect<R, RO, 256><<<grid, 256, smem, s>>>(u, f, r, tspec, tw, d, n, M, logL, hinv2, npts,
-                                                   npairs, norm_bits);
+                                                   npairs, norm_bits, fstride, spec_stride);
       break;
     case 512:
       e = prepare_smem(k_defect<R, RO, 512>, smem);
       if (e != cudaSuccess) return e;
       k_defect<R, RO, 512><<<grid, 512, smem, s>>>(u, f, r, tspec, tw, d, n, M, logL, hinv2, npts,
-                                                   npairs, norm_bits);
+                                                   npairs, norm_bits, fstride, spec_stride);
       break;
     default:
       e = prepare_smem(k_defect<R, RO, 1024>, smem);
       if (e != cudaSuccess) return e;
       k_defect<R, RO, 1024><<<grid, 1024, smem, s>>>(u, f, r, tspec, tw, d, n, M, logL, hinv2,
-                                                     npts, npairs, norm_bits);
+                                                     npts, npairs, norm_bits, fstride, spec_stride);
       break;
   }
   return counted(cudaGetLastError());
@@ -689,36 +733,42 @@ inline void line_grid(int M, int lines, int* log_tpl, unsigned* blocks) {
 }
 
 template <class R>
-cudaError_t launch_defect_from_delta(const R* delta, R* r, int d, int n, int M, int red_par, R hinv2,
-                                     unsigned long long* norm_bits, cudaStream_t s) {
-  const int npts = d == 1 ? n : n * n;
+cudaError_t launch_defect_from_delta(const R* delta, R* r, const LevelShape& ls, int red_par,
+                                     R hinv2, unsigned long long* norm_bits, cudaStream_t s) {
+  const int npts = ls.d == 1 ? ls.n : ls.n * ls.n;
+  if (ls.batch == 0) return cudaSuccess;
   int log_tpl;
   unsigned blocks;
-  line_grid(M, npts, &log_tpl, &blocks);
-  k_defect_from_delta<R><<<blocks, 128, 0, s>>>(delta, r, d, n, M, log_tpl, npts, red_par, hinv2,
-                                                norm_bits);
+  line_grid(ls.M, npts, &log_tpl, &blocks);
+  k_defect_from_delta<R><<<dim3(blocks, ls.batch), 128, 0, s>>>(
+      delta, r, ls.d, ls.n, ls.M, log_tpl, npts, red_par, hinv2, norm_bits, ls.field_stride());
   return counted(cudaGetLastError());
 }
 
 template <class R>
-cudaError_t launch_restrict(const R* r, R* fc, R* uc, int d, int n, int M, cudaStream_t s) {
-  const int nc = (n - 1) / 2;
-  const int ncpts = d == 1 ? nc : nc * nc;
-  if (ncpts == 0) return cudaSuccess;
+cudaError_t launch_restrict(const R* r, R* fc, R* uc, const LevelShape& ls, cudaStream_t s) {
+  const int nc = (ls.n - 1) / 2;
+  const int ncpts = ls.d == 1 ? nc : nc * nc;
+  if (ncpts == 0 || ls.batch == 0) return cudaSuccess;
   int log_tpl;
   unsigned blocks;
-  line_grid(M, ncpts, &log_tpl, &blocks);
-  k_restrict<R><<<blocks, 128, 0, s>>>(r, fc, uc, d, n, M, log_tpl, ncpts);
+  line_grid(ls.M, ncpts, &log_tpl, &blocks);
+  k_restrict<R><<<dim3(blocks, ls.batch), 128, 0, s>>>(r, fc, uc, ls.d, ls.n, ls.M, log_tpl, ncpts,
+                                                       ls.field_stride(), (size_t)ncpts * ls.M);
   return counted(cudaGetLastError());
 }
 
 template <class R>
-cudaError_t launch_prolong(R* u, const R* uc, int d, int n, int M, cudaStream_t s) {
-  const int npts = d == 1 ? n : n * n;
+cudaError_t launch_prolong(R* u, const R* uc, const LevelShape& ls, cudaStream_t s) {
+  const int npts = ls.d == 1 ? ls.n : ls.n * ls.n;
+  const int nc = (ls.n - 1) / 2;
+  const size_t cstride = (size_t)(ls.d == 1 ? nc : nc * nc) * ls.M;
+  if (ls.batch == 0) return cudaSuccess;
   int log_tpl;
   unsigned blocks;
-  line_grid(M, npts, &log_tpl, &blocks);
-  k_prolong<R><<<blocks, 128, 0, s>>>(u, uc, d, n, M, log_tpl, npts);
+  line_grid(ls.M, npts, &log_tpl, &blocks);
+  k_prolong<R><<<dim3(blocks, ls.batch), 128, 0, s>>>(u, uc, ls.d, ls.n, ls.M, log_tpl, npts,
+                                                      ls.field_stride(), cstride);
   return counted(cudaGetLastError());
 }
 
@@ -732,24 +782,25 @@ cudaError_t launch_round(float* dst, const double* src, size_t count, cudaStream
   return counted(cudaGetLastError());
 }
 
-cudaError_t launch_initial(double* u, double* f, const double* g, const double* dk, double c,
-                           int N, int M, cudaStream_t s) {
-  k_initial<<<elementwise_grid((size_t)N * M), 256, 0, s>>>(u, f, g, dk, c, N, M);
+cudaError_t launch_initial(double* u, double* f, const double* g, const double* dk, const double* c,
+                           int N, int M, int batch, cudaStream_t s) {
+  const unsigned bx = (unsigned)(N < 1024 ? N : 1024);
+  k_initial<<<dim3(bx, batch), 256, 0, s>>>(u, f, g, dk, c, N, M);
   return counted(cudaGetLastError());
 }
 
-cudaError_t launch_coefficients(double* r, double* dk, int M, double alpha, double c,
-                                cudaStream_t s) {
-  k_coefficients<<<(M + 255) / 256, 256, 0, s>>>(r, M, alpha, c);
+cudaError_t launch_coefficients(double* r, double* dk, int M, const double* alphas,
+                                const double* cs, int batch, cudaStream_t s) {
+  k_coefficients<<<dim3((M + 255) / 256, batch), 256, 0, s>>>(r, M, alphas, cs);
   cudaError_t e = counted(cudaGetLastError());
   if (e != cudaSuccess) return e;
-  k_weights_from_column<<<1, 32, 0, s>>>(dk, r, M, c);
+  k_weights_from_column<<<(batch + 63) / 64, 64, 0, s>>>(dk, r, M, cs, batch);
   return counted(cudaGetLastError());
 }
 
 cudaError_t launch_inverse_columns(double* kcol, const double* r, const double* sigma, int nlev,
-                                   int M, Cx<double>* work, cudaStream_t s) {
-  k_inverse_columns<<<nlev, 512, 0, s>>>(kcol, r, sigma, M, work);
+                                   int M, int batch, Cx<double>* work, cudaStream_t s) {
+  k_inverse_columns<<<dim3(nlev, batch), 512, 0, s>>>(kcol, r, sigma, M, work);
   return counted(cudaGetLastError());
 }
 
@@ -792,30 +843,27 @@ cudaError_t launch_round_cx(Cx<float>* dst, const Cx<double>* src, size_t count,
 }
 
 // explicit instantiations
-template cudaError_t launch_sweep<double>(const double*, double*, double*, const Cx<double>*,
-                                          const Cx<double>*, int, int, int, int, bool, double,
-                                          cudaStream_t);
-template cudaError_t launch_sweep<float>(const float*, float*, float*, const Cx<float>*,
-                                         const Cx<float>*, int, int, int, int, bool, float,
-                                         cudaStream_t);
-template cudaError_t launch_defect_from_delta<double>(const double*, double*, int, int, int, int,
-                                                      double, unsigned long long*, cudaStream_t);
-template cudaError_t launch_defect_from_delta<float>(const float*, float*, int, int, int, int, float,
-                                                     unsigned long long*, cudaStream_t);
+#define MGWR_INST_R(R)                                                                         \
+  template cudaError_t launch_sweep<R>(const R*, R*, R*, const Cx<R>*, size_t, const Cx<R>*,  \
+                                       const LevelShape&, int, bool, R, cudaStream_t);         \
+  template cudaError_t launch_defect_from_delta<R>(const R*, R*, const LevelShape&, int, R,    \
+                                                   unsigned long long*, cudaStream_t);         \
+  template cudaError_t launch_restrict<R>(const R*, R*, R*, const LevelShape&, cudaStream_t);  \
+  template cudaError_t launch_prolong<R>(R*, const R*, const LevelShape&, cudaStream_t);
+MGWR_INST_R(double)
+MGWR_INST_R(float)
+#undef MGWR_INST_R
 template cudaError_t launch_defect<double, double>(const double*, const double*, double*,
-                                                   const Cx<double>*, const Cx<double>*, int, int,
-                                                   int, double, unsigned long long*, cudaStream_t);
+                                                   const Cx<double>*, size_t, const Cx<double>*,
+                                                   const LevelShape&, double, unsigned long long*,
+                                                   cudaStream_t);
 template cudaError_t launch_defect<double, float>(const double*, const double*, float*,
-                                                  const Cx<double>*, const Cx<double>*, int, int,
-                                                  int, double, unsigned long long*, cudaStream_t);
+                                                  const Cx<double>*, size_t, const Cx<double>*,
+                                                  const LevelShape&, double, unsigned long long*,
+                                                  cudaStream_t);
 template cudaError_t launch_defect<float, float>(const float*, const float*, float*,
-                                                 const Cx<float>*, const Cx<float>*, int, int, int,
-                                                 float, unsigned long long*, cudaStream_t);
-template cudaError_t launch_restrict<double>(const double*, double*, double*, int, int, int,
-                                             cudaStream_t);
-template cudaError_t launch_restrict<float>(const float*, float*, float*, int, int, int,
-                                            cudaStream_t);
-template cudaError_t launch_prolong<double>(double*, const double*, int, int, int, cudaStream_t);
-template cudaError_t launch_prolong<float>(float*, const float*, int, int, int, cudaStream_t);
+                                                 const Cx<float>*, size_t, const Cx<float>*,
+                                                 const LevelShape&, float, unsigned long long*,
+                                                 cudaStream_t);
 
 }  // namespace mgwr

@@ -65,7 +65,7 @@ extern "C" int mgwr_inverse_column_noalloc(const double* r_dev, int M, double si
   // written before it is read inside the kernel)
   cudaError_t e = cudaMemcpyAsync(scratch, &sigma, sizeof(double), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
-    e = mgwr::launch_inverse_columns(k_dev, r_dev, scratch, 1, M,
+    e = mgwr::launch_inverse_columns(k_dev, r_dev, scratch, 1, M, 1,
                                      reinterpret_cast<mgwr::Cx<double>*>(scratch + kSigmaSlots), s);
   if (e != cudaSuccess) {
     cudaGetLastError();

@@ -42,6 +42,9 @@ _h = C.c_void_p
 _dp = C.POINTER(C.c_double)
 _SIGS = {
     "mgwr_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.POINTER(_h)]),
+    "mgwr_create_batch": (C.c_int, [C.c_int, C.c_int, C.c_int, _dp, _dp, C.c_int, C.POINTER(_h)]),
+    "mgwr_batch_size": (C.c_int, [_h, C.POINTER(C.c_int)]),
+    "mgwr_instance_relres": (C.c_int, [_h, _dp]),
     "mgwr_destroy": (C.c_int, [_h]),
     "mgwr_last_error": (C.c_char_p, [_h]),
     "mgwr_status_string": (C.c_char_p, [C.c_int]),
@@ -127,18 +130,28 @@ class Stats:
 
 
 class Solver:
-    """One MGWR problem (d, n, M, T, alpha) living on the current CUDA device."""
+    """MGWR problems (d, n, M) on the current CUDA device: one instance
+    (T and alpha scalars) or a batch (T and alpha sequences of equal length).
+    Field arrays are (N, M) for one instance and (batch, N, M) for a batch."""
 
-    def __init__(self, d: int, n: int, M: int, T: float, alpha: float):
+    def __init__(self, d: int, n: int, M: int, T, alpha):
         self.lib = load()
+        self.batched = np.ndim(alpha) > 0
+        alphas = np.atleast_1d(np.asarray(alpha, dtype=np.float64))
+        Ts = np.broadcast_to(np.asarray(T, dtype=np.float64), alphas.shape).copy()
         self.d, self.n, self.M, self.T, self.alpha = d, n, M, T, alpha
         self.N = n ** d
+        self.B = int(alphas.size)
         h = _h()
-        st = self.lib.mgwr_create(d, n, M, T, alpha, C.byref(h))
+        st = self.lib.mgwr_create_batch(d, n, M, _ptr(Ts), _ptr(alphas), self.B, C.byref(h))
         if st != MGWR_OK:
-            raise MGWRError(st, f"mgwr_create({d}, {n}, {M}, {T}, {alpha}) failed: "
+            raise MGWRError(st, f"mgwr_create_batch({d}, {n}, {M}, batch={self.B}) failed: "
                             + self.lib.mgwr_status_string(st).decode())
         self.h = h
+
+    def _shape(self, N=None):
+        N = self.N if N is None else N
+        return (self.B, N, self.M) if self.batched else (N, self.M)
 
     # -- plumbing --
     def _check(self, st: int, what: str, ok=(MGWR_OK,)):
@@ -179,8 +192,8 @@ class Solver:
     # -- data --
     def set_rhs(self, f: np.ndarray, g: np.ndarray | None = None):
         f = _f64(f)
-        assert f.shape == (self.N, self.M), f.shape
-        g = None if g is None else _f64(g).reshape(self.N)
+        assert f.shape == self._shape(), f.shape
+        g = None if g is None else _f64(g).reshape(self.B * self.N)
         self._check(self.lib.mgwr_set_rhs(self.h, _ptr(f), _ptr(g)), "mgwr_set_rhs")
 
     def set_rhs_dev(self, f_ptr: int, g_ptr: int | None = None):
@@ -189,7 +202,7 @@ class Solver:
 
     def set_initial(self, u0: np.ndarray):
         u0 = _f64(u0)
-        assert u0.shape == (self.N, self.M)
+        assert u0.shape == self._shape()
         self._check(self.lib.mgwr_set_initial(self.h, _ptr(u0)), "mgwr_set_initial")
 
     def solve(self, cycle=1, nu1=1, nu2=1, tol=1e-10, max_cycles=100, allow_noconv=False) -> Stats:
@@ -201,12 +214,17 @@ class Solver:
 
     def residual(self, want_field=False):
         rel = C.c_double()
-        r = np.empty((self.N, self.M)) if want_field else None
+        r = np.empty(self._shape()) if want_field else None
         self._check(self.lib.mgwr_residual(self.h, C.byref(rel), _ptr(r)), "mgwr_residual")
         return (rel.value, r) if want_field else rel.value
 
+    def instance_relres(self) -> np.ndarray:
+        out = np.empty(self.B)
+        self._check(self.lib.mgwr_instance_relres(self.h, _ptr(out)), "mgwr_instance_relres")
+        return out
+
     def solution(self) -> np.ndarray:
-        u = np.empty((self.N, self.M))
+        u = np.empty(self._shape())
         self._check(self.lib.mgwr_get_solution(self.h, _ptr(u)), "mgwr_get_solution")
         return u
 
@@ -227,12 +245,12 @@ class Solver:
     def field_set(self, hier: int, level: int, which: int, a: np.ndarray):
         a = _f64(a)
         nl = self.level_n(level)
-        assert a.shape == (nl ** self.d, self.M), a.shape
+        assert a.shape == self._shape(nl ** self.d), a.shape
         self._check(self.lib.mgwr_field_set(self.h, hier, level, which, _ptr(a)), "mgwr_field_set")
 
     def field_get(self, hier: int, level: int, which: int) -> np.ndarray:
         nl = self.level_n(level)
-        a = np.empty((nl ** self.d, self.M))
+        a = np.empty(self._shape(nl ** self.d))
         self._check(self.lib.mgwr_field_get(self.h, hier, level, which, _ptr(a)), "mgwr_field_get")
         return a
 
@@ -274,12 +292,12 @@ class Solver:
         return out
 
     def toeplitz_column(self) -> np.ndarray:
-        r = np.empty(self.M)
+        r = np.empty((self.B, self.M) if self.batched else self.M)
         self._check(self.lib.mgwr_toeplitz_column(self.h, _ptr(r)), "mgwr_toeplitz_column")
         return r
 
     def inverse_column(self, level: int) -> np.ndarray:
-        k = np.empty(self.M)
+        k = np.empty((self.B, self.M) if self.batched else self.M)
         self._check(self.lib.mgwr_inverse_column(self.h, level, _ptr(k)), "mgwr_inverse_column")
         return k
 

@@ -44,10 +44,11 @@ WORKLOADS = {
     "c2": (2, 255, 1024, 1, "t2", 1e-10, "fp64",
            "2-D plain MGWR 255x255 interior, M=1024 on (0,1], u=t^2 sin(pi x) sin(pi y)"),
     "c1": (1, 63, 64, 1, "t2", 1e-10, "fp64", "1-D plain MGWR 63 interior points, M=64, u=t^2 sin(pi x)"),
-    "c3": (2, 511, 4096, 1, "talpha", 1e-8, "mixed",
+    "c3": (2, 511, 4096, 1, "talpha", 1e-8, "mixed_dd",
            "2-D MGWR 511x511 interior, M=4096, u=t^alpha sin(pi x) sin(pi y)"),
-    "c5a": (2, 63, 256, 4096, "t2", 1e-8, "mixed",
+    "c5a": (2, 63, 256, 4096, "t2", 1e-8, "mixed_dd",
             "4096 independent 2-D 63x63, M=256 solves, alpha~U[0.1,0.9] (seed 1608), one batched handle"),
+    "c4": (0, 0, 0, 0, "", 1e-8, "mixed_dd", "served stream"),
 }
 UNIT = "unknowns/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -63,8 +64,10 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--precision", default=None, choices=["fp64", "mixed"])
+    p.add_argument("--precision", default=None, choices=["fp64", "mixed", "mixed_dd"])
     p.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    p.add_argument("--requests", type=int, default=200, help="c4: first R requests of the stream")
+    p.add_argument("--slots", type=int, default=4, help="c4: server slots")
     p.add_argument("--alpha", type=float, default=ALPHA)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
@@ -240,10 +243,94 @@ def run_reference(args):
     return 0
 
 
+def run_served(args):
+    """Config 4: a stream of mixed-shape requests through mgwr_submit / mgwr_poll.
+
+    Pass 1 submits the whole list at once and measures the sustained rate;
+    pass 2 replays it with Poisson arrivals at 0.7 x that rate and records the
+    latency of every request (submit -> result ready)."""
+    import threading
+
+    import torch
+
+    from paper_1608_05400_gb300 import inputs, mgwr
+
+    torch.cuda.set_device(0)
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(0.8 * free)
+    reqs = inputs.request_stream(count=2000, seed=1608, rate=1.0)[: args.requests]
+    tol = WORKLOADS["c4"][5]
+
+    def rhs(rq):
+        return inputs.Problem(rq["d"], rq["n"], rq["M"], 1.0, rq["alpha"], rq["kind"]).rhs()
+
+    def unknowns(rq):
+        return rq["n"] ** rq["d"] * rq["M"]
+
+    def run(arrivals):
+        lat, results = [None] * len(reqs), [None] * len(reqs)
+        with mgwr.Server(hbm_budget=budget, slots=args.slots) as srv:
+            tickets = [None] * len(reqs)
+            t0 = time.perf_counter()
+
+            def submitter():
+                for i, rq in enumerate(reqs):
+                    wait = t0 + arrivals[i] - time.perf_counter()
+                    if wait > 0:
+                        time.sleep(wait)
+                    tickets[i] = srv.submit(rq["d"], rq["n"], rq["M"], 1.0, rq["alpha"], rhs(rq),
+                                            precision=mgwr.MGWR_MIXED_DD, tol=tol)
+
+            th = threading.Thread(target=submitter)
+            th.start()
+            done = 0
+            while done < len(reqs):
+                for i in range(len(reqs)):
+                    if results[i] is None and tickets[i] is not None:
+                        r = srv.poll(tickets[i], timeout_us=0)
+                        if r is not None:
+                            results[i] = r
+                            lat[i] = r.latency_s
+                            done += 1
+                time.sleep(0.002)
+            th.join()
+            makespan = time.perf_counter() - t0
+            info = srv.info()
+        return makespan, lat, results, info
+
+    total = sum(unknowns(r) for r in reqs)
+    span1, _, res1, _ = run([0.0] * len(reqs))
+    rate = len(reqs) / span1
+    rng = np.random.default_rng(1608)
+    arr = np.cumsum(rng.exponential(1.0 / (0.7 * rate), size=len(reqs)))
+    span2, lat, res2, info = run(list(arr))
+    ok = sum(1 for r in res2 if r.status == mgwr.MGWR_OK)
+    lat_ms = np.array(lat) * 1e3
+    out = {
+        "metric": "served p50/p99 latency and space-time unknowns/s (mixed, rel-res 1e-8)",
+        "value": total / span2, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 0,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 cycles + f32x2 (double-float) defect/update", "data": "synthetic",
+        "config": {"workload": f"served stream: first {len(reqs)} of 2000 requests (seed 1608), "
+                               "1-D n=2^k-1 k~U{5..12} or 2-D k~U{5..9}, M=2^j j~U{7..12}, "
+                               "alpha~U[0.1,0.9], u=t^2 or t^alpha sin, Poisson arrivals at 0.7x "
+                               "the sustained rate", "name": "c4", "slots": args.slots,
+                   "hbm_budget_bytes": budget},
+        "served": {"p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+                   "sustained_requests_per_s": rate, "offered_requests_per_s": 0.7 * rate,
+                   "back_to_back_unknowns_per_s": total / span1, "completed_ok": ok,
+                   "requests": len(reqs), "total_unknowns": total, "peak_bytes": info["peak_bytes"]},
+    }
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "c4":
+        return run_served(args)
     import torch
 
     rank, world, local = dist_env()
@@ -274,8 +361,9 @@ def main():
         unknowns = batch * n ** d * Mw
     stream = torch.cuda.Stream()
     s.set_stream(stream.cuda_stream)
-    if precision == "mixed":
-        s.set_precision(mgwr.MGWR_MIXED)
+    prec_code = {"fp64": mgwr.MGWR_FP64, "mixed": mgwr.MGWR_MIXED, "mixed_dd": mgwr.MGWR_MIXED_DD}
+    if precision != "fp64":
+        s.set_precision(prec_code[precision])
 
     def step():
         s.set_rhs_dev(f_dev.data_ptr())
@@ -348,7 +436,8 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if precision == "fp64" else "f32 cycles + f64 defect/update",
+        "dtype": {"fp64": "f64", "mixed": "f32 cycles + f64 defect/update",
+                  "mixed_dd": "f32 cycles + f32x2 (double-float) defect/update"}[precision],
         "data": "synthetic",
         "config": {"workload": f"{desc}, " + (f"alpha={alpha}, " if batch == 1 else "")
                                + f"V({NU1},{NU2}) red-black, rel-res {tol}",

@@ -61,6 +61,12 @@ extern "C" {
 /* arithmetic of a solve (mgwr_set_precision) */
 #define MGWR_FP64 0  /* every kernel in IEEE double                          */
 #define MGWR_MIXED 1 /* FP32 V-cycles on the defect, FP64 defect + update     */
+#define MGWR_MIXED_DD 2 /* FP32 V-cycles; defect + update in double-float    */
+/* MGWR_MIXED_DD keeps the finest iterate and right-hand side as double-float
+ * pairs (hi + lo of two floats, about 48 significant bits) and computes the
+ * outer defect and the update with FP32 instructions only (GB300 runs FP32 64x
+ * faster than FP64).  Its stopping test uses that defect; mgwr_residual gives
+ * the IEEE-double defect of the result. */
 
 /* which hierarchy a component call addresses */
 #define MGWR_H64 64  /* the double-precision hierarchy                         */
@@ -116,14 +122,21 @@ int mgwr_destroy(mgwr_t h);
 const char* mgwr_last_error(mgwr_t h);
 const char* mgwr_status_string(int status);
 
-/* MGWR_FP64 (default) or MGWR_MIXED (allocates the FP32 hierarchy). */
+/* MGWR_FP64 (default), MGWR_MIXED or MGWR_MIXED_DD (both allocate the FP32
+ * hierarchy). */
 int mgwr_set_precision(mgwr_t h, int precision);
 /* MGWR_ORDER_TEXT (default) or MGWR_ORDER_TABLE. */
 int mgwr_set_order(mgwr_t h, int order);
 /* cudaStream_t to run on (NULL: the handle's own stream). */
 int mgwr_set_stream(mgwr_t h, void* stream);
-/* Inner FP32 cycles per FP64 defect in MGWR_MIXED (1..16, default 2). */
+/* Inner FP32 cycles per outer defect in the mixed modes (1..16, default 2). */
 int mgwr_set_inner_cycles(mgwr_t h, int cycles);
+/* enable != 0 (default): mgwr_solve captures one iteration of its loop (the
+ * cycle's launches, the defect norms and their copy to the host) as a CUDA
+ * graph on first use and replays it, one graph launch per iteration; 0:
+ * launches are issued one by one.  Results are identical either way.  The
+ * capture uses thread-local capture mode on the handle's stream. */
+int mgwr_set_graphs(mgwr_t h, int enable);
 
 /* ---- problem data -------------------------------------------------------- */
 
@@ -210,6 +223,55 @@ int mgwr_inverse_column(mgwr_t h, int level, double* k_host);  /* batch x (k_1..
 int mgwr_inverse_column_noalloc(const double* r_dev, int M, double sigma, double* k_dev,
                                 void* stream);
 
+/* Device bytes a handle of this shape needs at its peak (setup included), for
+ * admission control; host-only arithmetic, no CUDA call. */
+int mgwr_footprint(int d, int n, int M, int batch, int precision, size_t* bytes);
+
+/* ---- serving: submit / poll ----------------------------------------------- */
+/* A server owns `max_slots` worker threads, each running one request at a
+ * time on its own CUDA stream, and admits queued requests while the sum of
+ * their footprints (mgwr_footprint) stays within `hbm_budget` bytes.  Requests
+ * of any shape may be in flight together; their kernels overlap on the device.
+ * The oldest request that fits runs first; one passed over 64 times blocks
+ * younger ones until it fits.  Thread-safe: submit and poll from any thread. */
+typedef struct mgwr_server* mgwr_server_t;
+typedef struct {
+  int d, n, M;            /* shape, as for mgwr_create                         */
+  double T, alpha;
+  const double* f;        /* N*M right-hand side, host; copied by mgwr_submit  */
+  const double* g;        /* N initial values or NULL; copied                 */
+  int precision;          /* MGWR_FP64 or MGWR_MIXED                          */
+  int order;              /* MGWR_ORDER_TEXT or MGWR_ORDER_TABLE              */
+  int cycle, nu1, nu2;    /* as for mgwr_solve                                */
+  double tol;
+  int max_cycles;
+} mgwr_request;
+typedef struct {
+  int status;             /* mgwr_solve's status (or the failing call's)       */
+  mgwr_stats stats;
+  double queue_s;         /* submit -> admission, seconds                      */
+  double latency_s;       /* submit -> result ready, seconds                   */
+} mgwr_result;
+typedef struct {
+  long long queued, admitted, completed;
+  size_t in_use_bytes, peak_bytes, budget_bytes;
+  int slots;
+} mgwr_server_info;
+/* MGWR_E_INVAL (bad arguments), MGWR_E_CUDA (no device). */
+int mgwr_server_create(size_t hbm_budget, int max_slots, mgwr_server_t* out);
+/* Stops the workers after their current requests; queued requests are dropped. */
+int mgwr_server_destroy(mgwr_server_t s);
+/* Copies the request's data and queues it: MGWR_OK with *ticket set,
+ * MGWR_E_INVAL (bad request), MGWR_E_TOOBIG (footprint above the budget),
+ * MGWR_E_AGAIN (queue full). */
+int mgwr_submit(mgwr_server_t s, const mgwr_request* rq, uint64_t* ticket);
+/* Waits up to timeout_us (0: no wait) for the ticket.  MGWR_E_AGAIN (not
+ * ready, timeout 0) or MGWR_E_TIMEOUT (not ready after the wait); MGWR_OK:
+ * u_out (N*M doubles, may be NULL) and *res filled and the ticket released;
+ * MGWR_E_INVAL for an unknown ticket. */
+int mgwr_poll(mgwr_server_t s, uint64_t ticket, int timeout_us, double* u_out, mgwr_result* res);
+int mgwr_server_stats(mgwr_server_t s, mgwr_server_info* info);
+
 /* Number of CUDA kernel launches issued through the library so far
  * (process-wide; h may be NULL). */
 int mgwr_launch_count(mgwr_t h, long long* count);
@@ -225,7 +287,8 @@ int mgwr_launch_count(mgwr_t h, long long* count);
 #define MGWR_K_COARSEST 6   /* one-point solves                                 */
 #define MGWR_K_REFINE 7     /* mixed-precision update u64 += e32                */
 #define MGWR_K_DEFECT_DELTA 8 /* defect after a smoothing step, no convolution  */
-#define MGWR_NUM_KERNEL_CLASSES 9
+#define MGWR_K_DEFECT_DD 9  /* double-float outer defects (MGWR_MIXED_DD)      */
+#define MGWR_NUM_KERNEL_CLASSES 10
 /* enable != 0: from now on every launch of the solver is bracketed by CUDA
  * events on the handle's stream (clears the totals).  Adds event records
  * between launches; meant for a measurement run, not for timed runs. */

@@ -57,6 +57,12 @@ struct mgwr_handle {
   double* c_dev = nullptr;      // batch
   Hier<double> h64;
   Hier<float> h32;
+  // double-float copies of the finest iterate / right-hand side and of the
+  // Toeplitz spectra, for the outer defect of MGWR_MIXED_DD
+  mgwr::dd* u_dd = nullptr;
+  mgwr::dd* f_dd = nullptr;
+  Cx<mgwr::dd>* tspec_dd = nullptr;
+  Cx<mgwr::dd>* tw_dd = nullptr;
   unsigned long long* norm_bits = nullptr;  // device, one per instance
   unsigned long long* norm_host = nullptr;  // pinned, one per instance
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -64,6 +70,11 @@ struct mgwr_handle {
   bool r0_valid = false;
   std::vector<void*> allocs;
   std::string err;
+  // one solve-loop iteration captured as a CUDA graph, replayed every iteration
+  bool use_graphs = true;
+  cudaGraphExec_t iter_exec = nullptr;
+  long long iter_key = -1;   // (precision, cycle, nu1, nu2, inner, order) it was captured for
+  bool iter_exact = true;    // its norms come from the full defect
   // per-kernel-class timing (mgwr_profile): event pairs around each launch
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -96,13 +107,16 @@ int fail(mgwr_t h, int code, const std::string& msg) {
     if (s_ != MGWR_OK) return s_; \
   } while (0)
 
+// Stream-ordered allocation on the handle's stream: creating or destroying a
+// handle does not synchronise the device, so handles on other streams (other
+// server slots) keep running.
 template <class P>
 int dev_alloc(mgwr_t h, P** p, size_t bytes) {
   void* q = nullptr;
-  cudaError_t e = cudaMalloc(&q, bytes < 16 ? 16 : bytes);
+  cudaError_t e = cudaMallocAsync(&q, bytes < 16 ? 16 : bytes, h->stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    return fail(h, MGWR_E_NOMEM, std::string("cudaMalloc(") + std::to_string(bytes) + "): " +
+    return fail(h, MGWR_E_NOMEM, std::string("cudaMallocAsync(") + std::to_string(bytes) + "): " +
                                      cudaGetErrorString(e));
   }
   h->allocs.push_back(q);
@@ -178,6 +192,18 @@ int ensure_h32(mgwr_t h) {
   MGWR_CK(h, mgwr::launch_round_cx(H.tw, h->h64.tw, (size_t)h->L, h->stream));
   MGWR_CK(h, cudaStreamSynchronize(h->stream));
   H.ready = true;
+  return MGWR_OK;
+}
+
+int ensure_dd(mgwr_t h) {
+  if (h->u_dd != nullptr) return MGWR_OK;
+  const size_t cnt = level_count(h, h->nlev - 1);
+  MGWR_TRY(dev_alloc(h, &h->u_dd, cnt * sizeof(mgwr::dd)));
+  MGWR_TRY(dev_alloc(h, &h->f_dd, cnt * sizeof(mgwr::dd)));
+  MGWR_TRY(dev_alloc(h, &h->tspec_dd, sizeof(Cx<mgwr::dd>) * (size_t)h->B * h->L));
+  MGWR_TRY(dev_alloc(h, &h->tw_dd, sizeof(Cx<mgwr::dd>) * (size_t)h->L));
+  MGWR_CK(h, mgwr::launch_split_cx(h->tspec_dd, h->h64.tspec, (size_t)h->B * h->L, h->stream));
+  MGWR_CK(h, mgwr::launch_split_cx(h->tw_dd, h->h64.tw, (size_t)h->L, h->stream));
   return MGWR_OK;
 }
 
@@ -380,18 +406,18 @@ int finest_defect_norms(mgwr_t h, std::vector<double>& norms, bool to_h32) {
   return read_norms(h, norms);
 }
 
-// Finest-level defect norms after an FP64 cycle: from the last smoothing
-// step's changes when the cycle ended with one (*exact = false), else the
-// full form.
-int finest_cycle_norms(mgwr_t h, std::vector<double>& norms, bool* exact) {
+// Double-float defect of the finest iterate, rounded into the FP32 right-hand
+// side, with per-instance norms (MGWR_MIXED_DD).
+int finest_defect_norms_dd(mgwr_t h, std::vector<double>& norms) {
   const int L = h->nlev - 1;
-  if (h->h64.rs[L] != R_DELTA) {
-    *exact = true;
-    return finest_defect_norms(h, norms, false);
-  }
-  *exact = false;
   MGWR_TRY(clear_norms(h));
-  MGWR_TRY(defect_from_delta(h, h->h64, L, h->norm_bits));
+  const int pm = prof_begin(h, MGWR_K_DEFECT_DD, (double)(points(h, L) * h->B));
+  MGWR_CK(h, (mgwr::launch_defect<mgwr::dd, float>(h->u_dd, h->f_dd, h->h32.f[L], h->tspec_dd,
+                                                    (size_t)h->L, h->tw_dd, shape(h, L),
+                                                    mgwr::dd(h->hinv2[L]), h->norm_bits,
+                                                    h->stream)));
+  prof_end(h, pm);
+  h->h32.rs[L] = R_STALE;
   return read_norms(h, norms);
 }
 
@@ -405,6 +431,94 @@ double relative(mgwr_t h, const std::vector<double>& norms, std::vector<double>&
     if (worst == worst) worst = std::max(worst, rel[b]);
   }
   return worst;
+}
+
+// Enqueues one iteration of the solve loop and the copy of its per-instance
+// norms to pinned host memory, with no host synchronisation (so that it can be
+// captured into a graph).  FP64: one cycle, then the finest defect norms (from
+// the smoothing changes when the cycle ended with a smoothing step, *exact =
+// false).  Mixed: `inner` FP32 cycles on the defect equation from e = 0, the
+// update, and the outer defect (double or double-float) with its norms.
+int enqueue_iteration(mgwr_t h, int cyc, int nu1, int nu2, bool* exact) {
+  const int L = h->nlev - 1;
+  const size_t cnt = level_count(h, L);
+  if (h->precision == MGWR_FP64) {
+    MGWR_TRY(cycle(h, h->h64, L, cyc, nu1, nu2));
+    MGWR_TRY(clear_norms(h));
+    if (h->h64.rs[L] == R_DELTA) {
+      MGWR_TRY(defect_from_delta(h, h->h64, L, h->norm_bits));
+      *exact = false;
+    } else {
+      MGWR_TRY(defect(h, h->h64, L, h->norm_bits));
+      *exact = true;
+    }
+  } else {
+    const bool ddef = h->precision == MGWR_MIXED_DD;
+    MGWR_CK(h, cudaMemsetAsync(h->h32.u[L], 0, cnt * sizeof(float), h->stream));
+    h->h32.rs[L] = R_ZERO_U;  // f32 holds the outer defect, e32 = 0
+    for (int k = 0; k < h->inner; ++k) MGWR_TRY(cycle(h, h->h32, L, cyc, nu1, nu2));
+    const int pm = prof_begin(h, MGWR_K_REFINE, (double)(points(h, L) * h->B));
+    if (ddef)
+      MGWR_CK(h, mgwr::launch_refine_dd(h->u_dd, h->h32.u[L], cnt, h->stream));
+    else
+      MGWR_CK(h, mgwr::launch_refine(h->h64.u[L], h->h32.u[L], cnt, h->stream));
+    prof_end(h, pm);
+    MGWR_TRY(clear_norms(h));
+    const int pd = prof_begin(h, ddef ? MGWR_K_DEFECT_DD : MGWR_K_DEFECT64, (double)(points(h, L) * h->B));
+    if (ddef)
+      MGWR_CK(h, (mgwr::launch_defect<mgwr::dd, float>(h->u_dd, h->f_dd, h->h32.f[L], h->tspec_dd,
+                                                        (size_t)h->L, h->tw_dd, shape(h, L),
+                                                        mgwr::dd(h->hinv2[L]), h->norm_bits,
+                                                        h->stream)));
+    else
+      MGWR_CK(h, (mgwr::launch_defect<double, float>(h->h64.u[L], h->h64.f[L], h->h32.f[L],
+                                                      h->h64.tspec, (size_t)h->L, h->h64.tw,
+                                                      shape(h, L), h->hinv2[L], h->norm_bits,
+                                                      h->stream)));
+    prof_end(h, pd);
+    h->h32.rs[L] = R_STALE;
+    *exact = true;
+  }
+  MGWR_CK(h, cudaMemcpyAsync(h->norm_host, h->norm_bits, sizeof(unsigned long long) * h->B,
+                             cudaMemcpyDeviceToHost, h->stream));
+  return MGWR_OK;
+}
+
+// Runs one iteration: replays the captured graph when it matches the current
+// settings (capturing it first if needed), else enqueues the launches
+// directly; then waits and decodes the norms.
+int run_iteration(mgwr_t h, int cyc, int nu1, int nu2, std::vector<double>& norms, bool* exact) {
+  const long long key = ((((long long)h->precision * 4 + cyc) * 32 + nu1) * 32 + nu2) * 32 * 4 +
+                        (long long)h->inner * 4 + h->order;
+  if (h->use_graphs && !h->profiling) {
+    if (h->iter_exec == nullptr || h->iter_key != key) {
+      if (h->iter_exec) cudaGraphExecDestroy(h->iter_exec);
+      h->iter_exec = nullptr;
+      cudaGraph_t g = nullptr;
+      MGWR_CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+      bool ex = true;
+      const int st = enqueue_iteration(h, cyc, nu1, nu2, &ex);
+      const cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+      if (st != MGWR_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+      }
+      MGWR_CK(h, e);
+      const cudaError_t ei = cudaGraphInstantiate(&h->iter_exec, g, 0);
+      cudaGraphDestroy(g);
+      MGWR_CK(h, ei);
+      h->iter_key = key;
+      h->iter_exact = ex;
+    }
+    MGWR_CK(h, cudaGraphLaunch(h->iter_exec, h->stream));
+    *exact = h->iter_exact;
+  } else {
+    MGWR_TRY(enqueue_iteration(h, cyc, nu1, nu2, exact));
+  }
+  MGWR_CK(h, cudaStreamSynchronize(h->stream));
+  norms.resize(h->B);
+  for (int b = 0; b < h->B; ++b) std::memcpy(&norms[b], &h->norm_host[b], sizeof(double));
+  return MGWR_OK;
 }
 
 int check_level(mgwr_t h, int hierarchy, int level) {
@@ -518,7 +632,7 @@ int create_impl(int d, int n, int M, const double* T, const double* alpha, int b
     return bail(MGWR_E_CUDA);
   }
   // the divide-and-conquer work area is no longer needed
-  cudaFree(work);
+  cudaFreeAsync(work, h->stream);
   h->allocs.erase(std::find(h->allocs.begin(), h->allocs.end(), (void*)work));
   h->h64.ready = true;
   // the finest iterate and right-hand side always exist; the rest on demand
@@ -562,11 +676,13 @@ const char* mgwr_last_error(mgwr_t h) { return h == nullptr ? kNullHandleMsg : h
 int mgwr_destroy(mgwr_t h) {
   if (h == nullptr) return MGWR_OK;
   if (h->stream) cudaStreamSynchronize(h->stream);
-  for (void* p : h->allocs) cudaFree(p);
+  for (void* p : h->allocs) cudaFreeAsync(p, h->stream);
+  if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->norm_host) cudaFreeHost(h->norm_host);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  if (h->iter_exec) cudaGraphExecDestroy(h->iter_exec);
   if (h->own_stream) cudaStreamDestroy(h->own_stream);
   delete h;
   return MGWR_OK;
@@ -595,9 +711,13 @@ int mgwr_instance_relres(mgwr_t h, double* relres) {
 
 int mgwr_set_precision(mgwr_t h, int precision) {
   if (h == nullptr) return MGWR_E_INVAL;
-  if (precision != MGWR_FP64 && precision != MGWR_MIXED)
-    return fail(h, MGWR_E_INVAL, "precision must be MGWR_FP64 or MGWR_MIXED");
-  if (precision == MGWR_MIXED) MGWR_TRY(ensure_h32(h));
+  if (precision != MGWR_FP64 && precision != MGWR_MIXED && precision != MGWR_MIXED_DD)
+    return fail(h, MGWR_E_INVAL, "precision must be MGWR_FP64, MGWR_MIXED or MGWR_MIXED_DD");
+  if (precision != MGWR_FP64) MGWR_TRY(ensure_h32(h));
+  if (precision == MGWR_MIXED_DD) {
+    MGWR_TRY(ensure_dd(h));
+    MGWR_CK(h, cudaStreamSynchronize(h->stream));
+  }
   h->precision = precision;
   return MGWR_OK;
 }
@@ -614,6 +734,12 @@ int mgwr_set_stream(mgwr_t h, void* stream) {
   if (h == nullptr) return MGWR_E_INVAL;
   MGWR_CK(h, cudaStreamSynchronize(h->stream));
   h->stream = stream != nullptr ? static_cast<cudaStream_t>(stream) : h->own_stream;
+  return MGWR_OK;
+}
+
+int mgwr_set_graphs(mgwr_t h, int enable) {
+  if (h == nullptr) return MGWR_E_INVAL;
+  h->use_graphs = enable != 0;
   return MGWR_OK;
 }
 
@@ -637,8 +763,8 @@ static int set_rhs_impl(mgwr_t h, const double* f, const double* g, cudaMemcpyKi
     MGWR_CK(h, cudaMemcpyAsync(g_dev, g, N * h->B * sizeof(double), kind, h->stream));
     MGWR_CK(h, mgwr::launch_initial(h->h64.u[L], h->h64.f[L], g_dev, h->dk, h->c_dev, (int)N, h->M,
                                      h->B, h->stream));
+    MGWR_CK(h, cudaFreeAsync(g_dev, h->stream));
     MGWR_CK(h, cudaStreamSynchronize(h->stream));
-    cudaFree(g_dev);
     h->allocs.pop_back();
   } else {
     MGWR_CK(h, cudaMemsetAsync(h->h64.u[L], 0, bytes, h->stream));
@@ -673,13 +799,21 @@ int mgwr_solve(mgwr_t h, int cyc, int nu1, int nu2, double tol, int max_cycles, 
   if (h == nullptr) return MGWR_E_INVAL;
   MGWR_TRY(check_cycle_args(h, cyc, nu1, nu2));
   if (!(tol >= 0.0) || max_cycles < 1) return fail(h, MGWR_E_INVAL, "need tol >= 0, max_cycles >= 1");
-  const bool mixed = h->precision == MGWR_MIXED;
+  const bool mixed = h->precision != MGWR_FP64;
+  const bool ddef = h->precision == MGWR_MIXED_DD;
   if (!mixed) MGWR_TRY(ensure_full(h, h->h64));
   const int L = h->nlev - 1;
+  const size_t cntL = level_count(h, L);
   mgwr_stats local{};
   MGWR_CK(h, cudaEventRecord(h->ev0, h->stream));
   std::vector<double> norms;
-  MGWR_TRY(finest_defect_norms(h, norms, mixed));
+  if (ddef) {
+    MGWR_CK(h, mgwr::launch_split(h->u_dd, h->h64.u[L], cntL, h->stream));
+    MGWR_CK(h, mgwr::launch_split(h->f_dd, h->h64.f[L], cntL, h->stream));
+    MGWR_TRY(finest_defect_norms_dd(h, norms));
+  } else {
+    MGWR_TRY(finest_defect_norms(h, norms, mixed));
+  }
   if (!h->r0_valid) {
     h->r0 = norms;
     h->r0_valid = true;
@@ -697,35 +831,20 @@ int mgwr_solve(mgwr_t h, int cyc, int nu1, int nu2, double tol, int max_cycles, 
       status = MGWR_E_NOCONV;
       break;
     }
-    if (!mixed) {
-      MGWR_TRY(cycle(h, h->h64, L, cyc, nu1, nu2));
-      ++cycles;
-      bool exact = false;
-      MGWR_TRY(finest_cycle_norms(h, norms, &exact));
+    bool exact = true;
+    MGWR_TRY(run_iteration(h, cyc, nu1, nu2, norms, &exact));
+    cycles += mixed ? h->inner : 1;
+    rel = relative(h, norms, h->relres);
+    // the stopping decision is always taken on the full defect
+    if (!exact && rel <= tol) {
+      MGWR_TRY(finest_defect_norms(h, norms, false));
       rel = relative(h, norms, h->relres);
-      // the stopping decision is always taken on the full defect
-      if (!exact && rel <= tol) {
-        MGWR_TRY(finest_defect_norms(h, norms, false));
-        rel = relative(h, norms, h->relres);
-        exact = true;
-      }
-      rel_exact = exact;
-    } else {
-      const size_t cnt = level_count(h, L);
-      MGWR_CK(h, cudaMemsetAsync(h->h32.u[L], 0, cnt * sizeof(float), h->stream));
-      h->h32.rs[L] = R_ZERO_U;  // f32 holds the FP64 defect, e32 = 0
-      for (int k = 0; k < h->inner; ++k) {
-        MGWR_TRY(cycle(h, h->h32, L, cyc, nu1, nu2));
-        ++cycles;
-      }
-      const int pm = prof_begin(h, MGWR_K_REFINE, (double)(points(h, L) * h->B));
-      MGWR_CK(h, mgwr::launch_refine(h->h64.u[L], h->h32.u[L], cnt, h->stream));
-      prof_end(h, pm);
-      MGWR_TRY(finest_defect_norms(h, norms, true));
-      rel = relative(h, norms, h->relres);
+      exact = true;
     }
+    rel_exact = exact;
     ++outer;
   }
+  if (ddef) MGWR_CK(h, mgwr::launch_join(h->h64.u[L], h->u_dd, cntL, h->stream));
   if (!rel_exact) {  // report the full defect also when stopping on max_cycles
     MGWR_TRY(finest_defect_norms(h, norms, false));
     rel = relative(h, norms, h->relres);
@@ -988,6 +1107,40 @@ int mgwr_profile_read(mgwr_t h, int kernel_class, long long* launches, double* m
   if (launches) *launches = h->prof_launches[kernel_class];
   if (ms) *ms = h->prof_ms[kernel_class];
   if (lines) *lines = h->prof_lines[kernel_class];
+  return MGWR_OK;
+}
+
+int mgwr_footprint(int d, int n, int M, int batch, int precision, size_t* bytes) {
+  if (bytes == nullptr) return MGWR_E_INVAL;
+  if ((d != 1 && d != 2) || n < 1 || !is_pow2((long long)n + 1) || !is_pow2(M) || M < 4 ||
+      M > 4096 || batch < 1 ||
+      (precision != MGWR_FP64 && precision != MGWR_MIXED && precision != MGWR_MIXED_DD))
+    return MGWR_E_INVAL;
+  // mirrors the allocations of create_impl, ensure_full and ensure_h32, each
+  // rounded up to 512 bytes, plus 2 MiB of allocator slack per handle
+  auto r512 = [](size_t b) { return (b + 511) / 512 * 512; };
+  const size_t B = batch, L = 2 * (size_t)M;
+  std::vector<size_t> pts;
+  for (int m = n;; m = (m - 1) / 2) {
+    pts.push_back(d == 1 ? (size_t)m : (size_t)m * m);
+    if (m == 1) break;
+  }
+  const size_t nlev = pts.size();
+  size_t total = 2u << 20;
+  total += r512(8 * B) + r512(8 * B * M) + r512(8 * B * (M + 1)) + r512(8 * B * nlev * M);
+  total += 2 * r512(8 * B) + r512(8 * nlev);
+  total += r512(16 * B * nlev * 3 * M);  // divide-and-conquer work (freed after setup)
+  total += r512(16 * B * nlev * L) + r512(16 * B * L) + r512(16 * L);
+  if (precision == MGWR_FP64) {
+    for (size_t l = 0; l < nlev; ++l) total += (l + 1 < nlev ? 4 : 3) * r512(8 * B * pts[l] * M);
+  } else {
+    total += 2 * r512(8 * B * pts[0] * M);  // FP64 finest iterate and right-hand side
+    for (size_t l = 0; l < nlev; ++l) total += (l + 1 < nlev ? 4 : 3) * r512(4 * B * pts[l] * M);
+    total += r512(8 * B * nlev * L) + r512(8 * B * L) + r512(8 * L);
+    if (precision == MGWR_MIXED_DD)
+      total += 2 * r512(8 * B * pts[0] * M) + r512(16 * B * L) + r512(16 * L);
+  }
+  *bytes = total;
   return MGWR_OK;
 }
 

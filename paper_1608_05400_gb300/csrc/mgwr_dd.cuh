@@ -1,0 +1,85 @@
+// Double-float arithmetic: a value is the unevaluated sum hi + lo of two FP32
+// numbers (|lo| <= ulp(hi)/2), about 48 significant bits, computed with FP32
+// instructions only.  GB300 issues FP32 64 times faster than FP64, so the
+// defect of the mixed-precision refinement runs in this type.
+//
+// The error-free transformations are Knuth's TwoSum and Dekker's
+// Fast2Sum / FMA-based TwoProduct (Dekker 1971; Knuth, TAOCP vol. 2;
+// Hida, Li & Bailey 2001).  The rounded primitives __fadd_rn / __fsub_rn /
+// __fmul_rn are used wherever a compiler contraction into an FMA would break
+// an exact error term.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace mgwr {
+
+struct dd {
+  float hi, lo;
+  dd() = default;
+  __host__ __device__ constexpr dd(float h, float l) : hi(h), lo(l) {}
+  // exact for constants; at run time only used on the host or in setup
+  __host__ __device__ constexpr dd(double x) : hi((float)x), lo((float)(x - (double)(float)x)) {}
+  __host__ __device__ constexpr dd(int x) : dd((double)x) {}
+  __device__ __forceinline__ explicit operator float() const { return __fadd_rn(hi, lo); }
+};
+
+// s + e = a + b exactly (TwoSum, any a, b)
+__device__ __forceinline__ dd dd_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return dd(s, e);
+}
+
+// s + e = a + b exactly when |a| >= |b| (Fast2Sum)
+__device__ __forceinline__ dd dd_fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return dd(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+
+// Sum with one renormalisation: error below about 2^-44 (|a| + |b|); the
+// form used inside FFT butterflies, whose error is bounded in norm anyway.
+__device__ __forceinline__ dd operator+(dd a, dd b) {
+  dd s = dd_two_sum(a.hi, b.hi);
+  s.lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+  return dd_fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ dd operator-(dd a) { return dd(-a.hi, -a.lo); }
+__device__ __forceinline__ dd operator-(dd a, dd b) { return a + (-b); }
+__device__ __forceinline__ dd& operator+=(dd& a, dd b) {
+  a = a + b;
+  return a;
+}
+
+// Sum accurate also under cancellation: error below about 2^-47 |a + b|
+// (both pairs summed exactly, two renormalisations).  Used for the stencil
+// differences of the defect.
+__device__ __forceinline__ dd dd_add_accurate(dd a, dd b) {
+  dd s = dd_two_sum(a.hi, b.hi);
+  const dd t = dd_two_sum(a.lo, b.lo);
+  s.lo = __fadd_rn(s.lo, t.hi);
+  s = dd_fast_two_sum(s.hi, s.lo);
+  s.lo = __fadd_rn(s.lo, t.lo);
+  return dd_fast_two_sum(s.hi, s.lo);
+}
+
+// Product: hi*hi split exactly by an FMA, cross terms added once.
+__device__ __forceinline__ dd operator*(dd a, dd b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return dd_fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ dd dd_add_float(dd a, float b) {
+  dd s = dd_two_sum(a.hi, b);
+  s.lo = __fadd_rn(s.lo, a.lo);
+  return dd_fast_two_sum(s.hi, s.lo);
+}
+
+// magnitude used for norms: |hi| (relative error below 2^-23)
+__device__ __forceinline__ float dd_abs_hi(dd a) { return fabsf(a.hi); }
+
+}  // namespace mgwr

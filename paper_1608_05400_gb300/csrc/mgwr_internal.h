@@ -7,6 +7,8 @@
 #include <cstddef>
 #include <cstdint>
 
+#include "mgwr_dd.cuh"
+
 namespace mgwr {
 
 template <class R>
@@ -65,6 +67,11 @@ cudaError_t launch_prolong(R* u, const R* uc, const LevelShape& fine, cudaStream
 
 // u += (double) e, elementwise.
 cudaError_t launch_refine(double* u, const float* e, size_t count, cudaStream_t s);
+// double-float: dst = split(src); dst = hi + lo; u += e; complex split.
+cudaError_t launch_split(dd* dst, const double* src, size_t count, cudaStream_t s);
+cudaError_t launch_join(double* dst, const dd* src, size_t count, cudaStream_t s);
+cudaError_t launch_refine_dd(dd* u, const float* e, size_t count, cudaStream_t s);
+cudaError_t launch_split_cx(Cx<dd>* dst, const Cx<double>* src, size_t count, cudaStream_t s);
 // dst = (float) src.
 cudaError_t launch_round(float* dst, const double* src, size_t count, cudaStream_t s);
 // Per instance b: u = broadcast of g_b along time (initial iterate u^0(t) = g);

@@ -5,6 +5,7 @@
 #include <atomic>
 #include <cmath>
 
+#include "mgwr_dd.cuh"
 #include "mgwr_fft.cuh"
 #include "mgwr_internal.h"
 
@@ -86,6 +87,50 @@ template <class R>
 __device__ __forceinline__ R absmax_nan(R a, R b) {
   // max that lets NaN win
   return (a != a || a > b) ? a : b;
+}
+
+// Per arithmetic type: the magnitude type of norms, |x|, and the difference
+// and sum used by the defect's stencil and final subtraction (exact
+// renormalisation for double-float, where these operands nearly cancel).
+template <class R>
+struct Arith;
+template <>
+struct Arith<double> {
+  using Mag = double;
+  static __device__ __forceinline__ double mag(double x) { return fabs(x); }
+  static __device__ __forceinline__ double sub(double a, double b) { return a - b; }
+  static __device__ __forceinline__ double add(double a, double b) { return a + b; }
+};
+template <>
+struct Arith<float> {
+  using Mag = float;
+  static __device__ __forceinline__ float mag(float x) { return fabsf(x); }
+  static __device__ __forceinline__ float sub(float a, float b) { return a - b; }
+  static __device__ __forceinline__ float add(float a, float b) { return a + b; }
+};
+template <>
+struct Arith<dd> {
+  using Mag = float;
+  static __device__ __forceinline__ float mag(dd x) { return dd_abs_hi(x); }
+  static __device__ __forceinline__ dd sub(dd a, dd b) { return dd_add_accurate(a, -b); }
+  static __device__ __forceinline__ dd add(dd a, dd b) { return dd_add_accurate(a, b); }
+};
+
+// sum over the 2d neighbour directions of (u_p - u_q), u_q = 0 outside the grid:
+// equals (2d u_p - sum_q u_q), the 5-point (3-point) stencil times h^2, with
+// every difference formed before the sum so that smooth u loses no digits.
+template <class R>
+__device__ __forceinline__ R stencil_differences(const R* __restrict__ u, R up, int d, int n, int i,
+                                                 int j, size_t pM, int M, int m) {
+  using A = Arith<R>;
+  R s = i > 0 ? A::sub(up, u[pM - M + m]) : up;
+  s = A::add(s, i < n - 1 ? A::sub(up, u[pM + M + m]) : up);
+  if (d == 2) {
+    const size_t nM = (size_t)n * M;
+    s = A::add(s, j > 0 ? A::sub(up, u[pM - nM + m]) : up);
+    s = A::add(s, j < n - 1 ? A::sub(up, u[pM + nM + m]) : up);
+  }
+  return s;
 }
 
 // ---------------------------------------------------------------------------------
@@ -262,8 +307,6 @@ __global__ void __launch_bounds__(BLOCK)
   const size_t pAM = (size_t)pA * M, pBM = (size_t)pB * M;
   const int iA = d == 1 ? pA : pA % n, jA = d == 1 ? 0 : pA / n;
   const int iB = d == 1 ? pB : pB % n, jB = d == 1 ? 0 : pB / n;
-  const R diag = R(2 * d) * hinv2;
-
   auto load = [&](int m) -> Cx<R> {
     Cx<R> x{R(0), R(0)};
     if (valid) {
@@ -276,16 +319,22 @@ __global__ void __launch_bounds__(BLOCK)
   fft_forward(buf, t, sh, tw, load, v);
 #pragma unroll
   for (int q = 0; q < 8; ++q) v[q] = cmul(v[q], tspec[8 * t + q]);
-  R amax = R(0);
+  using A = Arith<R>;
+  typename A::Mag amax = 0;
+  // r = f - (T_M u) - h^-2 sum_q (u_p - u_q)
   auto store = [&](int m, Cx<R> y) {
     if (valid) {
-      const R ra = f[pAM + m] - y.x - (diag * u[pAM + m] - hinv2 * neighbour_sum(u, d, n, iA, jA, pAM, M, m));
+      const R ua = u[pAM + m];
+      const R ra = A::sub(A::sub(f[pAM + m], y.x),
+                          hinv2 * stencil_differences(u, ua, d, n, iA, jA, pAM, M, m));
       r[pAM + m] = RO(ra);
-      amax = absmax_nan(fabs(ra), amax);
+      amax = absmax_nan(A::mag(ra), amax);
       if (hasB) {
-        const R rb = f[pBM + m] - y.y - (diag * u[pBM + m] - hinv2 * neighbour_sum(u, d, n, iB, jB, pBM, M, m));
+        const R ub = u[pBM + m];
+        const R rb = A::sub(A::sub(f[pBM + m], y.y),
+                            hinv2 * stencil_differences(u, ub, d, n, iB, jB, pBM, M, m));
         r[pBM + m] = RO(rb);
-        amax = absmax_nan(fabs(rb), amax);
+        amax = absmax_nan(A::mag(rb), amax);
       }
     }
   };
@@ -408,6 +457,38 @@ __global__ void __launch_bounds__(128)
         up[m + k] += wa * a[m + k] + wb * b[m + k] + wc * c[m + k] + we * e[m + k];
     }
   }
+}
+
+// double <-> double-float conversions and the double-float update
+__global__ void k_split(dd* __restrict__ dst, const double* __restrict__ src, size_t count) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const double x = src[i];
+    const float hi = (float)x;
+    dst[i] = dd(hi, (float)(x - (double)hi));
+  }
+}
+
+__global__ void k_join(double* __restrict__ dst, const dd* __restrict__ src, size_t count) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
+       i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = (double)src[i].hi + (double)src[i].lo;
+}
+
+__global__ void k_split_cx(Cx<dd>* __restrict__ dst, const Cx<double>* __restrict__ src,
+                           size_t count) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const double x = src[i].x, y = src[i].y;
+    const float xh = (float)x, yh = (float)y;
+    dst[i] = Cx<dd>{dd(xh, (float)(x - (double)xh)), dd(yh, (float)(y - (double)yh))};
+  }
+}
+
+__global__ void k_refine_dd(dd* __restrict__ u, const float* __restrict__ e, size_t count) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
+       i += (size_t)gridDim.x * blockDim.x)
+    u[i] = dd_add_float(u[i], e[i]);
 }
 
 __global__ void k_refine(double* __restrict__ u, const float* __restrict__ e, size_t count) {
@@ -777,6 +858,26 @@ cudaError_t launch_refine(double* u, const float* e, size_t count, cudaStream_t 
   return counted(cudaGetLastError());
 }
 
+cudaError_t launch_split(dd* dst, const double* src, size_t count, cudaStream_t s) {
+  k_split<<<elementwise_grid(count), 256, 0, s>>>(dst, src, count);
+  return counted(cudaGetLastError());
+}
+
+cudaError_t launch_join(double* dst, const dd* src, size_t count, cudaStream_t s) {
+  k_join<<<elementwise_grid(count), 256, 0, s>>>(dst, src, count);
+  return counted(cudaGetLastError());
+}
+
+cudaError_t launch_split_cx(Cx<dd>* dst, const Cx<double>* src, size_t count, cudaStream_t s) {
+  k_split_cx<<<elementwise_grid(count), 256, 0, s>>>(dst, src, count);
+  return counted(cudaGetLastError());
+}
+
+cudaError_t launch_refine_dd(dd* u, const float* e, size_t count, cudaStream_t s) {
+  k_refine_dd<<<elementwise_grid(count), 256, 0, s>>>(u, e, count);
+  return counted(cudaGetLastError());
+}
+
 cudaError_t launch_round(float* dst, const double* src, size_t count, cudaStream_t s) {
   k_round<<<elementwise_grid(count), 256, 0, s>>>(dst, src, count);
   return counted(cudaGetLastError());
@@ -861,6 +962,9 @@ template cudaError_t launch_defect<double, float>(const double*, const double*, 
                                                   const Cx<double>*, size_t, const Cx<double>*,
                                                   const LevelShape&, double, unsigned long long*,
                                                   cudaStream_t);
+template cudaError_t launch_defect<dd, float>(const dd*, const dd*, float*, const Cx<dd>*, size_t,
+                                              const Cx<dd>*, const LevelShape&, dd,
+                                              unsigned long long*, cudaStream_t);
 template cudaError_t launch_defect<float, float>(const float*, const float*, float*,
                                                  const Cx<float>*, size_t, const Cx<float>*,
                                                  const LevelShape&, float, unsigned long long*,

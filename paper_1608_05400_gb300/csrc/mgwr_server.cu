@@ -1,0 +1,249 @@
+// Serving runtime: a request queue in front of the solver.  Requests of any
+// shape (d, n, M) and any (T, alpha, precision) are submitted from any host
+// thread, admitted while their device-memory footprint fits the budget and a
+// slot is free, and solved concurrently: every slot is a worker thread whose
+// handles run on their own CUDA stream, so the kernels of all admitted requests
+// overlap on the device.  A request that arrives while others run is admitted
+// as soon as memory and a slot are free (continuous batching at request
+// granularity); its result does not depend on what else runs (each solve is a
+// fixed sequence of kernels on its own data, and the only cross-block
+// reduction is an order-independent maximum).
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/mgwr.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Ticket {
+  uint64_t id = 0;
+  mgwr_request rq{};
+  std::vector<double> f, g, u;
+  size_t footprint = 0;
+  size_t N = 0;
+  int state = 0;  // 0 queued, 1 running, 2 done
+  int skipped = 0;
+  Clock::time_point t_submit, t_admit, t_done;
+  mgwr_result res{};
+};
+
+bool pow2(long long x) { return x > 0 && (x & (x - 1)) == 0; }
+
+}  // namespace
+
+struct mgwr_server {
+  size_t budget = 0, in_use = 0, peak = 0;
+  int slots = 1, max_queue = 1 << 20, device = 0;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Ticket*> queue;
+  std::unordered_map<uint64_t, std::unique_ptr<Ticket>> tickets;
+  std::vector<std::thread> workers;
+  bool stop = false;
+  uint64_t next_id = 1;
+  long long completed = 0, admitted = 0;
+};
+
+namespace {
+
+// Queue position that may start now: the oldest request that fits the free
+// memory.  A request that was passed over this many times blocks younger ones
+// until it fits (no starvation of large requests).
+constexpr int kMaxSkips = 64;
+
+Ticket* pick(mgwr_server* s) {
+  const size_t free_bytes = s->budget - s->in_use;
+  for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
+    Ticket* t = *it;
+    if (t->footprint <= free_bytes) {
+      for (auto jt = s->queue.begin(); jt != it; ++jt) (*jt)->skipped++;
+      s->queue.erase(it);
+      return t;
+    }
+    if (t->skipped >= kMaxSkips) return nullptr;
+  }
+  return nullptr;
+}
+
+int run_request(Ticket* t) {
+  const mgwr_request& q = t->rq;
+  mgwr_t h = nullptr;
+  int st = mgwr_create(q.d, q.n, q.M, q.T, q.alpha, &h);
+  if (st != MGWR_OK) return st;
+  if (q.precision != MGWR_FP64) st = mgwr_set_precision(h, q.precision);
+  if (st == MGWR_OK && q.order == MGWR_ORDER_TABLE) st = mgwr_set_order(h, q.order);
+  if (st == MGWR_OK) st = mgwr_set_rhs(h, t->f.data(), t->g.empty() ? nullptr : t->g.data());
+  mgwr_stats stats{};
+  if (st == MGWR_OK) {
+    st = mgwr_solve(h, q.cycle, q.nu1, q.nu2, q.tol, q.max_cycles, &stats);
+    t->res.stats = stats;
+    if (st == MGWR_OK || st == MGWR_E_NOCONV) {
+      t->u.resize(t->N * q.M);
+      const int st2 = mgwr_get_solution(h, t->u.data());
+      if (st2 != MGWR_OK) st = st2;
+    }
+  }
+  mgwr_destroy(h);
+  return st;
+}
+
+void worker(mgwr_server* s) {
+  cudaSetDevice(s->device);
+  for (;;) {
+    Ticket* t = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      s->cv_work.wait(lk, [&] { return s->stop || (t = pick(s)) != nullptr; });
+      if (t == nullptr) return;  // stopping
+      s->in_use += t->footprint;
+      if (s->in_use > s->peak) s->peak = s->in_use;
+      t->state = 1;
+      t->t_admit = Clock::now();
+      s->admitted++;
+    }
+    const int st = run_request(t);
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->in_use -= t->footprint;
+      t->t_done = Clock::now();
+      t->res.status = st;
+      t->res.queue_s = std::chrono::duration<double>(t->t_admit - t->t_submit).count();
+      t->res.latency_s = std::chrono::duration<double>(t->t_done - t->t_submit).count();
+      t->state = 2;
+      s->completed++;
+    }
+    s->cv_done.notify_all();
+    s->cv_work.notify_all();
+  }
+}
+
+int check_request(const mgwr_request* q) {
+  if (q == nullptr || q->f == nullptr) return MGWR_E_INVAL;
+  if (q->d != 1 && q->d != 2) return MGWR_E_INVAL;
+  if (q->n < 1 || !pow2((long long)q->n + 1)) return MGWR_E_INVAL;
+  if ((q->d == 1 && q->n > 32767) || (q->d == 2 && q->n > 4095)) return MGWR_E_INVAL;
+  if (!pow2(q->M) || q->M < 4 || q->M > 4096) return MGWR_E_INVAL;
+  if (!(q->T > 0.0) || !(q->alpha > 0.0) || !(q->alpha <= 1.0)) return MGWR_E_INVAL;
+  if (q->precision != MGWR_FP64 && q->precision != MGWR_MIXED && q->precision != MGWR_MIXED_DD)
+    return MGWR_E_INVAL;
+  if (q->cycle != 1 && q->cycle != 2) return MGWR_E_INVAL;
+  if (q->nu1 < 0 || q->nu2 < 0 || q->nu1 + q->nu2 == 0 || q->nu1 > 16 || q->nu2 > 16)
+    return MGWR_E_INVAL;
+  if (!(q->tol >= 0.0) || q->max_cycles < 1) return MGWR_E_INVAL;
+  return MGWR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mgwr_server_create(size_t hbm_budget, int max_slots, mgwr_server_t* out) {
+  if (out == nullptr) return MGWR_E_INVAL;
+  *out = nullptr;
+  if (hbm_budget == 0 || max_slots < 1 || max_slots > 64) return MGWR_E_INVAL;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || count < 1) {
+    cudaGetLastError();
+    return MGWR_E_CUDA;
+  }
+  mgwr_server_t s = new (std::nothrow) mgwr_server;
+  if (s == nullptr) return MGWR_E_NOMEM;
+  s->budget = hbm_budget;
+  s->slots = max_slots;
+  cudaGetDevice(&s->device);
+  for (int i = 0; i < max_slots; ++i) s->workers.emplace_back(worker, s);
+  *out = s;
+  return MGWR_OK;
+}
+
+int mgwr_server_destroy(mgwr_server_t s) {
+  if (s == nullptr) return MGWR_OK;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+    s->queue.clear();
+  }
+  s->cv_work.notify_all();
+  for (auto& w : s->workers) w.join();
+  delete s;
+  return MGWR_OK;
+}
+
+int mgwr_submit(mgwr_server_t s, const mgwr_request* rq, uint64_t* ticket) {
+  if (s == nullptr || ticket == nullptr) return MGWR_E_INVAL;
+  const int st = check_request(rq);
+  if (st != MGWR_OK) return st;
+  size_t fp = 0;
+  if (mgwr_footprint(rq->d, rq->n, rq->M, 1, rq->precision, &fp) != MGWR_OK) return MGWR_E_INVAL;
+  if (fp > s->budget) return MGWR_E_TOOBIG;
+  auto t = std::unique_ptr<Ticket>(new (std::nothrow) Ticket);
+  if (!t) return MGWR_E_NOMEM;
+  t->rq = *rq;
+  t->N = rq->d == 1 ? (size_t)rq->n : (size_t)rq->n * rq->n;
+  try {
+    t->f.assign(rq->f, rq->f + t->N * rq->M);
+    if (rq->g != nullptr) t->g.assign(rq->g, rq->g + t->N);
+  } catch (const std::bad_alloc&) {
+    return MGWR_E_NOMEM;
+  }
+  t->rq.f = nullptr;
+  t->rq.g = nullptr;
+  t->footprint = fp;
+  t->t_submit = Clock::now();
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->stop) return MGWR_E_STATE;
+    if ((int)s->queue.size() >= s->max_queue) return MGWR_E_AGAIN;
+    t->id = s->next_id++;
+    *ticket = t->id;
+    s->queue.push_back(t.get());
+    s->tickets.emplace(t->id, std::move(t));
+  }
+  s->cv_work.notify_one();
+  return MGWR_OK;
+}
+
+int mgwr_poll(mgwr_server_t s, uint64_t ticket, int timeout_us, double* u_out, mgwr_result* res) {
+  if (s == nullptr) return MGWR_E_INVAL;
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->tickets.find(ticket);
+  if (it == s->tickets.end()) return MGWR_E_INVAL;
+  Ticket* t = it->second.get();
+  if (t->state != 2) {
+    if (timeout_us <= 0) return MGWR_E_AGAIN;
+    const bool done = s->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us),
+                                          [&] { return t->state == 2; });
+    if (!done) return MGWR_E_TIMEOUT;
+  }
+  if (res != nullptr) *res = t->res;
+  if (u_out != nullptr && !t->u.empty()) std::memcpy(u_out, t->u.data(), t->u.size() * sizeof(double));
+  s->tickets.erase(it);
+  return MGWR_OK;
+}
+
+int mgwr_server_stats(mgwr_server_t s, mgwr_server_info* info) {
+  if (s == nullptr || info == nullptr) return MGWR_E_INVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  info->queued = (long long)s->queue.size();
+  info->completed = s->completed;
+  info->admitted = s->admitted;
+  info->in_use_bytes = s->in_use;
+  info->peak_bytes = s->peak;
+  info->budget_bytes = s->budget;
+  info->slots = s->slots;
+  return MGWR_OK;
+}
+
+}  // extern "C"

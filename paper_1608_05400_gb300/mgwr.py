@@ -26,7 +26,7 @@ MGWR_E_TIMEOUT = -7
 MGWR_E_CUDA = -8
 MGWR_E_STATE = -9
 
-MGWR_FP64, MGWR_MIXED = 0, 1
+MGWR_FP64, MGWR_MIXED, MGWR_MIXED_DD = 0, 1, 2
 MGWR_H64, MGWR_H32 = 64, 32
 MGWR_U, MGWR_F, MGWR_R = 0, 1, 2
 MGWR_RED, MGWR_BLACK = 0, 1
@@ -36,6 +36,24 @@ MGWR_ORDER_TEXT, MGWR_ORDER_TABLE = 0, 1
 class mgwr_stats(C.Structure):
     _fields_ = [("cycles", C.c_int), ("outer", C.c_int), ("relres", C.c_double),
                 ("factor", C.c_double), ("seconds", C.c_double)]
+
+
+class mgwr_request(C.Structure):
+    _fields_ = [("d", C.c_int), ("n", C.c_int), ("M", C.c_int), ("T", C.c_double),
+                ("alpha", C.c_double), ("f", C.POINTER(C.c_double)), ("g", C.POINTER(C.c_double)),
+                ("precision", C.c_int), ("order", C.c_int), ("cycle", C.c_int), ("nu1", C.c_int),
+                ("nu2", C.c_int), ("tol", C.c_double), ("max_cycles", C.c_int)]
+
+
+class mgwr_result(C.Structure):
+    _fields_ = [("status", C.c_int), ("stats", mgwr_stats), ("queue_s", C.c_double),
+                ("latency_s", C.c_double)]
+
+
+class mgwr_server_info(C.Structure):
+    _fields_ = [("queued", C.c_longlong), ("admitted", C.c_longlong), ("completed", C.c_longlong),
+                ("in_use_bytes", C.c_size_t), ("peak_bytes", C.c_size_t),
+                ("budget_bytes", C.c_size_t), ("slots", C.c_int)]
 
 
 _h = C.c_void_p
@@ -52,6 +70,7 @@ _SIGS = {
     "mgwr_set_order": (C.c_int, [_h, C.c_int]),
     "mgwr_set_stream": (C.c_int, [_h, C.c_void_p]),
     "mgwr_set_inner_cycles": (C.c_int, [_h, C.c_int]),
+    "mgwr_set_graphs": (C.c_int, [_h, C.c_int]),
     "mgwr_set_rhs": (C.c_int, [_h, _dp, _dp]),
     "mgwr_set_rhs_dev": (C.c_int, [_h, C.c_void_p, C.c_void_p]),
     "mgwr_set_initial": (C.c_int, [_h, _dp]),
@@ -74,12 +93,18 @@ _SIGS = {
     "mgwr_inverse_column": (C.c_int, [_h, C.c_int, _dp]),
     "mgwr_launch_count": (C.c_int, [_h, C.POINTER(C.c_longlong)]),
     "mgwr_inverse_column_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p]),
+    "mgwr_footprint": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_size_t)]),
+    "mgwr_server_create": (C.c_int, [C.c_size_t, C.c_int, C.POINTER(C.c_void_p)]),
+    "mgwr_server_destroy": (C.c_int, [C.c_void_p]),
+    "mgwr_submit": (C.c_int, [C.c_void_p, C.POINTER(mgwr_request), C.POINTER(C.c_uint64)]),
+    "mgwr_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int, _dp, C.POINTER(mgwr_result)]),
+    "mgwr_server_stats": (C.c_int, [C.c_void_p, C.POINTER(mgwr_server_info)]),
     "mgwr_profile": (C.c_int, [_h, C.c_int]),
     "mgwr_profile_read": (C.c_int, [_h, C.c_int, C.POINTER(C.c_longlong), _dp, _dp]),
 }
 
 KERNEL_CLASSES = ("sweep64", "sweep32", "defect64", "defect32", "restrict", "prolong",
-                  "coarsest", "refine", "defect_delta")
+                  "coarsest", "refine", "defect_delta", "defect_dd")
 
 _lib = None
 
@@ -185,6 +210,9 @@ class Solver:
 
     def set_stream(self, stream_ptr: int | None):
         self._check(self.lib.mgwr_set_stream(self.h, C.c_void_p(stream_ptr or 0)), "mgwr_set_stream")
+
+    def set_graphs(self, enable: bool):
+        self._check(self.lib.mgwr_set_graphs(self.h, int(enable)), "mgwr_set_graphs")
 
     def set_inner_cycles(self, k: int):
         self._check(self.lib.mgwr_set_inner_cycles(self.h, k), "mgwr_set_inner_cycles")
@@ -300,6 +328,88 @@ class Solver:
         k = np.empty((self.B, self.M) if self.batched else self.M)
         self._check(self.lib.mgwr_inverse_column(self.h, level, _ptr(k)), "mgwr_inverse_column")
         return k
+
+
+def footprint(d: int, n: int, M: int, batch: int = 1, precision: int = MGWR_FP64) -> int:
+    v = C.c_size_t()
+    st = load().mgwr_footprint(d, n, M, batch, precision, C.byref(v))
+    if st != MGWR_OK:
+        raise MGWRError(st, "mgwr_footprint: invalid shape")
+    return v.value
+
+
+@dataclass
+class Result:
+    status: int
+    stats: Stats
+    queue_s: float
+    latency_s: float
+    u: np.ndarray | None
+
+
+class Server:
+    """Request queue with HBM-budget admission and concurrent slots (mgwr_submit / mgwr_poll)."""
+
+    def __init__(self, hbm_budget: int, slots: int = 4):
+        self.lib = load()
+        h = C.c_void_p()
+        st = self.lib.mgwr_server_create(hbm_budget, slots, C.byref(h))
+        if st != MGWR_OK:
+            raise MGWRError(st, "mgwr_server_create failed")
+        self.h = h
+        self._shapes = {}
+
+    def submit(self, d, n, M, T, alpha, f, g=None, precision=MGWR_MIXED, order=MGWR_ORDER_TEXT,
+               cycle=1, nu1=1, nu2=1, tol=1e-8, max_cycles=100) -> int:
+        f = _f64(f)
+        N = n ** d
+        assert f.shape == (N, M), f.shape
+        gg = None if g is None else _f64(g).reshape(N)
+        rq = mgwr_request(d, n, M, T, alpha, _ptr(f), _ptr(gg), precision, order, cycle, nu1, nu2,
+                          tol, max_cycles)
+        t = C.c_uint64()
+        st = self.lib.mgwr_submit(self.h, C.byref(rq), C.byref(t))
+        if st != MGWR_OK:
+            raise MGWRError(st, "mgwr_submit: " + self.lib.mgwr_status_string(st).decode())
+        self._shapes[t.value] = (N, M)
+        return t.value
+
+    def poll(self, ticket: int, timeout_us: int = 0) -> Result | None:
+        N, M = self._shapes[ticket]
+        u = np.empty((N, M))
+        res = mgwr_result()
+        st = self.lib.mgwr_poll(self.h, ticket, timeout_us, _ptr(u), C.byref(res))
+        if st in (MGWR_E_AGAIN, MGWR_E_TIMEOUT):
+            return None
+        if st != MGWR_OK:
+            raise MGWRError(st, "mgwr_poll")
+        del self._shapes[ticket]
+        s = res.stats
+        ok = res.status in (MGWR_OK, MGWR_E_NOCONV)
+        return Result(res.status, Stats(s.cycles, s.outer, s.relres, s.factor, s.seconds, res.status),
+                      res.queue_s, res.latency_s, u if ok else None)
+
+    def info(self) -> dict:
+        i = mgwr_server_info()
+        self.lib.mgwr_server_stats(self.h, C.byref(i))
+        return {k: getattr(i, k) for k, _ in mgwr_server_info._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mgwr_server_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def launch_count() -> int:

@@ -70,3 +70,32 @@ def test_null_handle_calls_are_rejected(lib):
 def test_status_strings(lib):
     for code in range(-9, 1):
         assert lib.mgwr_status_string(code) not in (None, b"unknown status")
+
+
+def test_footprint_is_host_arithmetic_and_scales(lib):
+    from paper_1608_05400_gb300.mgwr import MGWR_FP64, MGWR_MIXED, footprint
+    # finest FP64 fields alone: u, f, r, dl of 255^2 x 1024 doubles
+    fields = 4 * 255 ** 2 * 1024 * 8
+    fp = footprint(2, 255, 1024, 1, MGWR_FP64)
+    assert fields < fp < 1.5 * fields
+    # mixed keeps the FP64 iterate and right-hand side and an FP32 hierarchy
+    mx = footprint(2, 255, 1024, 1, MGWR_MIXED)
+    assert 2 * 255 ** 2 * 1024 * 8 + 4 * 255 ** 2 * 1024 * 4 < mx < fp
+    # linear in the batch, monotone in n and M
+    assert abs(footprint(2, 63, 256, 64) - 64 * footprint(2, 63, 256, 1)) < 64 * (3 << 20)
+    assert footprint(1, 63, 64) < footprint(1, 127, 64) < footprint(1, 127, 128)
+    v = C.c_size_t()
+    assert lib.mgwr_footprint(2, 64, 256, 1, 0, C.byref(v)) == mgwr.MGWR_E_INVAL
+    assert lib.mgwr_footprint(2, 63, 256, 0, 0, C.byref(v)) == mgwr.MGWR_E_INVAL
+    assert lib.mgwr_footprint(2, 63, 256, 1, 7, C.byref(v)) == mgwr.MGWR_E_INVAL
+
+
+def test_server_calls_reject_null_and_bad_arguments(lib):
+    t = C.c_uint64()
+    rq = mgwr.mgwr_request()
+    assert lib.mgwr_submit(None, C.byref(rq), C.byref(t)) == mgwr.MGWR_E_INVAL
+    assert lib.mgwr_poll(None, 1, 0, None, None) == mgwr.MGWR_E_INVAL
+    assert lib.mgwr_server_destroy(None) == mgwr.MGWR_OK
+    h = C.c_void_p()
+    assert lib.mgwr_server_create(0, 4, C.byref(h)) == mgwr.MGWR_E_INVAL
+    assert lib.mgwr_server_create(1 << 30, 0, C.byref(h)) == mgwr.MGWR_E_INVAL

@@ -63,7 +63,7 @@ def test_batched_cycles_equal_single_instance_cycles(hier, d, n, M, cyc):
             np.testing.assert_array_equal(ub[b], s1.field_get(hier, L, G.MGWR_U))
 
 
-@pytest.mark.parametrize("precision", [G.MGWR_FP64, G.MGWR_MIXED])
+@pytest.mark.parametrize("precision", [G.MGWR_FP64, G.MGWR_MIXED, G.MGWR_MIXED_DD])
 def test_batched_solve_matches_oracle(precision):
     d, n, M = 2, 31, 64
     probs = [inputs.Problem(d, n, M, T, a, "t2") for T, a in zip(TS, ALPHAS)]

@@ -274,6 +274,41 @@ def test_mixed_precision_solve_matches_oracle():
     assert rel(u, ref) <= 1e-8
 
 
+@pytest.mark.parametrize("d,n,M,kind", [(2, 63, 128, "talpha"), (1, 255, 1024, "t2"), (2, 31, 4096, "t2")])
+def test_mixed_double_float_solve_matches_oracle(d, n, M, kind):
+    # FP32 cycles, double-float defect and update: same converged solution; the
+    # IEEE-double defect of the result agrees with the double-float stopping test
+    prob = inputs.Problem(d, n, M, 1.0, 0.5, kind)
+    f = prob.rhs()
+    with G.Solver(d, n, M, 1.0, 0.5) as s:
+        s.set_precision(G.MGWR_MIXED_DD)
+        s.set_rhs(f)
+        st = s.solve(1, 1, 1, tol=1e-10, max_cycles=40)
+        u = s.solution()
+        r64 = s.residual()
+    ref = separable.solution(d, n, M, 1.0, 0.5, prob.rhs_profile(), inputs.phi(d, n))
+    assert st.relres <= 1e-10 and r64 <= 2e-10
+    assert rel(u, ref) <= 1e-8
+
+
+@pytest.mark.parametrize("precision", [G.MGWR_FP64, G.MGWR_MIXED, G.MGWR_MIXED_DD])
+@pytest.mark.parametrize("cyc", [(1, 1, 1), (0, 1, 1), (1, 0, 2)])
+def test_graph_replayed_solve_equals_direct_launches(precision, cyc):
+    nu1, nu2, gamma = cyc
+    d, n, M = 2, 31, 64
+    f = inputs.Problem(d, n, M, 1.0, 0.4, "t2").rhs()
+    out = []
+    for graphs in (True, False):
+        with G.Solver(d, n, M, 1.0, 0.4) as s:
+            s.set_precision(precision)
+            s.set_graphs(graphs)
+            s.set_rhs(f)
+            st = s.solve(gamma, nu1, nu2, tol=1e-10, max_cycles=40)
+            out.append((s.solution(), st.cycles, st.relres))
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    assert out[0][1:] == out[1][1:]
+
+
 def test_paper_table_1d_iterations_on_gpu():
     # Table table_it_1d, V(0,1), delta = 0.4, 128 x 128 grid: 7 cycles (table order)
     import math

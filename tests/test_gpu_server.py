@@ -1,0 +1,89 @@
+"""Serving runtime (mgwr_submit / mgwr_poll): results of requests solved in a
+mix, concurrently on several slots, are identical to the same requests solved
+alone; admission respects the memory budget; polling and errors behave as
+documented."""
+import numpy as np
+import pytest
+
+from oracle import direct
+from paper_1608_05400_gb300 import inputs
+from paper_1608_05400_gb300 import mgwr as G
+
+pytestmark = pytest.mark.gpu
+
+REQUESTS = [  # d, n, M, alpha, kind, precision
+    (1, 63, 64, 0.5, "t2", G.MGWR_FP64),
+    (2, 31, 128, 0.3, "talpha", G.MGWR_MIXED),
+    (1, 255, 256, 0.8, "t2", G.MGWR_MIXED),
+    (2, 63, 64, 0.65, "t2", G.MGWR_FP64),
+    (2, 15, 512, 0.2, "talpha", G.MGWR_MIXED),
+    (1, 31, 1024, 0.45, "t2", G.MGWR_FP64),
+    (2, 127, 128, 0.9, "t2", G.MGWR_MIXED_DD),
+    (1, 7, 4096, 0.35, "talpha", G.MGWR_FP64),
+    (2, 31, 1024, 0.55, "t2", G.MGWR_MIXED_DD),
+]
+
+
+def _alone(d, n, M, a, f, precision, tol):
+    with G.Solver(d, n, M, 1.0, a) as s:
+        s.set_precision(precision)
+        s.set_rhs(f)
+        st = s.solve(1, 1, 1, tol=tol, max_cycles=100)
+        return s.solution(), st
+
+
+def test_results_in_the_mix_equal_results_alone():
+    tol = 1e-10
+    fs = [inputs.Problem(d, n, M, 1.0, a, k).rhs() for d, n, M, a, k, _ in REQUESTS]
+    with G.Server(hbm_budget=8 << 30, slots=4) as srv:
+        tickets = [srv.submit(d, n, M, 1.0, a, f, precision=p, tol=tol)
+                   for (d, n, M, a, k, p), f in zip(REQUESTS, fs)]
+        results = [srv.poll(t, timeout_us=120_000_000) for t in tickets]
+        info = srv.info()
+    assert info["completed"] == len(REQUESTS) and info["peak_bytes"] <= info["budget_bytes"]
+    for (d, n, M, a, k, p), f, res in zip(REQUESTS, fs, results):
+        assert res is not None and res.status == G.MGWR_OK
+        assert res.latency_s >= res.queue_s >= 0.0
+        u, st = _alone(d, n, M, a, f, p, tol)
+        np.testing.assert_array_equal(res.u, u)
+        assert res.stats.cycles == st.cycles and res.stats.relres == st.relres
+
+
+def test_served_result_matches_oracle():
+    d, n, M, a = 2, 31, 64, 0.4
+    f = inputs.Problem(d, n, M, 1.0, a, "t2").rhs()
+    with G.Server(hbm_budget=1 << 30, slots=2) as srv:
+        res = srv.poll(srv.submit(d, n, M, 1.0, a, f, precision=G.MGWR_MIXED, tol=1e-10),
+                       timeout_us=60_000_000)
+    ref = direct.time_stepping(d, n, M, 1.0, a, f)
+    assert np.abs(res.u - ref).max() <= 1e-9 * np.abs(ref).max()
+
+
+def test_admission_budget_and_refusal():
+    fp = G.footprint(2, 63, 256, 1, G.MGWR_FP64)
+    f = inputs.Problem(2, 63, 256, 1.0, 0.5, "t2").rhs()
+    # room for one such request at a time: all complete, never two at once
+    with G.Server(hbm_budget=int(1.5 * fp), slots=4) as srv:
+        ts = [srv.submit(2, 63, 256, 1.0, 0.5, f, precision=G.MGWR_FP64) for _ in range(3)]
+        for t in ts:
+            assert srv.poll(t, timeout_us=60_000_000).status == G.MGWR_OK
+        assert srv.info()["peak_bytes"] <= int(1.5 * fp)
+    # larger than the whole budget: refused at submit
+    with G.Server(hbm_budget=fp // 2, slots=2) as srv:
+        with pytest.raises(G.MGWRError) as e:
+            srv.submit(2, 63, 256, 1.0, 0.5, f)
+        assert e.value.status == G.MGWR_E_TOOBIG
+
+
+def test_poll_timeout_unknown_ticket_and_numeric_failure():
+    f = inputs.Problem(2, 255, 1024, 1.0, 0.5, "t2").rhs()
+    bad = inputs.Problem(1, 31, 64, 1.0, 0.5, "t2").rhs()
+    bad[3, 5] = np.nan
+    with G.Server(hbm_budget=8 << 30, slots=2) as srv:
+        t = srv.submit(2, 255, 1024, 1.0, 0.5, f, precision=G.MGWR_FP64, tol=1e-10)
+        assert srv.poll(t, timeout_us=0) is None          # still running: not ready
+        assert srv.poll(t, timeout_us=120_000_000).status == G.MGWR_OK
+        assert srv.lib.mgwr_poll(srv.h, 987654, 0, None, None) == G.MGWR_E_INVAL
+        tb = srv.submit(1, 31, 64, 1.0, 0.5, bad, precision=G.MGWR_FP64)
+        rb = srv.poll(tb, timeout_us=60_000_000)
+        assert rb.status == G.MGWR_E_NUMERIC

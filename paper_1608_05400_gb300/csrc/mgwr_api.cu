@@ -36,6 +36,7 @@ struct Hier {
   Cx<R>* spec = nullptr;          // batch * nlev * L: spectra of the inverse columns
   Cx<R>* tspec = nullptr;         // batch * L: spectra of the Toeplitz columns
   Cx<R>* tw = nullptr;            // L twiddles
+  R* zero = nullptr;              // M zeros: the neighbour line outside the grid
   bool ready = false;             // spectra present
   bool full = false;              // every level's u, f, r, dl allocated
 };
@@ -61,6 +62,7 @@ struct mgwr_handle {
   // Toeplitz spectra, for the outer defect of MGWR_MIXED_DD
   mgwr::dd* u_dd = nullptr;
   mgwr::dd* f_dd = nullptr;
+  mgwr::dd* zero_dd = nullptr;
   Cx<mgwr::dd>* tspec_dd = nullptr;
   Cx<mgwr::dd>* tw_dd = nullptr;
   unsigned long long* norm_bits = nullptr;  // device, one per instance
@@ -75,6 +77,7 @@ struct mgwr_handle {
   cudaGraphExec_t iter_exec = nullptr;
   long long iter_key = -1;   // (precision, cycle, nu1, nu2, inner, order) it was captured for
   bool iter_exact = true;    // its norms come from the full defect
+  long long iter_kernels = 0;  // kernel launches recorded in the graph
   // per-kernel-class timing (mgwr_profile): event pairs around each launch
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -183,6 +186,7 @@ int ensure_h32(mgwr_t h) {
   if (h->h32.ready) return MGWR_OK;
   Hier<float>& H = h->h32;
   MGWR_TRY(ensure_full(h, H));
+  MGWR_TRY(ensure_field(h, &H.zero, (size_t)h->M));
   const size_t nspec = (size_t)h->B * h->nlev * h->L;
   MGWR_TRY(dev_alloc(h, &H.spec, sizeof(Cx<float>) * nspec));
   MGWR_TRY(dev_alloc(h, &H.tspec, sizeof(Cx<float>) * (size_t)h->B * h->L));
@@ -200,6 +204,7 @@ int ensure_dd(mgwr_t h) {
   const size_t cnt = level_count(h, h->nlev - 1);
   MGWR_TRY(dev_alloc(h, &h->u_dd, cnt * sizeof(mgwr::dd)));
   MGWR_TRY(dev_alloc(h, &h->f_dd, cnt * sizeof(mgwr::dd)));
+  MGWR_TRY(ensure_field(h, &h->zero_dd, (size_t)h->M));
   MGWR_TRY(dev_alloc(h, &h->tspec_dd, sizeof(Cx<mgwr::dd>) * (size_t)h->B * h->L));
   MGWR_TRY(dev_alloc(h, &h->tw_dd, sizeof(Cx<mgwr::dd>) * (size_t)h->L));
   MGWR_CK(h, mgwr::launch_split_cx(h->tspec_dd, h->h64.tspec, (size_t)h->B * h->L, h->stream));
@@ -251,7 +256,7 @@ template <class R>
 int coarsest(mgwr_t h, Hier<R>& H) {
   const int pm = prof_begin(h, MGWR_K_COARSEST, (double)h->B);
   MGWR_CK(h, mgwr::launch_sweep<R>(H.f[0], H.u[0], (R*)nullptr, H.spec, (size_t)h->nlev * h->L,
-                                    H.tw, shape(h, 0), 0, true, R(0), h->stream));
+                                    H.tw, H.zero, shape(h, 0), 0, true, R(0), h->stream));
   prof_end(h, pm);
   H.rs[0] = R_STALE;
   return MGWR_OK;
@@ -266,8 +271,8 @@ int sweep_colour(mgwr_t h, Hier<R>& H, int l, int colour, R* delta) {
   const double lines = (double)h->B * (double)(par == 0 ? (N + 1) / 2 : N / 2);
   const int pm = prof_begin(h, sizeof(R) == 8 ? MGWR_K_SWEEP64 : MGWR_K_SWEEP32, lines);
   MGWR_CK(h, mgwr::launch_sweep<R>(H.f[l], H.u[l], delta, H.spec + (size_t)l * h->L,
-                                    (size_t)h->nlev * h->L, H.tw, shape(h, l), par, false,
-                                    R(h->hinv2[l]), h->stream));
+                                    (size_t)h->nlev * h->L, H.tw, H.zero, shape(h, l), par,
+                                    false, R(h->hinv2[l]), h->stream));
   prof_end(h, pm);
   return MGWR_OK;
 }
@@ -298,7 +303,8 @@ int defect(mgwr_t h, Hier<R>& H, int l, unsigned long long* norm_bits) {
   const int pm = prof_begin(h, sizeof(R) == 8 ? MGWR_K_DEFECT64 : MGWR_K_DEFECT32,
                             (double)(points(h, l) * h->B));
   MGWR_CK(h, (mgwr::launch_defect<R, R>(H.u[l], H.f[l], H.r[l], H.tspec, (size_t)h->L, H.tw,
-                                         shape(h, l), R(h->hinv2[l]), norm_bits, h->stream)));
+                                         H.zero, shape(h, l), R(h->hinv2[l]), norm_bits,
+                                         h->stream)));
   prof_end(h, pm);
   H.rs[l] = R_CURRENT;
   return MGWR_OK;
@@ -391,14 +397,14 @@ int finest_defect_norms(mgwr_t h, std::vector<double>& norms, bool to_h32) {
   if (to_h32) {
     MGWR_CK(h, (mgwr::launch_defect<double, float>(h->h64.u[L], h->h64.f[L], h->h32.f[L],
                                                     h->h64.tspec, (size_t)h->L, h->h64.tw,
-                                                    shape(h, L), h->hinv2[L], h->norm_bits,
+                                                    h->h64.zero, shape(h, L), h->hinv2[L], h->norm_bits,
                                                     h->stream)));
     h->h32.rs[L] = R_STALE;
   } else {
     MGWR_TRY(ensure_field(h, &h->h64.r[L], level_count(h, L)));
     MGWR_CK(h, (mgwr::launch_defect<double, double>(h->h64.u[L], h->h64.f[L], h->h64.r[L],
                                                      h->h64.tspec, (size_t)h->L, h->h64.tw,
-                                                     shape(h, L), h->hinv2[L], h->norm_bits,
+                                                     h->h64.zero, shape(h, L), h->hinv2[L], h->norm_bits,
                                                      h->stream)));
     h->h64.rs[L] = R_CURRENT;
   }
@@ -413,7 +419,7 @@ int finest_defect_norms_dd(mgwr_t h, std::vector<double>& norms) {
   MGWR_TRY(clear_norms(h));
   const int pm = prof_begin(h, MGWR_K_DEFECT_DD, (double)(points(h, L) * h->B));
   MGWR_CK(h, (mgwr::launch_defect<mgwr::dd, float>(h->u_dd, h->f_dd, h->h32.f[L], h->tspec_dd,
-                                                    (size_t)h->L, h->tw_dd, shape(h, L),
+                                                    (size_t)h->L, h->tw_dd, h->zero_dd, shape(h, L),
                                                     mgwr::dd(h->hinv2[L]), h->norm_bits,
                                                     h->stream)));
   prof_end(h, pm);
@@ -467,13 +473,13 @@ int enqueue_iteration(mgwr_t h, int cyc, int nu1, int nu2, bool* exact) {
     const int pd = prof_begin(h, ddef ? MGWR_K_DEFECT_DD : MGWR_K_DEFECT64, (double)(points(h, L) * h->B));
     if (ddef)
       MGWR_CK(h, (mgwr::launch_defect<mgwr::dd, float>(h->u_dd, h->f_dd, h->h32.f[L], h->tspec_dd,
-                                                        (size_t)h->L, h->tw_dd, shape(h, L),
+                                                        (size_t)h->L, h->tw_dd, h->zero_dd, shape(h, L),
                                                         mgwr::dd(h->hinv2[L]), h->norm_bits,
                                                         h->stream)));
     else
       MGWR_CK(h, (mgwr::launch_defect<double, float>(h->h64.u[L], h->h64.f[L], h->h32.f[L],
                                                       h->h64.tspec, (size_t)h->L, h->h64.tw,
-                                                      shape(h, L), h->hinv2[L], h->norm_bits,
+                                                      h->h64.zero, shape(h, L), h->hinv2[L], h->norm_bits,
                                                       h->stream)));
     prof_end(h, pd);
     h->h32.rs[L] = R_STALE;
@@ -497,8 +503,12 @@ int run_iteration(mgwr_t h, int cyc, int nu1, int nu2, std::vector<double>& norm
       cudaGraph_t g = nullptr;
       MGWR_CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
       bool ex = true;
+      const long long before = mgwr::launch_counter();
       const int st = enqueue_iteration(h, cyc, nu1, nu2, &ex);
       const cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+      // captured launches do not run; count them when the graph is replayed
+      const long long captured = mgwr::launch_counter() - before;
+      mgwr::add_launches(-captured);
       if (st != MGWR_OK) {
         if (g) cudaGraphDestroy(g);
         return st;
@@ -509,8 +519,10 @@ int run_iteration(mgwr_t h, int cyc, int nu1, int nu2, std::vector<double>& norm
       MGWR_CK(h, ei);
       h->iter_key = key;
       h->iter_exact = ex;
+      h->iter_kernels = captured;
     }
     MGWR_CK(h, cudaGraphLaunch(h->iter_exec, h->stream));
+    mgwr::add_launches(h->iter_kernels);
     *exact = h->iter_exact;
   } else {
     MGWR_TRY(enqueue_iteration(h, cyc, nu1, nu2, exact));
@@ -637,6 +649,7 @@ int create_impl(int d, int n, int M, const double* T, const double* alpha, int b
   h->h64.ready = true;
   // the finest iterate and right-hand side always exist; the rest on demand
   const int Lf = h->nlev - 1;
+  if ((s = ensure_field(h, &h->h64.zero, (size_t)M)) != MGWR_OK) return bail(s);
   if ((s = ensure_field(h, &h->h64.u[Lf], level_count(h, Lf))) != MGWR_OK) return bail(s);
   if ((s = ensure_field(h, &h->h64.f[Lf], level_count(h, Lf))) != MGWR_OK) return bail(s);
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) {

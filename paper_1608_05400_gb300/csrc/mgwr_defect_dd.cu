@@ -1,0 +1,9 @@
+// Defect instantiations: double-float iterate, FP32 output.
+#include "mgwr_defect.cuh"
+
+namespace mgwr {
+template cudaError_t launch_defect<dd, float>(const dd*, const dd*, float*, const Cx<dd>*, size_t,
+                                              const Cx<dd>*, const dd*, const LevelShape&, dd,
+                                              unsigned long long*, cudaStream_t);
+
+}  // namespace mgwr

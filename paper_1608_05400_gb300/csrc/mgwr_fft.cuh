@@ -92,10 +92,15 @@ __device__ __forceinline__ void dft8_half_input(Cx<R> (&v)[8]) {
   v[1] = b0; v[3] = b1; v[5] = b2; v[7] = b3;
 }
 
-// Shared-memory index with one pad slot per 8 elements (bank-conflict free for
-// the strided and the contiguous access patterns of the stages below).
-__device__ __forceinline__ int pad8(int x) { return x + (x >> 3); }
-__host__ __device__ __forceinline__ int padded_len(int L) { return L + (L >> 3); }
+// Shared-memory index with one pad slot per 8 (16-byte elements) or 16 (8-byte
+// elements) values: the contiguous-per-thread and the long-stride access
+// patterns of the stages below then hit distinct banks.
+template <class R>
+struct Pad {
+  static constexpr int shift = sizeof(Cx<R>) >= 16 ? 3 : 4;
+  static __device__ __forceinline__ int idx(int x) { return x + (x >> shift); }
+  static __host__ __device__ __forceinline__ int len(int L) { return L + (L >> shift); }
+};
 
 // Last-stage butterflies on the 8 contiguous values a thread owns.
 template <bool INV, class R>
@@ -113,72 +118,120 @@ __device__ __forceinline__ void last_stage(Cx<R> (&v)[8], int rlast) {
   }
 }
 
-struct FftShape {
+// Stage plan of a length-L = 2^logL transform: radix-8 stages 0 .. s8-1 and,
+// when logL is not a multiple of 3, a last stage of radix 2^(logL mod 3).
+// Stage 0 reads global memory; "middle" stages 1 .. kmid_end-1 run through
+// shared memory; the last stage (span 1) is done on 8 contiguous values.
+struct FftShape {  // run-time length
+  static constexpr bool kFixed = false;
   int L, logL, L8, rlast, kmid_end;
   __device__ __forceinline__ explicit FftShape(int logL_) : L(1 << logL_), logL(logL_) {
     L8 = L >> 3;
     const int rem = logL % 3;
     rlast = rem == 0 ? 8 : (1 << rem);
     const int s8 = logL / 3;
-    kmid_end = rem == 0 ? s8 - 1 : s8;  // radix-8 stages 1 .. kmid_end-1 are "middle"
+    kmid_end = rem == 0 ? s8 - 1 : s8;
   }
 };
 
+template <int LOGL>
+struct FixedShape {  // compile-time length: every index below folds to a constant offset
+  static constexpr bool kFixed = true;
+  static constexpr int logL = LOGL, L = 1 << LOGL, L8 = L >> 3;
+  static constexpr int rlast = LOGL % 3 == 0 ? 8 : (1 << (LOGL % 3));
+  static constexpr int kmid_end = LOGL % 3 == 0 ? LOGL / 3 - 1 : LOGL / 3;
+  __device__ __forceinline__ explicit FixedShape(int) {}
+};
+
+// v[q] *= w^(j q) (CONJ: by the conjugate), q = 1..7, w = exp(-2 pi i / L),
+// jstride = j L / S for a sub-transform of length S.  FP32 forms the seven
+// powers from w, w^2, w^4 (three table loads, four products; error a few
+// ulps); the wider types load each twiddle right before its product, which
+// keeps fewer values live.
+template <bool CONJ, class R>
+__device__ __forceinline__ void twiddle_mul(Cx<R> (&v)[8], const Cx<R>* __restrict__ tw,
+                                            int jstride) {
+  if constexpr (sizeof(R) == 4) {
+    Cx<R> w[8];
+    w[1] = tw[jstride];
+    w[2] = tw[2 * jstride];
+    w[4] = tw[4 * jstride];
+    w[3] = cmul(w[1], w[2]);
+    w[5] = cmul(w[1], w[4]);
+    w[6] = cmul(w[2], w[4]);
+    w[7] = cmul(w[3], w[4]);
+#pragma unroll
+    for (int q = 1; q < 8; ++q) v[q] = CONJ ? cmulc(v[q], w[q]) : cmul(v[q], w[q]);
+  } else {
+#pragma unroll
+    for (int q = 1; q < 8; ++q)
+      v[q] = CONJ ? cmulc(v[q], tw[jstride * q]) : cmul(v[q], tw[jstride * q]);
+  }
+}
+
 // Radix-8 middle stage k (span L >> 3(k+1)), forward or inverse, in shared memory.
-template <bool INV, class R>
-__device__ __forceinline__ void middle_stage(Cx<R>* buf, int t, const FftShape& sh, int k,
+template <bool INV, class R, class SH>
+__device__ __forceinline__ void middle_stage(Cx<R>* buf, int t, const SH& sh, int k,
                                              const Cx<R>* __restrict__ tw) {
+  using P = Pad<R>;
   const int shift = 3 * (k + 1);
   const int s = sh.L >> shift;
   const int j = t & (s - 1);
   const int base = ((t - j) << 3) + j;
-  const int tws = 3 * k;
   Cx<R> v[8];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) v[q] = buf[pad8(base + q * s)];
+  for (int q = 0; q < 8; ++q) v[q] = buf[P::idx(base + q * s)];
   if (!INV) {
     dft8<false>(v);
-#pragma unroll
-    for (int q = 1; q < 8; ++q) v[q] = cmul(v[q], tw[(j * q) << tws]);
+    twiddle_mul<false>(v, tw, j << (3 * k));
   } else {
-#pragma unroll
-    for (int q = 1; q < 8; ++q) v[q] = cmulc(v[q], tw[(j * q) << tws]);
+    twiddle_mul<true>(v, tw, j << (3 * k));
     dft8<true>(v);
   }
 #pragma unroll
-  for (int q = 0; q < 8; ++q) buf[pad8(base + q * s)] = v[q];
+  for (int q = 0; q < 8; ++q) buf[P::idx(base + q * s)] = v[q];
 }
 
 // Forward transform of one zero-padded line pair.  `load(m)` returns the pair's
 // input at time index m < M (called for m = t + q L/8, q < 4).  On return the
 // thread holds, in v, the transform values at spectral positions 8t .. 8t+7.
 // Every thread of the block must call this (it synchronises the block).
-template <class R, class Load>
-__device__ __forceinline__ void fft_forward(Cx<R>* buf, int t, const FftShape& sh,
+template <class R, class SH, class Load>
+__device__ __forceinline__ void fft_forward(Cx<R>* buf, int t, const SH& sh,
                                             const Cx<R>* __restrict__ tw, Load load, Cx<R> (&v)[8]) {
+  using P = Pad<R>;
 #pragma unroll
   for (int q = 0; q < 4; ++q) v[q] = load(t + q * sh.L8);
   dft8_half_input(v);
   if (sh.logL == 3) return;  // single stage: thread 0 holds positions 0..7
+  twiddle_mul<false>(v, tw, t);
 #pragma unroll
-  for (int q = 1; q < 8; ++q) v[q] = cmul(v[q], tw[t * q]);
-#pragma unroll
-  for (int q = 0; q < 8; ++q) buf[pad8(t + q * sh.L8)] = v[q];
+  for (int q = 0; q < 8; ++q) buf[P::idx(t + q * sh.L8)] = v[q];
   __syncthreads();
-  for (int k = 1; k < sh.kmid_end; ++k) {
-    middle_stage<false>(buf, t, sh, k, tw);
-    __syncthreads();
+  if constexpr (SH::kFixed) {
+#pragma unroll
+    for (int k = 1; k < sh.kmid_end; ++k) {
+      middle_stage<false>(buf, t, sh, k, tw);
+      __syncthreads();
+    }
+  } else {
+#pragma unroll 1
+    for (int k = 1; k < sh.kmid_end; ++k) {
+      middle_stage<false>(buf, t, sh, k, tw);
+      __syncthreads();
+    }
   }
 #pragma unroll
-  for (int q = 0; q < 8; ++q) v[q] = buf[pad8(8 * t + q)];
+  for (int q = 0; q < 8; ++q) v[q] = buf[P::idx(8 * t + q)];
   last_stage<false>(v, sh.rlast);
 }
 
 // Inverse transform starting from the spectral values in v (positions 8t..8t+7,
 // already multiplied).  `store(m, value)` receives the outputs for m < M.
-template <class R, class Store>
-__device__ __forceinline__ void fft_inverse(Cx<R>* buf, int t, const FftShape& sh,
+template <class R, class SH, class Store>
+__device__ __forceinline__ void fft_inverse(Cx<R>* buf, int t, const SH& sh,
                                             const Cx<R>* __restrict__ tw, Cx<R> (&v)[8], Store store) {
+  using P = Pad<R>;
   if (sh.logL == 3) {
     dft8<true>(v);
 #pragma unroll
@@ -188,16 +241,24 @@ __device__ __forceinline__ void fft_inverse(Cx<R>* buf, int t, const FftShape& s
   last_stage<true>(v, sh.rlast);
   // each thread rewrites only the 8 positions it read in fft_forward
 #pragma unroll
-  for (int q = 0; q < 8; ++q) buf[pad8(8 * t + q)] = v[q];
+  for (int q = 0; q < 8; ++q) buf[P::idx(8 * t + q)] = v[q];
   __syncthreads();
-  for (int k = sh.kmid_end - 1; k >= 1; --k) {
-    middle_stage<true>(buf, t, sh, k, tw);
-    __syncthreads();
+  if constexpr (SH::kFixed) {
+#pragma unroll
+    for (int k = sh.kmid_end - 1; k >= 1; --k) {
+      middle_stage<true>(buf, t, sh, k, tw);
+      __syncthreads();
+    }
+  } else {
+#pragma unroll 1
+    for (int k = sh.kmid_end - 1; k >= 1; --k) {
+      middle_stage<true>(buf, t, sh, k, tw);
+      __syncthreads();
+    }
   }
 #pragma unroll
-  for (int q = 0; q < 8; ++q) v[q] = buf[pad8(t + q * sh.L8)];
-#pragma unroll
-  for (int q = 1; q < 8; ++q) v[q] = cmulc(v[q], tw[t * q]);
+  for (int q = 0; q < 8; ++q) v[q] = buf[P::idx(t + q * sh.L8)];
+  twiddle_mul<true>(v, tw, t);
   dft8<true>(v);
 #pragma unroll
   for (int q = 0; q < 4; ++q) store(t + q * sh.L8, v[q]);

@@ -38,10 +38,11 @@ struct LevelShape {
 // spec + b * spec_stride).  all_points: every point, no neighbour term
 // (one-point coarsest solve).  delta != null: also delta_p = u_p(new) -
 // u_p(old) on the swept lines.
+// `zero` is a line of M zeros standing in for neighbours outside the grid.
 template <class R>
 cudaError_t launch_sweep(const R* f, R* u, R* delta, const Cx<R>* spec, size_t spec_stride,
-                         const Cx<R>* tw, const LevelShape& ls, int par, bool all_points, R hinv2,
-                         cudaStream_t s);
+                         const Cx<R>* tw, const R* zero, const LevelShape& ls, int par,
+                         bool all_points, R hinv2, cudaStream_t s);
 
 // Defect after a red-black step from the black half-sweep's delta: r = 0 on the
 // black points, r = hinv2 * sum of neighbour deltas on the red points
@@ -54,7 +55,7 @@ cudaError_t launch_defect_from_delta(const R* delta, R* r, const LevelShape& ls,
 // norm_bits[b] (bit pattern of a non-negative double, atomicMax) when non-null.
 template <class R, class RO>
 cudaError_t launch_defect(const R* u, const R* f, RO* r, const Cx<R>* tspec, size_t spec_stride,
-                          const Cx<R>* tw, const LevelShape& ls, R hinv2,
+                          const Cx<R>* tw, const R* zero, const LevelShape& ls, R hinv2,
                           unsigned long long* norm_bits, cudaStream_t s);
 
 // fc = full weighting of r (fine n -> coarse (n-1)/2), uc = 0.
@@ -95,7 +96,9 @@ cudaError_t launch_spectra(Cx<double>* spec, const double* lines, int count, int
                            const Cx<double>* tw, cudaStream_t s);
 cudaError_t launch_round_cx(Cx<float>* dst, const Cx<double>* src, size_t count, cudaStream_t s);
 
-// Kernel launches issued through the launchers above (process-wide counter).
+// Kernel launches issued through the launchers above (process-wide counter),
+// including those replayed from captured graphs (add_launches).
 long long launch_counter();
+void add_launches(long long n);
 
 }  // namespace mgwr

@@ -1,206 +1,28 @@
-// CUDA kernels of the MGWR solver (sm_103a).  See mgwr_fft.cuh for the FFT
-// engine shared by the smoother and the defect.
+// CUDA kernels of the MGWR solver (sm_103a): defect after a smoothing step,
+// grid transfers, precision conversions and the FP64 setup (coefficients,
+// inverse columns, twiddles, spectra).  The smoother and the full defect live
+// in mgwr_sweep.cu and mgwr_defect.cu.
 #include <cuda_runtime.h>
 
 #include <atomic>
 #include <cmath>
 
-#include "mgwr_dd.cuh"
-#include "mgwr_fft.cuh"
-#include "mgwr_internal.h"
+#include "mgwr_common.cuh"
 
 namespace mgwr {
 
 namespace {
 std::atomic<long long> g_launches{0};
+}  // namespace
 
-inline cudaError_t counted(cudaError_t e) {
+cudaError_t counted(cudaError_t e) {
   g_launches.fetch_add(1, std::memory_order_relaxed);
   return e;
 }
 
-// Threads per line pair: L/8.  Blocks hold 256 threads (several pairs) up to
-// L = 2048 and one pair of L/8 threads beyond.
-inline int block_threads(int L) { return L / 8 > 256 ? L / 8 : 256; }
-
-inline int ilog2(int x) {
-  int l = 0;
-  while ((1 << l) < x) ++l;
-  return l;
-}
-}  // namespace
-
 long long launch_counter() { return g_launches.load(); }
 
-// ---------------------------------------------------------------------------------
-// point enumeration
-// ---------------------------------------------------------------------------------
-
-// Number of points of parity `par`: (i & 1) == par in 1-D, ((i + j) & 1) == par in 2-D.
-__host__ __device__ __forceinline__ int colour_count(int d, int n, int par) {
-  if (d == 1) return (n - par + 1) / 2;
-  return ((n - 1) / 2) * n + (n - par + 1) / 2;
-}
-
-// k-th point of parity `par` in row-major order (p = i + n*j).
-__device__ __forceinline__ int colour_point(int k, int d, int n, int par, int& i, int& j) {
-  if (d == 1) {
-    i = par + 2 * k;
-    j = 0;
-    return i;
-  }
-  const int a = k / n;
-  const int rem = k - a * n;
-  const int c0 = (n - par + 1) / 2;  // points in row 2a (first i = par)
-  if (rem < c0) {
-    j = 2 * a;
-    i = par + 2 * rem;
-  } else {
-    j = 2 * a + 1;
-    i = (par ^ 1) + 2 * (rem - c0);
-  }
-  return i + n * j;
-}
-
-// Sum of the neighbour lines of point (i, j) at time m (zero Dirichlet values).
-template <class R>
-__device__ __forceinline__ R neighbour_sum(const R* __restrict__ u, int d, int n, int i, int j,
-                                           size_t pM, int M, int m) {
-  R s = R(0);
-  if (i > 0) s += u[pM - M + m];
-  if (i < n - 1) s += u[pM + M + m];
-  if (d == 2) {
-    const size_t nM = (size_t)n * M;
-    if (j > 0) s += u[pM - nM + m];
-    if (j < n - 1) s += u[pM + nM + m];
-  }
-  return s;
-}
-
-__device__ __forceinline__ void atomic_max_nonneg(unsigned long long* bits, double v) {
-  // non-negative doubles order like their bit patterns; NaN (all exponent bits
-  // set, non-zero mantissa) compares above +inf and so propagates
-  atomicMax(bits, (unsigned long long)__double_as_longlong(v));
-}
-
-template <class R>
-__device__ __forceinline__ R absmax_nan(R a, R b) {
-  // max that lets NaN win
-  return (a != a || a > b) ? a : b;
-}
-
-// Per arithmetic type: the magnitude type of norms, |x|, and the difference
-// and sum used by the defect's stencil and final subtraction (exact
-// renormalisation for double-float, where these operands nearly cancel).
-template <class R>
-struct Arith;
-template <>
-struct Arith<double> {
-  using Mag = double;
-  static __device__ __forceinline__ double mag(double x) { return fabs(x); }
-  static __device__ __forceinline__ double sub(double a, double b) { return a - b; }
-  static __device__ __forceinline__ double add(double a, double b) { return a + b; }
-};
-template <>
-struct Arith<float> {
-  using Mag = float;
-  static __device__ __forceinline__ float mag(float x) { return fabsf(x); }
-  static __device__ __forceinline__ float sub(float a, float b) { return a - b; }
-  static __device__ __forceinline__ float add(float a, float b) { return a + b; }
-};
-template <>
-struct Arith<dd> {
-  using Mag = float;
-  static __device__ __forceinline__ float mag(dd x) { return dd_abs_hi(x); }
-  static __device__ __forceinline__ dd sub(dd a, dd b) { return dd_add_accurate(a, -b); }
-  static __device__ __forceinline__ dd add(dd a, dd b) { return dd_add_accurate(a, b); }
-};
-
-// sum over the 2d neighbour directions of (u_p - u_q), u_q = 0 outside the grid:
-// equals (2d u_p - sum_q u_q), the 5-point (3-point) stencil times h^2, with
-// every difference formed before the sum so that smooth u loses no digits.
-template <class R>
-__device__ __forceinline__ R stencil_differences(const R* __restrict__ u, R up, int d, int n, int i,
-                                                 int j, size_t pM, int M, int m) {
-  using A = Arith<R>;
-  R s = i > 0 ? A::sub(up, u[pM - M + m]) : up;
-  s = A::add(s, i < n - 1 ? A::sub(up, u[pM + M + m]) : up);
-  if (d == 2) {
-    const size_t nM = (size_t)n * M;
-    s = A::add(s, j > 0 ? A::sub(up, u[pM - nM + m]) : up);
-    s = A::add(s, j < n - 1 ? A::sub(up, u[pM + nM + m]) : up);
-  }
-  return s;
-}
-
-// ---------------------------------------------------------------------------------
-// smoother: one colour half-sweep (Sec. 3 Eq. red-black, Sec. 6 Eq. red-black_2d)
-// ---------------------------------------------------------------------------------
-
-template <class R, int BLOCK>
-__global__ void __launch_bounds__(BLOCK)
-    k_sweep(const R* __restrict__ f, R* __restrict__ u, R* __restrict__ delta,
-            const Cx<R>* __restrict__ spec, const Cx<R>* __restrict__ tw, int d, int n, int M,
-            int logL, int par, int all_points, R hinv2, int npts, int npairs, size_t fstride,
-            size_t sstride) {
-  extern __shared__ unsigned char smem_raw[];
-  // instance of a batch: blockIdx.y
-  f += blockIdx.y * fstride;
-  u += blockIdx.y * fstride;
-  if (delta != nullptr) delta += blockIdx.y * fstride;
-  spec += blockIdx.y * sstride;
-  Cx<R>* smem = reinterpret_cast<Cx<R>*>(smem_raw);
-  const FftShape sh(logL);
-  const int TL = sh.L8;
-  const int g = threadIdx.x / TL;
-  const int t = threadIdx.x - g * TL;
-  const int groups = BLOCK / TL;
-  const int pair = blockIdx.x * groups + g;
-  Cx<R>* buf = smem + g * padded_len(sh.L);
-
-  const bool valid = pair < npairs;
-  const int kA = 2 * pair, kB = 2 * pair + 1;
-  const bool hasB = valid && kB < npts;
-  int iA = 0, jA = 0, iB = 0, jB = 0, pA = 0, pB = 0;
-  if (valid) {
-    if (all_points) {
-      pA = kA;
-      pB = kB;
-    } else {
-      pA = colour_point(kA, d, n, par, iA, jA);
-      if (hasB) pB = colour_point(kB, d, n, par, iB, jB);
-    }
-  }
-  const size_t pAM = (size_t)pA * M, pBM = (size_t)pB * M;
-
-  auto load = [&](int m) -> Cx<R> {
-    Cx<R> b{R(0), R(0)};
-    if (valid) {
-      b.x = f[pAM + m];
-      if (!all_points) b.x += hinv2 * neighbour_sum(u, d, n, iA, jA, pAM, M, m);
-      if (hasB) {
-        b.y = f[pBM + m];
-        if (!all_points) b.y += hinv2 * neighbour_sum(u, d, n, iB, jB, pBM, M, m);
-      }
-    }
-    return b;
-  };
-  Cx<R> v[8];
-  fft_forward(buf, t, sh, tw, load, v);
-#pragma unroll
-  for (int q = 0; q < 8; ++q) v[q] = cmul(v[q], spec[8 * t + q]);
-  auto store = [&](int m, Cx<R> y) {
-    if (valid) {
-      if (delta != nullptr) delta[pAM + m] = y.x - u[pAM + m];
-      u[pAM + m] = y.x;
-      if (hasB) {
-        if (delta != nullptr) delta[pBM + m] = y.y - u[pBM + m];
-        u[pBM + m] = y.y;
-      }
-    }
-  };
-  fft_inverse(buf, t, sh, tw, v, store);
-}
+void add_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 // Line-wise kernels: a group of TPL threads owns one time line (TPL = min(128,
 // M/2), 128 / TPL lines per 128-thread block); each thread handles two
@@ -273,86 +95,6 @@ __global__ void __launch_bounds__(128)
     }
   }
   if (norm_bits != nullptr) block_absmax<R>(amax, norm_bits);
-}
-
-// ---------------------------------------------------------------------------------
-// defect r = f - (T_M (x) I + A_h) u  (Algorithm 1; Sec. 5 circulant-embedding matvec)
-// ---------------------------------------------------------------------------------
-
-template <class R, class RO, int BLOCK>
-__global__ void __launch_bounds__(BLOCK)
-    k_defect(const R* __restrict__ u, const R* __restrict__ f, RO* __restrict__ r,
-             const Cx<R>* __restrict__ tspec, const Cx<R>* __restrict__ tw, int d, int n, int M,
-             int logL, R hinv2, int npts, int npairs, unsigned long long* __restrict__ norm_bits,
-             size_t fstride, size_t sstride) {
-  extern __shared__ unsigned char smem_raw[];
-  u += blockIdx.y * fstride;
-  f += blockIdx.y * fstride;
-  r += blockIdx.y * fstride;
-  tspec += blockIdx.y * sstride;
-  if (norm_bits != nullptr) norm_bits += blockIdx.y;
-  __shared__ double red[BLOCK / 32];
-  Cx<R>* smem = reinterpret_cast<Cx<R>*>(smem_raw);
-  const FftShape sh(logL);
-  const int TL = sh.L8;
-  const int g = threadIdx.x / TL;
-  const int t = threadIdx.x - g * TL;
-  const int groups = BLOCK / TL;
-  const int pair = blockIdx.x * groups + g;
-  Cx<R>* buf = smem + g * padded_len(sh.L);
-
-  const bool valid = pair < npairs;
-  const int pA = 2 * pair, pB = 2 * pair + 1;
-  const bool hasB = valid && pB < npts;
-  const size_t pAM = (size_t)pA * M, pBM = (size_t)pB * M;
-  const int iA = d == 1 ? pA : pA % n, jA = d == 1 ? 0 : pA / n;
-  const int iB = d == 1 ? pB : pB % n, jB = d == 1 ? 0 : pB / n;
-  auto load = [&](int m) -> Cx<R> {
-    Cx<R> x{R(0), R(0)};
-    if (valid) {
-      x.x = u[pAM + m];
-      if (hasB) x.y = u[pBM + m];
-    }
-    return x;
-  };
-  Cx<R> v[8];
-  fft_forward(buf, t, sh, tw, load, v);
-#pragma unroll
-  for (int q = 0; q < 8; ++q) v[q] = cmul(v[q], tspec[8 * t + q]);
-  using A = Arith<R>;
-  typename A::Mag amax = 0;
-  // r = f - (T_M u) - h^-2 sum_q (u_p - u_q)
-  auto store = [&](int m, Cx<R> y) {
-    if (valid) {
-      const R ua = u[pAM + m];
-      const R ra = A::sub(A::sub(f[pAM + m], y.x),
-                          hinv2 * stencil_differences(u, ua, d, n, iA, jA, pAM, M, m));
-      r[pAM + m] = RO(ra);
-      amax = absmax_nan(A::mag(ra), amax);
-      if (hasB) {
-        const R ub = u[pBM + m];
-        const R rb = A::sub(A::sub(f[pBM + m], y.y),
-                            hinv2 * stencil_differences(u, ub, d, n, iB, jB, pBM, M, m));
-        r[pBM + m] = RO(rb);
-        amax = absmax_nan(A::mag(rb), amax);
-      }
-    }
-  };
-  fft_inverse(buf, t, sh, tw, v, store);
-
-  if (norm_bits != nullptr) {
-    double a = (double)amax;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) a = absmax_nan(__shfl_xor_sync(0xffffffffu, a, o), a);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      a = threadIdx.x < BLOCK / 32 ? red[threadIdx.x] : 0.0;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) a = absmax_nan(__shfl_xor_sync(0xffffffffu, a, o), a);
-      if (threadIdx.x == 0) atomic_max_nonneg(norm_bits, a);
-    }
-  }
 }
 
 // ---------------------------------------------------------------------------------
@@ -685,7 +427,7 @@ __global__ void __launch_bounds__(BLOCK)
   const int groups = BLOCK / TL;
   const int line = blockIdx.x * groups + g;
   const bool valid = line < count;
-  Cx<double>* buf = smem + g * padded_len(sh.L);
+  Cx<double>* buf = smem + g * Pad<double>::len(sh.L);
   const double* x = lines + (size_t)(valid ? line : 0) * M;
   auto load = [&](int m) -> Cx<double> { return Cx<double>{valid ? x[m] : 0.0, 0.0}; };
   Cx<double> v[8];
@@ -709,100 +451,7 @@ __global__ void k_round_cx(Cx<float>* __restrict__ dst, const Cx<double>* __rest
 // launchers
 // ---------------------------------------------------------------------------------
 
-namespace {
 
-template <class K>
-cudaError_t prepare_smem(K kernel, size_t smem) {
-  if (smem > 48 * 1024) {
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  }
-  return cudaSuccess;
-}
-
-inline unsigned elementwise_grid(size_t total) {
-  size_t blocks = (total + 255) / 256;
-  const size_t cap = 152 * 16;
-  return (unsigned)(blocks < 1 ? 1 : (blocks > cap ? cap : blocks));
-}
-
-}  // namespace
-
-template <class R>
-cudaError_t launch_sweep(const R* f, R* u, R* delta, const Cx<R>* spec, size_t spec_stride,
-                         const Cx<R>* tw, const LevelShape& ls, int par, bool all_points, R hinv2,
-                         cudaStream_t s) {
-  const int d = ls.d, n = ls.n, M = ls.M;
-  const int L = 2 * M, logL = ilog2(L);
-  const int npts = all_points ? (d == 1 ? n : n * n) : colour_count(d, n, par);
-  const int npairs = (npts + 1) / 2;
-  if (npairs == 0 || ls.batch == 0) return cudaSuccess;
-  const size_t fstride = ls.field_stride();
-  const int block = block_threads(L);
-  const int groups = block / (L / 8);
-  const size_t smem = (size_t)groups * padded_len(L) * sizeof(Cx<R>);
-  const dim3 grid((unsigned)((npairs + groups - 1) / groups), (unsigned)ls.batch);
-  cudaError_t e;
-  switch (block) {
-    case 256:
-      e = prepare_smem(k_sweep<R, 256>, smem);
-      if (e != cudaSuccess) return e;
-      k_sweep<R, 256><<<grid, 256, smem, s>>>(f, u, delta, spec, tw, d, n, M, logL, par, all_points,
-                                              hinv2, npts, npairs, fstride, spec_stride);
-      break;
-    case 512:
-      e = prepare_smem(k_sweep<R, 512>, smem);
-      if (e != cudaSuccess) return e;
-      k_sweep<R, 512><<<grid, 512, smem, s>>>(f, u, delta, spec, tw, d, n, M, logL, par, all_points,
-                                              hinv2, npts, npairs, fstride, spec_stride);
-      break;
-    default:
-      e = prepare_smem(k_sweep<R, 1024>, smem);
-      if (e != cudaSuccess) return e;
-      k_sweep<R, 1024><<<grid, 1024, smem, s>>>(f, u, delta, spec, tw, d, n, M, logL, par,
-                                                all_points, hinv2, npts, npairs, fstride,
-                                                spec_stride);
-      break;
-  }
-  return counted(cudaGetLastError());
-}
-
-template <class R, class RO>
-cudaError_t launch_defect(const R* u, const R* f, RO* r, const Cx<R>* tspec, size_t spec_stride,
-                          const Cx<R>* tw, const LevelShape& ls, R hinv2,
-                          unsigned long long* norm_bits, cudaStream_t s) {
-  const int d = ls.d, n = ls.n, M = ls.M;
-  const int L = 2 * M, logL = ilog2(L);
-  const int npts = d == 1 ? n : n * n;
-  const int npairs = (npts + 1) / 2;
-  if (ls.batch == 0) return cudaSuccess;
-  const size_t fstride = ls.field_stride();
-  const int block = block_threads(L);
-  const int groups = block / (L / 8);
-  const size_t smem = (size_t)groups * padded_len(L) * sizeof(Cx<R>);
-  const dim3 grid((unsigned)((npairs + groups - 1) / groups), (unsigned)ls.batch);
-  cudaError_t e;
-  switch (block) {
-    case 256:
-      e = prepare_smem(k_defect<R, RO, 256>, smem);
-      if (e != cudaSuccess) return e;
-      k_defect<R, RO, 256><<<grid, 256, smem, s>>>(u, f, r, tspec, tw, d, n, M, logL, hinv2, npts,
-                                                   npairs, norm_bits, fstride, spec_stride);
-      break;
-    case 512:
-      e = prepare_smem(k_defect<R, RO, 512>, smem);
-      if (e != cudaSuccess) return e;
-      k_defect<R, RO, 512><<<grid, 512, smem, s>>>(u, f, r, tspec, tw, d, n, M, logL, hinv2, npts,
-                                                   npairs, norm_bits, fstride, spec_stride);
-      break;
-    default:
-      e = prepare_smem(k_defect<R, RO, 1024>, smem);
-      if (e != cudaSuccess) return e;
-      k_defect<R, RO, 1024><<<grid, 1024, smem, s>>>(u, f, r, tspec, tw, d, n, M, logL, hinv2,
-                                                     npts, npairs, norm_bits, fstride, spec_stride);
-      break;
-  }
-  return counted(cudaGetLastError());
-}
 
 // Launch geometry of the line-wise kernels: log2 of the threads per line and
 // the number of 128-thread blocks for `lines` lines.
@@ -915,7 +564,7 @@ cudaError_t launch_spectra(Cx<double>* spec, const double* lines, int count, int
   const int L = 2 * M, logL = ilog2(L);
   const int block = block_threads(L);
   const int groups = block / (L / 8);
-  const size_t smem = (size_t)groups * padded_len(L) * sizeof(Cx<double>);
+  const size_t smem = (size_t)groups * Pad<double>::len(L) * sizeof(Cx<double>);
   const unsigned grid = (unsigned)((count + groups - 1) / groups);
   cudaError_t e;
   switch (block) {
@@ -945,8 +594,6 @@ cudaError_t launch_round_cx(Cx<float>* dst, const Cx<double>* src, size_t count,
 
 // explicit instantiations
 #define MGWR_INST_R(R)                                                                         \
-  template cudaError_t launch_sweep<R>(const R*, R*, R*, const Cx<R>*, size_t, const Cx<R>*,  \
-                                       const LevelShape&, int, bool, R, cudaStream_t);         \
   template cudaError_t launch_defect_from_delta<R>(const R*, R*, const LevelShape&, int, R,    \
                                                    unsigned long long*, cudaStream_t);         \
   template cudaError_t launch_restrict<R>(const R*, R*, R*, const LevelShape&, cudaStream_t);  \
@@ -954,20 +601,6 @@ cudaError_t launch_round_cx(Cx<float>* dst, const Cx<double>* src, size_t count,
 MGWR_INST_R(double)
 MGWR_INST_R(float)
 #undef MGWR_INST_R
-template cudaError_t launch_defect<double, double>(const double*, const double*, double*,
-                                                   const Cx<double>*, size_t, const Cx<double>*,
-                                                   const LevelShape&, double, unsigned long long*,
-                                                   cudaStream_t);
-template cudaError_t launch_defect<double, float>(const double*, const double*, float*,
-                                                  const Cx<double>*, size_t, const Cx<double>*,
-                                                  const LevelShape&, double, unsigned long long*,
-                                                  cudaStream_t);
-template cudaError_t launch_defect<dd, float>(const dd*, const dd*, float*, const Cx<dd>*, size_t,
-                                              const Cx<dd>*, const LevelShape&, dd,
-                                              unsigned long long*, cudaStream_t);
-template cudaError_t launch_defect<float, float>(const float*, const float*, float*,
-                                                 const Cx<float>*, size_t, const Cx<float>*,
-                                                 const LevelShape&, float, unsigned long long*,
-                                                 cudaStream_t);
+
 
 }  // namespace mgwr

@@ -56,6 +56,10 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # chain: 1.20 TFLOP/s at 1995 MHz on 152 SMs); peak at the maximum clock.
 FP64_FMA_PER_CLK_PER_SM = 2
 SMS = 152
+# DRAM bytes (read + write) per smoothed line of k_sweep<double> from an ncu
+# capture of the finest-level half-sweep of the default workload (773.2 MB for
+# 32,513 lines of 1024 doubles; profiles/k_sweep_fp64_2d_255x255_M1024.md).
+SWEEP64_DRAM_BYTES_PER_LINE_M1024 = 23781.0
 
 
 def parse():
@@ -171,9 +175,13 @@ def roofline_from_profile(prof: dict, d: int, M: int, pk: dict) -> dict:
         word = 8
         bytes_alg = p["lines"] * 3 * word * M  # f, one line of the other colour, the output
         hbm = bytes_alg / (p["ms"] * 1e-3) / 1e9
+        lines_per_launch = p["lines"] / max(p["launches"], 1)
+        traffic = (SWEEP64_DRAM_BYTES_PER_LINE_M1024 * lines_per_launch
+                   if dom == "sweep64" and M == 1024 else None)
         return {"kernel": f"k_sweep<double>" if dom == "sweep64" else "k_defect<double>",
                 "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": traffic,
+                "traffic_note": "ncu dram bytes per line x lines per launch" if traffic else None,
                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x max SM clock",
                 "launches": p["launches"], "avg_launch_ms": p["ms"] / max(p["launches"], 1),
                 "hbm_view": {"achieved_gbs": hbm, "peak_gbs": pk.get("hbm_gbs"),

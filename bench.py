@@ -72,6 +72,7 @@ def parse():
     p.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     p.add_argument("--requests", type=int, default=200, help="c4: first R requests of the stream")
     p.add_argument("--slots", type=int, default=4, help="c4: server slots")
+    p.add_argument("--inner", type=int, default=None, help="mixed modes: FP32 cycles per outer defect")
     p.add_argument("--alpha", type=float, default=ALPHA)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
@@ -372,6 +373,8 @@ def main():
     prec_code = {"fp64": mgwr.MGWR_FP64, "mixed": mgwr.MGWR_MIXED, "mixed_dd": mgwr.MGWR_MIXED_DD}
     if precision != "fp64":
         s.set_precision(prec_code[precision])
+        if args.inner:
+            s.set_inner_cycles(args.inner)
 
     def step():
         s.set_rhs_dev(f_dev.data_ptr())

@@ -314,8 +314,9 @@ int defect(mgwr_t h, Hier<R>& H, int l, unsigned long long* norm_bits) {
 template <class R>
 int defect_from_delta(mgwr_t h, Hier<R>& H, int l, unsigned long long* norm_bits) {
   const int pm = prof_begin(h, MGWR_K_DEFECT_DELTA, (double)(points(h, l) * h->B));
-  MGWR_CK(h, mgwr::launch_defect_from_delta<R>(H.dl[l], H.r[l], shape(h, l), parity(h, MGWR_RED),
-                                                R(h->hinv2[l]), norm_bits, h->stream));
+  MGWR_CK(h, mgwr::launch_defect_from_delta<R>(H.dl[l], H.r[l], H.zero, shape(h, l),
+                                                parity(h, MGWR_RED), R(h->hinv2[l]), norm_bits,
+                                                h->stream));
   prof_end(h, pm);
   H.rs[l] = R_CURRENT;
   return MGWR_OK;

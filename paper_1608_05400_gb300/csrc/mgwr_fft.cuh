@@ -192,17 +192,24 @@ __device__ __forceinline__ void middle_stage(Cx<R>* buf, int t, const SH& sh, in
   for (int q = 0; q < 8; ++q) buf[P::idx(base + q * s)] = v[q];
 }
 
-// Forward transform of one zero-padded line pair.  `load(m)` returns the pair's
-// input at time index m < M (called for m = t + q L/8, q < 4).  On return the
+// Forward transform of one line pair.  `load(m)` returns the pair's input at
+// time index m (called for m = t + q L/8, q < 4: the upper half of the line is
+// zero padding; with FULL, q < 8: every position carries data).  On return the
 // thread holds, in v, the transform values at spectral positions 8t .. 8t+7.
 // Every thread of the block must call this (it synchronises the block).
-template <class R, class SH, class Load>
+template <class R, class SH, class Load, bool FULL = false>
 __device__ __forceinline__ void fft_forward(Cx<R>* buf, int t, const SH& sh,
                                             const Cx<R>* __restrict__ tw, Load load, Cx<R> (&v)[8]) {
   using P = Pad<R>;
+  if constexpr (FULL) {
 #pragma unroll
-  for (int q = 0; q < 4; ++q) v[q] = load(t + q * sh.L8);
-  dft8_half_input(v);
+    for (int q = 0; q < 8; ++q) v[q] = load(t + q * sh.L8);
+    dft8<false>(v);
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = load(t + q * sh.L8);
+    dft8_half_input(v);
+  }
   if (sh.logL == 3) return;  // single stage: thread 0 holds positions 0..7
   twiddle_mul<false>(v, tw, t);
 #pragma unroll

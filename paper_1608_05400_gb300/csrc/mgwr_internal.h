@@ -48,8 +48,9 @@ cudaError_t launch_sweep(const R* f, R* u, R* delta, const Cx<R>* spec, size_t s
 // black points, r = hinv2 * sum of neighbour deltas on the red points
 // (parity red_par); |r|_inf of instance b folded into norm_bits[b].
 template <class R>
-cudaError_t launch_defect_from_delta(const R* delta, R* r, const LevelShape& ls, int red_par,
-                                     R hinv2, unsigned long long* norm_bits, cudaStream_t s);
+cudaError_t launch_defect_from_delta(const R* delta, R* r, const R* zero, const LevelShape& ls,
+                                     int red_par, R hinv2, unsigned long long* norm_bits,
+                                     cudaStream_t s);
 
 // r = f - T_M u - A_h u for all points; |r|_inf of instance b folded into
 // norm_bits[b] (bit pattern of a non-negative double, atomicMax) when non-null.

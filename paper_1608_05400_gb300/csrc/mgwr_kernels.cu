@@ -57,8 +57,8 @@ __device__ __forceinline__ void block_absmax(double amax, unsigned long long* no
 // h^-2 * sum over its black neighbours of (new - old) = h^-2 sum delta.
 template <class R>
 __global__ void __launch_bounds__(128)
-    k_defect_from_delta(const R* __restrict__ delta, R* __restrict__ r, int d, int n, int M,
-                        int log_tpl, int npts, int red_par, R hinv2,
+    k_defect_from_delta(const R* __restrict__ delta, R* __restrict__ r, const R* __restrict__ zero,
+                        int d, int n, int M, int log_tpl, int npts, int red_par, R hinv2,
                         unsigned long long* __restrict__ norm_bits, size_t fstride) {
   const LineMap lm(log_tpl);
   delta += blockIdx.y * fstride;
@@ -76,18 +76,20 @@ __global__ void __launch_bounds__(128)
         rp[m + 1] = R(0);
       }
     } else {
-      // neighbour lines; out-of-grid neighbours read the line itself with weight 0
+      // neighbour lines, the zero line outside the grid; four reads, three
+      // additions and one product per value
       const size_t pM = (size_t)p * M, nM = (size_t)n * M;
-      const R* w = delta + (i > 0 ? pM - M : pM);
-      const R* e = delta + (i < n - 1 ? pM + M : pM);
-      const R* so = delta + (d == 2 && j > 0 ? pM - nM : pM);
-      const R* no = delta + (d == 2 && j < n - 1 ? pM + nM : pM);
-      const R cw = i > 0 ? hinv2 : R(0), ce = i < n - 1 ? hinv2 : R(0);
-      const R cs = d == 2 && j > 0 ? hinv2 : R(0), cn = d == 2 && j < n - 1 ? hinv2 : R(0);
+      const R* w = i > 0 ? delta + pM - M : zero;
+      const R* e = i < n - 1 ? delta + pM + M : zero;
+      const R* so = d == 2 && j > 0 ? delta + pM - nM : zero;
+      const R* no = d == 2 && j < n - 1 ? delta + pM + nM : zero;
+      const bool four = d == 2;
       for (int m = lm.m0; m < M; m += lm.step) {
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
-          const R v = cw * w[m + k] + ce * e[m + k] + cs * so[m + k] + cn * no[m + k];
+          R sum = w[m + k] + e[m + k];
+          if (four) sum = sum + (so[m + k] + no[m + k]);
+          const R v = hinv2 * sum;
           rp[m + k] = v;
           amax = absmax_nan((double)fabs(v), amax);
         }
@@ -146,22 +148,29 @@ __global__ void __launch_bounds__(128)
 }
 
 // 1-D interpolation taps of fine index i from the coarse grid (nc points):
-// fine 2J+1 takes coarse J; fine 2J takes the mean of coarse J-1 and J; coarse
-// indices outside the grid get weight 0 (and point at a valid line).
+// fine 2J+1 takes coarse J (one tap, weight 1); fine 2J takes the mean of
+// coarse J-1 and J (two taps, weight 1/2), or half of the one inside the grid
+// at the ends.  All taps of a point share one weight, so the interpolated
+// value is that weight times a plain sum of one, two or four coarse lines.
 struct Taps {
-  int i0, i1;
-  float w0, w1;
+  int i0, i1, count;
+  bool half;
   __device__ __forceinline__ Taps(int i, int nc) {
     if (i & 1) {
       i0 = i1 = (i - 1) >> 1;
-      w0 = 1.f;
-      w1 = 0.f;
+      count = 1;
+      half = false;
     } else {
       const int J = i >> 1;
-      i0 = J - 1 >= 0 ? J - 1 : 0;
-      w0 = J - 1 >= 0 ? 0.5f : 0.f;
-      i1 = J < nc ? J : nc - 1;
-      w1 = J < nc ? 0.5f : 0.f;
+      half = true;
+      if (J - 1 >= 0 && J < nc) {
+        i0 = J - 1;
+        i1 = J;
+        count = 2;
+      } else {
+        i0 = i1 = J - 1 >= 0 ? J - 1 : J;
+        count = 1;
+      }
     }
   }
 };
@@ -177,26 +186,29 @@ __global__ void __launch_bounds__(128)
   const int nc = (n - 1) / 2;
   const int p = lm.line;
   R* up = u + (size_t)p * M;
-  if (d == 1) {
-    const Taps tx(p, nc);
-    const R* a = uc + (size_t)tx.i0 * M;
-    const R* b = uc + (size_t)tx.i1 * M;
-    const R wa = R(tx.w0), wb = R(tx.w1);
-    for (int m = lm.m0; m < M; m += lm.step) {
+  const Taps tx(d == 1 ? p : p % n, nc);
+  const Taps ty(d == 1 ? 1 : p / n, nc);  // 1-D: a single tap of weight 1 in y
+  const size_t row0 = d == 1 ? 0 : (size_t)ty.i0 * nc, row1 = d == 1 ? 0 : (size_t)ty.i1 * nc;
+  const R* a = uc + ((size_t)tx.i0 + row0) * M;
+  const R* b = uc + ((size_t)tx.i1 + row0) * M;
+  const R* c = uc + ((size_t)tx.i0 + row1) * M;
+  const R* e = uc + ((size_t)tx.i1 + row1) * M;
+  const R w = R((tx.half ? 0.5f : 1.f) * (ty.half ? 0.5f : 1.f));
+  const int taps = tx.count * ty.count;  // 1, 2 (in x or in y) or 4
+  const bool two_y = ty.count == 2;
+  for (int m = lm.m0; m < M; m += lm.step) {
 #pragma unroll
-      for (int k = 0; k < 2; ++k) up[m + k] += wa * a[m + k] + wb * b[m + k];
-    }
-  } else {
-    const Taps tx(p % n, nc), ty(p / n, nc);
-    const R* a = uc + ((size_t)tx.i0 + (size_t)ty.i0 * nc) * M;
-    const R* b = uc + ((size_t)tx.i1 + (size_t)ty.i0 * nc) * M;
-    const R* c = uc + ((size_t)tx.i0 + (size_t)ty.i1 * nc) * M;
-    const R* e = uc + ((size_t)tx.i1 + (size_t)ty.i1 * nc) * M;
-    const R wa = R(tx.w0 * ty.w0), wb = R(tx.w1 * ty.w0), wc = R(tx.w0 * ty.w1), we = R(tx.w1 * ty.w1);
-    for (int m = lm.m0; m < M; m += lm.step) {
-#pragma unroll
-      for (int k = 0; k < 2; ++k)
-        up[m + k] += wa * a[m + k] + wb * b[m + k] + wc * c[m + k] + we * e[m + k];
+    for (int k = 0; k < 2; ++k) {
+      const int q = m + k;
+      R sum;
+      if (taps == 1) {
+        sum = a[q];
+      } else if (taps == 4) {
+        sum = (a[q] + b[q]) + (c[q] + e[q]);
+      } else {
+        sum = a[q] + (two_y ? c[q] : b[q]);
+      }
+      up[q] = w == R(1) ? up[q] + sum : up[q] + w * sum;
     }
   }
 }
@@ -463,15 +475,17 @@ inline void line_grid(int M, int lines, int* log_tpl, unsigned* blocks) {
 }
 
 template <class R>
-cudaError_t launch_defect_from_delta(const R* delta, R* r, const LevelShape& ls, int red_par,
-                                     R hinv2, unsigned long long* norm_bits, cudaStream_t s) {
+cudaError_t launch_defect_from_delta(const R* delta, R* r, const R* zero, const LevelShape& ls,
+                                     int red_par, R hinv2, unsigned long long* norm_bits,
+                                     cudaStream_t s) {
   const int npts = ls.d == 1 ? ls.n : ls.n * ls.n;
   if (ls.batch == 0) return cudaSuccess;
   int log_tpl;
   unsigned blocks;
   line_grid(ls.M, npts, &log_tpl, &blocks);
   k_defect_from_delta<R><<<dim3(blocks, ls.batch), 128, 0, s>>>(
-      delta, r, ls.d, ls.n, ls.M, log_tpl, npts, red_par, hinv2, norm_bits, ls.field_stride());
+      delta, r, zero, ls.d, ls.n, ls.M, log_tpl, npts, red_par, hinv2, norm_bits,
+      ls.field_stride());
   return counted(cudaGetLastError());
 }
 
@@ -594,8 +608,8 @@ cudaError_t launch_round_cx(Cx<float>* dst, const Cx<double>* src, size_t count,
 
 // explicit instantiations
 #define MGWR_INST_R(R)                                                                         \
-  template cudaError_t launch_defect_from_delta<R>(const R*, R*, const LevelShape&, int, R,    \
-                                                   unsigned long long*, cudaStream_t);         \
+  template cudaError_t launch_defect_from_delta<R>(const R*, R*, const R*, const LevelShape&,  \
+                                                   int, R, unsigned long long*, cudaStream_t); \
   template cudaError_t launch_restrict<R>(const R*, R*, R*, const LevelShape&, cudaStream_t);  \
   template cudaError_t launch_prolong<R>(R*, const R*, const LevelShape&, cudaStream_t);
 MGWR_INST_R(double)

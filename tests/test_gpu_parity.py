@@ -309,6 +309,21 @@ def test_graph_replayed_solve_equals_direct_launches(precision, cyc):
     assert out[0][1:] == out[1][1:]
 
 
+def test_colour_order_switch_on_one_handle():
+    # the black-change field keeps values from the other colour after a switch;
+    # defects computed from it must still ignore red lines and the boundary
+    d, n, M = 1, 63, 64
+    f = inputs.Problem(d, n, M, 1.0, 0.5, "t2").rhs()
+    ref = direct.time_stepping(d, n, M, 1.0, 0.5, f)
+    with G.Solver(d, n, M, 1.0, 0.5) as s:
+        for order in (G.MGWR_ORDER_TEXT, G.MGWR_ORDER_TABLE, G.MGWR_ORDER_TEXT):
+            s.set_order(order)
+            s.set_rhs(f)
+            st = s.solve(1, 1, 1, tol=1e-12, max_cycles=40, allow_noconv=True)
+            assert st.relres <= 2e-12
+            assert rel(s.solution(), ref) <= 1e-11
+
+
 def test_paper_table_1d_iterations_on_gpu():
     # Table table_it_1d, V(0,1), delta = 0.4, 128 x 128 grid: 7 cycles (table order)
     import math

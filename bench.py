@@ -9,10 +9,12 @@ FP64 field is 533 MB, larger than the 129 MB L2, so no flush is needed
 between steps.  Other workloads (--workload): c1 (1-D 63 points, M = 64),
 c3 (2-D 511 x 511, M = 4096, u = t^alpha sin sin, mixed to 1e-8) and c5a
 (4096 independent 2-D 63 x 63, M = 256 solves with alpha ~ U[0.1, 0.9] in one
-batched handle, mixed to 1e-8).
+batched handle, mixed to 1e-8), c5b (1-D 4095 points, M = 65536, alpha = 0.2,
+u = t^alpha sin, mixed to 1e-8; --precision fp64 for the FP64 form) and c4
+(the served request stream).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
-                  [--workload c2|c1|c3|c5a]
+                  [--workload c2|c1|c3|c5a|c5b|c4]
   python bench.py --impl reference ...   (the CPU oracle on the host cores)
 
 Prints one JSON line.  Multi-GPU runs (torchrun, one rank per GPU) are
@@ -48,8 +50,14 @@ WORKLOADS = {
            "2-D MGWR 511x511 interior, M=4096, u=t^alpha sin(pi x) sin(pi y)"),
     "c5a": (2, 63, 256, 4096, "t2", 1e-8, "mixed_dd",
             "4096 independent 2-D 63x63, M=256 solves, alpha~U[0.1,0.9] (seed 1608), one batched handle"),
+    "c5b": (1, 4095, 65536, 1, "talpha", 1e-8, "mixed_dd",
+            "1-D MGWR 4095 interior points, M=65536 (long memory), u=t^alpha sin(pi x)"),
     "c4": (0, 0, 0, 0, "", 1e-8, "mixed_dd", "served stream"),
 }
+# alpha of a workload when --alpha is not given
+WORKLOAD_ALPHA = {"c5b": 0.2}
+# oracle time steps in the CPU-baseline sample (about 10-30 s of host work)
+ORACLE_SAMPLE_STEPS = {"c2": 256, "c5b": 2048}
 UNIT = "unknowns/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP64 issue rate of a GB300 SM: 2 FP64 FMA per clock (measured with an FMA
@@ -73,7 +81,7 @@ def parse():
     p.add_argument("--requests", type=int, default=200, help="c4: first R requests of the stream")
     p.add_argument("--slots", type=int, default=4, help="c4: server slots")
     p.add_argument("--inner", type=int, default=None, help="mixed modes: FP32 cycles per outer defect")
-    p.add_argument("--alpha", type=float, default=ALPHA)
+    p.add_argument("--alpha", type=float, default=None)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     return p.parse_args()
@@ -150,18 +158,27 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def conv_flops_per_line(Mv: int) -> float:
+    """Algorithmic flops of one line's causal FFT convolution: half of a line
+    pair's complex work.  Up to M = 4096 one transform pair of length L = 2M
+    (5 L log2 L each) and the spectrum product (6 L); beyond, P = M/4096 blocks
+    with transforms of length 8192 and P(P+1)/2 block products accumulated
+    (8 flops per value)."""
+    if Mv <= 4096:
+        L = 2 * Mv
+        return 0.5 * (2 * 5 * L * math.log2(L) + 6 * L)
+    Lb, P = 8192, Mv // 4096
+    return 0.5 * (2 * P * 5 * Lb * math.log2(Lb) + 8 * Lb * P * (P + 1) / 2)
+
+
 def sweep_flops_per_line(d: int, Mv: int) -> float:
-    """Algorithmic FP64 flops of one smoothed time line: half a line pair's
-    complex FFT convolution of length L = 2M (5 L log2 L per transform, forward
-    and inverse, plus 6 L for the spectrum product) and the stencil gather
-    (2d adds, one multiply, one add per time value)."""
-    L = 2 * Mv
-    return 0.5 * (2 * 5 * L * math.log2(L) + 6 * L) + (2 * d + 2) * Mv
+    """Convolution plus the stencil gather (2d adds, one multiply, one add per
+    time value) of one smoothed time line."""
+    return conv_flops_per_line(Mv) + (2 * d + 2) * Mv
 
 
 def defect_flops_per_line(d: int, Mv: int) -> float:
-    L = 2 * Mv
-    return 0.5 * (2 * 5 * L * math.log2(L) + 6 * L) + (2 * d + 4) * Mv
+    return conv_flops_per_line(Mv) + (2 * d + 4) * Mv
 
 
 def roofline_from_profile(prof: dict, d: int, M: int, pk: dict) -> dict:
@@ -179,7 +196,10 @@ def roofline_from_profile(prof: dict, d: int, M: int, pk: dict) -> dict:
         lines_per_launch = p["lines"] / max(p["launches"], 1)
         traffic = (SWEEP64_DRAM_BYTES_PER_LINE_M1024 * lines_per_launch
                    if dom == "sweep64" and M == 1024 else None)
-        return {"kernel": f"k_sweep<double>" if dom == "sweep64" else "k_defect<double>",
+        long = M > 4096
+        kname = ("k_long_forward+k_long_inverse<double>" if long else "k_sweep<double>") \
+            if dom == "sweep64" else ("k_long_forward+k_long_inverse<double>" if long else "k_defect<double>")
+        return {"kernel": kname,
                 "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "traffic_note": "ncu dram bytes per line x lines per launch" if traffic else None,
@@ -197,35 +217,39 @@ def roofline_from_profile(prof: dict, d: int, M: int, pk: dict) -> dict:
             "avg_launch_ms": p["ms"] / max(p["launches"], 1)}
 
 
-def cpu_oracle_sample(steps_in_time: int = 256):
+def cpu_oracle_sample(d: int, n: int, Mv: int, alpha: float, kind: str, steps_in_time: int):
     """The CPU oracle (direct L1 time stepping) on the full grid for the first
     `steps_in_time` of the M time levels."""
     from oracle import direct
     from paper_1608_05400_gb300 import inputs
 
-    prob = inputs.Problem(D, NPTS, M, T, ALPHA, "t2")
+    prob = inputs.Problem(d, n, Mv, T, alpha, kind)
     f = prob.rhs()
     t0 = time.perf_counter()
-    direct.time_stepping(D, NPTS, M, T, ALPHA, f, steps=steps_in_time)
+    direct.time_stepping(d, n, Mv, T, alpha, f, steps=steps_in_time)
     dt = time.perf_counter() - t0
     unknowns = prob.N * steps_in_time
+    grid = f"{n}x{n}" if d == 2 else f"{n}-point"
     return {"value": unknowns / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
             "sample": f"direct L1 time stepping (sparse LU per step + history sums) on the full "
-                      f"{NPTS}x{NPTS} grid, first {steps_in_time} of {M} time levels "
+                      f"{grid} grid, first {steps_in_time} of {Mv} time levels "
                       f"({dt:.1f} s; later levels cost more: the history sum grows with the step)"}
 
 
-def cpu_baseline_leg(u: np.ndarray, alpha: float):
+def cpu_baseline_leg(u: np.ndarray, d: int, n: int, Mv: int, alpha: float, kind: str, steps: int):
     """The CPU-baseline leg: the oracle timed on a bounded sample, and the GPU
     result's error against the oracle's exact discrete solution of this
-    workload (separable source: one M x M triangular solve)."""
+    workload (separable source: one triangular solve in time)."""
     from oracle import separable
     from paper_1608_05400_gb300 import inputs
 
-    base = cpu_oracle_sample()
-    prob = inputs.Problem(D, NPTS, M, T, alpha, "t2")
-    ref = separable.solution(D, NPTS, M, T, alpha, prob.rhs_profile(), inputs.phi(D, NPTS))
-    return base, float(np.abs(u - ref).max() / np.abs(ref).max())
+    base = cpu_oracle_sample(d, n, Mv, alpha, kind, steps)
+    prob = inputs.Problem(d, n, Mv, T, alpha, kind)
+    w = separable.time_factor(d, n, Mv, T, alpha, prob.rhs_profile())
+    ph = inputs.phi(d, n)
+    # max |u - phi w| / max |phi w| row by row, without a second full field
+    err = max(float(np.abs(u[p] - ph[p] * w).max()) for p in range(u.shape[0]))
+    return base, err / float(np.abs(ph).max() * np.abs(w).max())
 
 
 def run_reference(args):
@@ -235,11 +259,11 @@ def run_reference(args):
     base = {"impl": "reference", "metric": METRIC, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True}
     for _ in range(args.warmup):
-        cpu_oracle_sample(16)
+        cpu_oracle_sample(D, NPTS, M, ALPHA, "t2", 16)
     vals = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        vals.append(cpu_oracle_sample(32))
+        vals.append(cpu_oracle_sample(D, NPTS, M, ALPHA, "t2", 32))
     dt = time.perf_counter() - t0
     v = statistics.median(x["value"] for x in vals)
     out = dict(base, value=v, ms_per_step=1e3 * dt / args.steps, scaling="weak", vs_baseline=None,
@@ -352,7 +376,7 @@ def main():
 
     d, n, Mw, batch, kind, tol, prec_default, desc = WORKLOADS[args.workload]
     precision = args.precision or prec_default
-    alpha = args.alpha
+    alpha = args.alpha if args.alpha is not None else WORKLOAD_ALPHA.get(args.workload, ALPHA)
     if batch == 1:
         prob = inputs.Problem(d, n, Mw, T, alpha, kind)
         f_host = prob.rhs()
@@ -463,8 +487,9 @@ def main():
         "clocks": clk.summary(),
         "e2e": e2e,
     }
-    if not args.no_cpu and world == 1 and args.workload == "c2":
-        out["cpu_baseline"], out["solve"]["rel_err_vs_oracle"] = cpu_baseline_leg(u, alpha)
+    if not args.no_cpu and world == 1 and args.workload in ORACLE_SAMPLE_STEPS:
+        out["cpu_baseline"], out["solve"]["rel_err_vs_oracle"] = cpu_baseline_leg(
+            u, d, n, Mw, alpha, kind, ORACLE_SAMPLE_STEPS[args.workload])
     print(json.dumps(out))
     if world > 1:
         torch.distributed.destroy_process_group()

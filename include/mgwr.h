@@ -99,13 +99,17 @@ typedef struct {
 /* ---- lifecycle --------------------------------------------------------- */
 
 /* Create a solver for (d, n, M, T, alpha).  d in {1,2}; n = 2^k - 1 with
- * 1 <= k <= 15 (1-D) or 1 <= k <= 12 (2-D); M = 2^j with 4 <= M <= 4096;
+ * 1 <= k <= 15 (1-D) or 1 <= k <= 12 (2-D); M = 2^j with 4 <= M <= 2^20;
  * T > 0 finite; 0 < alpha <= 1.  Allocates the double-precision hierarchy
  * and computes on the GPU, in FP64: the L1 Toeplitz column r_1..r_M
  * (Sec. 5 Eq. Toeplitz_matrix), the first column of (T_M + 2d/h_l^2 I)^{-1}
  * for every level l by divide and conquer (Sec. 5, smoothing procedure), and
- * their length-2M spectra (Sec. 5, circulant embedding).  Returns MGWR_E_INVAL
- * for bad arguments, MGWR_E_NOMEM if device memory runs out. */
+ * their length-2M spectra (Sec. 5, circulant embedding).  For M > 4096 every
+ * time-line convolution is partitioned into blocks of 4096 steps (transforms
+ * of length 8192; the spectra are those of the 2M/8192 kernel segments), and
+ * the handle also holds a scratch area of 16 bytes x ceil(n^d/2) x 2M per
+ * instance for the block spectra (mgwr_footprint counts it).  Returns
+ * MGWR_E_INVAL for bad arguments, MGWR_E_NOMEM if device memory runs out. */
 int mgwr_create(int d, int n, int M, double T, double alpha, mgwr_t* out);
 /* A batch of `batch` (1..65535) independent problems of the same (d, n, M),
  * instance b with final time T[b] and order alpha[b] (host arrays).  Every

@@ -1,6 +1,6 @@
 """Build the MGWR CUDA library in-tree: paper_1608_05400_gb300/libmgwr.so.
 
-Two translation units compiled in parallel with nvcc for sm_103a, linked with
+The translation units are compiled in parallel with nvcc for sm_103a, linked with
 the shared CUDA runtime.  Usage: ``python -m paper_1608_05400_gb300._build``.
 """
 from __future__ import annotations
@@ -16,7 +16,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libmgwr.so")
-SOURCES = ["mgwr_sweep.cu", "mgwr_defect_f64.cu", "mgwr_defect_f32.cu", "mgwr_defect_dd.cu", "mgwr_kernels.cu", "mgwr_api.cu", "mgwr_noalloc.cu", "mgwr_server.cu"]
+SOURCES = ["mgwr_sweep.cu", "mgwr_defect_f64.cu", "mgwr_defect_f32.cu", "mgwr_defect_dd.cu",
+           "mgwr_kernels.cu", "mgwr_long.cu", "mgwr_api.cu", "mgwr_noalloc.cu", "mgwr_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]

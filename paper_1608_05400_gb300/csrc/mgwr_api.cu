@@ -45,6 +45,7 @@ struct Hier {
 
 struct mgwr_handle {
   int d = 1, n = 1, M = 4, L = 8, nlev = 1, B = 1;
+  int Lt = 8;  // transform length of the convolution engine (twiddle table length)
   std::vector<double> alpha, T, c;  // per instance; c = tau^-alpha / Gamma(2 - alpha)
   int precision = MGWR_FP64, order = MGWR_ORDER_TEXT, inner = 2;
   std::vector<int> nl;          // interior points per dimension, level 0 = 1
@@ -65,6 +66,11 @@ struct mgwr_handle {
   mgwr::dd* zero_dd = nullptr;
   Cx<mgwr::dd>* tspec_dd = nullptr;
   Cx<mgwr::dd>* tw_dd = nullptr;
+  // partitioned-convolution scratch for M > kShortMaxM: the block spectra of
+  // the largest launch (finest level, all points), in 16-byte complex values;
+  // shared by every precision (one launch at a time on the handle's stream)
+  Cx<double>* scratch = nullptr;
+  size_t scratch_count = 0;
   unsigned long long* norm_bits = nullptr;  // device, one per instance
   unsigned long long* norm_host = nullptr;  // pinned, one per instance
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -138,6 +144,14 @@ int ensure_field(mgwr_t h, R** p, size_t count) {
 
 bool is_pow2(long long x) { return x > 0 && (x & (x - 1)) == 0; }
 
+// The handle's partitioned-convolution scratch viewed as complex values of R
+// (null for M <= kShortMaxM, where no launch uses it).
+template <class R>
+Cx<R>* scratch_for(mgwr_t h) {
+  static_assert(sizeof(Cx<R>) <= sizeof(Cx<double>), "scratch holds 16-byte values");
+  return reinterpret_cast<Cx<R>*>(h->scratch);
+}
+
 size_t points(const mgwr_handle* h, int l) {
   return h->d == 1 ? (size_t)h->nl[l] : (size_t)h->nl[l] * h->nl[l];
 }
@@ -190,10 +204,10 @@ int ensure_h32(mgwr_t h) {
   const size_t nspec = (size_t)h->B * h->nlev * h->L;
   MGWR_TRY(dev_alloc(h, &H.spec, sizeof(Cx<float>) * nspec));
   MGWR_TRY(dev_alloc(h, &H.tspec, sizeof(Cx<float>) * (size_t)h->B * h->L));
-  MGWR_TRY(dev_alloc(h, &H.tw, sizeof(Cx<float>) * (size_t)h->L));
+  MGWR_TRY(dev_alloc(h, &H.tw, sizeof(Cx<float>) * (size_t)h->Lt));
   MGWR_CK(h, mgwr::launch_round_cx(H.spec, h->h64.spec, nspec, h->stream));
   MGWR_CK(h, mgwr::launch_round_cx(H.tspec, h->h64.tspec, (size_t)h->B * h->L, h->stream));
-  MGWR_CK(h, mgwr::launch_round_cx(H.tw, h->h64.tw, (size_t)h->L, h->stream));
+  MGWR_CK(h, mgwr::launch_round_cx(H.tw, h->h64.tw, (size_t)h->Lt, h->stream));
   MGWR_CK(h, cudaStreamSynchronize(h->stream));
   H.ready = true;
   return MGWR_OK;
@@ -206,9 +220,9 @@ int ensure_dd(mgwr_t h) {
   MGWR_TRY(dev_alloc(h, &h->f_dd, cnt * sizeof(mgwr::dd)));
   MGWR_TRY(ensure_field(h, &h->zero_dd, (size_t)h->M));
   MGWR_TRY(dev_alloc(h, &h->tspec_dd, sizeof(Cx<mgwr::dd>) * (size_t)h->B * h->L));
-  MGWR_TRY(dev_alloc(h, &h->tw_dd, sizeof(Cx<mgwr::dd>) * (size_t)h->L));
+  MGWR_TRY(dev_alloc(h, &h->tw_dd, sizeof(Cx<mgwr::dd>) * (size_t)h->Lt));
   MGWR_CK(h, mgwr::launch_split_cx(h->tspec_dd, h->h64.tspec, (size_t)h->B * h->L, h->stream));
-  MGWR_CK(h, mgwr::launch_split_cx(h->tw_dd, h->h64.tw, (size_t)h->L, h->stream));
+  MGWR_CK(h, mgwr::launch_split_cx(h->tw_dd, h->h64.tw, (size_t)h->Lt, h->stream));
   return MGWR_OK;
 }
 
@@ -256,7 +270,7 @@ template <class R>
 int coarsest(mgwr_t h, Hier<R>& H) {
   const int pm = prof_begin(h, MGWR_K_COARSEST, (double)h->B);
   MGWR_CK(h, mgwr::launch_sweep<R>(H.f[0], H.u[0], (R*)nullptr, H.spec, (size_t)h->nlev * h->L,
-                                    H.tw, H.zero, shape(h, 0), 0, true, R(0), h->stream));
+                                    H.tw, H.zero, scratch_for<R>(h), shape(h, 0), 0, true, R(0), h->stream));
   prof_end(h, pm);
   H.rs[0] = R_STALE;
   return MGWR_OK;
@@ -271,7 +285,7 @@ int sweep_colour(mgwr_t h, Hier<R>& H, int l, int colour, R* delta) {
   const double lines = (double)h->B * (double)(par == 0 ? (N + 1) / 2 : N / 2);
   const int pm = prof_begin(h, sizeof(R) == 8 ? MGWR_K_SWEEP64 : MGWR_K_SWEEP32, lines);
   MGWR_CK(h, mgwr::launch_sweep<R>(H.f[l], H.u[l], delta, H.spec + (size_t)l * h->L,
-                                    (size_t)h->nlev * h->L, H.tw, H.zero, shape(h, l), par,
+                                    (size_t)h->nlev * h->L, H.tw, H.zero, scratch_for<R>(h), shape(h, l), par,
                                     false, R(h->hinv2[l]), h->stream));
   prof_end(h, pm);
   return MGWR_OK;
@@ -303,7 +317,7 @@ int defect(mgwr_t h, Hier<R>& H, int l, unsigned long long* norm_bits) {
   const int pm = prof_begin(h, sizeof(R) == 8 ? MGWR_K_DEFECT64 : MGWR_K_DEFECT32,
                             (double)(points(h, l) * h->B));
   MGWR_CK(h, (mgwr::launch_defect<R, R>(H.u[l], H.f[l], H.r[l], H.tspec, (size_t)h->L, H.tw,
-                                         H.zero, shape(h, l), R(h->hinv2[l]), norm_bits,
+                                         H.zero, scratch_for<R>(h), shape(h, l), R(h->hinv2[l]), norm_bits,
                                          h->stream)));
   prof_end(h, pm);
   H.rs[l] = R_CURRENT;
@@ -398,14 +412,14 @@ int finest_defect_norms(mgwr_t h, std::vector<double>& norms, bool to_h32) {
   if (to_h32) {
     MGWR_CK(h, (mgwr::launch_defect<double, float>(h->h64.u[L], h->h64.f[L], h->h32.f[L],
                                                     h->h64.tspec, (size_t)h->L, h->h64.tw,
-                                                    h->h64.zero, shape(h, L), h->hinv2[L], h->norm_bits,
+                                                    h->h64.zero, scratch_for<double>(h), shape(h, L), h->hinv2[L], h->norm_bits,
                                                     h->stream)));
     h->h32.rs[L] = R_STALE;
   } else {
     MGWR_TRY(ensure_field(h, &h->h64.r[L], level_count(h, L)));
     MGWR_CK(h, (mgwr::launch_defect<double, double>(h->h64.u[L], h->h64.f[L], h->h64.r[L],
                                                      h->h64.tspec, (size_t)h->L, h->h64.tw,
-                                                     h->h64.zero, shape(h, L), h->hinv2[L], h->norm_bits,
+                                                     h->h64.zero, scratch_for<double>(h), shape(h, L), h->hinv2[L], h->norm_bits,
                                                      h->stream)));
     h->h64.rs[L] = R_CURRENT;
   }
@@ -420,7 +434,7 @@ int finest_defect_norms_dd(mgwr_t h, std::vector<double>& norms) {
   MGWR_TRY(clear_norms(h));
   const int pm = prof_begin(h, MGWR_K_DEFECT_DD, (double)(points(h, L) * h->B));
   MGWR_CK(h, (mgwr::launch_defect<mgwr::dd, float>(h->u_dd, h->f_dd, h->h32.f[L], h->tspec_dd,
-                                                    (size_t)h->L, h->tw_dd, h->zero_dd, shape(h, L),
+                                                    (size_t)h->L, h->tw_dd, h->zero_dd, scratch_for<mgwr::dd>(h), shape(h, L),
                                                     mgwr::dd(h->hinv2[L]), h->norm_bits,
                                                     h->stream)));
   prof_end(h, pm);
@@ -474,13 +488,13 @@ int enqueue_iteration(mgwr_t h, int cyc, int nu1, int nu2, bool* exact) {
     const int pd = prof_begin(h, ddef ? MGWR_K_DEFECT_DD : MGWR_K_DEFECT64, (double)(points(h, L) * h->B));
     if (ddef)
       MGWR_CK(h, (mgwr::launch_defect<mgwr::dd, float>(h->u_dd, h->f_dd, h->h32.f[L], h->tspec_dd,
-                                                        (size_t)h->L, h->tw_dd, h->zero_dd, shape(h, L),
+                                                        (size_t)h->L, h->tw_dd, h->zero_dd, scratch_for<mgwr::dd>(h), shape(h, L),
                                                         mgwr::dd(h->hinv2[L]), h->norm_bits,
                                                         h->stream)));
     else
       MGWR_CK(h, (mgwr::launch_defect<double, float>(h->h64.u[L], h->h64.f[L], h->h32.f[L],
                                                       h->h64.tspec, (size_t)h->L, h->h64.tw,
-                                                      h->h64.zero, shape(h, L), h->hinv2[L], h->norm_bits,
+                                                      h->h64.zero, scratch_for<double>(h), shape(h, L), h->hinv2[L], h->norm_bits,
                                                       h->stream)));
     prof_end(h, pd);
     h->h32.rs[L] = R_STALE;
@@ -558,7 +572,7 @@ int create_impl(int d, int n, int M, const double* T, const double* alpha, int b
   if (d != 1 && d != 2) return MGWR_E_INVAL;
   if (n < 1 || !is_pow2((long long)n + 1)) return MGWR_E_INVAL;
   if ((d == 1 && n > 32767) || (d == 2 && n > 4095)) return MGWR_E_INVAL;
-  if (!is_pow2(M) || M < 4 || M > 4096) return MGWR_E_INVAL;
+  if (!is_pow2(M) || M < 4 || M > mgwr::kMaxM) return MGWR_E_INVAL;
   if (batch < 1 || batch > 65535 || T == nullptr || alpha == nullptr) return MGWR_E_INVAL;
   for (int b = 0; b < batch; ++b) {
     if (!(T[b] > 0.0) || !std::isfinite(T[b])) return MGWR_E_INVAL;
@@ -571,6 +585,7 @@ int create_impl(int d, int n, int M, const double* T, const double* alpha, int b
   h->n = n;
   h->M = M;
   h->L = 2 * M;
+  h->Lt = mgwr::engine_length(M);
   h->B = batch;
   h->alpha.assign(alpha, alpha + batch);
   h->T.assign(T, T + batch);
@@ -621,7 +636,12 @@ int create_impl(int d, int n, int M, const double* T, const double* alpha, int b
   if ((s = dev_alloc(h, &h->h64.spec, sizeof(Cx<double>) * B * h->nlev * h->L)) != MGWR_OK)
     return bail(s);
   if ((s = dev_alloc(h, &h->h64.tspec, sizeof(Cx<double>) * B * h->L)) != MGWR_OK) return bail(s);
-  if ((s = dev_alloc(h, &h->h64.tw, sizeof(Cx<double>) * (size_t)h->L)) != MGWR_OK) return bail(s);
+  if ((s = dev_alloc(h, &h->h64.tw, sizeof(Cx<double>) * (size_t)h->Lt)) != MGWR_OK) return bail(s);
+  if (h->M > mgwr::kShortMaxM) {
+    h->scratch_count = mgwr::long_scratch_count(shape(h, h->nlev - 1));
+    if ((s = dev_alloc(h, &h->scratch, sizeof(Cx<double>) * h->scratch_count)) != MGWR_OK)
+      return bail(s);
+  }
 
   cudaError_t e = cudaMemcpyAsync(sig_dev, h->sigma.data(), sizeof(double) * h->nlev,
                                   cudaMemcpyHostToDevice, h->stream);
@@ -635,7 +655,7 @@ int create_impl(int d, int n, int M, const double* T, const double* alpha, int b
     e = mgwr::launch_coefficients(h->r, h->dk, M, alpha_dev, h->c_dev, batch, h->stream);
   if (e == cudaSuccess)
     e = mgwr::launch_inverse_columns(h->kcol, h->r, sig_dev, h->nlev, M, batch, work, h->stream);
-  if (e == cudaSuccess) e = mgwr::launch_twiddles(h->h64.tw, h->L, h->stream);
+  if (e == cudaSuccess) e = mgwr::launch_twiddles(h->h64.tw, h->Lt, h->stream);
   if (e == cudaSuccess)
     e = mgwr::launch_spectra(h->h64.spec, h->kcol, batch * h->nlev, M, h->h64.tw, h->stream);
   if (e == cudaSuccess) e = mgwr::launch_spectra(h->h64.tspec, h->r, batch, M, h->h64.tw, h->stream);
@@ -1127,13 +1147,13 @@ int mgwr_profile_read(mgwr_t h, int kernel_class, long long* launches, double* m
 int mgwr_footprint(int d, int n, int M, int batch, int precision, size_t* bytes) {
   if (bytes == nullptr) return MGWR_E_INVAL;
   if ((d != 1 && d != 2) || n < 1 || !is_pow2((long long)n + 1) || !is_pow2(M) || M < 4 ||
-      M > 4096 || batch < 1 ||
+      M > mgwr::kMaxM || batch < 1 ||
       (precision != MGWR_FP64 && precision != MGWR_MIXED && precision != MGWR_MIXED_DD))
     return MGWR_E_INVAL;
   // mirrors the allocations of create_impl, ensure_full and ensure_h32, each
   // rounded up to 512 bytes, plus 2 MiB of allocator slack per handle
   auto r512 = [](size_t b) { return (b + 511) / 512 * 512; };
-  const size_t B = batch, L = 2 * (size_t)M;
+  const size_t B = batch, L = 2 * (size_t)M, Lt = (size_t)mgwr::engine_length(M);
   std::vector<size_t> pts;
   for (int m = n;; m = (m - 1) / 2) {
     pts.push_back(d == 1 ? (size_t)m : (size_t)m * m);
@@ -1144,15 +1164,17 @@ int mgwr_footprint(int d, int n, int M, int batch, int precision, size_t* bytes)
   total += r512(8 * B) + r512(8 * B * M) + r512(8 * B * (M + 1)) + r512(8 * B * nlev * M);
   total += 2 * r512(8 * B) + r512(8 * nlev);
   total += r512(16 * B * nlev * 3 * M);  // divide-and-conquer work (freed after setup)
-  total += r512(16 * B * nlev * L) + r512(16 * B * L) + r512(16 * L);
+  total += r512(16 * B * nlev * L) + r512(16 * B * L) + r512(16 * Lt);
+  if (M > mgwr::kShortMaxM)  // partitioned-convolution scratch: all block spectra of the finest level
+    total += r512(16 * B * ((pts[0] + 1) / 2) * L);
   if (precision == MGWR_FP64) {
     for (size_t l = 0; l < nlev; ++l) total += (l + 1 < nlev ? 4 : 3) * r512(8 * B * pts[l] * M);
   } else {
     total += 2 * r512(8 * B * pts[0] * M);  // FP64 finest iterate and right-hand side
     for (size_t l = 0; l < nlev; ++l) total += (l + 1 < nlev ? 4 : 3) * r512(4 * B * pts[l] * M);
-    total += r512(8 * B * nlev * L) + r512(8 * B * L) + r512(8 * L);
+    total += r512(8 * B * nlev * L) + r512(8 * B * L) + r512(8 * Lt);
     if (precision == MGWR_MIXED_DD)
-      total += 2 * r512(8 * B * pts[0] * M) + r512(16 * B * L) + r512(16 * L);
+      total += 2 * r512(8 * B * pts[0] * M) + r512(16 * B * L) + r512(16 * Lt);
   }
   *bytes = total;
   return MGWR_OK;

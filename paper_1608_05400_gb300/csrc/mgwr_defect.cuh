@@ -111,8 +111,11 @@ cudaError_t defect_launch(dim3 grid, size_t smem, cudaStream_t s, const R* u, co
 
 template <class R, class RO>
 cudaError_t launch_defect(const R* u, const R* f, RO* r, const Cx<R>* tspec, size_t spec_stride,
-                          const Cx<R>* tw, const R* zero, const LevelShape& ls, R hinv2,
-                          unsigned long long* norm_bits, cudaStream_t s) {
+                          const Cx<R>* tw, const R* zero, Cx<R>* scratch, const LevelShape& ls,
+                          R hinv2, unsigned long long* norm_bits, cudaStream_t s) {
+  if (ls.M > kShortMaxM)
+    return launch_defect_long<R, RO>(u, f, r, tspec, spec_stride, tw, scratch, ls, hinv2,
+                                     norm_bits, s);
   const int d = ls.d, n = ls.n, M = ls.M;
   const int L = 2 * M, logL = ilog2(L);
   const int npts = d == 1 ? n : n * n;

@@ -3,7 +3,7 @@
 
 namespace mgwr {
 template cudaError_t launch_defect<dd, float>(const dd*, const dd*, float*, const Cx<dd>*, size_t,
-                                              const Cx<dd>*, const dd*, const LevelShape&, dd,
-                                              unsigned long long*, cudaStream_t);
+                                              const Cx<dd>*, const dd*, Cx<dd>*, const LevelShape&,
+                                              dd, unsigned long long*, cudaStream_t);
 
 }  // namespace mgwr

@@ -2,8 +2,9 @@
 #include "mgwr_defect.cuh"
 
 namespace mgwr {
-template cudaError_t launch_defect<float, float>(const float*, const float*, float*, const Cx<float>*, size_t,
-                                              const Cx<float>*, const float*, const LevelShape&, float,
-                                              unsigned long long*, cudaStream_t);
+template cudaError_t launch_defect<float, float>(const float*, const float*, float*,
+                                                 const Cx<float>*, size_t, const Cx<float>*,
+                                                 const float*, Cx<float>*, const LevelShape&,
+                                                 float, unsigned long long*, cudaStream_t);
 
 }  // namespace mgwr

@@ -29,6 +29,24 @@ struct LevelShape {
   size_t field_stride() const { return (size_t)(d == 1 ? n : n * n) * M; }
 };
 
+// Time lines up to kShortMaxM values are convolved with one transform of
+// length 2M.  Longer lines (partitioned convolution) are cut into blocks of
+// kLongB values, each transformed at length 2 kLongB; their spectra and the
+// kernel segments keep the total length 2M per line (P = M / kLongB segments
+// of 2 kLongB values).  engine_length(M) is the transform length, and so the
+// length of the twiddle table.
+constexpr int kShortMaxM = 4096;
+constexpr int kLongB = 4096;
+constexpr int kMaxM = 1 << 20;
+inline int engine_length(int M) { return M <= kShortMaxM ? 2 * M : 2 * kLongB; }
+// Complex values of the partitioned-convolution scratch for one launch on a
+// level of shape ls: per instance, per line pair, the spectra of all blocks.
+inline size_t long_scratch_count(const LevelShape& ls) {
+  if (ls.M <= kShortMaxM) return 0;
+  const size_t pts = (size_t)(ls.d == 1 ? ls.n : ls.n * ls.n);
+  return (size_t)ls.batch * ((pts + 1) / 2) * 2 * (size_t)ls.M;
+}
+
 // ---- launchers (kernels in mgwr_kernels.cu); all return the launch status ----
 // Every launcher covers all `batch` instances (blockIdx.y = instance).
 
@@ -39,10 +57,12 @@ struct LevelShape {
 // (one-point coarsest solve).  delta != null: also delta_p = u_p(new) -
 // u_p(old) on the swept lines.
 // `zero` is a line of M zeros standing in for neighbours outside the grid.
+// For M > kShortMaxM, `scratch` holds long_scratch_count(ls) values (unused
+// otherwise, may be null).
 template <class R>
 cudaError_t launch_sweep(const R* f, R* u, R* delta, const Cx<R>* spec, size_t spec_stride,
-                         const Cx<R>* tw, const R* zero, const LevelShape& ls, int par,
-                         bool all_points, R hinv2, cudaStream_t s);
+                         const Cx<R>* tw, const R* zero, Cx<R>* scratch, const LevelShape& ls,
+                         int par, bool all_points, R hinv2, cudaStream_t s);
 
 // Defect after a red-black step from the black half-sweep's delta: r = 0 on the
 // black points, r = hinv2 * sum of neighbour deltas on the red points
@@ -54,10 +74,24 @@ cudaError_t launch_defect_from_delta(const R* delta, R* r, const R* zero, const 
 
 // r = f - T_M u - A_h u for all points; |r|_inf of instance b folded into
 // norm_bits[b] (bit pattern of a non-negative double, atomicMax) when non-null.
+// `scratch` as for launch_sweep.
 template <class R, class RO>
 cudaError_t launch_defect(const R* u, const R* f, RO* r, const Cx<R>* tspec, size_t spec_stride,
-                          const Cx<R>* tw, const R* zero, const LevelShape& ls, R hinv2,
-                          unsigned long long* norm_bits, cudaStream_t s);
+                          const Cx<R>* tw, const R* zero, Cx<R>* scratch, const LevelShape& ls,
+                          R hinv2, unsigned long long* norm_bits, cudaStream_t s);
+
+// The same two operations for M > kShortMaxM by partitioned convolution
+// (mgwr_long.cu); `spec` / `tspec` hold the kernel segment spectra written by
+// launch_spectra for that M.
+template <class R>
+cudaError_t launch_sweep_long(const R* f, R* u, R* delta, const Cx<R>* spec, size_t spec_stride,
+                              const Cx<R>* tw, Cx<R>* scratch, const LevelShape& ls, int par,
+                              bool all_points, R hinv2, cudaStream_t s);
+template <class R, class RO>
+cudaError_t launch_defect_long(const R* u, const R* f, RO* r, const Cx<R>* tspec,
+                               size_t spec_stride, const Cx<R>* tw, Cx<R>* scratch,
+                               const LevelShape& ls, R hinv2, unsigned long long* norm_bits,
+                               cudaStream_t s);
 
 // fc = full weighting of r (fine n -> coarse (n-1)/2), uc = 0.
 template <class R>
@@ -92,9 +126,14 @@ cudaError_t launch_inverse_columns(double* kcol, const double* r, const double* 
                                    int M, int batch, Cx<double>* work, cudaStream_t s);
 // tw[m] = exp(-2 pi i m / L), m < L.
 cudaError_t launch_twiddles(Cx<double>* tw, int L, cudaStream_t s);
-// spec[k*L ..] = FFT_L(pad(lines[k*M ..])) / L in the library's spectral order.
+// spec[k*2M ..] = FFT_2M(pad(lines[k*M ..])) / 2M in the library's spectral
+// order (M <= kShortMaxM); for longer M the kernel segment spectra of the
+// partitioned convolution (launch_spectra_long), also 2M values per line.
+// tw: engine_length(M) twiddles.
 cudaError_t launch_spectra(Cx<double>* spec, const double* lines, int count, int M,
                            const Cx<double>* tw, cudaStream_t s);
+cudaError_t launch_spectra_long(Cx<double>* spec, const double* lines, int count, int M,
+                                const Cx<double>* tw, cudaStream_t s);
 cudaError_t launch_round_cx(Cx<float>* dst, const Cx<double>* src, size_t count, cudaStream_t s);
 
 // Kernel launches issued through the launchers above (process-wide counter),

@@ -575,6 +575,7 @@ cudaError_t launch_twiddles(Cx<double>* tw, int L, cudaStream_t s) {
 
 cudaError_t launch_spectra(Cx<double>* spec, const double* lines, int count, int M,
                            const Cx<double>* tw, cudaStream_t s) {
+  if (M > kShortMaxM) return launch_spectra_long(spec, lines, count, M, tw, s);
   const int L = 2 * M, logL = ilog2(L);
   const int block = block_threads(L);
   const int groups = block / (L / 8);

@@ -134,7 +134,7 @@ int check_request(const mgwr_request* q) {
   if (q->d != 1 && q->d != 2) return MGWR_E_INVAL;
   if (q->n < 1 || !pow2((long long)q->n + 1)) return MGWR_E_INVAL;
   if ((q->d == 1 && q->n > 32767) || (q->d == 2 && q->n > 4095)) return MGWR_E_INVAL;
-  if (!pow2(q->M) || q->M < 4 || q->M > 4096) return MGWR_E_INVAL;
+  if (!pow2(q->M) || q->M < 4 || q->M > (1 << 20)) return MGWR_E_INVAL;
   if (!(q->T > 0.0) || !(q->alpha > 0.0) || !(q->alpha <= 1.0)) return MGWR_E_INVAL;
   if (q->precision != MGWR_FP64 && q->precision != MGWR_MIXED && q->precision != MGWR_MIXED_DD)
     return MGWR_E_INVAL;

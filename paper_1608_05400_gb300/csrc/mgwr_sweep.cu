@@ -101,8 +101,11 @@ cudaError_t sweep_launch(dim3 grid, size_t smem, cudaStream_t s, const R* f, R* 
 
 template <class R>
 cudaError_t launch_sweep(const R* f, R* u, R* delta, const Cx<R>* spec, size_t spec_stride,
-                         const Cx<R>* tw, const R* zero, const LevelShape& ls, int par,
-                         bool all_points, R hinv2, cudaStream_t s) {
+                         const Cx<R>* tw, const R* zero, Cx<R>* scratch, const LevelShape& ls,
+                         int par, bool all_points, R hinv2, cudaStream_t s) {
+  if (ls.M > kShortMaxM)
+    return launch_sweep_long(f, u, delta, spec, spec_stride, tw, scratch, ls, par, all_points,
+                             hinv2, s);
   const int d = ls.d, n = ls.n, M = ls.M;
   const int L = 2 * M, logL = ilog2(L);
   const int npts = all_points ? (d == 1 ? n : n * n) : colour_count(d, n, par);
@@ -154,10 +157,10 @@ cudaError_t launch_sweep(const R* f, R* u, R* delta, const Cx<R>* spec, size_t s
 }
 
 template cudaError_t launch_sweep<double>(const double*, double*, double*, const Cx<double>*,
-                                          size_t, const Cx<double>*, const double*,
+                                          size_t, const Cx<double>*, const double*, Cx<double>*,
                                           const LevelShape&, int, bool, double, cudaStream_t);
 template cudaError_t launch_sweep<float>(const float*, float*, float*, const Cx<float>*, size_t,
-                                         const Cx<float>*, const float*, const LevelShape&, int,
-                                         bool, float, cudaStream_t);
+                                         const Cx<float>*, const float*, Cx<float>*,
+                                         const LevelShape&, int, bool, float, cudaStream_t);
 
 }  // namespace mgwr

@@ -46,7 +46,7 @@ def test_library_exports_every_declared_function(lib):
     (2, 8191, 64, 1.0, 0.5),    # n too large in 2-D
     (1, 63, 48, 1.0, 0.5),      # M not a power of two
     (1, 63, 2, 1.0, 0.5),       # M too small
-    (1, 63, 8192, 1.0, 0.5),    # M too large
+    (1, 63, 1 << 21, 1.0, 0.5),  # M too large
     (1, 63, 64, 0.0, 0.5),      # T
     (1, 63, 64, float("inf"), 0.5),
     (1, 63, 64, 1.0, 0.0),      # alpha
@@ -84,6 +84,14 @@ def test_footprint_is_host_arithmetic_and_scales(lib):
     # linear in the batch, monotone in n and M
     assert abs(footprint(2, 63, 256, 64) - 64 * footprint(2, 63, 256, 1)) < 64 * (3 << 20)
     assert footprint(1, 63, 64) < footprint(1, 127, 64) < footprint(1, 127, 128)
+    # long lines (M > 4096) add the partitioned-convolution scratch: 16 bytes per
+    # line pair and transform value of the finest level, ceil(N/2) * 2M of them
+    n, M = 4095, 65536
+    fields = 4 * n * M * 8
+    scratch = 16 * ((n + 1) // 2) * 2 * M
+    lg = footprint(1, n, M, 1, MGWR_FP64)
+    assert 2 * fields + scratch < lg < 2 * fields + scratch + (64 << 20)
+    assert footprint(1, 63, 4096) < footprint(1, 63, 8192) < footprint(1, 63, 1 << 20)
     v = C.c_size_t()
     assert lib.mgwr_footprint(2, 64, 256, 1, 0, C.byref(v)) == mgwr.MGWR_E_INVAL
     assert lib.mgwr_footprint(2, 63, 256, 0, 0, C.byref(v)) == mgwr.MGWR_E_INVAL

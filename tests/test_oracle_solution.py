@@ -103,3 +103,26 @@ def test_time_stepping_partial_steps():
     part = direct.time_stepping(d, n, M, 1.0, 0.5, f, steps=5)
     np.testing.assert_array_equal(part[:, :5], full[:, :5])
     assert not part[:, 5:].any()
+
+
+@pytest.mark.parametrize("M,alpha", [(64, 0.5), (1000, 0.2), (4096, 0.85)])
+def test_separable_substitution_equals_dense(M, alpha):
+    # the O(M)-memory forward substitution used for long lines against the dense solve
+    F = inputs.random_field(1, M, seed=M)[0]
+    w1 = separable.time_factor_dense(1, 63, M, 0.9, alpha, F)
+    w2 = separable.time_factor_substitution(1, 63, M, 0.9, alpha, F)
+    np.testing.assert_allclose(w2, w1, rtol=0, atol=1e-13 * np.abs(w1).max())
+
+
+@pytest.mark.parametrize("alpha", [0.2, 0.7])
+def test_separable_substitution_linear_in_time_exact(alpha):
+    # T_M t = t^{1-alpha} / Gamma(2-alpha) exactly (the L1 sums telescope), so
+    # F = t^{1-alpha}/Gamma(2-alpha) + lambda_h t has the discrete solution w = t:
+    # a pin at long M that does not go through the dense matrix
+    d, n, M, T = 1, 4095, 16384, 1.0
+    t = inputs.time_nodes(M, T)
+    F = t ** (1 - alpha) / math.gamma(2 - alpha) + separable.eigenvalue(d, n) * t
+    w = separable.time_factor_substitution(d, n, M, T, alpha, F)
+    assert np.abs(w - t).max() <= 1e-11
+    # beyond the dense limit time_factor is this substitution
+    np.testing.assert_array_equal(separable.time_factor(d, n, M, T, alpha, F), w)

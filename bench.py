@@ -82,6 +82,7 @@ def parse():
     p.add_argument("--slots", type=int, default=4, help="c4: server slots")
     p.add_argument("--inner", type=int, default=None, help="mixed modes: FP32 cycles per outer defect")
     p.add_argument("--alpha", type=float, default=None)
+    p.add_argument("--no-autotune", action="store_true", help="keep the default engine launch shapes")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     return p.parse_args()
@@ -400,6 +401,10 @@ def main():
         if args.inner:
             s.set_inner_cycles(args.inner)
 
+    # launch shapes of the FFT-engine kernels, timed on this handle's data (setup,
+    # outside the timed region)
+    splits = None if args.no_autotune else s.autotune()
+
     def step():
         s.set_rhs_dev(f_dev.data_ptr())
         return s.solve(CYCLE, NU1, NU2, tol, 100)
@@ -477,6 +482,7 @@ def main():
         "config": {"workload": f"{desc}, " + (f"alpha={alpha}, " if batch == 1 else "")
                                + f"V({NU1},{NU2}) red-black, rel-res {tol}",
                    "name": args.workload, "precision": precision,
+                   "engine_splits": splits,
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": f"inputs larger than L2 ({unknowns * 8 / 1e6:.0f} MB per FP64 field)"},
         "solve": {"cycles": stats[-1].cycles, "outer": stats[-1].outer, "relres": stats[-1].relres,

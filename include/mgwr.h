@@ -135,6 +135,28 @@ int mgwr_set_order(mgwr_t h, int order);
 int mgwr_set_stream(mgwr_t h, void* stream);
 /* Inner FP32 cycles per outer defect in the mixed modes (1..16, default 2). */
 int mgwr_set_inner_cycles(mgwr_t h, int cycles);
+
+/* Launch shape of the FFT-engine kernels (no counterpart in the paper; the
+ * results are bitwise the same for every shape).  For kernel class
+ * MGWR_K_SWEEP64, MGWR_K_SWEEP32 (also the one-point solves of that
+ * arithmetic), MGWR_K_DEFECT64, MGWR_K_DEFECT32 or MGWR_K_DEFECT_DD, `split`
+ * = E in {1, 2, 4} radix-8 butterflies per thread and stage: a group of
+ * L/(8E) threads transforms one line pair of length L = 2M (8192 for
+ * M > 4096, where E is 1 or 2), synchronising with warp barriers when the
+ * group fits in one warp.  A request a length cannot take falls back to the
+ * nearest smaller E; mgwr_get_engine_split reports the E launches use.
+ * MGWR_E_INVAL for another class or split. */
+int mgwr_set_engine_split(mgwr_t h, int kernel_class, int split);
+int mgwr_get_engine_split(mgwr_t h, int kernel_class, int* split);
+/* Tuner: times every E of each engine class the current precision runs (the
+ * sweep and the full defect of its cycle hierarchy, and in the mixed modes
+ * the outer defect) on a sample of the handle's own data (the finest level
+ * holding at most 2^25 values per instance, as many instances as fit 2^25
+ * values), writing to a temporary field, and keeps the fastest.  The handle's
+ * state is unchanged.  The choices are also recorded process-wide for
+ * (class, d, n, M, batch): handles created later with that shape start with
+ * them.  Synchronises the handle's stream. */
+int mgwr_autotune(mgwr_t h);
 /* enable != 0 (default): mgwr_solve captures one iteration of its loop (the
  * cycle's launches, the defect norms and their copy to the host) as a CUDA
  * graph on first use and replays it, one graph launch per iteration; 0:

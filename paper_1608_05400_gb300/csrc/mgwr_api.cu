@@ -7,7 +7,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -80,6 +83,8 @@ struct mgwr_handle {
   std::string err;
   // one solve-loop iteration captured as a CUDA graph, replayed every iteration
   bool use_graphs = true;
+  // FFT-engine split (butterflies per thread) per kernel class; 0 = default
+  int split[MGWR_NUM_KERNEL_CLASSES] = {};
   cudaGraphExec_t iter_exec = nullptr;
   long long iter_key = -1;   // (precision, cycle, nu1, nu2, inner, order) it was captured for
   bool iter_exact = true;    // its norms come from the full defect
@@ -143,6 +148,8 @@ int ensure_field(mgwr_t h, R** p, size_t count) {
 }
 
 bool is_pow2(long long x) { return x > 0 && (x & (x - 1)) == 0; }
+
+int split_of(const mgwr_handle* h, int cls) { return h->split[cls]; }
 
 // The handle's partitioned-convolution scratch viewed as complex values of R
 // (null for M <= kShortMaxM, where no launch uses it).
@@ -216,8 +223,8 @@ int ensure_h32(mgwr_t h) {
 int ensure_dd(mgwr_t h) {
   if (h->u_dd != nullptr) return MGWR_OK;
   const size_t cnt = level_count(h, h->nlev - 1);
-  MGWR_TRY(dev_alloc(h, &h->u_dd, cnt * sizeof(mgwr::dd)));
-  MGWR_TRY(dev_alloc(h, &h->f_dd, cnt * sizeof(mgwr::dd)));
+  MGWR_TRY(ensure_field(h, &h->u_dd, cnt));
+  MGWR_TRY(ensure_field(h, &h->f_dd, cnt));
   MGWR_TRY(ensure_field(h, &h->zero_dd, (size_t)h->M));
   MGWR_TRY(dev_alloc(h, &h->tspec_dd, sizeof(Cx<mgwr::dd>) * (size_t)h->B * h->L));
   MGWR_TRY(dev_alloc(h, &h->tw_dd, sizeof(Cx<mgwr::dd>) * (size_t)h->Lt));
@@ -270,7 +277,9 @@ template <class R>
 int coarsest(mgwr_t h, Hier<R>& H) {
   const int pm = prof_begin(h, MGWR_K_COARSEST, (double)h->B);
   MGWR_CK(h, mgwr::launch_sweep<R>(H.f[0], H.u[0], (R*)nullptr, H.spec, (size_t)h->nlev * h->L,
-                                    H.tw, H.zero, scratch_for<R>(h), shape(h, 0), 0, true, R(0), h->stream));
+                                    H.tw, H.zero, scratch_for<R>(h), shape(h, 0), 0, true, R(0),
+                                    split_of(h, sizeof(R) == 8 ? MGWR_K_SWEEP64 : MGWR_K_SWEEP32),
+                                    h->stream));
   prof_end(h, pm);
   H.rs[0] = R_STALE;
   return MGWR_OK;
@@ -286,7 +295,9 @@ int sweep_colour(mgwr_t h, Hier<R>& H, int l, int colour, R* delta) {
   const int pm = prof_begin(h, sizeof(R) == 8 ? MGWR_K_SWEEP64 : MGWR_K_SWEEP32, lines);
   MGWR_CK(h, mgwr::launch_sweep<R>(H.f[l], H.u[l], delta, H.spec + (size_t)l * h->L,
                                     (size_t)h->nlev * h->L, H.tw, H.zero, scratch_for<R>(h), shape(h, l), par,
-                                    false, R(h->hinv2[l]), h->stream));
+                                    false, R(h->hinv2[l]),
+                                    split_of(h, sizeof(R) == 8 ? MGWR_K_SWEEP64 : MGWR_K_SWEEP32),
+                                    h->stream));
   prof_end(h, pm);
   return MGWR_OK;
 }
@@ -318,6 +329,7 @@ int defect(mgwr_t h, Hier<R>& H, int l, unsigned long long* norm_bits) {
                             (double)(points(h, l) * h->B));
   MGWR_CK(h, (mgwr::launch_defect<R, R>(H.u[l], H.f[l], H.r[l], H.tspec, (size_t)h->L, H.tw,
                                          H.zero, scratch_for<R>(h), shape(h, l), R(h->hinv2[l]), norm_bits,
+                                         split_of(h, sizeof(R) == 8 ? MGWR_K_DEFECT64 : MGWR_K_DEFECT32),
                                          h->stream)));
   prof_end(h, pm);
   H.rs[l] = R_CURRENT;
@@ -413,6 +425,7 @@ int finest_defect_norms(mgwr_t h, std::vector<double>& norms, bool to_h32) {
     MGWR_CK(h, (mgwr::launch_defect<double, float>(h->h64.u[L], h->h64.f[L], h->h32.f[L],
                                                     h->h64.tspec, (size_t)h->L, h->h64.tw,
                                                     h->h64.zero, scratch_for<double>(h), shape(h, L), h->hinv2[L], h->norm_bits,
+                                                    split_of(h, MGWR_K_DEFECT64),
                                                     h->stream)));
     h->h32.rs[L] = R_STALE;
   } else {
@@ -420,6 +433,7 @@ int finest_defect_norms(mgwr_t h, std::vector<double>& norms, bool to_h32) {
     MGWR_CK(h, (mgwr::launch_defect<double, double>(h->h64.u[L], h->h64.f[L], h->h64.r[L],
                                                      h->h64.tspec, (size_t)h->L, h->h64.tw,
                                                      h->h64.zero, scratch_for<double>(h), shape(h, L), h->hinv2[L], h->norm_bits,
+                                                    split_of(h, MGWR_K_DEFECT64),
                                                      h->stream)));
     h->h64.rs[L] = R_CURRENT;
   }
@@ -435,7 +449,7 @@ int finest_defect_norms_dd(mgwr_t h, std::vector<double>& norms) {
   const int pm = prof_begin(h, MGWR_K_DEFECT_DD, (double)(points(h, L) * h->B));
   MGWR_CK(h, (mgwr::launch_defect<mgwr::dd, float>(h->u_dd, h->f_dd, h->h32.f[L], h->tspec_dd,
                                                     (size_t)h->L, h->tw_dd, h->zero_dd, scratch_for<mgwr::dd>(h), shape(h, L),
-                                                    mgwr::dd(h->hinv2[L]), h->norm_bits,
+                                                    mgwr::dd(h->hinv2[L]), h->norm_bits, split_of(h, MGWR_K_DEFECT_DD),
                                                     h->stream)));
   prof_end(h, pm);
   h->h32.rs[L] = R_STALE;
@@ -489,12 +503,13 @@ int enqueue_iteration(mgwr_t h, int cyc, int nu1, int nu2, bool* exact) {
     if (ddef)
       MGWR_CK(h, (mgwr::launch_defect<mgwr::dd, float>(h->u_dd, h->f_dd, h->h32.f[L], h->tspec_dd,
                                                         (size_t)h->L, h->tw_dd, h->zero_dd, scratch_for<mgwr::dd>(h), shape(h, L),
-                                                        mgwr::dd(h->hinv2[L]), h->norm_bits,
+                                                        mgwr::dd(h->hinv2[L]), h->norm_bits, split_of(h, MGWR_K_DEFECT_DD),
                                                         h->stream)));
     else
       MGWR_CK(h, (mgwr::launch_defect<double, float>(h->h64.u[L], h->h64.f[L], h->h32.f[L],
                                                       h->h64.tspec, (size_t)h->L, h->h64.tw,
                                                       h->h64.zero, scratch_for<double>(h), shape(h, L), h->hinv2[L], h->norm_bits,
+                                                    split_of(h, MGWR_K_DEFECT64),
                                                       h->stream)));
     prof_end(h, pd);
     h->h32.rs[L] = R_STALE;
@@ -563,6 +578,135 @@ int check_cycle_args(mgwr_t h, int cyc, int nu1, int nu2) {
   if (nu1 < 0 || nu2 < 0 || nu1 > 16 || nu2 > 16 || nu1 + nu2 == 0)
     return fail(h, MGWR_E_INVAL, "need 0 <= nu1, nu2 <= 16 and nu1 + nu2 >= 1");
   return MGWR_OK;
+}
+
+// ---- FFT-engine launch-shape tuner ---------------------------------------------
+
+// Splits chosen by mgwr_autotune, per (kernel class, d, n, M, batch): handles of a
+// shape that was tuned before start with its choices.
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int, int>, int> g_tune;
+
+void load_tuned(mgwr_t h) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (int c = 0; c < MGWR_NUM_KERNEL_CLASSES; ++c) {
+    auto it = g_tune.find(std::make_tuple(c, h->d, h->n, h->M, h->B));
+    if (it != g_tune.end()) h->split[c] = it->second;
+  }
+}
+
+void drop_graph(mgwr_t h) {
+  if (h->iter_exec) cudaGraphExecDestroy(h->iter_exec);
+  h->iter_exec = nullptr;
+  h->iter_key = -1;
+}
+
+// The sample the tuner times: the finest level whose field holds at most 2^25
+// values per instance, and as many instances (at most the batch) as keep the
+// sample within 2^25 values (all pairs of those instances).
+LevelShape tune_sample(const mgwr_handle* h, int* level) {
+  const size_t cap = size_t(1) << 25;
+  int l = h->nlev - 1;
+  while (l > 0 && points(h, l) * (size_t)h->M > cap) --l;
+  const size_t per = points(h, l) * (size_t)h->M;
+  size_t b = per >= cap ? 1 : cap / per;
+  if (b > (size_t)h->B) b = h->B;
+  *level = l;
+  return LevelShape{h->d, h->nl[l], h->M, (int)b};
+}
+
+// Mean device time of `reps` launches after one warm-up launch.
+template <class F>
+int time_launches(mgwr_t h, F launch, float* ms) {
+  MGWR_CK(h, launch());
+  const int reps = 3;
+  MGWR_CK(h, cudaEventRecord(h->ev0, h->stream));
+  for (int i = 0; i < reps; ++i) MGWR_CK(h, launch());
+  MGWR_CK(h, cudaEventRecord(h->ev1, h->stream));
+  MGWR_CK(h, cudaEventSynchronize(h->ev1));
+  float t = 0.f;
+  MGWR_CK(h, cudaEventElapsedTime(&t, h->ev0, h->ev1));
+  *ms = t / reps;
+  return MGWR_OK;
+}
+
+// Times every split E in {1, 2, 4} of one kernel class with `launch(E)` and
+// keeps the fastest.
+template <class F>
+int tune_class(mgwr_t h, int cls, int word, F launch) {
+  int best = 1;
+  float best_ms = 0.f;
+  for (int E = 1; E <= 4; E *= 2) {
+    if (mgwr::effective_split(h->M, word, E) != E) continue;  // same launch as a smaller E
+    float ms = 0.f;
+    MGWR_TRY(time_launches(h, [&] { return launch(E); }, &ms));
+    if (E == 1 || ms < best_ms) {
+      best = E;
+      best_ms = ms;
+    }
+  }
+  h->split[cls] = best;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[std::make_tuple(cls, h->d, h->n, h->M, h->B)] = best;
+  return MGWR_OK;
+}
+
+// Sweeps (red points) and defects of the sample, written to a scratch field, in
+// the arithmetic `R` of hierarchy H; no state of the handle changes.
+template <class R>
+int tune_hierarchy(mgwr_t h, Hier<R>& H, int cls_sweep, int cls_defect) {
+  int l = 0;
+  const LevelShape ls = tune_sample(h, &l);
+  const size_t count = ls.field_stride() * ls.batch;
+  R* out = nullptr;
+  MGWR_TRY(ensure_field(h, &H.u[l], level_count(h, l)));
+  MGWR_TRY(ensure_field(h, &H.f[l], level_count(h, l)));
+  MGWR_TRY(dev_alloc(h, &out, count * sizeof(R)));
+  MGWR_CK(h, cudaMemsetAsync(out, 0, count * sizeof(R), h->stream));
+  int st = tune_class(h, cls_sweep, sizeof(R) == 4 ? 4 : 8, [&](int E) {
+    return mgwr::launch_sweep<R>(H.f[l], out, (R*)nullptr, H.spec + (size_t)l * h->L,
+                                 (size_t)h->nlev * h->L, H.tw, H.zero, scratch_for<R>(h), ls,
+                                 parity(h, MGWR_RED), false, R(h->hinv2[l]), E, h->stream);
+  });
+  if (st == MGWR_OK)
+    st = tune_class(h, cls_defect, sizeof(R) == 4 ? 4 : 8, [&](int E) {
+      return mgwr::launch_defect<R, R>(H.u[l], H.f[l], out, H.tspec, (size_t)h->L, H.tw, H.zero,
+                                       scratch_for<R>(h), ls, R(h->hinv2[l]), nullptr, E,
+                                       h->stream);
+    });
+  cudaFreeAsync(out, h->stream);
+  h->allocs.erase(std::find(h->allocs.begin(), h->allocs.end(), (void*)out));
+  return st;
+}
+
+// Outer defect of the mixed modes (FP64 or double-float iterate, FP32 output)
+// on the finest-level sample.
+int tune_outer(mgwr_t h) {
+  int l = 0;
+  const LevelShape ls = tune_sample(h, &l);
+  const int Lf = h->nlev - 1;
+  if (l != Lf) return MGWR_OK;  // the outer defect only runs on the finest level
+  const size_t count = ls.field_stride() * ls.batch;
+  float* out = nullptr;
+  MGWR_TRY(dev_alloc(h, &out, count * sizeof(float)));
+  int st;
+  if (h->precision == MGWR_MIXED_DD)
+    st = tune_class(h, MGWR_K_DEFECT_DD, 8, [&](int E) {
+      return mgwr::launch_defect<mgwr::dd, float>(h->u_dd, h->f_dd, out, h->tspec_dd, (size_t)h->L,
+                                                  h->tw_dd, h->zero_dd, scratch_for<mgwr::dd>(h),
+                                                  ls, mgwr::dd(h->hinv2[Lf]), nullptr, E,
+                                                  h->stream);
+    });
+  else
+    st = tune_class(h, MGWR_K_DEFECT64, 8, [&](int E) {
+      return mgwr::launch_defect<double, float>(h->h64.u[Lf], h->h64.f[Lf], out, h->h64.tspec,
+                                                (size_t)h->L, h->h64.tw, h->h64.zero,
+                                                scratch_for<double>(h), ls, h->hinv2[Lf],
+                                                nullptr, E, h->stream);
+    });
+  cudaFreeAsync(out, h->stream);
+  h->allocs.erase(std::find(h->allocs.begin(), h->allocs.end(), (void*)out));
+  return st;
 }
 
 int create_impl(int d, int n, int M, const double* T, const double* alpha, int batch,
@@ -677,6 +821,7 @@ int create_impl(int d, int n, int M, const double* T, const double* alpha, int b
     cudaGetLastError();
     return bail(MGWR_E_CUDA);
   }
+  load_tuned(h);
   *out = h;
   return MGWR_OK;
 }
@@ -774,6 +919,41 @@ int mgwr_set_stream(mgwr_t h, void* stream) {
 int mgwr_set_graphs(mgwr_t h, int enable) {
   if (h == nullptr) return MGWR_E_INVAL;
   h->use_graphs = enable != 0;
+  return MGWR_OK;
+}
+
+int mgwr_set_engine_split(mgwr_t h, int kernel_class, int split) {
+  if (h == nullptr) return MGWR_E_INVAL;
+  if (kernel_class != MGWR_K_SWEEP64 && kernel_class != MGWR_K_SWEEP32 &&
+      kernel_class != MGWR_K_DEFECT64 && kernel_class != MGWR_K_DEFECT32 &&
+      kernel_class != MGWR_K_DEFECT_DD)
+    return fail(h, MGWR_E_INVAL, "kernel class has no FFT engine");
+  if (split != 1 && split != 2 && split != 4) return fail(h, MGWR_E_INVAL, "split must be 1, 2 or 4");
+  h->split[kernel_class] = split;
+  drop_graph(h);
+  return MGWR_OK;
+}
+
+int mgwr_get_engine_split(mgwr_t h, int kernel_class, int* split) {
+  if (h == nullptr || split == nullptr || kernel_class < 0 ||
+      kernel_class >= MGWR_NUM_KERNEL_CLASSES)
+    return MGWR_E_INVAL;
+  const int word = kernel_class == MGWR_K_SWEEP32 || kernel_class == MGWR_K_DEFECT32 ? 4 : 8;
+  *split = mgwr::effective_split(h->M, word, h->split[kernel_class]);
+  return MGWR_OK;
+}
+
+int mgwr_autotune(mgwr_t h) {
+  if (h == nullptr) return MGWR_E_INVAL;
+  MGWR_CK(h, cudaStreamSynchronize(h->stream));
+  if (h->precision == MGWR_FP64) {
+    MGWR_TRY(tune_hierarchy(h, h->h64, MGWR_K_SWEEP64, MGWR_K_DEFECT64));
+  } else {
+    MGWR_TRY(tune_hierarchy(h, h->h32, MGWR_K_SWEEP32, MGWR_K_DEFECT32));
+    MGWR_TRY(tune_outer(h));
+  }
+  MGWR_CK(h, cudaStreamSynchronize(h->stream));
+  drop_graph(h);
   return MGWR_OK;
 }
 

@@ -18,11 +18,13 @@ namespace mgwr {
 cudaError_t counted(cudaError_t e);
 
 // Minimum resident blocks per SM asked of the compiler (it sets the register
-// cap): 1024 resident threads for the FP32 engine kernels (64 registers), 768
-// for the FP64 / double-float ones (85 registers at 256 threads per block).
+// cap), counted in butterfly slots (threads x E, E butterflies per thread):
+// 1024 slots for the FP32 engine kernels (64 registers per slot), 768 for the
+// FP64 / double-float ones (85 registers per slot at 256 threads per block).
 template <class R>
-constexpr int min_blocks(int block) {
-  return sizeof(R) == 4 ? (1024 / block > 1 ? 1024 / block : 1) : (768 / block > 1 ? 768 / block : 1);
+constexpr int min_blocks(int block, int E = 1) {
+  return sizeof(R) == 4 ? (1024 / (block * E) > 1 ? 1024 / (block * E) : 1)
+                        : (768 / (block * E) > 1 ? 768 / (block * E) : 1);
 }
 
 // Threads per line pair: L/8.  Blocks hold 256 threads (several pairs) up to

@@ -11,8 +11,8 @@ namespace mgwr {
 // defect r = f - (T_M (x) I + A_h) u  (Algorithm 1; Sec. 5 circulant-embedding matvec)
 // ---------------------------------------------------------------------------------
 
-template <class R, class RO, int BLOCK, class SH>
-__global__ void __launch_bounds__(BLOCK, min_blocks<R>(BLOCK))
+template <class R, class RO, int BLOCK, class SH, int E>
+__global__ void __launch_bounds__(BLOCK, min_blocks<R>(BLOCK, E))
     k_defect(const R* __restrict__ u, const R* __restrict__ f, RO* __restrict__ r,
              const Cx<R>* __restrict__ tspec, const Cx<R>* __restrict__ tw,
              const R* __restrict__ zero, int d, int n, int M, int logL, R hinv2, int npts,
@@ -27,12 +27,13 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<R>(BLOCK))
   __shared__ double red[BLOCK / 32];
   Cx<R>* smem = reinterpret_cast<Cx<R>*>(smem_raw);
   const SH sh(logL);
-  const int TL = sh.L8;
+  const int TL = sh.L8 / E;  // threads per line pair
   const int g = threadIdx.x / TL;
   const int t = threadIdx.x - g * TL;
   const int groups = BLOCK / TL;
   const int pair = blockIdx.x * groups + g;
   Cx<R>* buf = smem + g * Pad<R>::len(sh.L);
+  const GroupSync sync(TL, BLOCK, g);
 
   const bool valid = pair < npairs;
   const int pA = 2 * pair, pB = 2 * pair + 1;
@@ -48,10 +49,14 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<R>(BLOCK))
     neighbour_lines(u, zero, d, n, iB, jB, pBM, M, qB);
   }
   auto load = [&](int m) -> Cx<R> { return Cx<R>{uA[m], uB[m]}; };
-  Cx<R> v[8];
-  fft_forward(buf, t, sh, tw, load, v);
+  Cx<R> v[E][8];
+  fft_forward<E>(buf, t, sh, tw, load, v, sync);
 #pragma unroll
-  for (int q = 0; q < 8; ++q) v[q] = cmul(v[q], tspec[8 * t + q]);
+  for (int e = 0; e < E; ++e) {
+    const int b = t + e * TL;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[e][q] = cmul(v[e][q], tspec[8 * b + q]);
+  }
   using A = Arith<R>;
   typename A::Mag amax = 0;
   // r = f - (T_M u) - h^-2 sum_q (u_p - u_q): every difference is formed before
@@ -79,7 +84,7 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<R>(BLOCK))
       }
     }
   };
-  fft_inverse(buf, t, sh, tw, v, store);
+  fft_inverse<E>(buf, t, sh, tw, v, store, sync);
 
   if (norm_bits != nullptr) {
     double a = (double)amax;
@@ -96,72 +101,68 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<R>(BLOCK))
   }
 }
 
-template <class R, class RO, int BLOCK, class SH>
+template <class R, class RO, int BLOCK, class SH, int E>
 cudaError_t defect_launch(dim3 grid, size_t smem, cudaStream_t s, const R* u, const R* f, RO* r,
                           const Cx<R>* tspec, const Cx<R>* tw, const R* zero, int d, int n, int M,
                           int logL, R hinv2, int npts, int npairs, unsigned long long* norm_bits,
                           size_t fstride, size_t sstride) {
-  cudaError_t e = prepare_smem(k_defect<R, RO, BLOCK, SH>, smem);
+  cudaError_t e = prepare_smem(k_defect<R, RO, BLOCK, SH, E>, smem);
   if (e != cudaSuccess) return e;
-  k_defect<R, RO, BLOCK, SH><<<grid, BLOCK, smem, s>>>(u, f, r, tspec, tw, zero, d, n, M, logL,
-                                                       hinv2, npts, npairs, norm_bits, fstride,
-                                                       sstride);
+  k_defect<R, RO, BLOCK, SH, E><<<grid, BLOCK, smem, s>>>(u, f, r, tspec, tw, zero, d, n, M,
+                                                          logL, hinv2, npts, npairs, norm_bits,
+                                                          fstride, sstride);
   return cudaSuccess;
 }
 
 template <class R, class RO>
 cudaError_t launch_defect(const R* u, const R* f, RO* r, const Cx<R>* tspec, size_t spec_stride,
                           const Cx<R>* tw, const R* zero, Cx<R>* scratch, const LevelShape& ls,
-                          R hinv2, unsigned long long* norm_bits, cudaStream_t s) {
+                          R hinv2, unsigned long long* norm_bits, int E, cudaStream_t s) {
   if (ls.M > kShortMaxM)
     return launch_defect_long<R, RO>(u, f, r, tspec, spec_stride, tw, scratch, ls, hinv2,
-                                     norm_bits, s);
+                                     norm_bits, E, s);
   const int d = ls.d, n = ls.n, M = ls.M;
   const int L = 2 * M, logL = ilog2(L);
+  E = effective_split(M, (int)sizeof(R) == 4 ? 4 : 8, E);
   const int npts = d == 1 ? n : n * n;
   const int npairs = (npts + 1) / 2;
   if (ls.batch == 0) return cudaSuccess;
   const size_t fstride = ls.field_stride();
-  const int block = block_threads(L);
-  const int groups = block / (L / 8);
+  const int TL = L / (8 * E);
+  const int block = TL > 256 ? TL : 256;
+  const int groups = block / TL;
   const size_t smem = (size_t)groups * Pad<R>::len(L) * sizeof(Cx<R>);
   const dim3 grid((unsigned)((npairs + groups - 1) / groups), (unsigned)ls.batch);
-  cudaError_t e;
+  cudaError_t e = cudaErrorInvalidValue;
+#define MGWR_DEFECT_ARGS \
+  grid, smem, s, u, f, r, tspec, tw, zero, d, n, M, logL, hinv2, npts, npairs, norm_bits, fstride, spec_stride
   if constexpr (sizeof(R) == 4) {
-    switch (logL) {
-#define MGWR_CASE(LG)                                                                          \
-  case LG:                                                                                     \
-    e = defect_launch<R, RO, ((1 << LG) / 8 > 256 ? (1 << LG) / 8 : 256), FixedShape<LG>>(     \
-        grid, smem, s, u, f, r, tspec, tw, zero, d, n, M, logL, hinv2, npts, npairs, norm_bits, \
-        fstride, spec_stride);                                                                 \
+    switch (logL * 8 + E) {
+#define MGWR_CASE_E(LG, EE)                                                                       \
+  case LG * 8 + EE:                                                                               \
+    e = defect_launch<R, RO, ((1 << LG) / (8 * EE) > 256 ? (1 << LG) / (8 * EE) : 256),          \
+                      FixedShape<LG>, EE>(MGWR_DEFECT_ARGS);                                      \
     break;
+#define MGWR_CASE(LG) MGWR_CASE_E(LG, 1) MGWR_CASE_E(LG, 2) MGWR_CASE_E(LG, 4)
       MGWR_FIXED_LOGL(MGWR_CASE)
 #undef MGWR_CASE
+#undef MGWR_CASE_E
       default:
-        e = defect_launch<R, RO, 256, FftShape>(grid, smem, s, u, f, r, tspec, tw, zero, d, n, M,
-                                                logL, hinv2, npts, npairs, norm_bits, fstride,
-                                                spec_stride);
+        e = defect_launch<R, RO, 256, FftShape, 1>(MGWR_DEFECT_ARGS);
         break;
     }
   } else {
-    switch (block) {
-      case 256:
-        e = defect_launch<R, RO, 256, FftShape>(grid, smem, s, u, f, r, tspec, tw, zero, d, n, M,
-                                                logL, hinv2, npts, npairs, norm_bits, fstride,
-                                                spec_stride);
-        break;
-      case 512:
-        e = defect_launch<R, RO, 512, FftShape>(grid, smem, s, u, f, r, tspec, tw, zero, d, n, M,
-                                                logL, hinv2, npts, npairs, norm_bits, fstride,
-                                                spec_stride);
-        break;
-      default:
-        e = defect_launch<R, RO, 1024, FftShape>(grid, smem, s, u, f, r, tspec, tw, zero, d, n,
-                                                 M, logL, hinv2, npts, npairs, norm_bits, fstride,
-                                                 spec_stride);
-        break;
+    switch (block * 8 + E) {
+      case 256 * 8 + 1: e = defect_launch<R, RO, 256, FftShape, 1>(MGWR_DEFECT_ARGS); break;
+      case 512 * 8 + 1: e = defect_launch<R, RO, 512, FftShape, 1>(MGWR_DEFECT_ARGS); break;
+      case 1024 * 8 + 1: e = defect_launch<R, RO, 1024, FftShape, 1>(MGWR_DEFECT_ARGS); break;
+      case 256 * 8 + 2: e = defect_launch<R, RO, 256, FftShape, 2>(MGWR_DEFECT_ARGS); break;
+      case 512 * 8 + 2: e = defect_launch<R, RO, 512, FftShape, 2>(MGWR_DEFECT_ARGS); break;
+      case 256 * 8 + 4: e = defect_launch<R, RO, 256, FftShape, 4>(MGWR_DEFECT_ARGS); break;
+      default: break;
     }
   }
+#undef MGWR_DEFECT_ARGS
   if (e != cudaSuccess) return e;
   return counted(cudaGetLastError());
 }

@@ -4,6 +4,6 @@
 namespace mgwr {
 template cudaError_t launch_defect<dd, float>(const dd*, const dd*, float*, const Cx<dd>*, size_t,
                                               const Cx<dd>*, const dd*, Cx<dd>*, const LevelShape&,
-                                              dd, unsigned long long*, cudaStream_t);
+                                              dd, unsigned long long*, int, cudaStream_t);
 
 }  // namespace mgwr

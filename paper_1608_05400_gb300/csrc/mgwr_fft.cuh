@@ -7,10 +7,13 @@
 // real lines are packed as the real and imaginary parts of one complex line, so
 // one complex transform serves two spatial points.
 //
-// One thread group of L/8 threads owns one line pair.  Forward transform:
-// decimation in frequency, radix-8 stages (the first one reads the input from
-// global memory and skips the zero upper half), a last stage of radix 8, 4 or
-// 2 whose butterflies each thread does on 8 contiguous values.  The spectrum
+// One thread group of L/(8E) threads owns one line pair; each thread does E
+// radix-8 butterflies per stage (E = 1, 2 or 4: the launch shape, chosen per
+// length and arithmetic by the tuner; groups of at most 32 threads synchronise
+// with warp barriers only).  Forward transform: decimation in frequency,
+// radix-8 stages (the first one reads the input from global memory and skips
+// the zero upper half), a last stage of radix 8, 4 or 2 whose butterflies each
+// thread does on 8 contiguous values.  The spectrum
 // product is applied in registers right there, followed by the matching
 // inverse stage, so the result never needs reordering: the inverse cascade
 // runs the forward one backwards with conjugate twiddles and writes only the
@@ -169,15 +172,45 @@ __device__ __forceinline__ void twiddle_mul(Cx<R> (&v)[8], const Cx<R>* __restri
   }
 }
 
-// Radix-8 middle stage k (span L >> 3(k+1)), forward or inverse, in shared memory.
+// Barrier of the thread group that owns one line pair: the warp barrier when
+// the group fits in a warp, a named barrier (id 1 + group index) when several
+// groups of whole warps share the CTA, the CTA barrier when the group is the
+// CTA.  All three order the group's shared-memory accesses.
+struct GroupSync {
+  int kind;  // 0: CTA, 1: warp, 2: named
+  int id, nthreads;
+  __device__ __forceinline__ GroupSync(int group_threads, int block_threads, int group) {
+    if (group_threads >= block_threads) {
+      kind = 0;
+    } else if (group_threads <= 32) {
+      kind = 1;
+    } else {
+      kind = 2;
+    }
+    id = 1 + group;
+    nthreads = group_threads;
+  }
+  __device__ __forceinline__ void operator()() const {
+    if (kind == 0) {
+      __syncthreads();
+    } else if (kind == 1) {
+      __syncwarp();
+    } else {
+      asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+    }
+  }
+};
+
+// Radix-8 middle stage k (span L >> 3(k+1)) of butterfly b, forward or inverse,
+// in shared memory.
 template <bool INV, class R, class SH>
-__device__ __forceinline__ void middle_stage(Cx<R>* buf, int t, const SH& sh, int k,
+__device__ __forceinline__ void middle_stage(Cx<R>* buf, int b, const SH& sh, int k,
                                              const Cx<R>* __restrict__ tw) {
   using P = Pad<R>;
   const int shift = 3 * (k + 1);
   const int s = sh.L >> shift;
-  const int j = t & (s - 1);
-  const int base = ((t - j) << 3) + j;
+  const int j = b & (s - 1);
+  const int base = ((b - j) << 3) + j;
   Cx<R> v[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) v[q] = buf[P::idx(base + q * s)];
@@ -192,83 +225,111 @@ __device__ __forceinline__ void middle_stage(Cx<R>* buf, int t, const SH& sh, in
   for (int q = 0; q < 8; ++q) buf[P::idx(base + q * s)] = v[q];
 }
 
-// Forward transform of one line pair.  `load(m)` returns the pair's input at
-// time index m (called for m = t + q L/8, q < 4: the upper half of the line is
-// zero padding; with FULL, q < 8: every position carries data).  On return the
-// thread holds, in v, the transform values at spectral positions 8t .. 8t+7.
-// Every thread of the block must call this (it synchronises the block).
-template <class R, class SH, class Load, bool FULL = false>
+// Forward transform of one line pair by a group of T = L/(8E) threads: thread
+// t does the radix-8 butterflies b = t + eT, e < E, of every stage.  `load(m)`
+// returns the pair's input at time index m (called for m = b + q L/8, q < 4:
+// the upper half of the line is zero padding; with FULL, q < 8: every position
+// carries data).  On return the thread holds, in v[e], the transform values at
+// spectral positions 8b .. 8b+7 of its butterfly b = t + eT.  Every thread of
+// the group must call this (it synchronises the group through `sync`).
+template <int E, class R, class SH, class Load, bool FULL = false>
 __device__ __forceinline__ void fft_forward(Cx<R>* buf, int t, const SH& sh,
-                                            const Cx<R>* __restrict__ tw, Load load, Cx<R> (&v)[8]) {
+                                            const Cx<R>* __restrict__ tw, Load load,
+                                            Cx<R> (&v)[E][8], const GroupSync& sync) {
   using P = Pad<R>;
-  if constexpr (FULL) {
+  const int T = sh.L8 / E;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) v[q] = load(t + q * sh.L8);
-    dft8<false>(v);
-  } else {
+  for (int e = 0; e < E; ++e) {
+    const int b = t + e * T;
+    if constexpr (FULL) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) v[q] = load(t + q * sh.L8);
-    dft8_half_input(v);
+      for (int q = 0; q < 8; ++q) v[e][q] = load(b + q * sh.L8);
+      dft8<false>(v[e]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) v[e][q] = load(b + q * sh.L8);
+      dft8_half_input(v[e]);
+    }
+    if (sh.logL == 3) return;  // single stage: thread 0 holds positions 0..7 (E = 1)
+    twiddle_mul<false>(v[e], tw, b);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) buf[P::idx(b + q * sh.L8)] = v[e][q];
   }
-  if (sh.logL == 3) return;  // single stage: thread 0 holds positions 0..7
-  twiddle_mul<false>(v, tw, t);
-#pragma unroll
-  for (int q = 0; q < 8; ++q) buf[P::idx(t + q * sh.L8)] = v[q];
-  __syncthreads();
+  sync();
   if constexpr (SH::kFixed) {
 #pragma unroll
     for (int k = 1; k < sh.kmid_end; ++k) {
-      middle_stage<false>(buf, t, sh, k, tw);
-      __syncthreads();
+#pragma unroll
+      for (int e = 0; e < E; ++e) middle_stage<false>(buf, t + e * T, sh, k, tw);
+      sync();
     }
   } else {
 #pragma unroll 1
     for (int k = 1; k < sh.kmid_end; ++k) {
-      middle_stage<false>(buf, t, sh, k, tw);
-      __syncthreads();
+#pragma unroll
+      for (int e = 0; e < E; ++e) middle_stage<false>(buf, t + e * T, sh, k, tw);
+      sync();
     }
   }
 #pragma unroll
-  for (int q = 0; q < 8; ++q) v[q] = buf[P::idx(8 * t + q)];
-  last_stage<false>(v, sh.rlast);
+  for (int e = 0; e < E; ++e) {
+    const int b = t + e * T;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[e][q] = buf[P::idx(8 * b + q)];
+    last_stage<false>(v[e], sh.rlast);
+  }
 }
 
-// Inverse transform starting from the spectral values in v (positions 8t..8t+7,
-// already multiplied).  `store(m, value)` receives the outputs for m < M.
-template <class R, class SH, class Store>
+// Inverse transform starting from the spectral values in v (v[e] at positions
+// 8b..8b+7, b = t + eT, already multiplied).  `store(m, value)` receives the
+// outputs for m < L/2.
+template <int E, class R, class SH, class Store>
 __device__ __forceinline__ void fft_inverse(Cx<R>* buf, int t, const SH& sh,
-                                            const Cx<R>* __restrict__ tw, Cx<R> (&v)[8], Store store) {
+                                            const Cx<R>* __restrict__ tw, Cx<R> (&v)[E][8],
+                                            Store store, const GroupSync& sync) {
   using P = Pad<R>;
+  const int T = sh.L8 / E;
   if (sh.logL == 3) {
-    dft8<true>(v);
+    dft8<true>(v[0]);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) store(q, v[q]);
+    for (int q = 0; q < 4; ++q) store(q, v[0][q]);
     return;
   }
-  last_stage<true>(v, sh.rlast);
-  // each thread rewrites only the 8 positions it read in fft_forward
+  // each thread rewrites only the 8E positions it read in fft_forward
 #pragma unroll
-  for (int q = 0; q < 8; ++q) buf[P::idx(8 * t + q)] = v[q];
-  __syncthreads();
+  for (int e = 0; e < E; ++e) {
+    const int b = t + e * T;
+    last_stage<true>(v[e], sh.rlast);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) buf[P::idx(8 * b + q)] = v[e][q];
+  }
+  sync();
   if constexpr (SH::kFixed) {
 #pragma unroll
     for (int k = sh.kmid_end - 1; k >= 1; --k) {
-      middle_stage<true>(buf, t, sh, k, tw);
-      __syncthreads();
+#pragma unroll
+      for (int e = 0; e < E; ++e) middle_stage<true>(buf, t + e * T, sh, k, tw);
+      sync();
     }
   } else {
 #pragma unroll 1
     for (int k = sh.kmid_end - 1; k >= 1; --k) {
-      middle_stage<true>(buf, t, sh, k, tw);
-      __syncthreads();
+#pragma unroll
+      for (int e = 0; e < E; ++e) middle_stage<true>(buf, t + e * T, sh, k, tw);
+      sync();
     }
   }
 #pragma unroll
-  for (int q = 0; q < 8; ++q) v[q] = buf[P::idx(t + q * sh.L8)];
-  twiddle_mul<true>(v, tw, t);
-  dft8<true>(v);
+  for (int e = 0; e < E; ++e) {
+    const int b = t + e * T;
+    Cx<R> w[8];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) store(t + q * sh.L8, v[q]);
+    for (int q = 0; q < 8; ++q) w[q] = buf[P::idx(b + q * sh.L8)];
+    twiddle_mul<true>(w, tw, b);
+    dft8<true>(w);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) store(b + q * sh.L8, w[q]);
+  }
 }
 
 }  // namespace mgwr

@@ -39,6 +39,23 @@ constexpr int kShortMaxM = 4096;
 constexpr int kLongB = 4096;
 constexpr int kMaxM = 1 << 20;
 inline int engine_length(int M) { return M <= kShortMaxM ? 2 * M : 2 * kLongB; }
+// Butterflies per thread of the FFT engine for a transform of length L:
+// E in {1, 2, 4} and at most L/8; any other request selects 1.
+inline int engine_split(int L, int E) {
+  if (E != 2 && E != 4) E = 1;
+  while (E > 1 && L / 8 < E) E >>= 1;
+  return E;
+}
+// The split a launch on lines of M values in an arithmetic of `word` bytes
+// really uses when E is requested: the partitioned convolution has E = 1 or
+// 2, the FP32 kernels split only their compile-time lengths 2^7 .. 2^13.
+inline int effective_split(int M, int word, int E) {
+  if (M > kShortMaxM) return E == 2 ? 2 : 1;
+  const int L = 2 * M;
+  E = engine_split(L, E);
+  if (word == 4 && (L < 128 || L > 8192)) E = 1;
+  return E;
+}
 // Complex values of the partitioned-convolution scratch for one launch on a
 // level of shape ls: per instance, per line pair, the spectra of all blocks.
 inline size_t long_scratch_count(const LevelShape& ls) {
@@ -59,10 +76,12 @@ inline size_t long_scratch_count(const LevelShape& ls) {
 // `zero` is a line of M zeros standing in for neighbours outside the grid.
 // For M > kShortMaxM, `scratch` holds long_scratch_count(ls) values (unused
 // otherwise, may be null).
+// E: butterflies per thread of the FFT engine (engine_split; the launch shape
+// only, results are identical for every E).
 template <class R>
 cudaError_t launch_sweep(const R* f, R* u, R* delta, const Cx<R>* spec, size_t spec_stride,
                          const Cx<R>* tw, const R* zero, Cx<R>* scratch, const LevelShape& ls,
-                         int par, bool all_points, R hinv2, cudaStream_t s);
+                         int par, bool all_points, R hinv2, int E, cudaStream_t s);
 
 // Defect after a red-black step from the black half-sweep's delta: r = 0 on the
 // black points, r = hinv2 * sum of neighbour deltas on the red points
@@ -78,7 +97,7 @@ cudaError_t launch_defect_from_delta(const R* delta, R* r, const R* zero, const 
 template <class R, class RO>
 cudaError_t launch_defect(const R* u, const R* f, RO* r, const Cx<R>* tspec, size_t spec_stride,
                           const Cx<R>* tw, const R* zero, Cx<R>* scratch, const LevelShape& ls,
-                          R hinv2, unsigned long long* norm_bits, cudaStream_t s);
+                          R hinv2, unsigned long long* norm_bits, int E, cudaStream_t s);
 
 // The same two operations for M > kShortMaxM by partitioned convolution
 // (mgwr_long.cu); `spec` / `tspec` hold the kernel segment spectra written by
@@ -86,12 +105,12 @@ cudaError_t launch_defect(const R* u, const R* f, RO* r, const Cx<R>* tspec, siz
 template <class R>
 cudaError_t launch_sweep_long(const R* f, R* u, R* delta, const Cx<R>* spec, size_t spec_stride,
                               const Cx<R>* tw, Cx<R>* scratch, const LevelShape& ls, int par,
-                              bool all_points, R hinv2, cudaStream_t s);
+                              bool all_points, R hinv2, int E, cudaStream_t s);
 template <class R, class RO>
 cudaError_t launch_defect_long(const R* u, const R* f, RO* r, const Cx<R>* tspec,
                                size_t spec_stride, const Cx<R>* tw, Cx<R>* scratch,
                                const LevelShape& ls, R hinv2, unsigned long long* norm_bits,
-                               cudaStream_t s);
+                               int E, cudaStream_t s);
 
 // fc = full weighting of r (fine n -> coarse (n-1)/2), uc = 0.
 template <class R>

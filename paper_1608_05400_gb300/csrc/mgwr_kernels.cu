@@ -442,13 +442,14 @@ __global__ void __launch_bounds__(BLOCK)
   Cx<double>* buf = smem + g * Pad<double>::len(sh.L);
   const double* x = lines + (size_t)(valid ? line : 0) * M;
   auto load = [&](int m) -> Cx<double> { return Cx<double>{valid ? x[m] : 0.0, 0.0}; };
-  Cx<double> v[8];
-  fft_forward(buf, t, sh, tw, load, v);
+  Cx<double> v[1][8];
+  const GroupSync sync(TL, BLOCK, g);
+  fft_forward<1>(buf, t, sh, tw, load, v, sync);
   const double inv = 1.0 / (double)sh.L;
   if (valid) {
 #pragma unroll
     for (int q = 0; q < 8; ++q)
-      spec[(size_t)line * sh.L + 8 * t + q] = Cx<double>{v[q].x * inv, v[q].y * inv};
+      spec[(size_t)line * sh.L + 8 * t + q] = Cx<double>{v[0][q].x * inv, v[0][q].y * inv};
   }
 }
 

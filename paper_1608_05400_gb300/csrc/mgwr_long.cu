@@ -14,8 +14,9 @@
 // and finishes the block (smoother update or defect with its norm).
 //
 // Spectra here (scratch and kernel segments) are stored position-major within
-// a block: the value a thread t holds in slot q sits at q * Lb/8 + t, so the
-// accumulation loop of pass 2 reads whole warps of consecutive values.
+// a block: slot q of radix-8 butterfly b sits at q * Lb/8 + b, so the
+// accumulation loop of pass 2 reads whole warps of consecutive values (for
+// every engine split E: thread t owns the butterflies t + e Lb/(8E)).
 #include <type_traits>
 
 #include "mgwr_common.cuh"
@@ -24,9 +25,12 @@ namespace mgwr {
 
 namespace {
 
-constexpr int kLb = 2 * kLongB;    // transform length
-constexpr int kLogLb = 13;         // log2(kLb)
-constexpr int kThreads = kLb / 8;  // threads per line pair (one pair per block)
+constexpr int kLb = 2 * kLongB;  // transform length
+constexpr int kLogLb = 13;       // log2(kLb)
+constexpr int kL8 = kLb / 8;     // radix-8 butterflies per stage
+// threads per line pair (one pair per block) for engine split E
+template <int E>
+constexpr int long_threads() { return kL8 / E; }
 static_assert((1 << kLogLb) == kLb, "the long path is written for kLongB = 4096");
 
 // Shape type per arithmetic: the FP32 kernels unroll the fixed length, the
@@ -52,8 +56,8 @@ __device__ __forceinline__ int pair_point(int k, int d, int n, int par, bool eve
 // parity `par`, or x = f on every point (all_points, one-point solve);
 // MODE 1 (defect): x = u on every point.
 // Block (pair * P + j, instance): input block j of one line pair.
-template <class R, int MODE>
-__global__ void __launch_bounds__(kThreads, 1)
+template <class R, int MODE, int E>
+__global__ void __launch_bounds__(long_threads<E>(), 1)
     k_long_forward(const R* __restrict__ f, const R* __restrict__ u, Cx<R>* __restrict__ scratch,
                    const Cx<R>* __restrict__ tw, int d, int n, int M, int P, int par,
                    int all_points, R hinv2, int npts, int npairs, size_t fstride) {
@@ -88,11 +92,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     return x;
   };
-  Cx<R> v[8];
-  fft_forward(buf, t, sh, tw, load, v);
+  Cx<R> v[E][8];
+  const GroupSync sync(long_threads<E>(), long_threads<E>(), 0);
+  fft_forward<E>(buf, t, sh, tw, load, v, sync);
   Cx<R>* out = scratch + (((size_t)inst * npairs + pair) * P + j) * kLb + t;
 #pragma unroll
-  for (int q = 0; q < 8; ++q) out[q * kThreads] = v[q];
+  for (int e = 0; e < E; ++e)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) out[q * kL8 + e * long_threads<E>()] = v[e][q];
 }
 
 // ---- pass 2: accumulate, invert, finish ------------------------------------------
@@ -100,8 +107,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 // Block (pair * P + i, instance): output block i of one line pair.
 // MODE 0: u = y (delta = y - u_old when delta != null); MODE 1: r = f - y -
 // hinv2 * sum of (u_p - u_q), with |r|_inf folded into norm_bits[instance].
-template <class R, class RO, int MODE>
-__global__ void __launch_bounds__(kThreads, 1)
+template <class R, class RO, int MODE, int E>
+__global__ void __launch_bounds__(long_threads<E>(), 1)
     k_long_inverse(const R* __restrict__ f, R* __restrict__ u, R* __restrict__ delta,
                    RO* __restrict__ r, const Cx<R>* __restrict__ scratch,
                    const Cx<R>* __restrict__ seg, size_t seg_stride,
@@ -109,7 +116,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                    int all_points, R hinv2, int npts, int npairs, size_t fstride,
                    unsigned long long* __restrict__ norm_bits) {
   extern __shared__ unsigned char smem_raw[];
-  __shared__ double red[kThreads / 32];
+  __shared__ double red[long_threads<E>() / 32];
   const int pair = blockIdx.x / P, i = blockIdx.x - pair * P, inst = blockIdx.y;
   f += inst * fstride;
   u += inst * fstride;
@@ -130,15 +137,21 @@ __global__ void __launch_bounds__(kThreads, 1)
   // spectrum of output block i: sum over input blocks j <= i of K(i - j) . X(j)
   const Cx<R>* xs = scratch + ((size_t)inst * npairs + pair) * P * kLb + t;
   const Cx<R>* ks = seg + t;
-  Cx<R> v[8];
+  constexpr int TL = long_threads<E>();
+  Cx<R> v[E][8];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) v[q] = Cx<R>{R(0), R(0)};
+  for (int e = 0; e < E; ++e)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[e][q] = Cx<R>{R(0), R(0)};
 #pragma unroll 1
   for (int jb = 0; jb <= i; ++jb) {
     const Cx<R>* xj = xs + (size_t)jb * kLb;
     const Cx<R>* kd = ks + (size_t)(i - jb) * kLb;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) v[q] = cadd(v[q], cmul(xj[q * kThreads], kd[q * kThreads]));
+    for (int e = 0; e < E; ++e)
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        v[e][q] = cadd(v[e][q], cmul(xj[q * kL8 + e * TL], kd[q * kL8 + e * TL]));
   }
 
   const int m0 = i * kLongB;
@@ -166,7 +179,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   };
-  fft_inverse(buf, t, sh, tw, v, store);
+  const GroupSync sync(TL, TL, 0);
+  fft_inverse<E>(buf, t, sh, tw, v, store, sync);
 
   if constexpr (MODE == 1) {
     if (norm_bits != nullptr) {
@@ -176,7 +190,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
       __syncthreads();
       if (threadIdx.x < 32) {
-        a = red[threadIdx.x];  // kThreads / 32 == 32 partial maxima
+        a = threadIdx.x < TL / 32 ? red[threadIdx.x] : 0.0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) a = absmax_nan(__shfl_xor_sync(0xffffffffu, a, o), a);
         if (threadIdx.x == 0) atomic_max_nonneg(norm_bits + inst, a);
@@ -191,7 +205,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 // length-M kernel `lines[line]`: c[s] = k[dseg B + s] for 0 <= s < B,
 // c[Lb + s] = k[dseg B + s] for -B < s < 0 (zero where the lag leaves
 // [0, M)), c[B] = 0; scaled by 1/Lb, position-major.
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kL8, 1)
     k_long_spectra(Cx<double>* __restrict__ spec, const double* __restrict__ lines, int M, int P,
                    const Cx<double>* __restrict__ tw) {
   extern __shared__ unsigned char smem_raw[];
@@ -203,20 +217,40 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int lag = s < kLongB ? dseg * kLongB + s : (s > kLongB ? dseg * kLongB + s - kLb : -1);
     return Cx<double>{lag >= 0 && lag < M ? k[lag] : 0.0, 0.0};
   };
-  Cx<double> v[8];
-  fft_forward<double, FftShape, decltype(load), true>(buf, threadIdx.x, sh, tw, load, v);
+  Cx<double> v[1][8];
+  const GroupSync sync(kL8, kL8, 0);
+  fft_forward<1, double, FftShape, decltype(load), true>(buf, threadIdx.x, sh, tw, load, v, sync);
   const double inv = 1.0 / (double)kLb;
   Cx<double>* out = spec + ((size_t)line * P + dseg) * kLb + threadIdx.x;
 #pragma unroll
-  for (int q = 0; q < 8; ++q) out[q * kThreads] = Cx<double>{v[q].x * inv, v[q].y * inv};
+  for (int q = 0; q < 8; ++q) out[q * kL8] = Cx<double>{v[0][q].x * inv, v[0][q].y * inv};
 }
 
 // ---- launchers -------------------------------------------------------------------
 
+template <class R, int E>
+cudaError_t sweep_long_launch(dim3 grid, size_t smem, cudaStream_t s, const R* f, R* u, R* delta,
+                              const Cx<R>* spec, size_t spec_stride, const Cx<R>* tw,
+                              Cx<R>* scratch, int d, int n, int M, int P, int par, int all_points,
+                              R hinv2, int npts, int npairs, size_t fstride) {
+  cudaError_t e = prepare_smem(k_long_forward<R, 0, E>, smem);
+  if (e != cudaSuccess) return e;
+  k_long_forward<R, 0, E><<<grid, long_threads<E>(), smem, s>>>(
+      f, u, scratch, tw, d, n, M, P, par, all_points, hinv2, npts, npairs, fstride);
+  e = counted(cudaGetLastError());
+  if (e != cudaSuccess) return e;
+  e = prepare_smem(k_long_inverse<R, R, 0, E>, smem);
+  if (e != cudaSuccess) return e;
+  k_long_inverse<R, R, 0, E><<<grid, long_threads<E>(), smem, s>>>(
+      f, u, delta, (R*)nullptr, scratch, spec, spec_stride, tw, d, n, M, P, par, all_points,
+      hinv2, npts, npairs, fstride, nullptr);
+  return counted(cudaGetLastError());
+}
+
 template <class R>
 cudaError_t launch_sweep_long(const R* f, R* u, R* delta, const Cx<R>* spec, size_t spec_stride,
                               const Cx<R>* tw, Cx<R>* scratch, const LevelShape& ls, int par,
-                              bool all_points, R hinv2, cudaStream_t s) {
+                              bool all_points, R hinv2, int E, cudaStream_t s) {
   const int d = ls.d, n = ls.n, M = ls.M, P = M / kLongB;
   const int npts = all_points ? (d == 1 ? n : n * n) : colour_count(d, n, par);
   const int npairs = (npts + 1) / 2;
@@ -225,18 +259,29 @@ cudaError_t launch_sweep_long(const R* f, R* u, R* delta, const Cx<R>* spec, siz
   const size_t smem = (size_t)Pad<R>::len(kLb) * sizeof(Cx<R>);
   const dim3 grid((unsigned)((size_t)npairs * P), (unsigned)ls.batch);
   const size_t fstride = ls.field_stride();
-  cudaError_t e = prepare_smem(k_long_forward<R, 0>, smem);
+  if (effective_split(M, 8, E) == 2)
+    return sweep_long_launch<R, 2>(grid, smem, s, f, u, delta, spec, spec_stride, tw, scratch, d,
+                                   n, M, P, par, all_points ? 1 : 0, hinv2, npts, npairs, fstride);
+  return sweep_long_launch<R, 1>(grid, smem, s, f, u, delta, spec, spec_stride, tw, scratch, d, n,
+                                 M, P, par, all_points ? 1 : 0, hinv2, npts, npairs, fstride);
+}
+
+template <class R, class RO, int E>
+cudaError_t defect_long_launch(dim3 grid, size_t smem, cudaStream_t s, const R* u, const R* f,
+                               RO* r, const Cx<R>* tspec, size_t spec_stride, const Cx<R>* tw,
+                               Cx<R>* scratch, int d, int n, int M, int P, R hinv2, int npts,
+                               int npairs, size_t fstride, unsigned long long* norm_bits) {
+  cudaError_t e = prepare_smem(k_long_forward<R, 1, E>, smem);
   if (e != cudaSuccess) return e;
-  k_long_forward<R, 0><<<grid, kThreads, smem, s>>>(f, u, scratch, tw, d, n, M, P, par,
-                                                    all_points ? 1 : 0, hinv2, npts, npairs,
-                                                    fstride);
+  k_long_forward<R, 1, E><<<grid, long_threads<E>(), smem, s>>>(
+      f, u, scratch, tw, d, n, M, P, 0, 1, hinv2, npts, npairs, fstride);
   e = counted(cudaGetLastError());
   if (e != cudaSuccess) return e;
-  e = prepare_smem(k_long_inverse<R, R, 0>, smem);
+  e = prepare_smem(k_long_inverse<R, RO, 1, E>, smem);
   if (e != cudaSuccess) return e;
-  k_long_inverse<R, R, 0><<<grid, kThreads, smem, s>>>(
-      f, u, delta, (R*)nullptr, scratch, spec, spec_stride, tw, d, n, M, P, par,
-      all_points ? 1 : 0, hinv2, npts, npairs, fstride, nullptr);
+  k_long_inverse<R, RO, 1, E><<<grid, long_threads<E>(), smem, s>>>(
+      f, const_cast<R*>(u), (R*)nullptr, r, scratch, tspec, spec_stride, tw, d, n, M, P, 0, 1,
+      hinv2, npts, npairs, fstride, norm_bits);
   return counted(cudaGetLastError());
 }
 
@@ -244,7 +289,7 @@ template <class R, class RO>
 cudaError_t launch_defect_long(const R* u, const R* f, RO* r, const Cx<R>* tspec,
                                size_t spec_stride, const Cx<R>* tw, Cx<R>* scratch,
                                const LevelShape& ls, R hinv2, unsigned long long* norm_bits,
-                               cudaStream_t s) {
+                               int E, cudaStream_t s) {
   const int d = ls.d, n = ls.n, M = ls.M, P = M / kLongB;
   const int npts = d == 1 ? n : n * n;
   const int npairs = (npts + 1) / 2;
@@ -253,18 +298,11 @@ cudaError_t launch_defect_long(const R* u, const R* f, RO* r, const Cx<R>* tspec
   const size_t smem = (size_t)Pad<R>::len(kLb) * sizeof(Cx<R>);
   const dim3 grid((unsigned)((size_t)npairs * P), (unsigned)ls.batch);
   const size_t fstride = ls.field_stride();
-  cudaError_t e = prepare_smem(k_long_forward<R, 1>, smem);
-  if (e != cudaSuccess) return e;
-  k_long_forward<R, 1><<<grid, kThreads, smem, s>>>(f, u, scratch, tw, d, n, M, P, 0, 1, hinv2,
-                                                    npts, npairs, fstride);
-  e = counted(cudaGetLastError());
-  if (e != cudaSuccess) return e;
-  e = prepare_smem(k_long_inverse<R, RO, 1>, smem);
-  if (e != cudaSuccess) return e;
-  k_long_inverse<R, RO, 1><<<grid, kThreads, smem, s>>>(
-      f, const_cast<R*>(u), (R*)nullptr, r, scratch, tspec, spec_stride, tw, d, n, M, P, 0, 1,
-      hinv2, npts, npairs, fstride, norm_bits);
-  return counted(cudaGetLastError());
+  if (effective_split(M, 8, E) == 2)
+    return defect_long_launch<R, RO, 2>(grid, smem, s, u, f, r, tspec, spec_stride, tw, scratch,
+                                        d, n, M, P, hinv2, npts, npairs, fstride, norm_bits);
+  return defect_long_launch<R, RO, 1>(grid, smem, s, u, f, r, tspec, spec_stride, tw, scratch, d,
+                                      n, M, P, hinv2, npts, npairs, fstride, norm_bits);
 }
 
 cudaError_t launch_spectra_long(Cx<double>* spec, const double* lines, int count, int M,
@@ -275,22 +313,23 @@ cudaError_t launch_spectra_long(Cx<double>* spec, const double* lines, int count
   const size_t smem = (size_t)Pad<double>::len(kLb) * sizeof(Cx<double>);
   cudaError_t e = prepare_smem(k_long_spectra, smem);
   if (e != cudaSuccess) return e;
-  k_long_spectra<<<dim3((unsigned)count, (unsigned)P), kThreads, smem, s>>>(spec, lines, M, P, tw);
+  k_long_spectra<<<dim3((unsigned)count, (unsigned)P), kL8, smem, s>>>(spec, lines, M, P, tw);
   return counted(cudaGetLastError());
 }
 
 template cudaError_t launch_sweep_long<double>(const double*, double*, double*, const Cx<double>*,
                                                size_t, const Cx<double>*, Cx<double>*,
-                                               const LevelShape&, int, bool, double,
+                                               const LevelShape&, int, bool, double, int,
                                                cudaStream_t);
 template cudaError_t launch_sweep_long<float>(const float*, float*, float*, const Cx<float>*,
                                               size_t, const Cx<float>*, Cx<float>*,
-                                              const LevelShape&, int, bool, float, cudaStream_t);
+                                              const LevelShape&, int, bool, float, int,
+                                              cudaStream_t);
 #define MGWR_INST_LONG_DEFECT(R, RO)                                                          \
   template cudaError_t launch_defect_long<R, RO>(const R*, const R*, RO*, const Cx<R>*,        \
                                                  size_t, const Cx<R>*, Cx<R>*,                 \
                                                  const LevelShape&, R, unsigned long long*,    \
-                                                 cudaStream_t);
+                                                 int, cudaStream_t);
 MGWR_INST_LONG_DEFECT(double, double)
 MGWR_INST_LONG_DEFECT(double, float)
 MGWR_INST_LONG_DEFECT(float, float)

@@ -7,8 +7,8 @@ namespace mgwr {
 // smoother: one colour half-sweep (Sec. 3 Eq. red-black, Sec. 6 Eq. red-black_2d)
 // ---------------------------------------------------------------------------------
 
-template <class R, int BLOCK, class SH>
-__global__ void __launch_bounds__(BLOCK, min_blocks<R>(BLOCK))
+template <class R, int BLOCK, class SH, int E>
+__global__ void __launch_bounds__(BLOCK, min_blocks<R>(BLOCK, E))
     k_sweep(const R* __restrict__ f, R* __restrict__ u, R* __restrict__ delta,
             const Cx<R>* __restrict__ spec, const Cx<R>* __restrict__ tw,
             const R* __restrict__ zero, int d, int n, int M, int logL, int par, int all_points,
@@ -21,12 +21,13 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<R>(BLOCK))
   spec += blockIdx.y * sstride;
   Cx<R>* smem = reinterpret_cast<Cx<R>*>(smem_raw);
   const SH sh(logL);
-  const int TL = sh.L8;
+  const int TL = sh.L8 / E;  // threads per line pair
   const int g = threadIdx.x / TL;
   const int t = threadIdx.x - g * TL;
   const int groups = BLOCK / TL;
   const int pair = blockIdx.x * groups + g;
   Cx<R>* buf = smem + g * Pad<R>::len(sh.L);
+  const GroupSync sync(TL, BLOCK, g);
 
   const bool valid = pair < npairs;
   const int kA = 2 * pair, kB = 2 * pair + 1;
@@ -67,10 +68,14 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<R>(BLOCK))
       return b;
     }
   };
-  Cx<R> v[8];
-  fft_forward(buf, t, sh, tw, load, v);
+  Cx<R> v[E][8];
+  fft_forward<E>(buf, t, sh, tw, load, v, sync);
 #pragma unroll
-  for (int q = 0; q < 8; ++q) v[q] = cmul(v[q], spec[8 * t + q]);
+  for (int e = 0; e < E; ++e) {
+    const int b = t + e * TL;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[e][q] = cmul(v[e][q], spec[8 * b + q]);
+  }
   R* uA = u + pAM;
   R* uB = u + pBM;
   auto store = [&](int m, Cx<R> y) {
@@ -83,84 +88,81 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<R>(BLOCK))
       }
     }
   };
-  fft_inverse(buf, t, sh, tw, v, store);
+  fft_inverse<E>(buf, t, sh, tw, v, store, sync);
 }
 
-template <class R, int BLOCK, class SH>
+template <class R, int BLOCK, class SH, int E>
 cudaError_t sweep_launch(dim3 grid, size_t smem, cudaStream_t s, const R* f, R* u, R* delta,
                          const Cx<R>* spec, const Cx<R>* tw, const R* zero, int d, int n, int M,
                          int logL, int par, bool all_points, R hinv2, int npts, int npairs,
                          size_t fstride, size_t sstride) {
-  cudaError_t e = prepare_smem(k_sweep<R, BLOCK, SH>, smem);
+  cudaError_t e = prepare_smem(k_sweep<R, BLOCK, SH, E>, smem);
   if (e != cudaSuccess) return e;
-  k_sweep<R, BLOCK, SH><<<grid, BLOCK, smem, s>>>(f, u, delta, spec, tw, zero, d, n, M, logL, par,
-                                                  all_points, hinv2, npts, npairs, fstride,
-                                                  sstride);
+  k_sweep<R, BLOCK, SH, E><<<grid, BLOCK, smem, s>>>(f, u, delta, spec, tw, zero, d, n, M, logL,
+                                                     par, all_points, hinv2, npts, npairs, fstride,
+                                                     sstride);
   return cudaSuccess;
 }
 
 template <class R>
 cudaError_t launch_sweep(const R* f, R* u, R* delta, const Cx<R>* spec, size_t spec_stride,
                          const Cx<R>* tw, const R* zero, Cx<R>* scratch, const LevelShape& ls,
-                         int par, bool all_points, R hinv2, cudaStream_t s) {
+                         int par, bool all_points, R hinv2, int E, cudaStream_t s) {
   if (ls.M > kShortMaxM)
     return launch_sweep_long(f, u, delta, spec, spec_stride, tw, scratch, ls, par, all_points,
-                             hinv2, s);
+                             hinv2, E, s);
   const int d = ls.d, n = ls.n, M = ls.M;
   const int L = 2 * M, logL = ilog2(L);
+  E = effective_split(M, (int)sizeof(R) == 4 ? 4 : 8, E);
   const int npts = all_points ? (d == 1 ? n : n * n) : colour_count(d, n, par);
   const int npairs = (npts + 1) / 2;
   if (npairs == 0 || ls.batch == 0) return cudaSuccess;
   const size_t fstride = ls.field_stride();
-  const int block = block_threads(L);
-  const int groups = block / (L / 8);
+  const int TL = L / (8 * E);
+  const int block = TL > 256 ? TL : 256;
+  const int groups = block / TL;
   const size_t smem = (size_t)groups * Pad<R>::len(L) * sizeof(Cx<R>);
   const dim3 grid((unsigned)((npairs + groups - 1) / groups), (unsigned)ls.batch);
-  cudaError_t e;
+  cudaError_t e = cudaErrorInvalidValue;
+#define MGWR_SWEEP_ARGS                                                                     \
+  grid, smem, s, f, u, delta, spec, tw, zero, d, n, M, logL, par, all_points, hinv2, npts, \
+      npairs, fstride, spec_stride
   if constexpr (sizeof(R) == 4) {
-    switch (logL) {
-#define MGWR_CASE(LG)                                                                            \
-  case LG:                                                                                       \
-    e = sweep_launch<R, ((1 << LG) / 8 > 256 ? (1 << LG) / 8 : 256), FixedShape<LG>>(            \
-        grid, smem, s, f, u, delta, spec, tw, zero, d, n, M, logL, par, all_points, hinv2, npts, \
-        npairs, fstride, spec_stride);                                                           \
+    switch (logL * 8 + E) {
+#define MGWR_CASE_E(LG, EE)                                                                   \
+  case LG * 8 + EE:                                                                           \
+    e = sweep_launch<R, ((1 << LG) / (8 * EE) > 256 ? (1 << LG) / (8 * EE) : 256), FixedShape<LG>, \
+                     EE>(MGWR_SWEEP_ARGS);                                                    \
     break;
+#define MGWR_CASE(LG) MGWR_CASE_E(LG, 1) MGWR_CASE_E(LG, 2) MGWR_CASE_E(LG, 4)
       MGWR_FIXED_LOGL(MGWR_CASE)
 #undef MGWR_CASE
+#undef MGWR_CASE_E
       default:
-        e = sweep_launch<R, 256, FftShape>(grid, smem, s, f, u, delta, spec, tw, zero, d, n, M,
-                                           logL, par, all_points, hinv2, npts, npairs, fstride,
-                                           spec_stride);
+        e = sweep_launch<R, 256, FftShape, 1>(MGWR_SWEEP_ARGS);
         break;
     }
   } else {
-    switch (block) {
-      case 256:
-        e = sweep_launch<R, 256, FftShape>(grid, smem, s, f, u, delta, spec, tw, zero, d, n, M,
-                                           logL, par, all_points, hinv2, npts, npairs, fstride,
-                                           spec_stride);
-        break;
-      case 512:
-        e = sweep_launch<R, 512, FftShape>(grid, smem, s, f, u, delta, spec, tw, zero, d, n, M,
-                                           logL, par, all_points, hinv2, npts, npairs, fstride,
-                                           spec_stride);
-        break;
-      default:
-        e = sweep_launch<R, 1024, FftShape>(grid, smem, s, f, u, delta, spec, tw, zero, d, n, M,
-                                            logL, par, all_points, hinv2, npts, npairs, fstride,
-                                            spec_stride);
-        break;
+    switch (block * 8 + E) {
+      case 256 * 8 + 1: e = sweep_launch<R, 256, FftShape, 1>(MGWR_SWEEP_ARGS); break;
+      case 512 * 8 + 1: e = sweep_launch<R, 512, FftShape, 1>(MGWR_SWEEP_ARGS); break;
+      case 1024 * 8 + 1: e = sweep_launch<R, 1024, FftShape, 1>(MGWR_SWEEP_ARGS); break;
+      case 256 * 8 + 2: e = sweep_launch<R, 256, FftShape, 2>(MGWR_SWEEP_ARGS); break;
+      case 512 * 8 + 2: e = sweep_launch<R, 512, FftShape, 2>(MGWR_SWEEP_ARGS); break;
+      case 256 * 8 + 4: e = sweep_launch<R, 256, FftShape, 4>(MGWR_SWEEP_ARGS); break;
+      default: break;
     }
   }
+#undef MGWR_SWEEP_ARGS
   if (e != cudaSuccess) return e;
   return counted(cudaGetLastError());
 }
 
 template cudaError_t launch_sweep<double>(const double*, double*, double*, const Cx<double>*,
                                           size_t, const Cx<double>*, const double*, Cx<double>*,
-                                          const LevelShape&, int, bool, double, cudaStream_t);
+                                          const LevelShape&, int, bool, double, int, cudaStream_t);
 template cudaError_t launch_sweep<float>(const float*, float*, float*, const Cx<float>*, size_t,
                                          const Cx<float>*, const float*, Cx<float>*,
-                                         const LevelShape&, int, bool, float, cudaStream_t);
+                                         const LevelShape&, int, bool, float, int, cudaStream_t);
 
 }  // namespace mgwr

@@ -70,6 +70,9 @@ _SIGS = {
     "mgwr_set_order": (C.c_int, [_h, C.c_int]),
     "mgwr_set_stream": (C.c_int, [_h, C.c_void_p]),
     "mgwr_set_inner_cycles": (C.c_int, [_h, C.c_int]),
+    "mgwr_set_engine_split": (C.c_int, [_h, C.c_int, C.c_int]),
+    "mgwr_get_engine_split": (C.c_int, [_h, C.c_int, C.POINTER(C.c_int)]),
+    "mgwr_autotune": (C.c_int, [_h]),
     "mgwr_set_graphs": (C.c_int, [_h, C.c_int]),
     "mgwr_set_rhs": (C.c_int, [_h, _dp, _dp]),
     "mgwr_set_rhs_dev": (C.c_int, [_h, C.c_void_p, C.c_void_p]),
@@ -216,6 +219,22 @@ class Solver:
 
     def set_inner_cycles(self, k: int):
         self._check(self.lib.mgwr_set_inner_cycles(self.h, k), "mgwr_set_inner_cycles")
+
+    def set_engine_split(self, kernel_class: int, split: int):
+        self._check(self.lib.mgwr_set_engine_split(self.h, kernel_class, split),
+                    "mgwr_set_engine_split")
+
+    def engine_split(self, kernel_class: int) -> int:
+        e = C.c_int()
+        self._check(self.lib.mgwr_get_engine_split(self.h, kernel_class, C.byref(e)),
+                    "mgwr_get_engine_split")
+        return e.value
+
+    def autotune(self) -> dict:
+        """Run the launch-shape tuner; returns the split chosen per engine class."""
+        self._check(self.lib.mgwr_autotune(self.h), "mgwr_autotune")
+        return {name: self.engine_split(k) for k, name in enumerate(KERNEL_CLASSES)
+                if name in ("sweep64", "sweep32", "defect64", "defect32", "defect_dd")}
 
     # -- data --
     def set_rhs(self, f: np.ndarray, g: np.ndarray | None = None):

@@ -1,0 +1,121 @@
+"""FFT-engine launch shapes and the tuner: every split E (radix-8 butterflies per
+thread) computes the same butterflies in the same order, so sweeps and defects
+are bitwise identical for all E, and agree with the oracle; the tuner picks a
+valid split per kernel class, leaves the handle's state alone and records its
+choice for later handles of the same shape."""
+import numpy as np
+import pytest
+
+from oracle import mgwr as omg
+from paper_1608_05400_gb300 import inputs
+from paper_1608_05400_gb300 import mgwr as G
+
+pytestmark = pytest.mark.gpu
+
+K = {name: i for i, name in enumerate(G.KERNEL_CLASSES)}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    G.load()
+
+
+def rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def _run(d, n, M, hier, E, op):
+    s = G.Solver(d, n, M, 1.0, 0.45)
+    with s:
+        if hier == G.MGWR_H32:
+            s.set_precision(G.MGWR_MIXED)
+        word = "32" if hier == G.MGWR_H32 else "64"
+        s.set_engine_split(K["sweep" + word], E)
+        s.set_engine_split(K["defect" + word], E)
+        l = s.num_levels() - 1
+        N = n ** d
+        u = inputs.random_field(N, M, seed=1)
+        f = inputs.random_field(N, M, seed=2, scale=2.0 * d * (n + 1) ** 2)
+        s.field_set(hier, l, G.MGWR_U, u)
+        s.field_set(hier, l, G.MGWR_F, f)
+        if op == "sweep":
+            s.smooth(hier, l, G.MGWR_RED)
+            s.smooth(hier, l, G.MGWR_BLACK)
+            out = s.field_get(hier, l, G.MGWR_U)
+        else:
+            s.defect(hier, l)
+            out = s.field_get(hier, l, G.MGWR_R)
+        used = s.engine_split(K[op + word])
+    return out, used, u, f
+
+
+@pytest.mark.parametrize("hier", [G.MGWR_H64, G.MGWR_H32])
+@pytest.mark.parametrize("op", ["sweep", "defect"])
+@pytest.mark.parametrize("d,n,M", [(1, 15, 4), (1, 31, 16), (2, 15, 64), (1, 63, 128), (2, 31, 1024),
+                                   (1, 15, 2048), (2, 7, 4096), (1, 7, 8192)])
+def test_every_split_gives_identical_results(hier, op, d, n, M):
+    ref, used1, u, f = _run(d, n, M, hier, 1, op)
+    assert used1 == 1
+    for E in (2, 4):
+        out, used, _, _ = _run(d, n, M, hier, E, op)
+        assert used in (1, 2, 4) and used <= E
+        np.testing.assert_array_equal(out, ref)
+    # and against the oracle's direct sums
+    W = omg.WRMG(d, n, M, 1.0, 0.45) if M <= 4096 else None
+    if W is not None:
+        l = W.finest
+        if op == "sweep":
+            r = u.copy()
+            W.sweep(l, r, f, 0)
+            W.sweep(l, r, f, 1)
+        else:
+            r = W.defect(l, u, f)
+        tol = 1e-12 if hier == G.MGWR_H64 else 2e-5
+        if op == "sweep":
+            assert rel(ref, r) <= tol
+        else:
+            scale = np.abs(f).max() + W.levels[l].sigma * 2 * np.abs(u).max()
+            assert np.abs(ref - r).max() <= tol * scale
+
+
+def test_split_requests_fall_back_to_what_a_length_takes():
+    with G.Solver(1, 7, 4, 1.0, 0.5) as s:      # L = 8: one butterfly per stage
+        s.set_engine_split(K["sweep64"], 4)
+        assert s.engine_split(K["sweep64"]) == 1
+    with G.Solver(1, 7, 8192, 1.0, 0.5) as s:   # partitioned lines: E = 1 or 2
+        s.set_engine_split(K["defect64"], 4)
+        assert s.engine_split(K["defect64"]) == 1
+        s.set_engine_split(K["defect64"], 2)
+        assert s.engine_split(K["defect64"]) == 2
+        with pytest.raises(G.MGWRError):
+            s.set_engine_split(K["restrict"], 2)
+        with pytest.raises(G.MGWRError):
+            s.set_engine_split(K["sweep64"], 3)
+
+
+@pytest.mark.parametrize("precision", [G.MGWR_FP64, G.MGWR_MIXED, G.MGWR_MIXED_DD])
+def test_autotune_keeps_state_and_results(precision):
+    d, n, M = 2, 63, 256
+    f = inputs.Problem(d, n, M, 1.0, 0.4, "t2").rhs()
+    with G.Solver(d, n, M, 1.0, 0.4) as s0:
+        s0.set_precision(precision)
+        s0.set_rhs(f)
+        st0 = s0.solve(1, 1, 1, tol=1e-10, max_cycles=40)
+        u0 = s0.solution()
+    with G.Solver(d, n, M, 1.0, 0.4) as s:
+        s.set_precision(precision)
+        s.set_rhs(f)
+        s.solve(1, 1, 1, tol=1e-10, max_cycles=1, allow_noconv=True)
+        before = s.solution()
+        chosen = s.autotune()
+        assert all(v in (1, 2, 4) for v in chosen.values())
+        np.testing.assert_array_equal(s.solution(), before)  # tuning touches no state
+        s.set_rhs(f)
+        st = s.solve(1, 1, 1, tol=1e-10, max_cycles=40)
+        np.testing.assert_array_equal(s.solution(), u0)
+        assert (st.cycles, st.relres) == (st0.cycles, st0.relres)
+    # a later handle of the same shape starts with the recorded choices
+    with G.Solver(d, n, M, 1.0, 0.9) as s2:
+        s2.set_precision(precision)
+        for name, v in chosen.items():
+            assert s2.engine_split(K[name]) == v

@@ -31,6 +31,10 @@ enum RState {
   R_CURRENT = 3,  // r_l holds the defect of the current (u_l, f_l)
 };
 
+// Relative defect above which an outer step of the mixed modes computes its
+// defect in the FP32-convolution form (launch_defect_hybrid).
+constexpr double kLooseOuter = 1e-2;
+
 template <class R>
 struct Hier {
   std::vector<R*> u, f, r;        // per level: batch * N_l * M values each
@@ -81,14 +85,22 @@ struct mgwr_handle {
   bool r0_valid = false;
   std::vector<void*> allocs;
   std::string err;
-  // one solve-loop iteration captured as a CUDA graph, replayed every iteration
-  bool use_graphs = true;
   // FFT-engine split (butterflies per thread) per kernel class; 0 = default
   int split[MGWR_NUM_KERNEL_CLASSES] = {};
-  cudaGraphExec_t iter_exec = nullptr;
-  long long iter_key = -1;   // (precision, cycle, nu1, nu2, inner, order) it was captured for
-  bool iter_exact = true;    // its norms come from the full defect
-  long long iter_kernels = 0;  // kernel launches recorded in the graph
+  // solve-loop iterations captured as CUDA graphs (one per form of the
+  // iteration: settings and outer-defect form), replayed every iteration
+  bool use_graphs = true;
+  struct IterGraph {
+    long long key;        // (precision, cycle, nu1, nu2, inner, order, loose, finest state)
+    cudaGraphExec_t exec;
+    bool exact;           // its norms come from the full defect in the working precision
+    long long kernels;    // kernel launches recorded in the graph
+  };
+  std::vector<IterGraph> graphs;
+  // the finest iterate is zero (right-hand side just set without initial values)
+  bool u_zero = false;
+  // mixed modes: this iteration's outer defect takes the FP32-convolution form
+  bool loose_outer = false;
   // per-kernel-class timing (mgwr_profile): event pairs around each launch
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -150,6 +162,11 @@ int ensure_field(mgwr_t h, R** p, size_t count) {
 bool is_pow2(long long x) { return x > 0 && (x & (x - 1)) == 0; }
 
 int split_of(const mgwr_handle* h, int cls) { return h->split[cls]; }
+
+void drop_graph(mgwr_t h) {
+  for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+  h->graphs.clear();
+}
 
 // The handle's partitioned-convolution scratch viewed as complex values of R
 // (null for M <= kShortMaxM, where no launch uses it).
@@ -499,6 +516,24 @@ int enqueue_iteration(mgwr_t h, int cyc, int nu1, int nu2, bool* exact) {
       MGWR_CK(h, mgwr::launch_refine(h->h64.u[L], h->h32.u[L], cnt, h->stream));
     prof_end(h, pm);
     MGWR_TRY(clear_norms(h));
+    if (h->loose_outer && h->M <= mgwr::kShortMaxM) {
+      // large defect: FP32 time convolution, stencil and source in the iterate's arithmetic
+      const int pl = prof_begin(h, MGWR_K_DEFECT32, (double)(points(h, L) * h->B));
+      if (ddef)
+        MGWR_CK(h, mgwr::launch_defect_hybrid<mgwr::dd>(
+                       h->u_dd, h->f_dd, h->h32.f[L], h->h32.tspec, (size_t)h->L, h->h32.tw,
+                       h->zero_dd, shape(h, L), mgwr::dd(h->hinv2[L]), h->norm_bits, h->stream));
+      else
+        MGWR_CK(h, mgwr::launch_defect_hybrid<double>(
+                       h->h64.u[L], h->h64.f[L], h->h32.f[L], h->h32.tspec, (size_t)h->L,
+                       h->h32.tw, h->h64.zero, shape(h, L), h->hinv2[L], h->norm_bits, h->stream));
+      prof_end(h, pl);
+      h->h32.rs[L] = R_STALE;
+      *exact = false;
+      MGWR_CK(h, cudaMemcpyAsync(h->norm_host, h->norm_bits, sizeof(unsigned long long) * h->B,
+                                 cudaMemcpyDeviceToHost, h->stream));
+      return MGWR_OK;
+    }
     const int pd = prof_begin(h, ddef ? MGWR_K_DEFECT_DD : MGWR_K_DEFECT64, (double)(points(h, L) * h->B));
     if (ddef)
       MGWR_CK(h, (mgwr::launch_defect<mgwr::dd, float>(h->u_dd, h->f_dd, h->h32.f[L], h->tspec_dd,
@@ -524,12 +559,18 @@ int enqueue_iteration(mgwr_t h, int cyc, int nu1, int nu2, bool* exact) {
 // settings (capturing it first if needed), else enqueues the launches
 // directly; then waits and decodes the norms.
 int run_iteration(mgwr_t h, int cyc, int nu1, int nu2, std::vector<double>& norms, bool* exact) {
-  const long long key = ((((long long)h->precision * 4 + cyc) * 32 + nu1) * 32 + nu2) * 32 * 4 +
-                        (long long)h->inner * 4 + h->order;
+  // the launch sequence also depends on the state of the finest FP64 defect field
+  // it starts from (the first FP64 iteration from u = 0 restricts f itself)
+  const int rs_in = h->precision == MGWR_FP64 ? h->h64.rs[h->nlev - 1] : 0;
+  const long long key =
+      ((((((long long)h->precision * 4 + cyc) * 32 + nu1) * 32 + nu2) * 32 * 4 +
+        (long long)h->inner * 4 + h->order) * 2 + (h->loose_outer ? 1 : 0)) * 4 + rs_in;
   if (h->use_graphs && !h->profiling) {
-    if (h->iter_exec == nullptr || h->iter_key != key) {
-      if (h->iter_exec) cudaGraphExecDestroy(h->iter_exec);
-      h->iter_exec = nullptr;
+    const mgwr_handle::IterGraph* slot = nullptr;
+    for (const auto& g : h->graphs)
+      if (g.key == key) slot = &g;
+    if (slot == nullptr) {
+      if (h->graphs.size() >= 4) drop_graph(h);  // settings changed: start over
       cudaGraph_t g = nullptr;
       MGWR_CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
       bool ex = true;
@@ -544,16 +585,16 @@ int run_iteration(mgwr_t h, int cyc, int nu1, int nu2, std::vector<double>& norm
         return st;
       }
       MGWR_CK(h, e);
-      const cudaError_t ei = cudaGraphInstantiate(&h->iter_exec, g, 0);
+      cudaGraphExec_t exec = nullptr;
+      const cudaError_t ei = cudaGraphInstantiate(&exec, g, 0);
       cudaGraphDestroy(g);
       MGWR_CK(h, ei);
-      h->iter_key = key;
-      h->iter_exact = ex;
-      h->iter_kernels = captured;
+      h->graphs.push_back({key, exec, ex, captured});
+      slot = &h->graphs.back();
     }
-    MGWR_CK(h, cudaGraphLaunch(h->iter_exec, h->stream));
-    mgwr::add_launches(h->iter_kernels);
-    *exact = h->iter_exact;
+    MGWR_CK(h, cudaGraphLaunch(slot->exec, h->stream));
+    mgwr::add_launches(slot->kernels);
+    *exact = slot->exact;
   } else {
     MGWR_TRY(enqueue_iteration(h, cyc, nu1, nu2, exact));
   }
@@ -593,12 +634,6 @@ void load_tuned(mgwr_t h) {
     auto it = g_tune.find(std::make_tuple(c, h->d, h->n, h->M, h->B));
     if (it != g_tune.end()) h->split[c] = it->second;
   }
-}
-
-void drop_graph(mgwr_t h) {
-  if (h->iter_exec) cudaGraphExecDestroy(h->iter_exec);
-  h->iter_exec = nullptr;
-  h->iter_key = -1;
 }
 
 // The sample the tuner times: the finest level whose field holds at most 2^25
@@ -861,7 +896,7 @@ int mgwr_destroy(mgwr_t h) {
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
-  if (h->iter_exec) cudaGraphExecDestroy(h->iter_exec);
+  for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
   if (h->own_stream) cudaStreamDestroy(h->own_stream);
   delete h;
   return MGWR_OK;
@@ -984,6 +1019,7 @@ static int set_rhs_impl(mgwr_t h, const double* f, const double* g, cudaMemcpyKi
     MGWR_CK(h, cudaMemsetAsync(h->h64.u[L], 0, bytes, h->stream));
     MGWR_CK(h, cudaStreamSynchronize(h->stream));
   }
+  h->u_zero = g == nullptr;
   h->r0_valid = false;
   h->h64.rs[L] = R_STALE;
   return MGWR_OK;
@@ -999,6 +1035,7 @@ int mgwr_set_rhs_dev(mgwr_t h, const double* f_dev, const double* g_dev) {
 
 int mgwr_set_initial(mgwr_t h, const double* u0) {
   if (h == nullptr) return MGWR_E_INVAL;
+  h->u_zero = false;
   if (u0 == nullptr) return fail(h, MGWR_E_INVAL, "u0 must not be null");
   const int L = h->nlev - 1;
   MGWR_CK(h, cudaMemcpyAsync(h->h64.u[L], u0, level_count(h, L) * sizeof(double),
@@ -1024,6 +1061,18 @@ int mgwr_solve(mgwr_t h, int cyc, int nu1, int nu2, double tol, int max_cycles, 
   if (ddef) {
     MGWR_CK(h, mgwr::launch_split(h->u_dd, h->h64.u[L], cntL, h->stream));
     MGWR_CK(h, mgwr::launch_split(h->f_dd, h->h64.f[L], cntL, h->stream));
+  }
+  if (h->u_zero) {
+    // the defect of u = 0 is f itself (Algorithm 1 from the zero iterate)
+    MGWR_TRY(clear_norms(h));
+    MGWR_CK(h, mgwr::launch_absmax_round(h->h64.f[L], mixed ? h->h32.f[L] : nullptr,
+                                         cntL / h->B, h->B, h->norm_bits, h->stream));
+    if (mixed)
+      h->h32.rs[L] = R_STALE;
+    else
+      h->h64.rs[L] = R_ZERO_U;
+    MGWR_TRY(read_norms(h, norms));
+  } else if (ddef) {
     MGWR_TRY(finest_defect_norms_dd(h, norms));
   } else {
     MGWR_TRY(finest_defect_norms(h, norms, mixed));
@@ -1046,18 +1095,27 @@ int mgwr_solve(mgwr_t h, int cyc, int nu1, int nu2, double tol, int max_cycles, 
       break;
     }
     bool exact = true;
+    // outer defects of the mixed modes while the defect is large (above
+    // kLooseOuter of the initial one before this step) take the FP32-convolution
+    // form, whose error (about 1e-6 of |f|) is then below 1e-3 of the defect
+    h->loose_outer = mixed && rel >= kLooseOuter;
     MGWR_TRY(run_iteration(h, cyc, nu1, nu2, norms, &exact));
     cycles += mixed ? h->inner : 1;
     rel = relative(h, norms, h->relres);
     // the stopping decision is always taken on the full defect
     if (!exact && rel <= tol) {
-      MGWR_TRY(finest_defect_norms(h, norms, false));
+      if (ddef)
+        MGWR_TRY(finest_defect_norms_dd(h, norms));
+      else
+        MGWR_TRY(finest_defect_norms(h, norms, mixed));
       rel = relative(h, norms, h->relres);
       exact = true;
     }
     rel_exact = exact;
     ++outer;
   }
+  h->u_zero = false;
+  h->loose_outer = false;
   if (ddef) MGWR_CK(h, mgwr::launch_join(h->h64.u[L], h->u_dd, cntL, h->stream));
   if (!rel_exact) {  // report the full defect also when stopping on max_cycles
     MGWR_TRY(finest_defect_norms(h, norms, false));
@@ -1142,6 +1200,7 @@ static void* field_ptr(mgwr_t h, int hierarchy, int level, int which) {
 
 int mgwr_field_set(mgwr_t h, int hierarchy, int level, int which, const double* host) {
   if (h == nullptr) return MGWR_E_INVAL;
+  h->u_zero = false;
   MGWR_TRY(check_level(h, hierarchy, level));
   if (which < MGWR_U || which > MGWR_R || host == nullptr)
     return fail(h, MGWR_E_INVAL, "bad field or null pointer");
@@ -1185,6 +1244,7 @@ int mgwr_field_get(mgwr_t h, int hierarchy, int level, int which, double* host) 
 
 int mgwr_smooth(mgwr_t h, int hierarchy, int level, int colour) {
   if (h == nullptr) return MGWR_E_INVAL;
+  h->u_zero = false;
   MGWR_TRY(check_level(h, hierarchy, level));
   if (colour != MGWR_RED && colour != MGWR_BLACK) return fail(h, MGWR_E_INVAL, "bad colour");
   if (hierarchy == MGWR_H64)
@@ -1205,6 +1265,7 @@ static double max_norm(mgwr_t h, const std::vector<double>& norms) {
 
 int mgwr_smooth_defect(mgwr_t h, int hierarchy, int level, double* norm_inf) {
   if (h == nullptr) return MGWR_E_INVAL;
+  h->u_zero = false;
   MGWR_TRY(check_level(h, hierarchy, level));
   if (level == 0) return fail(h, MGWR_E_INVAL, "level 0 has a direct solve, not a smoother");
   MGWR_TRY(clear_norms(h));
@@ -1237,6 +1298,7 @@ int mgwr_defect(mgwr_t h, int hierarchy, int level, double* norm_inf) {
 
 int mgwr_restrict(mgwr_t h, int hierarchy, int level) {
   if (h == nullptr) return MGWR_E_INVAL;
+  h->u_zero = false;
   MGWR_TRY(check_level(h, hierarchy, level));
   if (level == 0) return fail(h, MGWR_E_INVAL, "level 0 has no coarser level");
   if (hierarchy == MGWR_H64)
@@ -1249,6 +1311,7 @@ int mgwr_restrict(mgwr_t h, int hierarchy, int level) {
 
 int mgwr_prolong(mgwr_t h, int hierarchy, int level) {
   if (h == nullptr) return MGWR_E_INVAL;
+  h->u_zero = false;
   MGWR_TRY(check_level(h, hierarchy, level));
   if (level == 0) return fail(h, MGWR_E_INVAL, "level 0 has no coarser level");
   if (hierarchy == MGWR_H64)
@@ -1261,6 +1324,7 @@ int mgwr_prolong(mgwr_t h, int hierarchy, int level) {
 
 int mgwr_coarsest(mgwr_t h, int hierarchy) {
   if (h == nullptr) return MGWR_E_INVAL;
+  h->u_zero = false;
   MGWR_TRY(check_level(h, hierarchy, 0));
   if (hierarchy == MGWR_H64)
     MGWR_TRY(coarsest(h, h->h64));
@@ -1272,6 +1336,7 @@ int mgwr_coarsest(mgwr_t h, int hierarchy) {
 
 int mgwr_cycle(mgwr_t h, int hierarchy, int cyc, int nu1, int nu2) {
   if (h == nullptr) return MGWR_E_INVAL;
+  h->u_zero = false;
   MGWR_TRY(check_level(h, hierarchy, h->nlev - 1));
   MGWR_TRY(check_cycle_args(h, cyc, nu1, nu2));
   if (hierarchy == MGWR_H64)

@@ -129,6 +129,23 @@ cudaError_t launch_refine_dd(dd* u, const float* e, size_t count, cudaStream_t s
 cudaError_t launch_split_cx(Cx<dd>* dst, const Cx<double>* src, size_t count, cudaStream_t s);
 // dst = (float) src.
 cudaError_t launch_round(float* dst, const double* src, size_t count, cudaStream_t s);
+// Per instance b (x holds batch * per values): |x_b|_inf folded into
+// norm_bits[b]; out_b = (float) x_b when out != null.
+cudaError_t launch_absmax_round(const double* x, float* out, size_t per, int batch,
+                                unsigned long long* norm_bits, cudaStream_t s);
+
+// Outer defect of the mixed modes in a cheaper form for the first outer steps:
+// r = (f - A_h u) - T_M u with f - A_h u in the iterate's arithmetic Tin
+// (double or double-float; the stencil differences are taken before the sum)
+// and T_M u by an FP32 FFT convolution of (float) u (FP32 spectra `tspec` and
+// twiddles `tw`); r rounded to FP32, |r|_inf of instance b into norm_bits[b].
+// Its error is that of one FP32 convolution, about 1e-6 of |T_M u|.  Lines of
+// M <= kShortMaxM only (else cudaErrorInvalidValue).
+template <class Tin>
+cudaError_t launch_defect_hybrid(const Tin* u, const Tin* f, float* r, const Cx<float>* tspec,
+                                 size_t spec_stride, const Cx<float>* tw, const Tin* zero,
+                                 const LevelShape& ls, Tin hinv2, unsigned long long* norm_bits,
+                                 cudaStream_t s);
 // Per instance b: u = broadcast of g_b along time (initial iterate u^0(t) = g);
 // f += c_b d_{b,m} g_b.  g: batch * N, dk: batch * (M+1), c: batch (device).
 cudaError_t launch_initial(double* u, double* f, const double* g, const double* dk, const double* c,

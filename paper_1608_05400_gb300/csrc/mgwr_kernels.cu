@@ -257,6 +257,23 @@ __global__ void k_round(float* __restrict__ dst, const double* __restrict__ src,
     dst[i] = (float)src[i];
 }
 
+// Per instance (blockIdx.y): |x|_inf folded into norm_bits[instance] and, when
+// out != null, out = (float) x.  The defect of u = 0 is f itself, so this is
+// the initial defect of a solve from zero.
+__global__ void __launch_bounds__(128)
+    k_absmax_round(const double* __restrict__ x, float* __restrict__ out, size_t per,
+                   unsigned long long* __restrict__ norm_bits) {
+  x += blockIdx.y * per;
+  if (out != nullptr) out += blockIdx.y * per;
+  double amax = 0.0;
+  for (size_t i = blockIdx.x * (size_t)128 + threadIdx.x; i < per; i += (size_t)gridDim.x * 128) {
+    const double v = x[i];
+    if (out != nullptr) out[i] = (float)v;
+    amax = absmax_nan(fabs(v), amax);
+  }
+  block_absmax<double>(amax, norm_bits + blockIdx.y);
+}
+
 // Initial value g of every instance (blockIdx.y): u = g along time (initial
 // iterate u^0(t) = g) and f += c d_m g (the u_0 term of the L1 scheme).
 __global__ void k_initial(double* __restrict__ u, double* __restrict__ f,
@@ -544,6 +561,15 @@ cudaError_t launch_refine_dd(dd* u, const float* e, size_t count, cudaStream_t s
 
 cudaError_t launch_round(float* dst, const double* src, size_t count, cudaStream_t s) {
   k_round<<<elementwise_grid(count), 256, 0, s>>>(dst, src, count);
+  return counted(cudaGetLastError());
+}
+
+cudaError_t launch_absmax_round(const double* x, float* out, size_t per, int batch,
+                                unsigned long long* norm_bits, cudaStream_t s) {
+  if (per == 0 || batch == 0) return cudaSuccess;
+  size_t bx = (per + 128 * 16 - 1) / (128 * 16);
+  if (bx > 2432) bx = 2432;
+  k_absmax_round<<<dim3((unsigned)bx, (unsigned)batch), 128, 0, s>>>(x, out, per, norm_bits);
   return counted(cudaGetLastError());
 }
 

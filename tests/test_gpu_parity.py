@@ -335,3 +335,26 @@ def test_paper_table_1d_iterations_on_gpu():
         s.set_rhs(np.zeros((n, M)), g)
         st = s.solve(1, 0, 1, tol=1e-10, max_cycles=40)
     assert abs(st.cycles - 7) <= 1
+
+
+@pytest.mark.parametrize("precision", [G.MGWR_FP64, G.MGWR_MIXED, G.MGWR_MIXED_DD])
+def test_solve_from_zero_skips_nothing_it_needs(precision):
+    # from u = 0 the initial defect is f itself and is not convolved; the solve must
+    # be bitwise the one that starts from an explicitly set zero iterate
+    d, n, M = 2, 31, 128
+    f = inputs.Problem(d, n, M, 1.0, 0.6, "talpha").rhs()
+    out = []
+    for explicit in (False, True):
+        with G.Solver(d, n, M, 1.0, 0.6) as s:
+            s.set_precision(precision)
+            s.set_rhs(f)
+            if explicit:
+                s.set_initial(np.zeros_like(f))
+            st = s.solve(1, 1, 1, tol=1e-10, max_cycles=40)
+            out.append((s.solution(), st.cycles, st.outer, st.relres))
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    assert out[0][1:3] == out[1][1:3]
+    # the double-float defect reports its norm from the leading FP32 word, so r_0
+    # from the explicit zero iterate differs from max |f| in the 8th digit
+    assert abs(out[0][3] - out[1][3]) <= 1e-6 * out[1][3]
+    assert rel(out[0][0], direct.time_stepping(d, n, M, 1.0, 0.6, f)) <= (1e-11 if precision == G.MGWR_FP64 else 1e-8)

@@ -146,16 +146,19 @@ int mgwr_set_inner_cycles(mgwr_t h, int cycles);
  * group fits in one warp.  A request a length cannot take falls back to the
  * nearest smaller E; mgwr_get_engine_split reports the E launches use.
  * MGWR_E_INVAL for another class or split. */
-int mgwr_set_engine_split(mgwr_t h, int kernel_class, int split);
-int mgwr_get_engine_split(mgwr_t h, int kernel_class, int* split);
+int mgwr_set_engine_split(mgwr_t h, int kernel_class, int level, int split);
+int mgwr_get_engine_split(mgwr_t h, int kernel_class, int level, int* split);
 /* Tuner: times every E of each engine class the current precision runs (the
- * sweep and the full defect of its cycle hierarchy, and in the mixed modes
- * the outer defect) on a sample of the handle's own data (the finest level
- * holding at most 2^25 values per instance, as many instances as fit 2^25
- * values), writing to a temporary field, and keeps the fastest.  The handle's
- * state is unchanged.  The choices are also recorded process-wide for
- * (class, d, n, M, batch): handles created later with that shape start with
- * them.  Synchronises the handle's stream. */
+ * sweep and the full defect of its cycle hierarchy on every level, and in
+ * the mixed modes the outer defect) on the handle's own data (per level, as
+ * many instances as fit 2^27 values, at least one), writing to a temporary
+ * field, and keeps the fastest per level (a larger E must win by 3 %).  The
+ * handle's state is unchanged.  The choices are also recorded process-wide
+ * for (class, d, n, M, batch): handles created later with that shape start
+ * with them.  mgwr_set_engine_split / mgwr_get_engine_split address
+ * one level (0 .. num_levels-1) or, with level -1, every level (set) and the
+ * finest (get).  Synchronises the
+ * handle's stream. */
 int mgwr_autotune(mgwr_t h);
 /* enable != 0 (default): mgwr_solve captures one iteration of its loop (the
  * cycle's launches, the defect norms and their copy to the host) as a CUDA

@@ -85,8 +85,8 @@ struct mgwr_handle {
   bool r0_valid = false;
   std::vector<void*> allocs;
   std::string err;
-  // FFT-engine split (butterflies per thread) per kernel class; 0 = default
-  int split[MGWR_NUM_KERNEL_CLASSES] = {};
+  // FFT-engine split (butterflies per thread) per kernel class and level; 0 = default
+  std::vector<int> split[MGWR_NUM_KERNEL_CLASSES];
   // solve-loop iterations captured as CUDA graphs (one per form of the
   // iteration: settings and outer-defect form), replayed every iteration
   bool use_graphs = true;
@@ -161,7 +161,9 @@ int ensure_field(mgwr_t h, R** p, size_t count) {
 
 bool is_pow2(long long x) { return x > 0 && (x & (x - 1)) == 0; }
 
-int split_of(const mgwr_handle* h, int cls) { return h->split[cls]; }
+int split_of(const mgwr_handle* h, int cls, int l) {
+  return h->split[cls].empty() ? 0 : h->split[cls][l];
+}
 
 void drop_graph(mgwr_t h) {
   for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
@@ -295,7 +297,7 @@ int coarsest(mgwr_t h, Hier<R>& H) {
   const int pm = prof_begin(h, MGWR_K_COARSEST, (double)h->B);
   MGWR_CK(h, mgwr::launch_sweep<R>(H.f[0], H.u[0], (R*)nullptr, H.spec, (size_t)h->nlev * h->L,
                                     H.tw, H.zero, scratch_for<R>(h), shape(h, 0), 0, true, R(0),
-                                    split_of(h, sizeof(R) == 8 ? MGWR_K_SWEEP64 : MGWR_K_SWEEP32),
+                                    split_of(h, sizeof(R) == 8 ? MGWR_K_SWEEP64 : MGWR_K_SWEEP32, 0),
                                     h->stream));
   prof_end(h, pm);
   H.rs[0] = R_STALE;
@@ -313,7 +315,7 @@ int sweep_colour(mgwr_t h, Hier<R>& H, int l, int colour, R* delta) {
   MGWR_CK(h, mgwr::launch_sweep<R>(H.f[l], H.u[l], delta, H.spec + (size_t)l * h->L,
                                     (size_t)h->nlev * h->L, H.tw, H.zero, scratch_for<R>(h), shape(h, l), par,
                                     false, R(h->hinv2[l]),
-                                    split_of(h, sizeof(R) == 8 ? MGWR_K_SWEEP64 : MGWR_K_SWEEP32),
+                                    split_of(h, sizeof(R) == 8 ? MGWR_K_SWEEP64 : MGWR_K_SWEEP32, l),
                                     h->stream));
   prof_end(h, pm);
   return MGWR_OK;
@@ -346,7 +348,7 @@ int defect(mgwr_t h, Hier<R>& H, int l, unsigned long long* norm_bits) {
                             (double)(points(h, l) * h->B));
   MGWR_CK(h, (mgwr::launch_defect<R, R>(H.u[l], H.f[l], H.r[l], H.tspec, (size_t)h->L, H.tw,
                                          H.zero, scratch_for<R>(h), shape(h, l), R(h->hinv2[l]), norm_bits,
-                                         split_of(h, sizeof(R) == 8 ? MGWR_K_DEFECT64 : MGWR_K_DEFECT32),
+                                         split_of(h, sizeof(R) == 8 ? MGWR_K_DEFECT64 : MGWR_K_DEFECT32, l),
                                          h->stream)));
   prof_end(h, pm);
   H.rs[l] = R_CURRENT;
@@ -442,7 +444,7 @@ int finest_defect_norms(mgwr_t h, std::vector<double>& norms, bool to_h32) {
     MGWR_CK(h, (mgwr::launch_defect<double, float>(h->h64.u[L], h->h64.f[L], h->h32.f[L],
                                                     h->h64.tspec, (size_t)h->L, h->h64.tw,
                                                     h->h64.zero, scratch_for<double>(h), shape(h, L), h->hinv2[L], h->norm_bits,
-                                                    split_of(h, MGWR_K_DEFECT64),
+                                                    split_of(h, MGWR_K_DEFECT64, L),
                                                     h->stream)));
     h->h32.rs[L] = R_STALE;
   } else {
@@ -450,7 +452,7 @@ int finest_defect_norms(mgwr_t h, std::vector<double>& norms, bool to_h32) {
     MGWR_CK(h, (mgwr::launch_defect<double, double>(h->h64.u[L], h->h64.f[L], h->h64.r[L],
                                                      h->h64.tspec, (size_t)h->L, h->h64.tw,
                                                      h->h64.zero, scratch_for<double>(h), shape(h, L), h->hinv2[L], h->norm_bits,
-                                                    split_of(h, MGWR_K_DEFECT64),
+                                                    split_of(h, MGWR_K_DEFECT64, L),
                                                      h->stream)));
     h->h64.rs[L] = R_CURRENT;
   }
@@ -466,7 +468,7 @@ int finest_defect_norms_dd(mgwr_t h, std::vector<double>& norms) {
   const int pm = prof_begin(h, MGWR_K_DEFECT_DD, (double)(points(h, L) * h->B));
   MGWR_CK(h, (mgwr::launch_defect<mgwr::dd, float>(h->u_dd, h->f_dd, h->h32.f[L], h->tspec_dd,
                                                     (size_t)h->L, h->tw_dd, h->zero_dd, scratch_for<mgwr::dd>(h), shape(h, L),
-                                                    mgwr::dd(h->hinv2[L]), h->norm_bits, split_of(h, MGWR_K_DEFECT_DD),
+                                                    mgwr::dd(h->hinv2[L]), h->norm_bits, split_of(h, MGWR_K_DEFECT_DD, L),
                                                     h->stream)));
   prof_end(h, pm);
   h->h32.rs[L] = R_STALE;
@@ -538,13 +540,13 @@ int enqueue_iteration(mgwr_t h, int cyc, int nu1, int nu2, bool* exact) {
     if (ddef)
       MGWR_CK(h, (mgwr::launch_defect<mgwr::dd, float>(h->u_dd, h->f_dd, h->h32.f[L], h->tspec_dd,
                                                         (size_t)h->L, h->tw_dd, h->zero_dd, scratch_for<mgwr::dd>(h), shape(h, L),
-                                                        mgwr::dd(h->hinv2[L]), h->norm_bits, split_of(h, MGWR_K_DEFECT_DD),
+                                                        mgwr::dd(h->hinv2[L]), h->norm_bits, split_of(h, MGWR_K_DEFECT_DD, L),
                                                         h->stream)));
     else
       MGWR_CK(h, (mgwr::launch_defect<double, float>(h->h64.u[L], h->h64.f[L], h->h32.f[L],
                                                       h->h64.tspec, (size_t)h->L, h->h64.tw,
                                                       h->h64.zero, scratch_for<double>(h), shape(h, L), h->hinv2[L], h->norm_bits,
-                                                    split_of(h, MGWR_K_DEFECT64),
+                                                    split_of(h, MGWR_K_DEFECT64, L),
                                                       h->stream)));
     prof_end(h, pd);
     h->h32.rs[L] = R_STALE;
@@ -626,7 +628,7 @@ int check_cycle_args(mgwr_t h, int cyc, int nu1, int nu2) {
 // Splits chosen by mgwr_autotune, per (kernel class, d, n, M, batch): handles of a
 // shape that was tuned before start with its choices.
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int, int>, int> g_tune;
+std::map<std::tuple<int, int, int, int, int>, std::vector<int>> g_tune;
 
 void load_tuned(mgwr_t h) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -636,17 +638,18 @@ void load_tuned(mgwr_t h) {
   }
 }
 
-// The sample the tuner times: the finest level whose field holds at most 2^25
-// values per instance, and as many instances (at most the batch) as keep the
-// sample within 2^25 values (all pairs of those instances).
-LevelShape tune_sample(const mgwr_handle* h, int* level) {
-  const size_t cap = size_t(1) << 25;
-  int l = h->nlev - 1;
-  while (l > 0 && points(h, l) * (size_t)h->M > cap) --l;
+void set_split(mgwr_t h, int cls, int l, int E) {
+  if (h->split[cls].empty()) h->split[cls].assign(h->nlev, 0);
+  h->split[cls][l] = E;
+}
+
+// The sample the tuner times on level l: as many instances (at most the batch,
+// at least one) as keep it within 2^27 values, all pairs of those instances.
+LevelShape tune_sample(const mgwr_handle* h, int l) {
+  const size_t cap = size_t(1) << 27;
   const size_t per = points(h, l) * (size_t)h->M;
   size_t b = per >= cap ? 1 : cap / per;
   if (b > (size_t)h->B) b = h->B;
-  *level = l;
   return LevelShape{h->d, h->nl[l], h->M, (int)b};
 }
 
@@ -654,7 +657,7 @@ LevelShape tune_sample(const mgwr_handle* h, int* level) {
 template <class F>
 int time_launches(mgwr_t h, F launch, float* ms) {
   MGWR_CK(h, launch());
-  const int reps = 3;
+  const int reps = 5;
   MGWR_CK(h, cudaEventRecord(h->ev0, h->stream));
   for (int i = 0; i < reps; ++i) MGWR_CK(h, launch());
   MGWR_CK(h, cudaEventRecord(h->ev1, h->stream));
@@ -666,74 +669,93 @@ int time_launches(mgwr_t h, F launch, float* ms) {
 }
 
 // Times every split E in {1, 2, 4} of one kernel class with `launch(E)` and
-// keeps the fastest.
+// keeps the fastest; a larger E must beat the best smaller one by 3 %.
 template <class F>
-int tune_class(mgwr_t h, int cls, int word, F launch) {
+int tune_class(mgwr_t h, int cls, int l, int word, F launch) {
   int best = 1;
   float best_ms = 0.f;
   for (int E = 1; E <= 4; E *= 2) {
     if (mgwr::effective_split(h->M, word, E) != E) continue;  // same launch as a smaller E
     float ms = 0.f;
     MGWR_TRY(time_launches(h, [&] { return launch(E); }, &ms));
-    if (E == 1 || ms < best_ms) {
+    if (E == 1 || ms < 0.97f * best_ms) {
       best = E;
       best_ms = ms;
     }
   }
-  h->split[cls] = best;
+  set_split(h, cls, l, best);
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_tune[std::make_tuple(cls, h->d, h->n, h->M, h->B)] = best;
+  g_tune[std::make_tuple(cls, h->d, h->n, h->M, h->B)] = h->split[cls];
   return MGWR_OK;
 }
 
-// Sweeps (red points) and defects of the sample, written to a scratch field, in
-// the arithmetic `R` of hierarchy H; no state of the handle changes.
+// Sweeps (red points, every level >= 1 and the one-point solve) and defects
+// (every level) of the samples, written to a scratch field, in the arithmetic
+// `R` of hierarchy H; no state of the handle changes.
 template <class R>
 int tune_hierarchy(mgwr_t h, Hier<R>& H, int cls_sweep, int cls_defect) {
-  int l = 0;
-  const LevelShape ls = tune_sample(h, &l);
-  const size_t count = ls.field_stride() * ls.batch;
-  R* out = nullptr;
-  MGWR_TRY(ensure_field(h, &H.u[l], level_count(h, l)));
-  MGWR_TRY(ensure_field(h, &H.f[l], level_count(h, l)));
+  size_t count = 0;
+  for (int l = 0; l < h->nlev; ++l) {
+    const LevelShape ls = tune_sample(h, l);
+    count = std::max(count, ls.field_stride() * ls.batch);
+  }
+  R *out = nullptr, *dlt = nullptr;
   MGWR_TRY(dev_alloc(h, &out, count * sizeof(R)));
+  MGWR_TRY(dev_alloc(h, &dlt, count * sizeof(R)));
   MGWR_CK(h, cudaMemsetAsync(out, 0, count * sizeof(R), h->stream));
-  int st = tune_class(h, cls_sweep, sizeof(R) == 4 ? 4 : 8, [&](int E) {
-    return mgwr::launch_sweep<R>(H.f[l], out, (R*)nullptr, H.spec + (size_t)l * h->L,
-                                 (size_t)h->nlev * h->L, H.tw, H.zero, scratch_for<R>(h), ls,
-                                 parity(h, MGWR_RED), false, R(h->hinv2[l]), E, h->stream);
-  });
-  if (st == MGWR_OK)
-    st = tune_class(h, cls_defect, sizeof(R) == 4 ? 4 : 8, [&](int E) {
-      return mgwr::launch_defect<R, R>(H.u[l], H.f[l], out, H.tspec, (size_t)h->L, H.tw, H.zero,
-                                       scratch_for<R>(h), ls, R(h->hinv2[l]), nullptr, E,
-                                       h->stream);
-    });
-  cudaFreeAsync(out, h->stream);
-  h->allocs.erase(std::find(h->allocs.begin(), h->allocs.end(), (void*)out));
+  int st = MGWR_OK;
+  for (int l = h->nlev - 1; l >= 0 && st == MGWR_OK; --l) {
+    const LevelShape ls = tune_sample(h, l);
+    st = ensure_field(h, &H.u[l], level_count(h, l));
+    if (st == MGWR_OK) st = ensure_field(h, &H.f[l], level_count(h, l));
+    if (st == MGWR_OK)
+      st = tune_class(h, cls_sweep, l, sizeof(R) == 4 ? 4 : 8, [&](int E) {
+        // one smoothing step as the cycle runs it: red, then black recording its changes
+        const Cx<R>* spec = H.spec + (size_t)l * h->L;
+        const size_t sstride = (size_t)h->nlev * h->L;
+        if (l == 0)
+          return mgwr::launch_sweep<R>(H.f[0], out, (R*)nullptr, spec, sstride, H.tw, H.zero,
+                                       scratch_for<R>(h), ls, 0, true, R(0), E, h->stream);
+        const cudaError_t e = mgwr::launch_sweep<R>(
+            H.f[l], out, (R*)nullptr, spec, sstride, H.tw, H.zero, scratch_for<R>(h), ls,
+            parity(h, MGWR_RED), false, R(h->hinv2[l]), E, h->stream);
+        if (e != cudaSuccess) return e;
+        return mgwr::launch_sweep<R>(H.f[l], out, dlt, spec, sstride, H.tw, H.zero,
+                                     scratch_for<R>(h), ls, parity(h, MGWR_BLACK), false,
+                                     R(h->hinv2[l]), E, h->stream);
+      });
+    if (st == MGWR_OK)
+      st = tune_class(h, cls_defect, l, sizeof(R) == 4 ? 4 : 8, [&](int E) {
+        return mgwr::launch_defect<R, R>(H.u[l], H.f[l], out, H.tspec, (size_t)h->L, H.tw,
+                                         H.zero, scratch_for<R>(h), ls, R(h->hinv2[l]), nullptr,
+                                         E, h->stream);
+      });
+  }
+  for (void* p : {(void*)out, (void*)dlt}) {
+    cudaFreeAsync(p, h->stream);
+    h->allocs.erase(std::find(h->allocs.begin(), h->allocs.end(), p));
+  }
   return st;
 }
 
 // Outer defect of the mixed modes (FP64 or double-float iterate, FP32 output)
 // on the finest-level sample.
 int tune_outer(mgwr_t h) {
-  int l = 0;
-  const LevelShape ls = tune_sample(h, &l);
   const int Lf = h->nlev - 1;
-  if (l != Lf) return MGWR_OK;  // the outer defect only runs on the finest level
+  const LevelShape ls = tune_sample(h, Lf);
   const size_t count = ls.field_stride() * ls.batch;
   float* out = nullptr;
   MGWR_TRY(dev_alloc(h, &out, count * sizeof(float)));
   int st;
   if (h->precision == MGWR_MIXED_DD)
-    st = tune_class(h, MGWR_K_DEFECT_DD, 8, [&](int E) {
+    st = tune_class(h, MGWR_K_DEFECT_DD, Lf, 8, [&](int E) {
       return mgwr::launch_defect<mgwr::dd, float>(h->u_dd, h->f_dd, out, h->tspec_dd, (size_t)h->L,
                                                   h->tw_dd, h->zero_dd, scratch_for<mgwr::dd>(h),
                                                   ls, mgwr::dd(h->hinv2[Lf]), nullptr, E,
                                                   h->stream);
     });
   else
-    st = tune_class(h, MGWR_K_DEFECT64, 8, [&](int E) {
+    st = tune_class(h, MGWR_K_DEFECT64, Lf, 8, [&](int E) {
       return mgwr::launch_defect<double, float>(h->h64.u[Lf], h->h64.f[Lf], out, h->h64.tspec,
                                                 (size_t)h->L, h->h64.tw, h->h64.zero,
                                                 scratch_for<double>(h), ls, h->hinv2[Lf],
@@ -957,24 +979,29 @@ int mgwr_set_graphs(mgwr_t h, int enable) {
   return MGWR_OK;
 }
 
-int mgwr_set_engine_split(mgwr_t h, int kernel_class, int split) {
+int mgwr_set_engine_split(mgwr_t h, int kernel_class, int level, int split) {
   if (h == nullptr) return MGWR_E_INVAL;
   if (kernel_class != MGWR_K_SWEEP64 && kernel_class != MGWR_K_SWEEP32 &&
       kernel_class != MGWR_K_DEFECT64 && kernel_class != MGWR_K_DEFECT32 &&
       kernel_class != MGWR_K_DEFECT_DD)
     return fail(h, MGWR_E_INVAL, "kernel class has no FFT engine");
   if (split != 1 && split != 2 && split != 4) return fail(h, MGWR_E_INVAL, "split must be 1, 2 or 4");
-  h->split[kernel_class] = split;
+  if (level < -1 || level >= h->nlev) return fail(h, MGWR_E_INVAL, "level out of range");
+  if (level == -1)
+    h->split[kernel_class].assign(h->nlev, split);
+  else
+    set_split(h, kernel_class, level, split);
   drop_graph(h);
   return MGWR_OK;
 }
 
-int mgwr_get_engine_split(mgwr_t h, int kernel_class, int* split) {
+int mgwr_get_engine_split(mgwr_t h, int kernel_class, int level, int* split) {
   if (h == nullptr || split == nullptr || kernel_class < 0 ||
-      kernel_class >= MGWR_NUM_KERNEL_CLASSES)
+      kernel_class >= MGWR_NUM_KERNEL_CLASSES || level < -1 || level >= h->nlev)
     return MGWR_E_INVAL;
   const int word = kernel_class == MGWR_K_SWEEP32 || kernel_class == MGWR_K_DEFECT32 ? 4 : 8;
-  *split = mgwr::effective_split(h->M, word, h->split[kernel_class]);
+  *split = mgwr::effective_split(h->M, word,
+                                 split_of(h, kernel_class, level == -1 ? h->nlev - 1 : level));
   return MGWR_OK;
 }
 

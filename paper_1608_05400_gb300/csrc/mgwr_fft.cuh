@@ -95,14 +95,20 @@ __device__ __forceinline__ void dft8_half_input(Cx<R> (&v)[8]) {
   v[1] = b0; v[3] = b1; v[5] = b2; v[7] = b3;
 }
 
-// Shared-memory index with one pad slot per 8 (16-byte elements) or 16 (8-byte
-// elements) values: the contiguous-per-thread and the long-stride access
-// patterns of the stages below then hit distinct banks.
+// Shared-memory index of transform position x.  16-byte elements: one pad
+// slot per 8 values.  8-byte elements: no padding; bits 4..9 of x are folded
+// into its bits 0..3 by an XOR (a bijection on every aligned block of 16), so
+// the three access patterns of the stages below (consecutive positions, the
+// span-s butterflies of the middle stages, 8 consecutive values per thread)
+// each put the 16 lanes of a half-warp on 16 different bank pairs.
 template <class R>
 struct Pad {
-  static constexpr int shift = sizeof(Cx<R>) >= 16 ? 3 : 4;
-  static __device__ __forceinline__ int idx(int x) { return x + (x >> shift); }
-  static __host__ __device__ __forceinline__ int len(int L) { return L + (L >> shift); }
+  static constexpr bool wide = sizeof(Cx<R>) >= 16;
+  static __device__ __forceinline__ int idx(int x) {
+    if constexpr (wide) return x + (x >> 3);
+    return x ^ (((x >> 3) & 14) ^ ((x >> 6) & 15));
+  }
+  static __host__ __device__ __forceinline__ int len(int L) { return wide ? L + (L >> 3) : L; }
 };
 
 // Last-stage butterflies on the 8 contiguous values a thread owns.

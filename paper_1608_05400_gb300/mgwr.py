@@ -70,8 +70,8 @@ _SIGS = {
     "mgwr_set_order": (C.c_int, [_h, C.c_int]),
     "mgwr_set_stream": (C.c_int, [_h, C.c_void_p]),
     "mgwr_set_inner_cycles": (C.c_int, [_h, C.c_int]),
-    "mgwr_set_engine_split": (C.c_int, [_h, C.c_int, C.c_int]),
-    "mgwr_get_engine_split": (C.c_int, [_h, C.c_int, C.POINTER(C.c_int)]),
+    "mgwr_set_engine_split": (C.c_int, [_h, C.c_int, C.c_int, C.c_int]),
+    "mgwr_get_engine_split": (C.c_int, [_h, C.c_int, C.c_int, C.POINTER(C.c_int)]),
     "mgwr_autotune": (C.c_int, [_h]),
     "mgwr_set_graphs": (C.c_int, [_h, C.c_int]),
     "mgwr_set_rhs": (C.c_int, [_h, _dp, _dp]),
@@ -220,20 +220,24 @@ class Solver:
     def set_inner_cycles(self, k: int):
         self._check(self.lib.mgwr_set_inner_cycles(self.h, k), "mgwr_set_inner_cycles")
 
-    def set_engine_split(self, kernel_class: int, split: int):
-        self._check(self.lib.mgwr_set_engine_split(self.h, kernel_class, split),
+    def set_engine_split(self, kernel_class: int, split: int, level: int = -1):
+        """E for one level, or every level (level -1)."""
+        self._check(self.lib.mgwr_set_engine_split(self.h, kernel_class, level, split),
                     "mgwr_set_engine_split")
 
-    def engine_split(self, kernel_class: int) -> int:
+    def engine_split(self, kernel_class: int, level: int = -1) -> int:
+        """E used on one level (level -1: the finest)."""
         e = C.c_int()
-        self._check(self.lib.mgwr_get_engine_split(self.h, kernel_class, C.byref(e)),
+        self._check(self.lib.mgwr_get_engine_split(self.h, kernel_class, level, C.byref(e)),
                     "mgwr_get_engine_split")
         return e.value
 
     def autotune(self) -> dict:
-        """Run the launch-shape tuner; returns the split chosen per engine class."""
+        """Run the launch-shape tuner; returns, per engine class, the split chosen
+        on each level (coarsest first)."""
         self._check(self.lib.mgwr_autotune(self.h), "mgwr_autotune")
-        return {name: self.engine_split(k) for k, name in enumerate(KERNEL_CLASSES)
+        return {name: [self.engine_split(k, l) for l in range(self.num_levels())]
+                for k, name in enumerate(KERNEL_CLASSES)
                 if name in ("sweep64", "sweep32", "defect64", "defect32", "defect_dd")}
 
     # -- data --

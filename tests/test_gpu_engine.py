@@ -91,6 +91,10 @@ def test_split_requests_fall_back_to_what_a_length_takes():
             s.set_engine_split(K["restrict"], 2)
         with pytest.raises(G.MGWRError):
             s.set_engine_split(K["sweep64"], 3)
+        with pytest.raises(G.MGWRError):
+            s.set_engine_split(K["sweep64"], 2, level=s.num_levels())
+        s.set_engine_split(K["sweep64"], 2, level=1)
+        assert s.engine_split(K["sweep64"], 1) == 2 and s.engine_split(K["sweep64"], 0) == 1
 
 
 @pytest.mark.parametrize("precision", [G.MGWR_FP64, G.MGWR_MIXED, G.MGWR_MIXED_DD])
@@ -108,7 +112,7 @@ def test_autotune_keeps_state_and_results(precision):
         s.solve(1, 1, 1, tol=1e-10, max_cycles=1, allow_noconv=True)
         before = s.solution()
         chosen = s.autotune()
-        assert all(v in (1, 2, 4) for v in chosen.values())
+        assert all(e in (1, 2, 4) for v in chosen.values() for e in v)
         np.testing.assert_array_equal(s.solution(), before)  # tuning touches no state
         s.set_rhs(f)
         st = s.solve(1, 1, 1, tol=1e-10, max_cycles=40)
@@ -118,4 +122,4 @@ def test_autotune_keeps_state_and_results(precision):
     with G.Solver(d, n, M, 1.0, 0.9) as s2:
         s2.set_precision(precision)
         for name, v in chosen.items():
-            assert s2.engine_split(K[name]) == v
+            assert [s2.engine_split(K[name], l) for l in range(s2.num_levels())] == v

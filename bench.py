@@ -65,9 +65,9 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_FMA_PER_CLK_PER_SM = 2
 SMS = 152
 # DRAM bytes (read + write) per smoothed line of k_sweep<double> from an ncu
-# capture of the finest-level half-sweep of the default workload (773.2 MB for
+# capture of the finest-level half-sweep of the default workload (772.5 MB for
 # 32,513 lines of 1024 doubles; profiles/k_sweep_fp64_2d_255x255_M1024.md).
-SWEEP64_DRAM_BYTES_PER_LINE_M1024 = 23781.0
+SWEEP64_DRAM_BYTES_PER_LINE_M1024 = 23758.0
 
 
 def parse():
@@ -83,6 +83,9 @@ def parse():
     p.add_argument("--inner", type=int, default=None, help="mixed modes: FP32 cycles per outer defect")
     p.add_argument("--alpha", type=float, default=None)
     p.add_argument("--no-autotune", action="store_true", help="keep the default engine launch shapes")
+    p.add_argument("--shape", default=None,
+                   help="d,n,M replacing the workload's grid (small cases for profiling)")
+    p.add_argument("--batch", type=int, default=None, help="instances replacing the workload's batch")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     return p.parse_args()
@@ -376,6 +379,12 @@ def main():
     from paper_1608_05400_gb300 import inputs, mgwr
 
     d, n, Mw, batch, kind, tol, prec_default, desc = WORKLOADS[args.workload]
+    if args.shape or args.batch:
+        if args.shape:
+            d, n, Mw = (int(x) for x in args.shape.split(","))
+        batch = args.batch or batch
+        desc = f"{args.workload} settings on {d}-D n={n}, M={Mw}, batch {batch} (profiling case)"
+        args.no_cpu = True
     precision = args.precision or prec_default
     alpha = args.alpha if args.alpha is not None else WORKLOAD_ALPHA.get(args.workload, ALPHA)
     if batch == 1:

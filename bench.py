@@ -56,6 +56,8 @@ WORKLOADS = {
 }
 # alpha of a workload when --alpha is not given
 WORKLOAD_ALPHA = {"c5b": 0.2}
+# FP32 cycles per outer defect of a mixed workload when --inner is not given
+WORKLOAD_INNER = {"c5a": 4}
 # oracle time steps in the CPU-baseline sample (about 10-30 s of host work)
 ORACLE_SAMPLE_STEPS = {"c2": 256, "c5b": 2048}
 UNIT = "unknowns/s"
@@ -283,9 +285,12 @@ def run_reference(args):
 def run_served(args):
     """Config 4: a stream of mixed-shape requests through mgwr_submit / mgwr_poll.
 
-    Pass 1 submits the whole list at once and measures the sustained rate;
-    pass 2 replays it with Poisson arrivals at 0.7 x that rate and records the
-    latency of every request (submit -> result ready)."""
+    Pass 1 submits the whole list as fast as the server takes it and measures
+    the sustained rate; pass 2 replays it with Poisson arrivals at 0.7 x that
+    rate and records the latency of every request (scheduled arrival -> result
+    ready).  Both passes keep at most 24 GB of submitted right-hand sides in
+    host memory (the server holds a copy of each until its request is done);
+    time a request waits for that window counts in its latency."""
     import threading
 
     import torch
@@ -304,8 +309,15 @@ def run_served(args):
     def unknowns(rq):
         return rq["n"] ** rq["d"] * rq["M"]
 
+    # host bytes of right-hand sides submitted and not yet completed: the server
+    # copies each f until its request finishes, so bound what is outstanding
+    host_cap = 24 << 30
+
     def run(arrivals):
         lat, results = [None] * len(reqs), [None] * len(reqs)
+        delay = [0.0] * len(reqs)
+        outstanding = [0]
+        lock = threading.Condition()
         with mgwr.Server(hbm_budget=budget, slots=args.slots) as srv:
             tickets = [None] * len(reqs)
             t0 = time.perf_counter()
@@ -315,6 +327,12 @@ def run_served(args):
                     wait = t0 + arrivals[i] - time.perf_counter()
                     if wait > 0:
                         time.sleep(wait)
+                    nbytes = 8 * unknowns(rq)
+                    with lock:
+                        lock.wait_for(lambda: outstanding[0] == 0 or outstanding[0] + nbytes <= host_cap)
+                        outstanding[0] += nbytes
+                    # time a request waited for host memory counts in its latency
+                    delay[i] = max(0.0, time.perf_counter() - (t0 + arrivals[i]))
                     tickets[i] = srv.submit(rq["d"], rq["n"], rq["M"], 1.0, rq["alpha"], rhs(rq),
                                             precision=mgwr.MGWR_MIXED_DD, tol=tol)
 
@@ -324,11 +342,14 @@ def run_served(args):
             while done < len(reqs):
                 for i in range(len(reqs)):
                     if results[i] is None and tickets[i] is not None:
-                        r = srv.poll(tickets[i], timeout_us=0)
+                        r = srv.poll(tickets[i], timeout_us=0, copy_solution=False)
                         if r is not None:
                             results[i] = r
-                            lat[i] = r.latency_s
+                            lat[i] = r.latency_s + delay[i]
                             done += 1
+                            with lock:
+                                outstanding[0] -= 8 * unknowns(reqs[i])
+                                lock.notify_all()
                 time.sleep(0.002)
             th.join()
             makespan = time.perf_counter() - t0
@@ -352,7 +373,7 @@ def run_served(args):
                                "1-D n=2^k-1 k~U{5..12} or 2-D k~U{5..9}, M=2^j j~U{7..12}, "
                                "alpha~U[0.1,0.9], u=t^2 or t^alpha sin, Poisson arrivals at 0.7x "
                                "the sustained rate", "name": "c4", "slots": args.slots,
-                   "hbm_budget_bytes": budget},
+                   "hbm_budget_bytes": budget, "host_window_bytes": host_cap},
         "served": {"p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
                    "sustained_requests_per_s": rate, "offered_requests_per_s": 0.7 * rate,
                    "back_to_back_unknowns_per_s": total / span1, "completed_ok": ok,
@@ -407,8 +428,9 @@ def main():
     prec_code = {"fp64": mgwr.MGWR_FP64, "mixed": mgwr.MGWR_MIXED, "mixed_dd": mgwr.MGWR_MIXED_DD}
     if precision != "fp64":
         s.set_precision(prec_code[precision])
-        if args.inner:
-            s.set_inner_cycles(args.inner)
+        inner = args.inner or WORKLOAD_INNER.get(args.workload)
+        if inner:
+            s.set_inner_cycles(inner)
 
     # launch shapes of the FFT-engine kernels, timed on this handle's data (setup,
     # outside the timed region)
@@ -492,6 +514,8 @@ def main():
                                + f"V({NU1},{NU2}) red-black, rel-res {tol}",
                    "name": args.workload, "precision": precision,
                    "engine_splits": splits,
+                   "inner_cycles": (args.inner or WORKLOAD_INNER.get(args.workload) or 2)
+                   if precision != "fp64" else None,
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": f"inputs larger than L2 ({unknowns * 8 / 1e6:.0f} MB per FP64 field)"},
         "solve": {"cycles": stats[-1].cycles, "outer": stats[-1].outer, "relres": stats[-1].relres,

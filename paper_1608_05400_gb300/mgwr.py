@@ -397,9 +397,9 @@ class Server:
         self._shapes[t.value] = (N, M)
         return t.value
 
-    def poll(self, ticket: int, timeout_us: int = 0) -> Result | None:
+    def poll(self, ticket: int, timeout_us: int = 0, copy_solution: bool = True) -> Result | None:
         N, M = self._shapes[ticket]
-        u = np.empty((N, M))
+        u = np.empty((N, M)) if copy_solution else None
         res = mgwr_result()
         st = self.lib.mgwr_poll(self.h, ticket, timeout_us, _ptr(u), C.byref(res))
         if st in (MGWR_E_AGAIN, MGWR_E_TIMEOUT):
@@ -410,7 +410,7 @@ class Server:
         s = res.stats
         ok = res.status in (MGWR_OK, MGWR_E_NOCONV)
         return Result(res.status, Stats(s.cycles, s.outer, s.relres, s.factor, s.seconds, res.status),
-                      res.queue_s, res.latency_s, u if ok else None)
+                      res.queue_s, res.latency_s, u if ok and copy_solution else None)
 
     def info(self) -> dict:
         i = mgwr_server_info()

@@ -24,29 +24,63 @@ long long launch_counter() { return g_launches.load(); }
 
 void add_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
-// Line-wise kernels: a group of TPL threads owns one time line (TPL = min(128,
-// M/2), 128 / TPL lines per 128-thread block); each thread handles two
-// consecutive time values per step.  Index arithmetic is done once per line.
-struct LineMap {
-  int line, m0, step;
-  __device__ __forceinline__ LineMap(int log_tpl) {
-    const int tpl = 1 << log_tpl;
-    line = blockIdx.x * (128 >> log_tpl) + (threadIdx.x >> log_tpl);
-    m0 = 2 * (threadIdx.x & (tpl - 1));
-    step = 2 * tpl;
-  }
+// Line-wise kernels: a group of TPL threads owns one time line (TPL =
+// min(64, M/W), 256 / TPL lines per 256-thread block); each thread moves W =
+// 16 / sizeof(R) consecutive time values per step with 16-byte accesses (every
+// line starts on a 16-byte boundary: M is a power of two >= 4 and the fields
+// are allocated 256-byte aligned).  Index arithmetic is done once per line.
+constexpr int kLineBlock = 256;
+
+template <class R>
+struct Vec {
+  static constexpr int W = 16 / sizeof(R);
+  R v[W];
 };
 
 template <class R>
+__device__ __forceinline__ Vec<R> vload(const R* p) {
+  Vec<R> x;
+  *reinterpret_cast<uint4*>(x.v) = __ldg(reinterpret_cast<const uint4*>(p));
+  return x;
+}
+
+// the same for a line the kernel also writes (no read-only cache path)
+template <class R>
+__device__ __forceinline__ Vec<R> vload_rw(const R* p) {
+  Vec<R> x;
+  *reinterpret_cast<uint4*>(x.v) = *reinterpret_cast<const uint4*>(p);
+  return x;
+}
+
+template <class R>
+__device__ __forceinline__ void vstore(R* p, const Vec<R>& x) {
+  *reinterpret_cast<uint4*>(p) = *reinterpret_cast<const uint4*>(x.v);
+}
+
+template <class R>
+struct LineMap {
+  int line, m0, step;
+  __device__ __forceinline__ explicit LineMap(int log_tpl) {
+    const int tpl = 1 << log_tpl;
+    line = blockIdx.x * (kLineBlock >> log_tpl) + (threadIdx.x >> log_tpl);
+    m0 = Vec<R>::W * (threadIdx.x & (tpl - 1));
+    step = Vec<R>::W * tpl;
+  }
+};
+
+// Block-wide maximum of `amax` folded into *norm_bits (any block of whole warps,
+// at most 1024 threads).
 __device__ __forceinline__ void block_absmax(double amax, unsigned long long* norm_bits) {
-  __shared__ double red[4];
+  __shared__ double red[32];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) amax = absmax_nan(__shfl_xor_sync(0xffffffffu, amax, o), amax);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = amax;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    amax = absmax_nan(absmax_nan(red[0], red[1]), absmax_nan(red[2], red[3]));
-    atomic_max_nonneg(norm_bits, amax);
+  if (threadIdx.x < 32) {
+    amax = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) amax = absmax_nan(__shfl_xor_sync(0xffffffffu, amax, o), amax);
+    if (threadIdx.x == 0) atomic_max_nonneg(norm_bits, amax);
   }
 }
 
@@ -56,11 +90,12 @@ __device__ __forceinline__ void block_absmax(double amax, unsigned long long* no
 // equation was solved with the old black neighbours, so its defect is
 // h^-2 * sum over its black neighbours of (new - old) = h^-2 sum delta.
 template <class R>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(kLineBlock)
     k_defect_from_delta(const R* __restrict__ delta, R* __restrict__ r, const R* __restrict__ zero,
                         int d, int n, int M, int log_tpl, int npts, int red_par, R hinv2,
                         unsigned long long* __restrict__ norm_bits, size_t fstride) {
-  const LineMap lm(log_tpl);
+  constexpr int W = Vec<R>::W;
+  const LineMap<R> lm(log_tpl);
   delta += blockIdx.y * fstride;
   r += blockIdx.y * fstride;
   if (norm_bits != nullptr) norm_bits += blockIdx.y;
@@ -71,10 +106,10 @@ __global__ void __launch_bounds__(128)
     const int par = d == 1 ? (i & 1) : ((i + j) & 1);
     R* rp = r + (size_t)p * M;
     if (par != red_par) {
-      for (int m = lm.m0; m < M; m += lm.step) {
-        rp[m] = R(0);
-        rp[m + 1] = R(0);
-      }
+      Vec<R> z;
+#pragma unroll
+      for (int k = 0; k < W; ++k) z.v[k] = R(0);
+      for (int m = lm.m0; m < M; m += lm.step) vstore(rp + m, z);
     } else {
       // neighbour lines, the zero line outside the grid; four reads, three
       // additions and one product per value
@@ -85,18 +120,24 @@ __global__ void __launch_bounds__(128)
       const R* no = d == 2 && j < n - 1 ? delta + pM + nM : zero;
       const bool four = d == 2;
       for (int m = lm.m0; m < M; m += lm.step) {
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          R sum = w[m + k] + e[m + k];
-          if (four) sum = sum + (so[m + k] + no[m + k]);
-          const R v = hinv2 * sum;
-          rp[m + k] = v;
-          amax = absmax_nan((double)fabs(v), amax);
+        const Vec<R> a = vload(w + m), b = vload(e + m);
+        Vec<R> c, g, out;
+        if (four) {
+          c = vload(so + m);
+          g = vload(no + m);
         }
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+          R sum = a.v[k] + b.v[k];
+          if (four) sum = sum + (c.v[k] + g.v[k]);
+          out.v[k] = hinv2 * sum;
+          amax = absmax_nan((double)fabs(out.v[k]), amax);
+        }
+        vstore(rp + m, out);
       }
     }
   }
-  if (norm_bits != nullptr) block_absmax<R>(amax, norm_bits);
+  if (norm_bits != nullptr) block_absmax(amax, norm_bits);
 }
 
 // ---------------------------------------------------------------------------------
@@ -105,10 +146,11 @@ __global__ void __launch_bounds__(128)
 
 // Full weighting, (1/4)[1 2 1] per dimension; also clears the coarse correction.
 template <class R>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(kLineBlock)
     k_restrict(const R* __restrict__ r, R* __restrict__ fc, R* __restrict__ uc, int d, int n, int M,
                int log_tpl, int ncpts, size_t fstride, size_t cstride) {
-  const LineMap lm(log_tpl);
+  constexpr int W = Vec<R>::W;
+  const LineMap<R> lm(log_tpl);
   r += blockIdx.y * fstride;
   fc += blockIdx.y * cstride;
   uc += blockIdx.y * cstride;
@@ -117,14 +159,18 @@ __global__ void __launch_bounds__(128)
   const int P = lm.line;
   R* fo = fc + (size_t)P * M;
   R* uo = uc + (size_t)P * M;
+  Vec<R> z;
+#pragma unroll
+  for (int k = 0; k < W; ++k) z.v[k] = R(0);
   if (d == 1) {
     const R* c = r + (size_t)(2 * P + 1) * M;
     for (int m = lm.m0; m < M; m += lm.step) {
+      const Vec<R> a = vload(c + m - M), b = vload(c + m), e = vload(c + m + M);
+      Vec<R> out;
 #pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        fo[m + k] = R(0.25) * (c[m + k - M] + R(2) * c[m + k] + c[m + k + M]);
-        uo[m + k] = R(0);
-      }
+      for (int k = 0; k < W; ++k) out.v[k] = R(0.25) * (a.v[k] + R(2) * b.v[k] + e.v[k]);
+      vstore(fo + m, out);
+      vstore(uo + m, z);
     }
   } else {
     const int I = P % nc, J = P / nc;
@@ -134,15 +180,24 @@ __global__ void __launch_bounds__(128)
     const R* cs = c - nM;
     const R* cn = c + nM;
     for (int m = lm.m0; m < M; m += lm.step) {
+      Vec<R> out;
+      {
+        const Vec<R> a = vload(cs + m - M), b = vload(cs + m), e = vload(cs + m + M);
 #pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        const int q = m + k;
-        const R row_m = cs[q - M] + R(2) * cs[q] + cs[q + M];
-        const R row_0 = c[q - M] + R(2) * c[q] + c[q + M];
-        const R row_p = cn[q - M] + R(2) * cn[q] + cn[q + M];
-        fo[q] = R(0.0625) * (row_m + R(2) * row_0 + row_p);
-        uo[q] = R(0);
+        for (int k = 0; k < W; ++k) out.v[k] = a.v[k] + R(2) * b.v[k] + e.v[k];
       }
+      {
+        const Vec<R> a = vload(c + m - M), b = vload(c + m), e = vload(c + m + M);
+#pragma unroll
+        for (int k = 0; k < W; ++k) out.v[k] = out.v[k] + R(2) * (a.v[k] + R(2) * b.v[k] + e.v[k]);
+      }
+      {
+        const Vec<R> a = vload(cn + m - M), b = vload(cn + m), e = vload(cn + m + M);
+#pragma unroll
+        for (int k = 0; k < W; ++k) out.v[k] = R(0.0625) * (out.v[k] + (a.v[k] + R(2) * b.v[k] + e.v[k]));
+      }
+      vstore(fo + m, out);
+      vstore(uo + m, z);
     }
   }
 }
@@ -176,10 +231,11 @@ struct Taps {
 };
 
 template <class R>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(kLineBlock)
     k_prolong(R* __restrict__ u, const R* __restrict__ uc, int d, int n, int M, int log_tpl,
               int npts, size_t fstride, size_t cstride) {
-  const LineMap lm(log_tpl);
+  constexpr int W = Vec<R>::W;
+  const LineMap<R> lm(log_tpl);
   u += blockIdx.y * fstride;
   uc += blockIdx.y * cstride;
   if (lm.line >= npts) return;
@@ -195,21 +251,23 @@ __global__ void __launch_bounds__(128)
   const R* e = uc + ((size_t)tx.i1 + row1) * M;
   const R w = R((tx.half ? 0.5f : 1.f) * (ty.half ? 0.5f : 1.f));
   const int taps = tx.count * ty.count;  // 1, 2 (in x or in y) or 4
-  const bool two_y = ty.count == 2;
+  // the second tap of a two-tap point: the other coarse line in x, or in y
+  const R* second = ty.count == 2 ? c : b;
   for (int m = lm.m0; m < M; m += lm.step) {
+    Vec<R> sum = vload(a + m);
+    if (taps == 4) {
+      const Vec<R> vb = vload(b + m), vc = vload(c + m), ve = vload(e + m);
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      const int q = m + k;
-      R sum;
-      if (taps == 1) {
-        sum = a[q];
-      } else if (taps == 4) {
-        sum = (a[q] + b[q]) + (c[q] + e[q]);
-      } else {
-        sum = a[q] + (two_y ? c[q] : b[q]);
-      }
-      up[q] = w == R(1) ? up[q] + sum : up[q] + w * sum;
+      for (int k = 0; k < W; ++k) sum.v[k] = (sum.v[k] + vb.v[k]) + (vc.v[k] + ve.v[k]);
+    } else if (taps == 2) {
+      const Vec<R> vs = vload(second + m);
+#pragma unroll
+      for (int k = 0; k < W; ++k) sum.v[k] = sum.v[k] + vs.v[k];
     }
+    Vec<R> cur = vload_rw(up + m);
+#pragma unroll
+    for (int k = 0; k < W; ++k) cur.v[k] = w == R(1) ? cur.v[k] + sum.v[k] : cur.v[k] + w * sum.v[k];
+    vstore(up + m, cur);
   }
 }
 
@@ -271,7 +329,7 @@ __global__ void __launch_bounds__(128)
     if (out != nullptr) out[i] = (float)v;
     amax = absmax_nan(fabs(v), amax);
   }
-  block_absmax<double>(amax, norm_bits + blockIdx.y);
+  block_absmax(amax, norm_bits + blockIdx.y);
 }
 
 // Initial value g of every instance (blockIdx.y): u = g along time (initial
@@ -484,11 +542,13 @@ __global__ void k_round_cx(Cx<float>* __restrict__ dst, const Cx<double>* __rest
 
 
 // Launch geometry of the line-wise kernels: log2 of the threads per line and
-// the number of 128-thread blocks for `lines` lines.
+// the number of 256-thread blocks for `lines` lines of M values of R.
+template <class R>
 inline void line_grid(int M, int lines, int* log_tpl, unsigned* blocks) {
-  const int tpl = M / 2 < 128 ? M / 2 : 128;
+  const int per = M / Vec<R>::W;
+  const int tpl = per < 64 ? per : 64;
   *log_tpl = ilog2(tpl);
-  const int lpb = 128 / tpl;
+  const int lpb = kLineBlock / tpl;
   *blocks = (unsigned)((lines + lpb - 1) / lpb);
 }
 
@@ -500,8 +560,8 @@ cudaError_t launch_defect_from_delta(const R* delta, R* r, const R* zero, const 
   if (ls.batch == 0) return cudaSuccess;
   int log_tpl;
   unsigned blocks;
-  line_grid(ls.M, npts, &log_tpl, &blocks);
-  k_defect_from_delta<R><<<dim3(blocks, ls.batch), 128, 0, s>>>(
+  line_grid<R>(ls.M, npts, &log_tpl, &blocks);
+  k_defect_from_delta<R><<<dim3(blocks, ls.batch), kLineBlock, 0, s>>>(
       delta, r, zero, ls.d, ls.n, ls.M, log_tpl, npts, red_par, hinv2, norm_bits,
       ls.field_stride());
   return counted(cudaGetLastError());
@@ -514,8 +574,8 @@ cudaError_t launch_restrict(const R* r, R* fc, R* uc, const LevelShape& ls, cuda
   if (ncpts == 0 || ls.batch == 0) return cudaSuccess;
   int log_tpl;
   unsigned blocks;
-  line_grid(ls.M, ncpts, &log_tpl, &blocks);
-  k_restrict<R><<<dim3(blocks, ls.batch), 128, 0, s>>>(r, fc, uc, ls.d, ls.n, ls.M, log_tpl, ncpts,
+  line_grid<R>(ls.M, ncpts, &log_tpl, &blocks);
+  k_restrict<R><<<dim3(blocks, ls.batch), kLineBlock, 0, s>>>(r, fc, uc, ls.d, ls.n, ls.M, log_tpl, ncpts,
                                                        ls.field_stride(), (size_t)ncpts * ls.M);
   return counted(cudaGetLastError());
 }
@@ -528,8 +588,8 @@ cudaError_t launch_prolong(R* u, const R* uc, const LevelShape& ls, cudaStream_t
   if (ls.batch == 0) return cudaSuccess;
   int log_tpl;
   unsigned blocks;
-  line_grid(ls.M, npts, &log_tpl, &blocks);
-  k_prolong<R><<<dim3(blocks, ls.batch), 128, 0, s>>>(u, uc, ls.d, ls.n, ls.M, log_tpl, npts,
+  line_grid<R>(ls.M, npts, &log_tpl, &blocks);
+  k_prolong<R><<<dim3(blocks, ls.batch), kLineBlock, 0, s>>>(u, uc, ls.d, ls.n, ls.M, log_tpl, npts,
                                                       ls.field_stride(), cstride);
   return counted(cudaGetLastError());
 }

@@ -16,6 +16,8 @@ Modules
   separable  exact discrete solution for separable sources (sine eigenvector)
   mgwr       Algorithm 1 (WRMG) in 1-D and 2-D: red-black waveform smoother,
              defect, full weighting, linear / bilinear interpolation, V/W cycles
+  mittag_leffler  E_alpha(z) by its power series: the exact solution of the
+             Sec. 7 experiment with initial value sin x
 
 Pin status: every function above is pinned by a CPU test against something
 other than itself (closed forms, a dense solve, brute force, special cases);

@@ -82,6 +82,10 @@ def parse():
     p.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     p.add_argument("--requests", type=int, default=200, help="c4: first R requests of the stream")
     p.add_argument("--slots", type=int, default=4, help="c4: server slots")
+    p.add_argument("--rate", type=float, default=None,
+                   help="c4: Poisson arrival rate, requests/s (default 0.7 x the sustained rate)")
+    p.add_argument("--policy", default="fifo", choices=["fifo", "smallest"],
+                   help="c4: server admission order")
     p.add_argument("--inner", type=int, default=None, help="mixed modes: FP32 cycles per outer defect")
     p.add_argument("--alpha", type=float, default=None)
     p.add_argument("--no-autotune", action="store_true", help="keep the default engine launch shapes")
@@ -319,6 +323,8 @@ def run_served(args):
         outstanding = [0]
         lock = threading.Condition()
         with mgwr.Server(hbm_budget=budget, slots=args.slots) as srv:
+            srv.set_policy(mgwr.MGWR_POLICY_SMALLEST if args.policy == "smallest"
+                           else mgwr.MGWR_POLICY_FIFO)
             tickets = [None] * len(reqs)
             t0 = time.perf_counter()
 
@@ -359,8 +365,9 @@ def run_served(args):
     total = sum(unknowns(r) for r in reqs)
     span1, _, res1, _ = run([0.0] * len(reqs))
     rate = len(reqs) / span1
+    offered = args.rate if args.rate else 0.7 * rate
     rng = np.random.default_rng(1608)
-    arr = np.cumsum(rng.exponential(1.0 / (0.7 * rate), size=len(reqs)))
+    arr = np.cumsum(rng.exponential(1.0 / offered, size=len(reqs)))
     span2, lat, res2, info = run(list(arr))
     ok = sum(1 for r in res2 if r.status == mgwr.MGWR_OK)
     lat_ms = np.array(lat) * 1e3
@@ -373,9 +380,10 @@ def run_served(args):
                                "1-D n=2^k-1 k~U{5..12} or 2-D k~U{5..9}, M=2^j j~U{7..12}, "
                                "alpha~U[0.1,0.9], u=t^2 or t^alpha sin, Poisson arrivals at 0.7x "
                                "the sustained rate", "name": "c4", "slots": args.slots,
+                   "admission": args.policy,
                    "hbm_budget_bytes": budget, "host_window_bytes": host_cap},
         "served": {"p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
-                   "sustained_requests_per_s": rate, "offered_requests_per_s": 0.7 * rate,
+                   "sustained_requests_per_s": rate, "offered_requests_per_s": offered,
                    "back_to_back_unknowns_per_s": total / span1, "completed_ok": ok,
                    "requests": len(reqs), "total_unknowns": total, "peak_bytes": info["peak_bytes"]},
     }

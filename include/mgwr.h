@@ -261,8 +261,14 @@ int mgwr_footprint(int d, int n, int M, int batch, int precision, size_t* bytes)
  * time on its own CUDA stream, and admits queued requests while the sum of
  * their footprints (mgwr_footprint) stays within `hbm_budget` bytes.  Requests
  * of any shape may be in flight together; their kernels overlap on the device.
- * The oldest request that fits runs first; one passed over 64 times blocks
- * younger ones until it fits.  Thread-safe: submit and poll from any thread. */
+ * Admission order (mgwr_server_set_policy; the paper has no counterpart):
+ * MGWR_POLICY_FIFO (default), the oldest request that fits runs first;
+ * MGWR_POLICY_SMALLEST, the request with the fewest space-time unknowns n^d*M
+ * that fits (ties: the oldest), which keeps small requests from waiting behind
+ * large ones.  Under both, a request passed over 64 times blocks the others
+ * until it fits.  Thread-safe: submit and poll from any thread. */
+#define MGWR_POLICY_FIFO 0
+#define MGWR_POLICY_SMALLEST 1
 typedef struct mgwr_server* mgwr_server_t;
 typedef struct {
   int d, n, M;            /* shape, as for mgwr_create                         */
@@ -290,6 +296,9 @@ typedef struct {
 int mgwr_server_create(size_t hbm_budget, int max_slots, mgwr_server_t* out);
 /* Stops the workers after their current requests; queued requests are dropped. */
 int mgwr_server_destroy(mgwr_server_t s);
+/* MGWR_POLICY_FIFO or MGWR_POLICY_SMALLEST; applies to requests admitted from
+ * now on.  MGWR_E_INVAL for another value. */
+int mgwr_server_set_policy(mgwr_server_t s, int policy);
 /* Copies the request's data and queues it: MGWR_OK with *ticket set,
  * MGWR_E_INVAL (bad request), MGWR_E_TOOBIG (footprint above the budget),
  * MGWR_E_AGAIN (queue full). */

@@ -46,6 +46,7 @@ bool pow2(long long x) { return x > 0 && (x & (x - 1)) == 0; }
 struct mgwr_server {
   size_t budget = 0, in_use = 0, peak = 0;
   int slots = 1, max_queue = 1 << 20, device = 0;
+  int policy = MGWR_POLICY_FIFO;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<Ticket*> queue;
@@ -58,23 +59,35 @@ struct mgwr_server {
 
 namespace {
 
-// Queue position that may start now: the oldest request that fits the free
-// memory.  A request that was passed over this many times blocks younger ones
-// until it fits (no starvation of large requests).
+// Queue position that may start now.  FIFO: the oldest request that fits the
+// free memory.  SMALLEST: the request with the fewest space-time unknowns
+// that fits (ties: the oldest).  Either way a request that was passed over
+// this many times blocks the others until it fits (no starvation of large
+// requests), and every request older than the one taken counts as passed over.
 constexpr int kMaxSkips = 64;
 
 Ticket* pick(mgwr_server* s) {
   const size_t free_bytes = s->budget - s->in_use;
+  auto chosen = s->queue.end();
   for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
     Ticket* t = *it;
-    if (t->footprint <= free_bytes) {
-      for (auto jt = s->queue.begin(); jt != it; ++jt) (*jt)->skipped++;
-      s->queue.erase(it);
-      return t;
+    if (t->skipped >= kMaxSkips) {  // starving: it goes next, or nothing does
+      if (t->footprint <= free_bytes) chosen = it;
+      break;
     }
-    if (t->skipped >= kMaxSkips) return nullptr;
+    if (t->footprint > free_bytes) continue;
+    if (chosen == s->queue.end()) {
+      chosen = it;
+      if (s->policy == MGWR_POLICY_FIFO) break;
+    } else if (t->N * (size_t)t->rq.M < (*chosen)->N * (size_t)(*chosen)->rq.M) {
+      chosen = it;
+    }
   }
-  return nullptr;
+  if (chosen == s->queue.end()) return nullptr;
+  for (auto jt = s->queue.begin(); jt != chosen; ++jt) (*jt)->skipped++;
+  Ticket* t = *chosen;
+  s->queue.erase(chosen);
+  return t;
 }
 
 int run_request(Ticket* t) {
@@ -165,6 +178,17 @@ int mgwr_server_create(size_t hbm_budget, int max_slots, mgwr_server_t* out) {
   cudaGetDevice(&s->device);
   for (int i = 0; i < max_slots; ++i) s->workers.emplace_back(worker, s);
   *out = s;
+  return MGWR_OK;
+}
+
+int mgwr_server_set_policy(mgwr_server_t s, int policy) {
+  if (s == nullptr) return MGWR_E_INVAL;
+  if (policy != MGWR_POLICY_FIFO && policy != MGWR_POLICY_SMALLEST) return MGWR_E_INVAL;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->policy = policy;
+  }
+  s->cv_work.notify_all();
   return MGWR_OK;
 }
 

@@ -31,6 +31,7 @@ MGWR_H64, MGWR_H32 = 64, 32
 MGWR_U, MGWR_F, MGWR_R = 0, 1, 2
 MGWR_RED, MGWR_BLACK = 0, 1
 MGWR_ORDER_TEXT, MGWR_ORDER_TABLE = 0, 1
+MGWR_POLICY_FIFO, MGWR_POLICY_SMALLEST = 0, 1
 
 
 class mgwr_stats(C.Structure):
@@ -99,6 +100,7 @@ _SIGS = {
     "mgwr_footprint": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_size_t)]),
     "mgwr_server_create": (C.c_int, [C.c_size_t, C.c_int, C.POINTER(C.c_void_p)]),
     "mgwr_server_destroy": (C.c_int, [C.c_void_p]),
+    "mgwr_server_set_policy": (C.c_int, [C.c_void_p, C.c_int]),
     "mgwr_submit": (C.c_int, [C.c_void_p, C.POINTER(mgwr_request), C.POINTER(C.c_uint64)]),
     "mgwr_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int, _dp, C.POINTER(mgwr_result)]),
     "mgwr_server_stats": (C.c_int, [C.c_void_p, C.POINTER(mgwr_server_info)]),
@@ -381,6 +383,11 @@ class Server:
             raise MGWRError(st, "mgwr_server_create failed")
         self.h = h
         self._shapes = {}
+
+    def set_policy(self, policy: int):
+        st = self.lib.mgwr_server_set_policy(self.h, policy)
+        if st != MGWR_OK:
+            raise MGWRError(st, "mgwr_server_set_policy")
 
     def submit(self, d, n, M, T, alpha, f, g=None, precision=MGWR_MIXED, order=MGWR_ORDER_TEXT,
                cycle=1, nu1=1, nu2=1, tol=1e-8, max_cycles=100) -> int:

@@ -106,4 +106,5 @@ def test_server_calls_reject_null_and_bad_arguments(lib):
     assert lib.mgwr_server_destroy(None) == mgwr.MGWR_OK
     h = C.c_void_p()
     assert lib.mgwr_server_create(0, 4, C.byref(h)) == mgwr.MGWR_E_INVAL
+    assert lib.mgwr_server_set_policy(None, mgwr.MGWR_POLICY_SMALLEST) == mgwr.MGWR_E_INVAL
     assert lib.mgwr_server_create(1 << 30, 0, C.byref(h)) == mgwr.MGWR_E_INVAL

@@ -87,3 +87,27 @@ def test_poll_timeout_unknown_ticket_and_numeric_failure():
         tb = srv.submit(1, 31, 64, 1.0, 0.5, bad, precision=G.MGWR_FP64)
         rb = srv.poll(tb, timeout_us=60_000_000)
         assert rb.status == G.MGWR_E_NUMERIC
+
+
+@pytest.mark.parametrize("policy", [G.MGWR_POLICY_FIFO, G.MGWR_POLICY_SMALLEST])
+def test_admission_policy_orders_queued_requests(policy):
+    # one slot: a blocker runs while a large and then three small requests queue;
+    # first in first out finishes the large one first, smallest first the small ones
+    blocker = inputs.Problem(2, 127, 512, 1.0, 0.5, "t2").rhs()
+    large = inputs.Problem(2, 255, 1024, 1.0, 0.5, "t2").rhs()
+    small = inputs.Problem(1, 63, 64, 1.0, 0.5, "t2").rhs()
+    with G.Server(hbm_budget=16 << 30, slots=1) as srv:
+        srv.set_policy(policy)
+        tb = srv.submit(2, 127, 512, 1.0, 0.5, blocker, precision=G.MGWR_FP64)
+        tl = srv.submit(2, 255, 1024, 1.0, 0.5, large, precision=G.MGWR_FP64)
+        ts = [srv.submit(1, 63, 64, 1.0, 0.5, small, precision=G.MGWR_FP64) for _ in range(3)]
+        rb = srv.poll(tb, timeout_us=120_000_000, copy_solution=False)
+        rl = srv.poll(tl, timeout_us=120_000_000, copy_solution=False)
+        rs = [srv.poll(t, timeout_us=120_000_000, copy_solution=False) for t in ts]
+    assert rb.status == rl.status == G.MGWR_OK and all(r.status == G.MGWR_OK for r in rs)
+    if policy == G.MGWR_POLICY_SMALLEST:
+        assert max(r.latency_s for r in rs) < rl.latency_s
+    else:
+        assert min(r.latency_s for r in rs) > rl.latency_s
+    with pytest.raises(G.MGWRError):
+        G.Server(hbm_budget=1 << 30, slots=1).set_policy(7)

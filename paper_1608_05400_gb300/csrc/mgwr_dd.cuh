@@ -79,6 +79,39 @@ __device__ __forceinline__ dd dd_add_float(dd a, float b) {
   return dd_fast_two_sum(s.hi, s.lo);
 }
 
+// Sum without the closing renormalisation (8 FP32 operations): hi is the
+// rounded sum of the leading words, lo their exact error plus the trailing
+// words.  The pair still stands for the sum to about 2^-46 of the operands'
+// magnitudes; the FFT butterflies chain these, and every product or accurate
+// sum that follows renormalises.
+__device__ __forceinline__ dd dd_add_lazy(dd a, dd b) {
+  dd s = dd_two_sum(a.hi, b.hi);
+  s.lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+  return s;
+}
+__device__ __forceinline__ dd dd_sub_lazy(dd a, dd b) {
+  dd s = dd_two_sum(a.hi, -b.hi);
+  s.lo = __fadd_rn(s.lo, __fsub_rn(a.lo, b.lo));
+  return s;
+}
+
+// a*b + c*e with one TwoSum (19 FP32 operations instead of two products and a
+// sum): the leading products p1, p2 with their exact errors from FMAs, the four
+// cross terms and both errors gathered in one FP32 sum, TwoSum(p1, p2) and one
+// Fast2Sum.  Error about 2^-46 (|a b| + |c e|), as for the separate operations.
+__device__ __forceinline__ dd dd_dot2(dd a, dd b, dd c, dd e) {
+  const float p1 = __fmul_rn(a.hi, b.hi);
+  const float p2 = __fmul_rn(c.hi, e.hi);
+  float t = __fmaf_rn(a.hi, b.hi, -p1);
+  t = __fadd_rn(t, __fmaf_rn(c.hi, e.hi, -p2));
+  t = __fmaf_rn(a.hi, b.lo, t);
+  t = __fmaf_rn(a.lo, b.hi, t);
+  t = __fmaf_rn(c.hi, e.lo, t);
+  t = __fmaf_rn(c.lo, e.hi, t);
+  const dd s = dd_two_sum(p1, p2);
+  return dd_fast_two_sum(s.hi, __fadd_rn(s.lo, t));
+}
+
 // magnitude used for norms: |hi| (relative error below 2^-23)
 __device__ __forceinline__ float dd_abs_hi(dd a) { return fabsf(a.hi); }
 

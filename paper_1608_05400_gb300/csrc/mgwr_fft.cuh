@@ -38,6 +38,25 @@ __device__ __forceinline__ Cx<R> cmulc(Cx<R> a, Cx<R> b) {
   return {a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y};
 }
 
+// Double-float complex arithmetic: butterfly sums without the closing
+// renormalisation, products as fused two-term dot products (mgwr_dd.cuh).
+template <>
+__device__ __forceinline__ Cx<dd> cadd<dd>(Cx<dd> a, Cx<dd> b) {
+  return {dd_add_lazy(a.x, b.x), dd_add_lazy(a.y, b.y)};
+}
+template <>
+__device__ __forceinline__ Cx<dd> csub<dd>(Cx<dd> a, Cx<dd> b) {
+  return {dd_sub_lazy(a.x, b.x), dd_sub_lazy(a.y, b.y)};
+}
+template <>
+__device__ __forceinline__ Cx<dd> cmul<dd>(Cx<dd> a, Cx<dd> b) {
+  return {dd_dot2(a.x, b.x, -a.y, b.y), dd_dot2(a.x, b.y, a.y, b.x)};
+}
+template <>
+__device__ __forceinline__ Cx<dd> cmulc<dd>(Cx<dd> a, Cx<dd> b) {
+  return {dd_dot2(a.x, b.x, a.y, b.y), dd_dot2(a.y, b.x, -a.x, b.y)};
+}
+
 // Multiplication by powers of w8 = exp(-+2 pi i / 8) (INV: the + sign).
 template <bool INV, class R>
 __device__ __forceinline__ Cx<R> mul_w1(Cx<R> a) {

@@ -78,7 +78,7 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--precision", default=None, choices=["fp64", "mixed", "mixed_dd"])
+    p.add_argument("--precision", default=None, choices=["fp64", "mixed", "mixed_dd", "dd"])
     p.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     p.add_argument("--requests", type=int, default=200, help="c4: first R requests of the stream")
     p.add_argument("--slots", type=int, default=4, help="c4: server slots")
@@ -433,12 +433,14 @@ def main():
         unknowns = batch * n ** d * Mw
     stream = torch.cuda.Stream()
     s.set_stream(stream.cuda_stream)
-    prec_code = {"fp64": mgwr.MGWR_FP64, "mixed": mgwr.MGWR_MIXED, "mixed_dd": mgwr.MGWR_MIXED_DD}
+    prec_code = {"fp64": mgwr.MGWR_FP64, "mixed": mgwr.MGWR_MIXED, "mixed_dd": mgwr.MGWR_MIXED_DD,
+                 "dd": mgwr.MGWR_DD}
+    mixed = precision in ("mixed", "mixed_dd")
     if precision != "fp64":
         s.set_precision(prec_code[precision])
-        inner = args.inner or WORKLOAD_INNER.get(args.workload)
-        if inner:
-            s.set_inner_cycles(inner)
+    inner = args.inner or WORKLOAD_INNER.get(args.workload)
+    if mixed and inner:
+        s.set_inner_cycles(inner)
 
     # launch shapes of the FFT-engine kernels, timed on this handle's data (setup,
     # outside the timed region)
@@ -516,14 +518,15 @@ def main():
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp64": "f64", "mixed": "f32 cycles + f64 defect/update",
-                  "mixed_dd": "f32 cycles + f32x2 (double-float) defect/update"}[precision],
+                  "mixed_dd": "f32 cycles + f32x2 (double-float) defect/update",
+                  "dd": "f32x2 (double-float)"}[precision],
         "data": "synthetic",
         "config": {"workload": f"{desc}, " + (f"alpha={alpha}, " if batch == 1 else "")
                                + f"V({NU1},{NU2}) red-black, rel-res {tol}",
                    "name": args.workload, "precision": precision,
                    "engine_splits": splits,
                    "inner_cycles": (args.inner or WORKLOAD_INNER.get(args.workload) or 2)
-                   if precision != "fp64" else None,
+                   if mixed else None,
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": f"inputs larger than L2 ({unknowns * 8 / 1e6:.0f} MB per FP64 field)"},
         "solve": {"cycles": stats[-1].cycles, "outer": stats[-1].outer, "relres": stats[-1].relres,

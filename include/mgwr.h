@@ -62,15 +62,25 @@ extern "C" {
 #define MGWR_FP64 0  /* every kernel in IEEE double                          */
 #define MGWR_MIXED 1 /* FP32 V-cycles on the defect, FP64 defect + update     */
 #define MGWR_MIXED_DD 2 /* FP32 V-cycles; defect + update in double-float    */
+#define MGWR_DD 3       /* refinement with double-float inner cycles         */
 /* MGWR_MIXED_DD keeps the finest iterate and right-hand side as double-float
  * pairs (hi + lo of two floats, about 48 significant bits) and computes the
  * outer defect and the update with FP32 instructions only (GB300 runs FP32 64x
  * faster than FP64).  Its stopping test uses that defect; mgwr_residual gives
- * the IEEE-double defect of the result. */
+ * the IEEE-double defect of the result.
+ * MGWR_DD is the same refinement with its inner cycles on a third hierarchy
+ * in double-float (8 bytes per value): each outer step reduces the defect as
+ * `inner` FP64 cycles do, also where FP32 rounding limits the mixed refinement
+ * (4 eps32 / (pi h)^2 close to 1), with FP32 instructions only.  The iterate
+ * itself never passes through a convolution (only corrections do), so the
+ * rounding of the transforms, about 2^-44 of a field's scale, is not amplified
+ * by the discrete Laplacian's 4/h^2.  Its norms and stopping test use the
+ * double-float defect. */
 
 /* which hierarchy a component call addresses */
 #define MGWR_H64 64  /* the double-precision hierarchy                         */
 #define MGWR_H32 32  /* the single-precision hierarchy (MGWR_MIXED only)       */
+#define MGWR_HDD 48  /* the double-float hierarchy (MGWR_DD only)              */
 
 /* fields of a level */
 #define MGWR_U 0 /* iterate (finest) or coarse correction e (coarser levels)  */
@@ -127,7 +137,7 @@ const char* mgwr_last_error(mgwr_t h);
 const char* mgwr_status_string(int status);
 
 /* MGWR_FP64 (default), MGWR_MIXED or MGWR_MIXED_DD (both allocate the FP32
- * hierarchy). */
+ * hierarchy), or MGWR_DD (allocates the double-float hierarchy). */
 int mgwr_set_precision(mgwr_t h, int precision);
 /* MGWR_ORDER_TEXT (default) or MGWR_ORDER_TABLE. */
 int mgwr_set_order(mgwr_t h, int order);
@@ -138,8 +148,8 @@ int mgwr_set_inner_cycles(mgwr_t h, int cycles);
 
 /* Launch shape of the FFT-engine kernels (no counterpart in the paper; the
  * results are bitwise the same for every shape).  For kernel class
- * MGWR_K_SWEEP64, MGWR_K_SWEEP32 (also the one-point solves of that
- * arithmetic), MGWR_K_DEFECT64, MGWR_K_DEFECT32 or MGWR_K_DEFECT_DD, `split`
+ * MGWR_K_SWEEP64, MGWR_K_SWEEP32, MGWR_K_SWEEP_DD (also the one-point solves
+ * of that arithmetic), MGWR_K_DEFECT64, MGWR_K_DEFECT32 or MGWR_K_DEFECT_DD, `split`
  * = E in {1, 2, 4} radix-8 butterflies per thread and stage: a group of
  * L/(8E) threads transforms one line pair of length L = 2M (8192 for
  * M > 4096, where E is 1 or 2), synchronising with warp barriers when the
@@ -275,7 +285,7 @@ typedef struct {
   double T, alpha;
   const double* f;        /* N*M right-hand side, host; copied by mgwr_submit  */
   const double* g;        /* N initial values or NULL; copied                 */
-  int precision;          /* MGWR_FP64 or MGWR_MIXED                          */
+  int precision;          /* MGWR_FP64, MGWR_MIXED, MGWR_MIXED_DD or MGWR_DD    */
   int order;              /* MGWR_ORDER_TEXT or MGWR_ORDER_TABLE              */
   int cycle, nu1, nu2;    /* as for mgwr_solve                                */
   double tol;
@@ -325,8 +335,9 @@ int mgwr_launch_count(mgwr_t h, long long* count);
 #define MGWR_K_COARSEST 6   /* one-point solves                                 */
 #define MGWR_K_REFINE 7     /* mixed-precision update u64 += e32                */
 #define MGWR_K_DEFECT_DELTA 8 /* defect after a smoothing step, no convolution  */
-#define MGWR_K_DEFECT_DD 9  /* double-float outer defects (MGWR_MIXED_DD)      */
-#define MGWR_NUM_KERNEL_CLASSES 10
+#define MGWR_K_DEFECT_DD 9  /* double-float defects (MGWR_MIXED_DD outer, MGWR_DD) */
+#define MGWR_K_SWEEP_DD 10  /* double-float colour half-sweeps (MGWR_DD)        */
+#define MGWR_NUM_KERNEL_CLASSES 11
 /* enable != 0: from now on every launch of the solver is bracketed by CUDA
  * events on the handle's stream (clears the totals).  Adds event records
  * between launches; meant for a measurement run, not for timed runs. */

@@ -11,6 +11,7 @@
 #include <mutex>
 #include <new>
 #include <tuple>
+#include <type_traits>
 #include <string>
 #include <vector>
 
@@ -66,6 +67,7 @@ struct mgwr_handle {
   double* c_dev = nullptr;      // batch
   Hier<double> h64;
   Hier<float> h32;
+  Hier<mgwr::dd> hdd;  // MGWR_DD: every level in double-float
   // double-float copies of the finest iterate / right-hand side and of the
   // Toeplitz spectra, for the outer defect of MGWR_MIXED_DD
   mgwr::dd* u_dd = nullptr;
@@ -161,6 +163,18 @@ int ensure_field(mgwr_t h, R** p, size_t count) {
 
 bool is_pow2(long long x) { return x > 0 && (x & (x - 1)) == 0; }
 
+// Engine kernel classes of a hierarchy's arithmetic.
+template <class R>
+constexpr int sweep_class() {
+  return std::is_same<R, float>::value ? MGWR_K_SWEEP32
+         : std::is_same<R, mgwr::dd>::value ? MGWR_K_SWEEP_DD : MGWR_K_SWEEP64;
+}
+template <class R>
+constexpr int defect_class() {
+  return std::is_same<R, float>::value ? MGWR_K_DEFECT32
+         : std::is_same<R, mgwr::dd>::value ? MGWR_K_DEFECT_DD : MGWR_K_DEFECT64;
+}
+
 int split_of(const mgwr_handle* h, int cls, int l) {
   return h->split[cls].empty() ? 0 : h->split[cls][l];
 }
@@ -252,6 +266,24 @@ int ensure_dd(mgwr_t h) {
   return MGWR_OK;
 }
 
+// The double-float hierarchy of MGWR_DD: every level's fields in double-float,
+// the inverse-column and Toeplitz spectra and the twiddles split from FP64.
+int ensure_hdd(mgwr_t h) {
+  if (h->hdd.ready) return MGWR_OK;
+  MGWR_TRY(ensure_dd(h));
+  Hier<mgwr::dd>& H = h->hdd;
+  MGWR_TRY(ensure_full(h, H));
+  const size_t nspec = (size_t)h->B * h->nlev * h->L;
+  MGWR_TRY(dev_alloc(h, &H.spec, sizeof(Cx<mgwr::dd>) * nspec));
+  MGWR_CK(h, mgwr::launch_split_cx(H.spec, h->h64.spec, nspec, h->stream));
+  H.tspec = h->tspec_dd;
+  H.tw = h->tw_dd;
+  H.zero = h->zero_dd;
+  MGWR_CK(h, cudaStreamSynchronize(h->stream));
+  H.ready = true;
+  return MGWR_OK;
+}
+
 // ---- per-class timing ----------------------------------------------------------
 
 // Records an event before a launch of class `cls` covering `lines` time lines;
@@ -297,7 +329,7 @@ int coarsest(mgwr_t h, Hier<R>& H) {
   const int pm = prof_begin(h, MGWR_K_COARSEST, (double)h->B);
   MGWR_CK(h, mgwr::launch_sweep<R>(H.f[0], H.u[0], (R*)nullptr, H.spec, (size_t)h->nlev * h->L,
                                     H.tw, H.zero, scratch_for<R>(h), shape(h, 0), 0, true, R(0),
-                                    split_of(h, sizeof(R) == 8 ? MGWR_K_SWEEP64 : MGWR_K_SWEEP32, 0),
+                                    split_of(h, sweep_class<R>(), 0),
                                     h->stream));
   prof_end(h, pm);
   H.rs[0] = R_STALE;
@@ -311,11 +343,11 @@ int sweep_colour(mgwr_t h, Hier<R>& H, int l, int colour, R* delta) {
   const int par = parity(h, colour);
   const size_t N = points(h, l);
   const double lines = (double)h->B * (double)(par == 0 ? (N + 1) / 2 : N / 2);
-  const int pm = prof_begin(h, sizeof(R) == 8 ? MGWR_K_SWEEP64 : MGWR_K_SWEEP32, lines);
+  const int pm = prof_begin(h, sweep_class<R>(), lines);
   MGWR_CK(h, mgwr::launch_sweep<R>(H.f[l], H.u[l], delta, H.spec + (size_t)l * h->L,
                                     (size_t)h->nlev * h->L, H.tw, H.zero, scratch_for<R>(h), shape(h, l), par,
                                     false, R(h->hinv2[l]),
-                                    split_of(h, sizeof(R) == 8 ? MGWR_K_SWEEP64 : MGWR_K_SWEEP32, l),
+                                    split_of(h, sweep_class<R>(), l),
                                     h->stream));
   prof_end(h, pm);
   return MGWR_OK;
@@ -344,11 +376,11 @@ int smooth(mgwr_t h, Hier<R>& H, int l, int steps) {
 // Full defect r = f - (T_M (x) I + A_h) u with one FFT convolution per line.
 template <class R>
 int defect(mgwr_t h, Hier<R>& H, int l, unsigned long long* norm_bits) {
-  const int pm = prof_begin(h, sizeof(R) == 8 ? MGWR_K_DEFECT64 : MGWR_K_DEFECT32,
+  const int pm = prof_begin(h, defect_class<R>(),
                             (double)(points(h, l) * h->B));
   MGWR_CK(h, (mgwr::launch_defect<R, R>(H.u[l], H.f[l], H.r[l], H.tspec, (size_t)h->L, H.tw,
                                          H.zero, scratch_for<R>(h), shape(h, l), R(h->hinv2[l]), norm_bits,
-                                         split_of(h, sizeof(R) == 8 ? MGWR_K_DEFECT64 : MGWR_K_DEFECT32, l),
+                                         split_of(h, defect_class<R>(), l),
                                          h->stream)));
   prof_end(h, pm);
   H.rs[l] = R_CURRENT;
@@ -487,25 +519,63 @@ double relative(mgwr_t h, const std::vector<double>& norms, std::vector<double>&
   return worst;
 }
 
+// Double-float defect of the double-float iterate (u_dd, f_dd) into the
+// double-float hierarchy's finest right-hand side, norms into norm_bits
+// (MGWR_DD's outer defect; the iterate itself never passes through a
+// convolution, so its rounding stays at the double-float level).
+int outer_defect_ddd(mgwr_t h) {
+  const int L = h->nlev - 1;
+  const int pd = prof_begin(h, MGWR_K_DEFECT_DD, (double)(points(h, L) * h->B));
+  MGWR_CK(h, (mgwr::launch_defect<mgwr::dd, mgwr::dd>(
+                 h->u_dd, h->f_dd, h->hdd.f[L], h->tspec_dd, (size_t)h->L, h->tw_dd, h->zero_dd,
+                 scratch_for<mgwr::dd>(h), shape(h, L), mgwr::dd(h->hinv2[L]), h->norm_bits,
+                 split_of(h, MGWR_K_DEFECT_DD, L), h->stream)));
+  prof_end(h, pd);
+  h->hdd.rs[L] = R_STALE;
+  return MGWR_OK;
+}
+
+// One cycle on hierarchy H and the finest defect norms (from the smoothing
+// changes when the cycle ended with a smoothing step: *exact = false).
+template <class R>
+int enqueue_plain(mgwr_t h, Hier<R>& H, int cyc, int nu1, int nu2, bool* exact) {
+  const int L = h->nlev - 1;
+  MGWR_TRY(cycle(h, H, L, cyc, nu1, nu2));
+  MGWR_TRY(clear_norms(h));
+  if (H.rs[L] == R_DELTA) {
+    MGWR_TRY(defect_from_delta(h, H, L, h->norm_bits));
+    *exact = false;
+  } else {
+    MGWR_TRY(defect(h, H, L, h->norm_bits));
+    *exact = true;
+  }
+  return MGWR_OK;
+}
+
 // Enqueues one iteration of the solve loop and the copy of its per-instance
 // norms to pinned host memory, with no host synchronisation (so that it can be
 // captured into a graph).  FP64: one cycle, then the finest defect norms (from
 // the smoothing changes when the cycle ended with a smoothing step, *exact =
 // false).  Mixed: `inner` FP32 cycles on the defect equation from e = 0, the
 // update, and the outer defect (double or double-float) with its norms.
+// MGWR_DD: the same with double-float inner cycles and outer defect.
 int enqueue_iteration(mgwr_t h, int cyc, int nu1, int nu2, bool* exact) {
   const int L = h->nlev - 1;
   const size_t cnt = level_count(h, L);
   if (h->precision == MGWR_FP64) {
-    MGWR_TRY(cycle(h, h->h64, L, cyc, nu1, nu2));
+    MGWR_TRY(enqueue_plain(h, h->h64, cyc, nu1, nu2, exact));
+  } else if (h->precision == MGWR_DD) {
+    // double-float cycles on the defect equation from e = 0, the update of the
+    // double-float iterate, its double-float defect as the next right-hand side
+    MGWR_CK(h, cudaMemsetAsync(h->hdd.u[L], 0, cnt * sizeof(mgwr::dd), h->stream));
+    h->hdd.rs[L] = R_ZERO_U;
+    for (int k = 0; k < h->inner; ++k) MGWR_TRY(cycle(h, h->hdd, L, cyc, nu1, nu2));
+    const int pm = prof_begin(h, MGWR_K_REFINE, (double)(points(h, L) * h->B));
+    MGWR_CK(h, mgwr::launch_refine_dd2(h->u_dd, h->hdd.u[L], cnt, h->stream));
+    prof_end(h, pm);
     MGWR_TRY(clear_norms(h));
-    if (h->h64.rs[L] == R_DELTA) {
-      MGWR_TRY(defect_from_delta(h, h->h64, L, h->norm_bits));
-      *exact = false;
-    } else {
-      MGWR_TRY(defect(h, h->h64, L, h->norm_bits));
-      *exact = true;
-    }
+    MGWR_TRY(outer_defect_ddd(h));
+    *exact = true;
   } else {
     const bool ddef = h->precision == MGWR_MIXED_DD;
     MGWR_CK(h, cudaMemsetAsync(h->h32.u[L], 0, cnt * sizeof(float), h->stream));
@@ -607,13 +677,23 @@ int run_iteration(mgwr_t h, int cyc, int nu1, int nu2, std::vector<double>& norm
 }
 
 int check_level(mgwr_t h, int hierarchy, int level) {
-  if (hierarchy != MGWR_H64 && hierarchy != MGWR_H32)
-    return fail(h, MGWR_E_INVAL, "hierarchy must be MGWR_H64 or MGWR_H32");
+  if (hierarchy != MGWR_H64 && hierarchy != MGWR_H32 && hierarchy != MGWR_HDD)
+    return fail(h, MGWR_E_INVAL, "hierarchy must be MGWR_H64, MGWR_H32 or MGWR_HDD");
   if (level < 0 || level >= h->nlev) return fail(h, MGWR_E_INVAL, "level out of range");
   if (hierarchy == MGWR_H32 && !h->h32.ready)
     return fail(h, MGWR_E_STATE, "the FP32 hierarchy exists only after mgwr_set_precision(MGWR_MIXED)");
+  if (hierarchy == MGWR_HDD && !h->hdd.ready)
+    return fail(h, MGWR_E_STATE, "the double-float hierarchy exists only after mgwr_set_precision(MGWR_DD)");
   if (hierarchy == MGWR_H64) MGWR_TRY(ensure_full(h, h->h64));
   return MGWR_OK;
+}
+
+// Calls f with the hierarchy a component call addresses (checked before).
+template <class F>
+int with_hier(mgwr_t h, int hierarchy, F f) {
+  if (hierarchy == MGWR_H64) return f(h->h64);
+  if (hierarchy == MGWR_H32) return f(h->h32);
+  return f(h->hdd);
 }
 
 int check_cycle_args(mgwr_t h, int cyc, int nu1, int nu2) {
@@ -807,6 +887,7 @@ int create_impl(int d, int n, int M, const double* T, const double* alpha, int b
   }
   init_hier(h, h->h64);
   init_hier(h, h->h32);
+  init_hier(h, h->hdd);
 
   auto bail = [&](int code) {
     mgwr_destroy(h);
@@ -947,9 +1028,12 @@ int mgwr_instance_relres(mgwr_t h, double* relres) {
 
 int mgwr_set_precision(mgwr_t h, int precision) {
   if (h == nullptr) return MGWR_E_INVAL;
-  if (precision != MGWR_FP64 && precision != MGWR_MIXED && precision != MGWR_MIXED_DD)
-    return fail(h, MGWR_E_INVAL, "precision must be MGWR_FP64, MGWR_MIXED or MGWR_MIXED_DD");
-  if (precision != MGWR_FP64) MGWR_TRY(ensure_h32(h));
+  if (precision != MGWR_FP64 && precision != MGWR_MIXED && precision != MGWR_MIXED_DD &&
+      precision != MGWR_DD)
+    return fail(h, MGWR_E_INVAL,
+                "precision must be MGWR_FP64, MGWR_MIXED, MGWR_MIXED_DD or MGWR_DD");
+  if (precision == MGWR_DD) MGWR_TRY(ensure_hdd(h));
+  if (precision == MGWR_MIXED || precision == MGWR_MIXED_DD) MGWR_TRY(ensure_h32(h));
   if (precision == MGWR_MIXED_DD) {
     MGWR_TRY(ensure_dd(h));
     MGWR_CK(h, cudaStreamSynchronize(h->stream));
@@ -983,7 +1067,7 @@ int mgwr_set_engine_split(mgwr_t h, int kernel_class, int level, int split) {
   if (h == nullptr) return MGWR_E_INVAL;
   if (kernel_class != MGWR_K_SWEEP64 && kernel_class != MGWR_K_SWEEP32 &&
       kernel_class != MGWR_K_DEFECT64 && kernel_class != MGWR_K_DEFECT32 &&
-      kernel_class != MGWR_K_DEFECT_DD)
+      kernel_class != MGWR_K_DEFECT_DD && kernel_class != MGWR_K_SWEEP_DD)
     return fail(h, MGWR_E_INVAL, "kernel class has no FFT engine");
   if (split != 1 && split != 2 && split != 4) return fail(h, MGWR_E_INVAL, "split must be 1, 2 or 4");
   if (level < -1 || level >= h->nlev) return fail(h, MGWR_E_INVAL, "level out of range");
@@ -1010,6 +1094,8 @@ int mgwr_autotune(mgwr_t h) {
   MGWR_CK(h, cudaStreamSynchronize(h->stream));
   if (h->precision == MGWR_FP64) {
     MGWR_TRY(tune_hierarchy(h, h->h64, MGWR_K_SWEEP64, MGWR_K_DEFECT64));
+  } else if (h->precision == MGWR_DD) {
+    MGWR_TRY(tune_hierarchy(h, h->hdd, MGWR_K_SWEEP_DD, MGWR_K_DEFECT_DD));
   } else {
     MGWR_TRY(tune_hierarchy(h, h->h32, MGWR_K_SWEEP32, MGWR_K_DEFECT32));
     MGWR_TRY(tune_outer(h));
@@ -1077,9 +1163,12 @@ int mgwr_solve(mgwr_t h, int cyc, int nu1, int nu2, double tol, int max_cycles, 
   if (h == nullptr) return MGWR_E_INVAL;
   MGWR_TRY(check_cycle_args(h, cyc, nu1, nu2));
   if (!(tol >= 0.0) || max_cycles < 1) return fail(h, MGWR_E_INVAL, "need tol >= 0, max_cycles >= 1");
+  // refinement: inner cycles on the defect equation (FP32 or double-float),
+  // the outer defect in FP64 or double-float
   const bool mixed = h->precision != MGWR_FP64;
-  const bool ddef = h->precision == MGWR_MIXED_DD;
-  if (!mixed) MGWR_TRY(ensure_full(h, h->h64));
+  const bool ddef = h->precision == MGWR_MIXED_DD || h->precision == MGWR_DD;
+  const bool ddc = h->precision == MGWR_DD;  // double-float inner cycles
+  if (h->precision == MGWR_FP64) MGWR_TRY(ensure_full(h, h->h64));
   const int L = h->nlev - 1;
   const size_t cntL = level_count(h, L);
   mgwr_stats local{};
@@ -1089,20 +1178,33 @@ int mgwr_solve(mgwr_t h, int cyc, int nu1, int nu2, double tol, int max_cycles, 
     MGWR_CK(h, mgwr::launch_split(h->u_dd, h->h64.u[L], cntL, h->stream));
     MGWR_CK(h, mgwr::launch_split(h->f_dd, h->h64.f[L], cntL, h->stream));
   }
+  // the full defect of the finest level in the outer precision, with norms (in
+  // the refinements written as the inner right-hand side)
+  auto full_defect = [&]() -> int {
+    if (ddc) {
+      MGWR_TRY(clear_norms(h));
+      MGWR_TRY(outer_defect_ddd(h));
+      return read_norms(h, norms);
+    }
+    if (ddef) return finest_defect_norms_dd(h, norms);
+    return finest_defect_norms(h, norms, mixed);
+  };
   if (h->u_zero) {
     // the defect of u = 0 is f itself (Algorithm 1 from the zero iterate)
     MGWR_TRY(clear_norms(h));
-    MGWR_CK(h, mgwr::launch_absmax_round(h->h64.f[L], mixed ? h->h32.f[L] : nullptr,
+    MGWR_CK(h, mgwr::launch_absmax_round(h->h64.f[L], mixed && !ddc ? h->h32.f[L] : nullptr,
                                          cntL / h->B, h->B, h->norm_bits, h->stream));
-    if (mixed)
+    if (ddc) {
+      MGWR_CK(h, mgwr::launch_split(h->hdd.f[L], h->h64.f[L], cntL, h->stream));
+      h->hdd.rs[L] = R_STALE;
+    } else if (mixed) {
       h->h32.rs[L] = R_STALE;
-    else
+    } else {
       h->h64.rs[L] = R_ZERO_U;
+    }
     MGWR_TRY(read_norms(h, norms));
-  } else if (ddef) {
-    MGWR_TRY(finest_defect_norms_dd(h, norms));
   } else {
-    MGWR_TRY(finest_defect_norms(h, norms, mixed));
+    MGWR_TRY(full_defect());
   }
   if (!h->r0_valid) {
     h->r0 = norms;
@@ -1125,16 +1227,13 @@ int mgwr_solve(mgwr_t h, int cyc, int nu1, int nu2, double tol, int max_cycles, 
     // outer defects of the mixed modes while the defect is large (above
     // kLooseOuter of the initial one before this step) take the FP32-convolution
     // form, whose error (about 1e-6 of |f|) is then below 1e-3 of the defect
-    h->loose_outer = mixed && rel >= kLooseOuter;
+    h->loose_outer = mixed && !ddc && rel >= kLooseOuter;
     MGWR_TRY(run_iteration(h, cyc, nu1, nu2, norms, &exact));
     cycles += mixed ? h->inner : 1;
     rel = relative(h, norms, h->relres);
     // the stopping decision is always taken on the full defect
     if (!exact && rel <= tol) {
-      if (ddef)
-        MGWR_TRY(finest_defect_norms_dd(h, norms));
-      else
-        MGWR_TRY(finest_defect_norms(h, norms, mixed));
+      MGWR_TRY(full_defect());
       rel = relative(h, norms, h->relres);
       exact = true;
     }
@@ -1217,12 +1316,12 @@ int mgwr_level_n(mgwr_t h, int level, int* n_level) {
 }
 
 static void* field_ptr(mgwr_t h, int hierarchy, int level, int which) {
-  if (hierarchy == MGWR_H64) {
-    Hier<double>& H = h->h64;
-    return which == MGWR_U ? (void*)H.u[level] : which == MGWR_F ? (void*)H.f[level] : (void*)H.r[level];
-  }
-  Hier<float>& H = h->h32;
-  return which == MGWR_U ? (void*)H.u[level] : which == MGWR_F ? (void*)H.f[level] : (void*)H.r[level];
+  void* p = nullptr;
+  with_hier(h, hierarchy, [&](auto& H) {
+    p = which == MGWR_U ? (void*)H.u[level] : which == MGWR_F ? (void*)H.f[level] : (void*)H.r[level];
+    return MGWR_OK;
+  });
+  return p;
 }
 
 int mgwr_field_set(mgwr_t h, int hierarchy, int level, int which, const double* host) {
@@ -1235,18 +1334,27 @@ int mgwr_field_set(mgwr_t h, int hierarchy, int level, int which, const double* 
   void* dst = field_ptr(h, hierarchy, level, which);
   if (hierarchy == MGWR_H64) {
     MGWR_CK(h, cudaMemcpyAsync(dst, host, cnt * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-  } else {
+  } else if (hierarchy == MGWR_H32) {
     std::vector<float> tmp(cnt);
     for (size_t i = 0; i < cnt; ++i) tmp[i] = (float)host[i];
     MGWR_CK(h, cudaMemcpyAsync(dst, tmp.data(), cnt * sizeof(float), cudaMemcpyHostToDevice, h->stream));
     MGWR_CK(h, cudaStreamSynchronize(h->stream));
+  } else {
+    std::vector<mgwr::dd> tmp(cnt);
+    for (size_t i = 0; i < cnt; ++i) {
+      const float hi = (float)host[i];
+      tmp[i] = mgwr::dd(hi, (float)(host[i] - (double)hi));
+    }
+    MGWR_CK(h, cudaMemcpyAsync(dst, tmp.data(), cnt * sizeof(mgwr::dd), cudaMemcpyHostToDevice,
+                               h->stream));
+    MGWR_CK(h, cudaStreamSynchronize(h->stream));
   }
   MGWR_CK(h, cudaStreamSynchronize(h->stream));
   if (hierarchy == MGWR_H64 && level == h->nlev - 1) h->r0_valid = false;
-  if (hierarchy == MGWR_H64)
-    h->h64.rs[level] = R_STALE;
-  else
-    h->h32.rs[level] = R_STALE;
+  with_hier(h, hierarchy, [&](auto& H) {
+    H.rs[level] = R_STALE;
+    return MGWR_OK;
+  });
   return MGWR_OK;
 }
 
@@ -1260,11 +1368,17 @@ int mgwr_field_get(mgwr_t h, int hierarchy, int level, int which, double* host) 
   if (hierarchy == MGWR_H64) {
     MGWR_CK(h, cudaMemcpyAsync(host, src, cnt * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     MGWR_CK(h, cudaStreamSynchronize(h->stream));
-  } else {
+  } else if (hierarchy == MGWR_H32) {
     std::vector<float> tmp(cnt);
     MGWR_CK(h, cudaMemcpyAsync(tmp.data(), src, cnt * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
     MGWR_CK(h, cudaStreamSynchronize(h->stream));
     for (size_t i = 0; i < cnt; ++i) host[i] = (double)tmp[i];
+  } else {
+    std::vector<mgwr::dd> tmp(cnt);
+    MGWR_CK(h, cudaMemcpyAsync(tmp.data(), src, cnt * sizeof(mgwr::dd), cudaMemcpyDeviceToHost,
+                               h->stream));
+    MGWR_CK(h, cudaStreamSynchronize(h->stream));
+    for (size_t i = 0; i < cnt; ++i) host[i] = (double)tmp[i].hi + (double)tmp[i].lo;
   }
   return MGWR_OK;
 }
@@ -1274,10 +1388,7 @@ int mgwr_smooth(mgwr_t h, int hierarchy, int level, int colour) {
   h->u_zero = false;
   MGWR_TRY(check_level(h, hierarchy, level));
   if (colour != MGWR_RED && colour != MGWR_BLACK) return fail(h, MGWR_E_INVAL, "bad colour");
-  if (hierarchy == MGWR_H64)
-    MGWR_TRY(smooth_colour(h, h->h64, level, colour));
-  else
-    MGWR_TRY(smooth_colour(h, h->h32, level, colour));
+  MGWR_TRY(with_hier(h, hierarchy, [&](auto& H) { return smooth_colour(h, H, level, colour); }));
   MGWR_CK(h, cudaStreamSynchronize(h->stream));
   return MGWR_OK;
 }
@@ -1296,13 +1407,10 @@ int mgwr_smooth_defect(mgwr_t h, int hierarchy, int level, double* norm_inf) {
   MGWR_TRY(check_level(h, hierarchy, level));
   if (level == 0) return fail(h, MGWR_E_INVAL, "level 0 has a direct solve, not a smoother");
   MGWR_TRY(clear_norms(h));
-  if (hierarchy == MGWR_H64) {
-    MGWR_TRY(smooth(h, h->h64, level, 1));
-    MGWR_TRY(defect_from_delta(h, h->h64, level, h->norm_bits));
-  } else {
-    MGWR_TRY(smooth(h, h->h32, level, 1));
-    MGWR_TRY(defect_from_delta(h, h->h32, level, h->norm_bits));
-  }
+  MGWR_TRY(with_hier(h, hierarchy, [&](auto& H) {
+    MGWR_TRY(smooth(h, H, level, 1));
+    return defect_from_delta(h, H, level, h->norm_bits);
+  }));
   std::vector<double> norms;
   MGWR_TRY(read_norms(h, norms));
   if (norm_inf != nullptr) *norm_inf = max_norm(h, norms);
@@ -1313,10 +1421,7 @@ int mgwr_defect(mgwr_t h, int hierarchy, int level, double* norm_inf) {
   if (h == nullptr) return MGWR_E_INVAL;
   MGWR_TRY(check_level(h, hierarchy, level));
   MGWR_TRY(clear_norms(h));
-  if (hierarchy == MGWR_H64)
-    MGWR_TRY(defect(h, h->h64, level, h->norm_bits));
-  else
-    MGWR_TRY(defect(h, h->h32, level, h->norm_bits));
+  MGWR_TRY(with_hier(h, hierarchy, [&](auto& H) { return defect(h, H, level, h->norm_bits); }));
   std::vector<double> norms;
   MGWR_TRY(read_norms(h, norms));
   if (norm_inf != nullptr) *norm_inf = max_norm(h, norms);
@@ -1328,10 +1433,7 @@ int mgwr_restrict(mgwr_t h, int hierarchy, int level) {
   h->u_zero = false;
   MGWR_TRY(check_level(h, hierarchy, level));
   if (level == 0) return fail(h, MGWR_E_INVAL, "level 0 has no coarser level");
-  if (hierarchy == MGWR_H64)
-    MGWR_TRY(restrict_into(h, h->h64, level, h->h64.r[level]));
-  else
-    MGWR_TRY(restrict_into(h, h->h32, level, h->h32.r[level]));
+  MGWR_TRY(with_hier(h, hierarchy, [&](auto& H) { return restrict_into(h, H, level, H.r[level]); }));
   MGWR_CK(h, cudaStreamSynchronize(h->stream));
   return MGWR_OK;
 }
@@ -1341,10 +1443,7 @@ int mgwr_prolong(mgwr_t h, int hierarchy, int level) {
   h->u_zero = false;
   MGWR_TRY(check_level(h, hierarchy, level));
   if (level == 0) return fail(h, MGWR_E_INVAL, "level 0 has no coarser level");
-  if (hierarchy == MGWR_H64)
-    MGWR_TRY(prolong_into(h, h->h64, level));
-  else
-    MGWR_TRY(prolong_into(h, h->h32, level));
+  MGWR_TRY(with_hier(h, hierarchy, [&](auto& H) { return prolong_into(h, H, level); }));
   MGWR_CK(h, cudaStreamSynchronize(h->stream));
   return MGWR_OK;
 }
@@ -1353,10 +1452,7 @@ int mgwr_coarsest(mgwr_t h, int hierarchy) {
   if (h == nullptr) return MGWR_E_INVAL;
   h->u_zero = false;
   MGWR_TRY(check_level(h, hierarchy, 0));
-  if (hierarchy == MGWR_H64)
-    MGWR_TRY(coarsest(h, h->h64));
-  else
-    MGWR_TRY(coarsest(h, h->h32));
+  MGWR_TRY(with_hier(h, hierarchy, [&](auto& H) { return coarsest(h, H); }));
   MGWR_CK(h, cudaStreamSynchronize(h->stream));
   return MGWR_OK;
 }
@@ -1366,10 +1462,8 @@ int mgwr_cycle(mgwr_t h, int hierarchy, int cyc, int nu1, int nu2) {
   h->u_zero = false;
   MGWR_TRY(check_level(h, hierarchy, h->nlev - 1));
   MGWR_TRY(check_cycle_args(h, cyc, nu1, nu2));
-  if (hierarchy == MGWR_H64)
-    MGWR_TRY(cycle(h, h->h64, h->nlev - 1, cyc, nu1, nu2));
-  else
-    MGWR_TRY(cycle(h, h->h32, h->nlev - 1, cyc, nu1, nu2));
+  MGWR_TRY(with_hier(h, hierarchy,
+                     [&](auto& H) { return cycle(h, H, h->nlev - 1, cyc, nu1, nu2); }));
   MGWR_CK(h, cudaStreamSynchronize(h->stream));
   return MGWR_OK;
 }
@@ -1420,9 +1514,10 @@ int mgwr_footprint(int d, int n, int M, int batch, int precision, size_t* bytes)
   if (bytes == nullptr) return MGWR_E_INVAL;
   if ((d != 1 && d != 2) || n < 1 || !is_pow2((long long)n + 1) || !is_pow2(M) || M < 4 ||
       M > mgwr::kMaxM || batch < 1 ||
-      (precision != MGWR_FP64 && precision != MGWR_MIXED && precision != MGWR_MIXED_DD))
+      (precision != MGWR_FP64 && precision != MGWR_MIXED && precision != MGWR_MIXED_DD &&
+       precision != MGWR_DD))
     return MGWR_E_INVAL;
-  // mirrors the allocations of create_impl, ensure_full and ensure_h32, each
+  // mirrors the allocations of create_impl, ensure_full, ensure_h32 and ensure_hdd, each
   // rounded up to 512 bytes, plus 2 MiB of allocator slack per handle
   auto r512 = [](size_t b) { return (b + 511) / 512 * 512; };
   const size_t B = batch, L = 2 * (size_t)M, Lt = (size_t)mgwr::engine_length(M);
@@ -1441,6 +1536,11 @@ int mgwr_footprint(int d, int n, int M, int batch, int precision, size_t* bytes)
     total += r512(16 * B * ((pts[0] + 1) / 2) * L);
   if (precision == MGWR_FP64) {
     for (size_t l = 0; l < nlev; ++l) total += (l + 1 < nlev ? 4 : 3) * r512(8 * B * pts[l] * M);
+  } else if (precision == MGWR_DD) {
+    total += 2 * r512(8 * B * pts[0] * M);  // FP64 finest iterate and right-hand side
+    total += 2 * r512(8 * B * pts[0] * M);  // double-float copies of the finest pair (ensure_dd)
+    for (size_t l = 0; l < nlev; ++l) total += (l + 1 < nlev ? 4 : 3) * r512(8 * B * pts[l] * M);
+    total += r512(16 * B * nlev * L) + r512(16 * B * L) + r512(16 * Lt) + r512(8 * (size_t)M);
   } else {
     total += 2 * r512(8 * B * pts[0] * M);  // FP64 finest iterate and right-hand side
     for (size_t l = 0; l < nlev; ++l) total += (l + 1 < nlev ? 4 : 3) * r512(4 * B * pts[l] * M);

@@ -126,6 +126,8 @@ cudaError_t launch_refine(double* u, const float* e, size_t count, cudaStream_t 
 cudaError_t launch_split(dd* dst, const double* src, size_t count, cudaStream_t s);
 cudaError_t launch_join(double* dst, const dd* src, size_t count, cudaStream_t s);
 cudaError_t launch_refine_dd(dd* u, const float* e, size_t count, cudaStream_t s);
+// u += e in double-float (both double-float; the sum renormalised twice).
+cudaError_t launch_refine_dd2(dd* u, const dd* e, size_t count, cudaStream_t s);
 cudaError_t launch_split_cx(Cx<dd>* dst, const Cx<double>* src, size_t count, cudaStream_t s);
 // dst = (float) src.
 cudaError_t launch_round(float* dst, const double* src, size_t count, cudaStream_t s);

@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(kLineBlock)
           R sum = a.v[k] + b.v[k];
           if (four) sum = sum + (c.v[k] + g.v[k]);
           out.v[k] = hinv2 * sum;
-          amax = absmax_nan((double)fabs(out.v[k]), amax);
+          amax = absmax_nan((double)Arith<R>::mag(out.v[k]), amax);
         }
         vstore(rp + m, out);
       }
@@ -249,7 +249,8 @@ __global__ void __launch_bounds__(kLineBlock)
   const R* b = uc + ((size_t)tx.i1 + row0) * M;
   const R* c = uc + ((size_t)tx.i0 + row1) * M;
   const R* e = uc + ((size_t)tx.i1 + row1) * M;
-  const R w = R((tx.half ? 0.5f : 1.f) * (ty.half ? 0.5f : 1.f));
+  const bool unit = !tx.half && !ty.half;
+  const R w = R((tx.half ? 0.5 : 1.0) * (ty.half ? 0.5 : 1.0));
   const int taps = tx.count * ty.count;  // 1, 2 (in x or in y) or 4
   // the second tap of a two-tap point: the other coarse line in x, or in y
   const R* second = ty.count == 2 ? c : b;
@@ -266,7 +267,7 @@ __global__ void __launch_bounds__(kLineBlock)
     }
     Vec<R> cur = vload_rw(up + m);
 #pragma unroll
-    for (int k = 0; k < W; ++k) cur.v[k] = w == R(1) ? cur.v[k] + sum.v[k] : cur.v[k] + w * sum.v[k];
+    for (int k = 0; k < W; ++k) cur.v[k] = unit ? cur.v[k] + sum.v[k] : cur.v[k] + w * sum.v[k];
     vstore(up + m, cur);
   }
 }
@@ -301,6 +302,12 @@ __global__ void k_refine_dd(dd* __restrict__ u, const float* __restrict__ e, siz
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
        i += (size_t)gridDim.x * blockDim.x)
     u[i] = dd_add_float(u[i], e[i]);
+}
+
+__global__ void k_refine_dd2(dd* __restrict__ u, const dd* __restrict__ e, size_t count) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
+       i += (size_t)gridDim.x * blockDim.x)
+    u[i] = dd_add_accurate(u[i], e[i]);
 }
 
 __global__ void k_refine(double* __restrict__ u, const float* __restrict__ e, size_t count) {
@@ -594,6 +601,11 @@ cudaError_t launch_prolong(R* u, const R* uc, const LevelShape& ls, cudaStream_t
   return counted(cudaGetLastError());
 }
 
+cudaError_t launch_refine_dd2(dd* u, const dd* e, size_t count, cudaStream_t s) {
+  k_refine_dd2<<<elementwise_grid(count), 256, 0, s>>>(u, e, count);
+  return counted(cudaGetLastError());
+}
+
 cudaError_t launch_refine(double* u, const float* e, size_t count, cudaStream_t s) {
   k_refine<<<elementwise_grid(count), 256, 0, s>>>(u, e, count);
   return counted(cudaGetLastError());
@@ -702,6 +714,7 @@ cudaError_t launch_round_cx(Cx<float>* dst, const Cx<double>* src, size_t count,
   template cudaError_t launch_prolong<R>(R*, const R*, const LevelShape&, cudaStream_t);
 MGWR_INST_R(double)
 MGWR_INST_R(float)
+MGWR_INST_R(dd)
 #undef MGWR_INST_R
 
 

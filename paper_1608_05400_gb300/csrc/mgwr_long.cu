@@ -321,6 +321,9 @@ template cudaError_t launch_sweep_long<double>(const double*, double*, double*, 
                                                size_t, const Cx<double>*, Cx<double>*,
                                                const LevelShape&, int, bool, double, int,
                                                cudaStream_t);
+template cudaError_t launch_sweep_long<dd>(const dd*, dd*, dd*, const Cx<dd>*, size_t,
+                                           const Cx<dd>*, Cx<dd>*, const LevelShape&, int, bool,
+                                           dd, int, cudaStream_t);
 template cudaError_t launch_sweep_long<float>(const float*, float*, float*, const Cx<float>*,
                                               size_t, const Cx<float>*, Cx<float>*,
                                               const LevelShape&, int, bool, float, int,
@@ -334,6 +337,7 @@ MGWR_INST_LONG_DEFECT(double, double)
 MGWR_INST_LONG_DEFECT(double, float)
 MGWR_INST_LONG_DEFECT(float, float)
 MGWR_INST_LONG_DEFECT(dd, float)
+MGWR_INST_LONG_DEFECT(dd, dd)
 #undef MGWR_INST_LONG_DEFECT
 
 }  // namespace mgwr

@@ -165,4 +165,8 @@ template cudaError_t launch_sweep<float>(const float*, float*, float*, const Cx<
                                          const Cx<float>*, const float*, Cx<float>*,
                                          const LevelShape&, int, bool, float, int, cudaStream_t);
 
+template cudaError_t launch_sweep<dd>(const dd*, dd*, dd*, const Cx<dd>*, size_t, const Cx<dd>*,
+                                      const dd*, Cx<dd>*, const LevelShape&, int, bool, dd, int,
+                                      cudaStream_t);
+
 }  // namespace mgwr

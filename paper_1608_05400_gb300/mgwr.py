@@ -26,8 +26,8 @@ MGWR_E_TIMEOUT = -7
 MGWR_E_CUDA = -8
 MGWR_E_STATE = -9
 
-MGWR_FP64, MGWR_MIXED, MGWR_MIXED_DD = 0, 1, 2
-MGWR_H64, MGWR_H32 = 64, 32
+MGWR_FP64, MGWR_MIXED, MGWR_MIXED_DD, MGWR_DD = 0, 1, 2, 3
+MGWR_H64, MGWR_H32, MGWR_HDD = 64, 32, 48
 MGWR_U, MGWR_F, MGWR_R = 0, 1, 2
 MGWR_RED, MGWR_BLACK = 0, 1
 MGWR_ORDER_TEXT, MGWR_ORDER_TABLE = 0, 1
@@ -109,7 +109,7 @@ _SIGS = {
 }
 
 KERNEL_CLASSES = ("sweep64", "sweep32", "defect64", "defect32", "restrict", "prolong",
-                  "coarsest", "refine", "defect_delta", "defect_dd")
+                  "coarsest", "refine", "defect_delta", "defect_dd", "sweep_dd")
 
 _lib = None
 
@@ -240,7 +240,7 @@ class Solver:
         self._check(self.lib.mgwr_autotune(self.h), "mgwr_autotune")
         return {name: [self.engine_split(k, l) for l in range(self.num_levels())]
                 for k, name in enumerate(KERNEL_CLASSES)
-                if name in ("sweep64", "sweep32", "defect64", "defect32", "defect_dd")}
+                if name in ("sweep64", "sweep32", "defect64", "defect32", "defect_dd", "sweep_dd")}
 
     # -- data --
     def set_rhs(self, f: np.ndarray, g: np.ndarray | None = None):

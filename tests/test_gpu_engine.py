@@ -97,7 +97,7 @@ def test_split_requests_fall_back_to_what_a_length_takes():
         assert s.engine_split(K["sweep64"], 1) == 2 and s.engine_split(K["sweep64"], 0) == 1
 
 
-@pytest.mark.parametrize("precision", [G.MGWR_FP64, G.MGWR_MIXED, G.MGWR_MIXED_DD])
+@pytest.mark.parametrize("precision", [G.MGWR_FP64, G.MGWR_MIXED, G.MGWR_MIXED_DD, G.MGWR_DD])
 def test_autotune_keeps_state_and_results(precision):
     d, n, M = 2, 63, 256
     f = inputs.Problem(d, n, M, 1.0, 0.4, "t2").rhs()

@@ -10,10 +10,12 @@ between steps.  Other workloads (--workload): c1 (1-D 63 points, M = 64),
 c3 (2-D 511 x 511, M = 4096, u = t^alpha sin sin, mixed to 1e-8) and c5a
 (4096 independent 2-D 63 x 63, M = 256 solves with alpha ~ U[0.1, 0.9] in one
 batched handle, mixed to 1e-8), c5b (1-D 4095 points, M = 65536, alpha = 0.2,
-u = t^alpha sin, mixed to 1e-8; --precision fp64 for the FP64 form) and c4
-(the served request stream).
+u = t^alpha sin, to 1e-8 with double-float inner cycles, as FP32 inner cycles
+stall on h = 1/4096; --precision fp64 for the FP64 form) and c4 (the served
+request stream; each request's precision chosen by MGWR_AUTO).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+  python bench.py [--gpus N] [--steps K] [--warmup W]
+                  [--precision fp64|mixed|mixed_dd|dd|auto]
                   [--workload c2|c1|c3|c5a|c5b|c4]
   python bench.py --impl reference ...   (the CPU oracle on the host cores)
 
@@ -50,9 +52,9 @@ WORKLOADS = {
            "2-D MGWR 511x511 interior, M=4096, u=t^alpha sin(pi x) sin(pi y)"),
     "c5a": (2, 63, 256, 4096, "t2", 1e-8, "mixed_dd",
             "4096 independent 2-D 63x63, M=256 solves, alpha~U[0.1,0.9] (seed 1608), one batched handle"),
-    "c5b": (1, 4095, 65536, 1, "talpha", 1e-8, "mixed_dd",
+    "c5b": (1, 4095, 65536, 1, "talpha", 1e-8, "dd",
             "1-D MGWR 4095 interior points, M=65536 (long memory), u=t^alpha sin(pi x)"),
-    "c4": (0, 0, 0, 0, "", 1e-8, "mixed_dd", "served stream"),
+    "c4": (0, 0, 0, 0, "", 1e-8, "auto", "served stream"),
 }
 # alpha of a workload when --alpha is not given
 WORKLOAD_ALPHA = {"c5b": 0.2}
@@ -61,6 +63,14 @@ WORKLOAD_INNER = {"c5a": 4}
 # oracle time steps in the CPU-baseline sample (about 10-30 s of host work)
 ORACLE_SAMPLE_STEPS = {"c2": 256, "c5b": 2048}
 UNIT = "unknowns/s"
+# --precision names and the library's codes (MGWR_FP64 .. MGWR_AUTO)
+PREC_CODES = {"fp64": 0, "mixed": 1, "mixed_dd": 2, "dd": 3, "auto": 4}
+PREC_NAMES = {v: k for k, v in PREC_CODES.items()}
+DTYPES = {"fp64": "f64", "mixed": "f32 cycles + f64 defect/update",
+          "mixed_dd": "f32 cycles + f32x2 (double-float) defect/update",
+          "dd": "f32x2 (double-float) cycles, defect and update",
+          "auto": "f32 cycles + f32x2 (double-float) defect/update, f32x2 cycles on grids "
+                  "with h <= 1/4096"}
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP64 issue rate of a GB300 SM: 2 FP64 FMA per clock (measured with an FMA
 # chain: 1.20 TFLOP/s at 1995 MHz on 152 SMs); peak at the maximum clock.
@@ -78,7 +88,7 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--precision", default=None, choices=["fp64", "mixed", "mixed_dd", "dd"])
+    p.add_argument("--precision", default=None, choices=["fp64", "mixed", "mixed_dd", "dd", "auto"])
     p.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     p.add_argument("--requests", type=int, default=200, help="c4: first R requests of the stream")
     p.add_argument("--slots", type=int, default=4, help="c4: server slots")
@@ -306,6 +316,8 @@ def run_served(args):
     budget = int(0.8 * free)
     reqs = inputs.request_stream(count=2000, seed=1608, rate=1.0)[: args.requests]
     tol = WORKLOADS["c4"][5]
+    precision = args.precision or WORKLOADS["c4"][6]
+    prec = PREC_CODES[precision]
 
     def rhs(rq):
         return inputs.Problem(rq["d"], rq["n"], rq["M"], 1.0, rq["alpha"], rq["kind"]).rhs()
@@ -340,7 +352,7 @@ def run_served(args):
                     # time a request waited for host memory counts in its latency
                     delay[i] = max(0.0, time.perf_counter() - (t0 + arrivals[i]))
                     tickets[i] = srv.submit(rq["d"], rq["n"], rq["M"], 1.0, rq["alpha"], rhs(rq),
-                                            precision=mgwr.MGWR_MIXED_DD, tol=tol)
+                                            precision=prec, tol=tol)
 
             th = threading.Thread(target=submitter)
             th.start()
@@ -373,9 +385,10 @@ def run_served(args):
     lat_ms = np.array(lat) * 1e3
     out = {
         "metric": "served p50/p99 latency and space-time unknowns/s (mixed, rel-res 1e-8)",
+        "precision": precision,
         "value": total / span2, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 0,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 cycles + f32x2 (double-float) defect/update", "data": "synthetic",
+        "dtype": DTYPES[precision], "data": "synthetic",
         "config": {"workload": f"served stream: first {len(reqs)} of 2000 requests (seed 1608), "
                                "1-D n=2^k-1 k~U{5..12} or 2-D k~U{5..9}, M=2^j j~U{7..12}, "
                                "alpha~U[0.1,0.9], u=t^2 or t^alpha sin, Poisson arrivals at 0.7x "
@@ -433,11 +446,10 @@ def main():
         unknowns = batch * n ** d * Mw
     stream = torch.cuda.Stream()
     s.set_stream(stream.cuda_stream)
-    prec_code = {"fp64": mgwr.MGWR_FP64, "mixed": mgwr.MGWR_MIXED, "mixed_dd": mgwr.MGWR_MIXED_DD,
-                 "dd": mgwr.MGWR_DD}
-    mixed = precision in ("mixed", "mixed_dd")
     if precision != "fp64":
-        s.set_precision(prec_code[precision])
+        s.set_precision(PREC_CODES[precision])
+        precision = PREC_NAMES[s.precision()]  # MGWR_AUTO resolves on this grid
+    mixed = precision in ("mixed", "mixed_dd")
     inner = args.inner or WORKLOAD_INNER.get(args.workload)
     if mixed and inner:
         s.set_inner_cycles(inner)
@@ -517,9 +529,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp64": "f64", "mixed": "f32 cycles + f64 defect/update",
-                  "mixed_dd": "f32 cycles + f32x2 (double-float) defect/update",
-                  "dd": "f32x2 (double-float)"}[precision],
+        "dtype": DTYPES[precision],
         "data": "synthetic",
         "config": {"workload": f"{desc}, " + (f"alpha={alpha}, " if batch == 1 else "")
                                + f"V({NU1},{NU2}) red-black, rel-res {tol}",

@@ -63,6 +63,7 @@ extern "C" {
 #define MGWR_MIXED 1 /* FP32 V-cycles on the defect, FP64 defect + update     */
 #define MGWR_MIXED_DD 2 /* FP32 V-cycles; defect + update in double-float    */
 #define MGWR_DD 3       /* refinement with double-float inner cycles         */
+#define MGWR_AUTO 4     /* MGWR_MIXED_DD or MGWR_DD by the grid (below)      */
 /* MGWR_MIXED_DD keeps the finest iterate and right-hand side as double-float
  * pairs (hi + lo of two floats, about 48 significant bits) and computes the
  * outer defect and the update with FP32 instructions only (GB300 runs FP32 64x
@@ -75,7 +76,10 @@ extern "C" {
  * itself never passes through a convolution (only corrections do), so the
  * rounding of the transforms, about 2^-44 of a field's scale, is not amplified
  * by the discrete Laplacian's 4/h^2.  Its norms and stopping test use the
- * double-float defect. */
+ * double-float defect.
+ * MGWR_AUTO resolves, when it is set, to MGWR_DD where the FP32 limit of an
+ * outer step, 4 eps32 / (pi h)^2 with h the finest spacing, is 0.2 or more
+ * (h <= 1/4096), else to MGWR_MIXED_DD (mgwr_auto_precision). */
 
 /* which hierarchy a component call addresses */
 #define MGWR_H64 64  /* the double-precision hierarchy                         */
@@ -137,8 +141,15 @@ const char* mgwr_last_error(mgwr_t h);
 const char* mgwr_status_string(int status);
 
 /* MGWR_FP64 (default), MGWR_MIXED or MGWR_MIXED_DD (both allocate the FP32
- * hierarchy), or MGWR_DD (allocates the double-float hierarchy). */
+ * hierarchy), MGWR_DD (allocates the double-float hierarchy), or MGWR_AUTO
+ * (one of MGWR_MIXED_DD and MGWR_DD, resolved now; mgwr_get_precision reads
+ * which). */
 int mgwr_set_precision(mgwr_t h, int precision);
+int mgwr_get_precision(mgwr_t h, int* precision);
+/* The precision MGWR_AUTO resolves to for a finest grid of n points per
+ * dimension (host arithmetic, no CUDA call; d and M are checked as in
+ * mgwr_create).  Other precisions are returned unchanged. */
+int mgwr_auto_precision(int d, int n, int M, int precision, int* resolved);
 /* MGWR_ORDER_TEXT (default) or MGWR_ORDER_TABLE. */
 int mgwr_set_order(mgwr_t h, int order);
 /* cudaStream_t to run on (NULL: the handle's own stream). */
@@ -285,7 +296,7 @@ typedef struct {
   double T, alpha;
   const double* f;        /* N*M right-hand side, host; copied by mgwr_submit  */
   const double* g;        /* N initial values or NULL; copied                 */
-  int precision;          /* MGWR_FP64, MGWR_MIXED, MGWR_MIXED_DD or MGWR_DD    */
+  int precision;          /* MGWR_FP64, MGWR_MIXED, MGWR_MIXED_DD, MGWR_DD, AUTO */
   int order;              /* MGWR_ORDER_TEXT or MGWR_ORDER_TABLE              */
   int cycle, nu1, nu2;    /* as for mgwr_solve                                */
   double tol;

@@ -1026,12 +1026,46 @@ int mgwr_instance_relres(mgwr_t h, double* relres) {
   return MGWR_OK;
 }
 
+namespace {
+bool known_precision(int p) {
+  return p == MGWR_FP64 || p == MGWR_MIXED || p == MGWR_MIXED_DD || p == MGWR_DD || p == MGWR_AUTO;
+}
+// FP32 rounding of a correction e limits what one outer step of the FP32
+// refinement can remove to about 4 eps32 / (pi h)^2 of the defect (the ratio of
+// the discrete Laplacian's largest to smallest eigenvalue times eps32); from
+// 0.2 on (h <= 1/4096) the outer steps cost more than double-float inner cycles,
+// whose reduction per step is that of FP64 cycles.
+constexpr double kAutoLimit = 0.2;
+int resolve_precision(int n, int precision) {
+  if (precision != MGWR_AUTO) return precision;
+  const double h = 1.0 / ((double)n + 1.0);
+  const double pi = 3.14159265358979323846;
+  const double limit = 4.0 * 0x1p-24 / (pi * pi * h * h);
+  return limit >= kAutoLimit ? MGWR_DD : MGWR_MIXED_DD;
+}
+}  // namespace
+
+int mgwr_auto_precision(int d, int n, int M, int precision, int* resolved) {
+  if (resolved == nullptr || (d != 1 && d != 2) || n < 1 || !is_pow2((long long)n + 1) ||
+      !is_pow2(M) || M < 4 || M > mgwr::kMaxM || !known_precision(precision))
+    return MGWR_E_INVAL;
+  *resolved = resolve_precision(n, precision);
+  return MGWR_OK;
+}
+
+int mgwr_get_precision(mgwr_t h, int* precision) {
+  if (h == nullptr || precision == nullptr) return MGWR_E_INVAL;
+  *precision = h->precision;
+  return MGWR_OK;
+}
+
 int mgwr_set_precision(mgwr_t h, int precision) {
   if (h == nullptr) return MGWR_E_INVAL;
+  if (known_precision(precision)) precision = resolve_precision(h->n, precision);
   if (precision != MGWR_FP64 && precision != MGWR_MIXED && precision != MGWR_MIXED_DD &&
       precision != MGWR_DD)
     return fail(h, MGWR_E_INVAL,
-                "precision must be MGWR_FP64, MGWR_MIXED, MGWR_MIXED_DD or MGWR_DD");
+                "precision must be MGWR_FP64, MGWR_MIXED, MGWR_MIXED_DD, MGWR_DD or MGWR_AUTO");
   if (precision == MGWR_DD) MGWR_TRY(ensure_hdd(h));
   if (precision == MGWR_MIXED || precision == MGWR_MIXED_DD) MGWR_TRY(ensure_h32(h));
   if (precision == MGWR_MIXED_DD) {
@@ -1513,10 +1547,9 @@ int mgwr_profile_read(mgwr_t h, int kernel_class, long long* launches, double* m
 int mgwr_footprint(int d, int n, int M, int batch, int precision, size_t* bytes) {
   if (bytes == nullptr) return MGWR_E_INVAL;
   if ((d != 1 && d != 2) || n < 1 || !is_pow2((long long)n + 1) || !is_pow2(M) || M < 4 ||
-      M > mgwr::kMaxM || batch < 1 ||
-      (precision != MGWR_FP64 && precision != MGWR_MIXED && precision != MGWR_MIXED_DD &&
-       precision != MGWR_DD))
+      M > mgwr::kMaxM || batch < 1 || !known_precision(precision))
     return MGWR_E_INVAL;
+  precision = resolve_precision(n, precision);
   // mirrors the allocations of create_impl, ensure_full, ensure_h32 and ensure_hdd, each
   // rounded up to 512 bytes, plus 2 MiB of allocator slack per handle
   auto r512 = [](size_t b) { return (b + 511) / 512 * 512; };

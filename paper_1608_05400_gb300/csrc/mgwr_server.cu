@@ -150,7 +150,7 @@ int check_request(const mgwr_request* q) {
   if (!pow2(q->M) || q->M < 4 || q->M > (1 << 20)) return MGWR_E_INVAL;
   if (!(q->T > 0.0) || !(q->alpha > 0.0) || !(q->alpha <= 1.0)) return MGWR_E_INVAL;
   if (q->precision != MGWR_FP64 && q->precision != MGWR_MIXED && q->precision != MGWR_MIXED_DD &&
-      q->precision != MGWR_DD)
+      q->precision != MGWR_DD && q->precision != MGWR_AUTO)
     return MGWR_E_INVAL;
   if (q->cycle != 1 && q->cycle != 2) return MGWR_E_INVAL;
   if (q->nu1 < 0 || q->nu2 < 0 || q->nu1 + q->nu2 == 0 || q->nu1 > 16 || q->nu2 > 16)

@@ -26,7 +26,7 @@ MGWR_E_TIMEOUT = -7
 MGWR_E_CUDA = -8
 MGWR_E_STATE = -9
 
-MGWR_FP64, MGWR_MIXED, MGWR_MIXED_DD, MGWR_DD = 0, 1, 2, 3
+MGWR_FP64, MGWR_MIXED, MGWR_MIXED_DD, MGWR_DD, MGWR_AUTO = 0, 1, 2, 3, 4
 MGWR_H64, MGWR_H32, MGWR_HDD = 64, 32, 48
 MGWR_U, MGWR_F, MGWR_R = 0, 1, 2
 MGWR_RED, MGWR_BLACK = 0, 1
@@ -98,6 +98,8 @@ _SIGS = {
     "mgwr_launch_count": (C.c_int, [_h, C.POINTER(C.c_longlong)]),
     "mgwr_inverse_column_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p]),
     "mgwr_footprint": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_size_t)]),
+    "mgwr_auto_precision": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int)]),
+    "mgwr_get_precision": (C.c_int, [_h, C.POINTER(C.c_int)]),
     "mgwr_server_create": (C.c_int, [C.c_size_t, C.c_int, C.POINTER(C.c_void_p)]),
     "mgwr_server_destroy": (C.c_int, [C.c_void_p]),
     "mgwr_server_set_policy": (C.c_int, [C.c_void_p, C.c_int]),
@@ -209,6 +211,11 @@ class Solver:
     # -- configuration --
     def set_precision(self, prec: int):
         self._check(self.lib.mgwr_set_precision(self.h, prec), "mgwr_set_precision")
+
+    def precision(self) -> int:
+        v = C.c_int()
+        self._check(self.lib.mgwr_get_precision(self.h, C.byref(v)), "mgwr_get_precision")
+        return v.value
 
     def set_order(self, order: int):
         self._check(self.lib.mgwr_set_order(self.h, order), "mgwr_set_order")
@@ -353,6 +360,15 @@ class Solver:
         k = np.empty((self.B, self.M) if self.batched else self.M)
         self._check(self.lib.mgwr_inverse_column(self.h, level, _ptr(k)), "mgwr_inverse_column")
         return k
+
+
+def auto_precision(d: int, n: int, M: int, precision: int = MGWR_AUTO) -> int:
+    """The precision MGWR_AUTO resolves to on this grid (others unchanged)."""
+    v = C.c_int()
+    st = load().mgwr_auto_precision(d, n, M, precision, C.byref(v))
+    if st != MGWR_OK:
+        raise MGWRError(st, "mgwr_auto_precision: invalid shape or precision")
+    return v.value
 
 
 def footprint(d: int, n: int, M: int, batch: int = 1, precision: int = MGWR_FP64) -> int:

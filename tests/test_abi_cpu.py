@@ -2,6 +2,7 @@
 function include/mgwr.h declares, and rejects invalid arguments on the host
 (no CUDA work is issued by any call made here)."""
 import ctypes as C
+import math
 import os
 import re
 import shutil
@@ -108,3 +109,23 @@ def test_server_calls_reject_null_and_bad_arguments(lib):
     assert lib.mgwr_server_create(0, 4, C.byref(h)) == mgwr.MGWR_E_INVAL
     assert lib.mgwr_server_set_policy(None, mgwr.MGWR_POLICY_SMALLEST) == mgwr.MGWR_E_INVAL
     assert lib.mgwr_server_create(1 << 30, 0, C.byref(h)) == mgwr.MGWR_E_INVAL
+
+
+def test_auto_precision_follows_the_fp32_refinement_limit(lib):
+    # 4 eps32 / (pi h)^2 >= 0.2 only from h = 1/4096 on: double-float inner cycles
+    # there, the FP32 refinement on coarser grids; host arithmetic only
+    from paper_1608_05400_gb300.mgwr import (MGWR_AUTO, MGWR_DD, MGWR_FP64, MGWR_MIXED,
+                                             MGWR_MIXED_DD, auto_precision, footprint)
+    limit = lambda n: 4 * 2.0 ** -24 / (math.pi / (n + 1)) ** 2
+    for d, n in [(1, 63), (1, 1023), (1, 2047), (2, 255), (2, 511), (1, 4095), (1, 8191), (2, 4095)]:
+        want = MGWR_DD if limit(n) >= 0.2 else MGWR_MIXED_DD
+        assert auto_precision(d, n, 256) == want, (d, n)
+        assert footprint(d, n, 256, 1, MGWR_AUTO) == footprint(d, n, 256, 1, want)
+    assert auto_precision(1, 2047, 64) == MGWR_MIXED_DD and auto_precision(1, 4095, 64) == MGWR_DD
+    for p in (MGWR_FP64, MGWR_MIXED, MGWR_MIXED_DD, MGWR_DD):
+        assert auto_precision(1, 4095, 64, p) == p
+    r = C.c_int()
+    assert lib.mgwr_auto_precision(1, 64, 64, MGWR_AUTO, C.byref(r)) == mgwr.MGWR_E_INVAL
+    assert lib.mgwr_auto_precision(1, 63, 64, 5, C.byref(r)) == mgwr.MGWR_E_INVAL
+    assert lib.mgwr_auto_precision(3, 63, 64, MGWR_AUTO, C.byref(r)) == mgwr.MGWR_E_INVAL
+    assert lib.mgwr_get_precision(None, C.byref(r)) == mgwr.MGWR_E_INVAL

@@ -159,3 +159,20 @@ def test_dd_fine_1d_grid_where_fp32_cycles_stall():
     assert stats[G.MGWR_DD].cycles <= stats[G.MGWR_FP64].cycles + 2
     ref = separable.solution(d, n, M, 1.0, alpha, prob.rhs_profile(), inputs.phi(d, n))
     assert rel(u, ref) <= 1e-7
+
+
+def test_auto_precision_resolves_on_the_handle_and_converges():
+    # MGWR_AUTO: double-float inner cycles on h = 1/4096, the FP32 refinement on h = 1/256.
+    # On h = 1/4096 the double-float iterate's own rounding, amplified by 4/h^2, leaves
+    # a relative defect of a few 1e-9: the tolerance there is 1e-8.
+    for d, n, M, want, tol in [(1, 4095, 256, G.MGWR_DD, 1e-8), (2, 255, 64, G.MGWR_MIXED_DD, 1e-10)]:
+        prob = inputs.Problem(d, n, M, 1.0, 0.3, "talpha")
+        with G.Solver(d, n, M, 1.0, 0.3) as s:
+            s.set_precision(G.MGWR_AUTO)
+            assert s.precision() == want == G.auto_precision(d, n, M)
+            s.set_rhs(prob.rhs())
+            st = s.solve(1, 1, 1, tol=tol, max_cycles=40)
+            u = s.solution()
+        assert st.outer <= 6, (d, n, st.outer)
+        ref = separable.solution(d, n, M, 1.0, 0.3, prob.rhs_profile(), inputs.phi(d, n))
+        assert rel(u, ref) <= 100 * tol

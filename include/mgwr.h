@@ -166,14 +166,22 @@ int mgwr_set_inner_cycles(mgwr_t h, int cycles);
  * M > 4096, where E is 1 or 2), synchronising with warp barriers when the
  * group fits in one warp.  A request a length cannot take falls back to the
  * nearest smaller E; mgwr_get_engine_split reports the E launches use.
- * MGWR_E_INVAL for another class or split. */
+ * For MGWR_K_SWEEP32 (not the one-point solve) with 64 <= M <= 4096, `split`
+ * may also be E | MGWR_SPLIT_STAGED: a persistent kernel whose thread groups
+ * receive the f and neighbour lines of their next line pair in shared memory
+ * through bulk asynchronous copies (cp.async.bulk, completing on an mbarrier)
+ * while they transform the current pair; bitwise the same results.  Its waits
+ * give up after half a second, and the call that ran it then returns
+ * MGWR_E_CUDA.  MGWR_E_INVAL for another class or split. */
+#define MGWR_SPLIT_STAGED 16
 int mgwr_set_engine_split(mgwr_t h, int kernel_class, int level, int split);
 int mgwr_get_engine_split(mgwr_t h, int kernel_class, int level, int* split);
 /* Tuner: times every E of each engine class the current precision runs (the
  * sweep and the full defect of its cycle hierarchy on every level, and in
  * the mixed modes the outer defect) on the handle's own data (per level, as
  * many instances as fit 2^27 values, at least one), writing to a temporary
- * field, and keeps the fastest per level (a larger E must win by 3 %).  The
+ * field, and keeps the fastest per level (a larger E, or staged input lines,
+ * must win by 3 %).  The
  * handle's state is unchanged.  The choices are also recorded process-wide
  * for (class, d, n, M, batch): handles created later with that shape start
  * with them.  mgwr_set_engine_split / mgwr_get_engine_split address

@@ -175,6 +175,15 @@ constexpr int defect_class() {
          : std::is_same<R, mgwr::dd>::value ? MGWR_K_DEFECT_DD : MGWR_K_DEFECT64;
 }
 
+// A staged sweep that gave up waiting for its copies (never expected: a copy of
+// a valid line always lands) turns into an error of the call that ran it.
+int check_staging(mgwr_t h) {
+  bool hit = false;
+  MGWR_CK(h, mgwr::take_stage_timeout(&hit));
+  if (hit) return fail(h, MGWR_E_CUDA, "staged sweep: wait for bulk copies gave up");
+  return MGWR_OK;
+}
+
 int split_of(const mgwr_handle* h, int cls, int l) {
   return h->split[cls].empty() ? 0 : h->split[cls][l];
 }
@@ -749,12 +758,17 @@ int time_launches(mgwr_t h, F launch, float* ms) {
 }
 
 // Times every split E in {1, 2, 4} of one kernel class with `launch(E)` and
-// keeps the fastest; a larger E must beat the best smaller one by 3 %.
+// keeps the fastest; a larger E must beat the best smaller one by 3 %.  FP32
+// sweeps also try each E with staged input lines (E | kStaged), which must
+// beat the best direct-load launch by 3 % as well.
 template <class F>
 int tune_class(mgwr_t h, int cls, int l, int word, F launch) {
   int best = 1;
   float best_ms = 0.f;
-  for (int E = 1; E <= 4; E *= 2) {
+  const int cands[6] = {1, 2, 4, 1 | mgwr::kStaged, 2 | mgwr::kStaged, 4 | mgwr::kStaged};
+  const int ncand = cls == MGWR_K_SWEEP32 ? 6 : 3;
+  for (int c = 0; c < ncand; ++c) {
+    const int E = cands[c];
     if (mgwr::effective_split(h->M, word, E) != E) continue;  // same launch as a smaller E
     float ms = 0.f;
     MGWR_TRY(time_launches(h, [&] { return launch(E); }, &ms));
@@ -1103,7 +1117,10 @@ int mgwr_set_engine_split(mgwr_t h, int kernel_class, int level, int split) {
       kernel_class != MGWR_K_DEFECT64 && kernel_class != MGWR_K_DEFECT32 &&
       kernel_class != MGWR_K_DEFECT_DD && kernel_class != MGWR_K_SWEEP_DD)
     return fail(h, MGWR_E_INVAL, "kernel class has no FFT engine");
-  if (split != 1 && split != 2 && split != 4) return fail(h, MGWR_E_INVAL, "split must be 1, 2 or 4");
+  const int E = split & ~mgwr::kStaged;
+  if (E != 1 && E != 2 && E != 4) return fail(h, MGWR_E_INVAL, "split must be 1, 2 or 4");
+  if ((split & mgwr::kStaged) && kernel_class != MGWR_K_SWEEP32)
+    return fail(h, MGWR_E_INVAL, "staged input lines exist for the FP32 sweep only");
   if (level < -1 || level >= h->nlev) return fail(h, MGWR_E_INVAL, "level out of range");
   if (level == -1)
     h->split[kernel_class].assign(h->nlev, split);
@@ -1136,7 +1153,7 @@ int mgwr_autotune(mgwr_t h) {
   }
   MGWR_CK(h, cudaStreamSynchronize(h->stream));
   drop_graph(h);
-  return MGWR_OK;
+  return check_staging(h);
 }
 
 int mgwr_set_inner_cycles(mgwr_t h, int cycles) {
@@ -1284,6 +1301,7 @@ int mgwr_solve(mgwr_t h, int cyc, int nu1, int nu2, double tol, int max_cycles, 
   if (!std::isfinite(rel)) status = MGWR_E_NUMERIC;
   MGWR_CK(h, cudaEventRecord(h->ev1, h->stream));
   MGWR_CK(h, cudaEventSynchronize(h->ev1));
+  MGWR_TRY(check_staging(h));
   prof_collect(h);
   float ms = 0.f;
   MGWR_CK(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
@@ -1424,7 +1442,7 @@ int mgwr_smooth(mgwr_t h, int hierarchy, int level, int colour) {
   if (colour != MGWR_RED && colour != MGWR_BLACK) return fail(h, MGWR_E_INVAL, "bad colour");
   MGWR_TRY(with_hier(h, hierarchy, [&](auto& H) { return smooth_colour(h, H, level, colour); }));
   MGWR_CK(h, cudaStreamSynchronize(h->stream));
-  return MGWR_OK;
+  return check_staging(h);
 }
 
 // largest per-instance norm of the last reduction
@@ -1499,7 +1517,7 @@ int mgwr_cycle(mgwr_t h, int hierarchy, int cyc, int nu1, int nu2) {
   MGWR_TRY(with_hier(h, hierarchy,
                      [&](auto& H) { return cycle(h, H, h->nlev - 1, cyc, nu1, nu2); }));
   MGWR_CK(h, cudaStreamSynchronize(h->stream));
-  return MGWR_OK;
+  return check_staging(h);
 }
 
 int mgwr_toeplitz_column(mgwr_t h, double* r_host) {

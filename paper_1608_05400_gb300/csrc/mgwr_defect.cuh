@@ -123,7 +123,7 @@ cudaError_t launch_defect(const R* u, const R* f, RO* r, const Cx<R>* tspec, siz
                                      norm_bits, E, s);
   const int d = ls.d, n = ls.n, M = ls.M;
   const int L = 2 * M, logL = ilog2(L);
-  E = effective_split(M, (int)sizeof(R) == 4 ? 4 : 8, E);
+  E = effective_split(M, (int)sizeof(R) == 4 ? 4 : 8, E) & ~kStaged;
   const int npts = d == 1 ? n : n * n;
   const int npairs = (npts + 1) / 2;
   if (ls.batch == 0) return cudaSuccess;

@@ -250,6 +250,10 @@ __device__ __forceinline__ void middle_stage(Cx<R>* buf, int b, const SH& sh, in
   for (int q = 0; q < 8; ++q) buf[P::idx(base + q * s)] = v[q];
 }
 
+struct NoHook {
+  __device__ __forceinline__ void operator()() const {}
+};
+
 // Forward transform of one line pair by a group of T = L/(8E) threads: thread
 // t does the radix-8 butterflies b = t + eT, e < E, of every stage.  `load(m)`
 // returns the pair's input at time index m (called for m = b + q L/8, q < 4:
@@ -257,10 +261,13 @@ __device__ __forceinline__ void middle_stage(Cx<R>* buf, int b, const SH& sh, in
 // carries data).  On return the thread holds, in v[e], the transform values at
 // spectral positions 8b .. 8b+7 of its butterfly b = t + eT.  Every thread of
 // the group must call this (it synchronises the group through `sync`).
-template <int E, class R, class SH, class Load, bool FULL = false>
+// `after_input()` runs in every thread right after the group barrier that
+// follows the last `load` call of the group.
+template <int E, class R, class SH, class Load, bool FULL = false, class Hook = NoHook>
 __device__ __forceinline__ void fft_forward(Cx<R>* buf, int t, const SH& sh,
                                             const Cx<R>* __restrict__ tw, Load load,
-                                            Cx<R> (&v)[E][8], const GroupSync& sync) {
+                                            Cx<R> (&v)[E][8], const GroupSync& sync,
+                                            Hook after_input = Hook()) {
   using P = Pad<R>;
   const int T = sh.L8 / E;
 #pragma unroll
@@ -281,6 +288,7 @@ __device__ __forceinline__ void fft_forward(Cx<R>* buf, int t, const SH& sh,
     for (int q = 0; q < 8; ++q) buf[P::idx(b + q * sh.L8)] = v[e][q];
   }
   sync();
+  after_input();
   if constexpr (SH::kFixed) {
 #pragma unroll
     for (int k = 1; k < sh.kmid_end; ++k) {

@@ -41,7 +41,12 @@ constexpr int kMaxM = 1 << 20;
 inline int engine_length(int M) { return M <= kShortMaxM ? 2 * M : 2 * kLongB; }
 // Butterflies per thread of the FFT engine for a transform of length L:
 // E in {1, 2, 4} and at most L/8; any other request selects 1.
+// A split value may carry kStaged: the FP32 sweep of lines of 64 .. 4096 steps
+// then runs persistently with its input lines staged in shared memory by bulk
+// copies (mgwr_sweep_staged.cu); every other launch ignores the bit.
+constexpr int kStaged = 16;
 inline int engine_split(int L, int E) {
+  E &= ~kStaged;
   if (E != 2 && E != 4) E = 1;
   while (E > 1 && L / 8 < E) E >>= 1;
   return E;
@@ -50,11 +55,13 @@ inline int engine_split(int L, int E) {
 // really uses when E is requested: the partitioned convolution has E = 1 or
 // 2, the FP32 kernels split only their compile-time lengths 2^7 .. 2^13.
 inline int effective_split(int M, int word, int E) {
+  const int staged = E & kStaged;
+  E &= ~kStaged;
   if (M > kShortMaxM) return E == 2 ? 2 : 1;
   const int L = 2 * M;
   E = engine_split(L, E);
-  if (word == 4 && (L < 128 || L > 8192)) E = 1;
-  return E;
+  if (word == 4 && (L < 128 || L > 8192)) return 1;
+  return word == 4 ? (E | staged) : E;
 }
 // Complex values of the partitioned-convolution scratch for one launch on a
 // level of shape ls: per instance, per line pair, the spectra of all blocks.
@@ -82,6 +89,20 @@ template <class R>
 cudaError_t launch_sweep(const R* f, R* u, R* delta, const Cx<R>* spec, size_t spec_stride,
                          const Cx<R>* tw, const R* zero, Cx<R>* scratch, const LevelShape& ls,
                          int par, bool all_points, R hinv2, int E, cudaStream_t s);
+
+// launch_sweep<float> for 64 <= M <= kShortMaxM without all_points, E carrying
+// kStaged: a persistent grid (as many CTAs as fit on the GPU) walks the line
+// pairs; while a group transforms one pair, the f and neighbour lines of its
+// next pair are copied into shared memory by cp.async.bulk, completing on an
+// mbarrier.  Same arithmetic in the same order as the direct-load kernel, so
+// the results are bitwise identical.  A wait that gives up (half a second) sets
+// a device flag read by take_stage_timeout.
+cudaError_t launch_sweep_staged(const float* f, float* u, float* delta, const Cx<float>* spec,
+                                size_t spec_stride, const Cx<float>* tw, const float* zero,
+                                const LevelShape& ls, int par, float hinv2, int E,
+                                cudaStream_t s);
+// Reads and clears the flag of the staged sweep's bounded waits (synchronous).
+cudaError_t take_stage_timeout(bool* hit);
 
 // Defect after a red-black step from the black half-sweep's delta: r = 0 on the
 // black points, r = hinv2 * sum of neighbour deltas on the red points

@@ -114,6 +114,11 @@ cudaError_t launch_sweep(const R* f, R* u, R* delta, const Cx<R>* spec, size_t s
   const int d = ls.d, n = ls.n, M = ls.M;
   const int L = 2 * M, logL = ilog2(L);
   E = effective_split(M, (int)sizeof(R) == 4 ? 4 : 8, E);
+  if constexpr (sizeof(R) == 4) {
+    if ((E & kStaged) && !all_points)
+      return launch_sweep_staged(f, u, delta, spec, spec_stride, tw, zero, ls, par, hinv2, E, s);
+  }
+  E &= ~kStaged;
   const int npts = all_points ? (d == 1 ? n : n * n) : colour_count(d, n, par);
   const int npairs = (npts + 1) / 2;
   if (npairs == 0 || ls.batch == 0) return cudaSuccess;

@@ -123,3 +123,83 @@ def test_autotune_keeps_state_and_results(precision):
         s2.set_precision(precision)
         for name, v in chosen.items():
             assert [s2.engine_split(K[name], l) for l in range(s2.num_levels())] == v
+
+
+def _sweep32(d, n, M, split, batch=1, delta=False):
+    # one FP32 smoothing step on the finest level (red, then black), split forced
+    alphas = [0.45] if batch == 1 else list(np.linspace(0.2, 0.8, batch))
+    s = G.Solver(d, n, M, 1.0, alphas if batch > 1 else 0.45)
+    with s:
+        s.set_precision(G.MGWR_MIXED)
+        s.set_engine_split(K["sweep32"], split)
+        l = s.num_levels() - 1
+        N = n ** d
+        shape = (N, M) if batch == 1 else (batch, N, M)
+        u = inputs.random_field(N * batch, M, seed=3).reshape(shape)
+        f = inputs.random_field(N * batch, M, seed=4, scale=2.0 * d * (n + 1) ** 2).reshape(shape)
+        s.field_set(G.MGWR_H32, l, G.MGWR_U, u)
+        s.field_set(G.MGWR_H32, l, G.MGWR_F, f)
+        if delta:
+            out = s.smooth_defect(G.MGWR_H32, l)
+            res = (s.field_get(G.MGWR_H32, l, G.MGWR_U), s.field_get(G.MGWR_H32, l, G.MGWR_R), out)
+        else:
+            s.smooth(G.MGWR_H32, l, G.MGWR_RED)
+            s.smooth(G.MGWR_H32, l, G.MGWR_BLACK)
+            res = (s.field_get(G.MGWR_H32, l, G.MGWR_U),)
+        used = s.engine_split(K["sweep32"])
+    return res, used
+
+
+@pytest.mark.parametrize("d,n,M,batch", [(1, 15, 64, 1), (1, 63, 128, 1), (2, 15, 64, 1), (2, 31, 256, 1),
+                                         (2, 63, 1024, 1), (1, 15, 2048, 1), (2, 7, 4096, 1),
+                                         (2, 3, 64, 1), (2, 15, 256, 3), (1, 31, 512, 5)])
+@pytest.mark.parametrize("E", [1, 2, 4])
+def test_staged_sweep_is_bitwise_the_direct_sweep(d, n, M, batch, E):
+    # input lines through bulk copies into shared memory: the same values summed
+    # in the same order, on every grid shape (boundary lines, the row-wrapping
+    # pairs, an odd last pair) and for batches
+    ref, used = _sweep32(d, n, M, E, batch)
+    got, used_s = _sweep32(d, n, M, E | G.MGWR_SPLIT_STAGED, batch)
+    assert used_s == used | G.MGWR_SPLIT_STAGED
+    for a, b in zip(got, ref):
+        np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("d,n,M", [(2, 31, 256), (1, 127, 1024)])
+def test_staged_sweep_records_the_same_changes(d, n, M):
+    ref, _ = _sweep32(d, n, M, 1, delta=True)
+    got, _ = _sweep32(d, n, M, 1 | G.MGWR_SPLIT_STAGED, delta=True)
+    for a, b in zip(got, ref):
+        np.testing.assert_array_equal(a, b)
+
+
+def test_staged_split_falls_back_and_is_checked():
+    with G.Solver(1, 7, 32, 1.0, 0.5) as s:  # M < 64: direct loads
+        s.set_precision(G.MGWR_MIXED)
+        s.set_engine_split(K["sweep32"], 1 | G.MGWR_SPLIT_STAGED)
+        assert s.engine_split(K["sweep32"]) == 1
+    with G.Solver(1, 7, 8192, 1.0, 0.5) as s:  # partitioned lines: direct loads
+        s.set_engine_split(K["sweep32"], 2 | G.MGWR_SPLIT_STAGED)
+        assert s.engine_split(K["sweep32"]) == 2
+        with pytest.raises(G.MGWRError):
+            s.set_engine_split(K["sweep64"], 1 | G.MGWR_SPLIT_STAGED)
+        with pytest.raises(G.MGWRError):
+            s.set_engine_split(K["defect32"], 1 | G.MGWR_SPLIT_STAGED)
+        with pytest.raises(G.MGWRError):
+            s.set_engine_split(K["sweep32"], 3 | G.MGWR_SPLIT_STAGED)
+
+
+@pytest.mark.parametrize("precision", [G.MGWR_MIXED, G.MGWR_MIXED_DD])
+def test_staged_solve_equals_direct_solve(precision):
+    d, n, M = 2, 63, 512
+    f = inputs.Problem(d, n, M, 1.0, 0.6, "t2").rhs()
+    out = []
+    for split in (1, 1 | G.MGWR_SPLIT_STAGED):
+        with G.Solver(d, n, M, 1.0, 0.6) as s:
+            s.set_precision(precision)
+            s.set_engine_split(K["sweep32"], split)
+            s.set_rhs(f)
+            st = s.solve(1, 1, 1, tol=1e-10, max_cycles=40)
+            out.append((s.solution(), st.cycles, st.relres))
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    assert out[0][1:] == out[1][1:]

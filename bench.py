@@ -114,6 +114,29 @@ def dist_env():
     return rank, world, local
 
 
+def rank_barrier(world: int) -> None:
+    """Barrier over the job's ranks (nothing to wait for with one rank)."""
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int, device: str) -> float:
+    """The largest of the ranks' values of x: the job's time is its slowest rank's."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, unknowns_per_rank: int, steps: int, t_max_ms: float) -> float:
+    """Whole-job unknowns per second: every rank solves its own replica."""
+    return world * unknowns_per_rank * steps / (t_max_ms * 1e-3)
+
+
 def peaks():
     try:
         with open(PEAKS_FILE) as fh:
@@ -464,7 +487,7 @@ def main():
 
     for _ in range(max(args.warmup, 3) if args.warmup >= 3 else args.warmup):
         st = step()
-    barrier = (lambda: torch.distributed.barrier()) if world > 1 else (lambda: None)
+    barrier = lambda: rank_barrier(world)  # noqa: E731
 
     l0 = mgwr.launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -480,13 +503,8 @@ def main():
         torch.cuda.synchronize()
         barrier()
     launches = mgwr.launch_count() - l0
-    ms = e0.elapsed_time(e1)
-    t_max = ms
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = world * unknowns * args.steps / (t_max * 1e-3)
+    t_max = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
+    value = job_throughput(world, unknowns, args.steps, t_max)
 
     u = s.solution() if batch == 1 else None
     # per-kernel-class times from one profiled solve (outside the timed region)
@@ -511,13 +529,9 @@ def main():
             s.lib.mgwr_get_solution(s.h, up.ctypes.data_as(mgwr._dp))
         ee1.record(stream)
         torch.cuda.synchronize()
-        ems = ee0.elapsed_time(ee1)
-        if world > 1:
-            t = torch.tensor([ems], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ems = float(t.item())
+        ems = max_over_ranks(ee0.elapsed_time(ee1), world, "cuda")
         nbytes = unknowns * 8
-        e2e = {"value": world * unknowns * args.steps / (ems * 1e-3), "unit": UNIT,
+        e2e = {"value": job_throughput(world, unknowns, args.steps, ems), "unit": UNIT,
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
     s.close()
     if rank != 0:

@@ -1,0 +1,67 @@
+"""The multi-rank path of bench.py on CPU: two gloo ranks (world size 2) run
+the barrier, the max-over-ranks timing and the whole-job throughput the GPU
+bench uses under torchrun, and ranks other than 0 of the reference arm exit
+without work.  No GPU: the ranks are host processes."""
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port() -> int:
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank: int, world: int, port: int, q) -> None:
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank,
+                            world_size=world)
+    try:
+        bench.rank_barrier(world)
+        t = bench.max_over_ranks(10.0 + 5.0 * rank, world, "cpu")  # rank 1 is the slow one
+        v = bench.job_throughput(world, 1000, 4, t)
+        bench.rank_barrier(world)
+        q.put((rank, t, v))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_time_the_job_by_the_slowest_rank():
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_rank, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    res = sorted(q.get(timeout=10) for _ in range(world))
+    for rank, t, v in res:
+        assert t == 15.0
+        assert v == pytest.approx(2 * 1000 * 4 / 15e-3)
+
+
+def test_single_rank_needs_no_process_group():
+    sys.path.insert(0, ROOT)
+    import bench
+    bench.rank_barrier(1)
+    assert bench.max_over_ranks(3.5, 1, "cpu") == 3.5
+    assert bench.job_throughput(1, 10, 2, 4.0) == pytest.approx(5000.0)
+
+
+def test_reference_arm_ranks_other_than_zero_exit_without_work():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    res = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--gpus", "2", "--steps", "1", "--warmup", "3"],
+                         capture_output=True, text=True, timeout=120, env=env)
+    assert res.returncode == 0 and res.stdout.strip() == ""

@@ -20,6 +20,8 @@
 // first M outputs.
 #pragma once
 
+#include <type_traits>
+
 #include "mgwr_internal.h"
 
 namespace mgwr {
@@ -91,27 +93,57 @@ __device__ __forceinline__ void dft2(Cx<R>& a0, Cx<R>& a1) {
   a0 = s;
 }
 
+// c + s q for a real s, one fused multiply-add per component.
+__device__ __forceinline__ Cx<float> cfma(float s, Cx<float> q, Cx<float> c) {
+  return {fmaf(s, q.x, c.x), fmaf(s, q.y, c.y)};
+}
+__device__ __forceinline__ Cx<double> cfma(double s, Cx<double> q, Cx<double> c) {
+  return {fma(s, q.x, c.x), fma(s, q.y, c.y)};
+}
+
+// Odd half of a length-8 DFT from b0 = x0 - x4, t1 = x1 - x5, b2 = w2 (x2 - x6),
+// t3 = x3 - x7: the length-4 DFT of (b0, w1 t1, b2, w3 t3), written to v[1],
+// v[3], v[5], v[7].  With IEEE types, w1 t1 and w3 t3 are s p1 and s p3
+// (s = 1/sqrt 2, p1 and p3 sums of t's components), and s is applied by the
+// fused multiply-adds of the outputs: 16 operations instead of 20.
+template <bool INV, class R>
+__device__ __forceinline__ void dft8_odd(Cx<R> (&v)[8], Cx<R> b0, Cx<R> t1, Cx<R> b2, Cx<R> t3) {
+  if constexpr (std::is_same<R, dd>::value) {
+    Cx<R> b1 = mul_w1<INV>(t1), b3 = mul_w3<INV>(t3);
+    dft4<INV>(b0, b1, b2, b3);
+    v[1] = b0; v[3] = b1; v[5] = b2; v[7] = b3;
+  } else {
+    const R s = R(0.70710678118654752440);
+    const Cx<R> p1 = INV ? Cx<R>{t1.x - t1.y, t1.x + t1.y} : Cx<R>{t1.x + t1.y, t1.y - t1.x};
+    const Cx<R> p3 = INV ? Cx<R>{-(t3.x + t3.y), t3.x - t3.y} : Cx<R>{t3.y - t3.x, -(t3.x + t3.y)};
+    const Cx<R> c0 = cadd(b0, b2), d0 = csub(b0, b2);
+    const Cx<R> q = cadd(p1, p3), r = mul_w2<INV>(csub(p1, p3));
+    v[1] = cfma(s, q, c0);
+    v[5] = cfma(-s, q, c0);
+    v[3] = cfma(s, r, d0);
+    v[7] = cfma(-s, r, d0);
+  }
+}
+
 // Length-8 DFT (one radix-2 layer, then two length-4 DFTs), natural order.
 template <bool INV, class R>
 __device__ __forceinline__ void dft8(Cx<R> (&v)[8]) {
   Cx<R> a0 = cadd(v[0], v[4]), a1 = cadd(v[1], v[5]), a2 = cadd(v[2], v[6]), a3 = cadd(v[3], v[7]);
-  Cx<R> b0 = csub(v[0], v[4]), b1 = mul_w1<INV>(csub(v[1], v[5]));
-  Cx<R> b2 = mul_w2<INV>(csub(v[2], v[6])), b3 = mul_w3<INV>(csub(v[3], v[7]));
+  const Cx<R> b0 = csub(v[0], v[4]), t1 = csub(v[1], v[5]);
+  const Cx<R> b2 = mul_w2<INV>(csub(v[2], v[6])), t3 = csub(v[3], v[7]);
   dft4<INV>(a0, a1, a2, a3);
-  dft4<INV>(b0, b1, b2, b3);
+  dft8_odd<INV>(v, b0, t1, b2, t3);
   v[0] = a0; v[2] = a1; v[4] = a2; v[6] = a3;
-  v[1] = b0; v[3] = b1; v[5] = b2; v[7] = b3;
 }
 
 // Forward length-8 DFT of (v0, v1, v2, v3, 0, 0, 0, 0).
 template <class R>
 __device__ __forceinline__ void dft8_half_input(Cx<R> (&v)[8]) {
   Cx<R> a0 = v[0], a1 = v[1], a2 = v[2], a3 = v[3];
-  Cx<R> b0 = v[0], b1 = mul_w1<false>(v[1]), b2 = mul_w2<false>(v[2]), b3 = mul_w3<false>(v[3]);
+  const Cx<R> b0 = v[0], t1 = v[1], b2 = mul_w2<false>(v[2]), t3 = v[3];
   dft4<false>(a0, a1, a2, a3);
-  dft4<false>(b0, b1, b2, b3);
+  dft8_odd<false>(v, b0, t1, b2, t3);
   v[0] = a0; v[2] = a1; v[4] = a2; v[6] = a3;
-  v[1] = b0; v[3] = b1; v[5] = b2; v[7] = b3;
 }
 
 // Shared-memory index of transform position x.  16-byte elements: one pad

@@ -6,17 +6,19 @@ u = t^2 sin(pi x) sin(pi y) (f from D^a t^2 = 2 t^(2-a) / Gamma(3-a)),
 5-point Laplacian, V(1,1) red-black cycles from u = 0 until the relative
 infinity-norm defect is below 1e-10, FP64.  6.66e7 space-time unknowns; each
 FP64 field is 533 MB, larger than the 129 MB L2, so no flush is needed
-between steps.  Other workloads (--workload): c1 (1-D 63 points, M = 64),
-c3 (2-D 511 x 511, M = 4096, u = t^alpha sin sin, mixed to 1e-8) and c5a
+between steps.  Other workloads (--workload): 1d-63-m64 (1-D 63 points, M = 64),
+2d-511-m4096 (2-D 511 x 511, M = 4096, u = t^alpha sin sin, mixed to 1e-8),
+batch4096-2d-63-m256
 (4096 independent 2-D 63 x 63, M = 256 solves with alpha ~ U[0.1, 0.9] in one
-batched handle, mixed to 1e-8), c5b (1-D 4095 points, M = 65536, alpha = 0.2,
+batched handle, mixed to 1e-8), 1d-4095-m65536 (1-D 4095 points, M = 65536, alpha = 0.2,
 u = t^alpha sin, to 1e-8 with double-float inner cycles, as FP32 inner cycles
-stall on h = 1/4096; --precision fp64 for the FP64 form) and c4 (the served
+stall on h = 1/4096; --precision fp64 for the FP64 form) and served (the served
 request stream; each request's precision chosen by MGWR_AUTO).
 
   python bench.py [--gpus N] [--steps K] [--warmup W]
                   [--precision fp64|mixed|mixed_dd|dd|auto]
-                  [--workload c2|c1|c3|c5a|c5b|c4]
+                  [--workload 2d-255-m1024|1d-63-m64|2d-511-m4096|
+                              batch4096-2d-63-m256|1d-4095-m65536|served]
   python bench.py --impl reference ...   (the CPU oracle on the host cores)
 
 Prints one JSON line.  Multi-GPU runs (torchrun, one rank per GPU) are
@@ -45,23 +47,23 @@ NU1, NU2, CYCLE = 1, 1, 1
 METRIC = "space-time unknowns/s to rel-res 1e-10 (FP64 vs mixed)"
 # workload name -> (d, n, M, batch, exact solution, tolerance, default precision, description)
 WORKLOADS = {
-    "c2": (2, 255, 1024, 1, "t2", 1e-10, "fp64",
+    "2d-255-m1024": (2, 255, 1024, 1, "t2", 1e-10, "fp64",
            "2-D plain MGWR 255x255 interior, M=1024 on (0,1], u=t^2 sin(pi x) sin(pi y)"),
-    "c1": (1, 63, 64, 1, "t2", 1e-10, "fp64", "1-D plain MGWR 63 interior points, M=64, u=t^2 sin(pi x)"),
-    "c3": (2, 511, 4096, 1, "talpha", 1e-8, "mixed_dd",
+    "1d-63-m64": (1, 63, 64, 1, "t2", 1e-10, "fp64", "1-D plain MGWR 63 interior points, M=64, u=t^2 sin(pi x)"),
+    "2d-511-m4096": (2, 511, 4096, 1, "talpha", 1e-8, "mixed_dd",
            "2-D MGWR 511x511 interior, M=4096, u=t^alpha sin(pi x) sin(pi y)"),
-    "c5a": (2, 63, 256, 4096, "t2", 1e-8, "mixed_dd",
+    "batch4096-2d-63-m256": (2, 63, 256, 4096, "t2", 1e-8, "mixed_dd",
             "4096 independent 2-D 63x63, M=256 solves, alpha~U[0.1,0.9] (seed 1608), one batched handle"),
-    "c5b": (1, 4095, 65536, 1, "talpha", 1e-8, "dd",
+    "1d-4095-m65536": (1, 4095, 65536, 1, "talpha", 1e-8, "dd",
             "1-D MGWR 4095 interior points, M=65536 (long memory), u=t^alpha sin(pi x)"),
-    "c4": (0, 0, 0, 0, "", 1e-8, "auto", "served stream"),
+    "served": (0, 0, 0, 0, "", 1e-8, "auto", "served stream"),
 }
 # alpha of a workload when --alpha is not given
-WORKLOAD_ALPHA = {"c5b": 0.2}
+WORKLOAD_ALPHA = {"1d-4095-m65536": 0.2}
 # FP32 cycles per outer defect of a mixed workload when --inner is not given
-WORKLOAD_INNER = {"c5a": 4}
+WORKLOAD_INNER = {"batch4096-2d-63-m256": 4}
 # oracle time steps in the CPU-baseline sample (about 10-30 s of host work)
-ORACLE_SAMPLE_STEPS = {"c2": 256, "c5b": 2048}
+ORACLE_SAMPLE_STEPS = {"2d-255-m1024": 256, "1d-4095-m65536": 2048}
 UNIT = "unknowns/s"
 # --precision names and the library's codes (MGWR_FP64 .. MGWR_AUTO)
 PREC_CODES = {"fp64": 0, "mixed": 1, "mixed_dd": 2, "dd": 3, "auto": 4}
@@ -89,13 +91,13 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--precision", default=None, choices=["fp64", "mixed", "mixed_dd", "dd", "auto"])
-    p.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
-    p.add_argument("--requests", type=int, default=200, help="c4: first R requests of the stream")
-    p.add_argument("--slots", type=int, default=4, help="c4: server slots")
+    p.add_argument("--workload", default="2d-255-m1024", choices=sorted(WORKLOADS))
+    p.add_argument("--requests", type=int, default=200, help="served: first R requests of the stream")
+    p.add_argument("--slots", type=int, default=4, help="served: server slots")
     p.add_argument("--rate", type=float, default=None,
-                   help="c4: Poisson arrival rate, requests/s (default 0.7 x the sustained rate)")
+                   help="served: Poisson arrival rate, requests/s (default 0.7 x the sustained rate)")
     p.add_argument("--policy", default="fifo", choices=["fifo", "smallest"],
-                   help="c4: server admission order")
+                   help="served: server admission order")
     p.add_argument("--inner", type=int, default=None, help="mixed modes: FP32 cycles per outer defect")
     p.add_argument("--alpha", type=float, default=None)
     p.add_argument("--no-autotune", action="store_true", help="keep the default engine launch shapes")
@@ -320,7 +322,7 @@ def run_reference(args):
 
 
 def run_served(args):
-    """Config 4: a stream of mixed-shape requests through mgwr_submit / mgwr_poll.
+    """The served workload: a stream of mixed-shape requests through mgwr_submit / mgwr_poll.
 
     Pass 1 submits the whole list as fast as the server takes it and measures
     the sustained rate; pass 2 replays it with Poisson arrivals at 0.7 x that
@@ -338,8 +340,8 @@ def run_served(args):
     free, _ = torch.cuda.mem_get_info()
     budget = int(0.8 * free)
     reqs = inputs.request_stream(count=2000, seed=1608, rate=1.0)[: args.requests]
-    tol = WORKLOADS["c4"][5]
-    precision = args.precision or WORKLOADS["c4"][6]
+    tol = WORKLOADS["served"][5]
+    precision = args.precision or WORKLOADS["served"][6]
     prec = PREC_CODES[precision]
 
     def rhs(rq):
@@ -415,7 +417,7 @@ def run_served(args):
         "config": {"workload": f"served stream: first {len(reqs)} of 2000 requests (seed 1608), "
                                "1-D n=2^k-1 k~U{5..12} or 2-D k~U{5..9}, M=2^j j~U{7..12}, "
                                "alpha~U[0.1,0.9], u=t^2 or t^alpha sin, Poisson arrivals at 0.7x "
-                               "the sustained rate", "name": "c4", "slots": args.slots,
+                               "the sustained rate", "name": "served", "slots": args.slots,
                    "admission": args.policy,
                    "hbm_budget_bytes": budget, "host_window_bytes": host_cap},
         "served": {"p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
@@ -431,7 +433,7 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload == "c4":
+    if args.workload == "served":
         return run_served(args)
     import torch
 

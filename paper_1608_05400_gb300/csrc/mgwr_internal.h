@@ -137,6 +137,14 @@ cudaError_t launch_defect_long(const R* u, const R* f, RO* r, const Cx<R>* tspec
 template <class R>
 cudaError_t launch_restrict(const R* r, R* fc, R* uc, const LevelShape& fine, cudaStream_t s);
 
+// fc = full weighting of the defect after a red-black step, formed from the
+// black half-sweep's changes delta (as launch_defect_from_delta would write
+// it, red points of parity red_par) without storing it; uc = 0.  Bitwise the
+// same fc as launch_defect_from_delta followed by launch_restrict.
+template <class R>
+cudaError_t launch_restrict_delta(const R* delta, R* fc, R* uc, const R* zero, const LevelShape& fine,
+                                  int red_par, R hinv2, cudaStream_t s);
+
 // u (fine, n) += linear / bilinear interpolation of uc (coarse (n-1)/2).
 template <class R>
 cudaError_t launch_prolong(R* u, const R* uc, const LevelShape& fine, cudaStream_t s);

@@ -202,6 +202,95 @@ __global__ void __launch_bounds__(kLineBlock)
   }
 }
 
+// a * b rounded on its own (never fused into a following addition), as when
+// the product is stored and read back.
+__device__ __forceinline__ float mul_rounded(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rounded(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ dd mul_rounded(dd a, dd b) { return a * b; }
+
+// Full weighting of the defect that a complete red-black step leaves (the
+// defect from the black half-sweep's changes, see k_defect_from_delta) without
+// storing that defect: every fine value of the stencil is formed where it is
+// needed, 0 at a black point and hinv2 * (sum of the black neighbours'
+// changes) at a red one, and the stencil sums them in k_restrict's order, so
+// fc is bitwise what k_defect_from_delta followed by k_restrict gives.  Reads
+// the black changes (half a fine field, neighbours shared through L2) instead
+// of writing and reading back a whole fine defect; also clears uc.
+template <class R>
+__global__ void __launch_bounds__(kLineBlock)
+    k_restrict_delta(const R* __restrict__ delta, R* __restrict__ fc, R* __restrict__ uc,
+                     const R* __restrict__ zero, int d, int n, int M, int log_tpl, int ncpts,
+                     int red_par, R hinv2, size_t fstride, size_t cstride) {
+  constexpr int W = Vec<R>::W;
+  const LineMap<R> lm(log_tpl);
+  delta += blockIdx.y * fstride;
+  fc += blockIdx.y * cstride;
+  uc += blockIdx.y * cstride;
+  if (lm.line >= ncpts) return;
+  const int nc = (n - 1) / 2;
+  const int P = lm.line;
+  R* fo = fc + (size_t)P * M;
+  R* uo = uc + (size_t)P * M;
+  Vec<R> z;
+#pragma unroll
+  for (int k = 0; k < W; ++k) z.v[k] = R(0);
+  const size_t nM = (size_t)n * M;
+  // the defect at fine point (i, j), time values m .. m+W-1
+  auto r_at = [&](int i, int j, int m) -> Vec<R> {
+    const bool red = d == 1 ? (i & 1) == red_par : ((i + j) & 1) == red_par;
+    if (!red) return z;
+    const size_t pM = ((size_t)i + (size_t)j * n) * M;
+    const R* w = i > 0 ? delta + pM - M : zero;
+    const R* e = i < n - 1 ? delta + pM + M : zero;
+    const Vec<R> a = vload(w + m), b = vload(e + m);
+    Vec<R> out;
+    if (d == 2) {
+      const R* so = j > 0 ? delta + pM - nM : zero;
+      const R* no = j < n - 1 ? delta + pM + nM : zero;
+      const Vec<R> c = vload(so + m), g = vload(no + m);
+#pragma unroll
+      for (int k = 0; k < W; ++k) out.v[k] = mul_rounded(hinv2, (a.v[k] + b.v[k]) + (c.v[k] + g.v[k]));
+    } else {
+#pragma unroll
+      for (int k = 0; k < W; ++k) out.v[k] = mul_rounded(hinv2, a.v[k] + b.v[k]);
+    }
+    return out;
+  };
+  if (d == 1) {
+    const int c = 2 * P + 1;
+    for (int m = lm.m0; m < M; m += lm.step) {
+      const Vec<R> a = r_at(c - 1, 0, m), b = r_at(c, 0, m), e = r_at(c + 1, 0, m);
+      Vec<R> out;
+#pragma unroll
+      for (int k = 0; k < W; ++k) out.v[k] = R(0.25) * (a.v[k] + R(2) * b.v[k] + e.v[k]);
+      vstore(fo + m, out);
+      vstore(uo + m, z);
+    }
+  } else {
+    const int ci = 2 * (P % nc) + 1, cj = 2 * (P / nc) + 1;
+    for (int m = lm.m0; m < M; m += lm.step) {
+      Vec<R> out;
+      {
+        const Vec<R> a = r_at(ci - 1, cj - 1, m), b = r_at(ci, cj - 1, m), e = r_at(ci + 1, cj - 1, m);
+#pragma unroll
+        for (int k = 0; k < W; ++k) out.v[k] = a.v[k] + R(2) * b.v[k] + e.v[k];
+      }
+      {
+        const Vec<R> a = r_at(ci - 1, cj, m), b = r_at(ci, cj, m), e = r_at(ci + 1, cj, m);
+#pragma unroll
+        for (int k = 0; k < W; ++k) out.v[k] = out.v[k] + R(2) * (a.v[k] + R(2) * b.v[k] + e.v[k]);
+      }
+      {
+        const Vec<R> a = r_at(ci - 1, cj + 1, m), b = r_at(ci, cj + 1, m), e = r_at(ci + 1, cj + 1, m);
+#pragma unroll
+        for (int k = 0; k < W; ++k) out.v[k] = R(0.0625) * (out.v[k] + (a.v[k] + R(2) * b.v[k] + e.v[k]));
+      }
+      vstore(fo + m, out);
+      vstore(uo + m, z);
+    }
+  }
+}
+
 // 1-D interpolation taps of fine index i from the coarse grid (nc points):
 // fine 2J+1 takes coarse J (one tap, weight 1); fine 2J takes the mean of
 // coarse J-1 and J (two taps, weight 1/2), or half of the one inside the grid
@@ -588,6 +677,21 @@ cudaError_t launch_restrict(const R* r, R* fc, R* uc, const LevelShape& ls, cuda
 }
 
 template <class R>
+cudaError_t launch_restrict_delta(const R* delta, R* fc, R* uc, const R* zero, const LevelShape& ls,
+                                  int red_par, R hinv2, cudaStream_t s) {
+  const int nc = (ls.n - 1) / 2;
+  const int ncpts = ls.d == 1 ? nc : nc * nc;
+  if (ncpts == 0 || ls.batch == 0) return cudaSuccess;
+  int log_tpl;
+  unsigned blocks;
+  line_grid<R>(ls.M, ncpts, &log_tpl, &blocks);
+  k_restrict_delta<R><<<dim3(blocks, ls.batch), kLineBlock, 0, s>>>(
+      delta, fc, uc, zero, ls.d, ls.n, ls.M, log_tpl, ncpts, red_par, hinv2, ls.field_stride(),
+      (size_t)ncpts * ls.M);
+  return counted(cudaGetLastError());
+}
+
+template <class R>
 cudaError_t launch_prolong(R* u, const R* uc, const LevelShape& ls, cudaStream_t s) {
   const int npts = ls.d == 1 ? ls.n : ls.n * ls.n;
   const int nc = (ls.n - 1) / 2;
@@ -711,7 +815,9 @@ cudaError_t launch_round_cx(Cx<float>* dst, const Cx<double>* src, size_t count,
   template cudaError_t launch_defect_from_delta<R>(const R*, R*, const R*, const LevelShape&,  \
                                                    int, R, unsigned long long*, cudaStream_t); \
   template cudaError_t launch_restrict<R>(const R*, R*, R*, const LevelShape&, cudaStream_t);  \
-  template cudaError_t launch_prolong<R>(R*, const R*, const LevelShape&, cudaStream_t);
+  template cudaError_t launch_prolong<R>(R*, const R*, const LevelShape&, cudaStream_t);     \
+  template cudaError_t launch_restrict_delta<R>(const R*, R*, R*, const R*, const LevelShape&, \
+                                                int, R, cudaStream_t);
 MGWR_INST_R(double)
 MGWR_INST_R(float)
 MGWR_INST_R(dd)

@@ -174,14 +174,23 @@ int mgwr_set_inner_cycles(mgwr_t h, int cycles);
  * give up after half a second, and the call that ran it then returns
  * MGWR_E_CUDA.  MGWR_E_INVAL for another class or split. */
 #define MGWR_SPLIT_STAGED 16
+/* For MGWR_K_SWEEP32 (not the one-point solve) with M = 64, 128 or 256,
+ * `split` may instead be 1 | MGWR_SPLIT_TENSOR: the half-sweep as a dense
+ * product with the lower-triangular Toeplitz matrix of the inverse column on
+ * the tensor cores (tcgen05.mma with bf16 operands split into three pieces
+ * each, FP32 accumulation in tensor memory), 128 lines per CTA.  Results agree
+ * with the FFT engine's to FP32 rounding, not bitwise.  Other lengths fall
+ * back to the FFT engine.  Its waits give up after half a second, and the call
+ * that ran it then returns MGWR_E_CUDA. */
+#define MGWR_SPLIT_TENSOR 32
 int mgwr_set_engine_split(mgwr_t h, int kernel_class, int level, int split);
 int mgwr_get_engine_split(mgwr_t h, int kernel_class, int level, int* split);
 /* Tuner: times every E of each engine class the current precision runs (the
  * sweep and the full defect of its cycle hierarchy on every level, and in
  * the mixed modes the outer defect) on the handle's own data (per level, as
  * many instances as fit 2^27 values, at least one), writing to a temporary
- * field, and keeps the fastest per level (a larger E, or staged input lines,
- * must win by 3 %).  The
+ * field, and keeps the fastest per level (a larger E, staged input lines or
+ * the tensor-core sweep must win by 3 %).  The
  * handle's state is unchanged.  The choices are also recorded process-wide
  * for (class, d, n, M, batch): handles created later with that shape start
  * with them.  mgwr_set_engine_split / mgwr_get_engine_split address

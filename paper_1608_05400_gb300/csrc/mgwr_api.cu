@@ -64,6 +64,7 @@ struct mgwr_handle {
   double* r = nullptr;          // batch * M: r_1..r_M
   double* dk = nullptr;         // batch * (M+1): d_0..d_M
   double* kcol = nullptr;       // batch * nlev * M inverse columns
+  __nv_bfloat16* kern3 = nullptr;  // their bf16 pieces (tensor-core sweeps, M <= 256)
   double* c_dev = nullptr;      // batch
   Hier<double> h64;
   Hier<float> h32;
@@ -181,6 +182,8 @@ int check_staging(mgwr_t h) {
   bool hit = false;
   MGWR_CK(h, mgwr::take_stage_timeout(&hit));
   if (hit) return fail(h, MGWR_E_CUDA, "staged sweep: wait for bulk copies gave up");
+  MGWR_CK(h, mgwr::take_tc_timeout(&hit));
+  if (hit) return fail(h, MGWR_E_CUDA, "tensor-core sweep: wait for its MMAs gave up");
   return MGWR_OK;
 }
 
@@ -257,6 +260,11 @@ int ensure_h32(mgwr_t h) {
   MGWR_CK(h, mgwr::launch_round_cx(H.spec, h->h64.spec, nspec, h->stream));
   MGWR_CK(h, mgwr::launch_round_cx(H.tspec, h->h64.tspec, (size_t)h->B * h->L, h->stream));
   MGWR_CK(h, mgwr::launch_round_cx(H.tw, h->h64.tw, (size_t)h->Lt, h->stream));
+  if (mgwr::tensor_length(h->M)) {
+    const size_t lines = (size_t)h->B * h->nlev;
+    MGWR_TRY(dev_alloc(h, &h->kern3, sizeof(__nv_bfloat16) * lines * 3 * h->M));
+    MGWR_CK(h, mgwr::launch_split_bf16x3(h->kcol, h->kern3, h->M, lines, h->stream));
+  }
   MGWR_CK(h, cudaStreamSynchronize(h->stream));
   H.ready = true;
   return MGWR_OK;
@@ -338,11 +346,28 @@ int coarsest(mgwr_t h, Hier<R>& H) {
   const int pm = prof_begin(h, MGWR_K_COARSEST, (double)h->B);
   MGWR_CK(h, mgwr::launch_sweep<R>(H.f[0], H.u[0], (R*)nullptr, H.spec, (size_t)h->nlev * h->L,
                                     H.tw, H.zero, scratch_for<R>(h), shape(h, 0), 0, true, R(0),
-                                    split_of(h, sweep_class<R>(), 0),
+                                    split_of(h, sweep_class<R>(), 0) & ~mgwr::kTensor,
                                     h->stream));
   prof_end(h, pm);
   H.rs[0] = R_STALE;
   return MGWR_OK;
+}
+
+// One colour half-sweep of level l >= 1 (parity par) of the fields f -> u with
+// launch shape E: the tensor-core form for FP32 lines of 64 .. 256 steps when E
+// carries kTensor, else the FFT engine.
+template <class R>
+cudaError_t level_sweep(mgwr_t h, Hier<R>& H, int l, const R* f, R* u, R* delta,
+                        const LevelShape& ls, int par, int E) {
+  if constexpr (std::is_same<R, float>::value) {
+    if ((mgwr::effective_split(h->M, 4, E) & mgwr::kTensor) && h->kern3 != nullptr)
+      return mgwr::launch_sweep_tc(f, u, delta, h->kern3 + (size_t)l * 3 * h->M,
+                                   (size_t)h->nlev * 3 * h->M, ls, par, (float)h->hinv2[l],
+                                   h->stream);
+  }
+  return mgwr::launch_sweep<R>(f, u, delta, H.spec + (size_t)l * h->L, (size_t)h->nlev * h->L,
+                               H.tw, H.zero, scratch_for<R>(h), ls, par, false, R(h->hinv2[l]),
+                               E & ~mgwr::kTensor, h->stream);
 }
 
 // One colour half-sweep at level l >= 1; delta != null also records the change of
@@ -353,11 +378,8 @@ int sweep_colour(mgwr_t h, Hier<R>& H, int l, int colour, R* delta) {
   const size_t N = points(h, l);
   const double lines = (double)h->B * (double)(par == 0 ? (N + 1) / 2 : N / 2);
   const int pm = prof_begin(h, sweep_class<R>(), lines);
-  MGWR_CK(h, mgwr::launch_sweep<R>(H.f[l], H.u[l], delta, H.spec + (size_t)l * h->L,
-                                    (size_t)h->nlev * h->L, H.tw, H.zero, scratch_for<R>(h), shape(h, l), par,
-                                    false, R(h->hinv2[l]),
-                                    split_of(h, sweep_class<R>(), l),
-                                    h->stream));
+  MGWR_CK(h, level_sweep(h, H, l, H.f[l], H.u[l], delta, shape(h, l), par,
+                         split_of(h, sweep_class<R>(), l)));
   prof_end(h, pm);
   return MGWR_OK;
 }
@@ -788,8 +810,9 @@ template <class F>
 int tune_class(mgwr_t h, int cls, int l, int word, F launch) {
   int best = 1;
   float best_ms = 0.f;
-  const int cands[6] = {1, 2, 4, 1 | mgwr::kStaged, 2 | mgwr::kStaged, 4 | mgwr::kStaged};
-  const int ncand = cls == MGWR_K_SWEEP32 ? 6 : 3;
+  const int cands[7] = {1, 2, 4, 1 | mgwr::kStaged, 2 | mgwr::kStaged, 4 | mgwr::kStaged,
+                        1 | mgwr::kTensor};
+  const int ncand = cls == MGWR_K_SWEEP32 ? 7 : 3;
   for (int c = 0; c < ncand; ++c) {
     const int E = cands[c];
     if (mgwr::effective_split(h->M, word, E) != E) continue;  // same launch as a smaller E
@@ -832,14 +855,12 @@ int tune_hierarchy(mgwr_t h, Hier<R>& H, int cls_sweep, int cls_defect) {
         const size_t sstride = (size_t)h->nlev * h->L;
         if (l == 0)
           return mgwr::launch_sweep<R>(H.f[0], out, (R*)nullptr, spec, sstride, H.tw, H.zero,
-                                       scratch_for<R>(h), ls, 0, true, R(0), E, h->stream);
-        const cudaError_t e = mgwr::launch_sweep<R>(
-            H.f[l], out, (R*)nullptr, spec, sstride, H.tw, H.zero, scratch_for<R>(h), ls,
-            parity(h, MGWR_RED), false, R(h->hinv2[l]), E, h->stream);
+                                       scratch_for<R>(h), ls, 0, true, R(0),
+                                       E & ~mgwr::kTensor, h->stream);
+        const cudaError_t e =
+            level_sweep(h, H, l, H.f[l], out, (R*)nullptr, ls, parity(h, MGWR_RED), E);
         if (e != cudaSuccess) return e;
-        return mgwr::launch_sweep<R>(H.f[l], out, dlt, spec, sstride, H.tw, H.zero,
-                                     scratch_for<R>(h), ls, parity(h, MGWR_BLACK), false,
-                                     R(h->hinv2[l]), E, h->stream);
+        return level_sweep(h, H, l, H.f[l], out, dlt, ls, parity(h, MGWR_BLACK), E);
       });
     if (st == MGWR_OK)
       st = tune_class(h, cls_defect, l, sizeof(R) == 4 ? 4 : 8, [&](int E) {
@@ -1140,10 +1161,12 @@ int mgwr_set_engine_split(mgwr_t h, int kernel_class, int level, int split) {
       kernel_class != MGWR_K_DEFECT64 && kernel_class != MGWR_K_DEFECT32 &&
       kernel_class != MGWR_K_DEFECT_DD && kernel_class != MGWR_K_SWEEP_DD)
     return fail(h, MGWR_E_INVAL, "kernel class has no FFT engine");
-  const int E = split & ~mgwr::kStaged;
+  const int E = split & ~(mgwr::kStaged | mgwr::kTensor);
   if (E != 1 && E != 2 && E != 4) return fail(h, MGWR_E_INVAL, "split must be 1, 2 or 4");
-  if ((split & mgwr::kStaged) && kernel_class != MGWR_K_SWEEP32)
-    return fail(h, MGWR_E_INVAL, "staged input lines exist for the FP32 sweep only");
+  if ((split & (mgwr::kStaged | mgwr::kTensor)) && kernel_class != MGWR_K_SWEEP32)
+    return fail(h, MGWR_E_INVAL, "staged and tensor-core sweeps exist for FP32 only");
+  if ((split & mgwr::kStaged) && (split & mgwr::kTensor))
+    return fail(h, MGWR_E_INVAL, "staged and tensor-core sweeps are exclusive");
   if (level < -1 || level >= h->nlev) return fail(h, MGWR_E_INVAL, "level out of range");
   if (level == -1)
     h->split[kernel_class].assign(h->nlev, split);
@@ -1619,6 +1642,7 @@ int mgwr_footprint(int d, int n, int M, int batch, int precision, size_t* bytes)
     total += 2 * r512(8 * B * pts[0] * M);  // FP64 finest iterate and right-hand side
     for (size_t l = 0; l < nlev; ++l) total += (l + 1 < nlev ? 4 : 3) * r512(4 * B * pts[l] * M);
     total += r512(8 * B * nlev * L) + r512(8 * B * L) + r512(8 * Lt);
+    if (mgwr::tensor_length(M)) total += r512(2 * 3 * B * nlev * (size_t)M);  // bf16 pieces
     if (precision == MGWR_MIXED_DD)
       total += 2 * r512(8 * B * pts[0] * M) + r512(16 * B * L) + r512(16 * Lt);
   }

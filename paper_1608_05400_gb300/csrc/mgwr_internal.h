@@ -2,6 +2,7 @@
 // MGWR library.  Not part of the public ABI (see include/mgwr.h).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstddef>
@@ -45,8 +46,12 @@ inline int engine_length(int M) { return M <= kShortMaxM ? 2 * M : 2 * kLongB; }
 // then runs persistently with its input lines staged in shared memory by bulk
 // copies (mgwr_sweep_staged.cu); every other launch ignores the bit.
 constexpr int kStaged = 16;
+// A split value may instead carry kTensor: the FP32 sweep of lines of 64, 128
+// or 256 steps then runs on the tensor cores (mgwr_sweep_tc.cu).
+constexpr int kTensor = 32;
+inline bool tensor_length(int M) { return M == 64 || M == 128 || M == 256; }
 inline int engine_split(int L, int E) {
-  E &= ~kStaged;
+  E &= ~(kStaged | kTensor);
   if (E != 2 && E != 4) E = 1;
   while (E > 1 && L / 8 < E) E >>= 1;
   return E;
@@ -56,11 +61,13 @@ inline int engine_split(int L, int E) {
 // 2, the FP32 kernels split only their compile-time lengths 2^7 .. 2^13.
 inline int effective_split(int M, int word, int E) {
   const int staged = E & kStaged;
-  E &= ~kStaged;
+  const int tensor = E & kTensor;
+  E &= ~(kStaged | kTensor);
   if (M > kShortMaxM) return E == 2 ? 2 : 1;
   const int L = 2 * M;
   E = engine_split(L, E);
   if (word == 4 && (L < 128 || L > 8192)) return 1;
+  if (word == 4 && tensor && tensor_length(M)) return 1 | kTensor;
   return word == 4 ? (E | staged) : E;
 }
 // Complex values of the partitioned-convolution scratch for one launch on a
@@ -103,6 +110,20 @@ cudaError_t launch_sweep_staged(const float* f, float* u, float* delta, const Cx
                                 cudaStream_t s);
 // Reads and clears the flag of the staged sweep's bounded waits (synchronous).
 cudaError_t take_stage_timeout(bool* hit);
+
+// One colour half-sweep of FP32 lines of M = 64, 128 or 256 steps on the
+// tensor cores (tcgen05.mma, bf16 x 3 pieces, FP32 accumulation): as
+// launch_sweep without all_points, with the inverse column of instance b given
+// as three bf16 pieces (kern3 + b * kstride: piece q at q * M).  Results agree
+// with the FFT engine's to FP32 rounding (not bitwise).  A wait for the MMAs
+// that gives up (half a second) sets a flag read by take_tc_timeout.
+cudaError_t launch_sweep_tc(const float* f, float* u, float* delta, const __nv_bfloat16* kern3,
+                            size_t kstride, const LevelShape& ls, int par, float hinv2,
+                            cudaStream_t s);
+// dst[line][q][m], q = 0, 1, 2: bf16 pieces of src[line][m] (x = x0 + x1 + x2).
+cudaError_t launch_split_bf16x3(const double* src, __nv_bfloat16* dst, int M, size_t lines,
+                                cudaStream_t s);
+cudaError_t take_tc_timeout(bool* hit);
 
 // Defect after a red-black step from the black half-sweep's delta: r = 0 on the
 // black points, r = hinv2 * sum of neighbour deltas on the red points

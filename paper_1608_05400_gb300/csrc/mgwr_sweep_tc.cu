@@ -1,0 +1,399 @@
+// Smoother half-sweep on the tensor cores (FP32 fields, lines of 64 .. 256
+// steps; Sec. 3 Eq. red-black, Sec. 6 Eq. red-black_2d).
+//
+// For short lines the triangular Toeplitz product u_p = k * b_p (k the inverse
+// column of (T_M + sigma I), b_p = f_p + h^-2 * sum of neighbour lines) is
+// computed as a dense product: for a tile of 128 lines of one colour,
+// U[128 x M] = B[128 x M] * Kt[M x M] with Kt[k][t] = k[t - k] (0 for t < k),
+// on tcgen05.mma (kind::f16, bf16 operands, FP32 accumulator in tensor memory).
+// Both operands are split into three bf16 pieces (x = x0 + x1 + x2, 24
+// significant bits) and the six products of pieces whose orders add up to at
+// most 2 are accumulated, so the result carries FP32 accuracy.  Per line this
+// is 6 M^2 multiply-adds against the FFT engine's ~10 M log2(2M) operations on
+// the SIMT pipes, which the tensor cores more than repay up to M = 256.
+//
+// Per CTA (512 threads): the band of Kt for the first 32 time steps (row t,
+// column k: k_{t-k}) is built once in shared memory in the K-major no-swizzle
+// layout (8 x 16-byte core matrices); because Kt is Toeplitz, the band of
+// steps 32c .. 32c+31 is the same band shifted down by 32c rows, so chunk c
+// multiplies into accumulator columns 32c .. M-1 only (N = M - 32c: the
+// triangle above the diagonal is never computed).  The 128 lines' b values are
+// gathered chunk by chunk into two alternating buffers, split and written in
+// the same layout; one thread issues the chunk's twelve MMAs and commits them
+// to the buffer's mbarrier, and the next chunk is gathered while they run.
+// Every wait is bounded.  The epilogue reads the accumulator with tcgen05.ld
+// and writes u (and the change record).
+#include <cuda_bf16.h>
+
+#include "mgwr_common.cuh"
+#include "mgwr_tma.cuh"
+
+namespace mgwr {
+
+// Set when a CTA gave up waiting for its MMAs (read by take_tc_timeout).
+__device__ unsigned g_tc_timeout;
+
+namespace {
+
+constexpr int kTileRows = 128;  // lines per CTA: the MMA's M
+constexpr int kChunk = 32;      // time steps per shared-memory chunk (two K = 16 steps)
+constexpr int kThreads = 512;
+
+// Byte offset of element (r, k) in a K-major tile of kChunk columns: core
+// matrices of 8 rows x 16 bytes; the kChunk / 8 core matrices of a row group
+// are adjacent (128 bytes apart: the descriptor's leading byte offset), row
+// groups follow each other (kChunk / 8 * 128 bytes: the stride byte offset).
+__device__ __forceinline__ int core_off(int r, int kcore) {
+  return (r >> 3) * (kChunk / 8) * 128 + kcore * 128 + (r & 7) * 16;
+}
+
+__device__ __forceinline__ uint64_t smem_desc(unsigned addr) {
+  uint64_t d = (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)(128 >> 4) << 16;                 // leading byte offset: next K core
+  d |= (uint64_t)((kChunk / 8 * 128) >> 4) << 32;  // stride byte offset: next 8 rows
+  d |= (uint64_t)1 << 46;                          // descriptor version (tcgen05)
+  return d;                                        // base offset 0, no swizzle
+}
+
+// Instruction descriptor: FP32 accumulator, bf16 A and B, both K-major,
+// N = n columns, M = 128 rows.
+__host__ __device__ constexpr uint32_t mma_idesc(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(kTileRows >> 4) << 24);
+}
+
+// x = x0 + x1 + x2 in bf16 (each piece the rounding of what the others leave).
+__device__ __forceinline__ void split3(float x, __nv_bfloat16& a, __nv_bfloat16& b,
+                                       __nv_bfloat16& c) {
+  a = __float2bfloat16_rn(x);
+  const float r1 = x - __bfloat162float(a);
+  b = __float2bfloat16_rn(r1);
+  c = __float2bfloat16_rn(r1 - __bfloat162float(b));
+}
+
+__device__ __forceinline__ unsigned pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+  return (unsigned)__bfloat16_as_ushort(lo) | ((unsigned)__bfloat16_as_ushort(hi) << 16);
+}
+
+__device__ __forceinline__ void mma_bf16(unsigned tmem, uint64_t da, uint64_t db, uint32_t idesc,
+                                         unsigned accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+      "l"(da), "l"(db), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Which pieces (of B and of Kt) the six products use.
+__constant__ int kPieceA[6] = {0, 0, 1, 0, 1, 2};
+__constant__ int kPieceB[6] = {0, 1, 0, 2, 1, 0};
+
+}  // namespace
+
+template <int M>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_sweep_tc(const float* __restrict__ f, float* __restrict__ u, float* __restrict__ delta,
+               const __nv_bfloat16* __restrict__ kern3, int d, int n, int par, float hinv2,
+               int npts, int tiles_per_inst, size_t fstride, size_t kstride) {
+  constexpr int kA = kTileRows * kChunk * 2;  // bytes per piece of a b-values chunk
+  constexpr int kB = M * kChunk * 2;          // bytes per piece of the Kt band
+  constexpr int kNumChunks = M / kChunk;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ unsigned tmem_slot;
+  __shared__ int rowp[kTileRows];
+  __shared__ unsigned rowm[kTileRows];
+  unsigned char* sA = smem_raw;               // 2 buffers x 3 pieces
+  unsigned char* sB = smem_raw + 6 * kA;      // 3 pieces
+  __nv_bfloat16* sK = reinterpret_cast<__nv_bfloat16*>(smem_raw + 6 * kA + 3 * kB);  // 3 x M
+
+  const int inst = blockIdx.x / tiles_per_inst;
+  const int rt = blockIdx.x - inst * tiles_per_inst;
+  f += (size_t)inst * fstride;
+  u += (size_t)inst * fstride;
+  if (delta != nullptr) delta += (size_t)inst * fstride;
+  kern3 += (size_t)inst * kstride;
+
+  // rows of the tile: the colour's points rt*128 .. rt*128+127 and their neighbours
+  if (threadIdx.x < kTileRows) {
+    const int k = rt * kTileRows + threadIdx.x;
+    unsigned m = 0;
+    int p = 0;
+    if (k < npts) {
+      int i = 0, j = 0;
+      p = colour_point(k, d, n, par, i, j);
+      m = 16u | (i > 0 ? 1u : 0u) | (i < n - 1 ? 2u : 0u);
+      if (d == 2) m |= (j > 0 ? 4u : 0u) | (j < n - 1 ? 8u : 0u);
+    }
+    rowp[threadIdx.x] = p;
+    rowm[threadIdx.x] = m;
+  }
+  for (int i = threadIdx.x; i < 3 * M; i += kThreads) sK[i] = kern3[i];
+  if (threadIdx.x == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    mbar_fence_init();
+  }
+  if (threadIdx.x < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"(M)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  __syncthreads();  // sK complete
+  // the band of the first chunk: row t, column k holds k_{t-k} (0 for t < k)
+  for (int item = threadIdx.x; item < 3 * M * 4; item += kThreads) {
+    const int piece = item / (M * 4);
+    const int rest = item - piece * (M * 4);
+    const int t = rest >> 2, kc = rest & 3;
+    const __nv_bfloat16* kp = sK + piece * M;
+    unsigned short v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int idx = t - (kc * 8 + q);
+      v[q] = idx >= 0 ? __bfloat16_as_ushort(kp[idx]) : (unsigned short)0;
+    }
+    *reinterpret_cast<uint4*>(sB + piece * kB + core_off(t, kc)) =
+        make_uint4(v[0] | ((unsigned)v[1] << 16), v[2] | ((unsigned)v[3] << 16),
+                   v[4] | ((unsigned)v[5] << 16), v[6] | ((unsigned)v[7] << 16));
+  }
+  const unsigned tmem = tmem_slot;
+  const size_t nM = (size_t)n * M;
+  bool ok = true;
+  int issued = -1;  // last chunk whose MMAs were issued (the same in every thread)
+
+  for (int ch = 0; ch < kNumChunks; ++ch) {
+    const int buf = ch & 1;
+    unsigned char* sAb = sA + buf * 3 * kA;
+    if (ch >= 2) {
+      // the MMAs of chunk ch - 2 have read this buffer
+      const int failed = mbar_wait_bounded(&bars[buf], (unsigned)(((ch - 2) >> 1) & 1)) ? 0 : 1;
+      if (__syncthreads_or(failed)) {
+        ok = false;
+        if (threadIdx.x == 0) atomicOr(&g_tc_timeout, 1u);
+        break;
+      }
+    }
+    // b values of the chunk: 128 rows x 4 core columns of 8 steps, one per thread
+    {
+      const int item = threadIdx.x;
+      const int r = item >> 2, kc = item & 3;
+      const int m0 = ch * kChunk + kc * 8;
+      const unsigned msk = rowm[r];
+      float b[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) b[q] = 0.f;
+      if (msk & 16u) {
+        const size_t pM = (size_t)rowp[r] * M + m0;
+        // 8 steps of a line, 0 for a neighbour outside the grid
+        auto line8 = [&](const float* src, bool present, float (&o)[8]) {
+          if (present) {
+            const float4 x = *reinterpret_cast<const float4*>(src);
+            const float4 y = *reinterpret_cast<const float4*>(src + 4);
+            o[0] = x.x; o[1] = x.y; o[2] = x.z; o[3] = x.w;
+            o[4] = y.x; o[5] = y.y; o[6] = y.z; o[7] = y.w;
+          } else {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) o[q] = 0.f;
+          }
+        };
+        // the neighbour sum in the FFT sweep's order: (west + east) + (south + north)
+        float fv[8], a[8], c[8], s2[8];
+        line8(u + pM - M, (msk & 1u) != 0, a);
+        line8(u + pM + M, (msk & 2u) != 0, c);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) s2[q] = a[q] + c[q];
+        if (d == 2) {
+          line8(u + pM - nM, (msk & 4u) != 0, a);
+          line8(u + pM + nM, (msk & 8u) != 0, c);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) s2[q] = s2[q] + (a[q] + c[q]);
+        }
+        line8(f + pM, true, fv);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) b[q] = fv[q] + hinv2 * s2[q];
+      }
+      __nv_bfloat16 p0[8], p1[8], p2[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) split3(b[q], p0[q], p1[q], p2[q]);
+      const int off = core_off(r, kc);
+      *reinterpret_cast<uint4*>(sAb + off) =
+          make_uint4(pack2(p0[0], p0[1]), pack2(p0[2], p0[3]), pack2(p0[4], p0[5]), pack2(p0[6], p0[7]));
+      *reinterpret_cast<uint4*>(sAb + kA + off) =
+          make_uint4(pack2(p1[0], p1[1]), pack2(p1[2], p1[3]), pack2(p1[4], p1[5]), pack2(p1[6], p1[7]));
+      *reinterpret_cast<uint4*>(sAb + 2 * kA + off) =
+          make_uint4(pack2(p2[0], p2[1]), pack2(p2[2], p2[3]), pack2(p2[4], p2[5]), pack2(p2[6], p2[7]));
+    }
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (threadIdx.x == 0) {
+      // chunk ch reaches output steps 32 ch .. M-1: N = M - 32 ch columns from 32 ch
+      const uint32_t idesc = mma_idesc(M - ch * kChunk);
+      const unsigned dcol = tmem + (unsigned)(ch * kChunk);
+#pragma unroll
+      for (int s = 0; s < kChunk / 16; ++s) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+          const uint64_t da = smem_desc(smem_u32(sAb + kPieceA[c] * kA) + s * 256);
+          const uint64_t db = smem_desc(smem_u32(sB + kPieceB[c] * kB) + s * 256);
+          mma_bf16(dcol, da, db, idesc, (ch > 0 || s > 0 || c > 0) ? 1u : 0u);
+        }
+      }
+      mma_commit(&bars[buf]);
+    }
+    issued = ch;
+  }
+  if (ok) {
+    // the last commit covers every MMA issued before it
+    const int last = kNumChunks - 1;
+    const int failed =
+        mbar_wait_bounded(&bars[last & 1], (unsigned)((last >> 1) & 1)) ? 0 : 1;
+    if (__syncthreads_or(failed)) {
+      ok = false;
+      if (threadIdx.x == 0) atomicOr(&g_tc_timeout, 1u);
+    }
+  }
+  if (!ok && issued >= 0 && threadIdx.x == 0) {
+    // let what was issued finish (its last commit covers all of it) before the
+    // accumulator is released
+    (void)mbar_wait_bounded(&bars[issued & 1], (unsigned)((issued >> 1) & 1));
+  }
+  tc_fence_after();
+
+  // epilogue: warp w reads lanes 32 (w % 4) .. +31 (its rows), columns of quarter w / 4
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r = 32 * (w & 3) + lane;
+  const unsigned msk = rowm[r];
+  float* ur = u + (size_t)rowp[r] * M;
+  float* dr = delta != nullptr ? delta + (size_t)rowp[r] * M : nullptr;
+  if (ok) {
+#pragma unroll 1
+    for (int c = (w >> 2) * (M / 4); c < (w >> 2) * (M / 4) + M / 4; c += 8) {
+      unsigned v[8];
+      const unsigned addr = tmem + ((unsigned)(32 * (w & 3)) << 16) + (unsigned)c;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+            "=r"(v[7])
+          : "r"(addr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (msk & 16u) {
+        const float4 y0 = make_float4(__uint_as_float(v[0]), __uint_as_float(v[1]),
+                                      __uint_as_float(v[2]), __uint_as_float(v[3]));
+        const float4 y1 = make_float4(__uint_as_float(v[4]), __uint_as_float(v[5]),
+                                      __uint_as_float(v[6]), __uint_as_float(v[7]));
+        if (dr != nullptr) {
+          const float4 o0 = *reinterpret_cast<const float4*>(ur + c);
+          const float4 o1 = *reinterpret_cast<const float4*>(ur + c + 4);
+          *reinterpret_cast<float4*>(dr + c) =
+              make_float4(y0.x - o0.x, y0.y - o0.y, y0.z - o0.z, y0.w - o0.w);
+          *reinterpret_cast<float4*>(dr + c + 4) =
+              make_float4(y1.x - o1.x, y1.y - o1.y, y1.z - o1.z, y1.w - o1.w);
+        }
+        *reinterpret_cast<float4*>(ur + c) = y0;
+        *reinterpret_cast<float4*>(ur + c + 4) = y1;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x < 32)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(M)
+                 : "memory");
+}
+
+namespace {
+
+template <int M>
+cudaError_t tc_launch(const float* f, float* u, float* delta, const __nv_bfloat16* kern3,
+                      size_t kstride, const LevelShape& ls, int par, float hinv2, cudaStream_t s) {
+  const int npts = colour_count(ls.d, ls.n, par);
+  if (npts == 0 || ls.batch == 0) return cudaSuccess;
+  const int tiles = (npts + kTileRows - 1) / kTileRows;
+  const long long grid = (long long)tiles * ls.batch;
+  if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
+  constexpr int kA = kTileRows * kChunk * 2, kB = M * kChunk * 2;
+  // shared memory also caps the CTAs per SM so that their tensor-memory columns
+  // (M each) fit the SM's 512 at once
+  size_t smem = 6 * (size_t)kA + 3 * (size_t)kB + 3 * (size_t)M * 2;
+  const size_t per_sm_cap = 512 / M;  // CTAs whose accumulators fit together
+  const size_t min_smem = (228 * 1024) / (per_sm_cap + 1) + 1;
+  if (smem < min_smem) smem = min_smem;
+  auto kern = k_sweep_tc<M>;
+  cudaError_t e = prepare_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  kern<<<(unsigned)grid, kThreads, smem, s>>>(f, u, delta, kern3, ls.d, ls.n, par, hinv2, npts,
+                                              tiles, ls.field_stride(), kstride);
+  return cudaSuccess;
+}
+
+__global__ void k_split_bf16x3(const double* __restrict__ src, __nv_bfloat16* __restrict__ dst,
+                               int M, size_t lines) {
+  const size_t total = lines * (size_t)M;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const size_t line = i / M, m = i - line * M;
+    const double x = src[i];
+    const __nv_bfloat16 a = __double2bfloat16(x);
+    const double r1 = x - (double)__bfloat162float(a);
+    const __nv_bfloat16 b = __double2bfloat16(r1);
+    const __nv_bfloat16 c = __double2bfloat16(r1 - (double)__bfloat162float(b));
+    __nv_bfloat16* o = dst + line * 3 * M;
+    o[m] = a;
+    o[M + m] = b;
+    o[2 * M + m] = c;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_sweep_tc(const float* f, float* u, float* delta, const __nv_bfloat16* kern3,
+                            size_t kstride, const LevelShape& ls, int par, float hinv2,
+                            cudaStream_t s) {
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (ls.M) {
+    case 64: e = tc_launch<64>(f, u, delta, kern3, kstride, ls, par, hinv2, s); break;
+    case 128: e = tc_launch<128>(f, u, delta, kern3, kstride, ls, par, hinv2, s); break;
+    case 256: e = tc_launch<256>(f, u, delta, kern3, kstride, ls, par, hinv2, s); break;
+    default: break;
+  }
+  if (e != cudaSuccess) return e;
+  return counted(cudaGetLastError());
+}
+
+cudaError_t launch_split_bf16x3(const double* src, __nv_bfloat16* dst, int M, size_t lines,
+                                cudaStream_t s) {
+  k_split_bf16x3<<<elementwise_grid(lines * (size_t)M), 256, 0, s>>>(src, dst, M, lines);
+  return counted(cudaGetLastError());
+}
+
+cudaError_t take_tc_timeout(bool* hit) {
+  unsigned v = 0;
+  cudaError_t e = cudaMemcpyFromSymbol(&v, g_tc_timeout, sizeof(v));
+  if (e != cudaSuccess) return e;
+  *hit = v != 0;
+  if (v != 0) {
+    const unsigned z = 0;
+    e = cudaMemcpyToSymbol(g_tc_timeout, &z, sizeof(z));
+  }
+  return e;
+}
+
+}  // namespace mgwr

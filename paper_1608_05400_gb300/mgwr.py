@@ -33,6 +33,7 @@ MGWR_RED, MGWR_BLACK = 0, 1
 MGWR_ORDER_TEXT, MGWR_ORDER_TABLE = 0, 1
 MGWR_POLICY_FIFO, MGWR_POLICY_SMALLEST = 0, 1
 MGWR_SPLIT_STAGED = 16
+MGWR_SPLIT_TENSOR = 32
 
 
 class mgwr_stats(C.Structure):

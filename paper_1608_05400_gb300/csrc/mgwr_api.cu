@@ -64,7 +64,7 @@ struct mgwr_handle {
   double* r = nullptr;          // batch * M: r_1..r_M
   double* dk = nullptr;         // batch * (M+1): d_0..d_M
   double* kcol = nullptr;       // batch * nlev * M inverse columns
-  __nv_bfloat16* kern3 = nullptr;  // their bf16 pieces (tensor-core sweeps, M <= 256)
+  unsigned char* tc_band = nullptr;  // their Toeplitz bands in bf16 pieces (tensor-core sweeps)
   double* c_dev = nullptr;      // batch
   Hier<double> h64;
   Hier<float> h32;
@@ -262,8 +262,8 @@ int ensure_h32(mgwr_t h) {
   MGWR_CK(h, mgwr::launch_round_cx(H.tw, h->h64.tw, (size_t)h->Lt, h->stream));
   if (mgwr::tensor_length(h->M)) {
     const size_t lines = (size_t)h->B * h->nlev;
-    MGWR_TRY(dev_alloc(h, &h->kern3, sizeof(__nv_bfloat16) * lines * 3 * h->M));
-    MGWR_CK(h, mgwr::launch_split_bf16x3(h->kcol, h->kern3, h->M, lines, h->stream));
+    MGWR_TRY(dev_alloc(h, &h->tc_band, mgwr::tc_band_bytes(h->M) * lines));
+    MGWR_CK(h, mgwr::launch_band_bf16x3(h->kcol, h->tc_band, h->M, lines, h->stream));
   }
   MGWR_CK(h, cudaStreamSynchronize(h->stream));
   H.ready = true;
@@ -360,10 +360,11 @@ template <class R>
 cudaError_t level_sweep(mgwr_t h, Hier<R>& H, int l, const R* f, R* u, R* delta,
                         const LevelShape& ls, int par, int E) {
   if constexpr (std::is_same<R, float>::value) {
-    if ((mgwr::effective_split(h->M, 4, E) & mgwr::kTensor) && h->kern3 != nullptr)
-      return mgwr::launch_sweep_tc(f, u, delta, h->kern3 + (size_t)l * 3 * h->M,
-                                   (size_t)h->nlev * 3 * h->M, ls, par, (float)h->hinv2[l],
-                                   h->stream);
+    if ((mgwr::effective_split(h->M, 4, E) & mgwr::kTensor) && h->tc_band != nullptr) {
+      const size_t bb = mgwr::tc_band_bytes(h->M);
+      return mgwr::launch_sweep_tc(f, u, delta, h->tc_band + (size_t)l * bb, (size_t)h->nlev * bb,
+                                   ls, par, (float)h->hinv2[l], h->stream);
+    }
   }
   return mgwr::launch_sweep<R>(f, u, delta, H.spec + (size_t)l * h->L, (size_t)h->nlev * h->L,
                                H.tw, H.zero, scratch_for<R>(h), ls, par, false, R(h->hinv2[l]),
@@ -1642,7 +1643,7 @@ int mgwr_footprint(int d, int n, int M, int batch, int precision, size_t* bytes)
     total += 2 * r512(8 * B * pts[0] * M);  // FP64 finest iterate and right-hand side
     for (size_t l = 0; l < nlev; ++l) total += (l + 1 < nlev ? 4 : 3) * r512(4 * B * pts[l] * M);
     total += r512(8 * B * nlev * L) + r512(8 * B * L) + r512(8 * Lt);
-    if (mgwr::tensor_length(M)) total += r512(2 * 3 * B * nlev * (size_t)M);  // bf16 pieces
+    if (mgwr::tensor_length(M)) total += r512(192 * B * nlev * (size_t)M);  // Toeplitz bands
     if (precision == MGWR_MIXED_DD)
       total += 2 * r512(8 * B * pts[0] * M) + r512(16 * B * L) + r512(16 * Lt);
   }

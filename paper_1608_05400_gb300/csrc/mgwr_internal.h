@@ -114,15 +114,20 @@ cudaError_t take_stage_timeout(bool* hit);
 // One colour half-sweep of FP32 lines of M = 64, 128 or 256 steps on the
 // tensor cores (tcgen05.mma, bf16 x 3 pieces, FP32 accumulation): as
 // launch_sweep without all_points, with the inverse column of instance b given
-// as three bf16 pieces (kern3 + b * kstride: piece q at q * M).  Results agree
-// with the FFT engine's to FP32 rounding (not bitwise).  A wait for the MMAs
-// that gives up (half a second) sets a flag read by take_tc_timeout.
-cudaError_t launch_sweep_tc(const float* f, float* u, float* delta, const __nv_bfloat16* kern3,
-                            size_t kstride, const LevelShape& ls, int par, float hinv2,
+// as its Toeplitz band (band + b * bstride, tc_band_bytes(M) bytes, written by
+// launch_band_bf16x3).  Results agree with the FFT engine's to FP32 rounding
+// (not bitwise).  A wait that gives up (half a second) sets a flag read by
+// take_tc_timeout.
+cudaError_t launch_sweep_tc(const float* f, float* u, float* delta, const unsigned char* band,
+                            size_t bstride, const LevelShape& ls, int par, float hinv2,
                             cudaStream_t s);
-// dst[line][q][m], q = 0, 1, 2: bf16 pieces of src[line][m] (x = x0 + x1 + x2).
-cudaError_t launch_split_bf16x3(const double* src, __nv_bfloat16* dst, int M, size_t lines,
-                                cudaStream_t s);
+// Bytes of one Toeplitz band: three bf16 pieces of M rows x 32 columns.
+size_t tc_band_bytes(int M);
+// band + line * tc_band_bytes(M): the band of the inverse column kcol[line]
+// (rows t, columns k < 32: k_{t-k}, 0 for t < k) split into three bf16 pieces
+// (x = x0 + x1 + x2), in the tensor-core kernel's shared-memory layout.
+cudaError_t launch_band_bf16x3(const double* kcol, unsigned char* band, int M, size_t lines,
+                               cudaStream_t s);
 cudaError_t take_tc_timeout(bool* hit);
 
 // Defect after a red-black step from the black half-sweep's delta: r = 0 on the

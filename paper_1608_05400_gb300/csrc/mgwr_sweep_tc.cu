@@ -13,8 +13,9 @@
 // the SIMT pipes, which the tensor cores more than repay up to M = 256.
 //
 // Per CTA (512 threads): the band of Kt for the first 32 time steps (row t,
-// column k: k_{t-k}) is built once in shared memory in the K-major no-swizzle
-// layout (8 x 16-byte core matrices); because Kt is Toeplitz, the band of
+// column k: k_{t-k}), built once per instance and level at setup in the
+// K-major no-swizzle layout (8 x 16-byte core matrices), arrives in shared
+// memory by one bulk copy (cp.async.bulk on an mbarrier); because Kt is Toeplitz, the band of
 // steps 32c .. 32c+31 is the same band shifted down by 32c rows, so chunk c
 // multiplies into accumulator columns 32c .. M-1 only (N = M - 32c: the
 // triangle above the diagonal is never computed).  The 128 lines' b values are
@@ -107,26 +108,25 @@ __constant__ int kPieceB[6] = {0, 1, 0, 2, 1, 0};
 template <int M>
 __global__ void __launch_bounds__(kThreads, 1)
     k_sweep_tc(const float* __restrict__ f, float* __restrict__ u, float* __restrict__ delta,
-               const __nv_bfloat16* __restrict__ kern3, int d, int n, int par, float hinv2,
-               int npts, int tiles_per_inst, size_t fstride, size_t kstride) {
+               const unsigned char* __restrict__ band, int d, int n, int par, float hinv2,
+               int npts, int tiles_per_inst, size_t fstride, size_t bstride) {
   constexpr int kA = kTileRows * kChunk * 2;  // bytes per piece of a b-values chunk
   constexpr int kB = M * kChunk * 2;          // bytes per piece of the Kt band
   constexpr int kNumChunks = M / kChunk;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ __align__(8) uint64_t bars[3];  // two operand buffers, the band
   __shared__ unsigned tmem_slot;
   __shared__ int rowp[kTileRows];
   __shared__ unsigned rowm[kTileRows];
   unsigned char* sA = smem_raw;               // 2 buffers x 3 pieces
   unsigned char* sB = smem_raw + 6 * kA;      // 3 pieces
-  __nv_bfloat16* sK = reinterpret_cast<__nv_bfloat16*>(smem_raw + 6 * kA + 3 * kB);  // 3 x M
 
   const int inst = blockIdx.x / tiles_per_inst;
   const int rt = blockIdx.x - inst * tiles_per_inst;
   f += (size_t)inst * fstride;
   u += (size_t)inst * fstride;
   if (delta != nullptr) delta += (size_t)inst * fstride;
-  kern3 += (size_t)inst * kstride;
+  band += (size_t)inst * bstride;
 
   // rows of the tile: the colour's points rt*128 .. rt*128+127 and their neighbours
   if (threadIdx.x < kTileRows) {
@@ -142,11 +142,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     rowp[threadIdx.x] = p;
     rowm[threadIdx.x] = m;
   }
-  for (int i = threadIdx.x; i < 3 * M; i += kThreads) sK[i] = kern3[i];
   if (threadIdx.x == 0) {
     mbar_init(&bars[0], 1);
     mbar_init(&bars[1], 1);
+    mbar_init(&bars[2], 1);
     mbar_fence_init();
+    // the three pieces of the band: 3 * kB contiguous bytes (16-byte multiples)
+    mbar_arrive_expect_tx(&bars[2], 3u * kB);
+    bulk_copy_g2s(sB, band, 3u * kB, &bars[2]);
   }
   if (threadIdx.x < 32) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -155,23 +158,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  __syncthreads();  // sK complete
-  // the band of the first chunk: row t, column k holds k_{t-k} (0 for t < k)
-  for (int item = threadIdx.x; item < 3 * M * 4; item += kThreads) {
-    const int piece = item / (M * 4);
-    const int rest = item - piece * (M * 4);
-    const int t = rest >> 2, kc = rest & 3;
-    const __nv_bfloat16* kp = sK + piece * M;
-    unsigned short v[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int idx = t - (kc * 8 + q);
-      v[q] = idx >= 0 ? __bfloat16_as_ushort(kp[idx]) : (unsigned short)0;
-    }
-    *reinterpret_cast<uint4*>(sB + piece * kB + core_off(t, kc)) =
-        make_uint4(v[0] | ((unsigned)v[1] << 16), v[2] | ((unsigned)v[3] << 16),
-                   v[4] | ((unsigned)v[5] << 16), v[6] | ((unsigned)v[7] << 16));
-  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
   const unsigned tmem = tmem_slot;
   const size_t nM = (size_t)n * M;
   bool ok = true;
@@ -243,6 +232,18 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    if (ch == 0) {
+      // the MMA issuer needs the band (the copy and the MMAs are both asynchronous)
+      const int failed = threadIdx.x == 0 && !mbar_wait_bounded(&bars[2], 0u) ? 1 : 0;
+      if (__syncthreads_or(failed)) {
+        ok = false;
+        if (threadIdx.x == 0) {
+          atomicOr(&g_tc_timeout, 1u);
+          (void)mbar_wait_bounded(&bars[2], 0u);
+        }
+        break;
+      }
+    }
     if (threadIdx.x == 0) {
       // chunk ch reaches output steps 32 ch .. M-1: N = M - 32 ch columns from 32 ch
       const uint32_t idesc = mma_idesc(M - ch * kChunk);
@@ -322,8 +323,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 namespace {
 
 template <int M>
-cudaError_t tc_launch(const float* f, float* u, float* delta, const __nv_bfloat16* kern3,
-                      size_t kstride, const LevelShape& ls, int par, float hinv2, cudaStream_t s) {
+cudaError_t tc_launch(const float* f, float* u, float* delta, const unsigned char* band,
+                      size_t bstride, const LevelShape& ls, int par, float hinv2, cudaStream_t s) {
   const int npts = colour_count(ls.d, ls.n, par);
   if (npts == 0 || ls.batch == 0) return cudaSuccess;
   const int tiles = (npts + kTileRows - 1) / kTileRows;
@@ -332,55 +333,63 @@ cudaError_t tc_launch(const float* f, float* u, float* delta, const __nv_bfloat1
   constexpr int kA = kTileRows * kChunk * 2, kB = M * kChunk * 2;
   // shared memory also caps the CTAs per SM so that their tensor-memory columns
   // (M each) fit the SM's 512 at once
-  size_t smem = 6 * (size_t)kA + 3 * (size_t)kB + 3 * (size_t)M * 2;
+  size_t smem = 6 * (size_t)kA + 3 * (size_t)kB;
   const size_t per_sm_cap = 512 / M;  // CTAs whose accumulators fit together
   const size_t min_smem = (228 * 1024) / (per_sm_cap + 1) + 1;
   if (smem < min_smem) smem = min_smem;
   auto kern = k_sweep_tc<M>;
   cudaError_t e = prepare_smem(kern, smem);
   if (e != cudaSuccess) return e;
-  kern<<<(unsigned)grid, kThreads, smem, s>>>(f, u, delta, kern3, ls.d, ls.n, par, hinv2, npts,
-                                              tiles, ls.field_stride(), kstride);
+  kern<<<(unsigned)grid, kThreads, smem, s>>>(f, u, delta, band, ls.d, ls.n, par, hinv2, npts,
+                                              tiles, ls.field_stride(), bstride);
   return cudaSuccess;
 }
 
-__global__ void k_split_bf16x3(const double* __restrict__ src, __nv_bfloat16* __restrict__ dst,
-                               int M, size_t lines) {
-  const size_t total = lines * (size_t)M;
+// The Kt band of every (instance, level) line of inverse columns: line l,
+// piece q, row t, column k (k < 32) holds piece q of k_{t-k} (0 for t < k), at
+// byte l * 3 * 64 M + q * 64 M + core_off(t, k / 8) + 2 (k % 8).
+__global__ void k_band_bf16x3(const double* __restrict__ kcol, unsigned char* __restrict__ band,
+                              int M, size_t lines) {
+  const size_t per_line = (size_t)M * kChunk;
+  const size_t total = lines * per_line;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
        i += (size_t)gridDim.x * blockDim.x) {
-    const size_t line = i / M, m = i - line * M;
-    const double x = src[i];
+    const size_t line = i / per_line;
+    const int rest = (int)(i - line * per_line);
+    const int t = rest / kChunk, k = rest - t * kChunk;
+    const double x = t >= k ? kcol[line * M + (t - k)] : 0.0;
     const __nv_bfloat16 a = __double2bfloat16(x);
     const double r1 = x - (double)__bfloat162float(a);
     const __nv_bfloat16 b = __double2bfloat16(r1);
     const __nv_bfloat16 c = __double2bfloat16(r1 - (double)__bfloat162float(b));
-    __nv_bfloat16* o = dst + line * 3 * M;
-    o[m] = a;
-    o[M + m] = b;
-    o[2 * M + m] = c;
+    unsigned char* o = band + line * 3 * (size_t)(2 * per_line) + core_off(t, k >> 3) + 2 * (k & 7);
+    *reinterpret_cast<__nv_bfloat16*>(o) = a;
+    *reinterpret_cast<__nv_bfloat16*>(o + 2 * per_line) = b;
+    *reinterpret_cast<__nv_bfloat16*>(o + 4 * per_line) = c;
   }
 }
 
 }  // namespace
 
-cudaError_t launch_sweep_tc(const float* f, float* u, float* delta, const __nv_bfloat16* kern3,
-                            size_t kstride, const LevelShape& ls, int par, float hinv2,
+cudaError_t launch_sweep_tc(const float* f, float* u, float* delta, const unsigned char* band,
+                            size_t bstride, const LevelShape& ls, int par, float hinv2,
                             cudaStream_t s) {
   cudaError_t e = cudaErrorInvalidValue;
   switch (ls.M) {
-    case 64: e = tc_launch<64>(f, u, delta, kern3, kstride, ls, par, hinv2, s); break;
-    case 128: e = tc_launch<128>(f, u, delta, kern3, kstride, ls, par, hinv2, s); break;
-    case 256: e = tc_launch<256>(f, u, delta, kern3, kstride, ls, par, hinv2, s); break;
+    case 64: e = tc_launch<64>(f, u, delta, band, bstride, ls, par, hinv2, s); break;
+    case 128: e = tc_launch<128>(f, u, delta, band, bstride, ls, par, hinv2, s); break;
+    case 256: e = tc_launch<256>(f, u, delta, band, bstride, ls, par, hinv2, s); break;
     default: break;
   }
   if (e != cudaSuccess) return e;
   return counted(cudaGetLastError());
 }
 
-cudaError_t launch_split_bf16x3(const double* src, __nv_bfloat16* dst, int M, size_t lines,
-                                cudaStream_t s) {
-  k_split_bf16x3<<<elementwise_grid(lines * (size_t)M), 256, 0, s>>>(src, dst, M, lines);
+size_t tc_band_bytes(int M) { return 3 * (size_t)M * kChunk * 2; }
+
+cudaError_t launch_band_bf16x3(const double* kcol, unsigned char* band, int M, size_t lines,
+                               cudaStream_t s) {
+  k_band_bf16x3<<<elementwise_grid(lines * (size_t)M * kChunk), 256, 0, s>>>(kcol, band, M, lines);
   return counted(cudaGetLastError());
 }
 

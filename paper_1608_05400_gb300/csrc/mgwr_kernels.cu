@@ -25,7 +25,8 @@ long long launch_counter() { return g_launches.load(); }
 void add_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 // Line-wise kernels: a group of TPL threads owns one time line (TPL =
-// min(64, M/W), 256 / TPL lines per 256-thread block); each thread moves W =
+// min(64, M/W), 256 for lines of more than 1024 vectors; 256 / TPL lines per
+// 256-thread block); each thread moves W =
 // 16 / sizeof(R) consecutive time values per step with 16-byte accesses (every
 // line starts on a 16-byte boundary: M is a power of two >= 4 and the fields
 // are allocated 256-byte aligned).  Index arithmetic is done once per line.
@@ -642,7 +643,10 @@ __global__ void k_round_cx(Cx<float>* __restrict__ dst, const Cx<double>* __rest
 template <class R>
 inline void line_grid(int M, int lines, int* log_tpl, unsigned* blocks) {
   const int per = M / Vec<R>::W;
-  const int tpl = per < 64 ? per : 64;
+  // 64 threads per line up to 1024 vectors (measured best at M = 256 .. 4096);
+  // the partitioned long lines take 256 (1-D 4095 x 65536 double-float solve:
+  // 564 -> 527 ms; at M = 1024 the wider groups lost 2-3 %)
+  const int tpl = per <= 1024 ? (per < 64 ? per : 64) : 256;
   *log_tpl = ilog2(tpl);
   const int lpb = kLineBlock / tpl;
   *blocks = (unsigned)((lines + lpb - 1) / lpb);

@@ -101,6 +101,9 @@ def parse():
     p.add_argument("--inner", type=int, default=None, help="mixed modes: FP32 cycles per outer defect")
     p.add_argument("--alpha", type=float, default=None)
     p.add_argument("--no-autotune", action="store_true", help="keep the default engine launch shapes")
+    p.add_argument("--split", default=None,
+                   help="CLASS=E[,CLASS=E]: engine launch shape of a kernel class on every level, "
+                        "set after the tuner (e.g. sweep32=33: the tensor-core sweep; profiling)")
     p.add_argument("--shape", default=None,
                    help="d,n,M replacing the workload's grid (small cases for profiling)")
     p.add_argument("--batch", type=int, default=None, help="instances replacing the workload's batch")
@@ -482,6 +485,11 @@ def main():
     # launch shapes of the FFT-engine kernels, timed on this handle's data (setup,
     # outside the timed region)
     splits = None if args.no_autotune else s.autotune()
+    if args.split:
+        for item in args.split.split(","):
+            name, val = item.split("=")
+            s.set_engine_split(mgwr.KERNEL_CLASSES.index(name), int(val))
+        splits = dict(splits or {}, forced=args.split)
 
     def step():
         s.set_rhs_dev(f_dev.data_ptr())

@@ -12,18 +12,21 @@
 // is 6 M^2 multiply-adds against the FFT engine's ~10 M log2(2M) operations on
 // the SIMT pipes, which the tensor cores more than repay up to M = 256.
 //
-// Per CTA (512 threads): the band of Kt for the first 32 time steps (row t,
+// Per CTA (17 warps): the band of Kt for the first 32 time steps (row t,
 // column k: k_{t-k}), built once per instance and level at setup in the
 // K-major no-swizzle layout (8 x 16-byte core matrices), arrives in shared
-// memory by one bulk copy (cp.async.bulk on an mbarrier); because Kt is Toeplitz, the band of
-// steps 32c .. 32c+31 is the same band shifted down by 32c rows, so chunk c
-// multiplies into accumulator columns 32c .. M-1 only (N = M - 32c: the
-// triangle above the diagonal is never computed).  The 128 lines' b values are
-// gathered chunk by chunk into two alternating buffers, split and written in
-// the same layout; one thread issues the chunk's twelve MMAs and commits them
-// to the buffer's mbarrier, and the next chunk is gathered while they run.
-// Every wait is bounded.  The epilogue reads the accumulator with tcgen05.ld
-// and writes u (and the change record).
+// memory by one bulk copy (cp.async.bulk on an mbarrier); because Kt is
+// Toeplitz, the band of steps 32c .. 32c+31 is the same band shifted down by
+// 32c rows, so chunk c multiplies into accumulator columns 32c .. M-1 only
+// (N = M - 32c: the triangle above the diagonal is never computed).  Two
+// producer groups of 8 warps gather the 128 lines' b values of alternate
+// chunks, split them and write them into their own buffer in the same layout,
+// then arrive on the buffer's "full" mbarrier; one warp waits for each chunk,
+// issues its twelve MMAs and commits them to the buffer's "empty" mbarrier,
+// which the group waits for before refilling.  No CTA-wide barrier separates
+// the chunks, so one group's memory latency overlaps the other's work.  Every
+// wait is bounded.  The epilogue reads the accumulator with tcgen05.ld and
+// writes u (and the change record).
 #include <cuda_bf16.h>
 
 #include "mgwr_common.cuh"
@@ -38,7 +41,11 @@ namespace {
 
 constexpr int kTileRows = 128;  // lines per CTA: the MMA's M
 constexpr int kChunk = 32;      // time steps per shared-memory chunk (two K = 16 steps)
-constexpr int kThreads = 512;
+// 16 producer warps in two groups of 8 (alternate chunks), one MMA-issuing warp
+constexpr int kGroupThreads = 256;
+constexpr int kIssuerWarp = 2 * kGroupThreads / 32;
+constexpr int kIssuer = kIssuerWarp * 32;
+constexpr int kThreads = kIssuer + 32;
 
 // Byte offset of element (r, k) in a K-major tile of kChunk columns: core
 // matrices of 8 rows x 16 bytes; the kChunk / 8 core matrices of a row group
@@ -106,7 +113,7 @@ __constant__ int kPieceB[6] = {0, 1, 0, 2, 1, 0};
 }  // namespace
 
 template <int M>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, 2)
     k_sweep_tc(const float* __restrict__ f, float* __restrict__ u, float* __restrict__ delta,
                const unsigned char* __restrict__ band, int d, int n, int par, float hinv2,
                int npts, int tiles_per_inst, size_t fstride, size_t bstride) {
@@ -114,7 +121,14 @@ __global__ void __launch_bounds__(kThreads, 1)
   constexpr int kB = M * kChunk * 2;          // bytes per piece of the Kt band
   constexpr int kNumChunks = M / kChunk;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t bars[3];  // two operand buffers, the band
+  // full[b]: producer group b has written a chunk into buffer b (one arrival per
+  // thread of the group); empty[b]: the MMAs reading buffer b have completed
+  // (commit); done: every MMA has completed (commit); band: the band has arrived
+  __shared__ __align__(8) uint64_t bars[6];
+  uint64_t* const full = bars;
+  uint64_t* const empty = bars + 2;
+  uint64_t* const done = bars + 4;
+  uint64_t* const band_bar = bars + 5;
   __shared__ unsigned tmem_slot;
   __shared__ int rowp[kTileRows];
   __shared__ unsigned rowm[kTileRows];
@@ -127,6 +141,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   u += (size_t)inst * fstride;
   if (delta != nullptr) delta += (size_t)inst * fstride;
   band += (size_t)inst * bstride;
+  const int warp = threadIdx.x >> 5;
 
   // rows of the tile: the colour's points rt*128 .. rt*128+127 and their neighbours
   if (threadIdx.x < kTileRows) {
@@ -142,16 +157,19 @@ __global__ void __launch_bounds__(kThreads, 1)
     rowp[threadIdx.x] = p;
     rowm[threadIdx.x] = m;
   }
-  if (threadIdx.x == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
-    mbar_init(&bars[2], 1);
+  if (threadIdx.x == kIssuer) {
+    mbar_init(&full[0], kGroupThreads);
+    mbar_init(&full[1], kGroupThreads);
+    mbar_init(&empty[0], 1);
+    mbar_init(&empty[1], 1);
+    mbar_init(done, 1);
+    mbar_init(band_bar, 1);
     mbar_fence_init();
     // the three pieces of the band: 3 * kB contiguous bytes (16-byte multiples)
-    mbar_arrive_expect_tx(&bars[2], 3u * kB);
-    bulk_copy_g2s(sB, band, 3u * kB, &bars[2]);
+    mbar_arrive_expect_tx(band_bar, 3u * kB);
+    bulk_copy_g2s(sB, band, 3u * kB, band_bar);
   }
-  if (threadIdx.x < 32) {
+  if (warp == kIssuerWarp) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&tmem_slot)),
                  "r"(M)
@@ -164,127 +182,123 @@ __global__ void __launch_bounds__(kThreads, 1)
   const unsigned tmem = tmem_slot;
   const size_t nM = (size_t)n * M;
   bool ok = true;
-  int issued = -1;  // last chunk whose MMAs were issued (the same in every thread)
 
-  for (int ch = 0; ch < kNumChunks; ++ch) {
-    const int buf = ch & 1;
-    unsigned char* sAb = sA + buf * 3 * kA;
-    if (ch >= 2) {
-      // the MMAs of chunk ch - 2 have read this buffer
-      const int failed = mbar_wait_bounded(&bars[buf], (unsigned)(((ch - 2) >> 1) & 1)) ? 0 : 1;
-      if (__syncthreads_or(failed)) {
-        ok = false;
-        if (threadIdx.x == 0) atomicOr(&g_tc_timeout, 1u);
-        break;
-      }
-    }
-    // b values of the chunk: 128 rows x 4 core columns of 8 steps, one per thread
-    {
-      const int item = threadIdx.x;
-      const int r = item >> 2, kc = item & 3;
-      const int m0 = ch * kChunk + kc * 8;
-      const unsigned msk = rowm[r];
-      float b[8];
+  if (warp == kIssuerWarp) {
+    // one thread issues every chunk's MMAs as soon as its buffer is full
+    if (threadIdx.x == kIssuer) {
+      int issued = -1;
+      ok = mbar_wait_bounded(band_bar, 0u);
+      for (int ch = 0; ok && ch < kNumChunks; ++ch) {
+        const int b = ch & 1;
+        if (!mbar_wait_bounded(&full[b], (unsigned)((ch >> 1) & 1))) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        // chunk ch reaches output steps 32 ch .. M-1: N = M - 32 ch columns from 32 ch
+        const uint32_t idesc = mma_idesc(M - ch * kChunk);
+        const unsigned dcol = tmem + (unsigned)(ch * kChunk);
+        unsigned char* sAb = sA + b * 3 * kA;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) b[q] = 0.f;
-      if (msk & 16u) {
-        const size_t pM = (size_t)rowp[r] * M + m0;
-        // 8 steps of a line, 0 for a neighbour outside the grid
-        auto line8 = [&](const float* src, bool present, float (&o)[8]) {
-          if (present) {
-            const float4 x = *reinterpret_cast<const float4*>(src);
-            const float4 y = *reinterpret_cast<const float4*>(src + 4);
-            o[0] = x.x; o[1] = x.y; o[2] = x.z; o[3] = x.w;
-            o[4] = y.x; o[5] = y.y; o[6] = y.z; o[7] = y.w;
-          } else {
+        for (int s = 0; s < kChunk / 16; ++s) {
 #pragma unroll
-            for (int q = 0; q < 8; ++q) o[q] = 0.f;
+          for (int c = 0; c < 6; ++c) {
+            const uint64_t da = smem_desc(smem_u32(sAb + kPieceA[c] * kA) + s * 256);
+            const uint64_t db = smem_desc(smem_u32(sB + kPieceB[c] * kB) + s * 256);
+            mma_bf16(dcol, da, db, idesc, (ch > 0 || s > 0 || c > 0) ? 1u : 0u);
           }
-        };
-        // the neighbour sum in the FFT sweep's order: (west + east) + (south + north)
-        float fv[8], a[8], c[8], s2[8];
-        line8(u + pM - M, (msk & 1u) != 0, a);
-        line8(u + pM + M, (msk & 2u) != 0, c);
-#pragma unroll
-        for (int q = 0; q < 8; ++q) s2[q] = a[q] + c[q];
-        if (d == 2) {
-          line8(u + pM - nM, (msk & 4u) != 0, a);
-          line8(u + pM + nM, (msk & 8u) != 0, c);
-#pragma unroll
-          for (int q = 0; q < 8; ++q) s2[q] = s2[q] + (a[q] + c[q]);
         }
-        line8(f + pM, true, fv);
-#pragma unroll
-        for (int q = 0; q < 8; ++q) b[q] = fv[q] + hinv2 * s2[q];
+        mma_commit(&empty[b]);
+        issued = ch;
       }
-      __nv_bfloat16 p0[8], p1[8], p2[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) split3(b[q], p0[q], p1[q], p2[q]);
-      const int off = core_off(r, kc);
-      *reinterpret_cast<uint4*>(sAb + off) =
-          make_uint4(pack2(p0[0], p0[1]), pack2(p0[2], p0[3]), pack2(p0[4], p0[5]), pack2(p0[6], p0[7]));
-      *reinterpret_cast<uint4*>(sAb + kA + off) =
-          make_uint4(pack2(p1[0], p1[1]), pack2(p1[2], p1[3]), pack2(p1[4], p1[5]), pack2(p1[6], p1[7]));
-      *reinterpret_cast<uint4*>(sAb + 2 * kA + off) =
-          make_uint4(pack2(p2[0], p2[1]), pack2(p2[2], p2[3]), pack2(p2[4], p2[5]), pack2(p2[6], p2[7]));
+      if (ok) {
+        mma_commit(done);
+      } else {
+        atomicOr(&g_tc_timeout, 1u);
+        // what was issued finishes before the accumulator is released
+        if (issued >= 0) (void)mbar_wait_bounded(&empty[issued & 1], (unsigned)((issued >> 1) & 1));
+      }
     }
-    fence_proxy_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    if (ch == 0) {
-      // the MMA issuer needs the band (the copy and the MMAs are both asynchronous)
-      const int failed = threadIdx.x == 0 && !mbar_wait_bounded(&bars[2], 0u) ? 1 : 0;
-      if (__syncthreads_or(failed)) {
+    __syncwarp();
+  } else {
+    // producer group g (warps 8g .. 8g+7) fills buffer g with chunks g, g + 2, ...
+    const int g = warp >> 3;
+    const int gt = threadIdx.x - g * kGroupThreads;
+    unsigned char* sAb = sA + g * 3 * kA;
+    for (int ch = g, k = 0; ch < kNumChunks; ch += 2, ++k) {
+      // the MMAs of this buffer's previous chunk have read it
+      if (k >= 1 && !mbar_wait_bounded(&empty[g], (unsigned)((k - 1) & 1))) {
         ok = false;
-        if (threadIdx.x == 0) {
-          atomicOr(&g_tc_timeout, 1u);
-          (void)mbar_wait_bounded(&bars[2], 0u);
-        }
         break;
       }
-    }
-    if (threadIdx.x == 0) {
-      // chunk ch reaches output steps 32 ch .. M-1: N = M - 32 ch columns from 32 ch
-      const uint32_t idesc = mma_idesc(M - ch * kChunk);
-      const unsigned dcol = tmem + (unsigned)(ch * kChunk);
 #pragma unroll
-      for (int s = 0; s < kChunk / 16; ++s) {
+      for (int s = 0; s < 2; ++s) {
+        const int item = gt + s * kGroupThreads;
+        const int r = item >> 2, kc = item & 3;
+        const int m0 = ch * kChunk + kc * 8;
+        const unsigned msk = rowm[r];
+        float b[8];
 #pragma unroll
-        for (int c = 0; c < 6; ++c) {
-          const uint64_t da = smem_desc(smem_u32(sAb + kPieceA[c] * kA) + s * 256);
-          const uint64_t db = smem_desc(smem_u32(sB + kPieceB[c] * kB) + s * 256);
-          mma_bf16(dcol, da, db, idesc, (ch > 0 || s > 0 || c > 0) ? 1u : 0u);
+        for (int q = 0; q < 8; ++q) b[q] = 0.f;
+        if (msk & 16u) {
+          const size_t pM = (size_t)rowp[r] * M + m0;
+          // 8 steps of a line, 0 for a neighbour outside the grid
+          auto line8 = [&](const float* src, bool present, float (&o)[8]) {
+            if (present) {
+              const float4 x = __ldg(reinterpret_cast<const float4*>(src));  // read-only in this kernel
+              const float4 y = __ldg(reinterpret_cast<const float4*>(src + 4));
+              o[0] = x.x; o[1] = x.y; o[2] = x.z; o[3] = x.w;
+              o[4] = y.x; o[5] = y.y; o[6] = y.z; o[7] = y.w;
+            } else {
+#pragma unroll
+              for (int q = 0; q < 8; ++q) o[q] = 0.f;
+            }
+          };
+          // the neighbour sum in the FFT sweep's order: (west + east) + (south + north)
+          float fv[8], a[8], c[8], s2[8];
+          line8(u + pM - M, (msk & 1u) != 0, a);
+          line8(u + pM + M, (msk & 2u) != 0, c);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) s2[q] = a[q] + c[q];
+          if (d == 2) {
+            line8(u + pM - nM, (msk & 4u) != 0, a);
+            line8(u + pM + nM, (msk & 8u) != 0, c);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) s2[q] = s2[q] + (a[q] + c[q]);
+          }
+          line8(f + pM, true, fv);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) b[q] = fv[q] + hinv2 * s2[q];
         }
+        __nv_bfloat16 p0[8], p1[8], p2[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) split3(b[q], p0[q], p1[q], p2[q]);
+        const int off = core_off(r, kc);
+        *reinterpret_cast<uint4*>(sAb + off) =
+            make_uint4(pack2(p0[0], p0[1]), pack2(p0[2], p0[3]), pack2(p0[4], p0[5]), pack2(p0[6], p0[7]));
+        *reinterpret_cast<uint4*>(sAb + kA + off) =
+            make_uint4(pack2(p1[0], p1[1]), pack2(p1[2], p1[3]), pack2(p1[4], p1[5]), pack2(p1[6], p1[7]));
+        *reinterpret_cast<uint4*>(sAb + 2 * kA + off) =
+            make_uint4(pack2(p2[0], p2[1]), pack2(p2[2], p2[3]), pack2(p2[4], p2[5]), pack2(p2[6], p2[7]));
       }
-      mma_commit(&bars[buf]);
+      fence_proxy_async_smem();  // these stores before the MMAs' reads
+      mbar_arrive(&full[g]);
     }
-    issued = ch;
+    // the accumulator is complete once every MMA has
+    if (ok && !mbar_wait_bounded(done, 0u)) ok = false;
+    if (!ok && gt == 0) atomicOr(&g_tc_timeout, 1u);
   }
-  if (ok) {
-    // the last commit covers every MMA issued before it
-    const int last = kNumChunks - 1;
-    const int failed =
-        mbar_wait_bounded(&bars[last & 1], (unsigned)((last >> 1) & 1)) ? 0 : 1;
-    if (__syncthreads_or(failed)) {
-      ok = false;
-      if (threadIdx.x == 0) atomicOr(&g_tc_timeout, 1u);
-    }
-  }
-  if (!ok && issued >= 0 && threadIdx.x == 0) {
-    // let what was issued finish (its last commit covers all of it) before the
-    // accumulator is released
-    (void)mbar_wait_bounded(&bars[issued & 1], (unsigned)((issued >> 1) & 1));
-  }
+  // every thread agrees on the outcome before the accumulator is read
+  ok = __syncthreads_and(ok ? 1 : 0) != 0;
   tc_fence_after();
 
-  // epilogue: warp w reads lanes 32 (w % 4) .. +31 (its rows), columns of quarter w / 4
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int r = 32 * (w & 3) + lane;
-  const unsigned msk = rowm[r];
-  float* ur = u + (size_t)rowp[r] * M;
-  float* dr = delta != nullptr ? delta + (size_t)rowp[r] * M : nullptr;
-  if (ok) {
+  // epilogue: warp w < 16 reads lanes 32 (w % 4) .. +31 (its rows), columns of quarter w / 4
+  if (ok && warp < 2 * kGroupThreads / 32) {
+    const int w = warp, lane = threadIdx.x & 31;
+    const int r = 32 * (w & 3) + lane;
+    const unsigned msk = rowm[r];
+    float* ur = u + (size_t)rowp[r] * M;
+    float* dr = delta != nullptr ? delta + (size_t)rowp[r] * M : nullptr;
 #pragma unroll 1
     for (int c = (w >> 2) * (M / 4); c < (w >> 2) * (M / 4) + M / 4; c += 8) {
       unsigned v[8];
@@ -315,7 +329,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   tc_fence_before();
   __syncthreads();
-  if (threadIdx.x < 32)
+  if (warp == kIssuerWarp)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(M)
                  : "memory");
 }

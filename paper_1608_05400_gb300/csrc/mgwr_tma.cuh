@@ -36,6 +36,11 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned by
                : "memory");
 }
 
+// One plain arrival on `bar`.
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // dst (shared) <- src (global), `bytes` a multiple of 16, both addresses
 // 16-byte aligned; completion is counted on `bar`.
 __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes,

@@ -316,8 +316,10 @@ def run_reference(args):
     v = statistics.median(x["value"] for x in vals)
     out = dict(base, value=v, ms_per_step=1e3 * dt / args.steps, scaling="weak", vs_baseline=None,
                dtype="f64", data="synthetic",
-               config={"workload": f"2-D MGWR {NPTS}x{NPTS}, M={M}, alpha={ALPHA}, V(1,1), rel-res {TOL}",
-                       "parallelism": "replicas"},
+               config={"workload": f"{WORKLOADS['2d-255-m1024'][7]}, alpha={ALPHA}, "
+                                   f"V({NU1},{NU2}) red-black, rel-res {TOL}",
+                       "name": "2d-255-m1024", "precision": "fp64",
+                       "parallelism": "replicas" if args.gpus > 1 else "single"},
                cpu_baseline=dict(vals[0], value=v),
                e2e={"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0})
     print(json.dumps(out))

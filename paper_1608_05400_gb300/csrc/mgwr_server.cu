@@ -13,7 +13,9 @@
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
+#include <cstdlib>
 #include <deque>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <new>
@@ -27,16 +29,111 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+// Pinned (page-locked) host buffers for the requests' right-hand sides and
+// results: they move between host and device at the copy engines' rate (about
+// 200 GB/s each way on GB300) instead of through the driver's staging of
+// pageable memory (about 25 GB/s).  Pinning pages is slow, so released buffers
+// are kept, up to kKeep bytes, and handed out again to requests that fit.
+class PinnedPool {
+ public:
+  static constexpr size_t kKeep = size_t(32) << 30;
+  ~PinnedPool() {
+    for (auto& kv : free_) cudaFreeHost(kv.second);
+  }
+  // A buffer of at least `count` doubles (its capacity in *cap), or nullptr
+  // when no page-locked memory can be had.
+  double* get(size_t count, size_t* cap) {
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      auto it = free_.lower_bound(count);
+      if (it != free_.end() && it->first <= 2 * count + (size_t(1) << 20)) {
+        double* p = it->second;
+        *cap = it->first;
+        kept_ -= it->first * sizeof(double);
+        free_.erase(it);
+        return p;
+      }
+    }
+    void* p = nullptr;
+    if (cudaMallocHost(&p, count * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    *cap = count;
+    return static_cast<double*>(p);
+  }
+  void put(double* p, size_t cap) {
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      if (kept_ + cap * sizeof(double) <= kKeep) {
+        kept_ += cap * sizeof(double);
+        free_.emplace(cap, p);
+        return;
+      }
+    }
+    cudaFreeHost(p);
+  }
+
+ private:
+  std::mutex mu_;
+  std::multimap<size_t, double*> free_;
+  size_t kept_ = 0;
+};
+
+// `count` doubles of host memory: pinned from the pool when it has some, else
+// ordinary (pageable) memory.
+class HostBuf {
+ public:
+  HostBuf() = default;
+  HostBuf(const HostBuf&) = delete;
+  HostBuf& operator=(const HostBuf&) = delete;
+  ~HostBuf() { release(); }
+  bool alloc(PinnedPool* pool, size_t count) {
+    release();
+    size_t cap = 0;
+    p_ = pool->get(count, &cap);
+    if (p_ != nullptr) {
+      pool_ = pool;
+      cap_ = cap;
+    } else {
+      p_ = static_cast<double*>(std::malloc(count * sizeof(double)));
+      if (p_ == nullptr) return false;
+    }
+    n_ = count;
+    return true;
+  }
+  double* data() const { return p_; }
+  size_t size() const { return n_; }
+  bool empty() const { return n_ == 0; }
+
+ private:
+  void release() {
+    if (p_ == nullptr) return;
+    if (pool_ != nullptr)
+      pool_->put(p_, cap_);
+    else
+      std::free(p_);
+    p_ = nullptr;
+    pool_ = nullptr;
+    n_ = cap_ = 0;
+  }
+  double* p_ = nullptr;
+  PinnedPool* pool_ = nullptr;
+  size_t n_ = 0, cap_ = 0;
+};
+
 struct Ticket {
   uint64_t id = 0;
   mgwr_request rq{};
-  std::vector<double> f, g, u;
+  HostBuf f, u;
+  std::vector<double> g;
   size_t footprint = 0;
   size_t N = 0;
   int state = 0;  // 0 queued, 1 running, 2 done
   int skipped = 0;
   Clock::time_point t_submit, t_admit, t_done;
   mgwr_result res{};
+  PinnedPool* pool = nullptr;  // where the result buffer comes from
 };
 
 bool pow2(long long x) { return x > 0 && (x & (x - 1)) == 0; }
@@ -44,6 +141,7 @@ bool pow2(long long x) { return x > 0 && (x & (x - 1)) == 0; }
 }  // namespace
 
 struct mgwr_server {
+  PinnedPool pool;  // declared first: outlives the tickets that hold its buffers
   size_t budget = 0, in_use = 0, peak = 0;
   int slots = 1, max_queue = 1 << 20, device = 0;
   int policy = MGWR_POLICY_FIFO;
@@ -103,8 +201,8 @@ int run_request(Ticket* t) {
     st = mgwr_solve(h, q.cycle, q.nu1, q.nu2, q.tol, q.max_cycles, &stats);
     t->res.stats = stats;
     if (st == MGWR_OK || st == MGWR_E_NOCONV) {
-      t->u.resize(t->N * q.M);
-      const int st2 = mgwr_get_solution(h, t->u.data());
+      const int st2 = t->u.alloc(t->pool, t->N * q.M) ? mgwr_get_solution(h, t->u.data())
+                                                      : MGWR_E_NOMEM;
       if (st2 != MGWR_OK) st = st2;
     }
   }
@@ -218,7 +316,9 @@ int mgwr_submit(mgwr_server_t s, const mgwr_request* rq, uint64_t* ticket) {
   t->rq = *rq;
   t->N = rq->d == 1 ? (size_t)rq->n : (size_t)rq->n * rq->n;
   try {
-    t->f.assign(rq->f, rq->f + t->N * rq->M);
+    if (!t->f.alloc(&s->pool, t->N * rq->M)) return MGWR_E_NOMEM;
+    std::memcpy(t->f.data(), rq->f, t->N * rq->M * sizeof(double));
+    t->pool = &s->pool;
     if (rq->g != nullptr) t->g.assign(rq->g, rq->g + t->N);
   } catch (const std::bad_alloc&) {
     return MGWR_E_NOMEM;

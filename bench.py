@@ -150,6 +150,45 @@ def peaks():
         return {}
 
 
+def gpu_local_cpus(index: int):
+    """The CPUs of the NUMA node the GPU is attached to (from its PCI device in
+    sysfs), or None when that cannot be read."""
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", str(index), "--query-gpu=pci.bus_id",
+                              "--format=csv,noheader"], capture_output=True, text=True,
+                             timeout=30).stdout.strip()
+        dom, rest = out.split(":", 1)
+        path = f"/sys/bus/pci/devices/{dom[-4:].lower()}:{rest.lower()}/local_cpulist"
+        cpus = set()
+        with open(path) as fh:
+            for part in fh.read().strip().split(","):
+                lo, _, hi = part.partition("-")
+                cpus.update(range(int(lo), int(hi or lo) + 1))
+        return cpus & set(os.sched_getaffinity(0)) or None
+    except (OSError, ValueError, subprocess.SubprocessError):
+        return None
+
+
+class GpuLocalHost:
+    """Runs a block on the GPU's local CPUs, so that host buffers first touched
+    there (pinned copies of the inputs and outputs) sit in the memory next to the
+    GPU; restores the process's affinity afterwards (a setting of this process)."""
+
+    def __init__(self, index: int):
+        self.cpus = gpu_local_cpus(index)
+        self.saved = None
+
+    def __enter__(self):
+        if self.cpus:
+            self.saved = os.sched_getaffinity(0)
+            os.sched_setaffinity(0, self.cpus)
+        return self
+
+    def __exit__(self, *exc):
+        if self.saved is not None:
+            os.sched_setaffinity(0, self.saved)
+
+
 class ClockSampler:
     """nvidia-smi samples (200 ms) during the timed region."""
 
@@ -405,12 +444,15 @@ def run_served(args):
         return makespan, lat, results, info
 
     total = sum(unknowns(r) for r in reqs)
-    span1, _, res1, _ = run([0.0] * len(reqs))
-    rate = len(reqs) / span1
-    offered = args.rate if args.rate else 0.7 * rate
-    rng = np.random.default_rng(1608)
-    arr = np.cumsum(rng.exponential(1.0 / offered, size=len(reqs)))
-    span2, lat, res2, info = run(list(arr))
+    # the server's pinned buffers are first touched by these threads: keep them on
+    # the GPU-local CPUs so that the buffers sit next to the GPU
+    with GpuLocalHost(0) as host:
+        span1, _, res1, _ = run([0.0] * len(reqs))
+        rate = len(reqs) / span1
+        offered = args.rate if args.rate else 0.7 * rate
+        rng = np.random.default_rng(1608)
+        arr = np.cumsum(rng.exponential(1.0 / offered, size=len(reqs)))
+        span2, lat, res2, info = run(list(arr))
     ok = sum(1 for r in res2 if r.status == mgwr.MGWR_OK)
     lat_ms = np.array(lat) * 1e3
     out = {
@@ -424,6 +466,8 @@ def run_served(args):
                                "alpha~U[0.1,0.9], u=t^2 or t^alpha sin, Poisson arrivals at 0.7x "
                                "the sustained rate", "name": "served", "slots": args.slots,
                    "admission": args.policy,
+                   "host_buffers": (f"pinned, on the {len(host.cpus)} GPU-local CPUs"
+                                    if host.cpus else "pinned"),
                    "hbm_budget_bytes": budget, "host_window_bytes": host_cap},
         "served": {"p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
                    "sustained_requests_per_s": rate, "offered_requests_per_s": offered,
@@ -527,32 +571,35 @@ def main():
 
     e2e = None
     if not args.no_e2e and f_host is not None:
-        pin_f = torch.from_numpy(f_host).pin_memory()
-        pin_u = torch.empty_like(pin_f).pin_memory()
-        fp = pin_f.numpy()
-        up = pin_u.numpy()
-        ee0, ee1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with GpuLocalHost(local) as host:
+            pin_f = torch.from_numpy(f_host).pin_memory()
+            pin_u = torch.empty_like(pin_f).pin_memory()
+            fp = pin_f.numpy()
+            up = pin_u.numpy()
+            ee0, ee1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
-        def e2e_step():
-            s.set_rhs(fp)
-            s.solve(CYCLE, NU1, NU2, tol, 100)
-            s.lib.mgwr_get_solution(s.h, up.ctypes.data_as(mgwr._dp))
+            def e2e_step():
+                s.set_rhs(fp)
+                s.solve(CYCLE, NU1, NU2, tol, 100)
+                s.lib.mgwr_get_solution(s.h, up.ctypes.data_as(mgwr._dp))
 
-        # untimed warm-up through the same path: the profiled solve above ran without
-        # graphs, so the first steps after it capture them again
-        for _ in range(max(args.warmup, 1)):
-            e2e_step()
-        barrier()
-        torch.cuda.synchronize()
-        ee0.record(stream)
-        for _ in range(args.steps):
-            e2e_step()
-        ee1.record(stream)
-        torch.cuda.synchronize()
-        ems = max_over_ranks(ee0.elapsed_time(ee1), world, "cuda")
-        nbytes = unknowns * 8
-        e2e = {"value": job_throughput(world, unknowns, args.steps, ems), "unit": UNIT,
-               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+            # untimed warm-up through the same path: the profiled solve above ran without
+            # graphs, so the first steps after it capture them again
+            for _ in range(max(args.warmup, 1)):
+                e2e_step()
+            barrier()
+            torch.cuda.synchronize()
+            ee0.record(stream)
+            for _ in range(args.steps):
+                e2e_step()
+            ee1.record(stream)
+            torch.cuda.synchronize()
+            ems = max_over_ranks(ee0.elapsed_time(ee1), world, "cuda")
+            nbytes = unknowns * 8
+            e2e = {"value": job_throughput(world, unknowns, args.steps, ems), "unit": UNIT,
+                   "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+                   "host_buffers": (f"pinned, first touched on the {len(host.cpus)} GPU-local CPUs"
+                                    if host.cpus else "pinned")}
     s.close()
     if rank != 0:
         if world > 1:

@@ -122,8 +122,12 @@ typedef struct {
  * time-line convolution is partitioned into blocks of 4096 steps (transforms
  * of length 8192; the spectra are those of the 2M/8192 kernel segments), and
  * the handle also holds a scratch area of 16 bytes x ceil(n^d/2) x 2M per
- * instance for the block spectra (mgwr_footprint counts it).  Returns
- * MGWR_E_INVAL for bad arguments, MGWR_E_NOMEM if device memory runs out. */
+ * instance for the block spectra (mgwr_footprint counts it).  Device memory
+ * comes stream-ordered from the device's default memory pool, whose release
+ * threshold the first handle on a device raises to its maximum: memory that
+ * handles free stays reserved by this process for the next handles (a setting
+ * of this process's pool, not of the GPU).  Returns MGWR_E_INVAL for bad
+ * arguments, MGWR_E_NOMEM if device memory runs out. */
 int mgwr_create(int d, int n, int M, double T, double alpha, mgwr_t* out);
 /* A batch of `batch` (1..65535) independent problems of the same (d, n, M),
  * instance b with final time T[b] and order alpha[b] (host arrays).  Every

@@ -343,7 +343,10 @@ int mgwr_server_destroy(mgwr_server_t s);
 int mgwr_server_set_policy(mgwr_server_t s, int policy);
 /* Copies the request's data and queues it: MGWR_OK with *ticket set,
  * MGWR_E_INVAL (bad request), MGWR_E_TOOBIG (footprint above the budget),
- * MGWR_E_AGAIN (queue full). */
+ * MGWR_E_AGAIN (queue full), MGWR_E_NOMEM (no host memory for the copy).
+ * The copy of f, and later the result, are held in page-locked host memory
+ * from a pool the server keeps (up to 32 GiB of released buffers are reused;
+ * pageable memory when no page-locked memory can be had). */
 int mgwr_submit(mgwr_server_t s, const mgwr_request* rq, uint64_t* ticket);
 /* Waits up to timeout_us (0: no wait) for the ticket.  MGWR_E_AGAIN (not
  * ready, timeout 0) or MGWR_E_TIMEOUT (not ready after the wait); MGWR_OK:

@@ -150,6 +150,25 @@ def peaks():
         return {}
 
 
+def parse_cpulist(text: str) -> set:
+    """CPUs of a sysfs cpulist such as "0-15,32,40-41"."""
+    cpus = set()
+    for part in text.strip().split(","):
+        if part:
+            lo, _, hi = part.partition("-")
+            cpus.update(range(int(lo), int(hi or lo) + 1))
+    return cpus
+
+
+def parse_splits(text: str, classes) -> dict:
+    """{class index: split} from "CLASS=E[,CLASS=E]" (names from `classes`)."""
+    out = {}
+    for item in text.split(","):
+        name, val = item.split("=")
+        out[list(classes).index(name.strip())] = int(val)
+    return out
+
+
 def gpu_local_cpus(index: int):
     """The CPUs of the NUMA node the GPU is attached to (from its PCI device in
     sysfs), or None when that cannot be read."""
@@ -159,11 +178,8 @@ def gpu_local_cpus(index: int):
                              timeout=30).stdout.strip()
         dom, rest = out.split(":", 1)
         path = f"/sys/bus/pci/devices/{dom[-4:].lower()}:{rest.lower()}/local_cpulist"
-        cpus = set()
         with open(path) as fh:
-            for part in fh.read().strip().split(","):
-                lo, _, hi = part.partition("-")
-                cpus.update(range(int(lo), int(hi or lo) + 1))
+            cpus = parse_cpulist(fh.read())
         return cpus & set(os.sched_getaffinity(0)) or None
     except (OSError, ValueError, subprocess.SubprocessError):
         return None
@@ -532,9 +548,8 @@ def main():
     # outside the timed region)
     splits = None if args.no_autotune else s.autotune()
     if args.split:
-        for item in args.split.split(","):
-            name, val = item.split("=")
-            s.set_engine_split(mgwr.KERNEL_CLASSES.index(name), int(val))
+        for cls, val in parse_splits(args.split, mgwr.KERNEL_CLASSES).items():
+            s.set_engine_split(cls, val)
         splits = dict(splits or {}, forced=args.split)
 
     def step():

@@ -1,4 +1,4 @@
-"""The multi-rank path of bench.py on CPU: two gloo ranks (world size 2) run
+"""The multi-rank path of bench.py on CPU, and its host-side helpers: two gloo ranks (world size 2) run
 the barrier, the max-over-ranks timing and the whole-job throughput the GPU
 bench uses under torchrun, and ranks other than 0 of the reference arm exit
 without work.  No GPU: the ranks are host processes."""
@@ -65,3 +65,20 @@ def test_reference_arm_ranks_other_than_zero_exit_without_work():
                           "--gpus", "2", "--steps", "1", "--warmup", "3"],
                          capture_output=True, text=True, timeout=120, env=env)
     assert res.returncode == 0 and res.stdout.strip() == ""
+
+
+def test_bench_helpers_parse_cpu_lists_and_splits():
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1608_05400_gb300 import mgwr
+    assert bench.parse_cpulist("0-3,8,10-11\n") == {0, 1, 2, 3, 8, 10, 11}
+    assert bench.parse_cpulist("5") == {5}
+    got = bench.parse_splits("sweep32=33,defect64=2", mgwr.KERNEL_CLASSES)
+    assert got == {mgwr.KERNEL_CLASSES.index("sweep32"): 33, mgwr.KERNEL_CLASSES.index("defect64"): 2}
+    with pytest.raises(ValueError):
+        bench.parse_splits("nosuchclass=1", mgwr.KERNEL_CLASSES)
+    # no GPU here: the placement helper finds nothing and changes nothing
+    before = os.sched_getaffinity(0)
+    with bench.GpuLocalHost(0) as host:
+        pass
+    assert os.sched_getaffinity(0) == before

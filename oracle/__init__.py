@@ -18,6 +18,9 @@ Modules
              defect, full weighting, linear / bilinear interpolation, V/W cycles
   mittag_leffler  E_alpha(z) by its power series: the exact solution of the
              Sec. 7 experiment with initial value sin x
+  sama       semi-algebraic mode analysis of the 1-D two-grid cycle (Sec. 4):
+             predicted smoothing and two-grid factors; a CPU tool as well
+             (python -m oracle.sama)
 
 Pin status: every function above is pinned by a CPU test against something
 other than itself (closed forms, a dense solve, brute force, special cases);

@@ -18,6 +18,9 @@ Modules
              defect, full weighting, linear / bilinear interpolation, V/W cycles
   mittag_leffler  E_alpha(z) by its power series: the exact solution of the
              Sec. 7 experiment with initial value sin x
+  fas        waveform relaxation FAS for the 1-D nonlinear problem of Sec. 7
+             (conservative flux, upwind convection) and a time-marching Newton
+             solver of the same discrete problem
   sama       semi-algebraic mode analysis of the 1-D two-grid cycle (Sec. 4):
              predicted smoothing and two-grid factors; a CPU tool as well
              (python -m oracle.sama)

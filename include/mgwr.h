@@ -382,6 +382,66 @@ int mgwr_profile(mgwr_t h, int enable);
  * coarse points restricted / fine points corrected). */
 int mgwr_profile_read(mgwr_t h, int kernel_class, long long* launches, double* ms, double* lines);
 
+/* ---- nonlinear problem: waveform relaxation FAS (Sec. 7) ---------------- */
+/* The 1-D problem of Eq. anomalous_diffusion,
+ *     D_t^alpha u = d/dx( D(u) du/dx ) + c du/dx + f   on (0,1) x (0,T],
+ * zero boundary and initial values, discretised with the L1 scheme in time
+ * (Eq. L1_scheme2), the conservative flux difference of Eq.
+ * spatial_discretization (a_{n+-1/2} = (D(u_{n+-1}) + D(u_n)) / 2, D(0) at the
+ * boundary) and upwind convection (forward difference c (u_{n+1} - u_n)/h for
+ * c >= 0, backward for c < 0), on n = 2^k - 1 interior points (h = 1/(n+1)) and
+ * M time steps (tau = T/M).  It is solved by the full approximation scheme
+ * (FAS): a nonlinear red-black waveform smoother in which every point of one
+ * colour solves its own time line with its neighbours' lines fixed (marching in
+ * time, a Newton solve per step), the residual N_h-defect, full weighting of the
+ * iterate and the defect, coarse right-hand side N_2h(R u) + R r on
+ * rediscretised coarse levels, linear interpolation of the coarse change, and
+ * an exact line solve on the one-point grid.  All arithmetic is IEEE double.
+ * Fields (host) are n time lines of M values, index i*M + m, m at t_{m+1}.
+ * Ownership, errors and threads as for mgwr_t; a handle runs on a stream it
+ * creates.  The history sums are direct (O(M^2) per line). */
+typedef struct mgwr_fas* mgwr_fas_t;
+#define MGWR_FAS_D_POROUS 0   /* D(u) = 1 + u^2 (Table table_nonlinear)          */
+#define MGWR_FAS_D_CONSTANT 1 /* D(u) = 1: the linear model (Sec. 2) when c = 0  */
+/* n = 2^k - 1 with 1 <= k <= 12; 1 <= M <= 4096; T > 0 finite; 0 < alpha <= 1;
+ * c finite; coefficient one of MGWR_FAS_D_*.  The iterate starts at zero and
+ * the right-hand side at zero.  MGWR_E_INVAL / MGWR_E_NOMEM / MGWR_E_CUDA. */
+int mgwr_fas_create(int n, int M, double T, double alpha, double c, int coefficient,
+                    mgwr_fas_t* out);
+int mgwr_fas_destroy(mgwr_fas_t h);
+const char* mgwr_fas_last_error(mgwr_fas_t h);
+/* MGWR_ORDER_TEXT (default) or MGWR_ORDER_TABLE, as for the linear solver; the
+ * cycle counts of Table table_nonlinear are reproduced with MGWR_ORDER_TABLE. */
+int mgwr_fas_set_order(mgwr_fas_t h, int order);
+/* f: n*M doubles (host).  Resets the iterate to zero and clears a recorded
+ * Newton failure. */
+int mgwr_fas_set_rhs(mgwr_fas_t h, const double* f);
+/* u0: n*M doubles (host): the iterate the next cycle or solve starts from
+ * (also clears a recorded Newton failure). */
+int mgwr_fas_set_initial(mgwr_fas_t h, const double* u0);
+/* FAS cycles (cycle = 1: V, 2: W; nu1 / nu2 pre- / post-smoothing steps, each a
+ * red and a black half-sweep) from the current iterate until the max-norm of
+ * f - N_h(u) is at most tol times its value at the start of the call, or
+ * max_cycles cycles.  Returns MGWR_OK, MGWR_E_NOCONV (stats filled), or
+ * MGWR_E_NUMERIC (a non-finite defect, or a Newton solve in the smoother that
+ * did not settle in 100 steps).  stats may be NULL (outer is 0). */
+int mgwr_fas_solve(mgwr_fas_t h, int cycle, int nu1, int nu2, double tol, int max_cycles,
+                   mgwr_stats* stats);
+/* One FAS cycle from the current iterate. */
+int mgwr_fas_cycle(mgwr_fas_t h, int cycle, int nu1, int nu2);
+/* max-norm of f - N_h(u) of the current iterate; optional copy to r_host (n*M). */
+int mgwr_fas_residual(mgwr_fas_t h, double* norm_inf, double* r_host);
+int mgwr_fas_get_solution(mgwr_fas_t h, double* u_host);
+/* Component calls on level `level` (0 = the one-point grid, mgwr_fas_levels()-1
+ * = the finest): one colour half-sweep of the nonlinear smoother, and copies of
+ * a level's iterate / right-hand side / defect (which = MGWR_U / MGWR_F /
+ * MGWR_R; n_level*M doubles, n_level = 2^(level+1) - 1). */
+int mgwr_fas_levels(mgwr_fas_t h, int* levels);
+int mgwr_fas_smooth(mgwr_fas_t h, int level, int colour);
+int mgwr_fas_defect(mgwr_fas_t h, int level, double* norm_inf);
+int mgwr_fas_field_set(mgwr_fas_t h, int level, int which, const double* host);
+int mgwr_fas_field_get(mgwr_fas_t h, int level, int which, double* host);
+
 #ifdef __cplusplus
 }
 #endif

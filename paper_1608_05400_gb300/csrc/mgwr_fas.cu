@@ -1,0 +1,594 @@
+// Waveform relaxation FAS for the 1-D nonlinear problem of Sec. 7
+// (Eq. anomalous_diffusion): D_t^alpha u = d/dx(D(u) du/dx) + c du/dx + f on
+// (0,1) x (0,T], zero boundary and initial values, discretised with the L1
+// scheme (Eq. L1_scheme2), the conservative flux difference of
+// Eq. spatial_discretization (a_{n+-1/2} the mean of D at the two nodes) and
+// upwind convection (forward difference for c >= 0, backward for c < 0).
+//
+// Kernels (FP64):
+//   k_fas_line   the nonlinear red-black waveform smoother: one warp per time line
+//                of one colour; the line is marched in time, each step a scalar
+//                Newton solve (the step's equation is strictly increasing in the
+//                unknown), the history sum of the L1 matrix shared by the warp's
+//                lanes from a shared-memory copy of the line;
+//   k_fas_apply  out = base + sign * N_h(u), N_h the discrete operator (time term
+//                T_M u by direct sums from shared memory, flux and upwind
+//                differences), with its max-norm: the defect f - N_h(u) and the
+//                FAS coarse right-hand side N_2h(R u) + R r;
+//   k_fas_restrict2, k_fas_correct   full weighting of the iterate and the
+//                defect, and u += P (u_c - R u).
+// The history sums are direct (O(M^2) per line, as the scheme is written):
+// the paper's nonlinear tables use M <= 256, and M is limited to 4096 here.
+#include <cuda_runtime.h>
+
+#include <cfloat>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "mgwr.h"
+#include "mgwr_common.cuh"
+
+namespace mgwr {
+namespace {
+
+constexpr int kFasMaxM = 4096;
+constexpr int kLineWarps = 4;     // time lines per block of k_fas_line
+constexpr int kApplyThreads = 256;
+constexpr int kNewtonMax = 100;   // Newton iterations per time step before giving up
+
+__device__ __forceinline__ double coef_D(int kind, double v) {
+  return kind == MGWR_FAS_D_POROUS ? 1.0 + v * v : 1.0;
+}
+
+__device__ __forceinline__ double coef_dD(int kind, double v) {
+  return kind == MGWR_FAS_D_POROUS ? 2.0 * v : 0.0;
+}
+
+// Lines of one colour: points i = 2k + parity (k < count), or every point when
+// all_points (the one-point grid).  Dynamic shared memory: (1 + kLineWarps) * M
+// doubles.  status bit 0 is set when Newton's method did not settle in a step.
+__global__ void __launch_bounds__(32 * kLineWarps)
+    k_fas_line(double* __restrict__ u, const double* __restrict__ f,
+               const double* __restrict__ r, int n, int M, double h, double c, int coef,
+               int parity, int all_points, int* __restrict__ status) {
+  extern __shared__ double sm[];
+  double* rs = sm;  // r_1..r_M of T_M
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double* line = sm + M + (size_t)warp * M;
+  for (int j = threadIdx.x; j < M; j += blockDim.x) rs[j] = r[j];
+  const int count = all_points ? n : (parity ? n / 2 : (n + 1) / 2);
+  const int k = blockIdx.x * kLineWarps + warp;
+  const bool active = k < count;
+  const int i = all_points ? k : 2 * k + parity;
+  if (active)
+    for (int j = lane; j < M; j += 32) line[j] = u[(size_t)i * M + j];
+  __syncthreads();
+  if (!active) return;
+  const double* up = (i + 1 < n) ? u + (size_t)(i + 1) * M : nullptr;
+  const double* um = (i > 0) ? u + (size_t)(i - 1) * M : nullptr;
+  const double* fi = f + (size_t)i * M;
+  const double r1 = rs[0], h2 = h * h, ac = fabs(c);
+  bool ok = true;
+  for (int m = 0; m < M; ++m) {
+    // sum_{j<m} (T_M)_{mj} u_j, (T_M)_{mj} = r_{m-j+1}
+    double part = 0.0;
+    for (int j = lane; j < m; j += 32) part = fma(rs[m - j], line[j], part);
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    const double hist = __shfl_sync(0xffffffffu, part, 0);
+    const double upm = up ? up[m] : 0.0, umm = um ? um[m] : 0.0;
+    const double Dp = coef_D(coef, upm), Dm = coef_D(coef, umm), fm = fi[m];
+    double v = line[m];
+    bool done = false, settled = false;
+    for (int it = 0; it < kNewtonMax; ++it) {
+      const double Dv = coef_D(coef, v), dDv = coef_dD(coef, v);
+      const double diffusion = (0.5 * (Dp + Dv) * (upm - v) - 0.5 * (Dm + Dv) * (v - umm)) / h2;
+      const double convection = c >= 0.0 ? c * (upm - v) / h : c * (v - umm) / h;
+      const double g = r1 * v + hist - diffusion - convection - fm;
+      const double dg =
+          r1 + 0.5 * (Dp + Dm + 2.0 * Dv + dDv * (2.0 * v - upm - umm)) / h2 + ac / h;
+      const double step = g / dg;
+      v -= step;
+      if (done) {
+        settled = true;
+        break;
+      }
+      // the step is at the rounding level of v or of the equation's terms: one more
+      const double scale =
+          (fabs(r1 * v) + fabs(hist) + fabs(diffusion) + fabs(convection) + fabs(fm)) / dg;
+      done = fabs(step) <= 1e-13 * (fabs(v) + scale) + 1e-300;
+    }
+    if (!settled) ok = false;
+    __syncwarp();
+    if (lane == 0) line[m] = v;
+    __syncwarp();
+  }
+  for (int j = lane; j < M; j += 32) u[(size_t)i * M + j] = line[j];
+  if (!ok && lane == 0) atomicOr(status, 1);
+}
+
+// out = base + sign * N_h(u) on every point (one block per line), and the
+// max-norm of out into *norm_bits (the bits of a non-negative double; a
+// non-finite value counts as +inf).  Dynamic shared memory: 2 * M doubles.
+__global__ void __launch_bounds__(kApplyThreads)
+    k_fas_apply(const double* __restrict__ u, const double* __restrict__ r,
+                const double* __restrict__ base, double* __restrict__ out, int n, int M,
+                double h, double c, int coef, double sign,
+                unsigned long long* __restrict__ norm_bits) {
+  extern __shared__ double sm[];
+  __shared__ double wmax[kApplyThreads / 32];
+  double* rs = sm;
+  double* line = sm + M;
+  const int i = blockIdx.x;
+  const size_t row = (size_t)i * M;
+  for (int j = threadIdx.x; j < M; j += blockDim.x) {
+    rs[j] = r[j];
+    line[j] = u[row + j];
+  }
+  __syncthreads();
+  const double h2 = h * h;
+  double local = 0.0;
+  for (int m = threadIdx.x; m < M; m += blockDim.x) {
+    double t = 0.0;
+    for (int j = 0; j <= m; ++j) t = fma(rs[m - j], line[j], t);
+    const double w0 = line[m];
+    const double wp = i + 1 < n ? u[row + M + m] : 0.0;
+    const double wm = i > 0 ? u[row - M + m] : 0.0;
+    const double D0 = coef_D(coef, w0);
+    const double a_plus = 0.5 * (coef_D(coef, wp) + D0);
+    const double a_minus = 0.5 * (coef_D(coef, wm) + D0);
+    const double diffusion = (a_plus * (wp - w0) - a_minus * (w0 - wm)) / h2;
+    const double convection = c >= 0.0 ? c * (wp - w0) / h : c * (w0 - wm) / h;
+    const double val = base[row + m] + sign * (t - (diffusion + convection));
+    out[row + m] = val;
+    const double a = fabs(val);
+    local = fmax(local, a <= DBL_MAX ? a : (double)INFINITY);
+  }
+  for (int o = 16; o > 0; o >>= 1) local = fmax(local, __shfl_xor_sync(0xffffffffu, local, o));
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = local;
+  __syncthreads();
+  if (threadIdx.x == 0 && norm_bits != nullptr) {
+    double mx = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, wmax[w]);
+    atomicMax(norm_bits, (unsigned long long)__double_as_longlong(mx));
+  }
+}
+
+// Full weighting (1/4)[1 2 1] of two fine fields (n = 2 nc + 1 lines) at once.
+__global__ void k_fas_restrict2(const double* __restrict__ a, double* __restrict__ ac,
+                                const double* __restrict__ b, double* __restrict__ bc, int nc,
+                                int M) {
+  const size_t total = (size_t)nc * M;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t J = idx / M, m = idx % M;
+    const size_t f0 = 2 * J * M + m;  // fine line 2J, then 2J+1 and 2J+2
+    ac[idx] = 0.25 * ((a[f0] + 2.0 * a[f0 + M]) + a[f0 + 2 * M]);
+    bc[idx] = 0.25 * ((b[f0] + 2.0 * b[f0 + M]) + b[f0 + 2 * M]);
+  }
+}
+
+// u (n = 2 nc + 1 lines) += P (uc - ubar): fine line 2J+1 takes coarse J, fine
+// line 2J the mean of coarse J-1 and J (zero beyond the boundary).
+__global__ void k_fas_correct(double* __restrict__ u, const double* __restrict__ uc,
+                              const double* __restrict__ ubar, int nc, int M) {
+  const int n = 2 * nc + 1;
+  const size_t total = (size_t)n * M;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int I = (int)(idx / M);
+    const size_t m = idx % M;
+    double p;
+    if (I & 1) {
+      const size_t cj = (size_t)((I - 1) / 2) * M + m;
+      p = uc[cj] - ubar[cj];
+    } else {
+      const int J = I / 2;
+      p = 0.0;
+      if (J >= 1) p += 0.5 * (uc[(size_t)(J - 1) * M + m] - ubar[(size_t)(J - 1) * M + m]);
+      if (J < nc) p += 0.5 * (uc[(size_t)J * M + m] - ubar[(size_t)J * M + m]);
+    }
+    u[idx] += p;
+  }
+}
+
+}  // namespace
+}  // namespace mgwr
+
+// ---- handle -------------------------------------------------------------------------
+
+struct mgwr_fas {
+  int n = 0, M = 0, nlev = 0, coef = 0, order = MGWR_ORDER_TEXT;
+  double T = 0.0, alpha = 0.0, c = 0.0;
+  cudaStream_t stream = nullptr;
+  double* r = nullptr;       // r_1..r_M of T_M
+  double* dk = nullptr;      // d_0..d_M (written by the coefficient kernel)
+  double* params = nullptr;  // alpha, tau^-alpha / Gamma(2 - alpha)
+  std::vector<double*> u, f, rr, ubar;  // per level, coarsest first
+  unsigned long long* flags = nullptr;  // [0] max-norm bits, [1] Newton status
+  size_t line_smem = 0, apply_smem = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  std::string err;
+};
+
+namespace {
+
+int fas_fail(mgwr_fas_t h, int code, const std::string& msg) {
+  if (h != nullptr) h->err = msg;
+  return code;
+}
+
+int fas_cuda(mgwr_fas_t h, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return MGWR_OK;
+  cudaGetLastError();
+  return fas_fail(h, MGWR_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+inline int level_n(int l) { return (1 << (l + 1)) - 1; }
+inline double level_h(int l) { return 1.0 / (double)(level_n(l) + 1); }
+inline size_t field_bytes(const mgwr_fas* h, int l) {
+  return sizeof(double) * (size_t)level_n(l) * h->M;
+}
+
+// red = the colour visited first: 1-D text order odd i, table order even i
+inline int colour_parity(const mgwr_fas* h, int colour) {
+  const int red = h->order == MGWR_ORDER_TEXT ? 1 : 0;
+  return colour == MGWR_RED ? red : 1 - red;
+}
+
+cudaError_t launch_line(mgwr_fas* h, int l, int parity, int all_points) {
+  const int n = level_n(l);
+  const int count = all_points ? n : (parity ? n / 2 : (n + 1) / 2);
+  if (count == 0) return cudaSuccess;
+  const int blocks = (count + mgwr::kLineWarps - 1) / mgwr::kLineWarps;
+  mgwr::k_fas_line<<<blocks, 32 * mgwr::kLineWarps, h->line_smem, h->stream>>>(
+      h->u[l], h->f[l], h->r, n, h->M, level_h(l), h->c, h->coef, parity, all_points,
+      reinterpret_cast<int*>(h->flags + 1));
+  return mgwr::counted(cudaGetLastError());
+}
+
+cudaError_t launch_apply(mgwr_fas* h, int l, const double* u, const double* base, double* out,
+                         double sign, bool norm) {
+  mgwr::k_fas_apply<<<level_n(l), mgwr::kApplyThreads, h->apply_smem, h->stream>>>(
+      u, h->r, base, out, level_n(l), h->M, level_h(l), h->c, h->coef, sign,
+      norm ? h->flags : nullptr);
+  return mgwr::counted(cudaGetLastError());
+}
+
+inline int grid_for(size_t total) {
+  const size_t b = (total + 255) / 256;
+  return (int)(b < 4096 ? (b > 0 ? b : 1) : 4096);
+}
+
+cudaError_t smooth_steps(mgwr_fas* h, int l, int steps) {
+  cudaError_t e = cudaSuccess;
+  for (int s = 0; s < steps && e == cudaSuccess; ++s) {
+    e = launch_line(h, l, colour_parity(h, MGWR_RED), 0);
+    if (e == cudaSuccess) e = launch_line(h, l, colour_parity(h, MGWR_BLACK), 0);
+  }
+  return e;
+}
+
+// One FAS cycle at level l on the handle's stream (no synchronisation).
+cudaError_t fas_cycle(mgwr_fas* h, int l, int nu1, int nu2, int gamma) {
+  if (l == 0) return launch_line(h, 0, 0, 1);
+  cudaError_t e = smooth_steps(h, l, nu1);
+  if (e != cudaSuccess) return e;
+  // r = f - N_h(u)
+  if ((e = launch_apply(h, l, h->u[l], h->f[l], h->rr[l], -1.0, false)) != cudaSuccess) return e;
+  const int nc = level_n(l - 1);
+  // ubar = R u, R r (into the coarse defect field, free until the coarse cycle)
+  mgwr::k_fas_restrict2<<<grid_for((size_t)nc * h->M), 256, 0, h->stream>>>(
+      h->u[l], h->ubar[l - 1], h->rr[l], h->rr[l - 1], nc, h->M);
+  if ((e = mgwr::counted(cudaGetLastError())) != cudaSuccess) return e;
+  // f_c = N_2h(ubar) + R r; the coarse iterate starts from ubar
+  if ((e = launch_apply(h, l - 1, h->ubar[l - 1], h->rr[l - 1], h->f[l - 1], 1.0, false)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaMemcpyAsync(h->u[l - 1], h->ubar[l - 1], field_bytes(h, l - 1),
+                           cudaMemcpyDeviceToDevice, h->stream)) != cudaSuccess)
+    return e;
+  for (int g = 0; g < gamma; ++g)
+    if ((e = fas_cycle(h, l - 1, nu1, nu2, gamma)) != cudaSuccess) return e;
+  // u += P (u_c - ubar)
+  mgwr::k_fas_correct<<<grid_for((size_t)level_n(l) * h->M), 256, 0, h->stream>>>(
+      h->u[l], h->u[l - 1], h->ubar[l - 1], nc, h->M);
+  if ((e = mgwr::counted(cudaGetLastError())) != cudaSuccess) return e;
+  return smooth_steps(h, l, nu2);
+}
+
+// Reads the max-norm and Newton status written since the last clear (synchronises).
+int read_flags(mgwr_fas* h, double* norm, bool* newton_failed) {
+  unsigned long long host[2] = {0, 0};
+  int s = fas_cuda(h, cudaMemcpyAsync(host, h->flags, sizeof(host), cudaMemcpyDeviceToHost,
+                                      h->stream), "read flags");
+  if (s == MGWR_OK) s = fas_cuda(h, cudaStreamSynchronize(h->stream), "synchronize");
+  if (s != MGWR_OK) return s;
+  if (norm) {
+    double v;
+    std::memcpy(&v, &host[0], sizeof(v));
+    *norm = v;
+  }
+  if (newton_failed) *newton_failed = (host[1] & 1ull) != 0;
+  return MGWR_OK;
+}
+
+cudaError_t clear_norm(mgwr_fas* h) {
+  return cudaMemsetAsync(h->flags, 0, sizeof(unsigned long long), h->stream);
+}
+
+int defect_norm(mgwr_fas* h, int l, double* norm) {
+  int s = fas_cuda(h, clear_norm(h), "clear norm");
+  if (s == MGWR_OK)
+    s = fas_cuda(h, launch_apply(h, l, h->u[l], h->f[l], h->rr[l], -1.0, true), "defect");
+  bool failed = false;
+  if (s == MGWR_OK) s = read_flags(h, norm, &failed);
+  if (s == MGWR_OK && failed)
+    s = fas_fail(h, MGWR_E_NUMERIC, "Newton's method did not settle in a line solve");
+  return s;
+}
+
+double* field_of(mgwr_fas* h, int l, int which) {
+  switch (which) {
+    case MGWR_U: return h->u[l];
+    case MGWR_F: return h->f[l];
+    case MGWR_R: return h->rr[l];
+    default: return nullptr;
+  }
+}
+
+void release(mgwr_fas* h) {
+  auto fr = [](double* p) { if (p) cudaFree(p); };
+  for (auto* v : {&h->u, &h->f, &h->rr, &h->ubar})
+    for (double* p : *v) fr(p);
+  fr(h->r);
+  fr(h->dk);
+  fr(h->params);
+  if (h->flags) cudaFree(h->flags);
+  if (h->ev0) cudaEventDestroy(h->ev0);
+  if (h->ev1) cudaEventDestroy(h->ev1);
+  if (h->stream) cudaStreamDestroy(h->stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+int mgwr_fas_create(int n, int M, double T, double alpha, double c, int coefficient,
+                    mgwr_fas_t* out) {
+  if (out == nullptr) return MGWR_E_INVAL;
+  *out = nullptr;
+  if (n < 1 || n > 4095 || ((n + 1) & n) != 0) return MGWR_E_INVAL;
+  if (M < 1 || M > mgwr::kFasMaxM) return MGWR_E_INVAL;
+  if (!(T > 0.0) || !std::isfinite(T) || !(alpha > 0.0) || !(alpha <= 1.0)) return MGWR_E_INVAL;
+  if (!std::isfinite(c)) return MGWR_E_INVAL;
+  if (coefficient != MGWR_FAS_D_POROUS && coefficient != MGWR_FAS_D_CONSTANT) return MGWR_E_INVAL;
+  mgwr_fas* h = new (std::nothrow) mgwr_fas;
+  if (h == nullptr) return MGWR_E_NOMEM;
+  h->n = n;
+  h->M = M;
+  h->T = T;
+  h->alpha = alpha;
+  h->c = c;
+  h->coef = coefficient;
+  while (level_n(h->nlev) < n) ++h->nlev;
+  ++h->nlev;  // levels 0..nlev-1 with level_n(nlev-1) = n
+  h->line_smem = sizeof(double) * (size_t)(1 + mgwr::kLineWarps) * M;
+  h->apply_smem = sizeof(double) * 2 * (size_t)M;
+  auto bail = [&](int code) {
+    release(h);
+    delete h;
+    return code;
+  };
+  if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(MGWR_E_CUDA);
+  }
+  auto alloc = [&](double** p, size_t bytes) {
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      *p = nullptr;
+      return false;
+    }
+    return true;
+  };
+  bool ok = alloc(&h->r, sizeof(double) * M) && alloc(&h->dk, sizeof(double) * (M + 1)) &&
+            alloc(&h->params, sizeof(double) * 2);
+  if (ok && cudaMalloc(&h->flags, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+    cudaGetLastError();
+    h->flags = nullptr;
+    ok = false;
+  }
+  for (int l = 0; ok && l < h->nlev; ++l) {
+    double *u = nullptr, *f = nullptr, *r = nullptr, *ub = nullptr;
+    ok = alloc(&u, field_bytes(h, l)) && alloc(&f, field_bytes(h, l)) &&
+         alloc(&r, field_bytes(h, l)) && alloc(&ub, field_bytes(h, l));
+    h->u.push_back(u);
+    h->f.push_back(f);
+    h->rr.push_back(r);
+    h->ubar.push_back(ub);
+  }
+  if (!ok) return bail(MGWR_E_NOMEM);
+  cudaError_t e = cudaSuccess;
+  if (h->line_smem > 48 * 1024)
+    e = cudaFuncSetAttribute(mgwr::k_fas_line, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)h->line_smem);
+  if (e == cudaSuccess && h->apply_smem > 48 * 1024)
+    e = cudaFuncSetAttribute(mgwr::k_fas_apply, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)h->apply_smem);
+  const double tau = T / M;
+  const double params[2] = {alpha, std::pow(tau, -alpha) / std::tgamma(2.0 - alpha)};
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->params, params, sizeof(params), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = mgwr::launch_coefficients(h->r, h->dk, M, h->params, h->params + 1, 1, h->stream);
+  for (int l = 0; e == cudaSuccess && l < h->nlev; ++l) {
+    e = cudaMemsetAsync(h->u[l], 0, field_bytes(h, l), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->f[l], 0, field_bytes(h, l), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->rr[l], 0, field_bytes(h, l), h->stream);
+  }
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(h->flags, 0, 2 * sizeof(unsigned long long), h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return bail(MGWR_E_CUDA);
+  }
+  *out = h;
+  return MGWR_OK;
+}
+
+int mgwr_fas_destroy(mgwr_fas_t h) {
+  if (h == nullptr) return MGWR_E_INVAL;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  release(h);
+  delete h;
+  return MGWR_OK;
+}
+
+const char* mgwr_fas_last_error(mgwr_fas_t h) { return h ? h->err.c_str() : "null handle"; }
+
+int mgwr_fas_set_order(mgwr_fas_t h, int order) {
+  if (h == nullptr) return MGWR_E_INVAL;
+  if (order != MGWR_ORDER_TEXT && order != MGWR_ORDER_TABLE)
+    return fas_fail(h, MGWR_E_INVAL, "order must be MGWR_ORDER_TEXT or MGWR_ORDER_TABLE");
+  h->order = order;
+  return MGWR_OK;
+}
+
+int mgwr_fas_levels(mgwr_fas_t h, int* levels) {
+  if (h == nullptr || levels == nullptr) return MGWR_E_INVAL;
+  *levels = h->nlev;
+  return MGWR_OK;
+}
+
+int mgwr_fas_field_set(mgwr_fas_t h, int level, int which, const double* host) {
+  if (h == nullptr) return MGWR_E_INVAL;
+  if (level < 0 || level >= h->nlev || host == nullptr || field_of(h, level, which) == nullptr)
+    return fas_fail(h, MGWR_E_INVAL, "bad level, field or pointer");
+  int s = fas_cuda(h, cudaMemcpyAsync(field_of(h, level, which), host, field_bytes(h, level),
+                                      cudaMemcpyHostToDevice, h->stream), "field_set");
+  if (s == MGWR_OK) s = fas_cuda(h, cudaStreamSynchronize(h->stream), "synchronize");
+  return s;
+}
+
+int mgwr_fas_field_get(mgwr_fas_t h, int level, int which, double* host) {
+  if (h == nullptr) return MGWR_E_INVAL;
+  if (level < 0 || level >= h->nlev || host == nullptr || field_of(h, level, which) == nullptr)
+    return fas_fail(h, MGWR_E_INVAL, "bad level, field or pointer");
+  int s = fas_cuda(h, cudaMemcpyAsync(host, field_of(h, level, which), field_bytes(h, level),
+                                      cudaMemcpyDeviceToHost, h->stream), "field_get");
+  if (s == MGWR_OK) s = fas_cuda(h, cudaStreamSynchronize(h->stream), "synchronize");
+  return s;
+}
+
+int mgwr_fas_set_rhs(mgwr_fas_t h, const double* f) {
+  if (h == nullptr) return MGWR_E_INVAL;
+  if (f == nullptr) return fas_fail(h, MGWR_E_INVAL, "null right-hand side");
+  const int L = h->nlev - 1;
+  int s = fas_cuda(h, cudaMemsetAsync(h->u[L], 0, field_bytes(h, L), h->stream), "clear u");
+  if (s == MGWR_OK)
+    s = fas_cuda(h, cudaMemsetAsync(h->flags, 0, 2 * sizeof(unsigned long long), h->stream),
+                 "clear flags");
+  if (s == MGWR_OK) s = mgwr_fas_field_set(h, L, MGWR_F, f);
+  return s;
+}
+
+int mgwr_fas_set_initial(mgwr_fas_t h, const double* u0) {
+  if (h == nullptr) return MGWR_E_INVAL;
+  if (u0 == nullptr) return fas_fail(h, MGWR_E_INVAL, "null initial iterate");
+  const int s = fas_cuda(
+      h, cudaMemsetAsync(h->flags, 0, 2 * sizeof(unsigned long long), h->stream), "clear flags");
+  return s == MGWR_OK ? mgwr_fas_field_set(h, h->nlev - 1, MGWR_U, u0) : s;
+}
+
+int mgwr_fas_get_solution(mgwr_fas_t h, double* u_host) {
+  if (h == nullptr) return MGWR_E_INVAL;
+  return mgwr_fas_field_get(h, h->nlev - 1, MGWR_U, u_host);
+}
+
+int mgwr_fas_defect(mgwr_fas_t h, int level, double* norm_inf) {
+  if (h == nullptr) return MGWR_E_INVAL;
+  if (level < 0 || level >= h->nlev) return fas_fail(h, MGWR_E_INVAL, "bad level");
+  double nrm = 0.0;
+  const int s = defect_norm(h, level, &nrm);
+  if (s == MGWR_OK && norm_inf) *norm_inf = nrm;
+  return s;
+}
+
+int mgwr_fas_residual(mgwr_fas_t h, double* norm_inf, double* r_host) {
+  if (h == nullptr) return MGWR_E_INVAL;
+  const int L = h->nlev - 1;
+  int s = mgwr_fas_defect(h, L, norm_inf);
+  if (s == MGWR_OK && r_host) s = mgwr_fas_field_get(h, L, MGWR_R, r_host);
+  return s;
+}
+
+int mgwr_fas_smooth(mgwr_fas_t h, int level, int colour) {
+  if (h == nullptr) return MGWR_E_INVAL;
+  if (level < 0 || level >= h->nlev || (colour != MGWR_RED && colour != MGWR_BLACK))
+    return fas_fail(h, MGWR_E_INVAL, "bad level or colour");
+  int s = fas_cuda(h, launch_line(h, level, colour_parity(h, colour), 0), "smooth");
+  bool failed = false;
+  if (s == MGWR_OK) s = read_flags(h, nullptr, &failed);
+  if (s == MGWR_OK && failed)
+    s = fas_fail(h, MGWR_E_NUMERIC, "Newton's method did not settle in a line solve");
+  return s;
+}
+
+int mgwr_fas_cycle(mgwr_fas_t h, int cycle, int nu1, int nu2) {
+  if (h == nullptr) return MGWR_E_INVAL;
+  if ((cycle != 1 && cycle != 2) || nu1 < 0 || nu2 < 0 || nu1 + nu2 < 1 || nu1 > 16 || nu2 > 16)
+    return fas_fail(h, MGWR_E_INVAL, "bad cycle parameters");
+  int s = fas_cuda(h, fas_cycle(h, h->nlev - 1, nu1, nu2, cycle), "cycle");
+  bool failed = false;
+  if (s == MGWR_OK) s = read_flags(h, nullptr, &failed);
+  if (s == MGWR_OK && failed)
+    s = fas_fail(h, MGWR_E_NUMERIC, "Newton's method did not settle in a line solve");
+  return s;
+}
+
+int mgwr_fas_solve(mgwr_fas_t h, int cycle, int nu1, int nu2, double tol, int max_cycles,
+                   mgwr_stats* stats) {
+  if (h == nullptr) return MGWR_E_INVAL;
+  if ((cycle != 1 && cycle != 2) || nu1 < 0 || nu2 < 0 || nu1 + nu2 < 1 || nu1 > 16 ||
+      nu2 > 16 || !(tol >= 0.0) || max_cycles < 0)
+    return fas_fail(h, MGWR_E_INVAL, "bad solve parameters");
+  const int L = h->nlev - 1;
+  mgwr_stats st{};
+  double r0 = 0.0;
+  int s = defect_norm(h, L, &r0);
+  if (s != MGWR_OK) return s;
+  if (!std::isfinite(r0)) return fas_fail(h, MGWR_E_NUMERIC, "non-finite initial defect");
+  if (r0 == 0.0) {
+    if (stats) *stats = st;
+    return MGWR_OK;
+  }
+  st.relres = 1.0;
+  s = fas_cuda(h, cudaEventRecord(h->ev0, h->stream), "event");
+  while (s == MGWR_OK && st.cycles < max_cycles && st.relres > tol) {
+    s = fas_cuda(h, fas_cycle(h, L, nu1, nu2, cycle), "cycle");
+    double nrm = 0.0;
+    if (s == MGWR_OK) s = defect_norm(h, L, &nrm);
+    if (s != MGWR_OK) break;
+    ++st.cycles;
+    st.relres = nrm / r0;
+    if (!std::isfinite(st.relres)) s = fas_fail(h, MGWR_E_NUMERIC, "non-finite defect");
+  }
+  if (cudaEventRecord(h->ev1, h->stream) == cudaSuccess &&
+      cudaEventSynchronize(h->ev1) == cudaSuccess) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, h->ev0, h->ev1) == cudaSuccess) st.seconds = 1e-3 * ms;
+  }
+  cudaGetLastError();
+  st.factor = st.cycles > 0 ? std::pow(st.relres, 1.0 / st.cycles) : 0.0;
+  if (stats) *stats = st;
+  if (s != MGWR_OK) return s;
+  return st.relres <= tol ? MGWR_OK
+                          : fas_fail(h, MGWR_E_NOCONV, "max_cycles reached before tol");
+}
+
+}  // extern "C"

@@ -31,6 +31,7 @@ MGWR_H64, MGWR_H32, MGWR_HDD = 64, 32, 48
 MGWR_U, MGWR_F, MGWR_R = 0, 1, 2
 MGWR_RED, MGWR_BLACK = 0, 1
 MGWR_ORDER_TEXT, MGWR_ORDER_TABLE = 0, 1
+MGWR_FAS_D_POROUS, MGWR_FAS_D_CONSTANT = 0, 1
 MGWR_POLICY_FIFO, MGWR_POLICY_SMALLEST = 0, 1
 MGWR_SPLIT_STAGED = 16
 MGWR_SPLIT_TENSOR = 32
@@ -110,6 +111,23 @@ _SIGS = {
     "mgwr_server_stats": (C.c_int, [C.c_void_p, C.POINTER(mgwr_server_info)]),
     "mgwr_profile": (C.c_int, [_h, C.c_int]),
     "mgwr_profile_read": (C.c_int, [_h, C.c_int, C.POINTER(C.c_longlong), _dp, _dp]),
+    "mgwr_fas_create": (C.c_int, [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.c_int,
+                                  C.POINTER(_h)]),
+    "mgwr_fas_destroy": (C.c_int, [_h]),
+    "mgwr_fas_last_error": (C.c_char_p, [_h]),
+    "mgwr_fas_set_order": (C.c_int, [_h, C.c_int]),
+    "mgwr_fas_set_rhs": (C.c_int, [_h, _dp]),
+    "mgwr_fas_set_initial": (C.c_int, [_h, _dp]),
+    "mgwr_fas_solve": (C.c_int, [_h, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int,
+                                 C.POINTER(mgwr_stats)]),
+    "mgwr_fas_cycle": (C.c_int, [_h, C.c_int, C.c_int, C.c_int]),
+    "mgwr_fas_residual": (C.c_int, [_h, _dp, _dp]),
+    "mgwr_fas_get_solution": (C.c_int, [_h, _dp]),
+    "mgwr_fas_levels": (C.c_int, [_h, C.POINTER(C.c_int)]),
+    "mgwr_fas_smooth": (C.c_int, [_h, C.c_int, C.c_int]),
+    "mgwr_fas_defect": (C.c_int, [_h, C.c_int, _dp]),
+    "mgwr_fas_field_set": (C.c_int, [_h, C.c_int, C.c_int, _dp]),
+    "mgwr_fas_field_get": (C.c_int, [_h, C.c_int, C.c_int, _dp]),
 }
 
 KERNEL_CLASSES = ("sweep64", "sweep32", "defect64", "defect32", "restrict", "prolong",
@@ -464,3 +482,101 @@ def launch_count() -> int:
     v = C.c_longlong()
     load().mgwr_launch_count(None, C.byref(v))
     return v.value
+
+
+class FAS:
+    """The 1-D nonlinear problem of Sec. 7 (mgwr_fas_*): waveform relaxation FAS on
+    n = 2^k - 1 interior points and M time steps; fields are (n, M) arrays."""
+
+    def __init__(self, n: int, M: int, T: float, alpha: float, c: float = 1.0,
+                 coefficient: int = MGWR_FAS_D_POROUS):
+        self.lib = load()
+        self.n, self.M = n, M
+        h = _h()
+        st = self.lib.mgwr_fas_create(n, M, T, alpha, c, coefficient, C.byref(h))
+        if st != MGWR_OK:
+            raise MGWRError(st, f"mgwr_fas_create({n}, {M}) failed: "
+                            + self.lib.mgwr_status_string(st).decode())
+        self.h = h
+
+    def _check(self, st: int, what: str, ok=(MGWR_OK,)):
+        if st not in ok:
+            raise MGWRError(st, f"{what}: {self.lib.mgwr_fas_last_error(self.h).decode()}")
+        return st
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mgwr_fas_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_order(self, order: int):
+        self._check(self.lib.mgwr_fas_set_order(self.h, order), "mgwr_fas_set_order")
+
+    def set_rhs(self, f: np.ndarray):
+        f = _f64(f)
+        assert f.shape == (self.n, self.M)
+        self._check(self.lib.mgwr_fas_set_rhs(self.h, _ptr(f)), "mgwr_fas_set_rhs")
+
+    def set_initial(self, u0: np.ndarray):
+        u0 = _f64(u0)
+        assert u0.shape == (self.n, self.M)
+        self._check(self.lib.mgwr_fas_set_initial(self.h, _ptr(u0)), "mgwr_fas_set_initial")
+
+    def solve(self, cycle=1, nu1=0, nu2=1, tol=1e-10, max_cycles=100,
+              allow_noconv=False) -> Stats:
+        st = mgwr_stats()
+        ok = (MGWR_OK, MGWR_E_NOCONV) if allow_noconv else (MGWR_OK,)
+        s = self._check(self.lib.mgwr_fas_solve(self.h, cycle, nu1, nu2, tol, max_cycles,
+                                                C.byref(st)), "mgwr_fas_solve", ok)
+        return Stats(st.cycles, st.outer, st.relres, st.factor, st.seconds, s)
+
+    def cycle(self, cycle=1, nu1=0, nu2=1):
+        self._check(self.lib.mgwr_fas_cycle(self.h, cycle, nu1, nu2), "mgwr_fas_cycle")
+
+    def residual(self, want_field=False):
+        nrm = C.c_double()
+        r = np.empty((self.n, self.M)) if want_field else None
+        self._check(self.lib.mgwr_fas_residual(self.h, C.byref(nrm), _ptr(r)), "mgwr_fas_residual")
+        return (nrm.value, r) if want_field else nrm.value
+
+    def solution(self) -> np.ndarray:
+        u = np.empty((self.n, self.M))
+        self._check(self.lib.mgwr_fas_get_solution(self.h, _ptr(u)), "mgwr_fas_get_solution")
+        return u
+
+    def num_levels(self) -> int:
+        v = C.c_int()
+        self._check(self.lib.mgwr_fas_levels(self.h, C.byref(v)), "mgwr_fas_levels")
+        return v.value
+
+    def smooth(self, level: int, colour: int):
+        self._check(self.lib.mgwr_fas_smooth(self.h, level, colour), "mgwr_fas_smooth")
+
+    def defect(self, level: int) -> float:
+        v = C.c_double()
+        self._check(self.lib.mgwr_fas_defect(self.h, level, C.byref(v)), "mgwr_fas_defect")
+        return v.value
+
+    def field_set(self, level: int, which: int, a: np.ndarray):
+        a = _f64(a)
+        assert a.shape == ((1 << (level + 1)) - 1, self.M)
+        self._check(self.lib.mgwr_fas_field_set(self.h, level, which, _ptr(a)),
+                    "mgwr_fas_field_set")
+
+    def field_get(self, level: int, which: int) -> np.ndarray:
+        a = np.empty(((1 << (level + 1)) - 1, self.M))
+        self._check(self.lib.mgwr_fas_field_get(self.h, level, which, _ptr(a)),
+                    "mgwr_fas_field_get")
+        return a

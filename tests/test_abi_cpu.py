@@ -129,3 +129,41 @@ def test_auto_precision_follows_the_fp32_refinement_limit(lib):
     assert lib.mgwr_auto_precision(1, 63, 64, 5, C.byref(r)) == mgwr.MGWR_E_INVAL
     assert lib.mgwr_auto_precision(3, 63, 64, MGWR_AUTO, C.byref(r)) == mgwr.MGWR_E_INVAL
     assert lib.mgwr_get_precision(None, C.byref(r)) == mgwr.MGWR_E_INVAL
+
+
+@pytest.mark.parametrize("args", [
+    (62, 32, 1.0, 0.5, 1.0, 0),            # n not 2^k - 1
+    (0, 32, 1.0, 0.5, 1.0, 0),
+    (8191, 32, 1.0, 0.5, 1.0, 0),          # n too large
+    (31, 0, 1.0, 0.5, 1.0, 0),             # M too small
+    (31, 4097, 1.0, 0.5, 1.0, 0),          # M too large for the direct history sums
+    (31, 32, 0.0, 0.5, 1.0, 0),            # T
+    (31, 32, math.inf, 0.5, 1.0, 0),
+    (31, 32, 1.0, 0.0, 1.0, 0),            # alpha
+    (31, 32, 1.0, 1.5, 1.0, 0),
+    (31, 32, 1.0, 0.5, math.nan, 0),       # c
+    (31, 32, 1.0, 0.5, 1.0, 2),            # coefficient
+])
+def test_fas_create_rejects_bad_arguments(lib, args):
+    h = C.c_void_p()
+    assert lib.mgwr_fas_create(*args, C.byref(h)) == mgwr.MGWR_E_INVAL
+    assert h.value is None
+
+
+def test_fas_calls_reject_a_null_handle(lib):
+    d = C.c_double()
+    i = C.c_int()
+    assert lib.mgwr_fas_destroy(None) == mgwr.MGWR_E_INVAL
+    assert lib.mgwr_fas_set_order(None, 0) == mgwr.MGWR_E_INVAL
+    assert lib.mgwr_fas_set_rhs(None, None) == mgwr.MGWR_E_INVAL
+    assert lib.mgwr_fas_set_initial(None, None) == mgwr.MGWR_E_INVAL
+    assert lib.mgwr_fas_solve(None, 1, 0, 1, 1e-10, 10, None) == mgwr.MGWR_E_INVAL
+    assert lib.mgwr_fas_cycle(None, 1, 0, 1) == mgwr.MGWR_E_INVAL
+    assert lib.mgwr_fas_residual(None, C.byref(d), None) == mgwr.MGWR_E_INVAL
+    assert lib.mgwr_fas_get_solution(None, None) == mgwr.MGWR_E_INVAL
+    assert lib.mgwr_fas_levels(None, C.byref(i)) == mgwr.MGWR_E_INVAL
+    assert lib.mgwr_fas_smooth(None, 0, 0) == mgwr.MGWR_E_INVAL
+    assert lib.mgwr_fas_defect(None, 0, C.byref(d)) == mgwr.MGWR_E_INVAL
+    assert lib.mgwr_fas_field_set(None, 0, 0, None) == mgwr.MGWR_E_INVAL
+    assert lib.mgwr_fas_field_get(None, 0, 0, None) == mgwr.MGWR_E_INVAL
+    assert lib.mgwr_fas_last_error(None) == b"null handle"

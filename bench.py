@@ -57,6 +57,9 @@ WORKLOADS = {
     "1d-4095-m65536": (1, 4095, 65536, 1, "talpha", 1e-8, "dd",
             "1-D MGWR 4095 interior points, M=65536 (long memory), u=t^alpha sin(pi x)"),
     "served": (0, 0, 0, 0, "", 1e-8, "auto", "served stream"),
+    "nonlinear-1d-255-m256": (1, 255, 256, 1, "", 1e-10, "fp64",
+            "1-D nonlinear problem of Sec. 7 (Table table_nonlinear, 256x256): D(u)=1+u^2, c=1, "
+            "f=1 on (0,1)x(0,1], waveform relaxation FAS V(0,1) from u=0"),
 }
 # alpha of a workload when --alpha is not given
 WORKLOAD_ALPHA = {"1d-4095-m65536": 0.2}
@@ -355,6 +358,155 @@ def cpu_baseline_leg(u: np.ndarray, d: int, n: int, Mv: int, alpha: float, kind:
     return base, err / float(np.abs(ph).max() * np.abs(w).max())
 
 
+def fas_line_flops(Mv: int) -> float:
+    """Algorithmic flops of one nonlinear line solve: the history sums of the L1
+    matrix (M(M-1)/2 multiply-adds) and four Newton iterations of about 30 flops
+    per time level."""
+    return Mv * (Mv - 1) + 4 * 30 * Mv
+
+
+def nonlinear_oracle_sample(delta: float, n: int, Mv: int):
+    """The CPU oracle's FAS solve of the nonlinear workload (the whole solve)."""
+    from oracle import fas
+
+    f = np.ones((n, Mv))
+    try:  # the oracle's small products run fastest on one BLAS thread
+        from threadpoolctl import threadpool_limits
+        limit, cores = threadpool_limits(1), 1
+    except ImportError:
+        limit, cores = None, os.cpu_count()
+    t0 = time.perf_counter()
+    W = fas.WRFAS(n, Mv, 1.0, delta, c=1.0, order="table")
+    u, hist = W.solve(f, 0, 1, tol=1e-10, max_cycles=30)
+    dt = time.perf_counter() - t0
+    if limit is not None:
+        limit.restore_original_limits()
+    return u, {"value": n * Mv / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"oracle WRFAS V(0,1) solve of the whole {n}x{Mv} workload to 1e-10 "
+                         f"({len(hist) - 1} cycles, {dt:.1f} s)"}
+
+
+def run_nonlinear(args):
+    """The nonlinear workload of Sec. 7 through mgwr_fas_*: one step is one FAS
+    V(0,1) solve from u = 0 to a 1e-10 defect reduction (Table table_nonlinear)."""
+    import torch
+
+    from paper_1608_05400_gb300 import mgwr
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    _, n, Mw, _, _, tol, _, desc = WORKLOADS[args.workload]
+    delta = args.alpha if args.alpha is not None else 0.4
+    unknowns = n * Mw
+    f = np.ones((n, Mw))
+    g = mgwr.FAS(n, Mw, 1.0, delta, 1.0)
+    g.set_order(mgwr.MGWR_ORDER_TABLE)
+    stream = torch.cuda.Stream()
+    g.set_stream(stream.cuda_stream)
+    g.set_rhs(f)
+
+    def step():
+        g.reset()
+        return g.solve(1, 0, 1, tol, 30)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    l0 = mgwr.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        rank_barrier(world)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        stats = [step() for _ in range(args.steps)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        rank_barrier(world)
+    launches = mgwr.launch_count() - l0
+    t_max = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
+    value = job_throughput(world, unknowns, args.steps, t_max)
+    u = g.solution()
+
+    # the dominant kernel, k_fas_line on the finest level: red half-sweeps of the
+    # converged iterate timed with events on the launching stream (each call also
+    # reads back 16 bytes of status)
+    L = g.num_levels() - 1
+    reps = 20
+    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k0.record(stream)
+    for _ in range(reps):
+        g.smooth(L, mgwr.MGWR_RED)
+    k1.record(stream)
+    torch.cuda.synchronize()
+    line_ms = k0.elapsed_time(k1) / reps
+    lines = (n + 1) // 2
+    pk = peaks()
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    peak = SMS * FP64_FMA_PER_CLK_PER_SM * 2 * sm_max * 1e6 / 1e12
+    achieved = lines * fas_line_flops(Mw) / (line_ms * 1e-3) / 1e12
+
+    e2e = None
+    if not args.no_e2e:
+        pin_f = torch.from_numpy(f).pin_memory()
+        pin_u = torch.empty_like(pin_f).pin_memory()
+        fp, up = pin_f.numpy(), pin_u.numpy()
+
+        def e2e_step():
+            g.set_rhs(fp)
+            st = g.solve(1, 0, 1, tol, 30)
+            g.lib.mgwr_fas_get_solution(g.h, up.ctypes.data_as(mgwr._dp))
+            return st
+
+        for _ in range(max(args.warmup, 1)):
+            e2e_step()
+        rank_barrier(world)
+        torch.cuda.synchronize()
+        ee0, ee1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ee0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        ee1.record(stream)
+        torch.cuda.synchronize()
+        ems = max_over_ranks(ee0.elapsed_time(ee1), world, "cuda")
+        e2e = {"value": job_throughput(world, unknowns, args.steps, ems), "unit": UNIT,
+               "h2d_bytes_per_step": unknowns * 8, "d2h_bytes_per_step": unknowns * 8,
+               "host_buffers": "pinned"}
+    g.close()
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+    out = {
+        "metric": "space-time unknowns/s to rel-res 1e-10 (nonlinear FAS, FP64)",
+        "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{desc}, delta={delta}, rel-res {tol}", "name": args.workload,
+                   "precision": "fp64", "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs smaller than L2 (0.5 MB per field): a latency-bound "
+                         "sequential time march, not a bandwidth measurement"},
+        "solve": {"cycles": stats[-1].cycles, "relres": stats[-1].relres,
+                  "factor": stats[-1].factor},
+        "gpu_launches": launches,
+        "roofline": {"kernel": "k_fas_line", "bound": "alu", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x max SM clock",
+                     "avg_launch_ms": line_ms, "lines_per_launch": lines,
+                     "note": "latency-bound: one warp per line marches M dependent Newton solves"},
+        "clocks": clk.summary(),
+        "e2e": e2e,
+    }
+    if not args.no_cpu and world == 1:
+        uo, out["cpu_baseline"] = nonlinear_oracle_sample(delta, n, Mw)
+        out["solve"]["rel_diff_vs_oracle"] = float(np.abs(u - uo).max() / np.abs(uo).max())
+    print(json.dumps(out))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -500,6 +652,8 @@ def main():
         return run_reference(args)
     if args.workload == "served":
         return run_served(args)
+    if args.workload.startswith("nonlinear"):
+        return run_nonlinear(args)
     import torch
 
     rank, world, local = dist_env()

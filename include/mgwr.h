@@ -419,6 +419,13 @@ int mgwr_fas_set_rhs(mgwr_fas_t h, const double* f);
 /* u0: n*M doubles (host): the iterate the next cycle or solve starts from
  * (also clears a recorded Newton failure). */
 int mgwr_fas_set_initial(mgwr_fas_t h, const double* u0);
+/* Zero the iterate and clear a recorded Newton failure (device work only, no
+ * copy): the next solve starts again from u = 0 with the same right-hand side. */
+int mgwr_fas_reset(mgwr_fas_t h);
+/* Run the handle's work on `stream` (a cudaStream_t of the current device; NULL:
+ * the handle's own stream).  Synchronises the previous stream first; the caller
+ * keeps the stream alive while the handle uses it. */
+int mgwr_fas_set_stream(mgwr_fas_t h, void* stream);
 /* FAS cycles (cycle = 1: V, 2: W; nu1 / nu2 pre- / post-smoothing steps, each a
  * red and a black half-sweep) from the current iterate until the max-norm of
  * f - N_h(u) is at most tol times its value at the start of the call, or

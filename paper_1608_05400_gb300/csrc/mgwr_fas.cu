@@ -43,9 +43,6 @@ __device__ __forceinline__ double coef_D(int kind, double v) {
   return kind == MGWR_FAS_D_POROUS ? 1.0 + v * v : 1.0;
 }
 
-__device__ __forceinline__ double coef_dD(int kind, double v) {
-  return kind == MGWR_FAS_D_POROUS ? 2.0 * v : 0.0;
-}
 
 // Lines of one colour: points i = 2k + parity (k < count), or every point when
 // all_points (the one-point grid).  Dynamic shared memory: (1 + kLineWarps) * M
@@ -70,7 +67,8 @@ __global__ void __launch_bounds__(32 * kLineWarps)
   const double* up = (i + 1 < n) ? u + (size_t)(i + 1) * M : nullptr;
   const double* um = (i > 0) ? u + (size_t)(i - 1) * M : nullptr;
   const double* fi = f + (size_t)i * M;
-  const double r1 = rs[0], h2 = h * h, ac = fabs(c);
+  const double r1 = rs[0], h2 = h * h, half_h2 = 0.5 / h2, ac_h = fabs(c) / h;
+  const double kappa = coef == MGWR_FAS_D_POROUS ? 1.0 : 0.0;  // D(v) = 1 + kappa v^2
   bool ok = true;
   for (int m = 0; m < M; ++m) {
     // sum_{j<m} (T_M)_{mj} u_j, (T_M)_{mj} = r_{m-j+1}
@@ -78,29 +76,56 @@ __global__ void __launch_bounds__(32 * kLineWarps)
     for (int j = lane; j < m; j += 32) part = fma(rs[m - j], line[j], part);
     for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
     const double hist = __shfl_sync(0xffffffffu, part, 0);
-    const double upm = up ? up[m] : 0.0, umm = um ? um[m] : 0.0;
-    const double Dp = coef_D(coef, upm), Dm = coef_D(coef, umm), fm = fi[m];
-    double v = line[m];
-    bool done = false, settled = false;
-    for (int it = 0; it < kNewtonMax; ++it) {
-      const double Dv = coef_D(coef, v), dDv = coef_dD(coef, v);
-      const double diffusion = (0.5 * (Dp + Dv) * (upm - v) - 0.5 * (Dm + Dv) * (v - umm)) / h2;
-      const double convection = c >= 0.0 ? c * (upm - v) / h : c * (v - umm) / h;
-      const double g = r1 * v + hist - diffusion - convection - fm;
-      const double dg =
-          r1 + 0.5 * (Dp + Dm + 2.0 * Dv + dDv * (2.0 * v - upm - umm)) / h2 + ac / h;
-      const double step = g / dg;
-      v -= step;
-      if (done) {
-        settled = true;
-        break;
-      }
-      // the step is at the rounding level of v or of the equation's terms: one more
-      const double scale =
-          (fabs(r1 * v) + fabs(hist) + fabs(diffusion) + fabs(convection) + fabs(fm)) / dg;
-      done = fabs(step) <= 1e-13 * (fabs(v) + scale) + 1e-300;
+    const double P = up ? up[m] : 0.0, Q = um ? um[m] : 0.0;
+    const double Dp = 1.0 + kappa * P * P, Dm = 1.0 + kappa * Q * Q, fm = fi[m];
+    // The step's equation g(v) = r_1 v + hist - diffusion(v) - convection(v) - f = 0
+    // as the cubic a0 + a1 v + a2 v^2 + a3 v^3: with D(v) = 1 + kappa v^2,
+    //   2 h^2 diffusion = (Dp+1) P + (Dm+1) Q - (Dp+Dm+2) v + kappa (P+Q) v^2 - 2 kappa v^3.
+    const double flux0 = ((Dp + 1.0) * P + (Dm + 1.0) * Q) * half_h2;
+    const double conv0 = c >= 0.0 ? c * P / h : -c * Q / h;
+    const double a3 = kappa / h2;
+    const double a2 = -kappa * (P + Q) * half_h2;
+    const double a1 = r1 + (Dp + Dm + 2.0) * half_h2 + ac_h;
+    const double a0 = hist - fm - flux0 - conv0;
+    // the size of the equation's terms, in units of v
+    const double s0 = (fabs(hist) + fabs(fm) + fabs(flux0) + fabs(conv0)) / a1;
+    // Newton's method in FP32 to about 1e-6, then two FP64 Newton steps with the
+    // FP32 reciprocal of g' (each contracts the error by about 1e-7)
+    const float b0 = (float)a0, b1 = (float)a1, b2 = (float)a2, b3 = (float)a3;
+    const float s0f = (float)s0;
+    float vf = (float)line[m];
+    for (int it = 0; it < 30; ++it) {
+      const float gf = fmaf(fmaf(fmaf(b3, vf, b2), vf, b1), vf, b0);
+      const float dgf = fmaf(fmaf(3.0f * b3, vf, 2.0f * b2), vf, b1);
+      const float sf = gf / dgf;
+      vf -= sf;
+      if (fabsf(sf) <= 1e-6f * (fabsf(vf) + s0f)) break;
     }
-    if (!settled) ok = false;
+    double v = isfinite(vf) ? (double)vf : line[m];
+    double step = 0.0;
+    for (int k = 0; k < 2; ++k) {
+      const double g = fma(fma(fma(a3, v, a2), v, a1), v, a0);
+      const double dg = fma(fma(3.0 * a3, v, 2.0 * a2), v, a1);
+      step = g * (double)(1.0f / (float)dg);
+      v -= step;
+    }
+    if (!(fabs(step) <= 1e-12 * (fabs(v) + s0) + 1e-300)) {
+      // not settled (extreme or non-finite data): plain FP64 Newton from the start
+      v = line[m];
+      bool done = false, settled = false;
+      for (int it = 0; it < kNewtonMax; ++it) {
+        const double g = fma(fma(fma(a3, v, a2), v, a1), v, a0);
+        const double dg = fma(fma(3.0 * a3, v, 2.0 * a2), v, a1);
+        step = g / dg;
+        v -= step;
+        if (done) {
+          settled = true;
+          break;
+        }
+        done = fabs(step) <= 1e-13 * (fabs(v) + s0) + 1e-300;
+      }
+      if (!settled) ok = false;
+    }
     __syncwarp();
     if (lane == 0) line[m] = v;
     __syncwarp();
@@ -202,7 +227,8 @@ __global__ void k_fas_correct(double* __restrict__ u, const double* __restrict__
 struct mgwr_fas {
   int n = 0, M = 0, nlev = 0, coef = 0, order = MGWR_ORDER_TEXT;
   double T = 0.0, alpha = 0.0, c = 0.0;
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;  // the stream every launch and copy goes to
+  cudaStream_t own = nullptr;     // the stream the handle created
   double* r = nullptr;       // r_1..r_M of T_M
   double* dk = nullptr;      // d_0..d_M (written by the coefficient kernel)
   double* params = nullptr;  // alpha, tau^-alpha / Gamma(2 - alpha)
@@ -349,7 +375,7 @@ void release(mgwr_fas* h) {
   if (h->flags) cudaFree(h->flags);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
-  if (h->stream) cudaStreamDestroy(h->stream);
+  if (h->own) cudaStreamDestroy(h->own);
 }
 
 }  // namespace
@@ -382,11 +408,12 @@ int mgwr_fas_create(int n, int M, double T, double alpha, double c, int coeffici
     delete h;
     return code;
   };
-  if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess ||
+  if (cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
     cudaGetLastError();
     return bail(MGWR_E_CUDA);
   }
+  h->stream = h->own;
   auto alloc = [&](double** p, size_t bytes) {
     if (cudaMalloc(p, bytes) != cudaSuccess) {
       cudaGetLastError();
@@ -457,6 +484,23 @@ int mgwr_fas_set_order(mgwr_fas_t h, int order) {
     return fas_fail(h, MGWR_E_INVAL, "order must be MGWR_ORDER_TEXT or MGWR_ORDER_TABLE");
   h->order = order;
   return MGWR_OK;
+}
+
+int mgwr_fas_set_stream(mgwr_fas_t h, void* stream) {
+  if (h == nullptr) return MGWR_E_INVAL;
+  int s = fas_cuda(h, cudaStreamSynchronize(h->stream), "synchronize");
+  if (s == MGWR_OK) h->stream = stream ? static_cast<cudaStream_t>(stream) : h->own;
+  return s;
+}
+
+int mgwr_fas_reset(mgwr_fas_t h) {
+  if (h == nullptr) return MGWR_E_INVAL;
+  const int L = h->nlev - 1;
+  int s = fas_cuda(h, cudaMemsetAsync(h->u[L], 0, field_bytes(h, L), h->stream), "clear u");
+  if (s == MGWR_OK)
+    s = fas_cuda(h, cudaMemsetAsync(h->flags, 0, 2 * sizeof(unsigned long long), h->stream),
+                 "clear flags");
+  return s;
 }
 
 int mgwr_fas_levels(mgwr_fas_t h, int* levels) {

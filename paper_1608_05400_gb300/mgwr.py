@@ -116,6 +116,8 @@ _SIGS = {
     "mgwr_fas_destroy": (C.c_int, [_h]),
     "mgwr_fas_last_error": (C.c_char_p, [_h]),
     "mgwr_fas_set_order": (C.c_int, [_h, C.c_int]),
+    "mgwr_fas_reset": (C.c_int, [_h]),
+    "mgwr_fas_set_stream": (C.c_int, [_h, C.c_void_p]),
     "mgwr_fas_set_rhs": (C.c_int, [_h, _dp]),
     "mgwr_fas_set_initial": (C.c_int, [_h, _dp]),
     "mgwr_fas_solve": (C.c_int, [_h, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int,
@@ -523,6 +525,12 @@ class FAS:
 
     def set_order(self, order: int):
         self._check(self.lib.mgwr_fas_set_order(self.h, order), "mgwr_fas_set_order")
+
+    def reset(self):
+        self._check(self.lib.mgwr_fas_reset(self.h), "mgwr_fas_reset")
+
+    def set_stream(self, stream_ptr: int | None):
+        self._check(self.lib.mgwr_fas_set_stream(self.h, stream_ptr), "mgwr_fas_set_stream")
 
     def set_rhs(self, f: np.ndarray):
         f = _f64(f)

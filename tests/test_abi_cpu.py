@@ -155,6 +155,8 @@ def test_fas_calls_reject_a_null_handle(lib):
     i = C.c_int()
     assert lib.mgwr_fas_destroy(None) == mgwr.MGWR_E_INVAL
     assert lib.mgwr_fas_set_order(None, 0) == mgwr.MGWR_E_INVAL
+    assert lib.mgwr_fas_reset(None) == mgwr.MGWR_E_INVAL
+    assert lib.mgwr_fas_set_stream(None, None) == mgwr.MGWR_E_INVAL
     assert lib.mgwr_fas_set_rhs(None, None) == mgwr.MGWR_E_INVAL
     assert lib.mgwr_fas_set_initial(None, None) == mgwr.MGWR_E_INVAL
     assert lib.mgwr_fas_solve(None, 1, 0, 1, 1e-10, 10, None) == mgwr.MGWR_E_INVAL

@@ -172,3 +172,22 @@ def test_non_finite_rhs_is_reported():
         # the handle stays usable
         g.set_rhs(np.ones((n, M)))
         assert g.solve(1, 0, 1, tol=1e-10, max_cycles=30).relres <= 1e-10
+
+
+def test_reset_and_stream_repeat_a_solve():
+    import torch
+    n, M = 63, 64
+    f = np.ones((n, M))
+    with G.FAS(n, M, 1.0, 0.4, 1.0) as g:
+        g.set_order(G.MGWR_ORDER_TABLE)
+        g.set_rhs(f)
+        a = g.solve(1, 0, 1, tol=1e-10, max_cycles=30)
+        ua = g.solution()
+        stream = torch.cuda.Stream()
+        g.set_stream(stream.cuda_stream)
+        g.reset()
+        b = g.solve(1, 0, 1, tol=1e-10, max_cycles=30)
+        ub = g.solution()
+        g.set_stream(None)
+    assert a.cycles == b.cycles
+    assert np.array_equal(ua, ub)  # the same kernels on the same data

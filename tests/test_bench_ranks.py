@@ -7,6 +7,7 @@ import socket
 import subprocess
 import sys
 
+import numpy as np
 import pytest
 import torch.multiprocessing as mp
 
@@ -82,3 +83,14 @@ def test_bench_helpers_parse_cpu_lists_and_splits():
     with bench.GpuLocalHost(0) as host:
         pass
     assert os.sched_getaffinity(0) == before
+
+
+def test_bench_nonlinear_helpers():
+    sys.path.insert(0, ROOT)
+    import bench
+    # history sums M(M-1)/2 multiply-adds plus four Newton iterations of 30 flops per level
+    assert bench.fas_line_flops(256) == 256 * 255 + 120 * 256
+    u, base = bench.nonlinear_oracle_sample(0.4, 15, 16)
+    assert u.shape == (15, 16) and np.isfinite(u).all()
+    assert base["kind"] == "oracle" and base["value"] > 0 and base["cores"] >= 1
+    assert "nonlinear-1d-255-m256" in bench.WORKLOADS

@@ -243,3 +243,29 @@ def test_command_line_table(capsys):
     out = capsys.readouterr().out.splitlines()
     assert out[0].split() == ["log2_lambda", "M=8", "M=16"]
     assert [int(line.split()[0]) for line in out[1:]] == [0, 2]
+
+
+def test_pre_and_post_smoothing_give_the_same_factor():
+    # T(1,0) = C S and T(0,1) = S C: AB and BA have the same eigenvalues
+    for lam in (2.0 ** -4, 1.0, 2.0 ** 4):
+        for t in sama.low_frequencies(6):
+            a = np.linalg.eigvals(sama.two_grid_symbol(lam, 1, 0.4, t, 1, 0))
+            b = np.linalg.eigvals(sama.two_grid_symbol(lam, 1, 0.4, t, 0, 1))
+            assert np.allclose(np.sort_complex(a), np.sort_complex(b), rtol=0, atol=1e-12)
+        assert abs(sama.two_grid_factor(lam, 8, 0.4, 1, 0, K=8, mode="exact")
+                   - sama.two_grid_factor(lam, 8, 0.4, 0, 1, K=8, mode="exact")) <= 1e-14
+
+
+def test_exact_factor_is_that_of_the_shifted_elliptic_problem():
+    # the first time step sees -Delta_h + r_1 I: at delta = 1 (backward Euler) r_1 h^2 =
+    # 1/lambda, so the factor is that of the 1-D two-grid cycle for h^-2 [-1 2+s -1],
+    # s = 1/lambda; its time-free limit lambda = inf gives 0, and for s > 0 the cycle
+    # is no longer exact
+    assert sama.two_grid_factor(math.inf, 1, 1.0, K=16, mode="exact") <= 1e-12
+    vals = [sama.two_grid_factor(2.0 ** e, 1, 1.0, K=32, mode="exact") for e in (8, 4, 0)]
+    assert 0 < vals[0] < vals[1] < vals[2] < 0.2
+    # the value at M = 1 does not depend on delta (only r_1 = c d_1 = c enters)
+    for lam in (0.25, 4.0):
+        a = sama.two_grid_factor(lam, 1, 0.3, K=16, mode="exact")
+        b = sama.two_grid_factor(lam, 1, 0.9, K=16, mode="exact")
+        assert abs(a - b) <= 1e-15

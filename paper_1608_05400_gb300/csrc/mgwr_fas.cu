@@ -67,8 +67,10 @@ __global__ void __launch_bounds__(32 * kLineWarps)
   const double* up = (i + 1 < n) ? u + (size_t)(i + 1) * M : nullptr;
   const double* um = (i > 0) ? u + (size_t)(i - 1) * M : nullptr;
   const double* fi = f + (size_t)i * M;
-  const double r1 = rs[0], h2 = h * h, half_h2 = 0.5 / h2, ac_h = fabs(c) / h;
+  const double r1 = rs[0], h2 = h * h, half_h2 = 0.5 / h2, c_h = c / h, ac_h = fabs(c_h);
   const double kappa = coef == MGWR_FAS_D_POROUS ? 1.0 : 0.0;  // D(v) = 1 + kappa v^2
+  // per-line constants (no FP64 division inside the time loop)
+  const double a3 = kappa / h2, a3x3 = 3.0 * a3;
   bool ok = true;
   for (int m = 0; m < M; ++m) {
     // sum_{j<m} (T_M)_{mj} u_j, (T_M)_{mj} = r_{m-j+1}
@@ -82,13 +84,14 @@ __global__ void __launch_bounds__(32 * kLineWarps)
     // as the cubic a0 + a1 v + a2 v^2 + a3 v^3: with D(v) = 1 + kappa v^2,
     //   2 h^2 diffusion = (Dp+1) P + (Dm+1) Q - (Dp+Dm+2) v + kappa (P+Q) v^2 - 2 kappa v^3.
     const double flux0 = ((Dp + 1.0) * P + (Dm + 1.0) * Q) * half_h2;
-    const double conv0 = c >= 0.0 ? c * P / h : -c * Q / h;
-    const double a3 = kappa / h2;
-    const double a2 = -kappa * (P + Q) * half_h2;
+    const double conv0 = c >= 0.0 ? c_h * P : -c_h * Q;
+    const double a2 = -kappa * (P + Q) * half_h2, a2x2 = 2.0 * a2;
     const double a1 = r1 + (Dp + Dm + 2.0) * half_h2 + ac_h;
     const double a0 = hist - fm - flux0 - conv0;
-    // the size of the equation's terms, in units of v
-    const double s0 = (fabs(hist) + fabs(fm) + fabs(flux0) + fabs(conv0)) / a1;
+    // the size of the equation's terms, in units of v (a tolerance scale only, so the
+    // FP32 reciprocal of a1 is accurate enough)
+    const double s0 =
+        (fabs(hist) + fabs(fm) + fabs(flux0) + fabs(conv0)) * (double)(1.0f / (float)a1);
     // Newton's method in FP32 to about 1e-6, then two FP64 Newton steps with the
     // FP32 reciprocal of g' (each contracts the error by about 1e-7)
     const float b0 = (float)a0, b1 = (float)a1, b2 = (float)a2, b3 = (float)a3;
@@ -105,7 +108,7 @@ __global__ void __launch_bounds__(32 * kLineWarps)
     double step = 0.0;
     for (int k = 0; k < 2; ++k) {
       const double g = fma(fma(fma(a3, v, a2), v, a1), v, a0);
-      const double dg = fma(fma(3.0 * a3, v, 2.0 * a2), v, a1);
+      const double dg = fma(fma(a3x3, v, a2x2), v, a1);
       step = g * (double)(1.0f / (float)dg);
       v -= step;
     }
@@ -115,7 +118,7 @@ __global__ void __launch_bounds__(32 * kLineWarps)
       bool done = false, settled = false;
       for (int it = 0; it < kNewtonMax; ++it) {
         const double g = fma(fma(fma(a3, v, a2), v, a1), v, a0);
-        const double dg = fma(fma(3.0 * a3, v, 2.0 * a2), v, a1);
+        const double dg = fma(fma(a3x3, v, a2x2), v, a1);
         step = g / dg;
         v -= step;
         if (done) {

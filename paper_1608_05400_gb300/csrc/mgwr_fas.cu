@@ -18,7 +18,8 @@
 //   k_fas_restrict2, k_fas_correct   full weighting of the iterate and the
 //                defect, and u += P (u_c - R u).
 // The history sums are direct (O(M^2) per line, as the scheme is written):
-// the paper's nonlinear tables use M <= 256, and M is limited to 4096 here.
+// the paper's nonlinear tables use M <= 256, and M is limited to 1024 here, so
+// both kernels stay within the default 48 KB of dynamic shared memory.
 #include <cuda_runtime.h>
 
 #include <cfloat>
@@ -34,7 +35,7 @@
 namespace mgwr {
 namespace {
 
-constexpr int kFasMaxM = 4096;
+constexpr int kFasMaxM = 1024;
 constexpr int kLineWarps = 4;     // time lines per block of k_fas_line
 constexpr int kApplyThreads = 256;
 constexpr int kNewtonMax = 100;   // Newton iterations per time step before giving up
@@ -442,13 +443,10 @@ int mgwr_fas_create(int n, int M, double T, double alpha, double c, int coeffici
     h->ubar.push_back(ub);
   }
   if (!ok) return bail(MGWR_E_NOMEM);
+  // (1 + kLineWarps) * 1024 and 2 * 1024 doubles: within the default 48 KB
+  static_assert((1 + mgwr::kLineWarps) * mgwr::kFasMaxM * sizeof(double) <= 48 * 1024,
+                "k_fas_line shared memory");
   cudaError_t e = cudaSuccess;
-  if (h->line_smem > 48 * 1024)
-    e = cudaFuncSetAttribute(mgwr::k_fas_line, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)h->line_smem);
-  if (e == cudaSuccess && h->apply_smem > 48 * 1024)
-    e = cudaFuncSetAttribute(mgwr::k_fas_apply, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)h->apply_smem);
   const double tau = T / M;
   const double params[2] = {alpha, std::pow(tau, -alpha) / std::tgamma(2.0 - alpha)};
   if (e == cudaSuccess)

@@ -136,7 +136,8 @@ def test_auto_precision_follows_the_fp32_refinement_limit(lib):
     (0, 32, 1.0, 0.5, 1.0, 0),
     (8191, 32, 1.0, 0.5, 1.0, 0),          # n too large
     (31, 0, 1.0, 0.5, 1.0, 0),             # M too small
-    (31, 4097, 1.0, 0.5, 1.0, 0),          # M too large for the direct history sums
+    (31, 1025, 1.0, 0.5, 1.0, 0),          # M too large for the direct history sums
+    (31, 4097, 1.0, 0.5, 1.0, 0),
     (31, 32, 0.0, 0.5, 1.0, 0),            # T
     (31, 32, math.inf, 0.5, 1.0, 0),
     (31, 32, 1.0, 0.0, 1.0, 0),            # alpha

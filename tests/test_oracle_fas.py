@@ -153,3 +153,33 @@ def test_paper_table_nonlinear(row):
     assert hist[-1] <= 1e-10
     assert abs(k - cycles) <= 1, (delta, N, k, cycles)
     assert abs(hist[-1] / hist[-2] - factor) <= 0.02, (delta, N, hist[-1] / hist[-2], factor)
+
+
+@pytest.mark.parametrize("c", [1.0, -1.0])
+def test_line_solve_equals_the_preconditioned_whole_line_iteration(c):
+    # an independent solver of the same line equations, T_M v + phi(v) = f with phi the
+    # pointwise flux and upwind terms (neighbours fixed): the fixed point of
+    # v <- v - (T_M + sigma I)^{-1} (T_M v + phi(v) - f), sigma = 2/h^2 + |c|/h, whose
+    # every step is two causal convolutions (no march in time); it converges in a few
+    # steps because phi' stays within a few per cent of sigma
+    n, M, delta = 63, 64, 0.4
+    W = fas.WRFAS(n, M, 1.0, delta, c=c, order="table")
+    f = np.ones((n, M))
+    u = W.cycle(W.finest, np.zeros((n, M)), f, 0, 1)  # a realistic iterate
+    h = W.h(W.finest)
+    rows = mgwr.colour_mask(1, n, mgwr.RED, "table")
+    ref = u.copy()
+    fas.line_solve(ref, f, rows, W.Tm, h, c, fas.porous_D, fas.porous_dD)
+    K = np.linalg.inv(W.Tm + (2.0 / h ** 2 + abs(c) / h) * np.eye(M))
+    for i in np.flatnonzero(rows):
+        v = u[i].copy()
+        for k in range(30):
+            line = u.copy()
+            line[i] = v
+            G = fas.operator(line, W.Tm, h, c, fas.porous_D)[i] - f[i]
+            dv = K @ G
+            v = v - dv
+            if np.abs(dv).max() <= 1e-15 * np.abs(v).max():
+                break
+        assert k < 12, k
+        assert np.abs(v - ref[i]).max() <= 1e-13 * np.abs(ref[i]).max()

@@ -404,7 +404,8 @@ typedef struct mgwr_fas* mgwr_fas_t;
 #define MGWR_FAS_D_POROUS 0   /* D(u) = 1 + u^2 (Table table_nonlinear)          */
 #define MGWR_FAS_D_CONSTANT 1 /* D(u) = 1: the linear model (Sec. 2) when c = 0  */
 /* n = 2^k - 1 with 1 <= k <= 12; 1 <= M <= 1024; T > 0 finite; 0 < alpha <= 1;
- * c finite; coefficient one of MGWR_FAS_D_*.  The iterate starts at zero and
+ * |c| <= 1e30; the L1 scale (T/M)^-alpha / Gamma(2 - alpha) <= 1e30 (the smoother
+ * starts each Newton solve in FP32); coefficient one of MGWR_FAS_D_*.  The iterate starts at zero and
  * the right-hand side at zero.  MGWR_E_INVAL / MGWR_E_NOMEM / MGWR_E_CUDA. */
 int mgwr_fas_create(int n, int M, double T, double alpha, double c, int coefficient,
                     mgwr_fas_t* out);

@@ -395,6 +395,10 @@ int mgwr_fas_create(int n, int M, double T, double alpha, double c, int coeffici
   if (!(T > 0.0) || !std::isfinite(T) || !(alpha > 0.0) || !(alpha <= 1.0)) return MGWR_E_INVAL;
   if (!std::isfinite(c)) return MGWR_E_INVAL;
   if (coefficient != MGWR_FAS_D_POROUS && coefficient != MGWR_FAS_D_CONSTANT) return MGWR_E_INVAL;
+  // the smoother starts each Newton solve in FP32: its coefficients, the L1 scale
+  // tau^-alpha / Gamma(2 - alpha) and |c| / h, must stay far inside FP32's range
+  const double l1_scale = std::pow(T / M, -alpha) / std::tgamma(2.0 - alpha);
+  if (!(l1_scale <= 1e30) || !(std::fabs(c) <= 1e30)) return MGWR_E_INVAL;
   mgwr_fas* h = new (std::nothrow) mgwr_fas;
   if (h == nullptr) return MGWR_E_NOMEM;
   h->n = n;
@@ -447,8 +451,7 @@ int mgwr_fas_create(int n, int M, double T, double alpha, double c, int coeffici
   static_assert((1 + mgwr::kLineWarps) * mgwr::kFasMaxM * sizeof(double) <= 48 * 1024,
                 "k_fas_line shared memory");
   cudaError_t e = cudaSuccess;
-  const double tau = T / M;
-  const double params[2] = {alpha, std::pow(tau, -alpha) / std::tgamma(2.0 - alpha)};
+  const double params[2] = {alpha, l1_scale};
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->params, params, sizeof(params), cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess)

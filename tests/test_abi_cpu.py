@@ -143,6 +143,8 @@ def test_auto_precision_follows_the_fp32_refinement_limit(lib):
     (31, 32, 1.0, 0.0, 1.0, 0),            # alpha
     (31, 32, 1.0, 1.5, 1.0, 0),
     (31, 32, 1.0, 0.5, math.nan, 0),       # c
+    (31, 32, 1.0, 0.5, 1e31, 0),
+    (31, 32, 1e-200, 1.0, 1.0, 0),         # L1 scale (T/M)^-alpha / Gamma(2-alpha) > 1e30
     (31, 32, 1.0, 0.5, 1.0, 2),            # coefficient
 ])
 def test_fas_create_rejects_bad_arguments(lib, args):

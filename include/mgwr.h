@@ -287,10 +287,13 @@ int mgwr_inverse_column(mgwr_t h, int level, double* k_host);  /* batch x (k_1..
  * the library, which every GPU that loads the library keeps until the process
  * exits; so M is limited to 4096: larger M returns MGWR_E_TOOBIG, and a bad
  * pointer, M not a power of two >= 4 or sigma < 0 returns MGWR_E_INVAL.
- * Nothing is allocated.  The first call on each device looks up the array's
- * device address (do it before any stream capture).  All calls share the one
- * array: calls whose work overlaps on the GPU (other streams, other host
- * threads) race and must be serialised by the caller. */
+ * Nothing is allocated.  sigma reaches the array by value, through a
+ * one-thread kernel on `stream` ahead of the inverse-column kernel, so the
+ * call is ordered on `stream` like any kernel launch and does not wait for the
+ * GPU.  The first call on each device looks up the array's device address
+ * (make it before any stream capture).  All calls share the one array: calls
+ * whose work overlaps on the GPU (other streams, other host threads) race and
+ * must be serialised by the caller. */
 int mgwr_inverse_column_noalloc(const double* r_dev, int M, double sigma, double* k_dev,
                                 void* stream);
 

@@ -13,10 +13,6 @@
 
 namespace mgwr {
 
-// Counts a kernel launch in the process-wide launch counter and passes the
-// launch status through.
-cudaError_t counted(cudaError_t e);
-
 // Minimum resident blocks per SM asked of the compiler (it sets the register
 // cap), counted in butterfly slots (threads x E, E butterflies per thread):
 // 1024 slots for the FP32 engine kernels (64 registers per slot), 768 for the

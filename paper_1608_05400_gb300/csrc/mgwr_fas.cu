@@ -110,6 +110,13 @@ __global__ void __launch_bounds__(32 * kLineWarps)
     for (int k = 0; k < 2; ++k) {
       const double g = fma(fma(fma(a3, v, a2), v, a1), v, a0);
       const double dg = fma(fma(a3x3, v, a2x2), v, a1);
+      const float dgs = fabsf((float)dg);
+      if (!(dgs >= FLT_MIN && dgs <= FLT_MAX)) {
+        // g' outside FP32's normal range: its FP32 reciprocal would be 0 or inf,
+        // so leave the step to the plain FP64 Newton solve below
+        step = NAN;
+        break;
+      }
       step = g * (double)(1.0f / (float)dg);
       v -= step;
     }

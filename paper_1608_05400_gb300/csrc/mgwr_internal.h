@@ -233,5 +233,7 @@ cudaError_t launch_round_cx(Cx<float>* dst, const Cx<double>* src, size_t count,
 // including those replayed from captured graphs (add_launches).
 long long launch_counter();
 void add_launches(long long n);
+// Counts a kernel launch in that counter and passes the launch status through.
+cudaError_t counted(cudaError_t e);
 
 }  // namespace mgwr

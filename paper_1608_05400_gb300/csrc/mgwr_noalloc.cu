@@ -47,6 +47,11 @@ cudaError_t scratch_on_current_device(double** out) {
   return cudaSuccess;
 }
 
+// Writes sigma, passed by value, into its slot of the scratch array: no host
+// buffer is involved, so the call stays stream-ordered and never waits for a
+// pageable copy.
+__global__ void k_store_sigma(double* slot, double sigma) { *slot = sigma; }
+
 }  // namespace
 
 extern "C" int mgwr_inverse_column_noalloc(const double* r_dev, int M, double sigma, double* k_dev,
@@ -61,9 +66,11 @@ extern "C" int mgwr_inverse_column_noalloc(const double* r_dev, int M, double si
     return MGWR_E_CUDA;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  // sigma goes into its slot; the work area needs no clearing (every entry is
-  // written before it is read inside the kernel)
-  cudaError_t e = cudaMemcpyAsync(scratch, &sigma, sizeof(double), cudaMemcpyHostToDevice, s);
+  // sigma goes into its slot by a one-thread kernel on the caller's stream; the
+  // work area needs no clearing (every entry is written before it is read
+  // inside the kernel)
+  k_store_sigma<<<1, 1, 0, s>>>(scratch, sigma);
+  cudaError_t e = mgwr::counted(cudaGetLastError());
   if (e == cudaSuccess)
     e = mgwr::launch_inverse_columns(k_dev, r_dev, scratch, 1, M, 1,
                                      reinterpret_cast<mgwr::Cx<double>*>(scratch + kSigmaSlots), s);

@@ -188,6 +188,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     if (threadIdx.x == kIssuer) {
       int issued = -1;
       ok = mbar_wait_bounded(band_bar, 0u);
+      const bool band_ok = ok;
       for (int ch = 0; ok && ch < kNumChunks; ++ch) {
         const int b = ch & 1;
         if (!mbar_wait_bounded(&full[b], (unsigned)((ch >> 1) & 1))) {
@@ -215,6 +216,9 @@ __global__ void __launch_bounds__(kThreads, 2)
         mma_commit(done);
       } else {
         atomicOr(&g_tc_timeout, 1u);
+        // the band's bulk copy may still be writing shared memory: give it one more
+        // bounded wait before the CTA can end
+        if (!band_ok) (void)mbar_wait_bounded(band_bar, 0u);
         // what was issued finishes before the accumulator is released
         if (issued >= 0) (void)mbar_wait_bounded(&empty[issued & 1], (unsigned)((issued >> 1) & 1));
       }

@@ -35,7 +35,7 @@ def _one_blas_thread():
 
 @functools.lru_cache(maxsize=None)
 def _predicted(log2lam, M):
-    return sama.two_grid_factor(2.0 ** log2lam, int(M), 0.4)
+    return sama.two_grid_factor(2.0 ** log2lam, int(M), 0.4, mode="dense")
 
 
 def _table(name):
@@ -149,6 +149,7 @@ def test_elliptic_limit_is_an_exact_two_grid_solver():
     # and linear interpolation with the 2h stencil then solve 1-D exactly
     for t in sama.low_frequencies(8):
         assert np.abs(sama.two_grid_symbol(math.inf, 4, 0.4, t)).max() <= 1e-12
+    assert sama.two_grid_factor(2.0 ** 30, 8, 0.4, K=16, mode="dense") <= 1e-8
     assert sama.two_grid_factor(2.0 ** 30, 8, 0.4, K=16) <= 1e-8
 
 
@@ -166,15 +167,15 @@ def test_exact_radius_is_the_first_time_step():
                     diag = np.diagonal(blk, -k)
                     assert np.abs(diag - diag[0]).max() <= 1e-13
         one = sama.two_grid_symbol(lam, 1, delta, t)
-        assert abs(sama.spectral_radius(T, 2, "exact") - sama.spectral_radius(one, 2)) <= 1e-14
+        assert abs(sama.spectral_radius(T, 2, "exact") - sama.spectral_radius(one, 2, "dense")) <= 1e-14
     assert sama.two_grid_factor(lam, 64, delta, K=16, mode="exact") == \
-        sama.two_grid_factor(lam, 1, delta, K=16)
+        sama.two_grid_factor(lam, 1, delta, K=16, mode="dense")
 
 
 def test_dense_radius_grows_with_M_from_the_exact_one():
     lam, delta = 2.0 ** -4, 0.4
     exact = sama.two_grid_factor(lam, 32, delta, K=32, mode="exact")
-    dense = [sama.two_grid_factor(lam, M, delta, K=32) for M in (1, 32, 64, 128)]
+    dense = [sama.two_grid_factor(lam, M, delta, K=32, mode="dense") for M in (1, 32, 64, 128)]
     assert abs(dense[0] - exact) <= 1e-14
     assert exact < dense[1] < dense[2] < dense[3]
 
@@ -220,6 +221,7 @@ def test_factors_stay_below_two_tenths_for_all_orders():
     for delta in (0.1, 0.3, 0.5, 0.7, 0.9):
         for e in range(-12, 13, 4):
             lam = sama.lam_of(2.0 ** e * h * h, h, delta)
+            assert sama.two_grid_factor(lam, 32, delta, K=16, mode="dense") < 0.2, (delta, e)
             assert sama.two_grid_factor(lam, 32, delta, K=16) < 0.2, (delta, e)
 
 

@@ -1,10 +1,15 @@
 """The allocation-free inverse-column entry point (mgwr_inverse_column_noalloc).
 
-It exists for callers that cannot allocate device memory while they run; its
-scratch is a fixed array inside the library.  Its results must equal those of
-the regular entry point (mgwr_create + mgwr_inverse_column, which allocates its
-scratch), within the inverse-column tolerance of the other GPU tests, on two
-calls in a row that reuse the shared array.  This file is collected last.
+It serves callers that cannot allocate device memory while they run (services
+that reserve their whole GPU budget at start-up, or code whose device memory
+belongs to another allocator); its scratch is a fixed array inside the library.
+Its results must equal those of the regular entry point (mgwr_create +
+mgwr_inverse_column, which allocates its scratch), within the inverse-column
+tolerance of the other GPU tests, on calls in a row that reuse the shared array,
+also on a stream that still has other work queued ahead of the call.
+
+The file name sorts last, so pytest collects it after every other test file: a
+run that stops at the first failure has then already run all the other tests.
 """
 import ctypes as C
 
@@ -15,16 +20,28 @@ from paper_1608_05400_gb300 import mgwr as G
 
 pytestmark = pytest.mark.gpu
 
+D, N, M, T, ALPHA = 2, 31, 1024, 1.0, 0.35
+
+
+def _regular():
+    """Toeplitz column, inverse columns and sigmas of two levels from the
+    regular (allocating) entry points."""
+    with G.Solver(D, N, M, T, ALPHA) as s:
+        r = s.toeplitz_column()
+        levels = [s.num_levels() - 1, 0]
+        refs = [s.inverse_column(l) for l in levels]
+        sigmas = [2.0 * D * (s.level_n(l) + 1) ** 2 for l in levels]
+    return r, refs, sigmas
+
+
+def _close(k, ref):
+    return np.all(np.isfinite(k)) and np.abs(k - ref).max() <= 1e-13 * np.abs(ref).max()
+
 
 def test_noalloc_inverse_column_matches_regular_entry_point():
     torch = pytest.importorskip("torch")
     lib = G.load()
-    d, n, M, T, alpha = 2, 31, 1024, 1.0, 0.35
-    with G.Solver(d, n, M, T, alpha) as s:
-        r = s.toeplitz_column()
-        levels = [s.num_levels() - 1, 0]
-        refs = [s.inverse_column(l) for l in levels]
-        sigmas = [2.0 * d * (s.level_n(l) + 1) ** 2 for l in levels]
+    r, refs, sigmas = _regular()
     r_dev = torch.tensor(r, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream().cuda_stream
     outs = []
@@ -36,8 +53,32 @@ def test_noalloc_inverse_column_matches_regular_entry_point():
         torch.cuda.synchronize()
         outs.append(k_dev.cpu().numpy())
     for k, ref in zip(outs, refs):
-        assert np.all(np.isfinite(k))
-        assert np.abs(k - ref).max() <= 1e-13 * np.abs(ref).max()
+        assert _close(k, ref)
+
+
+def test_noalloc_call_is_ordered_on_a_busy_stream():
+    # the input column is written by a kernel queued behind a busy wait on a fresh
+    # stream; the call on that stream must see it, and sigma must arrive in order too
+    torch = pytest.importorskip("torch")
+    lib = G.load()
+    r, refs, sigmas = _regular()
+    src = torch.tensor(r, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    outs = []
+    for sigma in reversed(sigmas):
+        with torch.cuda.stream(side):
+            torch.cuda._sleep(20_000_000)  # about 10 ms of GPU time ahead of the call
+            r_dev = src * 1.0
+            k_dev = torch.full((M,), float("nan"), dtype=torch.float64, device="cuda")
+        st = lib.mgwr_inverse_column_noalloc(C.c_void_p(r_dev.data_ptr()), M, sigma,
+                                             C.c_void_p(k_dev.data_ptr()),
+                                             C.c_void_p(side.cuda_stream))
+        assert st == G.MGWR_OK
+        side.synchronize()
+        outs.append(k_dev.cpu().numpy())
+    for k, ref in zip(outs, reversed(refs)):
+        assert _close(k, ref)
 
 
 def test_noalloc_rejects_sizes_beyond_its_array():

@@ -1,23 +1,27 @@
 """Benchmark: space-time unknowns per second of MGWR solves on GB300.
 
-Default workload (one "step" = one complete solve): 2-D plain MGWR, 255 x 255
-interior grid, M = 1024 time steps on (0, 1], alpha = 0.5, exact solution
-u = t^2 sin(pi x) sin(pi y) (f from D^a t^2 = 2 t^(2-a) / Gamma(3-a)),
-5-point Laplacian, V(1,1) red-black cycles from u = 0 until the relative
-infinity-norm defect is below 1e-10, FP64.  6.66e7 space-time unknowns; each
-FP64 field is 533 MB, larger than the 129 MB L2, so no flush is needed
-between steps.  Other workloads (--workload): 1d-63-m64 (1-D 63 points, M = 64),
-2d-511-m4096 (2-D 511 x 511, M = 4096, u = t^alpha sin sin, mixed to 1e-8),
-batch4096-2d-63-m256
-(4096 independent 2-D 63 x 63, M = 256 solves with alpha ~ U[0.1, 0.9] in one
-batched handle, mixed to 1e-8), 1d-4095-m65536 (1-D 4095 points, M = 65536, alpha = 0.2,
+Default workload (one "step" = one complete solve): 2-D MGWR, 511 x 511
+interior grid, M = 4096 time steps on (0, 1], alpha = 0.5, exact solution
+u = t^alpha sin(pi x) sin(pi y) (f from D^a t^a = Gamma(1+a)), 5-point
+Laplacian, V(1,1) red-black cycles from u = 0 until the relative
+infinity-norm defect is below 1e-8.  1.07e9 space-time unknowns; each FP64
+field is 8.56 GB, far larger than the 129 MB L2, so no flush is needed between
+steps.  `value` is the mixed form with FP32 cycles and an FP64 outer defect and
+update (MGWR_MIXED); the same line carries the plain FP64 solve and the mixed
+form with a double-float outer defect (MGWR_MIXED_DD) on the same workload
+(--arms), each with its error against the oracle's exact discrete solution and
+the IEEE-double defect of its result.  Other workloads (--workload):
+2d-255-m1024 (2-D 255 x 255, M = 1024, u = t^2 sin sin, FP64 to 1e-10),
+1d-63-m64 (1-D 63 points, M = 64), batch4096-2d-63-m256 (4096 independent 2-D
+63 x 63, M = 256 solves with alpha ~ U[0.1, 0.9] in one batched handle, mixed
+to 1e-8), 1d-4095-m65536 (1-D 4095 points, M = 65536, alpha = 0.2,
 u = t^alpha sin, to 1e-8 with double-float inner cycles, as FP32 inner cycles
 stall on h = 1/4096; --precision fp64 for the FP64 form) and served (the served
 request stream; each request's precision chosen by MGWR_AUTO).
 
   python bench.py [--gpus N] [--steps K] [--warmup W]
-                  [--precision fp64|mixed|mixed_dd|dd|auto]
-                  [--workload 2d-255-m1024|1d-63-m64|2d-511-m4096|
+                  [--precision fp64|mixed|mixed_dd|dd|auto] [--arms P,P]
+                  [--workload 2d-511-m4096|2d-255-m1024|1d-63-m64|
                               batch4096-2d-63-m256|1d-4095-m65536|served]
   python bench.py --impl reference ...   (the CPU oracle on the host cores)
 
@@ -42,15 +46,16 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-D, NPTS, M, T, ALPHA, TOL = 2, 255, 1024, 1.0, 0.5, 1e-10
+T, ALPHA = 1.0, 0.5
 NU1, NU2, CYCLE = 1, 1, 1
-METRIC = "space-time unknowns/s to rel-res 1e-10 (FP64 vs mixed)"
+METRIC = "space-time unknowns/s to rel-res 1e-8 (FP64 vs mixed); served p50/p99 latency"
+DEFAULT_WORKLOAD = "2d-511-m4096"
 # workload name -> (d, n, M, batch, exact solution, tolerance, default precision, description)
 WORKLOADS = {
     "2d-255-m1024": (2, 255, 1024, 1, "t2", 1e-10, "fp64",
            "2-D plain MGWR 255x255 interior, M=1024 on (0,1], u=t^2 sin(pi x) sin(pi y)"),
     "1d-63-m64": (1, 63, 64, 1, "t2", 1e-10, "fp64", "1-D plain MGWR 63 interior points, M=64, u=t^2 sin(pi x)"),
-    "2d-511-m4096": (2, 511, 4096, 1, "talpha", 1e-8, "mixed_dd",
+    "2d-511-m4096": (2, 511, 4096, 1, "talpha", 1e-8, "mixed",
            "2-D MGWR 511x511 interior, M=4096, u=t^alpha sin(pi x) sin(pi y)"),
     "batch4096-2d-63-m256": (2, 63, 256, 4096, "t2", 1e-8, "mixed_dd",
             "4096 independent 2-D 63x63, M=256 solves, alpha~U[0.1,0.9] (seed 1608), one batched handle"),
@@ -65,8 +70,13 @@ WORKLOADS = {
 WORKLOAD_ALPHA = {"1d-4095-m65536": 0.2}
 # FP32 cycles per outer defect of a mixed workload when --inner is not given
 WORKLOAD_INNER = {"batch4096-2d-63-m256": 4}
-# oracle time steps in the CPU-baseline sample (about 10-30 s of host work)
-ORACLE_SAMPLE_STEPS = {"2d-255-m1024": 256, "1d-4095-m65536": 2048}
+# extra precisions timed beside the value on the same workload, and their steps
+WORKLOAD_ARMS = {"2d-511-m4096": ("fp64", "mixed_dd")}
+# CPU-baseline sample: a complete oracle solve (every time level) of the workload's
+# spatial grid with this many time steps on the same (0, T] (a few seconds of host
+# work); the --impl reference arm times the same sample
+ORACLE_SAMPLE_M = {"2d-511-m4096": 32, "2d-255-m1024": 128, "1d-63-m64": 64,
+                   "batch4096-2d-63-m256": 256, "1d-4095-m65536": 512}
 UNIT = "unknowns/s"
 # --precision names and the library's codes (MGWR_FP64 .. MGWR_AUTO)
 PREC_CODES = {"fp64": 0, "mixed": 1, "mixed_dd": 2, "dd": 3, "auto": 4}
@@ -81,10 +91,15 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # chain: 1.20 TFLOP/s at 1995 MHz on 152 SMs); peak at the maximum clock.
 FP64_FMA_PER_CLK_PER_SM = 2
 SMS = 152
+# FP32 lanes of a GB300 SM (4 partitions x 32)
+FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) per smoothed line of k_sweep<double> from an ncu
 # capture of the finest-level half-sweep of the default workload (772.5 MB for
 # 32,513 lines of 1024 doubles; profiles/k_sweep_fp64_2d_255x255_M1024.md).
 SWEEP64_DRAM_BYTES_PER_LINE_M1024 = 23758.0
+# DRAM bytes per line of further kernels from single-kernel ncu captures (see
+# profiles/), by kernel class and M
+NCU_DRAM_BYTES_PER_LINE: dict = {}
 
 
 def parse():
@@ -94,7 +109,14 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--precision", default=None, choices=["fp64", "mixed", "mixed_dd", "dd", "auto"])
-    p.add_argument("--workload", default="2d-255-m1024", choices=sorted(WORKLOADS))
+    p.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    p.add_argument("--arms", default=None,
+                   help="comma-separated precisions timed beside the value on the same "
+                        "workload (default: the workload's list; 'none' for none)")
+    p.add_argument("--arm-steps", type=int, default=None,
+                   help="timed steps of each extra arm (default: fewer for slow arms)")
+    p.add_argument("--e2e-steps", type=int, default=None,
+                   help="timed steps of the end-to-end measurement (default min(steps, 5))")
     p.add_argument("--requests", type=int, default=200, help="served: first R requests of the stream")
     p.add_argument("--slots", type=int, default=4, help="served: server slots")
     p.add_argument("--rate", type=float, default=None,
@@ -287,75 +309,137 @@ def defect_flops_per_line(d: int, Mv: int) -> float:
     return conv_flops_per_line(Mv) + (2 * d + 4) * Mv
 
 
+def fp64_peak_tflops(pk: dict) -> float:
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    return SMS * FP64_FMA_PER_CLK_PER_SM * 2 * sm_max * 1e6 / 1e12
+
+
+def fp32_peak_tflops(pk: dict) -> float:
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    return SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+
+
+# kernel class -> (kernel name, word bytes of its fields, sweep or defect)
+CLASS_KERNELS = {
+    "sweep64": ("k_sweep<double>", 8, "sweep"), "sweep32": ("k_sweep<float>", 4, "sweep"),
+    "sweep_dd": ("k_sweep<dd>", 8, "sweep"), "defect64": ("k_defect<double>", 8, "defect"),
+    "defect32": ("k_defect<float> / k_defect_hybrid", 4, "defect"),
+    "defect_dd": ("k_defect<dd>", 8, "defect"),
+}
+
+
+def kernel_roofline(cls: str, p: dict, d: int, M: int, pk: dict) -> dict:
+    """Roofline of one kernel class from its summed event-timed launches: the
+    FP64 kernels against the FP64 ALU peak (GB300 runs FP64 at 1/64 of FP32),
+    the FP32 and line kernels against HBM with the FP32-issue view beside."""
+    secs = p["ms"] * 1e-3
+    name, word, kind = CLASS_KERNELS.get(cls, (cls, 8, "line"))
+    long = M > 4096
+    if long and kind != "line":
+        name = f"k_long_forward+k_long_inverse ({name})"
+    per_line = (sweep_flops_per_line(d, M) if kind == "sweep" else defect_flops_per_line(d, M)) \
+        if kind != "line" else 0.0
+    flops = p["lines"] * per_line
+    # algorithmic bytes: a sweep reads f and one line of the other colour and writes
+    # its line; a defect reads u and f and writes r (the FP64 outer defect of the
+    # mixed form writes FP32); line kernels: three words per line value
+    if kind == "defect":
+        bytes_per_line = (2 * word + (4 if cls == "defect64" else word)) * M
+    else:
+        bytes_per_line = 3 * word * M
+    bytes_alg = p["lines"] * bytes_per_line
+    hbm = bytes_alg / secs / 1e9
+    hbm_peak = float(pk.get("hbm_gbs", 6800.0))
+    out = {"kernel": name, "class": cls, "launches": p["launches"],
+           "avg_launch_ms": p["ms"] / max(p["launches"], 1),
+           "lines_per_launch": p["lines"] / max(p["launches"], 1),
+           "bytes_per_line": bytes_per_line, "flops_per_line": per_line}
+    if cls in ("sweep64", "defect64"):
+        peak = fp64_peak_tflops(pk)
+        achieved = flops / secs / 1e12
+        out.update({"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak,
+                    "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x max SM clock "
+                                   "(FMA-chain probe: 1.20 TFLOP/s at 1995 MHz)",
+                    "hbm_view": {"achieved_gbs": hbm, "peak_gbs": hbm_peak, "frac": hbm / hbm_peak}})
+    else:
+        out.update({"bound": "hbm", "achieved": hbm, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": hbm / hbm_peak, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"})
+        if per_line:
+            fl = flops / secs / 1e12
+            out["fp32_issue_view"] = {"achieved_tflops": fl, "peak_tflops": fp32_peak_tflops(pk),
+                                      "frac": fl / fp32_peak_tflops(pk),
+                                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop "
+                                                     "x max SM clock"}
+    out["traffic"] = None
+    if cls == "sweep64" and M == 1024:
+        out["traffic"] = SWEEP64_DRAM_BYTES_PER_LINE_M1024 * out["lines_per_launch"]
+        out["traffic_note"] = "ncu dram bytes per line x lines per launch"
+    elif cls in NCU_DRAM_BYTES_PER_LINE and M in NCU_DRAM_BYTES_PER_LINE[cls]:
+        out["traffic"] = NCU_DRAM_BYTES_PER_LINE[cls][M] * out["lines_per_launch"]
+        out["traffic_note"] = "ncu dram bytes per line (small-case capture) x lines per launch"
+    return out
+
+
 def roofline_from_profile(prof: dict, d: int, M: int, pk: dict) -> dict:
     dom = max(prof, key=lambda k: prof[k]["ms"])
-    p = prof[dom]
-    sm_max = float(pk.get("sm_max_mhz", 2070.0))
-    if dom in ("sweep64", "defect64"):
-        per_line = sweep_flops_per_line(d, M) if dom == "sweep64" else defect_flops_per_line(d, M)
-        flops = p["lines"] * per_line
-        achieved = flops / (p["ms"] * 1e-3) / 1e12
-        peak = SMS * FP64_FMA_PER_CLK_PER_SM * 2 * sm_max * 1e6 / 1e12
-        word = 8
-        bytes_alg = p["lines"] * 3 * word * M  # f, one line of the other colour, the output
-        hbm = bytes_alg / (p["ms"] * 1e-3) / 1e9
-        lines_per_launch = p["lines"] / max(p["launches"], 1)
-        traffic = (SWEEP64_DRAM_BYTES_PER_LINE_M1024 * lines_per_launch
-                   if dom == "sweep64" and M == 1024 else None)
-        long = M > 4096
-        kname = ("k_long_forward+k_long_inverse<double>" if long else "k_sweep<double>") \
-            if dom == "sweep64" else ("k_long_forward+k_long_inverse<double>" if long else "k_defect<double>")
-        return {"kernel": kname,
-                "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "traffic_note": "ncu dram bytes per line x lines per launch" if traffic else None,
-                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x max SM clock",
-                "launches": p["launches"], "avg_launch_ms": p["ms"] / max(p["launches"], 1),
-                "hbm_view": {"achieved_gbs": hbm, "peak_gbs": pk.get("hbm_gbs"),
-                             "frac": hbm / pk["hbm_gbs"] if pk.get("hbm_gbs") else None}}
-    word = 4 if dom.endswith("32") else 8
-    bytes_per_line = 3 * word * M
-    bytes_alg = p["lines"] * bytes_per_line
-    achieved = bytes_alg / (p["ms"] * 1e-3) / 1e9
-    peak = float(pk.get("hbm_gbs", 6800.0))
-    return {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": None, "launches": p["launches"],
-            "avg_launch_ms": p["ms"] / max(p["launches"], 1)}
+    return kernel_roofline(dom, prof[dom], d, M, pk)
 
 
-def cpu_oracle_sample(d: int, n: int, Mv: int, alpha: float, kind: str, steps_in_time: int):
-    """The CPU oracle (direct L1 time stepping) on the full grid for the first
-    `steps_in_time` of the M time levels."""
+def oracle_threads() -> int:
+    """Threads the oracle's library calls may use (its BLAS pool), else the host's CPUs."""
+    try:
+        from threadpoolctl import threadpool_info
+        return max(int(x.get("num_threads", 1)) for x in threadpool_info()) or os.cpu_count()
+    except Exception:  # noqa: BLE001 - optional helper, absent on some hosts
+        return os.cpu_count()
+
+
+def cpu_oracle_sample(d: int, n: int, Ms: int, alpha: float, kind: str):
+    """One complete CPU-oracle solve (direct L1 time stepping over every time
+    level) of the workload's spatial grid with Ms time steps on the same (0, T]."""
     from oracle import direct
     from paper_1608_05400_gb300 import inputs
 
-    prob = inputs.Problem(d, n, Mv, T, alpha, kind)
+    prob = inputs.Problem(d, n, Ms, T, alpha, kind)
     f = prob.rhs()
     t0 = time.perf_counter()
-    direct.time_stepping(d, n, Mv, T, alpha, f, steps=steps_in_time)
+    direct.time_stepping(d, n, Ms, T, alpha, f)
     dt = time.perf_counter() - t0
-    unknowns = prob.N * steps_in_time
     grid = f"{n}x{n}" if d == 2 else f"{n}-point"
-    return {"value": unknowns / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"direct L1 time stepping (sparse LU per step + history sums) on the full "
-                      f"{grid} grid, first {steps_in_time} of {Mv} time levels "
-                      f"({dt:.1f} s; later levels cost more: the history sum grows with the step)"}
+    return {"value": prob.unknowns / dt, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
+            "sample": f"full solve: direct L1 time stepping (sparse LU of r_1 I + A_h once, then "
+                      f"every one of the {Ms} time levels with its history sum) of the "
+                      f"{grid} grid, M={Ms} on (0,{T:g}], alpha={alpha}, {kind} source, "
+                      f"{prob.unknowns} unknowns in {dt:.2f} s"}
 
 
-def cpu_baseline_leg(u: np.ndarray, d: int, n: int, Mv: int, alpha: float, kind: str, steps: int):
-    """The CPU-baseline leg: the oracle timed on a bounded sample, and the GPU
-    result's error against the oracle's exact discrete solution of this
-    workload (separable source: one triangular solve in time)."""
+def oracle_time_factors(d: int, n: int, Mv: int, alphas, kind: str) -> np.ndarray:
+    """The oracle's exact discrete solution of each instance's separable source:
+    u_b = w_b(t) phi(x) with (T_M + lambda_h I) w_b = F_b (one triangular solve)."""
     from oracle import separable
     from paper_1608_05400_gb300 import inputs
 
-    base = cpu_oracle_sample(d, n, Mv, alpha, kind, steps)
-    prob = inputs.Problem(d, n, Mv, T, alpha, kind)
-    w = separable.time_factor(d, n, Mv, T, alpha, prob.rhs_profile())
-    ph = inputs.phi(d, n)
-    # max |u - phi w| / max |phi w| row by row, without a second full field
-    err = max(float(np.abs(u[p] - ph[p] * w).max()) for p in range(u.shape[0]))
-    return base, err / float(np.abs(ph).max() * np.abs(w).max())
+    return np.stack([separable.time_factor(d, n, Mv, T, float(a),
+                                           inputs.Problem(d, n, Mv, T, float(a), kind).rhs_profile())
+                     for a in alphas])
+
+
+def rel_err_device(torch, u, phi, W) -> float:
+    """max over instances of max |u_b - phi w_b| / max |phi w_b|, on the device in
+    blocks (u: (B, N, M) or (N, M) device tensor; W: (B, M) host array)."""
+    Wd = torch.from_numpy(W).to(u.device)
+    ub = u.reshape(Wd.shape[0], -1, Wd.shape[1])
+    worst = 0.0
+    rows = max(1, (1 << 27) // (ub.shape[1] * ub.shape[2]))
+    for b0 in range(0, ub.shape[0], rows):
+        ref_scale = phi.abs().max() * Wd[b0:b0 + rows].abs().amax(dim=1)
+        err = torch.zeros_like(ref_scale)
+        for a in range(0, ub.shape[1], 4096):
+            ref = phi[None, a:a + 4096, None] * Wd[b0:b0 + rows, None, :]
+            err = torch.maximum(err, (ub[b0:b0 + rows, a:a + 4096] - ref).abs().amax(dim=(1, 2)))
+        worst = max(worst, float((err / ref_scale).max()))
+    return worst
 
 
 def fas_line_flops(Mv: int) -> float:
@@ -507,28 +591,46 @@ def run_nonlinear(args):
     return 0
 
 
+def workload_config(name: str, d: int, n: int, Mw: int, batch: int, tol: float, desc: str,
+                    alpha, precision: str, world: int) -> dict:
+    return {"workload": f"{desc}, " + (f"alpha={alpha}, " if batch == 1 else "")
+                        + f"V({NU1},{NU2}) red-black, rel-res {tol}",
+            "name": name, "precision": precision,
+            "parallelism": "replicas" if world > 1 else "single",
+            "l2": f"inputs larger than L2 ({batch * n ** d * Mw * 8 / 1e6:.0f} MB per FP64 field)"}
+
+
 def run_reference(args):
+    """The reference arm: there is no reference implementation of this method, so
+    the CPU oracle stands in for it, timed as it is on the host cores.  Each step
+    is one complete oracle solve of the workload's grid at the CPU-baseline
+    sample's number of time steps."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    base = {"impl": "reference", "metric": METRIC, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True}
+    d, n, Mw, batch, kind, tol, prec, desc = WORKLOADS[args.workload]
+    if args.workload not in ORACLE_SAMPLE_M:
+        print(json.dumps({"impl": "reference", "unavailable": f"no oracle sample for {args.workload}"}))
+        return 0
+    alpha = args.alpha if args.alpha is not None else WORKLOAD_ALPHA.get(args.workload, ALPHA)
+    Ms = ORACLE_SAMPLE_M[args.workload]
     for _ in range(args.warmup):
-        cpu_oracle_sample(D, NPTS, M, ALPHA, "t2", 16)
+        cpu_oracle_sample(d, n, Ms, alpha, kind)
     vals = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        vals.append(cpu_oracle_sample(D, NPTS, M, ALPHA, "t2", 32))
+        vals.append(cpu_oracle_sample(d, n, Ms, alpha, kind))
     dt = time.perf_counter() - t0
-    v = statistics.median(x["value"] for x in vals)
-    out = dict(base, value=v, ms_per_step=1e3 * dt / args.steps, scaling="weak", vs_baseline=None,
-               dtype="f64", data="synthetic",
-               config={"workload": f"{WORKLOADS['2d-255-m1024'][7]}, alpha={ALPHA}, "
-                                   f"V({NU1},{NU2}) red-black, rel-res {TOL}",
-                       "name": "2d-255-m1024", "precision": "fp64",
-                       "parallelism": "replicas" if args.gpus > 1 else "single"},
-               cpu_baseline=dict(vals[0], value=v),
-               e2e={"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0})
+    unknowns = n ** d * Ms
+    v = args.steps * unknowns / dt
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": workload_config(args.workload, d, n, Mw, batch, tol, desc, alpha,
+                                     args.precision or prec, args.gpus),
+           "cpu_baseline": dict(vals[0], value=v),
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
     return 0
 
@@ -646,6 +748,113 @@ def run_served(args):
     return 0
 
 
+def measure_arm(args, torch, mgwr, wl: dict, precision: str, steps: int, warmup: int,
+                e2e_steps: int, stream, world: int, local: int, W=None, main_arm=False) -> dict:
+    """Times `steps` complete solves of the workload in one precision: inputs
+    resident on the device, CUDA events on the handle's stream, launch shapes
+    tuned first.  The main arm also samples clocks, profiles one extra solve per
+    kernel class and runs the end-to-end loop through host buffers."""
+    d, n, Mw, batch, tol = wl["d"], wl["n"], wl["M"], wl["batch"], wl["tol"]
+    s = mgwr.Solver(d, n, Mw, T, wl["alpha"])
+    s.set_stream(stream.cuda_stream)
+    if precision != "fp64":
+        s.set_precision(PREC_CODES[precision])
+        precision = PREC_NAMES[s.precision()]  # MGWR_AUTO resolves on this grid
+    mixed = precision in ("mixed", "mixed_dd")
+    inner = args.inner or WORKLOAD_INNER.get(args.workload)
+    if mixed and inner:
+        s.set_inner_cycles(inner)
+    # launch shapes of the FFT-engine kernels, timed on this handle's data (setup,
+    # outside the timed region)
+    splits = None if args.no_autotune else s.autotune()
+    if args.split:
+        for cls, val in parse_splits(args.split, mgwr.KERNEL_CLASSES).items():
+            s.set_engine_split(cls, val)
+        splits = dict(splits or {}, forced=args.split)
+    f_dev = wl["f_dev"]
+
+    def step():
+        s.set_rhs_dev(f_dev.data_ptr())
+        return s.solve(CYCLE, NU1, NU2, tol, 100)
+
+    for _ in range(warmup):
+        step()
+    l0 = mgwr.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clk = ClockSampler(local) if main_arm else None
+    if clk is not None:
+        clk.__enter__()
+    try:
+        rank_barrier(world)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        stats = [step() for _ in range(steps)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        rank_barrier(world)
+    finally:
+        if clk is not None:
+            clk.__exit__(None, None, None)
+    launches = mgwr.launch_count() - l0
+    t_max = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
+    out = {"precision": precision, "dtype": DTYPES[precision],
+           "value": job_throughput(world, wl["unknowns"], steps, t_max), "unit": UNIT,
+           "steps": steps, "warmup": warmup, "ms_per_step": t_max / steps,
+           "solve": {"cycles": stats[-1].cycles, "outer": stats[-1].outer,
+                     "relres": stats[-1].relres, "factor": stats[-1].factor},
+           "gpu_launches": launches, "engine_splits": splits,
+           "inner_cycles": (inner or 2) if mixed else None}
+    if clk is not None:
+        out["clocks"] = clk.summary()
+    # the IEEE-double defect of the result, recomputed in FP64 whatever the precision
+    out["solve"]["relres_fp64"] = s.residual()
+    if W is not None:
+        u = torch.empty((batch, n ** d, Mw), dtype=torch.float64, device="cuda")
+        s.solution_dev(u.data_ptr())
+        torch.cuda.synchronize()
+        out["solve"]["rel_err_vs_oracle"] = rel_err_device(torch, u, wl["phi_dev"], W)
+        del u
+    if main_arm:
+        # per-kernel-class times from one profiled solve (outside the timed region)
+        s.profile(True)
+        step()
+        out["kernel_classes"] = {k: v for k, v in s.profile_read().items() if v["launches"]}
+        s.profile(False)
+    if e2e_steps > 0 and wl.get("f_host") is not None:
+        with GpuLocalHost(local) as host:
+            pin_f = torch.from_numpy(wl["f_host"]).pin_memory()
+            pin_u = torch.empty_like(pin_f).pin_memory()
+            fp, up = pin_f.numpy(), pin_u.numpy()
+            ee0, ee1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+            def e2e_step():
+                s.set_rhs(fp)
+                s.solve(CYCLE, NU1, NU2, tol, 100)
+                s.lib.mgwr_get_solution(s.h, up.ctypes.data_as(mgwr._dp))
+
+            # untimed warm-up through the same path: the profiled solve above ran
+            # without graphs, so the first steps after it capture them again
+            for _ in range(max(min(warmup, 2), 1)):
+                e2e_step()
+            rank_barrier(world)
+            torch.cuda.synchronize()
+            ee0.record(stream)
+            for _ in range(e2e_steps):
+                e2e_step()
+            ee1.record(stream)
+            torch.cuda.synchronize()
+            ems = max_over_ranks(ee0.elapsed_time(ee1), world, "cuda")
+            nbytes = wl["unknowns"] * 8
+            out["e2e"] = {"value": job_throughput(world, wl["unknowns"], e2e_steps, ems),
+                          "unit": UNIT, "steps": e2e_steps,
+                          "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+                          "host_buffers": (f"pinned, first touched on the {len(host.cpus)} "
+                                           f"GPU-local CPUs" if host.cpus else "pinned")}
+            del pin_f, pin_u
+    s.close()
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -665,7 +874,8 @@ def main():
     from paper_1608_05400_gb300 import inputs, mgwr
 
     d, n, Mw, batch, kind, tol, prec_default, desc = WORKLOADS[args.workload]
-    if args.shape or args.batch:
+    profiling_case = bool(args.shape or args.batch)
+    if profiling_case:
         if args.shape:
             d, n, Mw = (int(x) for x in args.shape.split(","))
         batch = args.batch or batch
@@ -673,133 +883,71 @@ def main():
         args.no_cpu = True
     precision = args.precision or prec_default
     alpha = args.alpha if args.alpha is not None else WORKLOAD_ALPHA.get(args.workload, ALPHA)
+    ph = torch.from_numpy(inputs.phi(d, n)).cuda()
     if batch == 1:
-        prob = inputs.Problem(d, n, Mw, T, alpha, kind)
-        f_host = prob.rhs()
-        f_dev = torch.from_numpy(f_host).cuda()
-        s = mgwr.Solver(d, n, Mw, T, alpha)
-        unknowns = prob.unknowns
+        alphas = np.array([alpha])
+        F = inputs.Problem(d, n, Mw, T, alpha, kind).rhs_profile()[None, :]
     else:
-        # per-instance sources built on the device: f_b = F_b(t) phi(x)
         alphas = inputs.random_alphas(batch, seed=1608)
         F = np.stack([inputs.Problem(d, n, Mw, T, float(a), kind).rhs_profile() for a in alphas])
-        ph = torch.from_numpy(inputs.phi(d, n)).cuda()
-        f_dev = ph[None, :, None] * torch.from_numpy(F).cuda()[:, None, :]
-        f_host = None
-        s = mgwr.Solver(d, n, Mw, T, alphas)
-        unknowns = batch * n ** d * Mw
+    # f_b = F_b(t) phi(x), built on the device (and on the host for the e2e loop)
+    f_dev = (ph[None, :, None] * torch.from_numpy(F).cuda()[:, None, :]).reshape(-1, Mw)
+    unknowns = batch * n ** d * Mw
+    wl = {"d": d, "n": n, "M": Mw, "batch": batch, "tol": tol, "unknowns": unknowns,
+          "alpha": alpha if batch == 1 else alphas, "f_dev": f_dev, "phi_dev": ph}
+    e2e_steps = 0 if args.no_e2e else (args.e2e_steps or min(args.steps, 5))
+    if e2e_steps and batch == 1:
+        wl["f_host"] = f_dev.cpu().numpy()
+    cpu_leg = not args.no_cpu and world == 1
+    W = oracle_time_factors(d, n, Mw, alphas, kind) if cpu_leg else None
     stream = torch.cuda.Stream()
-    s.set_stream(stream.cuda_stream)
-    if precision != "fp64":
-        s.set_precision(PREC_CODES[precision])
-        precision = PREC_NAMES[s.precision()]  # MGWR_AUTO resolves on this grid
-    mixed = precision in ("mixed", "mixed_dd")
-    inner = args.inner or WORKLOAD_INNER.get(args.workload)
-    if mixed and inner:
-        s.set_inner_cycles(inner)
+    warmup = max(args.warmup, 3) if args.warmup >= 3 else args.warmup
 
-    # launch shapes of the FFT-engine kernels, timed on this handle's data (setup,
-    # outside the timed region)
-    splits = None if args.no_autotune else s.autotune()
-    if args.split:
-        for cls, val in parse_splits(args.split, mgwr.KERNEL_CLASSES).items():
-            s.set_engine_split(cls, val)
-        splits = dict(splits or {}, forced=args.split)
-
-    def step():
-        s.set_rhs_dev(f_dev.data_ptr())
-        return s.solve(CYCLE, NU1, NU2, tol, 100)
-
-    for _ in range(max(args.warmup, 3) if args.warmup >= 3 else args.warmup):
-        st = step()
-    barrier = lambda: rank_barrier(world)  # noqa: E731
-
-    l0 = mgwr.launch_count()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        barrier()
-        torch.cuda.synchronize()
-        with torch.cuda.stream(stream):
-            e0.record(stream)
-        stats = []
-        for _ in range(args.steps):
-            stats.append(step())
-        e1.record(stream)
-        torch.cuda.synchronize()
-        barrier()
-    launches = mgwr.launch_count() - l0
-    t_max = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
-    value = job_throughput(world, unknowns, args.steps, t_max)
-
-    u = s.solution() if batch == 1 else None
-    # per-kernel-class times from one profiled solve (outside the timed region)
-    s.profile(True)
-    step()
-    prof = s.profile_read()
-    s.profile(False)
-
-    e2e = None
-    if not args.no_e2e and f_host is not None:
-        with GpuLocalHost(local) as host:
-            pin_f = torch.from_numpy(f_host).pin_memory()
-            pin_u = torch.empty_like(pin_f).pin_memory()
-            fp = pin_f.numpy()
-            up = pin_u.numpy()
-            ee0, ee1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-
-            def e2e_step():
-                s.set_rhs(fp)
-                s.solve(CYCLE, NU1, NU2, tol, 100)
-                s.lib.mgwr_get_solution(s.h, up.ctypes.data_as(mgwr._dp))
-
-            # untimed warm-up through the same path: the profiled solve above ran without
-            # graphs, so the first steps after it capture them again
-            for _ in range(max(args.warmup, 1)):
-                e2e_step()
-            barrier()
-            torch.cuda.synchronize()
-            ee0.record(stream)
-            for _ in range(args.steps):
-                e2e_step()
-            ee1.record(stream)
-            torch.cuda.synchronize()
-            ems = max_over_ranks(ee0.elapsed_time(ee1), world, "cuda")
-            nbytes = unknowns * 8
-            e2e = {"value": job_throughput(world, unknowns, args.steps, ems), "unit": UNIT,
-                   "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
-                   "host_buffers": (f"pinned, first touched on the {len(host.cpus)} GPU-local CPUs"
-                                    if host.cpus else "pinned")}
-    s.close()
+    main_arm = measure_arm(args, torch, mgwr, wl, precision, args.steps, warmup, e2e_steps,
+                           stream, world, local, W=W, main_arm=True)
+    arms = []
+    if args.arms is not None:
+        arms = [] if args.arms == "none" else [a.strip() for a in args.arms.split(",") if a.strip()]
+    elif not profiling_case and args.precision is None:
+        arms = list(WORKLOAD_ARMS.get(args.workload, ()))
+    arm_out = {}
+    for a in arms:
+        if a == main_arm["precision"]:
+            continue
+        # the FP64 arm of the largest workload takes seconds per solve: fewer steps
+        k = args.arm_steps or (min(args.steps, 2) if a == "fp64" else min(args.steps, 5))
+        w = min(warmup, 1) if a == "fp64" else min(warmup, 3)
+        arm_out[a] = measure_arm(args, torch, mgwr, wl, a, k, w, 0, stream, world, local, W=W)
+    del f_dev, wl["f_dev"]
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
         return 0
     pk = peaks()
+    prof = main_arm.pop("kernel_classes")
     out = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
-        "dtype": DTYPES[precision],
-        "data": "synthetic",
-        "config": {"workload": f"{desc}, " + (f"alpha={alpha}, " if batch == 1 else "")
-                               + f"V({NU1},{NU2}) red-black, rel-res {tol}",
-                   "name": args.workload, "precision": precision,
-                   "engine_splits": splits,
-                   "inner_cycles": (args.inner or WORKLOAD_INNER.get(args.workload) or 2)
-                   if mixed else None,
-                   "parallelism": "replicas" if world > 1 else "single",
-                   "l2": f"inputs larger than L2 ({unknowns * 8 / 1e6:.0f} MB per FP64 field)"},
-        "solve": {"cycles": stats[-1].cycles, "outer": stats[-1].outer, "relres": stats[-1].relres,
-                  "factor": stats[-1].factor},
-        "gpu_launches": launches,
+        "metric": METRIC, "value": main_arm["value"], "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": warmup, "ms_per_step": main_arm["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": main_arm["dtype"], "data": "synthetic",
+        "config": dict(workload_config(args.workload, d, n, Mw, batch, tol, desc, alpha,
+                                       main_arm["precision"], world),
+                       engine_splits=main_arm["engine_splits"],
+                       inner_cycles=main_arm["inner_cycles"]),
+        "solve": main_arm["solve"],
+        "gpu_launches": main_arm["gpu_launches"],
         "roofline": roofline_from_profile(prof, d, Mw, pk),
-        "kernel_classes": {k: v for k, v in prof.items() if v["launches"]},
-        "clocks": clk.summary(),
-        "e2e": e2e,
+        "kernel_classes": prof,
+        "clocks": main_arm["clocks"],
+        "e2e": main_arm.get("e2e"),
     }
-    if not args.no_cpu and world == 1 and args.workload in ORACLE_SAMPLE_STEPS:
-        out["cpu_baseline"], out["solve"]["rel_err_vs_oracle"] = cpu_baseline_leg(
-            u, d, n, Mw, alpha, kind, ORACLE_SAMPLE_STEPS[args.workload])
+    if "sweep32" in prof and out["roofline"]["class"] != "sweep32":
+        out["roofline_sweep32"] = kernel_roofline("sweep32", prof["sweep32"], d, Mw, pk)
+    for a, res in arm_out.items():
+        res.pop("engine_splits", None)
+        out[f"{a}_arm"] = res
+    if cpu_leg and args.workload in ORACLE_SAMPLE_M:
+        out["cpu_baseline"] = cpu_oracle_sample(d, n, ORACLE_SAMPLE_M[args.workload], alpha, kind)
     print(json.dumps(out))
     if world > 1:
         torch.distributed.destroy_process_group()

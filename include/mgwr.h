@@ -264,6 +264,15 @@ int mgwr_defect(mgwr_t h, int hier, int level, double* norm_inf);
 int mgwr_smooth_defect(mgwr_t h, int hier, int level, double* norm_inf);
 /* f_{level-1} = full weighting of r_level; u_{level-1} = 0 (Algorithm 1). */
 int mgwr_restrict(mgwr_t h, int hier, int level);
+/* Algorithm 1's pre-smoothing step, defect and restriction as the cycle runs
+ * them at `level` >= 1: one smoothing step (red then black half-sweep), then
+ * f_{level-1} = full weighting of the defect f - A u and u_{level-1} = 0.  For
+ * MGWR_H32 the defect is formed inside the restriction from the black
+ * half-sweep's changes (0 at black points, h^-2 times the sum of the black
+ * neighbours' changes at red points) and never stored; for the other
+ * hierarchies it is written to field R first (mgwr_smooth_defect) and then
+ * restricted.  Field R of `level` is left unspecified. */
+int mgwr_smooth_restrict(mgwr_t h, int hier, int level);
 /* u_level += linear / bilinear interpolation of u_{level-1} (Algorithm 1). */
 int mgwr_prolong(mgwr_t h, int hier, int level);
 /* Exact solve on the one-point grid: u_0 = (T_M + 2d/h_0^2 I)^{-1} f_0. */

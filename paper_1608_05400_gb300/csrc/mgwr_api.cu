@@ -1542,6 +1542,19 @@ int mgwr_smooth_defect(mgwr_t h, int hierarchy, int level, double* norm_inf) {
   return MGWR_OK;
 }
 
+int mgwr_smooth_restrict(mgwr_t h, int hierarchy, int level) {
+  if (h == nullptr) return MGWR_E_INVAL;
+  h->u_zero = false;
+  MGWR_TRY(check_level(h, hierarchy, level));
+  if (level == 0) return fail(h, MGWR_E_INVAL, "level 0 has no coarser level");
+  MGWR_TRY(with_hier(h, hierarchy, [&](auto& H) {
+    MGWR_TRY(smooth(h, H, level, 1));
+    return defect_restrict(h, H, level);
+  }));
+  MGWR_CK(h, cudaStreamSynchronize(h->stream));
+  return check_staging(h);
+}
+
 int mgwr_defect(mgwr_t h, int hierarchy, int level, double* norm_inf) {
   if (h == nullptr) return MGWR_E_INVAL;
   MGWR_TRY(check_level(h, hierarchy, level));

@@ -93,6 +93,7 @@ _SIGS = {
     "mgwr_defect": (C.c_int, [_h, C.c_int, C.c_int, _dp]),
     "mgwr_smooth_defect": (C.c_int, [_h, C.c_int, C.c_int, _dp]),
     "mgwr_restrict": (C.c_int, [_h, C.c_int, C.c_int]),
+    "mgwr_smooth_restrict": (C.c_int, [_h, C.c_int, C.c_int]),
     "mgwr_prolong": (C.c_int, [_h, C.c_int, C.c_int]),
     "mgwr_coarsest": (C.c_int, [_h, C.c_int]),
     "mgwr_cycle": (C.c_int, [_h, C.c_int, C.c_int, C.c_int, C.c_int]),
@@ -351,6 +352,9 @@ class Solver:
 
     def restrict(self, hier: int, level: int):
         self._check(self.lib.mgwr_restrict(self.h, hier, level), "mgwr_restrict")
+
+    def smooth_restrict(self, hier: int, level: int):
+        self._check(self.lib.mgwr_smooth_restrict(self.h, hier, level), "mgwr_smooth_restrict")
 
     def prolong(self, hier: int, level: int):
         self._check(self.lib.mgwr_prolong(self.h, hier, level), "mgwr_prolong")

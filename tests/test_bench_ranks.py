@@ -2,6 +2,7 @@
 the barrier, the max-over-ranks timing and the whole-job throughput the GPU
 bench uses under torchrun, and ranks other than 0 of the reference arm exit
 without work.  No GPU: the ranks are host processes."""
+import json
 import os
 import socket
 import subprocess
@@ -66,6 +67,37 @@ def test_reference_arm_ranks_other_than_zero_exit_without_work():
                           "--gpus", "2", "--steps", "1", "--warmup", "3"],
                          capture_output=True, text=True, timeout=120, env=env)
     assert res.returncode == 0 and res.stdout.strip() == ""
+
+
+def test_reference_arm_times_complete_oracle_solves():
+    # the reference arm (the CPU oracle standing in for a reference implementation)
+    # times whole oracle solves of the workload's grid, with the headline metric
+    res = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--workload", "1d-63-m64", "--steps", "2", "--warmup", "0"],
+                         capture_output=True, text=True, timeout=300)
+    assert res.returncode == 0, res.stderr
+    line = json.loads(res.stdout.strip().splitlines()[-1])
+    base = json.load(open(os.path.join(ROOT, "BASELINE.json")))
+    assert line["impl"] == "reference" and line["metric"] == base["metric"]
+    assert line["value"] > 0 and line["steps"] == 2
+    assert line["cpu_baseline"]["sample"].startswith("full solve")
+    assert line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_device_error_helper_matches_numpy():
+    # bench's blockwise error against the separable solution, run on CPU tensors
+    torch = pytest.importorskip("torch")
+    sys.path.insert(0, ROOT)
+    import bench
+    rng = np.random.default_rng(3)
+    B, N, M = 3, 5000, 8
+    phi = rng.uniform(0.1, 1.0, N)
+    W = rng.uniform(-1.0, 1.0, (B, M))
+    u = phi[None, :, None] * W[:, None, :] + rng.uniform(-1e-6, 1e-6, (B, N, M)) * np.arange(1, B + 1)[:, None, None]
+    want = max(np.abs(u[b] - np.outer(phi, W[b])).max() / (np.abs(phi).max() * np.abs(W[b]).max())
+               for b in range(B))
+    got = bench.rel_err_device(torch, torch.from_numpy(u), torch.from_numpy(phi), W)
+    assert got == pytest.approx(want, rel=1e-12)
 
 
 def test_bench_helpers_parse_cpu_lists_and_splits():

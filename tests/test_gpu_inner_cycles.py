@@ -1,0 +1,157 @@
+"""GPU parity of the inner cycles of the refinement modes, through the C ABI.
+
+The mixed modes (MGWR_MIXED, MGWR_MIXED_DD) run their WRMG cycles (Algorithm 1)
+on the FP32 hierarchy and MGWR_DD on the double-float hierarchy.  An outer FP64
+refinement converges to the right answer even when an inner cycle is wrong
+(only more slowly), so these tests compare the inner cycles themselves, iterate
+by iterate, with the oracle's FP64 cycle on the same inputs: V(1,1), V(0,1) and
+W(1,0), 1-D and 2-D, M up to 4096, both FP32 smoother variants the tuner can pick
+(bulk-copy staged input lines, tensor-core dense Toeplitz product) besides the
+FFT engine.  They also compare the fused FP32 defect-restriction kernel, which
+only a cycle reaches, with the oracle's restriction of the defect after one
+smoothing step, and with the unfused kernels bit for bit.
+
+Tolerances.  FP32: every half-sweep and defect rounds each value to about
+eps32 * log2(2M) of its line's scale, and a cycle damps the errors of earlier
+cycles like any other error, so an iterate stays within the per-kernel bound
+of the FP32 component tests (2e-5 of the field's maximum).  Double-float: about
+2^-44 of the scale per transform, 1e-10 of the field's maximum per iterate.
+"""
+import numpy as np
+import pytest
+
+from oracle import mgwr as omg
+from paper_1608_05400_gb300 import inputs
+from paper_1608_05400_gb300 import mgwr as G
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 2e-5
+TOLDD = 1e-10
+
+
+def rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    G.load()
+
+
+# (d, n, M, (nu1, nu2, gamma), cycles compared)
+CASES = [
+    (2, 31, 64, (1, 1, 1), 3),
+    (2, 15, 256, (0, 1, 1), 3),
+    (2, 31, 128, (1, 0, 2), 3),
+    (1, 63, 64, (1, 1, 1), 3),
+    (1, 127, 512, (0, 1, 1), 3),
+    (2, 15, 1024, (1, 1, 1), 2),
+    (2, 15, 4096, (1, 1, 1), 2),
+]
+
+# launch shape of the FP32 sweep: the FFT engine, its bulk-copy staged form, or
+# the tensor-core form (M = 64, 128, 256 only)
+VARIANTS = {"fft": 1, "staged": 1 | G.MGWR_SPLIT_STAGED, "tensor": 1 | G.MGWR_SPLIT_TENSOR}
+
+
+def _run(precision, hier, tol, d, n, M, cyc, count, order, split=None):
+    nu1, nu2, gamma = cyc
+    name = "text" if order == G.MGWR_ORDER_TEXT else "table"
+    W = omg.WRMG(d, n, M, 1.0, 0.6, order=name)
+    with G.Solver(d, n, M, 1.0, 0.6) as s:
+        s.set_precision(precision)
+        s.set_order(order)
+        if split is not None:
+            s.set_engine_split(G.KERNEL_CLASSES.index("sweep32"), split)
+        L = s.num_levels() - 1
+        f = inputs.random_field(n ** d, M, seed=5)
+        if hier == G.MGWR_H32:
+            f = f.astype(np.float32).astype(np.float64)  # the values the FP32 fields hold
+        u = np.zeros_like(f)
+        s.field_set(hier, L, G.MGWR_F, f)
+        s.field_set(hier, L, G.MGWR_U, u)
+        for k in range(count):
+            s.cycle(hier, gamma, nu1, nu2)
+            u = W.cycle(L, u, f, nu1, nu2, gamma)
+            got = s.field_get(hier, L, G.MGWR_U)
+            assert rel(got, u) <= tol, (k, rel(got, u))
+
+
+@pytest.mark.parametrize("variant", sorted(VARIANTS))
+@pytest.mark.parametrize("d,n,M,cyc,count", CASES)
+def test_fp32_cycles_match_oracle_iterates(variant, d, n, M, cyc, count):
+    if variant == "tensor" and M not in (64, 128, 256):
+        pytest.skip("the tensor-core sweep serves M = 64, 128, 256")
+    _run(G.MGWR_MIXED, G.MGWR_H32, TOL32, d, n, M, cyc, count, G.MGWR_ORDER_TEXT,
+         VARIANTS[variant])
+
+
+@pytest.mark.parametrize("d,n,M,cyc,count", CASES)
+def test_double_float_cycles_match_oracle_iterates(d, n, M, cyc, count):
+    _run(G.MGWR_DD, G.MGWR_HDD, TOLDD, d, n, M, cyc, count, G.MGWR_ORDER_TEXT)
+
+
+@pytest.mark.parametrize("hier", [G.MGWR_H32, G.MGWR_HDD])
+def test_inner_cycles_in_table_order(hier):
+    precision, tol = (G.MGWR_MIXED, TOL32) if hier == G.MGWR_H32 else (G.MGWR_DD, TOLDD)
+    _run(precision, hier, tol, 1, 63, 128, (1, 1, 1), 3, G.MGWR_ORDER_TABLE)
+
+
+@pytest.mark.parametrize("d,n,M", [(2, 31, 64), (2, 15, 256), (2, 63, 128), (1, 63, 64),
+                                   (1, 31, 1024), (2, 7, 4096)])
+@pytest.mark.parametrize("order", [G.MGWR_ORDER_TEXT, G.MGWR_ORDER_TABLE])
+def test_fused_restriction_matches_oracle(d, n, M, order):
+    # one smoothing step, then the full weighting of its defect straight from the
+    # black half-sweep's changes (the FP32 cycle's fused kernel): against the
+    # oracle's restriction of its direct-sum defect, and bitwise against the
+    # unfused pair (defect from the changes written out, then restricted)
+    name = "text" if order == G.MGWR_ORDER_TEXT else "table"
+    W = omg.WRMG(d, n, M, 1.0, 0.45, order=name)
+    with G.Solver(d, n, M, 1.0, 0.45) as s:
+        s.set_precision(G.MGWR_MIXED)
+        s.set_order(order)
+        for l in range(1, s.num_levels()):
+            nl = s.level_n(l)
+            u = inputs.random_field(nl ** d, M, seed=100 + l).astype(np.float32).astype(np.float64)
+            f = inputs.random_field(nl ** d, M, seed=200 + l, scale=W.levels[l].sigma)
+            f = f.astype(np.float32).astype(np.float64)
+            s.field_set(G.MGWR_H32, l - 1, G.MGWR_U, np.ones(((nl - 1) // 2) ** d * M).reshape(-1, M))
+            s.field_set(G.MGWR_H32, l, G.MGWR_U, u)
+            s.field_set(G.MGWR_H32, l, G.MGWR_F, f)
+            s.smooth_restrict(G.MGWR_H32, l)
+            fused = s.field_get(G.MGWR_H32, l - 1, G.MGWR_F)
+            assert not s.field_get(G.MGWR_H32, l - 1, G.MGWR_U).any()  # the correction is cleared
+            ref_u = u.copy()
+            W.smooth(l, ref_u, f, 1)
+            ref = omg.restrict_fw(W.defect(l, ref_u, f), d, nl)
+            scale = np.abs(f).max() + W.levels[l].sigma * 2 * np.abs(ref_u).max()
+            assert np.abs(fused - ref).max() <= TOL32 * scale, (l, np.abs(fused - ref).max() / scale)
+            s.field_set(G.MGWR_H32, l, G.MGWR_U, u)
+            s.field_set(G.MGWR_H32, l, G.MGWR_F, f)
+            s.smooth_defect(G.MGWR_H32, l)
+            s.restrict(G.MGWR_H32, l)
+            np.testing.assert_array_equal(fused, s.field_get(G.MGWR_H32, l - 1, G.MGWR_F))
+
+
+@pytest.mark.parametrize("hier", [G.MGWR_H64, G.MGWR_HDD])
+def test_smooth_restrict_on_the_wide_hierarchies(hier):
+    # the same component on the FP64 and double-float hierarchies (defect written,
+    # then restricted) against the oracle
+    d, n, M = 2, 31, 128
+    W = omg.WRMG(d, n, M, 1.0, 0.45)
+    tol = 1e-12 if hier == G.MGWR_H64 else 1e-11
+    with G.Solver(d, n, M, 1.0, 0.45) as s:
+        if hier == G.MGWR_HDD:
+            s.set_precision(G.MGWR_DD)
+        l = s.num_levels() - 1
+        u = inputs.random_field(n ** d, M, seed=7)
+        f = inputs.random_field(n ** d, M, seed=8, scale=W.levels[l].sigma)
+        s.field_set(hier, l, G.MGWR_U, u)
+        s.field_set(hier, l, G.MGWR_F, f)
+        s.smooth_restrict(hier, l)
+        ref_u = u.copy()
+        W.smooth(l, ref_u, f, 1)
+        ref = omg.restrict_fw(W.defect(l, ref_u, f), d, n)
+        scale = np.abs(f).max() + W.levels[l].sigma * 2 * np.abs(ref_u).max()
+        assert np.abs(s.field_get(hier, l - 1, G.MGWR_F) - ref).max() <= tol * scale

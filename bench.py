@@ -124,6 +124,9 @@ def parse():
     p.add_argument("--policy", default="fifo", choices=["fifo", "smallest"],
                    help="served: server admission order")
     p.add_argument("--inner", type=int, default=None, help="mixed modes: FP32 cycles per outer defect")
+    p.add_argument("--outer-switch", type=float, default=None,
+                   help="mixed modes: relative defect at or above which an outer step's defect "
+                        "takes the FP32-convolution form (mgwr_set_outer_switch)")
     p.add_argument("--alpha", type=float, default=None)
     p.add_argument("--no-autotune", action="store_true", help="keep the default engine launch shapes")
     p.add_argument("--split", default=None,
@@ -764,6 +767,8 @@ def measure_arm(args, torch, mgwr, wl: dict, precision: str, steps: int, warmup:
     inner = args.inner or WORKLOAD_INNER.get(args.workload)
     if mixed and inner:
         s.set_inner_cycles(inner)
+    if mixed and args.outer_switch is not None:
+        s.set_outer_switch(args.outer_switch)
     # launch shapes of the FFT-engine kernels, timed on this handle's data (setup,
     # outside the timed region)
     splits = None if args.no_autotune else s.autotune()
@@ -803,17 +808,24 @@ def measure_arm(args, torch, mgwr, wl: dict, precision: str, steps: int, warmup:
            "solve": {"cycles": stats[-1].cycles, "outer": stats[-1].outer,
                      "relres": stats[-1].relres, "factor": stats[-1].factor},
            "gpu_launches": launches, "engine_splits": splits,
-           "inner_cycles": (inner or 2) if mixed else None}
+           "inner_cycles": (inner or (3 if precision == "mixed" else 2)) if mixed else None}
     if clk is not None:
         out["clocks"] = clk.summary()
-    # the IEEE-double defect of the result, recomputed in FP64 whatever the precision
-    out["solve"]["relres_fp64"] = s.residual()
+    field_bytes = wl["unknowns"] * 8
     if W is not None:
         u = torch.empty((batch, n ** d, Mw), dtype=torch.float64, device="cuda")
         s.solution_dev(u.data_ptr())
         torch.cuda.synchronize()
         out["solve"]["rel_err_vs_oracle"] = rel_err_device(torch, u, wl["phi_dev"], W)
         del u
+        torch.cuda.empty_cache()
+    # the IEEE-double defect of the result, recomputed in FP64 whatever the precision
+    # (it needs one more FP64 field on the device)
+    if precision == "fp64" or torch.cuda.mem_get_info()[0] > field_bytes + (2 << 30):
+        out["solve"]["relres_fp64"] = s.residual()
+    else:
+        out["solve"]["relres_fp64"] = None
+        out["solve"]["relres_fp64_note"] = "skipped: no room for one more FP64 field"
     if main_arm:
         # per-kernel-class times from one profiled solve (outside the timed region)
         s.profile(True)

@@ -158,8 +158,20 @@ int mgwr_auto_precision(int d, int n, int M, int precision, int* resolved);
 int mgwr_set_order(mgwr_t h, int order);
 /* cudaStream_t to run on (NULL: the handle's own stream). */
 int mgwr_set_stream(mgwr_t h, void* stream);
-/* Inner FP32 cycles per outer defect in the mixed modes (1..16, default 2). */
+/* Inner cycles per outer defect in the refinements (1..16).  Default: 3 for
+ * MGWR_MIXED, whose FP64 outer defect costs about four FP32 cycles on GB300,
+ * and 2 for MGWR_MIXED_DD and MGWR_DD, whose double-float outer defect costs
+ * about one. */
 int mgwr_set_inner_cycles(mgwr_t h, int cycles);
+/* Mixed modes (MGWR_MIXED, MGWR_MIXED_DD): an outer step that starts from a
+ * relative defect of at least `rel` (default 1e-2; +inf: never) computes the
+ * defect of its result as (f - A_h u) - T_M u with f - A_h u in the outer
+ * precision and T_M u by one FP32 convolution of the rounded iterate.  Its error,
+ * about 1e-6 of |T_M u|, is then far below the defect it drives, so the steps
+ * converge as with the exact defect; every stopping decision is still taken on
+ * the defect in the outer precision.  The paper has no counterpart (its
+ * solver is one precision).  MGWR_E_INVAL for rel < 0 or NaN. */
+int mgwr_set_outer_switch(mgwr_t h, double rel);
 
 /* Launch shape of the FFT-engine kernels (no counterpart in the paper; the
  * results are bitwise the same for every shape).  For kernel class
@@ -187,6 +199,14 @@ int mgwr_set_inner_cycles(mgwr_t h, int cycles);
  * back to the FFT engine.  Its waits give up after half a second, and the call
  * that ran it then returns MGWR_E_CUDA. */
 #define MGWR_SPLIT_TENSOR 32
+/* For MGWR_K_SWEEP32 (not the one-point solve) with 64 <= M <= 4096, `split`
+ * may instead be 1 | MGWR_SPLIT_RADIX: the half-sweep on the register-pass FFT
+ * engine, whose transform of length 2M runs as two or three passes of radix
+ * 4 .. 32 DFTs held in registers (last pass radix 32, spectrum product and
+ * first inverse pass in registers), so every value crosses shared memory once
+ * per pass.  Results agree with the other engine's to FP32 rounding, not
+ * bitwise.  Other lengths fall back to the FFT engine. */
+#define MGWR_SPLIT_RADIX 64
 int mgwr_set_engine_split(mgwr_t h, int kernel_class, int level, int split);
 int mgwr_get_engine_split(mgwr_t h, int kernel_class, int level, int* split);
 /* Tuner: times every E of each engine class the current precision runs (the

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libmgwr.so")
-SOURCES = ["mgwr_sweep.cu", "mgwr_sweep_staged.cu", "mgwr_sweep_tc.cu", "mgwr_defect_f64.cu", "mgwr_defect_f32.cu", "mgwr_defect_dd.cu", "mgwr_defect_ddd.cu",
+SOURCES = ["mgwr_sweep.cu", "mgwr_sweep_rp.cu", "mgwr_sweep_staged.cu", "mgwr_sweep_tc.cu", "mgwr_defect_f64.cu", "mgwr_defect_f32.cu", "mgwr_defect_dd.cu", "mgwr_defect_ddd.cu",
            "mgwr_defect_hybrid.cu", "mgwr_kernels.cu", "mgwr_long.cu", "mgwr_api.cu", "mgwr_noalloc.cu",
            "mgwr_server.cu", "mgwr_fas.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -32,8 +32,9 @@ enum RState {
   R_CURRENT = 3,  // r_l holds the defect of the current (u_l, f_l)
 };
 
-// Relative defect above which an outer step of the mixed modes computes its
-// defect in the FP32-convolution form (launch_defect_hybrid).
+// Default relative defect at or above which an outer step of the mixed modes
+// computes its defect in the FP32-convolution form (launch_defect_hybrid);
+// mgwr_set_outer_switch changes it per handle.
 constexpr double kLooseOuter = 1e-2;
 
 template <class R>
@@ -42,6 +43,7 @@ struct Hier {
   std::vector<R*> dl;             // per level: black-point changes of the last step
   std::vector<int> rs;            // per level: RState of r
   Cx<R>* spec = nullptr;          // batch * nlev * L: spectra of the inverse columns
+  Cx<R>* spec_rp = nullptr;       // the same in the register-pass engine's order (FP32)
   Cx<R>* tspec = nullptr;         // batch * L: spectra of the Toeplitz columns
   Cx<R>* tw = nullptr;            // L twiddles
   R* zero = nullptr;              // M zeros: the neighbour line outside the grid
@@ -55,7 +57,9 @@ struct mgwr_handle {
   int d = 1, n = 1, M = 4, L = 8, nlev = 1, B = 1;
   int Lt = 8;  // transform length of the convolution engine (twiddle table length)
   std::vector<double> alpha, T, c;  // per instance; c = tau^-alpha / Gamma(2 - alpha)
-  int precision = MGWR_FP64, order = MGWR_ORDER_TEXT, inner = 2;
+  int precision = MGWR_FP64, order = MGWR_ORDER_TEXT;
+  int inner = 0;  // inner cycles per outer defect; 0 = the precision's default (inner_cycles)
+  double loose_above = kLooseOuter;  // mgwr_set_outer_switch
   std::vector<int> nl;          // interior points per dimension, level 0 = 1
   std::vector<double> hinv2;    // 1/h_l^2
   std::vector<double> sigma;    // 2d/h_l^2
@@ -260,6 +264,11 @@ int ensure_h32(mgwr_t h) {
   MGWR_CK(h, mgwr::launch_round_cx(H.spec, h->h64.spec, nspec, h->stream));
   MGWR_CK(h, mgwr::launch_round_cx(H.tspec, h->h64.tspec, (size_t)h->B * h->L, h->stream));
   MGWR_CK(h, mgwr::launch_round_cx(H.tw, h->h64.tw, (size_t)h->Lt, h->stream));
+  if (mgwr::radix_length(h->M)) {
+    MGWR_TRY(dev_alloc(h, &H.spec_rp, sizeof(Cx<float>) * nspec));
+    MGWR_CK(h, mgwr::launch_spectra_rp(H.spec_rp, h->h64.spec, (size_t)h->B * h->nlev, h->M,
+                                       h->stream));
+  }
   if (mgwr::tensor_length(h->M)) {
     const size_t lines = (size_t)h->B * h->nlev;
     MGWR_TRY(dev_alloc(h, &h->tc_band, mgwr::tc_band_bytes(h->M) * lines));
@@ -346,7 +355,8 @@ int coarsest(mgwr_t h, Hier<R>& H) {
   const int pm = prof_begin(h, MGWR_K_COARSEST, (double)h->B);
   MGWR_CK(h, mgwr::launch_sweep<R>(H.f[0], H.u[0], (R*)nullptr, H.spec, (size_t)h->nlev * h->L,
                                     H.tw, H.zero, scratch_for<R>(h), shape(h, 0), 0, true, R(0),
-                                    split_of(h, sweep_class<R>(), 0) & ~mgwr::kTensor,
+                                    split_of(h, sweep_class<R>(), 0) &
+                                        ~(mgwr::kTensor | mgwr::kRadix),
                                     h->stream));
   prof_end(h, pm);
   H.rs[0] = R_STALE;
@@ -360,15 +370,20 @@ template <class R>
 cudaError_t level_sweep(mgwr_t h, Hier<R>& H, int l, const R* f, R* u, R* delta,
                         const LevelShape& ls, int par, int E) {
   if constexpr (std::is_same<R, float>::value) {
-    if ((mgwr::effective_split(h->M, 4, E) & mgwr::kTensor) && h->tc_band != nullptr) {
+    const int eff = mgwr::effective_split(h->M, 4, E);
+    if ((eff & mgwr::kTensor) && h->tc_band != nullptr) {
       const size_t bb = mgwr::tc_band_bytes(h->M);
       return mgwr::launch_sweep_tc(f, u, delta, h->tc_band + (size_t)l * bb, (size_t)h->nlev * bb,
                                    ls, par, (float)h->hinv2[l], h->stream);
     }
+    if ((eff & mgwr::kRadix) && H.spec_rp != nullptr)
+      return mgwr::launch_sweep_rp(f, u, delta, H.spec_rp + (size_t)l * h->L,
+                                   (size_t)h->nlev * h->L, H.tw, H.zero, ls, par,
+                                   (float)h->hinv2[l], h->stream);
   }
   return mgwr::launch_sweep<R>(f, u, delta, H.spec + (size_t)l * h->L, (size_t)h->nlev * h->L,
                                H.tw, H.zero, scratch_for<R>(h), ls, par, false, R(h->hinv2[l]),
-                               E & ~mgwr::kTensor, h->stream);
+                               E & ~(mgwr::kTensor | mgwr::kRadix), h->stream);
 }
 
 // One colour half-sweep at level l >= 1; delta != null also records the change of
@@ -590,6 +605,17 @@ int outer_defect_ddd(mgwr_t h) {
   return MGWR_OK;
 }
 
+// Inner cycles per outer defect of the refinements.  Default: 3 for MGWR_MIXED,
+// whose FP64 outer defect costs about four FP32 cycles on GB300 (FP64 runs at
+// 1/64 of the FP32 rate), so fewer outer steps pay (2-D 511 x 511, M = 4096 to
+// 1e-8: 5 outer steps of 2 cycles 1143 ms, 4 of 3 cycles 1024 ms); 2 for the
+// double-float outer defects, which cost about one FP32 cycle (709 against
+// 731 ms on the same solve).
+int inner_cycles(const mgwr_handle* h) {
+  if (h->inner > 0) return h->inner;
+  return h->precision == MGWR_MIXED ? 3 : 2;
+}
+
 // One cycle on hierarchy H and the finest defect norms (from the smoothing
 // changes when the cycle ended with a smoothing step: *exact = false).
 template <class R>
@@ -624,7 +650,7 @@ int enqueue_iteration(mgwr_t h, int cyc, int nu1, int nu2, bool* exact) {
     // double-float iterate, its double-float defect as the next right-hand side
     MGWR_CK(h, cudaMemsetAsync(h->hdd.u[L], 0, cnt * sizeof(mgwr::dd), h->stream));
     h->hdd.rs[L] = R_ZERO_U;
-    for (int k = 0; k < h->inner; ++k) MGWR_TRY(cycle(h, h->hdd, L, cyc, nu1, nu2));
+    for (int k = 0; k < inner_cycles(h); ++k) MGWR_TRY(cycle(h, h->hdd, L, cyc, nu1, nu2));
     const int pm = prof_begin(h, MGWR_K_REFINE, (double)(points(h, L) * h->B));
     MGWR_CK(h, mgwr::launch_refine_dd2(h->u_dd, h->hdd.u[L], cnt, h->stream));
     prof_end(h, pm);
@@ -635,7 +661,7 @@ int enqueue_iteration(mgwr_t h, int cyc, int nu1, int nu2, bool* exact) {
     const bool ddef = h->precision == MGWR_MIXED_DD;
     MGWR_CK(h, cudaMemsetAsync(h->h32.u[L], 0, cnt * sizeof(float), h->stream));
     h->h32.rs[L] = R_ZERO_U;  // f32 holds the outer defect, e32 = 0
-    for (int k = 0; k < h->inner; ++k) MGWR_TRY(cycle(h, h->h32, L, cyc, nu1, nu2));
+    for (int k = 0; k < inner_cycles(h); ++k) MGWR_TRY(cycle(h, h->h32, L, cyc, nu1, nu2));
     const int pm = prof_begin(h, MGWR_K_REFINE, (double)(points(h, L) * h->B));
     if (ddef)
       MGWR_CK(h, mgwr::launch_refine_dd(h->u_dd, h->h32.u[L], cnt, h->stream));
@@ -691,7 +717,7 @@ int run_iteration(mgwr_t h, int cyc, int nu1, int nu2, std::vector<double>& norm
   const int rs_in = h->precision == MGWR_FP64 ? h->h64.rs[h->nlev - 1] : 0;
   const long long key =
       ((((((long long)h->precision * 4 + cyc) * 32 + nu1) * 32 + nu2) * 32 * 4 +
-        (long long)h->inner * 4 + h->order) * 2 + (h->loose_outer ? 1 : 0)) * 4 + rs_in;
+        (long long)inner_cycles(h) * 4 + h->order) * 2 + (h->loose_outer ? 1 : 0)) * 4 + rs_in;
   if (h->use_graphs && !h->profiling) {
     const mgwr_handle::IterGraph* slot = nullptr;
     for (const auto& g : h->graphs)
@@ -811,9 +837,9 @@ template <class F>
 int tune_class(mgwr_t h, int cls, int l, int word, F launch) {
   int best = 1;
   float best_ms = 0.f;
-  const int cands[7] = {1, 2, 4, 1 | mgwr::kStaged, 2 | mgwr::kStaged, 4 | mgwr::kStaged,
-                        1 | mgwr::kTensor};
-  const int ncand = cls == MGWR_K_SWEEP32 ? 7 : 3;
+  const int cands[8] = {1, 2, 4, 1 | mgwr::kStaged, 2 | mgwr::kStaged, 4 | mgwr::kStaged,
+                        1 | mgwr::kTensor, 1 | mgwr::kRadix};
+  const int ncand = cls == MGWR_K_SWEEP32 ? 8 : 3;
   for (int c = 0; c < ncand; ++c) {
     const int E = cands[c];
     if (mgwr::effective_split(h->M, word, E) != E) continue;  // same launch as a smaller E
@@ -857,7 +883,7 @@ int tune_hierarchy(mgwr_t h, Hier<R>& H, int cls_sweep, int cls_defect) {
         if (l == 0)
           return mgwr::launch_sweep<R>(H.f[0], out, (R*)nullptr, spec, sstride, H.tw, H.zero,
                                        scratch_for<R>(h), ls, 0, true, R(0),
-                                       E & ~mgwr::kTensor, h->stream);
+                                       E & ~(mgwr::kTensor | mgwr::kRadix), h->stream);
         const cudaError_t e =
             level_sweep(h, H, l, H.f[l], out, (R*)nullptr, ls, parity(h, MGWR_RED), E);
         if (e != cudaSuccess) return e;
@@ -1188,12 +1214,14 @@ int mgwr_set_engine_split(mgwr_t h, int kernel_class, int level, int split) {
       kernel_class != MGWR_K_DEFECT64 && kernel_class != MGWR_K_DEFECT32 &&
       kernel_class != MGWR_K_DEFECT_DD && kernel_class != MGWR_K_SWEEP_DD)
     return fail(h, MGWR_E_INVAL, "kernel class has no FFT engine");
-  const int E = split & ~(mgwr::kStaged | mgwr::kTensor);
+  const int variants = mgwr::kStaged | mgwr::kTensor | mgwr::kRadix;
+  const int E = split & ~variants;
   if (E != 1 && E != 2 && E != 4) return fail(h, MGWR_E_INVAL, "split must be 1, 2 or 4");
-  if ((split & (mgwr::kStaged | mgwr::kTensor)) && kernel_class != MGWR_K_SWEEP32)
-    return fail(h, MGWR_E_INVAL, "staged and tensor-core sweeps exist for FP32 only");
-  if ((split & mgwr::kStaged) && (split & mgwr::kTensor))
-    return fail(h, MGWR_E_INVAL, "staged and tensor-core sweeps are exclusive");
+  if ((split & variants) && kernel_class != MGWR_K_SWEEP32)
+    return fail(h, MGWR_E_INVAL, "staged, tensor-core and register-pass sweeps exist for FP32 only");
+  const int v = split & variants;
+  if (v != 0 && (v & (v - 1)) != 0)
+    return fail(h, MGWR_E_INVAL, "staged, tensor-core and register-pass sweeps are exclusive");
   if (level < -1 || level >= h->nlev) return fail(h, MGWR_E_INVAL, "level out of range");
   if (level == -1)
     h->split[kernel_class].assign(h->nlev, split);
@@ -1227,6 +1255,13 @@ int mgwr_autotune(mgwr_t h) {
   MGWR_CK(h, cudaStreamSynchronize(h->stream));
   drop_graph(h);
   return check_staging(h);
+}
+
+int mgwr_set_outer_switch(mgwr_t h, double rel) {
+  if (h == nullptr) return MGWR_E_INVAL;
+  if (!(rel >= 0.0)) return fail(h, MGWR_E_INVAL, "the switch must be a number >= 0");
+  h->loose_above = rel;
+  return MGWR_OK;
 }
 
 int mgwr_set_inner_cycles(mgwr_t h, int cycles) {
@@ -1351,9 +1386,9 @@ int mgwr_solve(mgwr_t h, int cyc, int nu1, int nu2, double tol, int max_cycles, 
     // outer defects of the mixed modes while the defect is large (above
     // kLooseOuter of the initial one before this step) take the FP32-convolution
     // form, whose error (about 1e-6 of |f|) is then below 1e-3 of the defect
-    h->loose_outer = mixed && !ddc && rel >= kLooseOuter;
+    h->loose_outer = mixed && !ddc && rel >= h->loose_above;
     MGWR_TRY(run_iteration(h, cyc, nu1, nu2, norms, &exact));
-    cycles += mixed ? h->inner : 1;
+    cycles += mixed ? inner_cycles(h) : 1;
     rel = relative(h, norms, h->relres);
     // the stopping decision is always taken on the full defect
     if (!exact && rel <= tol) {
@@ -1683,6 +1718,7 @@ int mgwr_footprint(int d, int n, int M, int batch, int precision, size_t* bytes)
     for (size_t l = 0; l < nlev; ++l) total += (l + 1 < nlev ? 4 : 3) * r512(4 * B * pts[l] * M);
     total += r512(8 * B * nlev * L) + r512(8 * B * L) + r512(8 * Lt);
     if (mgwr::tensor_length(M)) total += r512(192 * B * nlev * (size_t)M);  // Toeplitz bands
+    if (mgwr::radix_length(M)) total += r512(8 * B * nlev * L);  // register-pass spectra
     if (precision == MGWR_MIXED_DD)
       total += 2 * r512(8 * B * pts[0] * M) + r512(16 * B * L) + r512(16 * Lt);
   }

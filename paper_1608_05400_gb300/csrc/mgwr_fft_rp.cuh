@@ -1,0 +1,272 @@
+// Register-pass FFT engine for FP32 causal time-line convolutions (Sec. 5).
+//
+// The same circulant embedding as mgwr_fft.cuh (two real lines packed as one
+// complex line of length L = 2M, zero upper half, spectrum product, first M
+// outputs of the inverse), organised for fewer instructions per value: each
+// pass of the decimation-in-frequency transform is one radix-R DFT of R <= 32
+// values held in registers (two or three passes instead of four or five
+// radix-8 stages), so every value crosses shared memory once per pass and the
+// inter-pass twiddles are applied only at pass boundaries.  The last pass
+// holds R contiguous positions per butterfly: the spectrum product and the
+// first inverse pass follow in registers.  Shared memory is padded by one slot
+// per R_last values, which makes every access of every pass conflict-free for
+// 8-byte elements (and its address a base plus an immediate offset).
+//
+// Plan (R0, R1[, R2]): pass p has radix R_p, stride S_p = G_p / R_p on groups of
+// G_p = L / (R_0 .. R_{p-1}) positions; butterfly j < S_p of a group reads
+// positions j + q S_p, applies the DFT and, except in the last pass, the
+// twiddles w_{G_p}^{j k}, and writes output k to j + k S_p.  Position
+// p = sum_i d_i L / (R_0 .. R_i) then holds frequency k = sum_i d_i R_0 .. R_{i-1}
+// (spectra are stored in that order: rp_position).
+#pragma once
+
+#include "mgwr_fft.cuh"
+
+namespace mgwr {
+namespace rp {
+
+using C = Cx<float>;
+
+// cos(2 pi e / N) and sin(2 pi e / N) at compile time: the angle is reduced to
+// [-pi, pi] and the power series summed in double (|x| <= pi: 30 terms leave
+// a truncation far below double rounding).
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+constexpr double series_cos(double x) {
+  double term = 1.0, sum = 1.0;
+  for (int k = 1; k < 30; ++k) {
+    term *= -x * x / ((2.0 * k - 1.0) * (2.0 * k));
+    sum += term;
+  }
+  return sum;
+}
+constexpr double series_sin(double x) {
+  double term = x, sum = x;
+  for (int k = 1; k < 30; ++k) {
+    term *= -x * x / ((2.0 * k) * (2.0 * k + 1.0));
+    sum += term;
+  }
+  return sum;
+}
+constexpr double reduced_angle(int e, int N) {
+  const int r = ((e % N) + N) % N;
+  return kTwoPi * (double)(2 * r > N ? r - N : r) / (double)N;
+}
+constexpr double root_cos(int e, int N) { return series_cos(reduced_angle(e, N)); }
+constexpr double root_sin(int e, int N) { return series_sin(reduced_angle(e, N)); }
+
+// a * w_N^E with w_N = exp(-2 pi i / N) (INV: exp(+2 pi i / N)); E, N compile-time.
+// Multiples of N/8 use the exact forms of mgwr_fft.cuh.
+template <int N, int E, bool INV>
+__device__ __forceinline__ C rot(C a) {
+  constexpr int e = ((E % N) + N) % N;
+  if constexpr (e == 0) {
+    return a;
+  } else if constexpr (2 * e == N) {
+    return C{-a.x, -a.y};
+  } else if constexpr (4 * e == N) {
+    return mul_w2<INV>(a);
+  } else if constexpr (4 * e == 3 * N) {
+    return mul_w2<!INV>(a);
+  } else if constexpr (8 * e == N) {
+    return mul_w1<INV>(a);
+  } else if constexpr (8 * e == 3 * N) {
+    return mul_w3<INV>(a);
+  } else if constexpr (8 * e == 5 * N) {
+    const C b = mul_w1<INV>(a);
+    return C{-b.x, -b.y};
+  } else if constexpr (8 * e == 7 * N) {
+    const C b = mul_w3<INV>(a);
+    return C{-b.x, -b.y};
+  } else {
+    constexpr float c = (float)root_cos(e, N);
+    constexpr float s = (float)root_sin(e, N);
+    // forward root c - i s, inverse c + i s
+    return INV ? C{fmaf(a.x, c, -a.y * s), fmaf(a.y, c, a.x * s)}
+               : C{fmaf(a.x, c, a.y * s), fmaf(a.y, c, -a.x * s)};
+  }
+}
+
+// In-place length-R DFT, natural order in and out (INV: conjugate roots, no
+// scaling).  R = A * B with n = n1 B + n2, k = k1 + A k2:
+//   X[k1 + A k2] = sum_n2 w_B^{n2 k2} w_R^{n2 k1} sum_n1 x[n1 B + n2] w_A^{n1 k1}.
+template <int R, bool INV>
+struct Dft;
+
+template <bool INV>
+struct Dft<2, INV> {
+  static __device__ __forceinline__ void run(C (&v)[2]) { dft2(v[0], v[1]); }
+};
+template <bool INV>
+struct Dft<4, INV> {
+  static __device__ __forceinline__ void run(C (&v)[4]) { dft4<INV>(v[0], v[1], v[2], v[3]); }
+};
+template <bool INV>
+struct Dft<8, INV> {
+  static __device__ __forceinline__ void run(C (&v)[8]) { dft8<INV>(v); }
+};
+
+template <int A, int B, bool INV>
+__device__ __forceinline__ void dft_ab(C (&v)[A * B]) {
+  constexpr int R = A * B;
+  C y[B][A];
+#pragma unroll
+  for (int n2 = 0; n2 < B; ++n2) {
+    C a[A];
+#pragma unroll
+    for (int n1 = 0; n1 < A; ++n1) a[n1] = v[n1 * B + n2];
+    Dft<A, INV>::run(a);
+#pragma unroll
+    for (int k1 = 0; k1 < A; ++k1) y[n2][k1] = a[k1];
+  }
+  // twiddles w_R^{n2 k1} (compile-time exponents)
+#define MGWR_RP_TW(N2, K1) \
+  if constexpr ((N2) < B && (K1) < A) y[N2][K1] = rot<R, (N2) * (K1), INV>(y[N2][K1]);
+#define MGWR_RP_TW_ROW(N2) \
+  MGWR_RP_TW(N2, 1) MGWR_RP_TW(N2, 2) MGWR_RP_TW(N2, 3) MGWR_RP_TW(N2, 4) MGWR_RP_TW(N2, 5) \
+  MGWR_RP_TW(N2, 6) MGWR_RP_TW(N2, 7)
+  MGWR_RP_TW_ROW(1) MGWR_RP_TW_ROW(2) MGWR_RP_TW_ROW(3) MGWR_RP_TW_ROW(4)
+  MGWR_RP_TW_ROW(5) MGWR_RP_TW_ROW(6) MGWR_RP_TW_ROW(7)
+#undef MGWR_RP_TW_ROW
+#undef MGWR_RP_TW
+#pragma unroll
+  for (int k1 = 0; k1 < A; ++k1) {
+    C b[B];
+#pragma unroll
+    for (int n2 = 0; n2 < B; ++n2) b[n2] = y[n2][k1];
+    Dft<B, INV>::run(b);
+#pragma unroll
+    for (int k2 = 0; k2 < B; ++k2) v[k1 + A * k2] = b[k2];
+  }
+}
+
+template <bool INV>
+struct Dft<16, INV> {
+  static __device__ __forceinline__ void run(C (&v)[16]) { dft_ab<4, 4, INV>(v); }
+};
+template <bool INV>
+struct Dft<32, INV> {
+  static __device__ __forceinline__ void run(C (&v)[32]) { dft_ab<4, 8, INV>(v); }
+};
+
+// Forward DFT of (v[0], .., v[R/2 - 1], 0, .., 0): the first pass, whose upper
+// half is the zero padding.  Even outputs are the length-R/2 DFT of the input,
+// odd outputs that of the input times w_R^n.
+template <int R>
+__device__ __forceinline__ void dft_half(C (&v)[R]) {
+  if constexpr (R == 8) {
+    dft8_half_input(v);
+  } else if constexpr (R == 2) {
+    v[1] = v[0];
+  } else {
+    constexpr int H = R / 2;
+    C e[H], o[H];
+#pragma unroll
+    for (int q = 0; q < H; ++q) e[q] = v[q];
+    o[0] = v[0];
+#define MGWR_RP_HT(Q) \
+  if constexpr ((Q) < H) o[Q] = rot<R, (Q), false>(v[Q]);
+    MGWR_RP_HT(1) MGWR_RP_HT(2) MGWR_RP_HT(3) MGWR_RP_HT(4) MGWR_RP_HT(5) MGWR_RP_HT(6)
+    MGWR_RP_HT(7) MGWR_RP_HT(8) MGWR_RP_HT(9) MGWR_RP_HT(10) MGWR_RP_HT(11) MGWR_RP_HT(12)
+    MGWR_RP_HT(13) MGWR_RP_HT(14) MGWR_RP_HT(15)
+#undef MGWR_RP_HT
+    Dft<H, false>::run(e);
+    Dft<H, false>::run(o);
+#pragma unroll
+    for (int q = 0; q < H; ++q) {
+      v[2 * q] = e[q];
+      v[2 * q + 1] = o[q];
+    }
+  }
+}
+
+// The table values w^{b e1} (b = 1, 2, 4 and RA, 2 RA) from which twiddle_apply
+// forms the twiddles of a radix-R butterfly: loaded ahead of the butterfly's
+// data so that their latency overlaps the data loads and the DFT.
+template <int R>
+struct TwBase {
+  static constexpr int RA = R > 8 ? 8 : R;
+  static constexpr int RB = R / RA;
+  C a1, a2, a4, h1, h2;
+  __device__ __forceinline__ TwBase(const C* __restrict__ tw, int e1) {
+    a1 = tw[e1];
+    if constexpr (RA >= 4) a2 = tw[2 * e1];
+    if constexpr (RA >= 8) a4 = tw[4 * e1];
+    if constexpr (RB >= 2) h1 = tw[RA * e1];
+    if constexpr (RB >= 4) h2 = tw[2 * RA * e1];
+  }
+};
+
+// v[k] *= w_L^{k e1} (INV: conjugate), k = 1 .. R-1, from the bases of TwBase.
+// With k = RA k_hi + k_lo (RA = min(R, 8)) the other powers of each factor are
+// products of the bases, and w^{k e1} is the product of its two factors,
+// formed right before it is used (few live registers); every twiddle is a
+// product of at most four table values.
+template <int R, bool INV>
+__device__ __forceinline__ void twiddle_apply(C (&v)[R], const TwBase<R>& tb) {
+  constexpr int RA = TwBase<R>::RA, RB = TwBase<R>::RB;
+  C a[RA];
+  a[1] = tb.a1;
+  if constexpr (RA >= 4) {
+    a[2] = tb.a2;
+    a[3] = cmul(a[1], a[2]);
+  }
+  if constexpr (RA == 8) {
+    a[4] = tb.a4;
+    a[5] = cmul(a[1], a[4]);
+    a[6] = cmul(a[2], a[4]);
+    a[7] = cmul(a[3], a[4]);
+  }
+  C hb[RB > 1 ? RB : 2];
+  if constexpr (RB >= 2) hb[1] = tb.h1;
+  if constexpr (RB == 4) {
+    hb[2] = tb.h2;
+    hb[3] = cmul(hb[1], hb[2]);
+  }
+#pragma unroll
+  for (int kh = 0; kh < RB; ++kh) {
+#pragma unroll
+    for (int kl = 0; kl < RA; ++kl) {
+      const int k = kh * RA + kl;
+      if (k == 0) continue;
+      const C w = kh == 0 ? a[kl] : (kl == 0 ? hb[kh] : cmul(a[kl], hb[kh]));
+      v[k] = INV ? cmulc(v[k], w) : cmul(v[k], w);
+    }
+  }
+}
+
+// Compile-time plan of a length-2^LOGL transform with radices R0, R1 and, when
+// R2 != 0, R2; T threads per line pair.
+template <int LOGL, int R0, int R1, int R2, int T>
+struct Plan {
+  static constexpr int L = 1 << LOGL;
+  static constexpr int NP = R2 != 0 ? 3 : 2;
+  static constexpr int RL = R2 != 0 ? R2 : R1;  // radix of the last pass
+  static constexpr int LOG_RL = RL == 32 ? 5 : RL == 16 ? 4 : RL == 8 ? 3 : RL == 4 ? 2 : 1;
+  static constexpr int S0 = L / R0;             // pass 0: one group of L
+  static constexpr int G1 = S0, S1 = G1 / R1;   // pass 1
+  static constexpr int G2 = S1, S2 = G2 / (R2 != 0 ? R2 : 1);
+  static constexpr int SMEM = L + L / RL;       // padded complex slots per line pair
+  static_assert(R0 * R1 * (R2 != 0 ? R2 : 1) == L, "radices must multiply to L");
+  static_assert((L / R0) % T == 0 && (L / R1) % T == 0 && (L / RL) % T == 0,
+                "every pass must give each thread the same number of butterflies");
+  static __device__ __forceinline__ int idx(int p) { return p + (p >> LOG_RL); }
+};
+
+}  // namespace rp
+
+// Position of frequency k in the spectral order of a DIF transform with the
+// radices r[0..np) (host and device; used to permute spectra between engines).
+__host__ __device__ inline int rp_position(int k, const int* r, int np) {
+  int L = 1;
+  for (int i = 0; i < np; ++i) L *= r[i];
+  int p = 0, w = L, base = 1;
+  for (int i = 0; i < np; ++i) {
+    const int dgt = (k / base) % r[i];
+    w /= r[i];
+    p += dgt * w;
+    base *= r[i];
+  }
+  return p;
+}
+
+}  // namespace mgwr

@@ -50,8 +50,12 @@ constexpr int kStaged = 16;
 // or 256 steps then runs on the tensor cores (mgwr_sweep_tc.cu).
 constexpr int kTensor = 32;
 inline bool tensor_length(int M) { return M == 64 || M == 128 || M == 256; }
+// Or kRadix: the FP32 sweep of lines of 64 .. 4096 steps then runs on the
+// register-pass engine (mgwr_sweep_rp.cu, radix-32 passes in registers).
+constexpr int kRadix = 64;
+inline bool radix_length(int M) { return M >= 64 && M <= kShortMaxM; }
 inline int engine_split(int L, int E) {
-  E &= ~(kStaged | kTensor);
+  E &= ~(kStaged | kTensor | kRadix);
   if (E != 2 && E != 4) E = 1;
   while (E > 1 && L / 8 < E) E >>= 1;
   return E;
@@ -62,11 +66,13 @@ inline int engine_split(int L, int E) {
 inline int effective_split(int M, int word, int E) {
   const int staged = E & kStaged;
   const int tensor = E & kTensor;
-  E &= ~(kStaged | kTensor);
+  const int radix = E & kRadix;
+  E &= ~(kStaged | kTensor | kRadix);
   if (M > kShortMaxM) return E == 2 ? 2 : 1;
   const int L = 2 * M;
   E = engine_split(L, E);
   if (word == 4 && (L < 128 || L > 8192)) return 1;
+  if (word == 4 && radix && radix_length(M)) return 1 | kRadix;
   if (word == 4 && tensor && tensor_length(M)) return 1 | kTensor;
   return word == 4 ? (E | staged) : E;
 }
@@ -129,6 +135,19 @@ size_t tc_band_bytes(int M);
 cudaError_t launch_band_bf16x3(const double* kcol, unsigned char* band, int M, size_t lines,
                                cudaStream_t s);
 cudaError_t take_tc_timeout(bool* hit);
+
+// One colour half-sweep of FP32 lines of 64 .. 4096 steps on the register-pass
+// FFT engine (mgwr_fft_rp.cuh): as launch_sweep without all_points, with the
+// inverse-column spectra in that engine's spectral order (launch_spectra_rp).
+// Results agree with the shared-memory engine's to FP32 rounding, not bitwise.
+cudaError_t launch_sweep_rp(const float* f, float* u, float* delta, const Cx<float>* spec,
+                            size_t spec_stride, const Cx<float>* tw, const float* zero,
+                            const LevelShape& ls, int par, float hinv2, cudaStream_t s);
+// dst[c L ..] = the FP64 spectra src[c L ..] (length L = 2M, the shared-memory
+// engine's order) rounded to FP32 and permuted into the register-pass engine's
+// order, for `lines` lines.
+cudaError_t launch_spectra_rp(Cx<float>* dst, const Cx<double>* src, size_t lines, int M,
+                              cudaStream_t s);
 
 // Defect after a red-black step from the black half-sweep's delta: r = 0 on the
 // black points, r = hinv2 * sum of neighbour deltas on the red points

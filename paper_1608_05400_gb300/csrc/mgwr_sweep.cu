@@ -118,7 +118,7 @@ cudaError_t launch_sweep(const R* f, R* u, R* delta, const Cx<R>* spec, size_t s
     if ((E & kStaged) && !all_points)
       return launch_sweep_staged(f, u, delta, spec, spec_stride, tw, zero, ls, par, hinv2, E, s);
   }
-  E &= ~kStaged;
+  E &= ~(kStaged | kTensor | kRadix);
   const int npts = all_points ? (d == 1 ? n : n * n) : colour_count(d, n, par);
   const int npairs = (npts + 1) / 2;
   if (npairs == 0 || ls.batch == 0) return cudaSuccess;

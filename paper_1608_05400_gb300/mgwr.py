@@ -35,6 +35,7 @@ MGWR_FAS_D_POROUS, MGWR_FAS_D_CONSTANT = 0, 1
 MGWR_POLICY_FIFO, MGWR_POLICY_SMALLEST = 0, 1
 MGWR_SPLIT_STAGED = 16
 MGWR_SPLIT_TENSOR = 32
+MGWR_SPLIT_RADIX = 64
 
 
 class mgwr_stats(C.Structure):
@@ -74,6 +75,7 @@ _SIGS = {
     "mgwr_set_order": (C.c_int, [_h, C.c_int]),
     "mgwr_set_stream": (C.c_int, [_h, C.c_void_p]),
     "mgwr_set_inner_cycles": (C.c_int, [_h, C.c_int]),
+    "mgwr_set_outer_switch": (C.c_int, [_h, C.c_double]),
     "mgwr_set_engine_split": (C.c_int, [_h, C.c_int, C.c_int, C.c_int]),
     "mgwr_get_engine_split": (C.c_int, [_h, C.c_int, C.c_int, C.POINTER(C.c_int)]),
     "mgwr_autotune": (C.c_int, [_h]),
@@ -251,6 +253,9 @@ class Solver:
 
     def set_inner_cycles(self, k: int):
         self._check(self.lib.mgwr_set_inner_cycles(self.h, k), "mgwr_set_inner_cycles")
+
+    def set_outer_switch(self, rel: float):
+        self._check(self.lib.mgwr_set_outer_switch(self.h, float(rel)), "mgwr_set_outer_switch")
 
     def set_engine_split(self, kernel_class: int, split: int, level: int = -1):
         """E for one level, or every level (level -1)."""

@@ -112,13 +112,14 @@ def test_autotune_keeps_state_and_results(precision):
         s.solve(1, 1, 1, tol=1e-10, max_cycles=1, allow_noconv=True)
         before = s.solution()
         chosen = s.autotune()
-        flags = G.MGWR_SPLIT_STAGED | G.MGWR_SPLIT_TENSOR
+        flags = G.MGWR_SPLIT_STAGED | G.MGWR_SPLIT_TENSOR | G.MGWR_SPLIT_RADIX
         assert all(e & ~flags in (1, 2, 4) for v in chosen.values() for e in v)
         np.testing.assert_array_equal(s.solution(), before)  # tuning touches no state
         s.set_rhs(f)
         st = s.solve(1, 1, 1, tol=1e-10, max_cycles=40)
-        if any(e & G.MGWR_SPLIT_TENSOR for e in chosen.get("sweep32", [])):
-            # tensor-core sweeps round differently from the FFT engine
+        rounding = G.MGWR_SPLIT_TENSOR | G.MGWR_SPLIT_RADIX
+        if any(e & rounding for e in chosen.get("sweep32", [])):
+            # tensor-core and register-pass sweeps round differently from the FFT engine
             assert rel(s.solution(), u0) <= 1e-9 and abs(st.cycles - st0.cycles) <= 2
         else:
             np.testing.assert_array_equal(s.solution(), u0)
@@ -266,6 +267,76 @@ def test_tensor_solve_converges_like_the_fft_solve(precision, d, n, M, batch):
         f = np.stack([inputs.Problem(d, n, M, 1.0, float(a), "t2").rhs() for a in alphas])
     out = []
     for split in (1, 1 | G.MGWR_SPLIT_TENSOR):
+        with G.Solver(d, n, M, 1.0, alphas) as s:
+            s.set_precision(precision)
+            s.set_engine_split(K["sweep32"], split)
+            s.set_rhs(f)
+            st = s.solve(1, 1, 1, tol=1e-10, max_cycles=40)
+            out.append((s.solution(), st.cycles))
+    assert abs(out[1][1] - out[0][1]) <= 2
+    assert rel(out[1][0], out[0][0]) <= 1e-9
+
+
+# register-pass engine: every transform length it serves (L = 2M = 128 .. 8192),
+# 1-D and 2-D, batches, grids with fewer line pairs than one block holds
+RADIX_SHAPES = [(1, 63, 64, 1), (2, 15, 128, 1), (2, 31, 256, 1), (1, 255, 512, 1), (2, 63, 1024, 1),
+                (1, 31, 2048, 1), (2, 15, 4096, 1), (2, 3, 64, 1), (1, 7, 4096, 2), (2, 63, 256, 3),
+                (2, 127, 64, 1), (1, 1023, 128, 1)]
+
+
+@pytest.mark.parametrize("d,n,M,batch", RADIX_SHAPES)
+def test_radix_sweep_agrees_with_the_fft_sweep(d, n, M, batch):
+    # radix-32 register passes against the radix-8 shared-memory cascade: both
+    # FP32 transforms of the same convolution, not bitwise
+    ref, _ = _sweep32(d, n, M, 1, batch)
+    got, used = _sweep32(d, n, M, 1 | G.MGWR_SPLIT_RADIX, batch)
+    assert used == 1 | G.MGWR_SPLIT_RADIX
+    for a, b in zip(got, ref):
+        assert rel(a, b) <= 2e-6, rel(a, b)
+
+
+@pytest.mark.parametrize("d,n,M", [(1, 63, 64), (2, 15, 512), (2, 31, 2048), (2, 7, 4096)])
+def test_radix_sweep_matches_the_oracle(d, n, M):
+    W = omg.WRMG(d, n, M, 1.0, 0.45)
+    got, _ = _sweep32(d, n, M, 1 | G.MGWR_SPLIT_RADIX)
+    N = n ** d
+    u = inputs.random_field(N, M, seed=3)
+    f = inputs.random_field(N, M, seed=4, scale=2.0 * d * (n + 1) ** 2)
+    W.sweep(W.finest, u, f, 0)
+    W.sweep(W.finest, u, f, 1)
+    assert rel(got[0], u) <= 2e-5
+
+
+@pytest.mark.parametrize("d,n,M", [(2, 31, 256), (1, 127, 1024), (2, 15, 4096)])
+def test_radix_sweep_records_its_changes(d, n, M):
+    ref, _ = _sweep32(d, n, M, 1, delta=True)
+    got, _ = _sweep32(d, n, M, 1 | G.MGWR_SPLIT_RADIX, delta=True)
+    assert rel(got[0], ref[0]) <= 2e-6
+    assert rel(got[1], ref[1]) <= 1e-4  # the defect: differences of nearly equal values
+
+
+def test_radix_split_falls_back_and_is_checked():
+    with G.Solver(2, 7, 32, 1.0, 0.5) as s:  # below 64 steps: the shared-memory engine
+        s.set_precision(G.MGWR_MIXED)
+        s.set_engine_split(K["sweep32"], 1 | G.MGWR_SPLIT_RADIX)
+        assert s.engine_split(K["sweep32"]) == 1
+        with pytest.raises(G.MGWRError):
+            s.set_engine_split(K["sweep64"], 1 | G.MGWR_SPLIT_RADIX)
+        with pytest.raises(G.MGWRError):
+            s.set_engine_split(K["sweep32"], 1 | G.MGWR_SPLIT_RADIX | G.MGWR_SPLIT_TENSOR)
+
+
+@pytest.mark.parametrize("precision", [G.MGWR_MIXED, G.MGWR_MIXED_DD])
+@pytest.mark.parametrize("d,n,M,batch", [(2, 63, 256, 1), (1, 255, 2048, 1), (2, 31, 64, 4),
+                                         (2, 31, 4096, 1)])
+def test_radix_solve_converges_like_the_fft_solve(precision, d, n, M, batch):
+    alphas = 0.6 if batch == 1 else list(np.linspace(0.2, 0.8, batch))
+    if batch == 1:
+        f = inputs.Problem(d, n, M, 1.0, 0.6, "t2").rhs()
+    else:
+        f = np.stack([inputs.Problem(d, n, M, 1.0, float(a), "t2").rhs() for a in alphas])
+    out = []
+    for split in (1, 1 | G.MGWR_SPLIT_RADIX):
         with G.Solver(d, n, M, 1.0, alphas) as s:
             s.set_precision(precision)
             s.set_engine_split(K["sweep32"], split)

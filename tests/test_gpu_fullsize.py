@@ -63,6 +63,7 @@ def test_2d_511_m4096_talpha_against_separable_solution(torch, precision):
         s.set_rhs_dev(f.data_ptr())
         torch.cuda.synchronize()
         del f
+        torch.cuda.empty_cache()
         st = s.solve(1, 1, 1, tol=TOL, max_cycles=40)
         r64 = s.residual()
         u = torch.empty((n * n, M), dtype=torch.float64, device="cuda")
@@ -88,20 +89,23 @@ def test_batch4096_2d_63_m256_against_separable_solutions(torch, precision):
         s.set_rhs_dev(f.data_ptr())
         torch.cuda.synchronize()
         del f
+        torch.cuda.empty_cache()
         st = s.solve(1, 1, 1, tol=TOL, max_cycles=40)
         rel_b = s.instance_relres()
-        s.residual()
-        rel64_b = s.instance_relres()
         u = torch.empty((B, N, M), dtype=torch.float64, device="cuda")
         s.solution_dev(u.data_ptr())
         torch.cuda.synchronize()
+        Wd = torch.from_numpy(W).cuda()
+        worst = 0.0
+        for b0 in range(0, B, 256):  # per instance: max |u_b - phi w_b| / max |phi w_b|
+            ub = u[b0:b0 + 256]
+            ref = phi[None, :, None] * Wd[b0:b0 + 256, None, :]
+            err = (ub - ref).abs().amax(dim=(1, 2)) / ref.abs().amax(dim=(1, 2))
+            worst = max(worst, float(err.max()))
+        del u, ub, ref
+        torch.cuda.empty_cache()  # the FP64 defect below needs another 33 GB field
+        s.residual()
+        rel64_b = s.instance_relres()
     assert st.relres <= TOL
     assert rel_b.max() <= TOL and rel64_b.max() <= 2 * TOL, (rel_b.max(), rel64_b.max())
-    Wd = torch.from_numpy(W).cuda()
-    worst = 0.0
-    for b0 in range(0, B, 256):  # per instance: max |u_b - phi w_b| / max |phi w_b|
-        ub = u[b0:b0 + 256]
-        ref = phi[None, :, None] * Wd[b0:b0 + 256, None, :]
-        err = (ub - ref).abs().amax(dim=(1, 2)) / ref.abs().amax(dim=(1, 2))
-        worst = max(worst, float(err.max()))
     assert worst <= TOL, worst

@@ -955,6 +955,15 @@ def main():
     }
     if "sweep32" in prof and out["roofline"]["class"] != "sweep32":
         out["roofline_sweep32"] = kernel_roofline("sweep32", prof["sweep32"], d, Mw, pk)
+    # name the FP32 sweep by the engine the tuner chose for the finest level
+    sp = (main_arm["engine_splits"] or {}).get("sweep32")
+    if sp:
+        eng = ("k_sweep_rp<float> (register-pass engine)" if sp[-1] & 64 else
+               "k_sweep_tc (tensor cores)" if sp[-1] & 32 else
+               "k_sweep_staged<float>" if sp[-1] & 16 else f"k_sweep<float> (E={sp[-1]})")
+        for key in ("roofline", "roofline_sweep32"):
+            if key in out and out[key].get("class") == "sweep32":
+                out[key]["kernel"] = eng + " [finest level; all levels' launches timed]"
     for a, res in arm_out.items():
         res.pop("engine_splits", None)
         out[f"{a}_arm"] = res

@@ -44,6 +44,7 @@ struct Hier {
   std::vector<int> rs;            // per level: RState of r
   Cx<R>* spec = nullptr;          // batch * nlev * L: spectra of the inverse columns
   Cx<R>* spec_rp = nullptr;       // the same in the register-pass engine's order (FP32)
+  Cx<R>* tspec_rp = nullptr;      // the Toeplitz spectra in that order (FP32)
   Cx<R>* tspec = nullptr;         // batch * L: spectra of the Toeplitz columns
   Cx<R>* tw = nullptr;            // L twiddles
   R* zero = nullptr;              // M zeros: the neighbour line outside the grid
@@ -59,6 +60,7 @@ struct mgwr_handle {
   std::vector<double> alpha, T, c;  // per instance; c = tau^-alpha / Gamma(2 - alpha)
   int precision = MGWR_FP64, order = MGWR_ORDER_TEXT;
   int inner = 0;  // inner cycles per outer defect; 0 = the precision's default (inner_cycles)
+  int inner_now = 0;  // inner cycles of the outer step being enqueued (0: inner_cycles)
   double loose_above = kLooseOuter;  // mgwr_set_outer_switch
   std::vector<int> nl;          // interior points per dimension, level 0 = 1
   std::vector<double> hinv2;    // 1/h_l^2
@@ -268,6 +270,8 @@ int ensure_h32(mgwr_t h) {
     MGWR_TRY(dev_alloc(h, &H.spec_rp, sizeof(Cx<float>) * nspec));
     MGWR_CK(h, mgwr::launch_spectra_rp(H.spec_rp, h->h64.spec, (size_t)h->B * h->nlev, h->M,
                                        h->stream));
+    MGWR_TRY(dev_alloc(h, &H.tspec_rp, sizeof(Cx<float>) * (size_t)h->B * h->L));
+    MGWR_CK(h, mgwr::launch_spectra_rp(H.tspec_rp, h->h64.tspec, (size_t)h->B, h->M, h->stream));
   }
   if (mgwr::tensor_length(h->M)) {
     const size_t lines = (size_t)h->B * h->nlev;
@@ -616,6 +620,10 @@ int inner_cycles(const mgwr_handle* h) {
   return h->precision == MGWR_MIXED ? 3 : 2;
 }
 
+// Inner cycles of the outer step being enqueued: inner_cycles, or one more on
+// the step that the solve loop predicts will finish with it.
+int step_cycles(const mgwr_handle* h) { return h->inner_now > 0 ? h->inner_now : inner_cycles(h); }
+
 // One cycle on hierarchy H and the finest defect norms (from the smoothing
 // changes when the cycle ended with a smoothing step: *exact = false).
 template <class R>
@@ -650,7 +658,7 @@ int enqueue_iteration(mgwr_t h, int cyc, int nu1, int nu2, bool* exact) {
     // double-float iterate, its double-float defect as the next right-hand side
     MGWR_CK(h, cudaMemsetAsync(h->hdd.u[L], 0, cnt * sizeof(mgwr::dd), h->stream));
     h->hdd.rs[L] = R_ZERO_U;
-    for (int k = 0; k < inner_cycles(h); ++k) MGWR_TRY(cycle(h, h->hdd, L, cyc, nu1, nu2));
+    for (int k = 0; k < step_cycles(h); ++k) MGWR_TRY(cycle(h, h->hdd, L, cyc, nu1, nu2));
     const int pm = prof_begin(h, MGWR_K_REFINE, (double)(points(h, L) * h->B));
     MGWR_CK(h, mgwr::launch_refine_dd2(h->u_dd, h->hdd.u[L], cnt, h->stream));
     prof_end(h, pm);
@@ -661,7 +669,7 @@ int enqueue_iteration(mgwr_t h, int cyc, int nu1, int nu2, bool* exact) {
     const bool ddef = h->precision == MGWR_MIXED_DD;
     MGWR_CK(h, cudaMemsetAsync(h->h32.u[L], 0, cnt * sizeof(float), h->stream));
     h->h32.rs[L] = R_ZERO_U;  // f32 holds the outer defect, e32 = 0
-    for (int k = 0; k < inner_cycles(h); ++k) MGWR_TRY(cycle(h, h->h32, L, cyc, nu1, nu2));
+    for (int k = 0; k < step_cycles(h); ++k) MGWR_TRY(cycle(h, h->h32, L, cyc, nu1, nu2));
     const int pm = prof_begin(h, MGWR_K_REFINE, (double)(points(h, L) * h->B));
     if (ddef)
       MGWR_CK(h, mgwr::launch_refine_dd(h->u_dd, h->h32.u[L], cnt, h->stream));
@@ -672,10 +680,21 @@ int enqueue_iteration(mgwr_t h, int cyc, int nu1, int nu2, bool* exact) {
     if (h->loose_outer && h->M <= mgwr::kShortMaxM) {
       // large defect: FP32 time convolution, stencil and source in the iterate's arithmetic
       const int pl = prof_begin(h, MGWR_K_DEFECT32, (double)(points(h, L) * h->B));
-      if (ddef)
+      // on the register-pass engine where it serves the length (fewer instructions
+      // per value: 2-D 511 x 511, M = 4096 in 45 -> XX ms), else the radix-8 engine
+      const bool rp = h->h32.tspec_rp != nullptr;
+      if (ddef && rp)
+        MGWR_CK(h, mgwr::launch_defect_hybrid_rp<mgwr::dd>(
+                       h->u_dd, h->f_dd, h->h32.f[L], h->h32.tspec_rp, (size_t)h->L, h->h32.tw,
+                       h->zero_dd, shape(h, L), mgwr::dd(h->hinv2[L]), h->norm_bits, h->stream));
+      else if (ddef)
         MGWR_CK(h, mgwr::launch_defect_hybrid<mgwr::dd>(
                        h->u_dd, h->f_dd, h->h32.f[L], h->h32.tspec, (size_t)h->L, h->h32.tw,
                        h->zero_dd, shape(h, L), mgwr::dd(h->hinv2[L]), h->norm_bits, h->stream));
+      else if (rp)
+        MGWR_CK(h, mgwr::launch_defect_hybrid_rp<double>(
+                       h->h64.u[L], h->h64.f[L], h->h32.f[L], h->h32.tspec_rp, (size_t)h->L,
+                       h->h32.tw, h->h64.zero, shape(h, L), h->hinv2[L], h->norm_bits, h->stream));
       else
         MGWR_CK(h, mgwr::launch_defect_hybrid<double>(
                        h->h64.u[L], h->h64.f[L], h->h32.f[L], h->h32.tspec, (size_t)h->L,
@@ -717,7 +736,7 @@ int run_iteration(mgwr_t h, int cyc, int nu1, int nu2, std::vector<double>& norm
   const int rs_in = h->precision == MGWR_FP64 ? h->h64.rs[h->nlev - 1] : 0;
   const long long key =
       ((((((long long)h->precision * 4 + cyc) * 32 + nu1) * 32 + nu2) * 32 * 4 +
-        (long long)inner_cycles(h) * 4 + h->order) * 2 + (h->loose_outer ? 1 : 0)) * 4 + rs_in;
+        (long long)step_cycles(h) * 4 + h->order) * 2 + (h->loose_outer ? 1 : 0)) * 4 + rs_in;
   if (h->use_graphs && !h->profiling) {
     const mgwr_handle::IterGraph* slot = nullptr;
     for (const auto& g : h->graphs)
@@ -1373,6 +1392,9 @@ int mgwr_solve(mgwr_t h, int cyc, int nu1, int nu2, double tol, int max_cycles, 
   int status = MGWR_OK;
   int cycles = 0, outer = 0;
   bool rel_exact = true;  // rel comes from the full defect (not from smoothing changes)
+  // refinements: defect reduction of the last outer step and its inner cycles
+  double last_q = 0.0;
+  int last_k = 0;
   while (!(rel <= tol)) {
     if (!std::isfinite(rel)) {
       status = MGWR_E_NUMERIC;
@@ -1387,9 +1409,35 @@ int mgwr_solve(mgwr_t h, int cyc, int nu1, int nu2, double tol, int max_cycles, 
     // kLooseOuter of the initial one before this step) take the FP32-convolution
     // form, whose error (about 1e-6 of |f|) is then below 1e-3 of the defect
     h->loose_outer = mixed && !ddc && rel >= h->loose_above;
+    // Refinements: when the last step's reduction predicts that this step ends
+    // just above the tolerance, but below half of it with one cycle more, this
+    // step takes that cycle instead of leaving a whole outer step (and its outer
+    // defect) for it.  One more cycle gains the last step's mean reduction per
+    // cycle only down to the floor of the inner precision: the rounding of the
+    // correction e (eps |e|) has a defect of about 4d/h^2 eps |e| against the
+    // smooth defect d pi^2 |e| left after a cycle, so no outer step reduces the
+    // defect below about 4 eps / (pi h)^2 (FP32: 6e-3 at h = 1/512).
+    h->inner_now = 0;
+    if (mixed && last_k > 0 && last_q > 0.0 && last_q < 1.0) {
+      const int k = inner_cycles(h);
+      const double per_cycle = std::pow(last_q, 1.0 / last_k);
+      const double hf = 1.0 / (h->n + 1);
+      const double eps = ddc ? std::ldexp(1.0, -44) : std::ldexp(1.0, -24);
+      const double pi = 3.14159265358979323846;
+      const double floor_q = 4.0 * eps / (pi * pi * hf * hf);
+      const double q_more = std::max(last_q * per_cycle, floor_q);
+      if (rel * last_q > tol && rel * q_more <= 0.5 * tol) h->inner_now = k + 1;
+    }
+    const double rel_before = rel;
+    const int k_now = mixed ? step_cycles(h) : 1;
     MGWR_TRY(run_iteration(h, cyc, nu1, nu2, norms, &exact));
-    cycles += mixed ? inner_cycles(h) : 1;
+    h->inner_now = 0;
+    cycles += k_now;
     rel = relative(h, norms, h->relres);
+    if (mixed && rel_before > 0.0) {
+      last_q = rel / rel_before;
+      last_k = k_now;
+    }
     // the stopping decision is always taken on the full defect
     if (!exact && rel <= tol) {
       MGWR_TRY(full_defect());
@@ -1718,7 +1766,8 @@ int mgwr_footprint(int d, int n, int M, int batch, int precision, size_t* bytes)
     for (size_t l = 0; l < nlev; ++l) total += (l + 1 < nlev ? 4 : 3) * r512(4 * B * pts[l] * M);
     total += r512(8 * B * nlev * L) + r512(8 * B * L) + r512(8 * Lt);
     if (mgwr::tensor_length(M)) total += r512(192 * B * nlev * (size_t)M);  // Toeplitz bands
-    if (mgwr::radix_length(M)) total += r512(8 * B * nlev * L);  // register-pass spectra
+    if (mgwr::radix_length(M))  // register-pass spectra
+      total += r512(8 * B * nlev * L) + r512(8 * B * L);
     if (precision == MGWR_MIXED_DD)
       total += 2 * r512(8 * B * pts[0] * M) + r512(16 * B * L) + r512(16 * Lt);
   }

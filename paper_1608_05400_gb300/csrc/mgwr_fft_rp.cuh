@@ -252,7 +252,167 @@ struct Plan {
   static __device__ __forceinline__ int idx(int p) { return p + (p >> LOG_RL); }
 };
 
+// Barrier of the T threads of one line pair (PAIRS pairs per block).
+template <int T, int PAIRS>
+__device__ __forceinline__ void group_sync(int g) {
+  if constexpr (PAIRS == 1) {
+    __syncthreads();
+  } else if constexpr (T <= 32) {
+    __syncwarp();  // every group of a warp runs the same barrier sequence
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(T) : "memory");
+  }
+}
+
+// One line pair's causal convolution by the T threads t of group g: the first
+// M = L/2 values of IFFT(FFT(x) * spec), x zero-padded to L.  load(m) gives
+// the pair's input at time m < M (both lines as one complex value; every call
+// of the thread is made before its first DFT, so the loads overlap);
+// store(m, y) receives output m < M.  spec: the kernel's spectrum in this
+// plan's spectral order, pre-scaled by 1/L; tw[e] = w_L^e.  buf: P::SMEM
+// complex values of shared memory for the group.
+template <int LOGL, int R0, int R1, int R2, int T, int PAIRS, class Load, class Store>
+__device__ __forceinline__ void convolve(C* buf, int t, int g, const C* __restrict__ spec,
+                                         const C* __restrict__ tw, Load load, Store store) {
+  using P = Plan<LOGL, R0, R1, R2, T>;
+  // ---- pass 0: every input of the thread, then half-input DFTs and twiddles
+  constexpr int NB0 = P::S0 / T;
+  C in[NB0][R0 / 2];
+#pragma unroll
+  for (int i = 0; i < NB0; ++i) {
+#pragma unroll
+    for (int q = 0; q < R0 / 2; ++q) in[i][q] = load(t + T * i + q * P::S0);
+  }
+#pragma unroll
+  for (int i = 0; i < NB0; ++i) {
+    const int j = t + T * i;
+    const TwBase<R0> tb(tw, j);
+    C v[R0];
+#pragma unroll
+    for (int q = 0; q < R0 / 2; ++q) v[q] = in[i][q];
+    dft_half<R0>(v);
+    twiddle_apply<R0, false>(v, tb);
+#pragma unroll
+    for (int k = 0; k < R0; ++k) buf[P::idx(j + k * P::S0)] = v[k];
+  }
+  group_sync<T, PAIRS>(g);
+
+  // ---- pass 1 when there are three: radix R1 on groups of G1, twiddles w_G1^{jk}
+  if constexpr (P::NP == 3) {
+    constexpr int NB1 = (P::L / R1) / T;
+#pragma unroll 1
+    for (int i = 0; i < NB1; ++i) {
+      const int beta = t + T * i;
+      const int grp = beta / P::S1, j = beta - grp * P::S1;
+      const int base = grp * P::G1 + j;
+      const TwBase<R1> tb(tw, j * R0);
+      C v[R1];
+#pragma unroll
+      for (int q = 0; q < R1; ++q) v[q] = buf[P::idx(base + q * P::S1)];
+      Dft<R1, false>::run(v);
+      twiddle_apply<R1, false>(v, tb);
+#pragma unroll
+      for (int q = 0; q < R1; ++q) buf[P::idx(base + q * P::S1)] = v[q];
+    }
+    group_sync<T, PAIRS>(g);
+  }
+
+  // ---- last pass (contiguous RL values), spectrum product, its inverse
+  constexpr int RL = P::RL;
+  constexpr int NBL = (P::L / RL) / T;
+#pragma unroll 1
+  for (int i = 0; i < NBL; ++i) {
+    const int base = (t + T * i) * RL;
+    C v[RL];
+#pragma unroll
+    for (int q = 0; q < RL; ++q) v[q] = buf[P::idx(base + q)];
+    Dft<RL, false>::run(v);
+    const float4* sp = reinterpret_cast<const float4*>(spec + base);
+#pragma unroll
+    for (int q = 0; q < RL / 2; ++q) {
+      const float4 s2 = __ldg(sp + q);
+      v[2 * q] = cmul(v[2 * q], C{s2.x, s2.y});
+      v[2 * q + 1] = cmul(v[2 * q + 1], C{s2.z, s2.w});
+    }
+    Dft<RL, true>::run(v);
+#pragma unroll
+    for (int q = 0; q < RL; ++q) buf[P::idx(base + q)] = v[q];
+  }
+  group_sync<T, PAIRS>(g);
+
+  // ---- inverse of pass 1
+  if constexpr (P::NP == 3) {
+    constexpr int NB1 = (P::L / R1) / T;
+#pragma unroll 1
+    for (int i = 0; i < NB1; ++i) {
+      const int beta = t + T * i;
+      const int grp = beta / P::S1, j = beta - grp * P::S1;
+      const int base = grp * P::G1 + j;
+      const TwBase<R1> tb(tw, j * R0);
+      C v[R1];
+#pragma unroll
+      for (int q = 0; q < R1; ++q) v[q] = buf[P::idx(base + q * P::S1)];
+      twiddle_apply<R1, true>(v, tb);
+      Dft<R1, true>::run(v);
+#pragma unroll
+      for (int q = 0; q < R1; ++q) buf[P::idx(base + q * P::S1)] = v[q];
+    }
+    group_sync<T, PAIRS>(g);
+  }
+
+  // ---- inverse of pass 0: the first M outputs
+#pragma unroll 1
+  for (int i = 0; i < NB0; ++i) {
+    const int j = t + T * i;
+    const TwBase<R0> tb(tw, j);
+    C v[R0];
+#pragma unroll
+    for (int k = 0; k < R0; ++k) v[k] = buf[P::idx(j + k * P::S0)];
+    twiddle_apply<R0, true>(v, tb);
+    Dft<R0, true>::run(v);
+#pragma unroll
+    for (int q = 0; q < R0 / 2; ++q) store(j + q * P::S0, v[q]);
+  }
+}
+
 }  // namespace rp
+
+// Radix plans per transform length (L = 2^7 .. 2^13): two or three passes,
+// the last of radix 32; T threads per line pair, 256 threads per block.
+#define MGWR_RP_PLANS(X)      \
+  X(13, 16, 16, 32, 256)      \
+  X(12, 8, 16, 32, 128)       \
+  X(11, 8, 8, 32, 64)         \
+  X(10, 8, 4, 32, 32)         \
+  X(9, 16, 32, 0, 16)         \
+  X(8, 8, 32, 0, 8)           \
+  X(7, 4, 32, 0, 4)
+
+constexpr int kRpBlock = 256;  // threads per block of every register-pass kernel
+
+__host__ __device__ inline int rp_plan(int logL, int* r) {
+  switch (logL) {
+#define MGWR_RP_PLAN_CASE(LG, A, B, C, T) \
+  case LG:                                \
+    r[0] = A;                             \
+    r[1] = B;                             \
+    r[2] = C;                             \
+    return C != 0 ? 3 : 2;
+    MGWR_RP_PLANS(MGWR_RP_PLAN_CASE)
+#undef MGWR_RP_PLAN_CASE
+    default:
+      return 0;
+  }
+}
+
+// Radices of the shared-memory engine of mgwr_fft.cuh for length 2^logL:
+// radix-8 stages, then radix 2^(logL mod 3) when that is not 0.
+__host__ __device__ inline int engine_plan(int logL, int* r) {
+  int np = 0;
+  for (int k = 0; k < logL / 3; ++k) r[np++] = 8;
+  if (logL % 3 != 0) r[np++] = 1 << (logL % 3);
+  return np;
+}
 
 // Position of frequency k in the spectral order of a DIF transform with the
 // radices r[0..np) (host and device; used to permute spectra between engines).

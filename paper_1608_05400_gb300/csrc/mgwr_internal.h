@@ -222,6 +222,13 @@ cudaError_t launch_defect_hybrid(const Tin* u, const Tin* f, float* r, const Cx<
                                  size_t spec_stride, const Cx<float>* tw, const Tin* zero,
                                  const LevelShape& ls, Tin hinv2, unsigned long long* norm_bits,
                                  cudaStream_t s);
+// The same on the register-pass engine (64 <= M <= kShortMaxM), tspec in its
+// spectral order (launch_spectra_rp).
+template <class Tin>
+cudaError_t launch_defect_hybrid_rp(const Tin* u, const Tin* f, float* r, const Cx<float>* tspec,
+                                    size_t spec_stride, const Cx<float>* tw, const Tin* zero,
+                                    const LevelShape& ls, Tin hinv2, unsigned long long* norm_bits,
+                                    cudaStream_t s);
 // Per instance b: u = broadcast of g_b along time (initial iterate u^0(t) = g);
 // f += c_b d_{b,m} g_b.  g: batch * N, dk: batch * (M+1), c: batch (device).
 cudaError_t launch_initial(double* u, double* f, const double* g, const double* dk, const double* c,

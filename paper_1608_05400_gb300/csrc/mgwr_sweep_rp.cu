@@ -7,55 +7,6 @@ namespace mgwr {
 
 namespace {
 
-// Radix plans per transform length (L = 2^7 .. 2^13): two or three passes,
-// the last of radix 32; T threads per line pair, 256 threads per block.
-#define MGWR_RP_PLANS(X)      \
-  X(13, 16, 16, 32, 256)      \
-  X(12, 8, 16, 32, 128)       \
-  X(11, 8, 8, 32, 64)         \
-  X(10, 32, 32, 0, 32)        \
-  X(9, 16, 32, 0, 16)         \
-  X(8, 8, 32, 0, 8)           \
-  X(7, 4, 32, 0, 4)
-
-constexpr int kRpBlock = 256;
-
-__host__ __device__ inline int rp_plan(int logL, int* r) {
-  switch (logL) {
-#define MGWR_RP_PLAN_CASE(LG, A, B, C, T) \
-  case LG:                                \
-    r[0] = A;                             \
-    r[1] = B;                             \
-    r[2] = C;                             \
-    return C != 0 ? 3 : 2;
-    MGWR_RP_PLANS(MGWR_RP_PLAN_CASE)
-#undef MGWR_RP_PLAN_CASE
-    default:
-      return 0;
-  }
-}
-
-// Radices of the shared-memory engine of mgwr_fft.cuh for length 2^logL:
-// radix-8 stages, then radix 2^(logL mod 3) when that is not 0.
-__host__ __device__ inline int engine_plan(int logL, int* r) {
-  int np = 0;
-  for (int k = 0; k < logL / 3; ++k) r[np++] = 8;
-  if (logL % 3 != 0) r[np++] = 1 << (logL % 3);
-  return np;
-}
-
-// Barrier of the T threads of one line pair (PAIRS pairs per block).
-template <int T, int PAIRS>
-__device__ __forceinline__ void group_sync(int g) {
-  if constexpr (PAIRS == 1) {
-    __syncthreads();
-  } else if constexpr (T <= 32) {
-    __syncwarp();  // every group of a warp runs the same barrier sequence
-  } else {
-    asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(T) : "memory");
-  }
-}
-
 template <int LOGL, int R0, int R1, int R2, int T>
 __global__ void __launch_bounds__(kRpBlock, 2)
     k_sweep_rp(const float* __restrict__ f, float* __restrict__ u, float* __restrict__ delta,
@@ -92,124 +43,25 @@ __global__ void __launch_bounds__(kRpBlock, 2)
   if (!valid) qA[0] = qA[1] = qA[2] = qA[3] = zero;
   if (!hasB) qB[0] = qB[1] = qB[2] = qB[3] = zero;
 
-  // ---- pass 0: gather the right-hand sides (every load of the thread issued
-  // before the first DFT), half-input DFT, twiddles
-  constexpr int NB0 = P::S0 / T;
-  C in[NB0][R0 / 2];
-#pragma unroll
-  for (int i = 0; i < NB0; ++i) {
-#pragma unroll
-    for (int q = 0; q < R0 / 2; ++q) {
-      const int m = t + T * i + q * P::S0;
-      if (d == 2)
-        in[i][q] = C{fA[m] + hinv2 * ((qA[0][m] + qA[1][m]) + (qA[2][m] + qA[3][m])),
-                     fB[m] + hinv2 * ((qB[0][m] + qB[1][m]) + (qB[2][m] + qB[3][m]))};
-      else
-        in[i][q] = C{fA[m] + hinv2 * (qA[0][m] + qA[1][m]), fB[m] + hinv2 * (qB[0][m] + qB[1][m])};
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < NB0; ++i) {
-    const int j = t + T * i;
-    const rp::TwBase<R0> tb(tw, j);
-    C v[R0];
-#pragma unroll
-    for (int q = 0; q < R0 / 2; ++q) v[q] = in[i][q];
-    rp::dft_half<R0>(v);
-    rp::twiddle_apply<R0, false>(v, tb);
-#pragma unroll
-    for (int k = 0; k < R0; ++k) buf[P::idx(j + k * P::S0)] = v[k];
-  }
-  group_sync<T, PAIRS>(g);
-
-  // ---- pass 1 when there are three: radix R1 on groups of G1, twiddles w_G1^{jk}
-  if constexpr (P::NP == 3) {
-    constexpr int NB1 = (P::L / R1) / T;
-#pragma unroll 1
-    for (int i = 0; i < NB1; ++i) {
-      const int beta = t + T * i;
-      const int grp = beta / P::S1, j = beta - grp * P::S1;
-      const int base = grp * P::G1 + j;
-      const rp::TwBase<R1> tb(tw, j * R0);
-      C v[R1];
-#pragma unroll
-      for (int q = 0; q < R1; ++q) v[q] = buf[P::idx(base + q * P::S1)];
-      rp::Dft<R1, false>::run(v);
-      rp::twiddle_apply<R1, false>(v, tb);
-#pragma unroll
-      for (int q = 0; q < R1; ++q) buf[P::idx(base + q * P::S1)] = v[q];
-    }
-    group_sync<T, PAIRS>(g);
-  }
-
-  // ---- last pass (contiguous RL values), spectrum product, its inverse
-  constexpr int RL = P::RL;
-  constexpr int NBL = (P::L / RL) / T;
-#pragma unroll 1
-  for (int i = 0; i < NBL; ++i) {
-    const int base = (t + T * i) * RL;
-    C v[RL];
-#pragma unroll
-    for (int q = 0; q < RL; ++q) v[q] = buf[P::idx(base + q)];
-    rp::Dft<RL, false>::run(v);
-    const float4* sp = reinterpret_cast<const float4*>(spec + base);
-#pragma unroll
-    for (int q = 0; q < RL / 2; ++q) {
-      const float4 s2 = __ldg(sp + q);
-      v[2 * q] = cmul(v[2 * q], C{s2.x, s2.y});
-      v[2 * q + 1] = cmul(v[2 * q + 1], C{s2.z, s2.w});
-    }
-    rp::Dft<RL, true>::run(v);
-#pragma unroll
-    for (int q = 0; q < RL; ++q) buf[P::idx(base + q)] = v[q];
-  }
-  group_sync<T, PAIRS>(g);
-
-  // ---- inverse of pass 1
-  if constexpr (P::NP == 3) {
-    constexpr int NB1 = (P::L / R1) / T;
-#pragma unroll 1
-    for (int i = 0; i < NB1; ++i) {
-      const int beta = t + T * i;
-      const int grp = beta / P::S1, j = beta - grp * P::S1;
-      const int base = grp * P::G1 + j;
-      const rp::TwBase<R1> tb(tw, j * R0);
-      C v[R1];
-#pragma unroll
-      for (int q = 0; q < R1; ++q) v[q] = buf[P::idx(base + q * P::S1)];
-      rp::twiddle_apply<R1, true>(v, tb);
-      rp::Dft<R1, true>::run(v);
-#pragma unroll
-      for (int q = 0; q < R1; ++q) buf[P::idx(base + q * P::S1)] = v[q];
-    }
-    group_sync<T, PAIRS>(g);
-  }
-
-  // ---- inverse of pass 0: the first M outputs, the update and the change record
+  auto load = [&](int m) -> C {
+    if (d == 2)
+      return C{fA[m] + hinv2 * ((qA[0][m] + qA[1][m]) + (qA[2][m] + qA[3][m])),
+               fB[m] + hinv2 * ((qB[0][m] + qB[1][m]) + (qB[2][m] + qB[3][m]))};
+    return C{fA[m] + hinv2 * (qA[0][m] + qA[1][m]), fB[m] + hinv2 * (qB[0][m] + qB[1][m])};
+  };
   float* uA = u + pAM;
   float* uB = u + pBM;
-#pragma unroll
-  for (int i = 0; i < NB0; ++i) {
-    const int j = t + T * i;
-    const rp::TwBase<R0> tb(tw, j);
-    C v[R0];
-#pragma unroll
-    for (int k = 0; k < R0; ++k) v[k] = buf[P::idx(j + k * P::S0)];
-    rp::twiddle_apply<R0, true>(v, tb);
-    rp::Dft<R0, true>::run(v);
+  auto store = [&](int m, C y) {
     if (valid) {
-#pragma unroll
-      for (int q = 0; q < R0 / 2; ++q) {
-        const int m = j + q * P::S0;
-        if (delta != nullptr) delta[pAM + m] = v[q].x - uA[m];
-        uA[m] = v[q].x;
-        if (hasB) {
-          if (delta != nullptr) delta[pBM + m] = v[q].y - uB[m];
-          uB[m] = v[q].y;
-        }
+      if (delta != nullptr) delta[pAM + m] = y.x - uA[m];
+      uA[m] = y.x;
+      if (hasB) {
+        if (delta != nullptr) delta[pBM + m] = y.y - uB[m];
+        uB[m] = y.y;
       }
     }
-  }
+  };
+  rp::convolve<LOGL, R0, R1, R2, T, PAIRS>(buf, t, g, spec, tw, load, store);
 }
 
 // spec_rp[c L + rp position of k] = (float) spec64[c L + engine position of k]

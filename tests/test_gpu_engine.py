@@ -272,8 +272,8 @@ def test_tensor_solve_converges_like_the_fft_solve(precision, d, n, M, batch):
             s.set_engine_split(K["sweep32"], split)
             s.set_rhs(f)
             st = s.solve(1, 1, 1, tol=1e-10, max_cycles=40)
-            out.append((s.solution(), st.cycles))
-    assert abs(out[1][1] - out[0][1]) <= 2
+            out.append((s.solution(), st.outer))
+    assert abs(out[1][1] - out[0][1]) <= 1  # outer steps: different FP32 rounding may need one more
     assert rel(out[1][0], out[0][0]) <= 1e-9
 
 
@@ -342,6 +342,6 @@ def test_radix_solve_converges_like_the_fft_solve(precision, d, n, M, batch):
             s.set_engine_split(K["sweep32"], split)
             s.set_rhs(f)
             st = s.solve(1, 1, 1, tol=1e-10, max_cycles=40)
-            out.append((s.solution(), st.cycles))
-    assert abs(out[1][1] - out[0][1]) <= 2
+            out.append((s.solution(), st.outer))
+    assert abs(out[1][1] - out[0][1]) <= 1  # outer steps: different FP32 rounding may need one more
     assert rel(out[1][0], out[0][0]) <= 1e-9

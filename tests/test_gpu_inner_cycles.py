@@ -172,3 +172,31 @@ def test_smooth_restrict_on_the_wide_hierarchies(hier):
         ref = omg.restrict_fw(W.defect(l, ref_u, f), d, n)
         scale = np.abs(f).max() + W.levels[l].sigma * 2 * np.abs(ref_u).max()
         assert np.abs(s.field_get(hier, l - 1, G.MGWR_F) - ref).max() <= tol * scale
+
+
+@pytest.mark.parametrize("precision", [G.MGWR_MIXED, G.MGWR_MIXED_DD])
+@pytest.mark.parametrize("d,n,M", [(2, 31, 1024), (1, 255, 64), (2, 15, 4096), (1, 63, 512)])
+def test_outer_defect_of_a_refinement_step_matches_oracle(precision, d, n, M):
+    # One outer step of the refinement, then its outer defect, which becomes the
+    # FP32 right-hand side of the next step's inner cycles: with the switch at 0
+    # every outer defect takes the FP32-convolution form (T_M u by one FP32
+    # convolution of the rounded iterate, f - A_h u in the outer precision), whose
+    # error is about 1e-6 of |T_M u|; with the switch at +inf the defect is exact
+    # before its rounding to FP32.  Both against the oracle's direct-sum defect.
+    W = omg.WRMG(d, n, M, 1.0, 0.55)
+    f = inputs.random_field(n ** d, M, seed=21)
+    L = W.finest
+    for switch in (0.0, math.inf):
+        with G.Solver(d, n, M, 1.0, 0.55) as s:
+            s.set_precision(precision)
+            s.set_outer_switch(switch)
+            s.set_rhs(f)
+            s.solve(1, 1, 1, tol=1e-300, max_cycles=1, allow_noconv=True)
+            u = s.solution()
+            r32 = s.field_get(G.MGWR_H32, L, G.MGWR_F)
+        ref = W.defect(L, u, f)
+        tu = np.abs(u @ W.Tm.T).max()
+        err = np.abs(r32 - ref).max()
+        rounding = 2.0 ** -23 * np.abs(ref).max()
+        bound = (2e-6 * tu if switch == 0.0 else 0.0) + rounding
+        assert err <= bound, (switch, err, bound, tu)

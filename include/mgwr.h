@@ -137,6 +137,15 @@ int mgwr_create(int d, int n, int M, double T, double alpha, mgwr_t* out);
 int mgwr_create_batch(int d, int n, int M, const double* T, const double* alpha, int batch,
                       mgwr_t* out);
 int mgwr_batch_size(mgwr_t h, int* batch);
+/* Gives the handle's instances new final times T[b] and orders alpha[b]
+ * (batch values each, host; as for mgwr_create_batch) without allocating:
+ * the L1 columns, the inverse columns of every level and their spectra
+ * (Sec. 5) are recomputed in place, with every copy the handle's precisions
+ * keep.  Nothing is recomputed when the values are the ones the handle has.
+ * The right-hand side and iterate stay; the next solve measures its relative
+ * defect from its own start.  A handle set up this way solves bitwise as one
+ * created with these values.  MGWR_E_INVAL for bad values. */
+int mgwr_set_problem(mgwr_t h, const double* T, const double* alpha);
 /* Per-instance relative defect ||f_b - A u_b||_inf / ||f_b - A u0_b||_inf after
  * the last mgwr_solve / mgwr_residual (batch doubles). */
 int mgwr_instance_relres(mgwr_t h, double* relres);
@@ -252,6 +261,45 @@ int mgwr_set_initial(mgwr_t h, const double* u0);
  * stats may be NULL. */
 int mgwr_solve(mgwr_t h, int cycle, int nu1, int nu2, double tol, int max_cycles,
                mgwr_stats* stats);
+/* ---- groups: several solves advancing together --------------------------- */
+/* A group runs the solves of several handles together (no counterpart in the
+ * paper).  Members may differ in every respect (d, n, M, batch, T, alpha,
+ * precision, cycle, tolerance); each runs exactly the launches mgwr_solve
+ * would, so its result is bitwise the one it gets alone, and each iteration of
+ * all running members is one CUDA graph launch on the group's stream whose
+ * branches, one per member on the member's own stream, run concurrently on
+ * the device (graphs of the recent member combinations are kept, at most 8).
+ * Handles join (mgwr_group_add, which computes the initial defect) and leave
+ * (their solve ended: collected with mgwr_group_collect) between iterations,
+ * so a serving loop admits new work while other solves are in flight.  While
+ * in a group a handle must not be used otherwise, and no two members may share
+ * a stream.  Group calls are not thread-safe per group. */
+typedef struct mgwr_group* mgwr_group_t;
+int mgwr_group_create(mgwr_group_t* out);
+int mgwr_group_destroy(mgwr_group_t g);
+const char* mgwr_group_last_error(mgwr_group_t g);
+/* Starts h's solve as mgwr_solve does (arguments as there): the initial defect
+ * is computed now, synchronously on h's stream.  MGWR_E_STATE for a handle
+ * with profiling on, or one already in the group or sharing a member's
+ * stream. */
+int mgwr_group_add(mgwr_group_t g, mgwr_t h, int cycle, int nu1, int nu2, double tol,
+                   int max_cycles);
+/* One iteration of every running member (one graph launch, synchronous).
+ * Members whose solve has ended move to the finished list; *running (may be
+ * NULL) gets the number still running. */
+int mgwr_group_step(mgwr_group_t g, int* running);
+/* Takes the oldest finished member: its handle, mgwr_solve's status for it and
+ * its statistics.  MGWR_E_AGAIN when none has finished. */
+int mgwr_group_collect(mgwr_group_t g, mgwr_t* h, int* status, mgwr_stats* stats);
+/* Graph launches so far, member iterations they ran, most members in one. */
+int mgwr_group_info(mgwr_group_t g, long long* launches, long long* member_iterations,
+                    int* max_members);
+/* All `count` handles solved as one group until every solve has ended;
+ * status[i] and stats[i] (stats may be NULL) as mgwr_solve's for handles[i].
+ * Returns MGWR_OK, or the first error of the group itself. */
+int mgwr_group_solve(mgwr_t* handles, int count, int cycle, int nu1, int nu2, double tol,
+                     int max_cycles, int* status, mgwr_stats* stats);
+
 /* Defect of the current iterate in FP64: *relres = ||f - A u||_inf /
  * ||f - A u0||_inf (u0 the iterate at set_rhs / set_initial), optional copy of
  * the defect to r_host (N*M doubles). */
@@ -331,10 +379,18 @@ int mgwr_inverse_column_noalloc(const double* r_dev, int M, double sigma, double
 int mgwr_footprint(int d, int n, int M, int batch, int precision, size_t* bytes);
 
 /* ---- serving: submit / poll ----------------------------------------------- */
-/* A server owns `max_slots` worker threads, each running one request at a
- * time on its own CUDA stream, and admits queued requests while the sum of
- * their footprints (mgwr_footprint) stays within `hbm_budget` bytes.  Requests
- * of any shape may be in flight together; their kernels overlap on the device.
+/* A server admits queued requests while the sum of their footprints
+ * (mgwr_footprint) and of its idle handles stays within `hbm_budget` bytes,
+ * at most `max_slots` at a time.  A worker thread per slot prepares each
+ * admitted request's handle (an idle handle of the same d, n, M and resolved
+ * precision, set up in place for the request's T and alpha by
+ * mgwr_set_problem, else a new one; at most 8 idle handles are kept, the least
+ * recently used evicted first, also when their memory keeps a request out) and
+ * copies its data in; then the request joins the server's group
+ * (mgwr_group_*): one batcher thread advances every running request together,
+ * each iteration of all of them one CUDA graph launch whose branches run
+ * concurrently on the device.  A request that arrives while others run starts
+ * at the next iteration boundary; its result is bitwise what it gets alone.
  * Admission order (mgwr_server_set_policy; the paper has no counterpart):
  * MGWR_POLICY_FIFO (default), the oldest request that fits runs first;
  * MGWR_POLICY_SMALLEST, the request with the fewest space-time unknowns n^d*M
@@ -363,8 +419,12 @@ typedef struct {
 } mgwr_result;
 typedef struct {
   long long queued, admitted, completed;
-  size_t in_use_bytes, peak_bytes, budget_bytes;
+  size_t in_use_bytes, peak_bytes, budget_bytes;  /* in use: running + idle handles */
   int slots;
+  int max_group_members;      /* most solves advanced by one graph launch        */
+  long long group_launches;   /* graph launches of the group so far              */
+  long long member_iterations;/* solve iterations those launches ran             */
+  long long reused_handles;   /* requests served by an idle handle of their shape */
 } mgwr_server_info;
 /* MGWR_E_INVAL (bad arguments), MGWR_E_CUDA (no device). */
 int mgwr_server_create(size_t hbm_budget, int max_slots, mgwr_server_t* out);

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <deque>
 #include <map>
 #include <mutex>
 #include <new>
@@ -730,13 +731,17 @@ int enqueue_iteration(mgwr_t h, int cyc, int nu1, int nu2, bool* exact) {
 // Runs one iteration: replays the captured graph when it matches the current
 // settings (capturing it first if needed), else enqueues the launches
 // directly; then waits and decodes the norms.
-int run_iteration(mgwr_t h, int cyc, int nu1, int nu2, std::vector<double>& norms, bool* exact) {
-  // the launch sequence also depends on the state of the finest FP64 defect field
-  // it starts from (the first FP64 iteration from u = 0 restricts f itself)
+// Identifies the launch sequence of the next iteration: the settings, the
+// outer-defect form and the state of the finest FP64 defect field it starts
+// from (the first FP64 iteration from u = 0 restricts f itself).
+long long iteration_key(const mgwr_handle* h, int cyc, int nu1, int nu2) {
   const int rs_in = h->precision == MGWR_FP64 ? h->h64.rs[h->nlev - 1] : 0;
-  const long long key =
-      ((((((long long)h->precision * 4 + cyc) * 32 + nu1) * 32 + nu2) * 32 * 4 +
-        (long long)step_cycles(h) * 4 + h->order) * 2 + (h->loose_outer ? 1 : 0)) * 4 + rs_in;
+  return ((((((long long)h->precision * 4 + cyc) * 32 + nu1) * 32 + nu2) * 32 * 4 +
+           (long long)step_cycles(h) * 4 + h->order) * 2 + (h->loose_outer ? 1 : 0)) * 4 + rs_in;
+}
+
+int run_iteration(mgwr_t h, int cyc, int nu1, int nu2, std::vector<double>& norms, bool* exact) {
+  const long long key = iteration_key(h, cyc, nu1, nu2);
   if (h->use_graphs && !h->profiling) {
     const mgwr_handle::IterGraph* slot = nullptr;
     for (const auto& g : h->graphs)
@@ -975,6 +980,79 @@ void keep_pool_memory() {
   done.push_back(dev);
 }
 
+// The per-instance setup of Sec. 5 from h->alpha, h->c: the L1 Toeplitz
+// columns, the inverse columns of every level by divide and conquer, and the
+// FP64 spectra of both (twiddles already in place).  Temporaries come
+// stream-ordered from the pool and are returned; synchronises the stream.
+int setup_columns(mgwr_t h) {
+  const size_t B = h->B;
+  const int M = h->M;
+  double *sig_dev = nullptr, *alpha_dev = nullptr;
+  Cx<double>* work = nullptr;
+  int s = dev_alloc(h, &alpha_dev, sizeof(double) * B);
+  if (s == MGWR_OK) s = dev_alloc(h, &sig_dev, sizeof(double) * h->nlev);
+  if (s == MGWR_OK) s = dev_alloc(h, &work, sizeof(Cx<double>) * B * h->nlev * 3 * M);
+  cudaError_t e = cudaSuccess;
+  if (s == MGWR_OK) {
+    e = cudaMemcpyAsync(sig_dev, h->sigma.data(), sizeof(double) * h->nlev,
+                        cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h->c_dev, h->c.data(), sizeof(double) * B, cudaMemcpyHostToDevice,
+                          h->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(alpha_dev, h->alpha.data(), sizeof(double) * B, cudaMemcpyHostToDevice,
+                          h->stream);
+    if (e == cudaSuccess)
+      e = mgwr::launch_coefficients(h->r, h->dk, M, alpha_dev, h->c_dev, h->B, h->stream);
+    if (e == cudaSuccess)
+      e = mgwr::launch_inverse_columns(h->kcol, h->r, sig_dev, h->nlev, M, h->B, work, h->stream);
+    if (e == cudaSuccess)
+      e = mgwr::launch_spectra(h->h64.spec, h->kcol, h->B * h->nlev, M, h->h64.tw, h->stream);
+    if (e == cudaSuccess)
+      e = mgwr::launch_spectra(h->h64.tspec, h->r, h->B, M, h->h64.tw, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  }
+  // the temporaries are no longer needed
+  for (void* p : {(void*)work, (void*)sig_dev, (void*)alpha_dev}) {
+    if (p == nullptr) continue;
+    cudaFreeAsync(p, h->stream);
+    h->allocs.erase(std::find(h->allocs.begin(), h->allocs.end(), p));
+  }
+  if (s != MGWR_OK) return s;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, MGWR_E_CUDA, std::string("setup: ") + cudaGetErrorString(e));
+  }
+  h->h64.ready = true;
+  return MGWR_OK;
+}
+
+// The copies of the FP64 setup that the other arithmetics keep (rounded FP32
+// spectra, their register-pass order, the tensor-core bands, double-float
+// splits), recomputed after setup_columns changed the FP64 ones.
+int refresh_derived(mgwr_t h) {
+  const size_t nspec = (size_t)h->B * h->nlev * h->L;
+  if (h->h32.ready) {
+    MGWR_CK(h, mgwr::launch_round_cx(h->h32.spec, h->h64.spec, nspec, h->stream));
+    MGWR_CK(h, mgwr::launch_round_cx(h->h32.tspec, h->h64.tspec, (size_t)h->B * h->L, h->stream));
+    if (h->h32.spec_rp != nullptr)
+      MGWR_CK(h, mgwr::launch_spectra_rp(h->h32.spec_rp, h->h64.spec, (size_t)h->B * h->nlev,
+                                         h->M, h->stream));
+    if (h->h32.tspec_rp != nullptr)
+      MGWR_CK(h, mgwr::launch_spectra_rp(h->h32.tspec_rp, h->h64.tspec, (size_t)h->B, h->M,
+                                         h->stream));
+    if (h->tc_band != nullptr)
+      MGWR_CK(h, mgwr::launch_band_bf16x3(h->kcol, h->tc_band, h->M, (size_t)h->B * h->nlev,
+                                          h->stream));
+  }
+  if (h->tspec_dd != nullptr)
+    MGWR_CK(h, mgwr::launch_split_cx(h->tspec_dd, h->h64.tspec, (size_t)h->B * h->L, h->stream));
+  if (h->hdd.ready)
+    MGWR_CK(h, mgwr::launch_split_cx(h->hdd.spec, h->h64.spec, nspec, h->stream));
+  MGWR_CK(h, cudaStreamSynchronize(h->stream));
+  return MGWR_OK;
+}
+
 int create_impl(int d, int n, int M, const double* T, const double* alpha, int batch,
                 mgwr_t* out) {
   if (out == nullptr) return MGWR_E_INVAL;
@@ -1035,16 +1113,11 @@ int create_impl(int d, int n, int M, const double* T, const double* alpha, int b
   }
   const size_t B = batch;
   int s;
-  double *sig_dev = nullptr, *alpha_dev = nullptr;
-  Cx<double>* work = nullptr;
   if ((s = dev_alloc(h, &h->norm_bits, sizeof(unsigned long long) * B)) != MGWR_OK) return bail(s);
   if ((s = dev_alloc(h, &h->r, sizeof(double) * B * M)) != MGWR_OK) return bail(s);
   if ((s = dev_alloc(h, &h->dk, sizeof(double) * B * (M + 1))) != MGWR_OK) return bail(s);
   if ((s = dev_alloc(h, &h->kcol, sizeof(double) * B * h->nlev * M)) != MGWR_OK) return bail(s);
   if ((s = dev_alloc(h, &h->c_dev, sizeof(double) * B)) != MGWR_OK) return bail(s);
-  if ((s = dev_alloc(h, &alpha_dev, sizeof(double) * B)) != MGWR_OK) return bail(s);
-  if ((s = dev_alloc(h, &sig_dev, sizeof(double) * h->nlev)) != MGWR_OK) return bail(s);
-  if ((s = dev_alloc(h, &work, sizeof(Cx<double>) * B * h->nlev * 3 * M)) != MGWR_OK) return bail(s);
   if ((s = dev_alloc(h, &h->h64.spec, sizeof(Cx<double>) * B * h->nlev * h->L)) != MGWR_OK)
     return bail(s);
   if ((s = dev_alloc(h, &h->h64.tspec, sizeof(Cx<double>) * B * h->L)) != MGWR_OK) return bail(s);
@@ -1054,31 +1127,11 @@ int create_impl(int d, int n, int M, const double* T, const double* alpha, int b
     if ((s = dev_alloc(h, &h->scratch, sizeof(Cx<double>) * h->scratch_count)) != MGWR_OK)
       return bail(s);
   }
-
-  cudaError_t e = cudaMemcpyAsync(sig_dev, h->sigma.data(), sizeof(double) * h->nlev,
-                                  cudaMemcpyHostToDevice, h->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(h->c_dev, h->c.data(), sizeof(double) * B, cudaMemcpyHostToDevice,
-                        h->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(alpha_dev, h->alpha.data(), sizeof(double) * B, cudaMemcpyHostToDevice,
-                        h->stream);
-  if (e == cudaSuccess)
-    e = mgwr::launch_coefficients(h->r, h->dk, M, alpha_dev, h->c_dev, batch, h->stream);
-  if (e == cudaSuccess)
-    e = mgwr::launch_inverse_columns(h->kcol, h->r, sig_dev, h->nlev, M, batch, work, h->stream);
-  if (e == cudaSuccess) e = mgwr::launch_twiddles(h->h64.tw, h->Lt, h->stream);
-  if (e == cudaSuccess)
-    e = mgwr::launch_spectra(h->h64.spec, h->kcol, batch * h->nlev, M, h->h64.tw, h->stream);
-  if (e == cudaSuccess) e = mgwr::launch_spectra(h->h64.tspec, h->r, batch, M, h->h64.tw, h->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  if (e != cudaSuccess) {
+  if (mgwr::launch_twiddles(h->h64.tw, h->Lt, h->stream) != cudaSuccess) {
     cudaGetLastError();
     return bail(MGWR_E_CUDA);
   }
-  // the divide-and-conquer work area is no longer needed
-  cudaFreeAsync(work, h->stream);
-  h->allocs.erase(std::find(h->allocs.begin(), h->allocs.end(), (void*)work));
+  if ((s = setup_columns(h)) != MGWR_OK) return bail(s);
   h->h64.ready = true;
   // the finest iterate and right-hand side always exist; the rest on demand
   const int Lf = h->nlev - 1;
@@ -1142,6 +1195,26 @@ int mgwr_create(int d, int n, int M, double T, double alpha, mgwr_t* out) {
 int mgwr_create_batch(int d, int n, int M, const double* T, const double* alpha, int batch,
                       mgwr_t* out) {
   return create_impl(d, n, M, T, alpha, batch, out);
+}
+
+int mgwr_set_problem(mgwr_t h, const double* T, const double* alpha) {
+  if (h == nullptr) return MGWR_E_INVAL;
+  if (T == nullptr || alpha == nullptr) return fail(h, MGWR_E_INVAL, "null T or alpha");
+  for (int b = 0; b < h->B; ++b) {
+    if (!(T[b] > 0.0) || !std::isfinite(T[b]) || !(alpha[b] > 0.0) || !(alpha[b] <= 1.0))
+      return fail(h, MGWR_E_INVAL, "need T > 0 finite and 0 < alpha <= 1");
+  }
+  bool same = true;
+  for (int b = 0; b < h->B; ++b) same = same && T[b] == h->T[b] && alpha[b] == h->alpha[b];
+  h->r0_valid = false;
+  if (same) return MGWR_OK;  // the setup of this (T, alpha) is already resident
+  for (int b = 0; b < h->B; ++b) {
+    h->T[b] = T[b];
+    h->alpha[b] = alpha[b];
+    h->c[b] = std::pow(T[b] / h->M, -alpha[b]) / std::tgamma(2.0 - alpha[b]);
+  }
+  MGWR_TRY(setup_columns(h));
+  return refresh_derived(h);
 }
 
 int mgwr_batch_size(mgwr_t h, int* batch) {
@@ -1337,139 +1410,467 @@ int mgwr_set_initial(mgwr_t h, const double* u0) {
   return MGWR_OK;
 }
 
-int mgwr_solve(mgwr_t h, int cyc, int nu1, int nu2, double tol, int max_cycles, mgwr_stats* st) {
-  if (h == nullptr) return MGWR_E_INVAL;
-  MGWR_TRY(check_cycle_args(h, cyc, nu1, nu2));
-  if (!(tol >= 0.0) || max_cycles < 1) return fail(h, MGWR_E_INVAL, "need tol >= 0, max_cycles >= 1");
-  // refinement: inner cycles on the defect equation (FP32 or double-float),
-  // the outer defect in FP64 or double-float
-  const bool mixed = h->precision != MGWR_FP64;
-  const bool ddef = h->precision == MGWR_MIXED_DD || h->precision == MGWR_DD;
-  const bool ddc = h->precision == MGWR_DD;  // double-float inner cycles
-  if (h->precision == MGWR_FP64) MGWR_TRY(ensure_full(h, h->h64));
-  const int L = h->nlev - 1;
-  const size_t cntL = level_count(h, L);
-  mgwr_stats local{};
-  MGWR_CK(h, cudaEventRecord(h->ev0, h->stream));
-  std::vector<double> norms;
-  if (ddef) {
-    MGWR_CK(h, mgwr::launch_split(h->u_dd, h->h64.u[L], cntL, h->stream));
-    MGWR_CK(h, mgwr::launch_split(h->f_dd, h->h64.f[L], cntL, h->stream));
-  }
-  // the full defect of the finest level in the outer precision, with norms (in
-  // the refinements written as the inner right-hand side)
-  auto full_defect = [&]() -> int {
-    if (ddc) {
-      MGWR_TRY(clear_norms(h));
-      MGWR_TRY(outer_defect_ddd(h));
-      return read_norms(h, norms);
-    }
-    if (ddef) return finest_defect_norms_dd(h, norms);
-    return finest_defect_norms(h, norms, mixed);
-  };
-  if (h->u_zero) {
-    // the defect of u = 0 is f itself (Algorithm 1 from the zero iterate)
-    MGWR_TRY(clear_norms(h));
-    MGWR_CK(h, mgwr::launch_absmax_round(h->h64.f[L], mixed && !ddc ? h->h32.f[L] : nullptr,
-                                         cntL / h->B, h->B, h->norm_bits, h->stream));
-    if (ddc) {
-      MGWR_CK(h, mgwr::launch_split(h->hdd.f[L], h->h64.f[L], cntL, h->stream));
-      h->hdd.rs[L] = R_STALE;
-    } else if (mixed) {
-      h->h32.rs[L] = R_STALE;
-    } else {
-      h->h64.rs[L] = R_ZERO_U;
-    }
-    MGWR_TRY(read_norms(h, norms));
-  } else {
-    MGWR_TRY(full_defect());
-  }
-  if (!h->r0_valid) {
-    h->r0 = norms;
-    h->r0_valid = true;
-  }
-  double rel = relative(h, norms, h->relres);
+}  // extern "C"
+
+namespace {
+
+// State of one solve between its iterations: the loop of mgwr_solve, split so
+// that a group of handles can run each iteration of all its members as one
+// graph launch (mgwr_group_*) with exactly the launches a solo solve makes.
+struct SolveState {
+  int cyc = 1, nu1 = 1, nu2 = 1, max_cycles = 1;
+  double tol = 0.0;
+  bool mixed = false, ddef = false, ddc = false;
+  double rel = 0.0;
   int status = MGWR_OK;
   int cycles = 0, outer = 0;
   bool rel_exact = true;  // rel comes from the full defect (not from smoothing changes)
   // refinements: defect reduction of the last outer step and its inner cycles
   double last_q = 0.0;
   int last_k = 0;
-  while (!(rel <= tol)) {
-    if (!std::isfinite(rel)) {
-      status = MGWR_E_NUMERIC;
-      break;
-    }
-    if ((mixed ? outer : cycles) >= max_cycles) {
-      status = MGWR_E_NOCONV;
-      break;
-    }
-    bool exact = true;
-    // outer defects of the mixed modes while the defect is large (above
-    // kLooseOuter of the initial one before this step) take the FP32-convolution
-    // form, whose error (about 1e-6 of |f|) is then below 1e-3 of the defect
-    h->loose_outer = mixed && !ddc && rel >= h->loose_above;
-    // Refinements: when the last step's reduction predicts that this step ends
-    // just above the tolerance, but below half of it with one cycle more, this
-    // step takes that cycle instead of leaving a whole outer step (and its outer
-    // defect) for it.  One more cycle gains the last step's mean reduction per
-    // cycle only down to the floor of the inner precision: the rounding of the
-    // correction e (eps |e|) has a defect of about 4d/h^2 eps |e| against the
-    // smooth defect d pi^2 |e| left after a cycle, so no outer step reduces the
-    // defect below about 4 eps / (pi h)^2 (FP32: 6e-3 at h = 1/512).
-    h->inner_now = 0;
-    if (mixed && last_k > 0 && last_q > 0.0 && last_q < 1.0) {
-      const int k = inner_cycles(h);
-      const double per_cycle = std::pow(last_q, 1.0 / last_k);
-      const double hf = 1.0 / (h->n + 1);
-      const double eps = ddc ? std::ldexp(1.0, -44) : std::ldexp(1.0, -24);
-      const double pi = 3.14159265358979323846;
-      const double floor_q = 4.0 * eps / (pi * pi * hf * hf);
-      const double q_more = std::max(last_q * per_cycle, floor_q);
-      if (rel * last_q > tol && rel * q_more <= 0.5 * tol) h->inner_now = k + 1;
-    }
-    const double rel_before = rel;
-    const int k_now = mixed ? step_cycles(h) : 1;
-    MGWR_TRY(run_iteration(h, cyc, nu1, nu2, norms, &exact));
-    h->inner_now = 0;
-    cycles += k_now;
-    rel = relative(h, norms, h->relres);
-    if (mixed && rel_before > 0.0) {
-      last_q = rel / rel_before;
-      last_k = k_now;
-    }
-    // the stopping decision is always taken on the full defect
-    if (!exact && rel <= tol) {
-      MGWR_TRY(full_defect());
-      rel = relative(h, norms, h->relres);
-      exact = true;
-    }
-    rel_exact = exact;
-    ++outer;
+  // the iteration being run
+  double rel_before = 0.0;
+  int k_now = 1;
+  std::vector<double> norms;
+};
+
+// The full defect of the finest level in the outer precision, with norms (in
+// the refinements written as the inner right-hand side).
+int solve_full_defect(mgwr_t h, SolveState& S) {
+  if (S.ddc) {
+    MGWR_TRY(clear_norms(h));
+    MGWR_TRY(outer_defect_ddd(h));
+    return read_norms(h, S.norms);
   }
+  if (S.ddef) return finest_defect_norms_dd(h, S.norms);
+  return finest_defect_norms(h, S.norms, S.mixed);
+}
+
+// Checks the arguments, starts the timing and computes the initial defect and
+// its norms (synchronises the handle's stream).
+int solve_begin(mgwr_t h, SolveState& S, int cyc, int nu1, int nu2, double tol, int max_cycles) {
+  MGWR_TRY(check_cycle_args(h, cyc, nu1, nu2));
+  if (!(tol >= 0.0) || max_cycles < 1) return fail(h, MGWR_E_INVAL, "need tol >= 0, max_cycles >= 1");
+  S = SolveState{};
+  S.cyc = cyc;
+  S.nu1 = nu1;
+  S.nu2 = nu2;
+  S.tol = tol;
+  S.max_cycles = max_cycles;
+  // refinement: inner cycles on the defect equation (FP32 or double-float),
+  // the outer defect in FP64 or double-float
+  S.mixed = h->precision != MGWR_FP64;
+  S.ddef = h->precision == MGWR_MIXED_DD || h->precision == MGWR_DD;
+  S.ddc = h->precision == MGWR_DD;  // double-float inner cycles
+  if (h->precision == MGWR_FP64) MGWR_TRY(ensure_full(h, h->h64));
+  const int L = h->nlev - 1;
+  const size_t cntL = level_count(h, L);
+  MGWR_CK(h, cudaEventRecord(h->ev0, h->stream));
+  if (S.ddef) {
+    MGWR_CK(h, mgwr::launch_split(h->u_dd, h->h64.u[L], cntL, h->stream));
+    MGWR_CK(h, mgwr::launch_split(h->f_dd, h->h64.f[L], cntL, h->stream));
+  }
+  if (h->u_zero) {
+    // the defect of u = 0 is f itself (Algorithm 1 from the zero iterate)
+    MGWR_TRY(clear_norms(h));
+    MGWR_CK(h, mgwr::launch_absmax_round(h->h64.f[L], S.mixed && !S.ddc ? h->h32.f[L] : nullptr,
+                                         cntL / h->B, h->B, h->norm_bits, h->stream));
+    if (S.ddc) {
+      MGWR_CK(h, mgwr::launch_split(h->hdd.f[L], h->h64.f[L], cntL, h->stream));
+      h->hdd.rs[L] = R_STALE;
+    } else if (S.mixed) {
+      h->h32.rs[L] = R_STALE;
+    } else {
+      h->h64.rs[L] = R_ZERO_U;
+    }
+    MGWR_TRY(read_norms(h, S.norms));
+  } else {
+    MGWR_TRY(solve_full_defect(h, S));
+  }
+  if (!h->r0_valid) {
+    h->r0 = S.norms;
+    h->r0_valid = true;
+  }
+  S.rel = relative(h, S.norms, h->relres);
+  return MGWR_OK;
+}
+
+// Decides whether another iteration runs (false: the loop ends, S.status set)
+// and prepares its form on the handle (outer-defect form, inner cycles).
+bool solve_plan(mgwr_t h, SolveState& S) {
+  if (S.rel <= S.tol) return false;
+  if (!std::isfinite(S.rel)) {
+    S.status = MGWR_E_NUMERIC;
+    return false;
+  }
+  if ((S.mixed ? S.outer : S.cycles) >= S.max_cycles) {
+    S.status = MGWR_E_NOCONV;
+    return false;
+  }
+  // outer defects of the mixed modes while the defect is large (at least the
+  // handle's switch, kLooseOuter by default) take the FP32-convolution form,
+  // whose error (about 1e-6 of |T_M u|) is then far below the defect
+  h->loose_outer = S.mixed && !S.ddc && S.rel >= h->loose_above;
+  // Refinements: when the last step's reduction predicts that this step ends
+  // just above the tolerance, but below half of it with one cycle more, this
+  // step takes that cycle instead of leaving a whole outer step (and its outer
+  // defect) for it.  One more cycle gains the last step's mean reduction per
+  // cycle only down to the floor of the inner precision: the rounding of the
+  // correction e (eps |e|) has a defect of about 4d/h^2 eps |e| against the
+  // smooth defect d pi^2 |e| left after a cycle, so no outer step reduces the
+  // defect below about 4 eps / (pi h)^2 (FP32: 6e-3 at h = 1/512).
+  h->inner_now = 0;
+  if (S.mixed && S.last_k > 0 && S.last_q > 0.0 && S.last_q < 1.0) {
+    const int k = inner_cycles(h);
+    const double per_cycle = std::pow(S.last_q, 1.0 / S.last_k);
+    const double hf = 1.0 / (h->n + 1);
+    const double eps = S.ddc ? std::ldexp(1.0, -44) : std::ldexp(1.0, -24);
+    const double pi = 3.14159265358979323846;
+    const double floor_q = 4.0 * eps / (pi * pi * hf * hf);
+    const double q_more = std::max(S.last_q * per_cycle, floor_q);
+    if (S.rel * S.last_q > S.tol && S.rel * q_more <= 0.5 * S.tol) h->inner_now = k + 1;
+  }
+  S.rel_before = S.rel;
+  S.k_now = S.mixed ? step_cycles(h) : 1;
+  return true;
+}
+
+// Takes in the norms an iteration left in the handle's pinned buffer (the
+// stream is synchronised); the stopping decision is always taken on the full
+// defect, computed here when the iteration's norms came from smoothing changes.
+int solve_after(mgwr_t h, SolveState& S, bool exact) {
+  h->inner_now = 0;
+  S.norms.resize(h->B);
+  for (int b = 0; b < h->B; ++b) std::memcpy(&S.norms[b], &h->norm_host[b], sizeof(double));
+  S.cycles += S.k_now;
+  S.rel = relative(h, S.norms, h->relres);
+  if (S.mixed && S.rel_before > 0.0) {
+    S.last_q = S.rel / S.rel_before;
+    S.last_k = S.k_now;
+  }
+  if (!exact && S.rel <= S.tol) {
+    MGWR_TRY(solve_full_defect(h, S));
+    S.rel = relative(h, S.norms, h->relres);
+    exact = true;
+  }
+  S.rel_exact = exact;
+  ++S.outer;
+  return MGWR_OK;
+}
+
+// Ends a solve: the iterate back in FP64, the full defect when the last norms
+// were not, the timing and the statistics.
+int solve_end(mgwr_t h, SolveState& S, mgwr_stats* st) {
+  const int L = h->nlev - 1;
+  const size_t cntL = level_count(h, L);
   h->u_zero = false;
   h->loose_outer = false;
-  if (ddef) MGWR_CK(h, mgwr::launch_join(h->h64.u[L], h->u_dd, cntL, h->stream));
-  if (!rel_exact) {  // report the full defect also when stopping on max_cycles
-    MGWR_TRY(finest_defect_norms(h, norms, false));
-    rel = relative(h, norms, h->relres);
+  if (S.ddef) MGWR_CK(h, mgwr::launch_join(h->h64.u[L], h->u_dd, cntL, h->stream));
+  if (!S.rel_exact) {  // report the full defect also when stopping on max_cycles
+    MGWR_TRY(finest_defect_norms(h, S.norms, false));
+    S.rel = relative(h, S.norms, h->relres);
   }
-  if (!std::isfinite(rel)) status = MGWR_E_NUMERIC;
+  int status = S.status;
+  if (!std::isfinite(S.rel)) status = MGWR_E_NUMERIC;
   MGWR_CK(h, cudaEventRecord(h->ev1, h->stream));
   MGWR_CK(h, cudaEventSynchronize(h->ev1));
   MGWR_TRY(check_staging(h));
   prof_collect(h);
   float ms = 0.f;
   MGWR_CK(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
-  local.cycles = cycles;
-  local.outer = outer;
-  local.relres = rel;
-  local.factor = cycles > 0 && rel > 0.0 ? std::pow(rel, 1.0 / cycles) : 0.0;
+  mgwr_stats local{};
+  local.cycles = S.cycles;
+  local.outer = S.outer;
+  local.relres = S.rel;
+  local.factor = S.cycles > 0 && S.rel > 0.0 ? std::pow(S.rel, 1.0 / S.cycles) : 0.0;
   local.seconds = ms * 1e-3;
   if (st != nullptr) *st = local;
   if (status == MGWR_E_NOCONV) h->err = "max_cycles reached before the tolerance";
   if (status == MGWR_E_NUMERIC) h->err = "non-finite residual norm";
   return status;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mgwr_solve(mgwr_t h, int cyc, int nu1, int nu2, double tol, int max_cycles, mgwr_stats* st) {
+  if (h == nullptr) return MGWR_E_INVAL;
+  SolveState S;
+  MGWR_TRY(solve_begin(h, S, cyc, nu1, nu2, tol, max_cycles));
+  while (solve_plan(h, S)) {
+    bool exact = true;
+    std::vector<double> unused;
+    MGWR_TRY(run_iteration(h, cyc, nu1, nu2, unused, &exact));
+    MGWR_TRY(solve_after(h, S, exact));
+  }
+  return solve_end(h, S, st);
+}
+
+}  // extern "C"
+
+// A group of handles solved together: each member runs exactly the launches of
+// its own solve (mgwr_solve), and every iteration of all running members is
+// one CUDA graph launch whose branches, one per member, run concurrently on
+// the device.  Members may differ in every setting (d, n, M, batch, precision,
+// cycle); they join and leave between iterations.
+struct mgwr_group {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t fork = nullptr;
+  struct Member {
+    mgwr_t h = nullptr;
+    SolveState S;
+    cudaEvent_t join = nullptr;
+  };
+  std::vector<Member> running;
+  struct Done {
+    mgwr_t h;
+    int status;
+    mgwr_stats st;
+  };
+  std::deque<Done> finished;
+  // instantiated iteration graphs by the (member, iteration key) list they serve
+  struct Entry {
+    std::vector<std::pair<mgwr_t, long long>> key;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<char> exact;
+    long long kernels = 0;
+    unsigned long long used = 0;
+  };
+  std::vector<Entry> graphs;
+  unsigned long long clock = 0;
+  long long launches = 0, member_iterations = 0;
+  int max_members = 0;
+  std::string err;
+};
+
+namespace {
+
+constexpr size_t kGroupGraphs = 8;
+
+void group_drop_graphs_of(mgwr_group* g, mgwr_t h) {
+  for (size_t i = 0; i < g->graphs.size();) {
+    bool uses = false;
+    for (const auto& k : g->graphs[i].key) uses = uses || k.first == h;
+    if (uses) {
+      cudaGraphExecDestroy(g->graphs[i].exec);
+      g->graphs.erase(g->graphs.begin() + i);
+    } else {
+      ++i;
+    }
+  }
+}
+
+void group_finish(mgwr_group* g, size_t i, int status) {
+  mgwr_group::Member& m = g->running[i];
+  mgwr_stats st{};
+  int code = status;
+  if (code == MGWR_OK) code = solve_end(m.h, m.S, &st);
+  group_drop_graphs_of(g, m.h);
+  cudaEventDestroy(m.join);
+  g->finished.push_back({m.h, code, st});
+  g->running.erase(g->running.begin() + i);
+}
+
+// Captures one iteration of every running member (their launches on their own
+// streams, forked from and joined to the group's stream) as one graph.
+int group_capture(mgwr_group* g, mgwr_group::Entry& e) {
+  cudaGraph_t graph = nullptr;
+  cudaError_t ce = cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal);
+  if (ce != cudaSuccess) {
+    cudaGetLastError();
+    g->err = cudaGetErrorString(ce);
+    return MGWR_E_CUDA;
+  }
+  const long long before = mgwr::launch_counter();
+  int st = MGWR_OK;
+  if (cudaEventRecord(g->fork, g->stream) != cudaSuccess) st = MGWR_E_CUDA;
+  e.exact.assign(g->running.size(), 1);
+  for (size_t i = 0; i < g->running.size() && st == MGWR_OK; ++i) {
+    mgwr_group::Member& m = g->running[i];
+    const mgwr_group::Member& mm = m;
+    if (cudaStreamWaitEvent(m.h->stream, g->fork, 0) != cudaSuccess) {
+      st = MGWR_E_CUDA;
+      break;
+    }
+    bool ex = true;
+    st = enqueue_iteration(m.h, mm.S.cyc, mm.S.nu1, mm.S.nu2, &ex);
+    e.exact[i] = ex ? 1 : 0;
+    if (st == MGWR_OK && (cudaEventRecord(m.join, m.h->stream) != cudaSuccess ||
+                          cudaStreamWaitEvent(g->stream, m.join, 0) != cudaSuccess))
+      st = MGWR_E_CUDA;
+  }
+  ce = cudaStreamEndCapture(g->stream, &graph);
+  const long long captured = mgwr::launch_counter() - before;
+  mgwr::add_launches(-captured);  // counted when the graph runs
+  if (st == MGWR_OK && ce != cudaSuccess) st = MGWR_E_CUDA;
+  if (st == MGWR_OK && cudaGraphInstantiate(&e.exec, graph, 0) != cudaSuccess) st = MGWR_E_CUDA;
+  if (graph != nullptr) cudaGraphDestroy(graph);
+  if (st != MGWR_OK) {
+    cudaGetLastError();
+    g->err = "capture of the group iteration failed";
+    return st;
+  }
+  e.kernels = captured;
+  return MGWR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mgwr_group_create(mgwr_group_t* out) {
+  if (out == nullptr) return MGWR_E_INVAL;
+  *out = nullptr;
+  mgwr_group_t g = new (std::nothrow) mgwr_group;
+  if (g == nullptr) return MGWR_E_NOMEM;
+  if (cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&g->fork, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    mgwr_group_destroy(g);
+    return MGWR_E_CUDA;
+  }
+  *out = g;
+  return MGWR_OK;
+}
+
+int mgwr_group_destroy(mgwr_group_t g) {
+  if (g == nullptr) return MGWR_OK;
+  if (g->stream) cudaStreamSynchronize(g->stream);
+  for (auto& e : g->graphs) cudaGraphExecDestroy(e.exec);
+  for (auto& m : g->running) cudaEventDestroy(m.join);
+  if (g->fork) cudaEventDestroy(g->fork);
+  if (g->stream) cudaStreamDestroy(g->stream);
+  cudaGetLastError();
+  delete g;
+  return MGWR_OK;
+}
+
+const char* mgwr_group_last_error(mgwr_group_t g) {
+  return g == nullptr ? "null group" : g->err.c_str();
+}
+
+int mgwr_group_add(mgwr_group_t g, mgwr_t h, int cyc, int nu1, int nu2, double tol,
+                   int max_cycles) {
+  if (g == nullptr || h == nullptr) return MGWR_E_INVAL;
+  if (h->profiling) return fail(h, MGWR_E_STATE, "a profiled handle cannot join a group");
+  for (const auto& m : g->running)
+    if (m.h == h || m.h->stream == h->stream)
+      return fail(h, MGWR_E_STATE, "the handle, or its stream, is already in the group");
+  mgwr_group::Member m;
+  m.h = h;
+  MGWR_TRY(solve_begin(h, m.S, cyc, nu1, nu2, tol, max_cycles));
+  if (cudaEventCreateWithFlags(&m.join, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, MGWR_E_CUDA, "event creation failed");
+  }
+  g->running.push_back(m);
+  return MGWR_OK;
+}
+
+int mgwr_group_step(mgwr_group_t g, int* running) {
+  if (g == nullptr) return MGWR_E_INVAL;
+  // members whose solve has ended leave; the others prepare their next iteration
+  for (size_t i = 0; i < g->running.size();) {
+    if (!solve_plan(g->running[i].h, g->running[i].S))
+      group_finish(g, i, MGWR_OK);
+    else
+      ++i;
+  }
+  if (g->running.empty()) {
+    if (running != nullptr) *running = 0;
+    return MGWR_OK;
+  }
+  std::vector<std::pair<mgwr_t, long long>> key;
+  for (const auto& m : g->running)
+    key.emplace_back(m.h, iteration_key(m.h, m.S.cyc, m.S.nu1, m.S.nu2));
+  mgwr_group::Entry* e = nullptr;
+  for (auto& c : g->graphs)
+    if (c.key == key) e = &c;
+  if (e == nullptr) {
+    if (g->graphs.size() >= kGroupGraphs) {  // the least recently used one goes
+      size_t old = 0;
+      for (size_t i = 1; i < g->graphs.size(); ++i)
+        if (g->graphs[i].used < g->graphs[old].used) old = i;
+      cudaGraphExecDestroy(g->graphs[old].exec);
+      g->graphs.erase(g->graphs.begin() + old);
+    }
+    mgwr_group::Entry fresh;
+    fresh.key = key;
+    MGWR_TRY(group_capture(g, fresh));
+    g->graphs.push_back(std::move(fresh));
+    e = &g->graphs.back();
+  }
+  e->used = ++g->clock;
+  cudaError_t ce = cudaGraphLaunch(e->exec, g->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(g->stream);
+  if (ce != cudaSuccess) {
+    cudaGetLastError();
+    g->err = cudaGetErrorString(ce);
+    return MGWR_E_CUDA;
+  }
+  mgwr::add_launches(e->kernels);
+  g->launches++;
+  g->member_iterations += (long long)g->running.size();
+  g->max_members = std::max(g->max_members, (int)g->running.size());
+  const std::vector<char> exact = e->exact;
+  for (size_t i = 0, k = 0; i < g->running.size(); ++k) {
+    const int st = solve_after(g->running[i].h, g->running[i].S, exact[k] != 0);
+    if (st != MGWR_OK)
+      group_finish(g, i, st);
+    else
+      ++i;
+  }
+  if (running != nullptr) *running = (int)g->running.size();
+  return MGWR_OK;
+}
+
+int mgwr_group_collect(mgwr_group_t g, mgwr_t* h, int* status, mgwr_stats* st) {
+  if (g == nullptr || h == nullptr) return MGWR_E_INVAL;
+  if (g->finished.empty()) return MGWR_E_AGAIN;
+  const mgwr_group::Done d = g->finished.front();
+  g->finished.pop_front();
+  *h = d.h;
+  if (status != nullptr) *status = d.status;
+  if (st != nullptr) *st = d.st;
+  return MGWR_OK;
+}
+
+int mgwr_group_info(mgwr_group_t g, long long* launches, long long* member_iterations,
+                    int* max_members) {
+  if (g == nullptr) return MGWR_E_INVAL;
+  if (launches != nullptr) *launches = g->launches;
+  if (member_iterations != nullptr) *member_iterations = g->member_iterations;
+  if (max_members != nullptr) *max_members = g->max_members;
+  return MGWR_OK;
+}
+
+int mgwr_group_solve(mgwr_t* handles, int count, int cyc, int nu1, int nu2, double tol,
+                     int max_cycles, int* status, mgwr_stats* stats) {
+  if (handles == nullptr || count < 1 || status == nullptr) return MGWR_E_INVAL;
+  for (int i = 0; i < count; ++i)
+    if (handles[i] == nullptr) return MGWR_E_INVAL;
+  mgwr_group_t g = nullptr;
+  MGWR_TRY(mgwr_group_create(&g));
+  int st = MGWR_OK;
+  for (int i = 0; i < count; ++i) {
+    status[i] = mgwr_group_add(g, handles[i], cyc, nu1, nu2, tol, max_cycles);
+    if (status[i] != MGWR_OK && st == MGWR_OK) st = status[i];
+  }
+  int left = 1;
+  while (st == MGWR_OK && left > 0) st = mgwr_group_step(g, &left);
+  mgwr_t h = nullptr;
+  int code = 0;
+  mgwr_stats one{};
+  while (mgwr_group_collect(g, &h, &code, &one) == MGWR_OK) {
+    for (int i = 0; i < count; ++i) {
+      if (handles[i] != h) continue;
+      status[i] = code;
+      if (stats != nullptr) stats[i] = one;
+    }
+  }
+  mgwr_group_destroy(g);
+  return st;
 }
 
 int mgwr_residual(mgwr_t h, double* relres, double* r_host) {

@@ -1,13 +1,16 @@
 // Serving runtime: a request queue in front of the solver.  Requests of any
 // shape (d, n, M) and any (T, alpha, precision) are submitted from any host
-// thread, admitted while their device-memory footprint fits the budget and a
-// slot is free, and solved concurrently: every slot is a worker thread whose
-// handles run on their own CUDA stream, so the kernels of all admitted requests
-// overlap on the device.  A request that arrives while others run is admitted
-// as soon as memory and a slot are free (continuous batching at request
-// granularity); its result does not depend on what else runs (each solve is a
-// fixed sequence of kernels on its own data, and the only cross-block
-// reduction is an order-independent maximum).
+// thread and admitted while their device-memory footprint fits the budget and
+// a slot is free.  A slot's worker thread prepares the request's handle (from
+// a pool of idle handles of the same shape and precision, re-parameterised in
+// place by mgwr_set_problem, else a new one) and copies its data in; the
+// request then joins the server's group (mgwr_group_*), where one batcher
+// thread advances every admitted solve together: each iteration of all of them
+// is one CUDA graph launch whose branches run concurrently on the device.
+// Requests join and leave between iterations, so one that arrives while others
+// are on the GPU starts at the next iteration (continuous batching at
+// iteration granularity).  Each solve runs exactly the launches it runs alone,
+// so its result does not depend on what else runs.
 #include <cuda_runtime.h>
 
 #include <chrono>
@@ -16,8 +19,10 @@
 #include <cstdlib>
 #include <deque>
 #include <map>
+#include <list>
 #include <memory>
 #include <mutex>
+#include <tuple>
 #include <new>
 #include <thread>
 #include <unordered_map>
@@ -130,6 +135,8 @@ struct Ticket {
   size_t footprint = 0;
   size_t N = 0;
   int state = 0;  // 0 queued, 1 running, 2 done
+  mgwr_t h = nullptr;   // its handle while it runs
+  bool solved = false;  // the group has finished its solve (status in res)
   int skipped = 0;
   Clock::time_point t_submit, t_admit, t_done;
   mgwr_result res{};
@@ -140,19 +147,35 @@ bool pow2(long long x) { return x > 0 && (x & (x - 1)) == 0; }
 
 }  // namespace
 
+// Idle handles kept for later requests of the same shape and precision.
+struct IdleHandle {
+  std::tuple<int, int, int, int> key;  // d, n, M, resolved precision
+  mgwr_t h;
+  size_t bytes;
+};
+
 struct mgwr_server {
   PinnedPool pool;  // declared first: outlives the tickets that hold its buffers
   size_t budget = 0, in_use = 0, peak = 0;
   int slots = 1, max_queue = 1 << 20, device = 0;
   int policy = MGWR_POLICY_FIFO;
   std::mutex mu;
-  std::condition_variable cv_work, cv_done;
+  std::condition_variable cv_work, cv_done, cv_batch, cv_solved;
   std::deque<Ticket*> queue;
   std::unordered_map<uint64_t, std::unique_ptr<Ticket>> tickets;
   std::vector<std::thread> workers;
+  std::thread batcher;
   bool stop = false;
+  bool stop_batcher = false;  // set once every worker has left
   uint64_t next_id = 1;
   long long completed = 0, admitted = 0;
+  // the group every admitted solve runs in, and the requests about to join it
+  mgwr_group_t group = nullptr;
+  std::vector<Ticket*> joining;
+  // idle handles, most recently used first; their bytes count in in_use
+  std::list<IdleHandle> idle;
+  size_t idle_bytes = 0;
+  long long reused = 0;
 };
 
 namespace {
@@ -188,25 +211,87 @@ Ticket* pick(mgwr_server* s) {
   return t;
 }
 
-int run_request(Ticket* t) {
+constexpr size_t kMaxIdle = 8;  // idle handles kept at most
+
+std::tuple<int, int, int, int> shape_key(const mgwr_request& q) {
+  int prec = q.precision;
+  mgwr_auto_precision(q.d, q.n, q.M, q.precision, &prec);
+  return std::make_tuple(q.d, q.n, q.M, prec);
+}
+
+// Destroys idle handles (least recently used first) until `need` more bytes fit
+// the budget or none is left; called with the lock held, destroys outside it.
+std::vector<mgwr_t> evict_for(mgwr_server* s, size_t need) {
+  std::vector<mgwr_t> out;
+  while (!s->idle.empty() && (s->in_use + need > s->budget || s->idle.size() > kMaxIdle)) {
+    out.push_back(s->idle.back().h);
+    s->in_use -= s->idle.back().bytes;
+    s->idle_bytes -= s->idle.back().bytes;
+    s->idle.pop_back();
+  }
+  return out;
+}
+
+// The request's handle: an idle one of its shape and precision, set up in
+// place for its (T, alpha) (nothing to redo when those match too), else a new
+// one; then its settings and data.
+int prepare(mgwr_server* s, Ticket* t) {
   const mgwr_request& q = t->rq;
   mgwr_t h = nullptr;
-  int st = mgwr_create(q.d, q.n, q.M, q.T, q.alpha, &h);
-  if (st != MGWR_OK) return st;
-  if (q.precision != MGWR_FP64) st = mgwr_set_precision(h, q.precision);
-  if (st == MGWR_OK && q.order == MGWR_ORDER_TABLE) st = mgwr_set_order(h, q.order);
-  if (st == MGWR_OK) st = mgwr_set_rhs(h, t->f.data(), t->g.empty() ? nullptr : t->g.data());
-  mgwr_stats stats{};
-  if (st == MGWR_OK) {
-    st = mgwr_solve(h, q.cycle, q.nu1, q.nu2, q.tol, q.max_cycles, &stats);
-    t->res.stats = stats;
-    if (st == MGWR_OK || st == MGWR_E_NOCONV) {
-      const int st2 = t->u.alloc(t->pool, t->N * q.M) ? mgwr_get_solution(h, t->u.data())
-                                                      : MGWR_E_NOMEM;
-      if (st2 != MGWR_OK) st = st2;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    for (auto it = s->idle.begin(); it != s->idle.end(); ++it) {
+      if (it->key != shape_key(q)) continue;
+      h = it->h;
+      // its bytes now belong to the request: the request's footprint was added on
+      // admission, so the idle share goes
+      s->in_use -= it->bytes;
+      s->idle_bytes -= it->bytes;
+      s->idle.erase(it);
+      s->reused++;
+      break;
     }
   }
-  mgwr_destroy(h);
+  int st = MGWR_OK;
+  if (h != nullptr) {
+    st = mgwr_set_problem(h, &q.T, &q.alpha);
+  } else {
+    st = mgwr_create(q.d, q.n, q.M, q.T, q.alpha, &h);
+    if (st == MGWR_OK && q.precision != MGWR_FP64) st = mgwr_set_precision(h, q.precision);
+  }
+  if (st == MGWR_OK) st = mgwr_set_order(h, q.order);
+  if (st == MGWR_OK) st = mgwr_set_rhs(h, t->f.data(), t->g.empty() ? nullptr : t->g.data());
+  if (st != MGWR_OK && h != nullptr) {
+    mgwr_destroy(h);
+    h = nullptr;
+  }
+  t->h = h;
+  return st;
+}
+
+// After the solve: the result copied out, the handle kept idle (or destroyed).
+int finish(mgwr_server* s, Ticket* t, int st) {
+  const mgwr_request& q = t->rq;
+  if (st == MGWR_OK || st == MGWR_E_NOCONV) {
+    const int st2 = t->u.alloc(t->pool, t->N * q.M) ? mgwr_get_solution(t->h, t->u.data())
+                                                    : MGWR_E_NOMEM;
+    if (st2 != MGWR_OK) st = st2;
+  }
+  std::vector<mgwr_t> drop;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->in_use -= t->footprint;
+    if (st == MGWR_OK || st == MGWR_E_NOCONV) {
+      s->idle.push_front({shape_key(q), t->h, t->footprint});
+      s->in_use += t->footprint;
+      s->idle_bytes += t->footprint;
+      drop = evict_for(s, 0);
+    } else {
+      drop.push_back(t->h);
+    }
+    t->h = nullptr;
+  }
+  for (mgwr_t h : drop) mgwr_destroy(h);
   return st;
 }
 
@@ -214,9 +299,19 @@ void worker(mgwr_server* s) {
   cudaSetDevice(s->device);
   for (;;) {
     Ticket* t = nullptr;
+    std::vector<mgwr_t> drop;
     {
       std::unique_lock<std::mutex> lk(s->mu);
-      s->cv_work.wait(lk, [&] { return s->stop || (t = pick(s)) != nullptr; });
+      s->cv_work.wait(lk, [&] {
+        if (s->stop) return true;
+        t = pick(s);
+        if (t == nullptr && !s->idle.empty() && !s->queue.empty()) {
+          // idle handles may be what keeps the oldest request out
+          drop = evict_for(s, s->queue.front()->footprint);
+          t = pick(s);
+        }
+        return t != nullptr;
+      });
       if (t == nullptr) return;  // stopping
       s->in_use += t->footprint;
       if (s->in_use > s->peak) s->peak = s->in_use;
@@ -224,10 +319,24 @@ void worker(mgwr_server* s) {
       t->t_admit = Clock::now();
       s->admitted++;
     }
-    const int st = run_request(t);
-    {
+    for (mgwr_t h : drop) mgwr_destroy(h);
+    int st = prepare(s, t);
+    if (st == MGWR_OK) {
+      // the batcher adds it to the group at the next iteration boundary
+      std::unique_lock<std::mutex> lk(s->mu);
+      s->joining.push_back(t);
+      s->cv_batch.notify_all();
+      s->cv_solved.wait(lk, [&] { return t->solved; });
+      st = t->res.status;
+    }
+    if (t->h != nullptr) {
+      st = finish(s, t, st);
+    } else {
       std::lock_guard<std::mutex> lk(s->mu);
       s->in_use -= t->footprint;
+    }
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
       t->t_done = Clock::now();
       t->res.status = st;
       t->res.queue_s = std::chrono::duration<double>(t->t_admit - t->t_submit).count();
@@ -237,6 +346,64 @@ void worker(mgwr_server* s) {
     }
     s->cv_done.notify_all();
     s->cv_work.notify_all();
+  }
+}
+
+// The batcher: admits prepared requests into the group between iterations and
+// advances all of them, one graph launch per iteration.
+void batcher(mgwr_server* s) {
+  cudaSetDevice(s->device);
+  std::unordered_map<mgwr_t, Ticket*> members;
+  for (;;) {
+    std::vector<Ticket*> join;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      s->cv_batch.wait(lk, [&] {
+        return s->stop_batcher || !s->joining.empty() || !members.empty();
+      });
+      if (s->stop_batcher && members.empty() && s->joining.empty()) return;
+      join.swap(s->joining);
+    }
+    std::vector<Ticket*> failed;
+    for (Ticket* t : join) {
+      const mgwr_request& q = t->rq;
+      const int st = mgwr_group_add(s->group, t->h, q.cycle, q.nu1, q.nu2, q.tol, q.max_cycles);
+      if (st == MGWR_OK) {
+        members[t->h] = t;
+      } else {
+        t->res.status = st;
+        failed.push_back(t);
+      }
+    }
+    int left = 0;
+    const int gst = members.empty() ? MGWR_OK : mgwr_group_step(s->group, &left);
+    std::vector<Ticket*> done = failed;
+    mgwr_t h = nullptr;
+    int code = 0;
+    mgwr_stats st{};
+    while (mgwr_group_collect(s->group, &h, &code, &st) == MGWR_OK) {
+      auto it = members.find(h);
+      if (it == members.end()) continue;
+      it->second->res.status = code;
+      it->second->res.stats = st;
+      done.push_back(it->second);
+      members.erase(it);
+    }
+    if (gst != MGWR_OK) {  // the group itself failed: every member fails with it
+      mgwr_group_destroy(s->group);
+      s->group = nullptr;
+      mgwr_group_create(&s->group);
+      for (auto& kv : members) {
+        kv.second->res.status = gst;
+        done.push_back(kv.second);
+      }
+      members.clear();
+    }
+    if (!done.empty()) {
+      std::lock_guard<std::mutex> lk(s->mu);
+      for (Ticket* t : done) t->solved = true;
+      s->cv_solved.notify_all();
+    }
   }
 }
 
@@ -275,7 +442,12 @@ int mgwr_server_create(size_t hbm_budget, int max_slots, mgwr_server_t* out) {
   s->budget = hbm_budget;
   s->slots = max_slots;
   cudaGetDevice(&s->device);
+  if (mgwr_group_create(&s->group) != MGWR_OK) {
+    delete s;
+    return MGWR_E_CUDA;
+  }
   for (int i = 0; i < max_slots; ++i) s->workers.emplace_back(worker, s);
+  s->batcher = std::thread(batcher, s);
   *out = s;
   return MGWR_OK;
 }
@@ -299,7 +471,15 @@ int mgwr_server_destroy(mgwr_server_t s) {
     s->queue.clear();
   }
   s->cv_work.notify_all();
-  for (auto& w : s->workers) w.join();
+  for (auto& w : s->workers) w.join();  // each finishes its running request first
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop_batcher = true;
+  }
+  s->cv_batch.notify_all();
+  s->batcher.join();
+  for (auto& i : s->idle) mgwr_destroy(i.h);
+  mgwr_group_destroy(s->group);
   delete s;
   return MGWR_OK;
 }
@@ -368,6 +548,13 @@ int mgwr_server_stats(mgwr_server_t s, mgwr_server_info* info) {
   info->peak_bytes = s->peak;
   info->budget_bytes = s->budget;
   info->slots = s->slots;
+  info->reused_handles = s->reused;
+  long long launches = 0, iters = 0;
+  int most = 0;
+  mgwr_group_info(s->group, &launches, &iters, &most);
+  info->group_launches = launches;
+  info->member_iterations = iters;
+  info->max_group_members = most;
   return MGWR_OK;
 }
 

@@ -58,7 +58,9 @@ class mgwr_result(C.Structure):
 class mgwr_server_info(C.Structure):
     _fields_ = [("queued", C.c_longlong), ("admitted", C.c_longlong), ("completed", C.c_longlong),
                 ("in_use_bytes", C.c_size_t), ("peak_bytes", C.c_size_t),
-                ("budget_bytes", C.c_size_t), ("slots", C.c_int)]
+                ("budget_bytes", C.c_size_t), ("slots", C.c_int),
+                ("max_group_members", C.c_int), ("group_launches", C.c_longlong),
+                ("member_iterations", C.c_longlong), ("reused_handles", C.c_longlong)]
 
 
 _h = C.c_void_p
@@ -67,6 +69,18 @@ _SIGS = {
     "mgwr_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.POINTER(_h)]),
     "mgwr_create_batch": (C.c_int, [C.c_int, C.c_int, C.c_int, _dp, _dp, C.c_int, C.POINTER(_h)]),
     "mgwr_batch_size": (C.c_int, [_h, C.POINTER(C.c_int)]),
+    "mgwr_set_problem": (C.c_int, [_h, _dp, _dp]),
+    "mgwr_group_create": (C.c_int, [C.POINTER(C.c_void_p)]),
+    "mgwr_group_destroy": (C.c_int, [C.c_void_p]),
+    "mgwr_group_last_error": (C.c_char_p, [C.c_void_p]),
+    "mgwr_group_add": (C.c_int, [C.c_void_p, _h, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int]),
+    "mgwr_group_step": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
+    "mgwr_group_collect": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_int),
+                                     C.POINTER(mgwr_stats)]),
+    "mgwr_group_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
+                                  C.POINTER(C.c_int)]),
+    "mgwr_group_solve": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int, C.c_int,
+                                   C.c_double, C.c_int, C.POINTER(C.c_int), C.POINTER(mgwr_stats)]),
     "mgwr_instance_relres": (C.c_int, [_h, _dp]),
     "mgwr_destroy": (C.c_int, [_h]),
     "mgwr_last_error": (C.c_char_p, [_h]),
@@ -234,6 +248,14 @@ class Solver:
         self.close()
 
     # -- configuration --
+    def set_problem(self, T, alpha):
+        """New final times and orders for the instances, set up in place."""
+        alphas = np.atleast_1d(np.asarray(alpha, dtype=np.float64)).copy()
+        Ts = np.broadcast_to(np.asarray(T, dtype=np.float64), alphas.shape).copy()
+        assert alphas.size == self.B
+        self._check(self.lib.mgwr_set_problem(self.h, _ptr(Ts), _ptr(alphas)), "mgwr_set_problem")
+        self.T, self.alpha = T, alpha
+
     def set_precision(self, prec: int):
         self._check(self.lib.mgwr_set_precision(self.h, prec), "mgwr_set_precision")
 
@@ -475,6 +497,76 @@ class Server:
         if getattr(self, "h", None):
             self.lib.mgwr_server_destroy(self.h)
             self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Group:
+    """Solvers advancing together (mgwr_group_*): every iteration of all running
+    members is one CUDA graph launch; results are bitwise those of solo solves."""
+
+    def __init__(self):
+        self.lib = load()
+        g = C.c_void_p()
+        st = self.lib.mgwr_group_create(C.byref(g))
+        if st != MGWR_OK:
+            raise MGWRError(st, "mgwr_group_create failed")
+        self.g = g
+        self.members = {}
+
+    def _check(self, st: int, what: str, solver=None, ok=(MGWR_OK,)):
+        if st not in ok:
+            msg = (self.lib.mgwr_last_error(solver.h).decode() if solver is not None
+                   else self.lib.mgwr_group_last_error(self.g).decode())
+            raise MGWRError(st, f"{what}: {msg}")
+        return st
+
+    def add(self, solver: "Solver", cycle=1, nu1=1, nu2=1, tol=1e-10, max_cycles=100):
+        self._check(self.lib.mgwr_group_add(self.g, solver.h, cycle, nu1, nu2, tol, max_cycles),
+                    "mgwr_group_add", solver)
+        self.members[solver.h.value] = solver
+
+    def step(self) -> int:
+        left = C.c_int()
+        self._check(self.lib.mgwr_group_step(self.g, C.byref(left)), "mgwr_group_step")
+        return left.value
+
+    def collect(self):
+        """[(solver, Stats)] of the members finished since the last call."""
+        out = []
+        while True:
+            h, code, st = C.c_void_p(), C.c_int(), mgwr_stats()
+            if self.lib.mgwr_group_collect(self.g, C.byref(h), C.byref(code), C.byref(st)) != MGWR_OK:
+                return out
+            solver = self.members.pop(h.value)
+            out.append((solver, Stats(st.cycles, st.outer, st.relres, st.factor, st.seconds,
+                                      code.value)))
+
+    def run(self):
+        """Steps until every member has finished; returns collect()'s list."""
+        while self.step() > 0:
+            pass
+        return self.collect()
+
+    def info(self) -> dict:
+        a, b, c = C.c_longlong(), C.c_longlong(), C.c_int()
+        self._check(self.lib.mgwr_group_info(self.g, C.byref(a), C.byref(b), C.byref(c)), "info")
+        return {"launches": a.value, "member_iterations": b.value, "max_members": c.value}
+
+    def close(self):
+        if getattr(self, "g", None):
+            self.lib.mgwr_group_destroy(self.g)
+            self.g = None
 
     def __enter__(self):
         return self

@@ -172,3 +172,16 @@ def test_fas_calls_reject_a_null_handle(lib):
     assert lib.mgwr_fas_field_set(None, 0, 0, None) == mgwr.MGWR_E_INVAL
     assert lib.mgwr_fas_field_get(None, 0, 0, None) == mgwr.MGWR_E_INVAL
     assert lib.mgwr_fas_last_error(None) == b"null handle"
+
+
+def test_group_and_set_problem_reject_invalid_arguments_on_host(lib):
+    h = C.c_void_p()
+    assert lib.mgwr_group_add(None, None, 1, 1, 1, 1e-10, 10) == mgwr.MGWR_E_INVAL
+    assert lib.mgwr_group_step(None, None) == mgwr.MGWR_E_INVAL
+    assert lib.mgwr_group_collect(None, C.byref(h), None, None) == mgwr.MGWR_E_INVAL
+    assert lib.mgwr_group_info(None, None, None, None) == mgwr.MGWR_E_INVAL
+    assert lib.mgwr_group_destroy(None) == mgwr.MGWR_OK
+    assert lib.mgwr_group_create(None) == mgwr.MGWR_E_INVAL
+    st = (C.c_int * 1)()
+    assert lib.mgwr_group_solve(None, 1, 1, 1, 1, 1e-10, 10, st, None) == mgwr.MGWR_E_INVAL
+    assert lib.mgwr_set_problem(None, None, None) == mgwr.MGWR_E_INVAL

@@ -116,3 +116,36 @@ def test_admission_policy_orders_queued_requests(policy):
         assert min(r.latency_s for r in rs) > rl.latency_s
     with pytest.raises(G.MGWRError):
         G.Server(hbm_budget=1 << 30, slots=1).set_policy(7)
+
+
+def test_requests_in_flight_share_graph_launches_and_reuse_handles():
+    # requests submitted together run in the server's group: one graph launch
+    # advances several of them; a later request of a shape seen before is served
+    # by the idle handle of that shape, set up again for its (T, alpha); every
+    # result is bitwise the request solved alone
+    reqs = [(1, 63, 64, 0.5, "t2", G.MGWR_FP64), (2, 31, 128, 0.3, "talpha", G.MGWR_MIXED),
+            (2, 15, 256, 0.7, "t2", G.MGWR_MIXED_DD), (1, 255, 512, 0.45, "t2", G.MGWR_MIXED),
+            (2, 63, 64, 0.9, "t2", G.MGWR_FP64), (1, 127, 256, 0.25, "talpha", G.MGWR_DD)]
+    fs = [inputs.Problem(d, n, M, 1.0, a, k).rhs() for d, n, M, a, k, _ in reqs]
+    with G.Server(hbm_budget=8 << 30, slots=6) as srv:
+        tickets = [srv.submit(d, n, M, 1.0, a, f, precision=p, tol=1e-10)
+                   for (d, n, M, a, k, p), f in zip(reqs, fs)]
+        results = [srv.poll(t, timeout_us=120_000_000) for t in tickets]
+        info = srv.info()
+        # the same shapes again with other orders: idle handles set up in place
+        again = [(d, n, M, min(a + 0.05, 0.95), k, p) for d, n, M, a, k, p in reqs]
+        fs2 = [inputs.Problem(d, n, M, 1.0, a, k).rhs() for d, n, M, a, k, _ in again]
+        results2 = []
+        for (d, n, M, a, k, p), f in zip(again, fs2):
+            t = srv.submit(d, n, M, 1.0, a, f, precision=p, tol=1e-10)
+            results2.append(srv.poll(t, timeout_us=120_000_000))
+        info2 = srv.info()
+    assert info["max_group_members"] >= 2
+    assert info["member_iterations"] > info["group_launches"]
+    assert info2["reused_handles"] >= len(again)
+    for rq, f, res in list(zip(reqs, fs, results)) + list(zip(again, fs2, results2)):
+        d, n, M, a, k, p = rq
+        assert res.status == G.MGWR_OK
+        u, st = _alone(d, n, M, a, f, p, 1e-10)
+        np.testing.assert_array_equal(res.u, u)
+        assert res.stats.cycles == st.cycles and res.stats.relres == st.relres

@@ -117,7 +117,7 @@ def parse():
                    help="timed steps of each extra arm (default: fewer for slow arms)")
     p.add_argument("--e2e-steps", type=int, default=None,
                    help="timed steps of the end-to-end measurement (default min(steps, 5))")
-    p.add_argument("--requests", type=int, default=200, help="served: first R requests of the stream")
+    p.add_argument("--requests", type=int, default=2000, help="served: first R requests of the stream")
     p.add_argument("--slots", type=int, default=4, help="served: server slots")
     p.add_argument("--rate", type=float, default=None,
                    help="served: Poisson arrival rate, requests/s (default 0.7 x the sustained rate)")
@@ -683,18 +683,38 @@ def run_served(args):
             t0 = time.perf_counter()
 
             def submitter():
-                for i, rq in enumerate(reqs):
-                    wait = t0 + arrivals[i] - time.perf_counter()
-                    if wait > 0:
-                        time.sleep(wait)
-                    nbytes = 8 * unknowns(rq)
-                    with lock:
-                        lock.wait_for(lambda: outstanding[0] == 0 or outstanding[0] + nbytes <= host_cap)
-                        outstanding[0] += nbytes
-                    # time a request waited for host memory counts in its latency
-                    delay[i] = max(0.0, time.perf_counter() - (t0 + arrivals[i]))
-                    tickets[i] = srv.submit(rq["d"], rq["n"], rq["M"], 1.0, rq["alpha"], rhs(rq),
-                                            precision=prec, tol=tol)
+                # right-hand sides are generated ahead of their arrival by a pool of
+                # host threads (numpy releases the GIL), within the host window
+                import concurrent.futures as cf
+                pending = {}
+                nxt = [0]
+
+                def fill(pool):
+                    while nxt[0] < len(reqs):
+                        nbytes = 8 * unknowns(reqs[nxt[0]])
+                        with lock:
+                            if outstanding[0] and outstanding[0] + nbytes > host_cap:
+                                return
+                            outstanding[0] += nbytes
+                        pending[nxt[0]] = pool.submit(rhs, reqs[nxt[0]])
+                        nxt[0] += 1
+
+                with cf.ThreadPoolExecutor(8) as pool:
+                    for i, rq in enumerate(reqs):
+                        fill(pool)
+                        while i not in pending:  # the window is full: wait for completions
+                            with lock:
+                                lock.wait(0.01)
+                            fill(pool)
+                        f = pending.pop(i).result()
+                        wait = t0 + arrivals[i] - time.perf_counter()
+                        if wait > 0:
+                            time.sleep(wait)
+                        # time a request waited for its data counts in its latency
+                        delay[i] = max(0.0, time.perf_counter() - (t0 + arrivals[i]))
+                        tickets[i] = srv.submit(rq["d"], rq["n"], rq["M"], 1.0, rq["alpha"], f,
+                                                precision=prec, tol=tol)
+                        del f
 
             th = threading.Thread(target=submitter)
             th.start()
@@ -734,7 +754,7 @@ def run_served(args):
         "value": total / span2, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 0,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": DTYPES[precision], "data": "synthetic",
-        "config": {"workload": f"served stream: first {len(reqs)} of 2000 requests (seed 1608), "
+        "config": {"workload": f"served stream: {len(reqs)} of 2000 requests (seed 1608), "
                                "1-D n=2^k-1 k~U{5..12} or 2-D k~U{5..9}, M=2^j j~U{7..12}, "
                                "alpha~U[0.1,0.9], u=t^2 or t^alpha sin, Poisson arrivals at 0.7x "
                                "the sustained rate", "name": "served", "slots": args.slots,

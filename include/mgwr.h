@@ -387,9 +387,11 @@ int mgwr_footprint(int d, int n, int M, int batch, int precision, size_t* bytes)
  * mgwr_set_problem, else a new one; at most 8 idle handles are kept, the least
  * recently used evicted first, also when their memory keeps a request out) and
  * copies its data in; then the request joins the server's group
- * (mgwr_group_*): one batcher thread advances every running request together,
- * each iteration of all of them one CUDA graph launch whose branches run
- * concurrently on the device.  A request that arrives while others run starts
+ * (mgwr_group_*): per size class (space-time unknowns n^d M below 2^22, below
+ * 2^26, larger) one batcher thread advances every running request of the
+ * class together, each iteration of all of them one CUDA graph launch whose
+ * branches run concurrently on the device (the classes' launches overlap too,
+ * and small solves do not wait for the iterations of large ones).  A request that arrives while others run starts
  * at the next iteration boundary; its result is bitwise what it gets alone.
  * Admission order (mgwr_server_set_policy; the paper has no counterpart):
  * MGWR_POLICY_FIFO (default), the oldest request that fits runs first;

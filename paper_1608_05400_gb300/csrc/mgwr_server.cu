@@ -13,6 +13,7 @@
 // so its result does not depend on what else runs.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -164,18 +165,26 @@ struct mgwr_server {
   std::deque<Ticket*> queue;
   std::unordered_map<uint64_t, std::unique_ptr<Ticket>> tickets;
   std::vector<std::thread> workers;
-  std::thread batcher;
   bool stop = false;
   bool stop_batcher = false;  // set once every worker has left
   uint64_t next_id = 1;
   long long completed = 0, admitted = 0;
-  // the group every admitted solve runs in, and the requests about to join it
-  mgwr_group_t group = nullptr;
-  std::vector<Ticket*> joining;
+  // the groups admitted solves run in, one per size class (space-time unknowns
+  // below 2^22, below 2^26, larger), each advanced by its own batcher thread, so
+  // that small solves do not wait for the iterations of large ones; and the
+  // requests about to join each
+  static constexpr int kClasses = 3;
+  mgwr_group_t group[kClasses] = {};
+  std::vector<Ticket*> joining[kClasses];
+  std::thread batchers[kClasses];
   // idle handles, most recently used first; their bytes count in in_use
   std::list<IdleHandle> idle;
   size_t idle_bytes = 0;
   long long reused = 0;
+  // each group's counters, copied by its batcher after every step
+  long long launches[kClasses] = {}, iterations[kClasses] = {};
+  long long launches_seen[kClasses] = {}, iterations_seen[kClasses] = {};  // of the current group
+  int most[kClasses] = {};
 };
 
 namespace {
@@ -230,6 +239,12 @@ std::vector<mgwr_t> evict_for(mgwr_server* s, size_t need) {
     s->idle.pop_back();
   }
   return out;
+}
+
+// Size class of a request by its space-time unknowns n^d M.
+int size_class(const Ticket* t) {
+  const double u = (double)t->N * t->rq.M;
+  return u < (double)(1 << 22) ? 0 : u < (double)(1 << 26) ? 1 : 2;
 }
 
 // The request's handle: an idle one of its shape and precision, set up in
@@ -324,7 +339,7 @@ void worker(mgwr_server* s) {
     if (st == MGWR_OK) {
       // the batcher adds it to the group at the next iteration boundary
       std::unique_lock<std::mutex> lk(s->mu);
-      s->joining.push_back(t);
+      s->joining[size_class(t)].push_back(t);
       s->cv_batch.notify_all();
       s->cv_solved.wait(lk, [&] { return t->solved; });
       st = t->res.status;
@@ -349,25 +364,26 @@ void worker(mgwr_server* s) {
   }
 }
 
-// The batcher: admits prepared requests into the group between iterations and
-// advances all of them, one graph launch per iteration.
-void batcher(mgwr_server* s) {
+// The batcher of size class `cls`: admits prepared requests into its group
+// between iterations and advances all of them, one graph launch per iteration.
+void batcher(mgwr_server* s, int cls) {
   cudaSetDevice(s->device);
   std::unordered_map<mgwr_t, Ticket*> members;
+  mgwr_group_t& group = s->group[cls];
   for (;;) {
     std::vector<Ticket*> join;
     {
       std::unique_lock<std::mutex> lk(s->mu);
       s->cv_batch.wait(lk, [&] {
-        return s->stop_batcher || !s->joining.empty() || !members.empty();
+        return s->stop_batcher || !s->joining[cls].empty() || !members.empty();
       });
-      if (s->stop_batcher && members.empty() && s->joining.empty()) return;
-      join.swap(s->joining);
+      if (s->stop_batcher && members.empty() && s->joining[cls].empty()) return;
+      join.swap(s->joining[cls]);
     }
     std::vector<Ticket*> failed;
     for (Ticket* t : join) {
       const mgwr_request& q = t->rq;
-      const int st = mgwr_group_add(s->group, t->h, q.cycle, q.nu1, q.nu2, q.tol, q.max_cycles);
+      const int st = mgwr_group_add(group, t->h, q.cycle, q.nu1, q.nu2, q.tol, q.max_cycles);
       if (st == MGWR_OK) {
         members[t->h] = t;
       } else {
@@ -376,12 +392,12 @@ void batcher(mgwr_server* s) {
       }
     }
     int left = 0;
-    const int gst = members.empty() ? MGWR_OK : mgwr_group_step(s->group, &left);
+    const int gst = members.empty() ? MGWR_OK : mgwr_group_step(group, &left);
     std::vector<Ticket*> done = failed;
     mgwr_t h = nullptr;
     int code = 0;
     mgwr_stats st{};
-    while (mgwr_group_collect(s->group, &h, &code, &st) == MGWR_OK) {
+    while (mgwr_group_collect(group, &h, &code, &st) == MGWR_OK) {
       auto it = members.find(h);
       if (it == members.end()) continue;
       it->second->res.status = code;
@@ -390,20 +406,32 @@ void batcher(mgwr_server* s) {
       members.erase(it);
     }
     if (gst != MGWR_OK) {  // the group itself failed: every member fails with it
-      mgwr_group_destroy(s->group);
-      s->group = nullptr;
-      mgwr_group_create(&s->group);
+      mgwr_group_destroy(group);
+      group = nullptr;
+      mgwr_group_create(&group);
+      {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->launches_seen[cls] = s->iterations_seen[cls] = 0;
+      }
       for (auto& kv : members) {
         kv.second->res.status = gst;
         done.push_back(kv.second);
       }
       members.clear();
     }
-    if (!done.empty()) {
+    long long launches = 0, iters = 0;
+    int most = 0;
+    if (group != nullptr) mgwr_group_info(group, &launches, &iters, &most);
+    {
       std::lock_guard<std::mutex> lk(s->mu);
+      s->launches[cls] += launches - s->launches_seen[cls];
+      s->iterations[cls] += iters - s->iterations_seen[cls];
+      s->launches_seen[cls] = launches;
+      s->iterations_seen[cls] = iters;
+      s->most[cls] = std::max(s->most[cls], most);
       for (Ticket* t : done) t->solved = true;
-      s->cv_solved.notify_all();
     }
+    if (!done.empty()) s->cv_solved.notify_all();
   }
 }
 
@@ -442,12 +470,15 @@ int mgwr_server_create(size_t hbm_budget, int max_slots, mgwr_server_t* out) {
   s->budget = hbm_budget;
   s->slots = max_slots;
   cudaGetDevice(&s->device);
-  if (mgwr_group_create(&s->group) != MGWR_OK) {
-    delete s;
-    return MGWR_E_CUDA;
+  for (int c = 0; c < mgwr_server::kClasses; ++c) {
+    if (mgwr_group_create(&s->group[c]) != MGWR_OK) {
+      for (int k = 0; k < c; ++k) mgwr_group_destroy(s->group[k]);
+      delete s;
+      return MGWR_E_CUDA;
+    }
   }
   for (int i = 0; i < max_slots; ++i) s->workers.emplace_back(worker, s);
-  s->batcher = std::thread(batcher, s);
+  for (int c = 0; c < mgwr_server::kClasses; ++c) s->batchers[c] = std::thread(batcher, s, c);
   *out = s;
   return MGWR_OK;
 }
@@ -477,9 +508,9 @@ int mgwr_server_destroy(mgwr_server_t s) {
     s->stop_batcher = true;
   }
   s->cv_batch.notify_all();
-  s->batcher.join();
+  for (auto& b : s->batchers) b.join();
   for (auto& i : s->idle) mgwr_destroy(i.h);
-  mgwr_group_destroy(s->group);
+  for (auto& g : s->group) mgwr_group_destroy(g);
   delete s;
   return MGWR_OK;
 }
@@ -549,12 +580,14 @@ int mgwr_server_stats(mgwr_server_t s, mgwr_server_info* info) {
   info->budget_bytes = s->budget;
   info->slots = s->slots;
   info->reused_handles = s->reused;
-  long long launches = 0, iters = 0;
-  int most = 0;
-  mgwr_group_info(s->group, &launches, &iters, &most);
-  info->group_launches = launches;
-  info->member_iterations = iters;
-  info->max_group_members = most;
+  info->group_launches = 0;
+  info->member_iterations = 0;
+  info->max_group_members = 0;
+  for (int c = 0; c < mgwr_server::kClasses; ++c) {
+    info->group_launches += s->launches[c];
+    info->member_iterations += s->iterations[c];
+    info->max_group_members = std::max(info->max_group_members, s->most[c]);
+  }
   return MGWR_OK;
 }
 

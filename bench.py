@@ -516,11 +516,15 @@ def run_nonlinear(args):
     value = job_throughput(world, unknowns, args.steps, t_max)
     u = g.solution()
 
-    # the dominant kernel, k_fas_line on the finest level: red half-sweeps of the
-    # converged iterate timed with events on the launching stream (each call also
-    # reads back 16 bytes of status)
+    # the dominant kernel, the finest level's smoother: red half-sweeps of the
+    # iterate after a cycle, timed with events on the launching stream (each call
+    # also reads back 16 bytes of status); the whole-line fixed point (M a power of
+    # two from 128) counts its iterations, each one FFT convolution per line
     L = g.num_levels() - 1
     reps = 20
+    g.reset()
+    g.cycle(1, 0, 1)
+    it0 = g.line_iterations()
     k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     k0.record(stream)
     for _ in range(reps):
@@ -528,11 +532,15 @@ def run_nonlinear(args):
     k1.record(stream)
     torch.cuda.synchronize()
     line_ms = k0.elapsed_time(k1) / reps
+    line_iters = (g.line_iterations() - it0) / reps
     lines = (n + 1) // 2
     pk = peaks()
     sm_max = float(pk.get("sm_max_mhz", 2070.0))
     peak = SMS * FP64_FMA_PER_CLK_PER_SM * 2 * sm_max * 1e6 / 1e12
-    achieved = lines * fas_line_flops(Mw) / (line_ms * 1e-3) / 1e12
+    fixed = line_iters > 0
+    flops = (line_iters * (conv_flops_per_line(Mw) + 20 * Mw) if fixed
+             else lines * fas_line_flops(Mw))
+    achieved = flops / (line_ms * 1e-3) / 1e12
 
     e2e = None
     if not args.no_e2e:
@@ -577,11 +585,15 @@ def run_nonlinear(args):
         "solve": {"cycles": stats[-1].cycles, "relres": stats[-1].relres,
                   "factor": stats[-1].factor},
         "gpu_launches": launches,
-        "roofline": {"kernel": "k_fas_line", "bound": "alu", "achieved": achieved, "peak": peak,
+        "roofline": {"kernel": "k_fas_fixed" if fixed else "k_fas_line", "bound": "alu",
+                     "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                      "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x max SM clock",
                      "avg_launch_ms": line_ms, "lines_per_launch": lines,
-                     "note": "latency-bound: one warp per line marches M dependent Newton solves"},
+                     "fixed_point_iterations_per_line": line_iters / lines if fixed else None,
+                     "note": ("whole-line fixed point: one FP64 FFT convolution per line and "
+                              "iteration, a few hundred lines per launch (latency-bound)") if fixed
+                     else "latency-bound: one warp per line marches M dependent Newton solves"},
         "clocks": clk.summary(),
         "e2e": e2e,
     }

@@ -508,6 +508,25 @@ const char* mgwr_fas_last_error(mgwr_fas_t h);
 /* MGWR_ORDER_TEXT (default) or MGWR_ORDER_TABLE, as for the linear solver; the
  * cycle counts of Table table_nonlinear are reproduced with MGWR_ORDER_TABLE. */
 int mgwr_fas_set_order(mgwr_fas_t h, int order);
+/* The nonlinear smoother's line solve (the paper names a nonlinear red-black
+ * Gauss-Seidel waveform relaxation and leaves the line solve open):
+ * MGWR_FAS_SMOOTHER_MARCH marches each line in time, a scalar Newton solve per
+ * step (one warp per line); MGWR_FAS_SMOOTHER_FIXED iterates on whole lines,
+ * v <- (T_M + sigma I)^{-1} (f + sigma v - phi(v)) with phi the point's spatial
+ * term (its neighbours' lines fixed) and sigma = 2/h^2 + |c|/h, each iteration
+ * one FFT convolution per line with the precomputed inverse column of
+ * T_M + sigma I (Sec. 5), until the largest change is at most 1e-15 of the
+ * line pair's largest value (at most 200 iterations; else the call reports
+ * MGWR_E_NUMERIC); both give the line's exact solution to rounding.
+ * MGWR_FAS_SMOOTHER_AUTO (default): the fixed point when M is a power of two in
+ * 128 .. 1024, else the march.  MGWR_E_INVAL for the fixed point on other M. */
+#define MGWR_FAS_SMOOTHER_AUTO 0
+#define MGWR_FAS_SMOOTHER_MARCH 1
+#define MGWR_FAS_SMOOTHER_FIXED 2
+int mgwr_fas_set_smoother(mgwr_fas_t h, int smoother);
+/* Whole-line fixed-point iterations run so far, summed over lines (zero when
+ * only the march ran); for measuring the smoother's work. */
+int mgwr_fas_line_iterations(mgwr_fas_t h, long long* count);
 /* f: n*M doubles (host).  Resets the iterate to zero and clears a recorded
  * Newton failure. */
 int mgwr_fas_set_rhs(mgwr_fas_t h, const double* f);

@@ -145,6 +145,110 @@ __global__ void __launch_bounds__(32 * kLineWarps)
   if (!ok && lane == 0) atomicOr(status, 1);
 }
 
+// The same half-sweep as k_fas_line by a whole-line fixed point instead of a
+// march in time: with the splitting N(v) = (T_M + sigma I) v - (sigma v - phi(v)),
+// phi the point's spatial term (flux difference and upwind convection with its
+// neighbours' lines fixed), sigma = 2/h^2 + |c|/h the spatial term's slope at
+// D = 1, every iteration is
+//     v <- (T_M + sigma I)^{-1} (f + sigma v - phi(v)),
+// one causal convolution per line with the inverse column of T_M + sigma I
+// (spectrum kspec) on the FFT engine, two lines per thread group.  For D = 1
+// it is the linear smoother (one iteration); otherwise it contracts by about
+// max |1 - phi'(v) / sigma| and runs until the largest change of the pair is at
+// most 1e-15 of its largest value, at most max_it times (status bit 1 set when
+// that is not reached).  One line pair per block of L/8 threads (E = 1).
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+    k_fas_fixed(double* __restrict__ u, const double* __restrict__ f,
+                const Cx<double>* __restrict__ kspec, const Cx<double>* __restrict__ tw, int n,
+                int M, int logL, double hinv, double hinv2, double c, double sigma, int coef,
+                int parity, int all_points, int max_it, int* __restrict__ status,
+                unsigned long long* __restrict__ iterations) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ double red[2][BLOCK / 32 > 0 ? BLOCK / 32 : 1];
+  __shared__ int done_flag;
+  Cx<double>* buf = reinterpret_cast<Cx<double>*>(smem_raw);
+  const FftShape sh(logL);
+  const int t = threadIdx.x;
+  const GroupSync sync(BLOCK, BLOCK, 0);
+  const int count = all_points ? n : (parity ? n / 2 : (n + 1) / 2);
+  const int kA = 2 * blockIdx.x, kB = kA + 1;
+  const bool hasB = kB < count;
+  const int iA = all_points ? kA : 2 * kA + parity;
+  const int iB = all_points ? kB : 2 * kB + parity;
+  double* uA = u + (size_t)iA * M;
+  double* uB = u + (size_t)(hasB ? iB : iA) * M;
+  const double* fA = f + (size_t)iA * M;
+  const double* fB = f + (size_t)(hasB ? iB : iA) * M;
+  // neighbour lines (the other colour, fixed in this half-sweep); none on the one-point grid
+  const double* pA = (!all_points && iA + 1 < n) ? u + (size_t)(iA + 1) * M : nullptr;
+  const double* qA = (!all_points && iA > 0) ? u + (size_t)(iA - 1) * M : nullptr;
+  const double* pB = (!all_points && iB + 1 < n) ? u + (size_t)(iB + 1) * M : nullptr;
+  const double* qB = (!all_points && iB > 0) ? u + (size_t)(iB - 1) * M : nullptr;
+  // f + sigma v - phi(v) at one point: phi(v) = -(diffusion + convection)
+  auto rhs = [&](double fm, double v, double P, double Q) {
+    const double D0 = coef_D(coef, v);
+    const double a_plus = 0.5 * (coef_D(coef, P) + D0);
+    const double a_minus = 0.5 * (coef_D(coef, Q) + D0);
+    const double diffusion = (a_plus * (P - v) - a_minus * (v - Q)) * hinv2;
+    const double convection = c >= 0.0 ? c * (P - v) * hinv : c * (v - Q) * hinv;
+    return fm + sigma * v + (diffusion + convection);
+  };
+  auto load = [&](int m) -> Cx<double> {
+    const double bA = rhs(fA[m], uA[m], pA ? pA[m] : 0.0, qA ? qA[m] : 0.0);
+    const double bB = hasB ? rhs(fB[m], uB[m], pB ? pB[m] : 0.0, qB ? qB[m] : 0.0) : 0.0;
+    return Cx<double>{bA, bB};
+  };
+  bool settled = false;
+  int it = 0;
+  for (; it < max_it; ++it) {
+    double dmax = 0.0, vmax = 0.0;
+    auto store = [&](int m, Cx<double> y) {
+      dmax = fmax(dmax, fabs(y.x - uA[m]));
+      vmax = fmax(vmax, fabs(y.x));
+      uA[m] = y.x;
+      if (hasB) {
+        dmax = fmax(dmax, fabs(y.y - uB[m]));
+        vmax = fmax(vmax, fabs(y.y));
+        uB[m] = y.y;
+      }
+    };
+    Cx<double> v[1][8];
+    fft_forward<1>(buf, t, sh, tw, load, v, sync);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[0][q] = cmul(v[0][q], kspec[8 * t + q]);
+    fft_inverse<1>(buf, t, sh, tw, v, store, sync);
+    // the pair's largest change and value (non-finite values count as not settled)
+    for (int o = 16; o > 0; o >>= 1) {
+      dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+      vmax = fmax(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+    }
+    if (BLOCK >= 32 && (t & 31) == 0) {
+      red[0][t >> 5] = dmax;
+      red[1][t >> 5] = vmax;
+    }
+    __syncthreads();
+    if (t == 0) {
+      double d = 0.0, w = 0.0;
+      for (int k = 0; k < (BLOCK >= 32 ? BLOCK / 32 : 1); ++k) {
+        d = fmax(d, BLOCK >= 32 ? red[0][k] : dmax);
+        w = fmax(w, BLOCK >= 32 ? red[1][k] : vmax);
+      }
+      done_flag = (d <= 1e-15 * w && w <= DBL_MAX) ? 1 : 0;
+    }
+    __syncthreads();  // also orders this iteration's stores before the next loads
+    if (done_flag) {
+      settled = true;
+      ++it;
+      break;
+    }
+  }
+  if (t == 0) {
+    if (!settled) atomicOr(status, 2);
+    atomicAdd(iterations, (unsigned long long)it * (hasB ? 2 : 1));  // line iterations
+  }
+}
+
 // out = base + sign * N_h(u) on every point (one block per line), and the
 // max-norm of out into *norm_bits (the bits of a non-negative double; a
 // non-finite value counts as +inf).  Dynamic shared memory: 2 * M doubles.
@@ -235,6 +339,8 @@ __global__ void k_fas_correct(double* __restrict__ u, const double* __restrict__
 
 // ---- handle -------------------------------------------------------------------------
 
+using mgwr::Cx;
+
 struct mgwr_fas {
   int n = 0, M = 0, nlev = 0, coef = 0, order = MGWR_ORDER_TEXT;
   double T = 0.0, alpha = 0.0, c = 0.0;
@@ -244,7 +350,16 @@ struct mgwr_fas {
   double* dk = nullptr;      // d_0..d_M (written by the coefficient kernel)
   double* params = nullptr;  // alpha, tau^-alpha / Gamma(2 - alpha)
   std::vector<double*> u, f, rr, ubar;  // per level, coarsest first
-  unsigned long long* flags = nullptr;  // [0] max-norm bits, [1] Newton status
+  unsigned long long* flags = nullptr;  // [0] max-norm bits, [1] line-solve status,
+                                        // [2] fixed-point line iterations so far
+  // whole-line fixed-point smoother (k_fas_fixed): twiddles, per-level inverse
+  // columns of T_M + sigma_l I and their spectra; null when M is not a power of
+  // two in 128 .. 1024, where the time march serves
+  int smoother = MGWR_FAS_SMOOTHER_AUTO;
+  Cx<double>* tw = nullptr;
+  double* kcol = nullptr;
+  Cx<double>* kspec = nullptr;
+  std::vector<double> sigma;
   size_t line_smem = 0, apply_smem = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::string err;
@@ -275,10 +390,37 @@ inline int colour_parity(const mgwr_fas* h, int colour) {
   return colour == MGWR_RED ? red : 1 - red;
 }
 
+bool fixed_point(const mgwr_fas* h) {
+  return h->kspec != nullptr && h->smoother != MGWR_FAS_SMOOTHER_MARCH;
+}
+
+constexpr int kFixedMaxIt = 200;  // fixed-point iterations per half-sweep before giving up
+
 cudaError_t launch_line(mgwr_fas* h, int l, int parity, int all_points) {
   const int n = level_n(l);
   const int count = all_points ? n : (parity ? n / 2 : (n + 1) / 2);
   if (count == 0) return cudaSuccess;
+  if (fixed_point(h)) {
+    const int L = 2 * h->M, logL = mgwr::ilog2(L);
+    const double hl = level_h(l);
+    const unsigned grid = (unsigned)((count + 1) / 2);
+    const size_t smem = mgwr::Pad<double>::len(L) * sizeof(Cx<double>);
+    const Cx<double>* ks = h->kspec + (size_t)l * L;
+    int* st = reinterpret_cast<int*>(h->flags + 1);
+#define MGWR_FIXED_LAUNCH(B)                                                                    \
+  mgwr::k_fas_fixed<B><<<grid, B, smem, h->stream>>>(h->u[l], h->f[l], ks, h->tw, n, h->M, logL, \
+                                                     1.0 / hl, 1.0 / (hl * hl), h->c,           \
+                                                     h->sigma[l], h->coef, parity, all_points,   \
+                                                     kFixedMaxIt, st, h->flags + 2)
+    switch (L / 8) {
+      case 32: MGWR_FIXED_LAUNCH(32); break;
+      case 64: MGWR_FIXED_LAUNCH(64); break;
+      case 128: MGWR_FIXED_LAUNCH(128); break;
+      default: MGWR_FIXED_LAUNCH(256); break;
+    }
+#undef MGWR_FIXED_LAUNCH
+    return mgwr::counted(cudaGetLastError());
+  }
   const int blocks = (count + mgwr::kLineWarps - 1) / mgwr::kLineWarps;
   mgwr::k_fas_line<<<blocks, 32 * mgwr::kLineWarps, h->line_smem, h->stream>>>(
       h->u[l], h->f[l], h->r, n, h->M, level_h(l), h->c, h->coef, parity, all_points,
@@ -348,7 +490,7 @@ int read_flags(mgwr_fas* h, double* norm, bool* newton_failed) {
     std::memcpy(&v, &host[0], sizeof(v));
     *norm = v;
   }
-  if (newton_failed) *newton_failed = (host[1] & 1ull) != 0;
+  if (newton_failed) *newton_failed = (host[1] & 3ull) != 0;
   return MGWR_OK;
 }
 
@@ -363,7 +505,7 @@ int defect_norm(mgwr_fas* h, int l, double* norm) {
   bool failed = false;
   if (s == MGWR_OK) s = read_flags(h, norm, &failed);
   if (s == MGWR_OK && failed)
-    s = fas_fail(h, MGWR_E_NUMERIC, "Newton's method did not settle in a line solve");
+    s = fas_fail(h, MGWR_E_NUMERIC, "a line solve did not settle (Newton's method or the whole-line fixed point)");
   return s;
 }
 
@@ -383,6 +525,9 @@ void release(mgwr_fas* h) {
   fr(h->r);
   fr(h->dk);
   fr(h->params);
+  fr(h->kcol);
+  if (h->kspec) cudaFree(h->kspec);
+  if (h->tw) cudaFree(h->tw);
   if (h->flags) cudaFree(h->flags);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
@@ -439,7 +584,7 @@ int mgwr_fas_create(int n, int M, double T, double alpha, double c, int coeffici
   };
   bool ok = alloc(&h->r, sizeof(double) * M) && alloc(&h->dk, sizeof(double) * (M + 1)) &&
             alloc(&h->params, sizeof(double) * 2);
-  if (ok && cudaMalloc(&h->flags, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+  if (ok && cudaMalloc(&h->flags, 3 * sizeof(unsigned long long)) != cudaSuccess) {
     cudaGetLastError();
     h->flags = nullptr;
     ok = false;
@@ -469,7 +614,38 @@ int mgwr_fas_create(int n, int M, double T, double alpha, double c, int coeffici
     if (e == cudaSuccess) e = cudaMemsetAsync(h->rr[l], 0, field_bytes(h, l), h->stream);
   }
   if (e == cudaSuccess)
-    e = cudaMemsetAsync(h->flags, 0, 2 * sizeof(unsigned long long), h->stream);
+    e = cudaMemsetAsync(h->flags, 0, 3 * sizeof(unsigned long long), h->stream);
+  // the fixed-point smoother's setup (Sec. 5): per level sigma_l = 2/h_l^2 + |c|/h_l,
+  // the first column of (T_M + sigma_l I)^{-1} by divide and conquer, its spectrum
+  if (e == cudaSuccess && M >= 128 && (M & (M - 1)) == 0) {
+    const int L = 2 * M;
+    for (int l = 0; l < h->nlev; ++l) {
+      const double hl = level_h(l);
+      h->sigma.push_back(2.0 / (hl * hl) + std::fabs(c) / hl);
+    }
+    double* sig_dev = nullptr;
+    Cx<double>* work = nullptr;
+    ok = alloc(&h->kcol, sizeof(double) * (size_t)h->nlev * M) &&
+         alloc(&sig_dev, sizeof(double) * (size_t)h->nlev) &&
+         cudaMalloc(&h->kspec, sizeof(Cx<double>) * (size_t)h->nlev * L) == cudaSuccess &&
+         cudaMalloc(&h->tw, sizeof(Cx<double>) * (size_t)L) == cudaSuccess &&
+         cudaMalloc(&work, sizeof(Cx<double>) * (size_t)h->nlev * 3 * M) == cudaSuccess;
+    if (ok) {
+      e = cudaMemcpyAsync(sig_dev, h->sigma.data(), sizeof(double) * h->nlev,
+                          cudaMemcpyHostToDevice, h->stream);
+      if (e == cudaSuccess)
+        e = mgwr::launch_inverse_columns(h->kcol, h->r, sig_dev, h->nlev, M, 1, work, h->stream);
+      if (e == cudaSuccess) e = mgwr::launch_twiddles(h->tw, L, h->stream);
+      if (e == cudaSuccess)
+        e = mgwr::launch_spectra(h->kspec, h->kcol, h->nlev, M, h->tw, h->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    } else {
+      cudaGetLastError();
+    }
+    if (sig_dev) cudaFree(sig_dev);
+    if (work) cudaFree(work);
+    if (!ok) return bail(MGWR_E_NOMEM);
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -582,6 +758,27 @@ int mgwr_fas_residual(mgwr_fas_t h, double* norm_inf, double* r_host) {
   return s;
 }
 
+int mgwr_fas_set_smoother(mgwr_fas_t h, int smoother) {
+  if (h == nullptr) return MGWR_E_INVAL;
+  if (smoother != MGWR_FAS_SMOOTHER_AUTO && smoother != MGWR_FAS_SMOOTHER_MARCH &&
+      smoother != MGWR_FAS_SMOOTHER_FIXED)
+    return fas_fail(h, MGWR_E_INVAL, "unknown smoother");
+  if (smoother == MGWR_FAS_SMOOTHER_FIXED && h->kspec == nullptr)
+    return fas_fail(h, MGWR_E_INVAL, "the fixed-point smoother needs M a power of two in 128..1024");
+  h->smoother = smoother;
+  return MGWR_OK;
+}
+
+int mgwr_fas_line_iterations(mgwr_fas_t h, long long* count) {
+  if (h == nullptr || count == nullptr) return MGWR_E_INVAL;
+  unsigned long long v = 0;
+  int s = fas_cuda(h, cudaMemcpyAsync(&v, h->flags + 2, sizeof(v), cudaMemcpyDeviceToHost,
+                                      h->stream), "read count");
+  if (s == MGWR_OK) s = fas_cuda(h, cudaStreamSynchronize(h->stream), "synchronize");
+  if (s == MGWR_OK) *count = (long long)v;
+  return s;
+}
+
 int mgwr_fas_smooth(mgwr_fas_t h, int level, int colour) {
   if (h == nullptr) return MGWR_E_INVAL;
   if (level < 0 || level >= h->nlev || (colour != MGWR_RED && colour != MGWR_BLACK))
@@ -590,7 +787,7 @@ int mgwr_fas_smooth(mgwr_fas_t h, int level, int colour) {
   bool failed = false;
   if (s == MGWR_OK) s = read_flags(h, nullptr, &failed);
   if (s == MGWR_OK && failed)
-    s = fas_fail(h, MGWR_E_NUMERIC, "Newton's method did not settle in a line solve");
+    s = fas_fail(h, MGWR_E_NUMERIC, "a line solve did not settle (Newton's method or the whole-line fixed point)");
   return s;
 }
 
@@ -602,7 +799,7 @@ int mgwr_fas_cycle(mgwr_fas_t h, int cycle, int nu1, int nu2) {
   bool failed = false;
   if (s == MGWR_OK) s = read_flags(h, nullptr, &failed);
   if (s == MGWR_OK && failed)
-    s = fas_fail(h, MGWR_E_NUMERIC, "Newton's method did not settle in a line solve");
+    s = fas_fail(h, MGWR_E_NUMERIC, "a line solve did not settle (Newton's method or the whole-line fixed point)");
   return s;
 }
 

@@ -32,6 +32,7 @@ MGWR_U, MGWR_F, MGWR_R = 0, 1, 2
 MGWR_RED, MGWR_BLACK = 0, 1
 MGWR_ORDER_TEXT, MGWR_ORDER_TABLE = 0, 1
 MGWR_FAS_D_POROUS, MGWR_FAS_D_CONSTANT = 0, 1
+MGWR_FAS_SMOOTHER_AUTO, MGWR_FAS_SMOOTHER_MARCH, MGWR_FAS_SMOOTHER_FIXED = 0, 1, 2
 MGWR_POLICY_FIFO, MGWR_POLICY_SMALLEST = 0, 1
 MGWR_SPLIT_STAGED = 16
 MGWR_SPLIT_TENSOR = 32
@@ -133,6 +134,8 @@ _SIGS = {
     "mgwr_fas_destroy": (C.c_int, [_h]),
     "mgwr_fas_last_error": (C.c_char_p, [_h]),
     "mgwr_fas_set_order": (C.c_int, [_h, C.c_int]),
+    "mgwr_fas_set_smoother": (C.c_int, [_h, C.c_int]),
+    "mgwr_fas_line_iterations": (C.c_int, [_h, C.POINTER(C.c_longlong)]),
     "mgwr_fas_reset": (C.c_int, [_h]),
     "mgwr_fas_set_stream": (C.c_int, [_h, C.c_void_p]),
     "mgwr_fas_set_rhs": (C.c_int, [_h, _dp]),
@@ -626,6 +629,14 @@ class FAS:
 
     def set_order(self, order: int):
         self._check(self.lib.mgwr_fas_set_order(self.h, order), "mgwr_fas_set_order")
+
+    def set_smoother(self, smoother: int):
+        self._check(self.lib.mgwr_fas_set_smoother(self.h, smoother), "mgwr_fas_set_smoother")
+
+    def line_iterations(self) -> int:
+        v = C.c_longlong()
+        self._check(self.lib.mgwr_fas_line_iterations(self.h, C.byref(v)), "mgwr_fas_line_iterations")
+        return v.value
 
     def reset(self):
         self._check(self.lib.mgwr_fas_reset(self.h), "mgwr_fas_reset")

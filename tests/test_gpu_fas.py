@@ -191,3 +191,82 @@ def test_reset_and_stream_repeat_a_solve():
         g.set_stream(None)
     assert a.cycles == b.cycles
     assert np.array_equal(ua, ub)  # the same kernels on the same data
+
+
+SMOOTHERS = {"march": G.MGWR_FAS_SMOOTHER_MARCH, "fixed": G.MGWR_FAS_SMOOTHER_FIXED}
+
+
+@pytest.mark.parametrize("smoother", sorted(SMOOTHERS))
+@pytest.mark.parametrize("n,M,c,order", [(31, 128, 1.0, "table"), (63, 256, -2.0, "text"),
+                                         (15, 1024, 0.0, "table"), (127, 128, 2.0, "text")])
+def test_half_sweep_of_both_smoothers_matches_oracle(smoother, n, M, c, order):
+    # the time march (Newton per step) and the whole-line fixed point (one FFT
+    # convolution with the inverse column of T_M + sigma I per iteration) both
+    # solve each line of the colour to rounding: against the oracle's march
+    T, delta = 1.0, 0.45
+    W = fas.WRFAS(n, M, T, delta, c=c, order=order)
+    u = inputs.random_field(n, M, seed=23, scale=0.3)
+    f = inputs.random_field(n, M, seed=24)
+    uo = u.copy()
+    with G.FAS(n, M, T, delta, c) as g:
+        g.set_order(ORDER[order])
+        g.set_smoother(SMOOTHERS[smoother])
+        L = g.num_levels() - 1
+        g.field_set(L, G.MGWR_U, u)
+        g.field_set(L, G.MGWR_F, f)
+        for colour in (G.MGWR_RED, G.MGWR_BLACK):
+            g.smooth(L, colour)
+            W.sweep(W.finest, uo, f, colour)
+            assert rel(g.field_get(L, G.MGWR_U), uo) <= 1e-12
+        iters = g.line_iterations()
+    assert (iters > 0) == (smoother == "fixed")
+
+
+@pytest.mark.parametrize("nu,gamma", [((0, 1), 1), ((1, 1), 2)])
+def test_fixed_point_cycles_match_oracle(nu, gamma):
+    n, M, T, delta, c = 63, 128, 1.0, 0.4, 1.0
+    f = inputs.random_field(n, M, seed=42, scale=4.0)
+    W = fas.WRFAS(n, M, T, delta, c=c, order="table")
+    uo = np.zeros((n, M))
+    with G.FAS(n, M, T, delta, c) as g:
+        g.set_order(G.MGWR_ORDER_TABLE)
+        g.set_smoother(G.MGWR_FAS_SMOOTHER_FIXED)
+        g.set_rhs(f)
+        for _ in range(3):
+            g.cycle(gamma, *nu)
+            uo = W.cycle(W.finest, uo, f, nu[0], nu[1], gamma)
+            assert rel(g.solution(), uo) <= 1e-11
+
+
+def test_smoother_choice_is_checked_and_both_solve_alike():
+    with G.FAS(31, 24, 1.0, 0.5, 1.0) as g:  # M not a power of two >= 128: the march only
+        with pytest.raises(G.MGWRError):
+            g.set_smoother(G.MGWR_FAS_SMOOTHER_FIXED)
+        g.set_smoother(G.MGWR_FAS_SMOOTHER_MARCH)
+        with pytest.raises(G.MGWRError):
+            g.set_smoother(7)
+    n, M = 127, 128
+    out = []
+    for sm in (G.MGWR_FAS_SMOOTHER_MARCH, G.MGWR_FAS_SMOOTHER_FIXED):
+        with G.FAS(n, M, 1.0, 0.4, 1.0) as g:
+            g.set_order(G.MGWR_ORDER_TABLE)
+            g.set_smoother(sm)
+            g.set_rhs(np.ones((n, M)))
+            st = g.solve(1, 0, 1, tol=1e-10, max_cycles=30)
+            out.append((g.solution(), st.cycles))
+    assert out[0][1] == out[1][1]
+    assert rel(out[1][0], out[0][0]) <= 1e-11
+
+
+def test_fixed_point_non_finite_rhs_is_reported():
+    n, M = 31, 128
+    f = np.ones((n, M))
+    f[5, 7] = np.nan
+    with G.FAS(n, M, 1.0, 0.5, 1.0) as g:
+        g.set_smoother(G.MGWR_FAS_SMOOTHER_FIXED)
+        g.set_rhs(f)
+        with pytest.raises(G.MGWRError) as e:
+            g.solve(1, 0, 1, tol=1e-10, max_cycles=3)
+        assert e.value.status == G.MGWR_E_NUMERIC
+        g.set_rhs(np.ones((n, M)))
+        assert g.solve(1, 0, 1, tol=1e-10, max_cycles=30).relres <= 1e-10

@@ -515,9 +515,10 @@ int mgwr_fas_set_order(mgwr_fas_t h, int order);
  * v <- (T_M + sigma I)^{-1} (f + sigma v - phi(v)) with phi the point's spatial
  * term (its neighbours' lines fixed) and sigma = 2/h^2 + |c|/h, each iteration
  * one FFT convolution per line with the precomputed inverse column of
- * T_M + sigma I (Sec. 5), until the largest change is at most 1e-15 of the
- * line pair's largest value (at most 200 iterations; else the call reports
- * MGWR_E_NUMERIC); both give the line's exact solution to rounding.
+ * T_M + sigma I (Sec. 5), until the largest change is at the convolution's
+ * rounding level (4e-15 of the line pair's largest value) or stops falling
+ * within 1e-12 of it (at most 200 iterations; else the call reports
+ * MGWR_E_NUMERIC); both give the line's solution to rounding.
  * MGWR_FAS_SMOOTHER_AUTO (default): the fixed point when M is a power of two in
  * 128 .. 1024, else the march.  MGWR_E_INVAL for the fixed point on other M. */
 #define MGWR_FAS_SMOOTHER_AUTO 0

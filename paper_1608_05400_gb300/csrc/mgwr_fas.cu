@@ -155,8 +155,9 @@ __global__ void __launch_bounds__(32 * kLineWarps)
 // (spectrum kspec) on the FFT engine, two lines per thread group.  For D = 1
 // it is the linear smoother (one iteration); otherwise it contracts by about
 // max |1 - phi'(v) / sigma| and runs until the largest change of the pair is at
-// most 1e-15 of its largest value, at most max_it times (status bit 1 set when
-// that is not reached).  One line pair per block of L/8 threads (E = 1).
+// the convolution's rounding level (4e-15 of its largest value), or stops
+// falling below 1e-12 of it, at most max_it times (status bit 1 set when
+// neither is reached).  One line pair per block of L/8 threads (E = 1).
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK)
     k_fas_fixed(double* __restrict__ u, const double* __restrict__ f,
@@ -201,6 +202,7 @@ __global__ void __launch_bounds__(BLOCK)
   };
   bool settled = false;
   int it = 0;
+  double d_prev = 0.0;  // the last iteration's largest change (thread 0)
   for (; it < max_it; ++it) {
     double dmax = 0.0, vmax = 0.0;
     auto store = [&](int m, Cx<double> y) {
@@ -234,7 +236,11 @@ __global__ void __launch_bounds__(BLOCK)
         d = fmax(d, BLOCK >= 32 ? red[0][k] : dmax);
         w = fmax(w, BLOCK >= 32 ? red[1][k] : vmax);
       }
-      done_flag = (d <= 1e-15 * w && w <= DBL_MAX) ? 1 : 0;
+      // settled: the change is at the level of the convolution's rounding (the
+      // right-hand side holds sigma v, so v carries about log2(L) eps of itself),
+      // or it has stopped falling within 1e-12 of the line
+      done_flag = (w <= DBL_MAX && (d <= 4e-15 * w || (d <= 1e-12 * w && d >= 0.5 * d_prev))) ? 1 : 0;
+      d_prev = d;
     }
     __syncthreads();  // also orders this iteration's stores before the next loads
     if (done_flag) {

@@ -7,11 +7,8 @@ namespace mgwr {
 
 namespace {
 
-// MINB resident blocks per SM asked of the compiler: 2 (128 registers per
-// thread, no spills of note) or 3 (80 registers, a few dozen bytes spilled, 24
-// warps per SM instead of 16 to hide the gather's latency); the tuner picks.
-template <int LOGL, int R0, int R1, int R2, int T, int MINB>
-__global__ void __launch_bounds__(kRpBlock, MINB)
+template <int LOGL, int R0, int R1, int R2, int T>
+__global__ void __launch_bounds__(kRpBlock, 2)
     k_sweep_rp(const float* __restrict__ f, float* __restrict__ u, float* __restrict__ delta,
                const Cx<float>* __restrict__ spec, const Cx<float>* __restrict__ tw,
                const float* __restrict__ zero, int d, int n, int M, int par, float hinv2,
@@ -84,16 +81,16 @@ __global__ void k_spectra_rp(Cx<float>* __restrict__ dst, const Cx<double>* __re
   }
 }
 
-template <int LOGL, int R0, int R1, int R2, int T, int MINB>
+template <int LOGL, int R0, int R1, int R2, int T>
 cudaError_t sweep_rp_launch(dim3 grid, cudaStream_t s, const float* f, float* u, float* delta,
                             const Cx<float>* spec, const Cx<float>* tw, const float* zero, int d,
                             int n, int M, int par, float hinv2, int npts, int npairs,
                             size_t fstride, size_t sstride) {
   using P = rp::Plan<LOGL, R0, R1, R2, T>;
   const size_t smem = (size_t)(kRpBlock / T) * P::SMEM * sizeof(Cx<float>);
-  cudaError_t e = prepare_smem(k_sweep_rp<LOGL, R0, R1, R2, T, MINB>, smem);
+  cudaError_t e = prepare_smem(k_sweep_rp<LOGL, R0, R1, R2, T>, smem);
   if (e != cudaSuccess) return e;
-  k_sweep_rp<LOGL, R0, R1, R2, T, MINB><<<grid, kRpBlock, smem, s>>>(
+  k_sweep_rp<LOGL, R0, R1, R2, T><<<grid, kRpBlock, smem, s>>>(
       f, u, delta, spec, tw, zero, d, n, M, par, hinv2, npts, npairs, fstride, sstride);
   return cudaSuccess;
 }
@@ -102,8 +99,7 @@ cudaError_t sweep_rp_launch(dim3 grid, cudaStream_t s, const float* f, float* u,
 
 cudaError_t launch_sweep_rp(const float* f, float* u, float* delta, const Cx<float>* spec,
                             size_t spec_stride, const Cx<float>* tw, const float* zero,
-                            const LevelShape& ls, int par, float hinv2, int occupancy,
-                            cudaStream_t s) {
+                            const LevelShape& ls, int par, float hinv2, cudaStream_t s) {
   const int d = ls.d, n = ls.n, M = ls.M;
   if (!radix_length(M)) return cudaErrorInvalidValue;
   const int logL = ilog2(2 * M);
@@ -116,12 +112,8 @@ cudaError_t launch_sweep_rp(const float* f, float* u, float* delta, const Cx<flo
 #define MGWR_RP_LAUNCH(LG, A, B, C, T)                                                       \
   case LG: {                                                                                 \
     const dim3 grid((unsigned)((npairs + kRpBlock / T - 1) / (kRpBlock / T)), (unsigned)ls.batch); \
-    if (occupancy == 3)                                                                      \
-      e = sweep_rp_launch<LG, A, B, C, T, 3>(grid, s, f, u, delta, spec, tw, zero, d, n, M,   \
-                                             par, hinv2, npts, npairs, fstride, spec_stride); \
-    else                                                                                     \
-      e = sweep_rp_launch<LG, A, B, C, T, 2>(grid, s, f, u, delta, spec, tw, zero, d, n, M,   \
-                                             par, hinv2, npts, npairs, fstride, spec_stride); \
+    e = sweep_rp_launch<LG, A, B, C, T>(grid, s, f, u, delta, spec, tw, zero, d, n, M, par,   \
+                                        hinv2, npts, npairs, fstride, spec_stride);          \
     break;                                                                                   \
   }
     MGWR_RP_PLANS(MGWR_RP_LAUNCH)

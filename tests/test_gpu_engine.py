@@ -345,14 +345,3 @@ def test_radix_solve_converges_like_the_fft_solve(precision, d, n, M, batch):
             out.append((s.solution(), st.outer))
     assert abs(out[1][1] - out[0][1]) <= 1  # outer steps: different FP32 rounding may need one more
     assert rel(out[1][0], out[0][0]) <= 1e-9
-
-
-@pytest.mark.parametrize("d,n,M,batch", [(2, 63, 1024, 1), (1, 255, 512, 1), (2, 15, 4096, 1),
-                                         (2, 31, 64, 2), (1, 127, 128, 1)])
-def test_radix_occupancy_variants_are_bitwise_equal(d, n, M, batch):
-    # 2 | MGWR_SPLIT_RADIX builds the same kernel for three blocks per SM
-    a, used_a = _sweep32(d, n, M, 1 | G.MGWR_SPLIT_RADIX, batch, delta=True)
-    b, used_b = _sweep32(d, n, M, 2 | G.MGWR_SPLIT_RADIX, batch, delta=True)
-    assert (used_a, used_b) == (1 | G.MGWR_SPLIT_RADIX, 2 | G.MGWR_SPLIT_RADIX)
-    for x, y in zip(a[:2], b[:2]):
-        np.testing.assert_array_equal(x, y)

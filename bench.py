@@ -99,7 +99,10 @@ FP32_LANES_PER_SM = 128
 SWEEP64_DRAM_BYTES_PER_LINE_M1024 = 23758.0
 # DRAM bytes per line of further kernels from single-kernel ncu captures (see
 # profiles/), by kernel class and M
-NCU_DRAM_BYTES_PER_LINE: dict = {}
+# (k_defect<double, float>: 1059.1 MB read + 254.9 MB written for 16,129 lines of 4096,
+# profiles/k_defect_fp64_outer_2d_127x127_M4096.md; k_sweep_rp: 264.5 + 103.5 MB for 8065
+# lines of 4096, profiles/k_sweep_rp_fp32_2d_127x127_M4096.md)
+NCU_DRAM_BYTES_PER_LINE: dict = {"defect64": {4096: 81468.0}, "sweep32": {4096: 45629.0}}
 
 
 def parse():

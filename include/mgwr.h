@@ -214,7 +214,9 @@ int mgwr_set_outer_switch(mgwr_t h, double rel);
  * 4 .. 32 DFTs held in registers (last pass radix 32, spectrum product and
  * first inverse pass in registers), so every value crosses shared memory once
  * per pass.  Results agree with the other engine's to FP32 rounding, not
- * bitwise.  Other lengths fall back to the FFT engine. */
+ * bitwise.  2 | MGWR_SPLIT_RADIX takes the first pass's adjacent butterflies
+ * two at a time, with 8-byte global loads and stores (the same arithmetic;
+ * results agree to FP32 rounding).  Other lengths fall back to the FFT engine. */
 #define MGWR_SPLIT_RADIX 64
 int mgwr_set_engine_split(mgwr_t h, int kernel_class, int level, int split);
 int mgwr_get_engine_split(mgwr_t h, int kernel_class, int level, int* split);

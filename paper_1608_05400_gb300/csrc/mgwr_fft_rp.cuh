@@ -375,6 +375,131 @@ __device__ __forceinline__ void convolve(C* buf, int t, int g, const C* __restri
   }
 }
 
+// Two consecutive complex inputs of the first pass (times m and m + 1).
+struct Pair2 {
+  C a, b;
+};
+
+// The same convolution with the first pass's butterflies taken two adjacent at
+// a time (j = 2 (t + T i) and j + 1), so that the inputs and outputs of a
+// thread come as pairs of consecutive times: load2(m) gives the inputs at m and
+// m + 1 (Pair2), store2(m, y0, y1) receives the outputs at m and m + 1; the
+// global accesses are then 8-byte vectors (half the load and store
+// instructions), for 2-way bank conflicts on the first pass's shared-memory
+// accesses.  spec: the kernel's spectrum in this
+// plan's spectral order, pre-scaled by 1/L; tw[e] = w_L^e.  buf: P::SMEM
+// complex values of shared memory for the group.
+template <int LOGL, int R0, int R1, int R2, int T, int PAIRS, class Load2, class Store2>
+__device__ __forceinline__ void convolve2(C* buf, int t, int g, const C* __restrict__ spec,
+                                          const C* __restrict__ tw, Load2 load2, Store2 store2) {
+  using P = Plan<LOGL, R0, R1, R2, T>;
+  // ---- pass 0: every input of the thread, then half-input DFTs and twiddles
+  constexpr int NB0 = P::S0 / T;
+  static_assert(NB0 % 2 == 0, "the first pass takes butterflies in adjacent pairs");
+  Pair2 in[NB0 / 2][R0 / 2];
+#pragma unroll
+  for (int i = 0; i < NB0 / 2; ++i) {
+#pragma unroll
+    for (int q = 0; q < R0 / 2; ++q) in[i][q] = load2(2 * (t + T * i) + q * P::S0);
+  }
+#pragma unroll
+  for (int i = 0; i < NB0; ++i) {
+    const int j = 2 * (t + T * (i >> 1)) + (i & 1);
+    const TwBase<R0> tb(tw, j);
+    C v[R0];
+#pragma unroll
+    for (int q = 0; q < R0 / 2; ++q) v[q] = (i & 1) ? in[i >> 1][q].b : in[i >> 1][q].a;
+    dft_half<R0>(v);
+    twiddle_apply<R0, false>(v, tb);
+#pragma unroll
+    for (int k = 0; k < R0; ++k) buf[P::idx(j + k * P::S0)] = v[k];
+  }
+  group_sync<T, PAIRS>(g);
+
+  // ---- pass 1 when there are three: radix R1 on groups of G1, twiddles w_G1^{jk}
+  if constexpr (P::NP == 3) {
+    constexpr int NB1 = (P::L / R1) / T;
+#pragma unroll 1
+    for (int i = 0; i < NB1; ++i) {
+      const int beta = t + T * i;
+      const int grp = beta / P::S1, j = beta - grp * P::S1;
+      const int base = grp * P::G1 + j;
+      const TwBase<R1> tb(tw, j * R0);
+      C v[R1];
+#pragma unroll
+      for (int q = 0; q < R1; ++q) v[q] = buf[P::idx(base + q * P::S1)];
+      Dft<R1, false>::run(v);
+      twiddle_apply<R1, false>(v, tb);
+#pragma unroll
+      for (int q = 0; q < R1; ++q) buf[P::idx(base + q * P::S1)] = v[q];
+    }
+    group_sync<T, PAIRS>(g);
+  }
+
+  // ---- last pass (contiguous RL values), spectrum product, its inverse
+  constexpr int RL = P::RL;
+  constexpr int NBL = (P::L / RL) / T;
+#pragma unroll 1
+  for (int i = 0; i < NBL; ++i) {
+    const int base = (t + T * i) * RL;
+    C v[RL];
+#pragma unroll
+    for (int q = 0; q < RL; ++q) v[q] = buf[P::idx(base + q)];
+    Dft<RL, false>::run(v);
+    const float4* sp = reinterpret_cast<const float4*>(spec + base);
+#pragma unroll
+    for (int q = 0; q < RL / 2; ++q) {
+      const float4 s2 = __ldg(sp + q);
+      v[2 * q] = cmul(v[2 * q], C{s2.x, s2.y});
+      v[2 * q + 1] = cmul(v[2 * q + 1], C{s2.z, s2.w});
+    }
+    Dft<RL, true>::run(v);
+#pragma unroll
+    for (int q = 0; q < RL; ++q) buf[P::idx(base + q)] = v[q];
+  }
+  group_sync<T, PAIRS>(g);
+
+  // ---- inverse of pass 1
+  if constexpr (P::NP == 3) {
+    constexpr int NB1 = (P::L / R1) / T;
+#pragma unroll 1
+    for (int i = 0; i < NB1; ++i) {
+      const int beta = t + T * i;
+      const int grp = beta / P::S1, j = beta - grp * P::S1;
+      const int base = grp * P::G1 + j;
+      const TwBase<R1> tb(tw, j * R0);
+      C v[R1];
+#pragma unroll
+      for (int q = 0; q < R1; ++q) v[q] = buf[P::idx(base + q * P::S1)];
+      twiddle_apply<R1, true>(v, tb);
+      Dft<R1, true>::run(v);
+#pragma unroll
+      for (int q = 0; q < R1; ++q) buf[P::idx(base + q * P::S1)] = v[q];
+    }
+    group_sync<T, PAIRS>(g);
+  }
+
+  // ---- inverse of pass 0: the first M outputs, two adjacent butterflies at a time
+#pragma unroll 1
+  for (int i = 0; i < NB0 / 2; ++i) {
+    const int j = 2 * (t + T * i);
+    C y[2][R0 / 2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const TwBase<R0> tb(tw, j + h);
+      C v[R0];
+#pragma unroll
+      for (int k = 0; k < R0; ++k) v[k] = buf[P::idx(j + h + k * P::S0)];
+      twiddle_apply<R0, true>(v, tb);
+      Dft<R0, true>::run(v);
+#pragma unroll
+      for (int q = 0; q < R0 / 2; ++q) y[h][q] = v[q];
+    }
+#pragma unroll
+    for (int q = 0; q < R0 / 2; ++q) store2(j + q * P::S0, y[0][q], y[1][q]);
+  }
+}
+
 }  // namespace rp
 
 // Radix plans per transform length (L = 2^7 .. 2^13): two or three passes,

@@ -72,7 +72,7 @@ inline int effective_split(int M, int word, int E) {
   const int L = 2 * M;
   E = engine_split(L, E);
   if (word == 4 && (L < 128 || L > 8192)) return 1;
-  if (word == 4 && radix && radix_length(M)) return 1 | kRadix;
+  if (word == 4 && radix && radix_length(M)) return (E == 1 ? 1 : 2) | kRadix;
   if (word == 4 && tensor && tensor_length(M)) return 1 | kTensor;
   return word == 4 ? (E | staged) : E;
 }
@@ -140,9 +140,12 @@ cudaError_t take_tc_timeout(bool* hit);
 // FFT engine (mgwr_fft_rp.cuh): as launch_sweep without all_points, with the
 // inverse-column spectra in that engine's spectral order (launch_spectra_rp).
 // Results agree with the shared-memory engine's to FP32 rounding, not bitwise.
+// paired: the first pass's adjacent butterflies two at a time with 8-byte
+// global accesses (the split's E: 1 | kRadix single, 2 | kRadix paired).
 cudaError_t launch_sweep_rp(const float* f, float* u, float* delta, const Cx<float>* spec,
                             size_t spec_stride, const Cx<float>* tw, const float* zero,
-                            const LevelShape& ls, int par, float hinv2, cudaStream_t s);
+                            const LevelShape& ls, int par, float hinv2, bool paired,
+                            cudaStream_t s);
 // dst[c L ..] = the FP64 spectra src[c L ..] (length L = 2M, the shared-memory
 // engine's order) rounded to FP32 and permuted into the register-pass engine's
 // order, for `lines` lines.

@@ -7,7 +7,10 @@ namespace mgwr {
 
 namespace {
 
-template <int LOGL, int R0, int R1, int R2, int T>
+// PAIRED: the first pass takes adjacent butterflies two at a time, with 8-byte
+// gathers and stores (rp::convolve2), else one at a time (rp::convolve); the
+// tuner picks per level (faster for 256-step lines, slower for 1024 and 4096).
+template <int LOGL, int R0, int R1, int R2, int T, bool PAIRED>
 __global__ void __launch_bounds__(kRpBlock, 2)
     k_sweep_rp(const float* __restrict__ f, float* __restrict__ u, float* __restrict__ delta,
                const Cx<float>* __restrict__ spec, const Cx<float>* __restrict__ tw,
@@ -43,25 +46,63 @@ __global__ void __launch_bounds__(kRpBlock, 2)
   if (!valid) qA[0] = qA[1] = qA[2] = qA[3] = zero;
   if (!hasB) qB[0] = qB[1] = qB[2] = qB[3] = zero;
 
-  auto load = [&](int m) -> C {
-    if (d == 2)
-      return C{fA[m] + hinv2 * ((qA[0][m] + qA[1][m]) + (qA[2][m] + qA[3][m])),
-               fB[m] + hinv2 * ((qB[0][m] + qB[1][m]) + (qB[2][m] + qB[3][m]))};
-    return C{fA[m] + hinv2 * (qA[0][m] + qA[1][m]), fB[m] + hinv2 * (qB[0][m] + qB[1][m])};
+  if constexpr (!PAIRED) {
+    auto load = [&](int m) -> C {
+      if (d == 2)
+        return C{fA[m] + hinv2 * ((qA[0][m] + qA[1][m]) + (qA[2][m] + qA[3][m])),
+                 fB[m] + hinv2 * ((qB[0][m] + qB[1][m]) + (qB[2][m] + qB[3][m]))};
+      return C{fA[m] + hinv2 * (qA[0][m] + qA[1][m]), fB[m] + hinv2 * (qB[0][m] + qB[1][m])};
+    };
+    float* uA = u + pAM;
+    float* uB = u + pBM;
+    auto store = [&](int m, C y) {
+      if (valid) {
+        if (delta != nullptr) delta[pAM + m] = y.x - uA[m];
+        uA[m] = y.x;
+        if (hasB) {
+          if (delta != nullptr) delta[pBM + m] = y.y - uB[m];
+          uB[m] = y.y;
+        }
+      }
+    };
+    rp::convolve<LOGL, R0, R1, R2, T, PAIRS>(buf, t, g, spec, tw, load, store);
+    return;
+  }
+  // times m and m + 1 (m even) of a line as one 8-byte load
+  auto ld2 = [](const float* p, int m) { return *reinterpret_cast<const float2*>(p + m); };
+  auto load2 = [&](int m) -> rp::Pair2 {
+    const float2 a = ld2(fA, m), b = ld2(fB, m);
+    const float2 a0 = ld2(qA[0], m), a1 = ld2(qA[1], m), b0 = ld2(qB[0], m), b1 = ld2(qB[1], m);
+    float2 sa{a0.x + a1.x, a0.y + a1.y}, sb{b0.x + b1.x, b0.y + b1.y};
+    if (d == 2) {
+      const float2 a2 = ld2(qA[2], m), a3 = ld2(qA[3], m), b2 = ld2(qB[2], m), b3 = ld2(qB[3], m);
+      sa = float2{sa.x + (a2.x + a3.x), sa.y + (a2.y + a3.y)};
+      sb = float2{sb.x + (b2.x + b3.x), sb.y + (b2.y + b3.y)};
+    }
+    return rp::Pair2{C{a.x + hinv2 * sa.x, b.x + hinv2 * sb.x},
+                     C{a.y + hinv2 * sa.y, b.y + hinv2 * sb.y}};
   };
   float* uA = u + pAM;
   float* uB = u + pBM;
-  auto store = [&](int m, C y) {
+  auto store2 = [&](int m, C y0, C y1) {
     if (valid) {
-      if (delta != nullptr) delta[pAM + m] = y.x - uA[m];
-      uA[m] = y.x;
+      float2* ua = reinterpret_cast<float2*>(uA + m);
+      if (delta != nullptr) {
+        const float2 o = *ua;
+        *reinterpret_cast<float2*>(delta + pAM + m) = float2{y0.x - o.x, y1.x - o.y};
+      }
+      *ua = float2{y0.x, y1.x};
       if (hasB) {
-        if (delta != nullptr) delta[pBM + m] = y.y - uB[m];
-        uB[m] = y.y;
+        float2* ub = reinterpret_cast<float2*>(uB + m);
+        if (delta != nullptr) {
+          const float2 o = *ub;
+          *reinterpret_cast<float2*>(delta + pBM + m) = float2{y0.y - o.x, y1.y - o.y};
+        }
+        *ub = float2{y0.y, y1.y};
       }
     }
   };
-  rp::convolve<LOGL, R0, R1, R2, T, PAIRS>(buf, t, g, spec, tw, load, store);
+  rp::convolve2<LOGL, R0, R1, R2, T, PAIRS>(buf, t, g, spec, tw, load2, store2);
 }
 
 // spec_rp[c L + rp position of k] = (float) spec64[c L + engine position of k]
@@ -81,16 +122,16 @@ __global__ void k_spectra_rp(Cx<float>* __restrict__ dst, const Cx<double>* __re
   }
 }
 
-template <int LOGL, int R0, int R1, int R2, int T>
+template <int LOGL, int R0, int R1, int R2, int T, bool PAIRED>
 cudaError_t sweep_rp_launch(dim3 grid, cudaStream_t s, const float* f, float* u, float* delta,
                             const Cx<float>* spec, const Cx<float>* tw, const float* zero, int d,
                             int n, int M, int par, float hinv2, int npts, int npairs,
                             size_t fstride, size_t sstride) {
   using P = rp::Plan<LOGL, R0, R1, R2, T>;
   const size_t smem = (size_t)(kRpBlock / T) * P::SMEM * sizeof(Cx<float>);
-  cudaError_t e = prepare_smem(k_sweep_rp<LOGL, R0, R1, R2, T>, smem);
+  cudaError_t e = prepare_smem(k_sweep_rp<LOGL, R0, R1, R2, T, PAIRED>, smem);
   if (e != cudaSuccess) return e;
-  k_sweep_rp<LOGL, R0, R1, R2, T><<<grid, kRpBlock, smem, s>>>(
+  k_sweep_rp<LOGL, R0, R1, R2, T, PAIRED><<<grid, kRpBlock, smem, s>>>(
       f, u, delta, spec, tw, zero, d, n, M, par, hinv2, npts, npairs, fstride, sstride);
   return cudaSuccess;
 }
@@ -99,7 +140,8 @@ cudaError_t sweep_rp_launch(dim3 grid, cudaStream_t s, const float* f, float* u,
 
 cudaError_t launch_sweep_rp(const float* f, float* u, float* delta, const Cx<float>* spec,
                             size_t spec_stride, const Cx<float>* tw, const float* zero,
-                            const LevelShape& ls, int par, float hinv2, cudaStream_t s) {
+                            const LevelShape& ls, int par, float hinv2, bool paired,
+                            cudaStream_t s) {
   const int d = ls.d, n = ls.n, M = ls.M;
   if (!radix_length(M)) return cudaErrorInvalidValue;
   const int logL = ilog2(2 * M);
@@ -112,8 +154,12 @@ cudaError_t launch_sweep_rp(const float* f, float* u, float* delta, const Cx<flo
 #define MGWR_RP_LAUNCH(LG, A, B, C, T)                                                       \
   case LG: {                                                                                 \
     const dim3 grid((unsigned)((npairs + kRpBlock / T - 1) / (kRpBlock / T)), (unsigned)ls.batch); \
-    e = sweep_rp_launch<LG, A, B, C, T>(grid, s, f, u, delta, spec, tw, zero, d, n, M, par,   \
-                                        hinv2, npts, npairs, fstride, spec_stride);          \
+    if (paired)                                                                              \
+      e = sweep_rp_launch<LG, A, B, C, T, true>(grid, s, f, u, delta, spec, tw, zero, d, n, M,  \
+                                                par, hinv2, npts, npairs, fstride, spec_stride); \
+    else                                                                                     \
+      e = sweep_rp_launch<LG, A, B, C, T, false>(grid, s, f, u, delta, spec, tw, zero, d, n, M, \
+                                                 par, hinv2, npts, npairs, fstride, spec_stride); \
     break;                                                                                   \
   }
     MGWR_RP_PLANS(MGWR_RP_LAUNCH)

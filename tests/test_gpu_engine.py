@@ -345,3 +345,16 @@ def test_radix_solve_converges_like_the_fft_solve(precision, d, n, M, batch):
             out.append((s.solution(), st.outer))
     assert abs(out[1][1] - out[0][1]) <= 1  # outer steps: different FP32 rounding may need one more
     assert rel(out[1][0], out[0][0]) <= 1e-9
+
+
+@pytest.mark.parametrize("d,n,M,batch", [(2, 63, 1024, 1), (1, 255, 512, 1), (2, 15, 4096, 1),
+                                         (2, 31, 64, 2), (1, 127, 128, 1), (2, 63, 256, 3)])
+def test_radix_paired_first_pass_matches_the_single_one(d, n, M, batch):
+    # 2 | MGWR_SPLIT_RADIX: the same butterflies with 8-byte gathers and stores;
+    # the compiler may fuse multiply-adds differently in the two code shapes, so
+    # the fields agree to a few FP32 roundings of their scale, not bitwise
+    a, used_a = _sweep32(d, n, M, 1 | G.MGWR_SPLIT_RADIX, batch, delta=True)
+    b, used_b = _sweep32(d, n, M, 2 | G.MGWR_SPLIT_RADIX, batch, delta=True)
+    assert (used_a, used_b) == (1 | G.MGWR_SPLIT_RADIX, 2 | G.MGWR_SPLIT_RADIX)
+    for x, y in zip(a[:2], b[:2]):
+        assert np.abs(x - y).max() <= 16 * 2.0 ** -24 * np.abs(x).max()

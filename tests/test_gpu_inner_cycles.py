@@ -7,7 +7,7 @@ refinement converges to the right answer even when an inner cycle is wrong
 by iterate, with the oracle's FP64 cycle on the same inputs: V(1,1), V(0,1) and
 W(1,0), 1-D and 2-D, M up to 4096, every FP32 smoother variant the tuner can pick
 (bulk-copy staged input lines, tensor-core dense Toeplitz product, register-pass
-FFT engine) besides the shared-memory FFT engine.  They also compare the fused FP32 defect-restriction kernel, which
+FFT engine, single and paired first pass) besides the shared-memory FFT engine.  They also compare the fused FP32 defect-restriction kernel, which
 only a cycle reaches, with the oracle's restriction of the defect after one
 smoothing step, and with the unfused kernels bit for bit.
 
@@ -67,9 +67,10 @@ CASES = [
 ]
 
 # launch shape of the FP32 sweep: the FFT engine, its bulk-copy staged form, the
-# tensor-core form (M = 64, 128, 256 only) or the register-pass engine
+# tensor-core form (M = 64, 128, 256 only) or the register-pass engine (single
+# or paired first pass)
 VARIANTS = {"fft": 1, "staged": 1 | G.MGWR_SPLIT_STAGED, "tensor": 1 | G.MGWR_SPLIT_TENSOR,
-            "radix": 1 | G.MGWR_SPLIT_RADIX}
+            "radix": 1 | G.MGWR_SPLIT_RADIX, "radix2": 2 | G.MGWR_SPLIT_RADIX}
 
 
 def _run(precision, hier, tol, d, n, M, cyc, count, order, split=None):

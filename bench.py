@@ -69,7 +69,7 @@ WORKLOADS = {
 # alpha of a workload when --alpha is not given
 WORKLOAD_ALPHA = {"1d-4095-m65536": 0.2}
 # FP32 cycles per outer defect of a mixed workload when --inner is not given
-WORKLOAD_INNER = {"batch4096-2d-63-m256": 4}
+WORKLOAD_INNER = {"batch4096-2d-63-m256": 3}
 # extra precisions timed beside the value on the same workload, and their steps
 WORKLOAD_ARMS = {"2d-511-m4096": ("fp64", "mixed_dd")}
 # CPU-baseline sample: a complete oracle solve (every time level) of the workload's
@@ -128,8 +128,8 @@ def parse():
                    help="served: server admission order")
     p.add_argument("--inner", type=int, default=None, help="mixed modes: FP32 cycles per outer defect")
     p.add_argument("--outer-switch", type=float, default=None,
-                   help="mixed modes: relative defect at or above which an outer step's defect "
-                        "takes the FP32-convolution form (mgwr_set_outer_switch)")
+                   help="mixed modes: fraction of the last full outer defect down to which an "
+                        "outer step carries its defect by the correction (mgwr_set_outer_switch)")
     p.add_argument("--alpha", type=float, default=None)
     p.add_argument("--no-autotune", action="store_true", help="keep the default engine launch shapes")
     p.add_argument("--split", default=None,
@@ -843,7 +843,7 @@ def measure_arm(args, torch, mgwr, wl: dict, precision: str, steps: int, warmup:
            "solve": {"cycles": stats[-1].cycles, "outer": stats[-1].outer,
                      "relres": stats[-1].relres, "factor": stats[-1].factor},
            "gpu_launches": launches, "engine_splits": splits,
-           "inner_cycles": (inner or (3 if precision == "mixed" else 2)) if mixed else None}
+           "inner_cycles": (inner or 2) if mixed else None}
     if clk is not None:
         out["clocks"] = clk.summary()
     field_bytes = wl["unknowns"] * 8

@@ -167,19 +167,25 @@ int mgwr_auto_precision(int d, int n, int M, int precision, int* resolved);
 int mgwr_set_order(mgwr_t h, int order);
 /* cudaStream_t to run on (NULL: the handle's own stream). */
 int mgwr_set_stream(mgwr_t h, void* stream);
-/* Inner cycles per outer defect in the refinements (1..16).  Default: 3 for
- * MGWR_MIXED, whose FP64 outer defect costs about four FP32 cycles on GB300,
- * and 2 for MGWR_MIXED_DD and MGWR_DD, whose double-float outer defect costs
- * about one. */
+/* Inner cycles per outer defect in the refinements (1..16).  Default 2 in
+ * every refinement: most outer steps carry their defect by the correction at
+ * the cost of about one FP32 cycle (mgwr_set_outer_switch), and the full
+ * defects they leave (anchors and the stopping test) do not grow with the
+ * number of steps. */
 int mgwr_set_inner_cycles(mgwr_t h, int cycles);
-/* Mixed modes (MGWR_MIXED, MGWR_MIXED_DD): an outer step that starts from a
- * relative defect of at least `rel` (default 1e-2; +inf: never) computes the
- * defect of its result as (f - A_h u) - T_M u with f - A_h u in the outer
- * precision and T_M u by one FP32 convolution of the rounded iterate.  Its error,
- * about 1e-6 of |T_M u|, is then far below the defect it drives, so the steps
- * converge as with the exact defect; every stopping decision is still taken on
- * the defect in the outer precision.  The paper has no counterpart (its
- * solver is one precision).  MGWR_E_INVAL for rel < 0 or NaN. */
+/* Mixed modes (MGWR_MIXED, MGWR_MIXED_DD), lines of M <= 4096: the outer
+ * defect of a step's result u + e is carried from the step's starting defect r
+ * by its correction, r - (T_M (x) I + A_h) e, with A_h e and the subtraction in
+ * the outer precision and T_M e by one FP32 convolution of e (residual
+ * replacement), instead of computed in full (a convolution in the outer
+ * precision, the solve's dearest kernel in MGWR_MIXED).  A carried defect errs
+ * by about 1e-6 of the defect at the last full computation (the anchor), so a
+ * step carries it while its starting relative defect is at least `rel` times
+ * the anchor's (default 1e-2; 0: every step; +inf: none), in every instance of
+ * a batch whose anchor is not already below the tolerance / rel; the other
+ * steps compute it in full and so set a new anchor.  Every stopping decision is
+ * taken on a full defect.  The paper has no counterpart (its solver is one
+ * precision).  MGWR_E_INVAL for rel < 0 or NaN. */
 int mgwr_set_outer_switch(mgwr_t h, double rel);
 
 /* Launch shape of the FFT-engine kernels (no counterpart in the paper; the

@@ -33,9 +33,11 @@ enum RState {
   R_CURRENT = 3,  // r_l holds the defect of the current (u_l, f_l)
 };
 
-// Default relative defect at or above which an outer step of the mixed modes
-// computes its defect in the FP32-convolution form (launch_defect_hybrid);
-// mgwr_set_outer_switch changes it per handle.
+// Default switch of the mixed modes' outer defect (mgwr_set_outer_switch): an
+// outer step carries the defect by its correction (launch_defect_update, error
+// about 1e-6 of the defect at the last full computation, the anchor) while
+// the relative defect is at least this fraction of the anchor's, so that the
+// carried error stays near 1e-4 of the defect it updates.
 constexpr double kLooseOuter = 1e-2;
 
 template <class R>
@@ -101,7 +103,7 @@ struct mgwr_handle {
   // iteration: settings and outer-defect form), replayed every iteration
   bool use_graphs = true;
   struct IterGraph {
-    long long key;        // (precision, cycle, nu1, nu2, inner, order, loose, finest state)
+    long long key;        // (precision, cycle, nu1, nu2, inner, order, outer form, finest state)
     cudaGraphExec_t exec;
     bool exact;           // its norms come from the full defect in the working precision
     long long kernels;    // kernel launches recorded in the graph
@@ -109,8 +111,14 @@ struct mgwr_handle {
   std::vector<IterGraph> graphs;
   // the finest iterate is zero (right-hand side just set without initial values)
   bool u_zero = false;
-  // mixed modes: this iteration's outer defect takes the FP32-convolution form
-  bool loose_outer = false;
+  // mixed modes: the outer defect of the iteration being enqueued is carried by
+  // the step's correction (launch_defect_update) instead of computed in full
+  bool carry_outer = false;
+  // where the outer defect in double-float is held for the carried form: -1
+  // nowhere (full form only), 0 the right-hand side f_dd (u = 0), 1 outer_field
+  int outer_src = -1;
+  // the finest outer defect of MGWR_MIXED, M <= kShortMaxM, in double-float (outer_field)
+  double* r_outer = nullptr;
   // per-kernel-class timing (mgwr_profile): event pairs around each launch
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -541,20 +549,68 @@ int read_norms(mgwr_t h, std::vector<double>& out) {
   return MGWR_OK;
 }
 
+// The field that holds a solve's finest outer defect in double-float for the
+// carried form (launch_defect_update; 8 bytes a value): its own field r_outer
+// in MGWR_MIXED; in MGWR_MIXED_DD the FP64 iterate's field, which a solve
+// leaves unused while it holds the iterate in double-float (u_dd, joined back
+// at its end), so only solves may write it.  Null where no line length or
+// precision has the carried form.
+mgwr::dd* outer_field(const mgwr_handle* h) {
+  static_assert(sizeof(mgwr::dd) == sizeof(double), "a double-float value fills a double's slot");
+  if (h->M > mgwr::kShortMaxM) return nullptr;
+  if (h->precision == MGWR_MIXED) return reinterpret_cast<mgwr::dd*>(h->r_outer);
+  if (h->precision == MGWR_MIXED_DD) return reinterpret_cast<mgwr::dd*>(h->h64.u[h->nlev - 1]);
+  return nullptr;
+}
+
+bool carries(const mgwr_handle* h) { return outer_field(h) != nullptr; }
+
+// The full outer defect of the mixed modes (FP64 for MGWR_MIXED, double-float
+// for MGWR_MIXED_DD) rounded into the FP32 right-hand side, norms into
+// norm_bits (cleared by the caller); when the handle carries its outer defect,
+// first into outer_field in double-float, then rounded from there.  Called by
+// solves only (outer_field may be the FP64 iterate's field).
+int enqueue_outer_full(mgwr_t h) {
+  const int L = h->nlev - 1;
+  const size_t cnt = level_count(h, L);
+  const bool ddef = h->precision == MGWR_MIXED_DD;
+  mgwr::dd* keep = outer_field(h);
+  const int pd = prof_begin(h, ddef ? MGWR_K_DEFECT_DD : MGWR_K_DEFECT64, (double)(points(h, L) * h->B));
+  if (ddef && keep != nullptr)
+    MGWR_CK(h, (mgwr::launch_defect<mgwr::dd, mgwr::dd>(
+                   h->u_dd, h->f_dd, keep, h->tspec_dd, (size_t)h->L, h->tw_dd, h->zero_dd,
+                   scratch_for<mgwr::dd>(h), shape(h, L), mgwr::dd(h->hinv2[L]), h->norm_bits,
+                   split_of(h, MGWR_K_DEFECT_DD, L), h->stream)));
+  else if (ddef)
+    MGWR_CK(h, (mgwr::launch_defect<mgwr::dd, float>(
+                   h->u_dd, h->f_dd, h->h32.f[L], h->tspec_dd, (size_t)h->L, h->tw_dd, h->zero_dd,
+                   scratch_for<mgwr::dd>(h), shape(h, L), mgwr::dd(h->hinv2[L]), h->norm_bits,
+                   split_of(h, MGWR_K_DEFECT_DD, L), h->stream)));
+  else if (keep != nullptr)
+    MGWR_CK(h, (mgwr::launch_defect<double, mgwr::dd>(
+                   h->h64.u[L], h->h64.f[L], keep, h->h64.tspec, (size_t)h->L, h->h64.tw,
+                   h->h64.zero, scratch_for<double>(h), shape(h, L), h->hinv2[L], h->norm_bits,
+                   split_of(h, MGWR_K_DEFECT64, L), h->stream)));
+  else
+    MGWR_CK(h, (mgwr::launch_defect<double, float>(
+                   h->h64.u[L], h->h64.f[L], h->h32.f[L], h->h64.tspec, (size_t)h->L, h->h64.tw,
+                   h->h64.zero, scratch_for<double>(h), shape(h, L), h->hinv2[L], h->norm_bits,
+                   split_of(h, MGWR_K_DEFECT64, L), h->stream)));
+  prof_end(h, pd);
+  if (keep != nullptr) MGWR_CK(h, mgwr::launch_round_dd(keep, h->h32.f[L], cnt, h->stream));
+  h->h32.rs[L] = R_STALE;
+  return MGWR_OK;
+}
+
 // FP64 defect of the finest iterate with its per-instance infinity norms.  In
 // mixed mode the defect is written, rounded, as the FP32 right-hand side.
 int finest_defect_norms(mgwr_t h, std::vector<double>& norms, bool to_h32) {
   const int L = h->nlev - 1;
   MGWR_TRY(clear_norms(h));
-  const int pm = prof_begin(h, MGWR_K_DEFECT64, (double)(points(h, L) * h->B));
   if (to_h32) {
-    MGWR_CK(h, (mgwr::launch_defect<double, float>(h->h64.u[L], h->h64.f[L], h->h32.f[L],
-                                                    h->h64.tspec, (size_t)h->L, h->h64.tw,
-                                                    h->h64.zero, scratch_for<double>(h), shape(h, L), h->hinv2[L], h->norm_bits,
-                                                    split_of(h, MGWR_K_DEFECT64, L),
-                                                    h->stream)));
-    h->h32.rs[L] = R_STALE;
+    MGWR_TRY(enqueue_outer_full(h));
   } else {
+    const int pm = prof_begin(h, MGWR_K_DEFECT64, (double)(points(h, L) * h->B));
     MGWR_TRY(ensure_field(h, &h->h64.r[L], level_count(h, L)));
     MGWR_CK(h, (mgwr::launch_defect<double, double>(h->h64.u[L], h->h64.f[L], h->h64.r[L],
                                                      h->h64.tspec, (size_t)h->L, h->h64.tw,
@@ -562,23 +618,16 @@ int finest_defect_norms(mgwr_t h, std::vector<double>& norms, bool to_h32) {
                                                     split_of(h, MGWR_K_DEFECT64, L),
                                                      h->stream)));
     h->h64.rs[L] = R_CURRENT;
+    prof_end(h, pm);
   }
-  prof_end(h, pm);
   return read_norms(h, norms);
 }
 
 // Double-float defect of the finest iterate, rounded into the FP32 right-hand
 // side, with per-instance norms (MGWR_MIXED_DD).
 int finest_defect_norms_dd(mgwr_t h, std::vector<double>& norms) {
-  const int L = h->nlev - 1;
   MGWR_TRY(clear_norms(h));
-  const int pm = prof_begin(h, MGWR_K_DEFECT_DD, (double)(points(h, L) * h->B));
-  MGWR_CK(h, (mgwr::launch_defect<mgwr::dd, float>(h->u_dd, h->f_dd, h->h32.f[L], h->tspec_dd,
-                                                    (size_t)h->L, h->tw_dd, h->zero_dd, scratch_for<mgwr::dd>(h), shape(h, L),
-                                                    mgwr::dd(h->hinv2[L]), h->norm_bits, split_of(h, MGWR_K_DEFECT_DD, L),
-                                                    h->stream)));
-  prof_end(h, pm);
-  h->h32.rs[L] = R_STALE;
+  MGWR_TRY(enqueue_outer_full(h));
   return read_norms(h, norms);
 }
 
@@ -610,15 +659,16 @@ int outer_defect_ddd(mgwr_t h) {
   return MGWR_OK;
 }
 
-// Inner cycles per outer defect of the refinements.  Default: 3 for MGWR_MIXED,
-// whose FP64 outer defect costs about four FP32 cycles on GB300 (FP64 runs at
-// 1/64 of the FP32 rate), so fewer outer steps pay (2-D 511 x 511, M = 4096 to
-// 1e-8: 5 outer steps of 2 cycles 1143 ms, 4 of 3 cycles 1024 ms); 2 for the
-// double-float outer defects, which cost about one FP32 cycle (709 against
-// 731 ms on the same solve).
+// Inner cycles per outer defect of the refinements.  Default 2: the outer
+// steps that carry their defect by the correction (launch_defect_update) cost
+// about one FP32 cycle, so the full FP64 defects (about eight FP32 cycles on
+// GB300, FP64 running at 1/64 of the FP32 rate) are needed only as anchors and
+// for the stopping test, whatever the number of steps (2-D 511 x 511, M = 4096
+// to 1e-8: 5 outer steps of 2 cycles 797 ms, of 3 cycles 906 ms in
+// MGWR_MIXED; 513 against 623 ms in MGWR_MIXED_DD).
 int inner_cycles(const mgwr_handle* h) {
   if (h->inner > 0) return h->inner;
-  return h->precision == MGWR_MIXED ? 3 : 2;
+  return 2;
 }
 
 // Inner cycles of the outer step being enqueued: inner_cycles, or one more on
@@ -678,50 +728,29 @@ int enqueue_iteration(mgwr_t h, int cyc, int nu1, int nu2, bool* exact) {
       MGWR_CK(h, mgwr::launch_refine(h->h64.u[L], h->h32.u[L], cnt, h->stream));
     prof_end(h, pm);
     MGWR_TRY(clear_norms(h));
-    if (h->loose_outer && h->M <= mgwr::kShortMaxM) {
-      // large defect: FP32 time convolution, stencil and source in the iterate's arithmetic
+    if (h->carry_outer) {
+      // the defect carried by the correction e = h32.u: outer_field = r - A e, with
+      // r the double-float right-hand side f_dd after MGWR_MIXED_DD's start from
+      // u = 0, else outer_field
       const int pl = prof_begin(h, MGWR_K_DEFECT32, (double)(points(h, L) * h->B));
-      // on the register-pass engine where it serves the length (fewer instructions
-      // per value: 2-D 511 x 511, M = 4096 in 45 -> XX ms), else the radix-8 engine
-      const bool rp = h->h32.tspec_rp != nullptr;
-      if (ddef && rp)
-        MGWR_CK(h, mgwr::launch_defect_hybrid_rp<mgwr::dd>(
-                       h->u_dd, h->f_dd, h->h32.f[L], h->h32.tspec_rp, (size_t)h->L, h->h32.tw,
-                       h->zero_dd, shape(h, L), mgwr::dd(h->hinv2[L]), h->norm_bits, h->stream));
-      else if (ddef)
-        MGWR_CK(h, mgwr::launch_defect_hybrid<mgwr::dd>(
-                       h->u_dd, h->f_dd, h->h32.f[L], h->h32.tspec, (size_t)h->L, h->h32.tw,
-                       h->zero_dd, shape(h, L), mgwr::dd(h->hinv2[L]), h->norm_bits, h->stream));
-      else if (rp)
-        MGWR_CK(h, mgwr::launch_defect_hybrid_rp<double>(
-                       h->h64.u[L], h->h64.f[L], h->h32.f[L], h->h32.tspec_rp, (size_t)h->L,
-                       h->h32.tw, h->h64.zero, shape(h, L), h->hinv2[L], h->norm_bits, h->stream));
-      else
-        MGWR_CK(h, mgwr::launch_defect_hybrid<double>(
-                       h->h64.u[L], h->h64.f[L], h->h32.f[L], h->h32.tspec, (size_t)h->L,
-                       h->h32.tw, h->h64.zero, shape(h, L), h->hinv2[L], h->norm_bits, h->stream));
+      const bool rp = h->h32.tspec_rp != nullptr;  // the register-pass engine serves M
+      const Cx<float>* ts = rp ? h->h32.tspec_rp : h->h32.tspec;
+      mgwr::dd* ro = outer_field(h);
+      const mgwr::dd* ri = h->outer_src == 0 ? h->f_dd : ro;
+      const mgwr::dd hi2(h->hinv2[L]);
+      MGWR_CK(h, rp ? mgwr::launch_defect_update_rp<mgwr::dd>(
+                          h->h32.u[L], ri, ro, h->h32.f[L], ts, (size_t)h->L, h->h32.tw,
+                          h->h32.zero, shape(h, L), hi2, h->norm_bits, h->stream)
+                    : mgwr::launch_defect_update<mgwr::dd>(
+                          h->h32.u[L], ri, ro, h->h32.f[L], ts, (size_t)h->L, h->h32.tw,
+                          h->h32.zero, shape(h, L), hi2, h->norm_bits, h->stream));
       prof_end(h, pl);
       h->h32.rs[L] = R_STALE;
       *exact = false;
-      MGWR_CK(h, cudaMemcpyAsync(h->norm_host, h->norm_bits, sizeof(unsigned long long) * h->B,
-                                 cudaMemcpyDeviceToHost, h->stream));
-      return MGWR_OK;
+    } else {
+      MGWR_TRY(enqueue_outer_full(h));
+      *exact = true;
     }
-    const int pd = prof_begin(h, ddef ? MGWR_K_DEFECT_DD : MGWR_K_DEFECT64, (double)(points(h, L) * h->B));
-    if (ddef)
-      MGWR_CK(h, (mgwr::launch_defect<mgwr::dd, float>(h->u_dd, h->f_dd, h->h32.f[L], h->tspec_dd,
-                                                        (size_t)h->L, h->tw_dd, h->zero_dd, scratch_for<mgwr::dd>(h), shape(h, L),
-                                                        mgwr::dd(h->hinv2[L]), h->norm_bits, split_of(h, MGWR_K_DEFECT_DD, L),
-                                                        h->stream)));
-    else
-      MGWR_CK(h, (mgwr::launch_defect<double, float>(h->h64.u[L], h->h64.f[L], h->h32.f[L],
-                                                      h->h64.tspec, (size_t)h->L, h->h64.tw,
-                                                      h->h64.zero, scratch_for<double>(h), shape(h, L), h->hinv2[L], h->norm_bits,
-                                                    split_of(h, MGWR_K_DEFECT64, L),
-                                                      h->stream)));
-    prof_end(h, pd);
-    h->h32.rs[L] = R_STALE;
-    *exact = true;
   }
   MGWR_CK(h, cudaMemcpyAsync(h->norm_host, h->norm_bits, sizeof(unsigned long long) * h->B,
                              cudaMemcpyDeviceToHost, h->stream));
@@ -737,7 +766,8 @@ int enqueue_iteration(mgwr_t h, int cyc, int nu1, int nu2, bool* exact) {
 long long iteration_key(const mgwr_handle* h, int cyc, int nu1, int nu2) {
   const int rs_in = h->precision == MGWR_FP64 ? h->h64.rs[h->nlev - 1] : 0;
   return ((((((long long)h->precision * 4 + cyc) * 32 + nu1) * 32 + nu2) * 32 * 4 +
-           (long long)step_cycles(h) * 4 + h->order) * 2 + (h->loose_outer ? 1 : 0)) * 4 + rs_in;
+           (long long)step_cycles(h) * 4 + h->order) * 4 + (h->carry_outer ? 1 + h->outer_src : 0)) *
+             4 + rs_in;
 }
 
 int run_iteration(mgwr_t h, int cyc, int nu1, int nu2, std::vector<double>& norms, bool* exact) {
@@ -1270,7 +1300,13 @@ int mgwr_set_precision(mgwr_t h, int precision) {
     return fail(h, MGWR_E_INVAL,
                 "precision must be MGWR_FP64, MGWR_MIXED, MGWR_MIXED_DD, MGWR_DD or MGWR_AUTO");
   if (precision == MGWR_DD) MGWR_TRY(ensure_hdd(h));
-  if (precision == MGWR_MIXED || precision == MGWR_MIXED_DD) MGWR_TRY(ensure_h32(h));
+  if (precision == MGWR_MIXED || precision == MGWR_MIXED_DD) {
+    MGWR_TRY(ensure_h32(h));
+    // the double-float outer defect of MGWR_MIXED, for the carried form
+    // (MGWR_MIXED_DD keeps its own in the FP64 iterate's field during a solve)
+    if (precision == MGWR_MIXED && h->M <= mgwr::kShortMaxM)
+      MGWR_TRY(ensure_field(h, &h->r_outer, level_count(h, h->nlev - 1)));
+  }
   if (precision == MGWR_MIXED_DD) {
     MGWR_TRY(ensure_dd(h));
     MGWR_CK(h, cudaStreamSynchronize(h->stream));
@@ -1428,6 +1464,9 @@ struct SolveState {
   // refinements: defect reduction of the last outer step and its inner cycles
   double last_q = 0.0;
   int last_k = 0;
+  // mixed modes: per-instance relative defect at the last full outer defect
+  // (the anchor of the carried defects since)
+  std::vector<double> anchor;
   // the iteration being run
   double rel_before = 0.0;
   int k_now = 1;
@@ -1492,7 +1531,33 @@ int solve_begin(mgwr_t h, SolveState& S, int cyc, int nu1, int nu2, double tol, 
     h->r0_valid = true;
   }
   S.rel = relative(h, S.norms, h->relres);
+  // the outer defect to carry from: from u = 0 f itself (f_dd in MGWR_MIXED_DD;
+  // split into outer_field in MGWR_MIXED), else the full defect just computed
+  // (kept in outer_field by enqueue_outer_full)
+  h->outer_src = -1;
+  if (S.mixed && !S.ddc && carries(h) && std::isfinite(h->loose_above)) {
+    h->outer_src = h->u_zero && S.ddef ? 0 : 1;
+    if (h->u_zero && !S.ddef)
+      MGWR_CK(h, mgwr::launch_split(outer_field(h), h->h64.f[L], cntL, h->stream));
+  }
+  S.anchor = h->relres;
   return MGWR_OK;
+}
+
+// Mixed modes: whether the next outer defect may be carried by the step's
+// correction.  Its error is about 1e-6 of the anchor (the defect at the last
+// full computation); every instance must still be at least the switch times
+// its anchor, or have an anchor so small against the tolerance that the
+// carried error cannot decide its stopping test (which the full defect
+// confirms anyway).
+bool carry_next(const mgwr_handle* h, const SolveState& S) {
+  if (!S.mixed || S.ddc || h->outer_src < 0) return false;
+  const double x = h->loose_above;
+  for (int b = 0; b < h->B; ++b) {
+    const double a = x * S.anchor[b];
+    if (!(h->relres[b] >= a || a <= S.tol)) return false;
+  }
+  return true;
 }
 
 // Decides whether another iteration runs (false: the loop ends, S.status set)
@@ -1507,10 +1572,9 @@ bool solve_plan(mgwr_t h, SolveState& S) {
     S.status = MGWR_E_NOCONV;
     return false;
   }
-  // outer defects of the mixed modes while the defect is large (at least the
-  // handle's switch, kLooseOuter by default) take the FP32-convolution form,
-  // whose error (about 1e-6 of |T_M u|) is then far below the defect
-  h->loose_outer = S.mixed && !S.ddc && S.rel >= h->loose_above;
+  // outer defects of the mixed modes carried by the correction while the
+  // defect is large against the anchor (mgwr_set_outer_switch)
+  h->carry_outer = carry_next(h, S);
   // Refinements: when the last step's reduction predicts that this step ends
   // just above the tolerance, but below half of it with one cycle more, this
   // step takes that cycle instead of leaving a whole outer step (and its outer
@@ -1548,10 +1612,18 @@ int solve_after(mgwr_t h, SolveState& S, bool exact) {
     S.last_q = S.rel / S.rel_before;
     S.last_k = S.k_now;
   }
+  const bool mixed_outer = S.mixed && !S.ddc;
+  if (mixed_outer) {
+    // outer_field now holds the step's outer defect (carried or full)
+    h->outer_src = carries(h) ? 1 : -1;
+    if (exact) S.anchor = h->relres;
+  }
+  h->carry_outer = false;
   if (!exact && S.rel <= S.tol) {
     MGWR_TRY(solve_full_defect(h, S));
     S.rel = relative(h, S.norms, h->relres);
     exact = true;
+    if (mixed_outer) S.anchor = h->relres;
   }
   S.rel_exact = exact;
   ++S.outer;
@@ -1564,7 +1636,8 @@ int solve_end(mgwr_t h, SolveState& S, mgwr_stats* st) {
   const int L = h->nlev - 1;
   const size_t cntL = level_count(h, L);
   h->u_zero = false;
-  h->loose_outer = false;
+  h->carry_outer = false;
+  h->outer_src = -1;
   if (S.ddef) MGWR_CK(h, mgwr::launch_join(h->h64.u[L], h->u_dd, cntL, h->stream));
   if (!S.rel_exact) {  // report the full defect also when stopping on max_cycles
     MGWR_TRY(finest_defect_norms(h, S.norms, false));
@@ -2171,6 +2244,8 @@ int mgwr_footprint(int d, int n, int M, int batch, int precision, size_t* bytes)
       total += r512(8 * B * nlev * L) + r512(8 * B * L);
     if (precision == MGWR_MIXED_DD)
       total += 2 * r512(8 * B * pts[0] * M) + r512(16 * B * L) + r512(16 * Lt);
+    if (precision == MGWR_MIXED && M <= (size_t)mgwr::kShortMaxM)
+      total += r512(8 * B * pts[0] * M);  // carried double-float outer defect
   }
   *bytes = total;
   return MGWR_OK;

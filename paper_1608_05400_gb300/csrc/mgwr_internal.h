@@ -213,25 +213,29 @@ cudaError_t launch_round(float* dst, const double* src, size_t count, cudaStream
 cudaError_t launch_absmax_round(const double* x, float* out, size_t per, int batch,
                                 unsigned long long* norm_bits, cudaStream_t s);
 
-// Outer defect of the mixed modes in a cheaper form for the first outer steps:
-// r = (f - A_h u) - T_M u with f - A_h u in the iterate's arithmetic Tin
-// (double or double-float; the stencil differences are taken before the sum)
-// and T_M u by an FP32 FFT convolution of (float) u (FP32 spectra `tspec` and
-// twiddles `tw`); r rounded to FP32, |r|_inf of instance b into norm_bits[b].
-// Its error is that of one FP32 convolution, about 1e-6 of |T_M u|.  Lines of
-// M <= kShortMaxM only (else cudaErrorInvalidValue).
-template <class Tin>
-cudaError_t launch_defect_hybrid(const Tin* u, const Tin* f, float* r, const Cx<float>* tspec,
-                                 size_t spec_stride, const Cx<float>* tw, const Tin* zero,
-                                 const LevelShape& ls, Tin hinv2, unsigned long long* norm_bits,
-                                 cudaStream_t s);
+// Outer defect of the mixed modes carried by the correction of an outer step
+// (residual replacement): r_out = r_in - (T_M (x) I + A_h) e, where e is the
+// step's FP32 correction (u_new = u_old + e), T_M e an FP32 FFT convolution
+// (FP32 spectra `tspec`, twiddles `tw`) and the stencil on e, widened, and the
+// subtraction in double-float (W = dd, the one instantiation); r_out also
+// rounded into r32, |r_out|_inf of instance b into norm_bits[b].  r_in and
+// r_out may be the same field.  Its error is that of one FP32 convolution of
+// e, about 1e-6 of |T_M e|.  Lines of M <= kShortMaxM only (else
+// cudaErrorInvalidValue).  zero: M FP32 zeros.
+template <class W>
+cudaError_t launch_defect_update(const float* e, const W* r_in, W* r_out, float* r32,
+                                 const Cx<float>* tspec, size_t spec_stride, const Cx<float>* tw,
+                                 const float* zero, const LevelShape& ls, W hinv2,
+                                 unsigned long long* norm_bits, cudaStream_t s);
 // The same on the register-pass engine (64 <= M <= kShortMaxM), tspec in its
 // spectral order (launch_spectra_rp).
-template <class Tin>
-cudaError_t launch_defect_hybrid_rp(const Tin* u, const Tin* f, float* r, const Cx<float>* tspec,
-                                    size_t spec_stride, const Cx<float>* tw, const Tin* zero,
-                                    const LevelShape& ls, Tin hinv2, unsigned long long* norm_bits,
-                                    cudaStream_t s);
+template <class W>
+cudaError_t launch_defect_update_rp(const float* e, const W* r_in, W* r_out, float* r32,
+                                    const Cx<float>* tspec, size_t spec_stride,
+                                    const Cx<float>* tw, const float* zero, const LevelShape& ls,
+                                    W hinv2, unsigned long long* norm_bits, cudaStream_t s);
+// out = (float) x for a double-float field of `count` values.
+cudaError_t launch_round_dd(const dd* x, float* out, size_t count, cudaStream_t s);
 // Per instance b: u = broadcast of g_b along time (initial iterate u^0(t) = g);
 // f += c_b d_{b,m} g_b.  g: batch * N, dk: batch * (M+1), c: batch (device).
 cudaError_t launch_initial(double* u, double* f, const double* g, const double* dk, const double* c,

@@ -378,6 +378,12 @@ __global__ void k_join(double* __restrict__ dst, const dd* __restrict__ src, siz
     dst[i] = (double)src[i].hi + (double)src[i].lo;
 }
 
+__global__ void k_round_dd(float* __restrict__ dst, const dd* __restrict__ src, size_t count) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
+       i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = float(src[i]);
+}
+
 __global__ void k_split_cx(Cx<dd>* __restrict__ dst, const Cx<double>* __restrict__ src,
                            size_t count) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
@@ -726,6 +732,11 @@ cudaError_t launch_split(dd* dst, const double* src, size_t count, cudaStream_t 
 
 cudaError_t launch_join(double* dst, const dd* src, size_t count, cudaStream_t s) {
   k_join<<<elementwise_grid(count), 256, 0, s>>>(dst, src, count);
+  return counted(cudaGetLastError());
+}
+
+cudaError_t launch_round_dd(const dd* x, float* out, size_t count, cudaStream_t s) {
+  k_round_dd<<<elementwise_grid(count), 256, 0, s>>>(out, x, count);
   return counted(cudaGetLastError());
 }
 

@@ -335,6 +335,7 @@ template cudaError_t launch_sweep_long<float>(const float*, float*, float*, cons
                                                  int, cudaStream_t);
 MGWR_INST_LONG_DEFECT(double, double)
 MGWR_INST_LONG_DEFECT(double, float)
+MGWR_INST_LONG_DEFECT(double, dd)
 MGWR_INST_LONG_DEFECT(float, float)
 MGWR_INST_LONG_DEFECT(dd, float)
 MGWR_INST_LONG_DEFECT(dd, dd)

@@ -79,9 +79,10 @@ def test_footprint_is_host_arithmetic_and_scales(lib):
     fields = 4 * 255 ** 2 * 1024 * 8
     fp = footprint(2, 255, 1024, 1, MGWR_FP64)
     assert fields < fp < 1.5 * fields
-    # mixed keeps the FP64 iterate and right-hand side and an FP32 hierarchy
+    # mixed keeps the FP64 iterate, right-hand side and carried outer defect and
+    # an FP32 hierarchy: about 8 / 7 of FP64 on a 2-D grid
     mx = footprint(2, 255, 1024, 1, MGWR_MIXED)
-    assert 2 * 255 ** 2 * 1024 * 8 + 4 * 255 ** 2 * 1024 * 4 < mx < fp
+    assert 3 * 255 ** 2 * 1024 * 8 + 4 * 255 ** 2 * 1024 * 4 < mx < 1.15 * fp
     # linear in the batch, monotone in n and M
     assert abs(footprint(2, 63, 256, 64) - 64 * footprint(2, 63, 256, 1)) < 64 * (3 << 20)
     assert footprint(1, 63, 64) < footprint(1, 127, 64) < footprint(1, 127, 128)

@@ -201,3 +201,78 @@ def test_outer_defect_of_a_refinement_step_matches_oracle(precision, d, n, M):
         rounding = 2.0 ** -23 * np.abs(ref).max()
         bound = (2e-6 * tu if switch == 0.0 else 0.0) + rounding
         assert err <= bound, (switch, err, bound, tu)
+
+
+@pytest.mark.parametrize("precision", [G.MGWR_MIXED, G.MGWR_MIXED_DD])
+@pytest.mark.parametrize("d,n,M", [(2, 31, 1024), (1, 127, 64), (2, 15, 4096), (1, 63, 16)])
+def test_carried_defect_from_a_full_anchor_matches_oracle(precision, d, n, M):
+    # One outer step with a full defect (switch +inf) leaves u_old; the next solve
+    # computes the full defect of u_old (the anchor, kept in double-float) and,
+    # with the switch at 0, carries it through one more step:
+    # r = r_old - (T_M (x) I + A_h) e, e = u_new - u_old.  Against the oracle's
+    # direct-sum defect of u_new, the FP32 right-hand side it leaves errs by the
+    # FP32 convolution of e (about 1e-6 of |T_M e|), its rounding to FP32, and
+    # the anchor's own rounding (a few FP64 or double-float units of the defect's
+    # terms); carrying from the wrong defect (f, or the anchor's FP32 rounding)
+    # misses by |A u_old| or eps32 |r_old|.
+    W = omg.WRMG(d, n, M, 1.0, 0.55)
+    f = inputs.random_field(n ** d, M, seed=23)
+    L = W.finest
+    with G.Solver(d, n, M, 1.0, 0.55) as s:
+        s.set_precision(precision)
+        s.set_inner_cycles(1)
+        s.set_outer_switch(math.inf)
+        s.set_rhs(f)
+        s.solve(1, 1, 1, tol=1e-300, max_cycles=1, allow_noconv=True)
+        u_old = s.solution()
+        s.set_outer_switch(0.0)
+        s.solve(1, 1, 1, tol=1e-300, max_cycles=1, allow_noconv=True)
+        u_new = s.solution()
+        r32 = s.field_get(G.MGWR_H32, L, G.MGWR_F)
+    ref = W.defect(L, u_new, f)
+    e = u_new - u_old
+    te = np.abs(e @ W.Tm.T).max()
+    err = np.abs(r32 - ref).max()
+    terms = np.abs(f).max() + np.abs(u_old @ W.Tm.T).max() + 4 * d * (n + 1) ** 2 * np.abs(u_old).max()
+    anchor = (2.0 ** -44 if precision == G.MGWR_MIXED_DD else 2.0 ** -50) * terms
+    bound = 2e-6 * te + 2.0 ** -23 * np.abs(ref).max() + anchor
+    assert err <= bound, (err, bound, te, anchor)
+    # the step made progress from the anchor, so the check is not vacuous
+    assert np.abs(ref).max() < 0.5 * np.abs(W.defect(L, u_old, f)).max()
+
+
+@pytest.mark.parametrize("precision", [G.MGWR_MIXED, G.MGWR_MIXED_DD])
+def test_carried_defects_save_full_defects_and_solve_the_same(precision):
+    # default switch (carry while the defect is >= 1e-2 of the anchor's) against
+    # +inf (every outer defect in full): the same solution to the tolerance, about
+    # the same outer steps, fewer full outer defects, and the reported relative
+    # defect is the full one of the returned iterate
+    d, n, M, tol = 2, 63, 256, 1e-10
+    prob = inputs.Problem(d, n, M, 1.0, 0.6, "t2")
+    full_class = "defect64" if precision == G.MGWR_MIXED else "defect_dd"
+    out = {}
+    for switch in (None, math.inf):
+        with G.Solver(d, n, M, 1.0, 0.6) as s:
+            s.set_precision(precision)
+            if switch is not None:
+                s.set_outer_switch(switch)
+            s.set_rhs(prob.rhs())
+            s.profile(True)
+            st = s.solve(1, 1, 1, tol=tol, max_cycles=40)
+            prof = s.profile_read()
+            u = s.solution()
+            W = omg.WRMG(d, n, M, 1.0, 0.6)
+            rel_o = np.abs(W.defect(W.finest, u, prob.rhs())).max() / np.abs(prob.rhs()).max()
+            out[switch] = (st, prof[full_class]["launches"], prof["defect32"]["launches"], u, rel_o)
+    (st_c, full_c, carried_c, u_c, rel_c), (st_f, full_f, carried_f, u_f, rel_f) = out[None], out[math.inf]
+    assert st_c.status == st_f.status == G.MGWR_OK
+    assert carried_f == 0 and carried_c > 0
+    assert full_c < full_f
+    assert abs(st_c.outer - st_f.outer) <= 1
+    # the reported defect against the oracle's: both in FP64 (or double-float),
+    # summed in different orders, so they differ by a few units of the terms
+    fmax = np.abs(prob.rhs()).max()
+    terms = fmax + 4 * d * (n + 1) ** 2 * np.abs(u_c).max() + np.abs(u_c @ W.Tm.T).max()
+    eps = 2.0 ** -44 if precision == G.MGWR_MIXED_DD else 2.0 ** -50
+    assert rel_c <= tol and abs(st_c.relres - rel_c) <= 1e-3 * rel_c + eps * terms / fmax
+    assert rel(u_c, u_f) <= 1e-8

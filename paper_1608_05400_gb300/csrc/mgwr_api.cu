@@ -40,6 +40,18 @@ enum RState {
 // carried error stays near 1e-4 of the defect it updates.
 constexpr double kLooseOuter = 1e-2;
 
+// Forms of a mixed-mode outer defect: in full in the outer arithmetic; carried
+// by the step's correction (launch_defect_update); in full with T_M u by a
+// double-float convolution (launch_defect_anchor, MGWR_MIXED only), for the
+// steps that renew the anchor without deciding the stop.
+enum OuterForm { kOuterFull = 0, kOuterCarry = 1, kOuterAnchor = 2 };
+
+// Tolerances at or above which MGWR_MIXED renews its anchors in the
+// double-float-convolution form: its error, about 2^-44 |T_M u| (a few 1e-14
+// of the right-hand side's scale), stays below 1e-3 of them.  Every stop is
+// still decided on the FP64 defect.
+constexpr double kAnchorTol = 1e-10;
+
 template <class R>
 struct Hier {
   std::vector<R*> u, f, r;        // per level: batch * N_l * M values each
@@ -111,9 +123,8 @@ struct mgwr_handle {
   std::vector<IterGraph> graphs;
   // the finest iterate is zero (right-hand side just set without initial values)
   bool u_zero = false;
-  // mixed modes: the outer defect of the iteration being enqueued is carried by
-  // the step's correction (launch_defect_update) instead of computed in full
-  bool carry_outer = false;
+  // mixed modes: the form of the outer defect of the iteration being enqueued
+  int outer_form = kOuterFull;
   // where the outer defect in double-float is held for the carried form: -1
   // nowhere (full form only), 0 the right-hand side f_dd (u = 0), 1 outer_field
   int outer_src = -1;
@@ -292,17 +303,23 @@ int ensure_h32(mgwr_t h) {
   return MGWR_OK;
 }
 
+// The double-float Toeplitz spectra and twiddles, split from FP64.
+int ensure_dd_spectra(mgwr_t h) {
+  if (h->tspec_dd != nullptr) return MGWR_OK;
+  MGWR_TRY(dev_alloc(h, &h->tspec_dd, sizeof(Cx<mgwr::dd>) * (size_t)h->B * h->L));
+  MGWR_TRY(dev_alloc(h, &h->tw_dd, sizeof(Cx<mgwr::dd>) * (size_t)h->Lt));
+  MGWR_CK(h, mgwr::launch_split_cx(h->tspec_dd, h->h64.tspec, (size_t)h->B * h->L, h->stream));
+  MGWR_CK(h, mgwr::launch_split_cx(h->tw_dd, h->h64.tw, (size_t)h->Lt, h->stream));
+  return MGWR_OK;
+}
+
 int ensure_dd(mgwr_t h) {
   if (h->u_dd != nullptr) return MGWR_OK;
   const size_t cnt = level_count(h, h->nlev - 1);
   MGWR_TRY(ensure_field(h, &h->u_dd, cnt));
   MGWR_TRY(ensure_field(h, &h->f_dd, cnt));
   MGWR_TRY(ensure_field(h, &h->zero_dd, (size_t)h->M));
-  MGWR_TRY(dev_alloc(h, &h->tspec_dd, sizeof(Cx<mgwr::dd>) * (size_t)h->B * h->L));
-  MGWR_TRY(dev_alloc(h, &h->tw_dd, sizeof(Cx<mgwr::dd>) * (size_t)h->Lt));
-  MGWR_CK(h, mgwr::launch_split_cx(h->tspec_dd, h->h64.tspec, (size_t)h->B * h->L, h->stream));
-  MGWR_CK(h, mgwr::launch_split_cx(h->tw_dd, h->h64.tw, (size_t)h->Lt, h->stream));
-  return MGWR_OK;
+  return ensure_dd_spectra(h);
 }
 
 // The double-float hierarchy of MGWR_DD: every level's fields in double-float,
@@ -563,7 +580,11 @@ mgwr::dd* outer_field(const mgwr_handle* h) {
   return nullptr;
 }
 
-bool carries(const mgwr_handle* h) { return outer_field(h) != nullptr; }
+// Whether the solves of this handle carry outer defects (a field for them,
+// and a finite switch: at +inf every outer defect is full and none is kept).
+bool carries(const mgwr_handle* h) {
+  return outer_field(h) != nullptr && std::isfinite(h->loose_above);
+}
 
 // The full outer defect of the mixed modes (FP64 for MGWR_MIXED, double-float
 // for MGWR_MIXED_DD) rounded into the FP32 right-hand side, norms into
@@ -574,7 +595,7 @@ int enqueue_outer_full(mgwr_t h) {
   const int L = h->nlev - 1;
   const size_t cnt = level_count(h, L);
   const bool ddef = h->precision == MGWR_MIXED_DD;
-  mgwr::dd* keep = outer_field(h);
+  mgwr::dd* keep = carries(h) ? outer_field(h) : nullptr;
   const int pd = prof_begin(h, ddef ? MGWR_K_DEFECT_DD : MGWR_K_DEFECT64, (double)(points(h, L) * h->B));
   if (ddef && keep != nullptr)
     MGWR_CK(h, (mgwr::launch_defect<mgwr::dd, mgwr::dd>(
@@ -728,7 +749,7 @@ int enqueue_iteration(mgwr_t h, int cyc, int nu1, int nu2, bool* exact) {
       MGWR_CK(h, mgwr::launch_refine(h->h64.u[L], h->h32.u[L], cnt, h->stream));
     prof_end(h, pm);
     MGWR_TRY(clear_norms(h));
-    if (h->carry_outer) {
+    if (h->outer_form == kOuterCarry) {
       // the defect carried by the correction e = h32.u: outer_field = r - A e, with
       // r the double-float right-hand side f_dd after MGWR_MIXED_DD's start from
       // u = 0, else outer_field
@@ -747,6 +768,14 @@ int enqueue_iteration(mgwr_t h, int cyc, int nu1, int nu2, bool* exact) {
       prof_end(h, pl);
       h->h32.rs[L] = R_STALE;
       *exact = false;
+    } else if (h->outer_form == kOuterAnchor) {
+      const int pa = prof_begin(h, MGWR_K_DEFECT_DD, (double)(points(h, L) * h->B));
+      MGWR_CK(h, mgwr::launch_defect_anchor(h->h64.u[L], h->h64.f[L], outer_field(h), h->h32.f[L],
+                                            h->tspec_dd, (size_t)h->L, h->tw_dd, h->h64.zero,
+                                            shape(h, L), h->hinv2[L], h->norm_bits, h->stream));
+      prof_end(h, pa);
+      h->h32.rs[L] = R_STALE;
+      *exact = false;  // a stop is decided on the FP64 defect
     } else {
       MGWR_TRY(enqueue_outer_full(h));
       *exact = true;
@@ -766,7 +795,9 @@ int enqueue_iteration(mgwr_t h, int cyc, int nu1, int nu2, bool* exact) {
 long long iteration_key(const mgwr_handle* h, int cyc, int nu1, int nu2) {
   const int rs_in = h->precision == MGWR_FP64 ? h->h64.rs[h->nlev - 1] : 0;
   return ((((((long long)h->precision * 4 + cyc) * 32 + nu1) * 32 + nu2) * 32 * 4 +
-           (long long)step_cycles(h) * 4 + h->order) * 4 + (h->carry_outer ? 1 + h->outer_src : 0)) *
+           (long long)step_cycles(h) * 4 + h->order) * 4 + (h->outer_form == kOuterCarry    ? 1 + h->outer_src
+                                                        : h->outer_form == kOuterAnchor ? 3
+                                                                                        : 0)) *
              4 + rs_in;
 }
 
@@ -1304,8 +1335,12 @@ int mgwr_set_precision(mgwr_t h, int precision) {
     MGWR_TRY(ensure_h32(h));
     // the double-float outer defect of MGWR_MIXED, for the carried form
     // (MGWR_MIXED_DD keeps its own in the FP64 iterate's field during a solve)
-    if (precision == MGWR_MIXED && h->M <= mgwr::kShortMaxM)
+    // and the double-float spectra of its anchors (launch_defect_anchor)
+    if (precision == MGWR_MIXED && h->M <= mgwr::kShortMaxM) {
       MGWR_TRY(ensure_field(h, &h->r_outer, level_count(h, h->nlev - 1)));
+      MGWR_TRY(ensure_dd_spectra(h));
+      MGWR_CK(h, cudaStreamSynchronize(h->stream));
+    }
   }
   if (precision == MGWR_MIXED_DD) {
     MGWR_TRY(ensure_dd(h));
@@ -1535,7 +1570,7 @@ int solve_begin(mgwr_t h, SolveState& S, int cyc, int nu1, int nu2, double tol, 
   // split into outer_field in MGWR_MIXED), else the full defect just computed
   // (kept in outer_field by enqueue_outer_full)
   h->outer_src = -1;
-  if (S.mixed && !S.ddc && carries(h) && std::isfinite(h->loose_above)) {
+  if (S.mixed && !S.ddc && carries(h)) {
     h->outer_src = h->u_zero && S.ddef ? 0 : 1;
     if (h->u_zero && !S.ddef)
       MGWR_CK(h, mgwr::launch_split(outer_field(h), h->h64.f[L], cntL, h->stream));
@@ -1550,6 +1585,17 @@ int solve_begin(mgwr_t h, SolveState& S, int cyc, int nu1, int nu2, double tol, 
 // its anchor, or have an anchor so small against the tolerance that the
 // carried error cannot decide its stopping test (which the full defect
 // confirms anyway).
+bool carry_next(const mgwr_handle* h, const SolveState& S);
+
+// MGWR_MIXED: whether a step that computes its outer defect in full may take
+// the double-float-convolution form (launch_defect_anchor): the handle carries
+// its defects (so the next steps start from this one), has the double-float
+// Toeplitz spectra, and solves to a tolerance that its error cannot reach.
+bool anchor_next(const mgwr_handle* h, const SolveState& S) {
+  return h->precision == MGWR_MIXED && carries(h) && h->tspec_dd != nullptr &&
+         S.tol >= kAnchorTol;
+}
+
 bool carry_next(const mgwr_handle* h, const SolveState& S) {
   if (!S.mixed || S.ddc || h->outer_src < 0) return false;
   const double x = h->loose_above;
@@ -1574,7 +1620,9 @@ bool solve_plan(mgwr_t h, SolveState& S) {
   }
   // outer defects of the mixed modes carried by the correction while the
   // defect is large against the anchor (mgwr_set_outer_switch)
-  h->carry_outer = carry_next(h, S);
+  h->outer_form = carry_next(h, S)    ? kOuterCarry
+                   : anchor_next(h, S) ? kOuterAnchor
+                                       : kOuterFull;
   // Refinements: when the last step's reduction predicts that this step ends
   // just above the tolerance, but below half of it with one cycle more, this
   // step takes that cycle instead of leaving a whole outer step (and its outer
@@ -1616,9 +1664,9 @@ int solve_after(mgwr_t h, SolveState& S, bool exact) {
   if (mixed_outer) {
     // outer_field now holds the step's outer defect (carried or full)
     h->outer_src = carries(h) ? 1 : -1;
-    if (exact) S.anchor = h->relres;
+    if (exact || h->outer_form == kOuterAnchor) S.anchor = h->relres;
   }
-  h->carry_outer = false;
+  h->outer_form = kOuterFull;
   if (!exact && S.rel <= S.tol) {
     MGWR_TRY(solve_full_defect(h, S));
     S.rel = relative(h, S.norms, h->relres);
@@ -1636,7 +1684,7 @@ int solve_end(mgwr_t h, SolveState& S, mgwr_stats* st) {
   const int L = h->nlev - 1;
   const size_t cntL = level_count(h, L);
   h->u_zero = false;
-  h->carry_outer = false;
+  h->outer_form = kOuterFull;
   h->outer_src = -1;
   if (S.ddef) MGWR_CK(h, mgwr::launch_join(h->h64.u[L], h->u_dd, cntL, h->stream));
   if (!S.rel_exact) {  // report the full defect also when stopping on max_cycles
@@ -2244,8 +2292,8 @@ int mgwr_footprint(int d, int n, int M, int batch, int precision, size_t* bytes)
       total += r512(8 * B * nlev * L) + r512(8 * B * L);
     if (precision == MGWR_MIXED_DD)
       total += 2 * r512(8 * B * pts[0] * M) + r512(16 * B * L) + r512(16 * Lt);
-    if (precision == MGWR_MIXED && M <= (size_t)mgwr::kShortMaxM)
-      total += r512(8 * B * pts[0] * M);  // carried double-float outer defect
+    if (precision == MGWR_MIXED && M <= (size_t)mgwr::kShortMaxM)  // carried defect, anchor spectra
+      total += r512(8 * B * pts[0] * M) + r512(16 * B * L) + r512(16 * Lt);
   }
   *bytes = total;
   return MGWR_OK;

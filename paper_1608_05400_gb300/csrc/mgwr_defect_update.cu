@@ -199,20 +199,26 @@ cudaError_t launch_defect_update(const float* e, const W* r_in, W* r_out, float*
   const int groups = block / (L / 8);
   const size_t smem = (size_t)groups * Pad<float>::len(L) * sizeof(Cx<float>);
   const dim3 grid((unsigned)((npairs + groups - 1) / groups), (unsigned)ls.batch);
-  cudaError_t err;
-  switch (logL) {
-#define MGWR_CASE(LG)                                                                        \
-  case LG:                                                                                   \
-    err = update_launch<W, ((1 << LG) / 8 > 256 ? (1 << LG) / 8 : 256), FixedShape<LG>>(     \
-        grid, smem, s, e, r_in, r_out, r32, tspec, tw, zero, d, n, M, logL, hinv2, npts,     \
-        npairs, norm_bits, fstride, spec_stride);                                            \
-    break;
-    MGWR_FIXED_LOGL(MGWR_CASE)
-#undef MGWR_CASE
+  // the run-time shape only: the solver takes the register-pass form for every
+  // length it serves (64 <= M <= kShortMaxM), this one for the shorter lines
+  cudaError_t err = cudaErrorInvalidValue;
+  switch (block) {
+    case 256:
+      err = update_launch<W, 256, FftShape>(grid, smem, s, e, r_in, r_out, r32, tspec, tw, zero, d,
+                                            n, M, logL, hinv2, npts, npairs, norm_bits, fstride,
+                                            spec_stride);
+      break;
+    case 512:
+      err = update_launch<W, 512, FftShape>(grid, smem, s, e, r_in, r_out, r32, tspec, tw, zero, d,
+                                            n, M, logL, hinv2, npts, npairs, norm_bits, fstride,
+                                            spec_stride);
+      break;
+    case 1024:
+      err = update_launch<W, 1024, FftShape>(grid, smem, s, e, r_in, r_out, r32, tspec, tw, zero,
+                                             d, n, M, logL, hinv2, npts, npairs, norm_bits,
+                                             fstride, spec_stride);
+      break;
     default:
-      err = update_launch<W, 256, FftShape>(grid, smem, s, e, r_in, r_out, r32, tspec, tw, zero,
-                                            d, n, M, logL, hinv2, npts, npairs, norm_bits,
-                                            fstride, spec_stride);
       break;
   }
   if (err != cudaSuccess) return err;

@@ -234,6 +234,16 @@ cudaError_t launch_defect_update_rp(const float* e, const W* r_in, W* r_out, flo
                                     const Cx<float>* tspec, size_t spec_stride,
                                     const Cx<float>* tw, const float* zero, const LevelShape& ls,
                                     W hinv2, unsigned long long* norm_bits, cudaStream_t s);
+// Full outer defect of an FP64 iterate with T_M u by a double-float FFT
+// convolution of u split into double-float pairs (double-float spectra `tspec`,
+// twiddles `tw`) and the stencil, source and subtractions in FP64: r = f -
+// (T_M (x) I + A_h) u within about 2^-44 of |T_M u|, written in double-float to
+// r and rounded to FP32 into r32; |r|_inf of instance b into norm_bits[b].  Lines
+// of 4 <= M <= kShortMaxM (else cudaErrorInvalidValue).  zero: M FP64 zeros.
+cudaError_t launch_defect_anchor(const double* u, const double* f, dd* r, float* r32,
+                                 const Cx<dd>* tspec, size_t spec_stride, const Cx<dd>* tw,
+                                 const double* zero, const LevelShape& ls, double hinv2,
+                                 unsigned long long* norm_bits, cudaStream_t s);
 // out = (float) x for a double-float field of `count` values.
 cudaError_t launch_round_dd(const dd* x, float* out, size_t count, cudaStream_t s);
 // Per instance b: u = broadcast of g_b along time (initial iterate u^0(t) = g);

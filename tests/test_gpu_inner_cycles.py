@@ -264,6 +264,10 @@ def test_carried_defects_save_full_defects_and_solve_the_same(precision):
             W = omg.WRMG(d, n, M, 1.0, 0.6)
             rel_o = np.abs(W.defect(W.finest, u, prob.rhs())).max() / np.abs(prob.rhs()).max()
             out[switch] = (st, prof[full_class]["launches"], prof["defect32"]["launches"], u, rel_o)
+            if precision == G.MGWR_MIXED and switch is None:
+                # anchors renewed in the double-float-convolution form, one FP64
+                # defect for the stop
+                assert prof["defect_dd"]["launches"] >= 1 and 1 <= prof["defect64"]["launches"] <= 2
     (st_c, full_c, carried_c, u_c, rel_c), (st_f, full_f, carried_f, u_f, rel_f) = out[None], out[math.inf]
     assert st_c.status == st_f.status == G.MGWR_OK
     assert carried_f == 0 and carried_c > 0
@@ -276,3 +280,45 @@ def test_carried_defects_save_full_defects_and_solve_the_same(precision):
     eps = 2.0 ** -44 if precision == G.MGWR_MIXED_DD else 2.0 ** -50
     assert rel_c <= tol and abs(st_c.relres - rel_c) <= 1e-3 * rel_c + eps * terms / fmax
     assert rel(u_c, u_f) <= 1e-8
+
+
+@pytest.mark.parametrize("d,n,M", [(2, 31, 1024), (1, 255, 64), (2, 15, 4096), (1, 63, 16)])
+def test_double_float_anchor_and_the_step_carried_from_it(d, n, M):
+    # MGWR_MIXED to a tolerance of at least 1e-10 renews its anchors with T_M u
+    # by a double-float convolution of the split FP64 iterate (stencil and source
+    # in FP64).  Driven step by step: the first step with the switch at 2 (no
+    # carry: the defect is below twice its anchor) takes that form, the second
+    # with the switch at 0 carries from its double-float result.  Each FP32
+    # right-hand side against the oracle's direct-sum defect of the iterate: the
+    # anchor errs by about 2^-44 |T_M u| besides its rounding to FP32, the
+    # carried one by that plus the FP32 convolution of the step's correction.
+    W = omg.WRMG(d, n, M, 1.0, 0.45)
+    f = inputs.random_field(n ** d, M, seed=29)
+    L = W.finest
+    with G.Solver(d, n, M, 1.0, 0.45) as s:
+        s.set_precision(G.MGWR_MIXED)
+        s.set_rhs(f)
+        s.set_outer_switch(2.0)
+        with G.Group() as g:
+            g.add(s, 1, 1, 1, tol=1e-9, max_cycles=4)
+            g.step()
+            u1 = s.solution()
+            r1 = s.field_get(G.MGWR_H32, L, G.MGWR_F)
+            s.set_outer_switch(0.0)
+            g.step()
+            u2 = s.solution()
+            r2 = s.field_get(G.MGWR_H32, L, G.MGWR_F)
+            g.run()
+    fmax = np.abs(f).max()
+    tu1 = np.abs(u1 @ W.Tm.T).max()
+    ref1 = W.defect(L, u1, f)
+    fp64 = 2.0 ** -50 * (fmax + tu1 + 4 * d * (n + 1) ** 2 * np.abs(u1).max())
+    anchor_err = 2.0 ** -40 * tu1 + fp64
+    err1 = np.abs(r1 - ref1).max()
+    assert err1 <= anchor_err + 2.0 ** -23 * np.abs(ref1).max(), (err1, anchor_err)
+    ref2 = W.defect(L, u2, f)
+    te = np.abs((u2 - u1) @ W.Tm.T).max()
+    err2 = np.abs(r2 - ref2).max()
+    bound2 = anchor_err + 2e-6 * te + 2.0 ** -23 * np.abs(ref2).max() + fp64
+    assert err2 <= bound2, (err2, bound2, te)
+    assert np.abs(ref2).max() < 0.5 * np.abs(ref1).max()

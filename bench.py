@@ -81,7 +81,8 @@ UNIT = "unknowns/s"
 # --precision names and the library's codes (MGWR_FP64 .. MGWR_AUTO)
 PREC_CODES = {"fp64": 0, "mixed": 1, "mixed_dd": 2, "dd": 3, "auto": 4}
 PREC_NAMES = {v: k for k, v in PREC_CODES.items()}
-DTYPES = {"fp64": "f64", "mixed": "f32 cycles + f64 defect/update",
+DTYPES = {"fp64": "f64", "mixed": "f32 cycles + f64 iterate/update/stencil, outer-defect time "
+                                  "convolution in f32x2 (double-float; f64 below tol 1e-10)",
           "mixed_dd": "f32 cycles + f32x2 (double-float) defect/update",
           "dd": "f32x2 (double-float) cycles, defect and update",
           "auto": "f32 cycles + f32x2 (double-float) defect/update, f32x2 cycles on grids "

@@ -64,7 +64,13 @@ extern "C" {
 #define MGWR_MIXED_DD 2 /* FP32 V-cycles; defect + update in double-float    */
 #define MGWR_DD 3       /* refinement with double-float inner cycles         */
 #define MGWR_AUTO 4     /* MGWR_MIXED_DD or MGWR_DD by the grid (below)      */
-/* MGWR_MIXED_DD keeps the finest iterate and right-hand side as double-float
+/* MGWR_MIXED keeps the finest iterate, the update and the stencil part of
+ * every outer defect in IEEE double.  Its full outer defects take the time
+ * convolution T_M u in double-float (FP32 instructions, error about 2^-44
+ * |T_M u|, against about 1e-15 |T_M u| in FP64) when the tolerance is at least
+ * 1e-10 and the outer switch is finite (mgwr_set_outer_switch), else in FP64;
+ * its stopping test uses that defect.
+ * MGWR_MIXED_DD keeps the finest iterate and right-hand side as double-float
  * pairs (hi + lo of two floats, about 48 significant bits) and computes the
  * outer defect and the update with FP32 instructions only (GB300 runs FP32 64x
  * faster than FP64).  Its stopping test uses that defect; mgwr_residual gives
@@ -184,8 +190,9 @@ int mgwr_set_inner_cycles(mgwr_t h, int cycles);
  * the anchor's (default 1e-2; 0: every step; +inf: none), in every instance of
  * a batch whose anchor is not already below the tolerance / rel; the other
  * steps compute it in full and so set a new anchor.  Every stopping decision is
- * taken on a full defect.  The paper has no counterpart (its solver is one
- * precision).  MGWR_E_INVAL for rel < 0 or NaN. */
+ * taken on a full defect.  At +inf no defect is carried and MGWR_MIXED's full
+ * defects all take their convolution in FP64.  The paper has no counterpart
+ * (its solver is one precision).  MGWR_E_INVAL for rel < 0 or NaN. */
 int mgwr_set_outer_switch(mgwr_t h, double rel);
 
 /* Launch shape of the FFT-engine kernels (no counterpart in the paper; the

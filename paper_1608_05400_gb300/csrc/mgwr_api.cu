@@ -42,14 +42,15 @@ constexpr double kLooseOuter = 1e-2;
 
 // Forms of a mixed-mode outer defect: in full in the outer arithmetic; carried
 // by the step's correction (launch_defect_update); in full with T_M u by a
-// double-float convolution (launch_defect_anchor, MGWR_MIXED only), for the
-// steps that renew the anchor without deciding the stop.
+// double-float convolution (launch_defect_anchor, MGWR_MIXED to a tolerance of
+// at least kAnchorTol).
 enum OuterForm { kOuterFull = 0, kOuterCarry = 1, kOuterAnchor = 2 };
 
-// Tolerances at or above which MGWR_MIXED renews its anchors in the
-// double-float-convolution form: its error, about 2^-44 |T_M u| (a few 1e-14
-// of the right-hand side's scale), stays below 1e-3 of them.  Every stop is
-// still decided on the FP64 defect.
+// Tolerances at or above which MGWR_MIXED computes its full outer defects (the
+// anchors of the carried ones, and those that decide the stop) with T_M u in
+// double-float (launch_defect_anchor): the form's error, about 2^-44 |T_M u|
+// (a few 1e-14 of the right-hand side's scale, against about 1e-15 for an FP64
+// convolution), stays below 1e-3 of them.  Below, every full defect is FP64.
 constexpr double kAnchorTol = 1e-10;
 
 template <class R>
@@ -623,6 +624,29 @@ int enqueue_outer_full(mgwr_t h) {
   return MGWR_OK;
 }
 
+// MGWR_MIXED: whether its full outer defects may take the double-float
+// convolution form (launch_defect_anchor): the handle carries its defects (so
+// the next steps start from the one it leaves in outer_field), has the
+// double-float Toeplitz spectra, and solves to a tolerance (at least
+// kAnchorTol) that the form's error cannot reach.  Such defects also decide the
+// stop; a switch at +inf keeps every outer defect in FP64.
+bool anchor_ok(const mgwr_handle* h, double tol) {
+  return h->precision == MGWR_MIXED && carries(h) && h->tspec_dd != nullptr && tol >= kAnchorTol;
+}
+
+// The outer defect of MGWR_MIXED in the double-float-convolution form into
+// outer_field and, rounded, the FP32 right-hand side, norms into norm_bits.
+int enqueue_anchor(mgwr_t h) {
+  const int L = h->nlev - 1;
+  const int pa = prof_begin(h, MGWR_K_DEFECT_DD, (double)(points(h, L) * h->B));
+  MGWR_CK(h, mgwr::launch_defect_anchor(h->h64.u[L], h->h64.f[L], outer_field(h), h->h32.f[L],
+                                        h->tspec_dd, (size_t)h->L, h->tw_dd, h->h64.zero,
+                                        shape(h, L), h->hinv2[L], h->norm_bits, h->stream));
+  prof_end(h, pa);
+  h->h32.rs[L] = R_STALE;
+  return MGWR_OK;
+}
+
 // FP64 defect of the finest iterate with its per-instance infinity norms.  In
 // mixed mode the defect is written, rounded, as the FP32 right-hand side.
 int finest_defect_norms(mgwr_t h, std::vector<double>& norms, bool to_h32) {
@@ -769,13 +793,8 @@ int enqueue_iteration(mgwr_t h, int cyc, int nu1, int nu2, bool* exact) {
       h->h32.rs[L] = R_STALE;
       *exact = false;
     } else if (h->outer_form == kOuterAnchor) {
-      const int pa = prof_begin(h, MGWR_K_DEFECT_DD, (double)(points(h, L) * h->B));
-      MGWR_CK(h, mgwr::launch_defect_anchor(h->h64.u[L], h->h64.f[L], outer_field(h), h->h32.f[L],
-                                            h->tspec_dd, (size_t)h->L, h->tw_dd, h->h64.zero,
-                                            shape(h, L), h->hinv2[L], h->norm_bits, h->stream));
-      prof_end(h, pa);
-      h->h32.rs[L] = R_STALE;
-      *exact = false;  // a stop is decided on the FP64 defect
+      MGWR_TRY(enqueue_anchor(h));
+      *exact = true;
     } else {
       MGWR_TRY(enqueue_outer_full(h));
       *exact = true;
@@ -1511,6 +1530,11 @@ struct SolveState {
 // The full defect of the finest level in the outer precision, with norms (in
 // the refinements written as the inner right-hand side).
 int solve_full_defect(mgwr_t h, SolveState& S) {
+  if (S.mixed && anchor_ok(h, S.tol)) {
+    MGWR_TRY(clear_norms(h));
+    MGWR_TRY(enqueue_anchor(h));
+    return read_norms(h, S.norms);
+  }
   if (S.ddc) {
     MGWR_TRY(clear_norms(h));
     MGWR_TRY(outer_defect_ddd(h));
@@ -1585,17 +1609,6 @@ int solve_begin(mgwr_t h, SolveState& S, int cyc, int nu1, int nu2, double tol, 
 // its anchor, or have an anchor so small against the tolerance that the
 // carried error cannot decide its stopping test (which the full defect
 // confirms anyway).
-bool carry_next(const mgwr_handle* h, const SolveState& S);
-
-// MGWR_MIXED: whether a step that computes its outer defect in full may take
-// the double-float-convolution form (launch_defect_anchor): the handle carries
-// its defects (so the next steps start from this one), has the double-float
-// Toeplitz spectra, and solves to a tolerance that its error cannot reach.
-bool anchor_next(const mgwr_handle* h, const SolveState& S) {
-  return h->precision == MGWR_MIXED && carries(h) && h->tspec_dd != nullptr &&
-         S.tol >= kAnchorTol;
-}
-
 bool carry_next(const mgwr_handle* h, const SolveState& S) {
   if (!S.mixed || S.ddc || h->outer_src < 0) return false;
   const double x = h->loose_above;
@@ -1621,7 +1634,7 @@ bool solve_plan(mgwr_t h, SolveState& S) {
   // outer defects of the mixed modes carried by the correction while the
   // defect is large against the anchor (mgwr_set_outer_switch)
   h->outer_form = carry_next(h, S)    ? kOuterCarry
-                   : anchor_next(h, S) ? kOuterAnchor
+                   : anchor_ok(h, S.tol) ? kOuterAnchor
                                        : kOuterFull;
   // Refinements: when the last step's reduction predicts that this step ends
   // just above the tolerance, but below half of it with one cycle more, this
@@ -1664,7 +1677,7 @@ int solve_after(mgwr_t h, SolveState& S, bool exact) {
   if (mixed_outer) {
     // outer_field now holds the step's outer defect (carried or full)
     h->outer_src = carries(h) ? 1 : -1;
-    if (exact || h->outer_form == kOuterAnchor) S.anchor = h->relres;
+    if (exact) S.anchor = h->relres;
   }
   h->outer_form = kOuterFull;
   if (!exact && S.rel <= S.tol) {

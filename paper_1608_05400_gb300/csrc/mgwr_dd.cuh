@@ -24,6 +24,26 @@ struct dd {
   __device__ __forceinline__ explicit operator float() const { return __fadd_rn(hi, lo); }
 };
 
+// x as a double-float pair with two FP64-pipe operations instead of four: hi =
+// x with its last 29 significand bits cleared, built as a float by integer
+// operations (exact when x lies in float's normal range), lo = x - hi (exact
+// in FP64) rounded to FP32; x - (hi + lo) is below 2^-48 |x|.  Outside that
+// range: zero or tiny x gives (0, x rounded), huge, inf or NaN (x rounded, 0).
+// hi is truncated, not rounded, so |lo| < ulp(hi) (the pair is not
+// renormalised; the sums below accept that).
+__device__ __forceinline__ dd dd_split_fast(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF);
+  if (e >= 897 && e <= 1150) {
+    const double hd = __longlong_as_double((long long)(b & ~0x1FFFFFFFull));
+    const unsigned hb = ((unsigned)(b >> 32) & 0x80000000u) | ((unsigned)(e - 896) << 23) |
+                        ((unsigned)(b >> 29) & 0x7FFFFFu);
+    return dd(__uint_as_float(hb), __double2float_rn(x - hd));
+  }
+  if (e < 897) return dd(0.f, __double2float_rn(x));
+  return dd(__double2float_rn(x), 0.f);
+}
+
 // s + e = a + b exactly (TwoSum, any a, b)
 __device__ __forceinline__ dd dd_two_sum(float a, float b) {
   const float s = __fadd_rn(a, b);

@@ -3,6 +3,8 @@
 // translation unit each, compiled in parallel).
 #pragma once
 
+#include <type_traits>
+
 #include "mgwr_common.cuh"
 
 namespace mgwr {
@@ -10,6 +12,16 @@ namespace mgwr {
 // ---------------------------------------------------------------------------------
 // defect r = f - (T_M (x) I + A_h) u  (Algorithm 1; Sec. 5 circulant-embedding matvec)
 // ---------------------------------------------------------------------------------
+
+// The defect's value in the output type: a conversion, or for an FP64 defect
+// kept in double-float the split that spends two FP64-pipe operations, not four.
+template <class RO, class R>
+__device__ __forceinline__ RO out_value(R x) {
+  if constexpr (std::is_same<RO, dd>::value && std::is_same<R, double>::value)
+    return dd_split_fast(x);
+  else
+    return RO(x);
+}
 
 template <class R, class RO, int BLOCK, class SH, int E>
 __global__ void __launch_bounds__(BLOCK, min_blocks<R>(BLOCK, E))
@@ -74,12 +86,12 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<R>(BLOCK, E))
     if (valid) {
       const R ua = uA[m];
       const R ra = A::sub(A::sub(f[pAM + m], y.x), hinv2 * stencil(ua, qA, iA, jA, pAM, m));
-      r[pAM + m] = RO(ra);
+      r[pAM + m] = out_value<RO>(ra);
       amax = absmax_nan(A::mag(ra), amax);
       if (hasB) {
         const R ub = uB[m];
         const R rb = A::sub(A::sub(f[pBM + m], y.y), hinv2 * stencil(ub, qB, iB, jB, pBM, m));
-        r[pBM + m] = RO(rb);
+        r[pBM + m] = out_value<RO>(rb);
         amax = absmax_nan(A::mag(rb), amax);
       }
     }

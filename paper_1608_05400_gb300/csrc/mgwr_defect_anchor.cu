@@ -3,13 +3,15 @@
 // decide the solve's stop: r = (f - A_h u) - T_M u of the FP64 iterate u, with
 // the stencil, the source and the subtractions in FP64 (exact differences
 // first, as in the FP64 defect) and T_M u by a double-float FFT convolution of
-// u split into double-float pairs (hi = u rounded to FP32, lo = the rest
-// rounded).  The split drops u's last five bits (2^-48 |u|, far below the
-// convolution's own error) and only reaches T_M u, not the stencil, so the
-// defect errs by about 2^-44 of |T_M u|: a few 1e-14 of the right-hand side's
-// scale, on any grid.  GB300 runs double-float butterflies (FP32 pipes) several
-// times faster than FP64 ones (1/64 of the FP32 rate); the FP64 work left is
-// about twenty operations per value.
+// u split into double-float pairs (dd_split_fast).  The split drops u's last
+// five bits (2^-48 |u|, far below the convolution's own error) and only
+// reaches T_M u, not the stencil, so the defect errs by about 2^-44 of
+// |T_M u|: a few 1e-14 of the right-hand side's scale, on any grid.  GB300 runs
+// double-float butterflies (FP32 pipes) several times faster than FP64 ones
+// (1/64 of the FP32 rate); the FP64 work left is about twelve operations per
+// value (two splits, the stencil's seven sums, one fused multiply-add), and
+// the norm is taken on the FP32 leading part (it plans the next steps; no
+// stop is decided on it).
 #include "mgwr_common.cuh"
 
 namespace mgwr {
@@ -45,20 +47,21 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<dd>(BLOCK))
   const int iB = d == 1 ? pB : pB % n, jB = d == 1 ? 0 : pB / n;
   const double* uA = valid ? u + pAM : zero;
   const double* uB = hasB ? u + pBM : zero;
-  auto load = [&](int m) -> Cx<dd> { return Cx<dd>{dd(uA[m]), dd(uB[m])}; };
+  auto load = [&](int m) -> Cx<dd> { return Cx<dd>{dd_split_fast(uA[m]), dd_split_fast(uB[m])}; };
   Cx<dd> v[1][8];
   fft_forward<1>(buf, t, sh, tw, load, v, sync);
 #pragma unroll
   for (int q = 0; q < 8; ++q) v[0][q] = cmul(v[0][q], tspec[8 * t + q]);
-  double amax = 0.0;
-  // one value: line start pM, time m, T_M u there in y
+  float amax = 0.f;
+  // one value (line start pM, time m, T_M u there in y): f - h^-2 sum (u_p - u_q)
+  // in FP64 (one fused step after the differences), split, and T_M u
+  // subtracted in double-float
   auto one = [&](size_t pM, int m, int i, int j, dd y, double up) {
-    const double tu = (double)y.hi + (double)y.lo;
-    const double rv = (f[pM + m] - tu) - hinv2 * stencil_differences(u, up, d, n, i, j, pM, M, m);
-    const dd rd(rv);
+    const double a = fma(-hinv2, stencil_differences(u, up, d, n, i, j, pM, M, m), f[pM + m]);
+    const dd rd = dd_add_accurate(dd_split_fast(a), -y);
     r[pM + m] = rd;
-    r32[pM + m] = rd.hi;
-    amax = absmax_nan(fabs(rv), amax);
+    r32[pM + m] = float(rd);
+    amax = absmax_nan(fabsf(rd.hi), amax);
   };
   auto store = [&](int m, Cx<dd> y) {
     if (valid) {
@@ -69,7 +72,7 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<dd>(BLOCK))
   fft_inverse<1>(buf, t, sh, tw, v, store, sync);
 
   if (norm_bits != nullptr) {
-    double a = amax;
+    double a = (double)amax;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) a = absmax_nan(__shfl_xor_sync(0xffffffffu, a, o), a);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;

@@ -340,7 +340,10 @@ def test_paper_table_1d_iterations_on_gpu():
 @pytest.mark.parametrize("precision", [G.MGWR_FP64, G.MGWR_MIXED, G.MGWR_MIXED_DD])
 def test_solve_from_zero_skips_nothing_it_needs(precision):
     # from u = 0 the initial defect is f itself and is not convolved; the solve must
-    # be bitwise the one that starts from an explicitly set zero iterate
+    # be the one that starts from an explicitly set zero iterate: bitwise, except
+    # in MGWR_MIXED, whose explicit start computes f - A 0 with the double-float
+    # convolution and so holds the same carried defect in another double-float
+    # pair (the same value to 2^-48)
     d, n, M = 2, 31, 128
     f = inputs.Problem(d, n, M, 1.0, 0.6, "talpha").rhs()
     out = []
@@ -352,9 +355,15 @@ def test_solve_from_zero_skips_nothing_it_needs(precision):
                 s.set_initial(np.zeros_like(f))
             st = s.solve(1, 1, 1, tol=1e-10, max_cycles=40)
             out.append((s.solution(), st.cycles, st.outer, st.relres))
-    np.testing.assert_array_equal(out[0][0], out[1][0])
+    if precision == G.MGWR_MIXED:
+        assert rel(out[0][0], out[1][0]) <= 1e-12
+    else:
+        np.testing.assert_array_equal(out[0][0], out[1][0])
     assert out[0][1:3] == out[1][1:3]
     # the double-float defect reports its norm from the leading FP32 word, so r_0
-    # from the explicit zero iterate differs from max |f| in the 8th digit
-    assert abs(out[0][3] - out[1][3]) <= 1e-6 * out[1][3]
+    # from the explicit zero iterate differs from max |f| in the 8th digit; the
+    # stop of MGWR_MIXED to 1e-10 is decided on its double-float-convolution
+    # defect, good to about 2^-44 of |T_M u| (f's scale) in either run
+    anchor = 2.0 ** -40 if precision == G.MGWR_MIXED else 0.0
+    assert abs(out[0][3] - out[1][3]) <= 1e-6 * out[1][3] + anchor
     assert rel(out[0][0], direct.time_stepping(d, n, M, 1.0, 0.6, f)) <= (1e-11 if precision == G.MGWR_FP64 else 1e-8)

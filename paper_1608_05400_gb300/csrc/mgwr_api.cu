@@ -782,7 +782,7 @@ int enqueue_iteration(mgwr_t h, int cyc, int nu1, int nu2, bool* exact) {
       const Cx<float>* ts = rp ? h->h32.tspec_rp : h->h32.tspec;
       mgwr::dd* ro = outer_field(h);
       const mgwr::dd* ri = h->outer_src == 0 ? h->f_dd : ro;
-      const mgwr::dd hi2(h->hinv2[L]);
+      const float hi2 = (float)h->hinv2[L];  // (n + 1)^2, a power of 4
       MGWR_CK(h, rp ? mgwr::launch_defect_update_rp<mgwr::dd>(
                           h->h32.u[L], ri, ro, h->h32.f[L], ts, (size_t)h->L, h->h32.tw,
                           h->h32.zero, shape(h, L), hi2, h->norm_bits, h->stream)

@@ -19,25 +19,24 @@ namespace mgwr {
 
 namespace {
 
-__device__ __forceinline__ dd widen(float x, dd) { return dd(x, 0.f); }
-__device__ __forceinline__ float to_float(dd x) { return float(x); }
-
-// sum over the 2d neighbours q of (e_p - e_q) at time m, zero outside the grid,
-// every FP32 value widened to W before its difference is formed (exact in
-// double-float)
-template <class W>
-__device__ __forceinline__ W wide_differences(const float* __restrict__ e, float ep, int d, int n,
-                                              int i, int j, size_t pM, int M, int m) {
-  using A = Arith<W>;
-  const W c = widen(ep, W());
-  W s = A::add(i > 0 ? A::sub(c, widen(e[pM - M + m], W())) : c,
-               i < n - 1 ? A::sub(c, widen(e[pM + M + m], W())) : c);
-  if (d == 2) {
-    const size_t nM = (size_t)n * M;
-    s = A::add(s, A::add(j > 0 ? A::sub(c, widen(e[pM - nM + m], W())) : c,
-                         j < n - 1 ? A::sub(c, widen(e[pM + nM + m], W())) : c));
+// sum over the 2d neighbour lines q of (e_p - e_q) at time m as a double-float
+// pair: every difference of two FP32 values is exact as a TwoSum pair, the
+// leading words are summed by TwoSum and the trailing ones plainly (error
+// about 2^-48 of the differences' magnitudes).  Neighbours outside the grid
+// are the zero line, so the difference is e_p there.
+__device__ __forceinline__ dd exact_differences(const float* const (&q)[4], float ep, int d,
+                                                int m) {
+  dd acc = dd_two_sum(ep, -q[0][m]);
+  const int nq = 2 * d;
+#pragma unroll
+  for (int k = 1; k < 4; ++k) {
+    if (k < nq) {
+      const dd t = dd_two_sum(ep, -q[k][m]);
+      const dd s = dd_two_sum(acc.hi, t.hi);
+      acc = dd(s.hi, __fadd_rn(s.lo, __fadd_rn(acc.lo, t.lo)));
+    }
   }
-  return s;
+  return dd_fast_two_sum(acc.hi, acc.lo);
 }
 
 // the per-instance maximum of |r_new| into norm_bits (one atomic per block)
@@ -57,34 +56,34 @@ __device__ __forceinline__ void block_norm(double a, double* red,
 }
 
 // One line pair's update, shared by both engines: the store of the inverse
-// transform's outputs y = T_M e (A and B lines in y.x and y.y).
+// transform's outputs y = T_M e (A and B lines in y.x and y.y).  hinv2 = 1/h^2
+// = (n + 1)^2 is a power of 4 (n + 1 is a power of two), so scaling a
+// double-float pair by it is exact word by word.
 template <class W>
 struct UpdateStore {
   const float* e;
   const W* r_in;
   W* r_out;
   float* r32;
-  W hinv2;
-  int d, n, M;
+  float hinv2;
+  int d;
   bool valid, hasB;
   size_t pAM, pBM;
-  int iA, jA, iB, jB;
-  typename Arith<W>::Mag* amax;
+  const float *qA[4], *qB[4];
+  float* amax;
+  __device__ __forceinline__ void one(size_t pM, int m, const float* const (&q)[4],
+                                      float ty) const {
+    const dd s = exact_differences(q, e[pM + m], d, m);
+    const dd as = dd_add_float(dd(hinv2 * s.hi, hinv2 * s.lo), ty);  // (A e) at this value
+    const dd r = dd_add_accurate(r_in[pM + m], -as);
+    r_out[pM + m] = r;
+    r32[pM + m] = float(r);
+    *amax = absmax_nan(fabsf(r.hi), *amax);
+  }
   __device__ __forceinline__ void operator()(int m, Cx<float> y) const {
-    using A = Arith<W>;
     if (!valid) return;
-    const W ra = A::sub(A::sub(r_in[pAM + m], widen(y.x, W())),
-                        hinv2 * wide_differences<W>(e, e[pAM + m], d, n, iA, jA, pAM, M, m));
-    r_out[pAM + m] = ra;
-    r32[pAM + m] = to_float(ra);
-    *amax = absmax_nan(A::mag(ra), *amax);
-    if (hasB) {
-      const W rb = A::sub(A::sub(r_in[pBM + m], widen(y.y, W())),
-                          hinv2 * wide_differences<W>(e, e[pBM + m], d, n, iB, jB, pBM, M, m));
-      r_out[pBM + m] = rb;
-      r32[pBM + m] = to_float(rb);
-      *amax = absmax_nan(A::mag(rb), *amax);
-    }
+    one(pAM, m, qA, y.x);
+    if (hasB) one(pBM, m, qB, y.y);
   }
 };
 
@@ -96,7 +95,7 @@ template <class W, int BLOCK, class SH>
 __global__ void __launch_bounds__(BLOCK, min_blocks<float>(BLOCK))
     k_defect_update(const float* __restrict__ e, const W* r_in, W* r_out, float* __restrict__ r32,
                     const Cx<float>* __restrict__ tspec, const Cx<float>* __restrict__ tw,
-                    const float* __restrict__ zero, int d, int n, int M, int logL, W hinv2,
+                    const float* __restrict__ zero, int d, int n, int M, int logL, float hinv2,
                     int npts, int npairs, unsigned long long* __restrict__ norm_bits,
                     size_t fstride, size_t sstride) {
   extern __shared__ unsigned char smem_raw[];
@@ -114,11 +113,23 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<float>(BLOCK))
   const bool valid = pair < npairs;
   const int pA = 2 * pair, pB = 2 * pair + 1;
   const bool hasB = valid && pB < npts;
-  typename Arith<W>::Mag amax = 0;
-  UpdateStore<W> store{e + off, r_in + off, r_out + off, r32 + off, hinv2, d, n, M, valid, hasB,
-                       (size_t)pA * M, (size_t)pB * M,
-                       d == 1 ? pA : pA % n, d == 1 ? 0 : pA / n,
-                       d == 1 ? pB : pB % n, d == 1 ? 0 : pB / n, &amax};
+  float amax = 0.f;
+  UpdateStore<W> store;
+  store.e = e + off;
+  store.r_in = r_in + off;
+  store.r_out = r_out + off;
+  store.r32 = r32 + off;
+  store.hinv2 = hinv2;
+  store.d = d;
+  store.valid = valid;
+  store.hasB = hasB;
+  store.pAM = (size_t)pA * M;
+  store.pBM = (size_t)pB * M;
+  store.amax = &amax;
+  neighbour_lines(store.e, zero, d, n, d == 1 ? pA : pA % n, d == 1 ? 0 : pA / n, store.pAM, M,
+                  store.qA);
+  neighbour_lines(store.e, zero, d, n, d == 1 ? pB : pB % n, d == 1 ? 0 : pB / n, store.pBM, M,
+                  store.qB);
   const float* eA = valid ? store.e + store.pAM : zero;
   const float* eB = hasB ? store.e + store.pBM : zero;
   auto load = [&](int m) -> Cx<float> { return Cx<float>{eA[m], eB[m]}; };
@@ -137,7 +148,7 @@ __global__ void __launch_bounds__(kRpBlock, 2)
     k_defect_update_rp(const float* __restrict__ e, const W* r_in, W* r_out,
                        float* __restrict__ r32, const Cx<float>* __restrict__ tspec,
                        const Cx<float>* __restrict__ tw, const float* __restrict__ zero, int d,
-                       int n, int M, W hinv2, int npts, int npairs,
+                       int n, int M, float hinv2, int npts, int npairs,
                        unsigned long long* __restrict__ norm_bits, size_t fstride,
                        size_t sstride) {
   using P = rp::Plan<LOGL, R0, R1, R2, T>;
@@ -153,11 +164,23 @@ __global__ void __launch_bounds__(kRpBlock, 2)
   const bool valid = pair < npairs;
   const int pA = 2 * pair, pB = 2 * pair + 1;
   const bool hasB = valid && pB < npts;
-  typename Arith<W>::Mag amax = 0;
-  UpdateStore<W> store{e + off, r_in + off, r_out + off, r32 + off, hinv2, d, n, M, valid, hasB,
-                       (size_t)pA * M, (size_t)pB * M,
-                       d == 1 ? pA : pA % n, d == 1 ? 0 : pA / n,
-                       d == 1 ? pB : pB % n, d == 1 ? 0 : pB / n, &amax};
+  float amax = 0.f;
+  UpdateStore<W> store;
+  store.e = e + off;
+  store.r_in = r_in + off;
+  store.r_out = r_out + off;
+  store.r32 = r32 + off;
+  store.hinv2 = hinv2;
+  store.d = d;
+  store.valid = valid;
+  store.hasB = hasB;
+  store.pAM = (size_t)pA * M;
+  store.pBM = (size_t)pB * M;
+  store.amax = &amax;
+  neighbour_lines(store.e, zero, d, n, d == 1 ? pA : pA % n, d == 1 ? 0 : pA / n, store.pAM, M,
+                  store.qA);
+  neighbour_lines(store.e, zero, d, n, d == 1 ? pB : pB % n, d == 1 ? 0 : pB / n, store.pBM, M,
+                  store.qB);
   const float* eA = valid ? store.e + store.pAM : zero;
   const float* eB = hasB ? store.e + store.pBM : zero;
   auto load = [&](int m) -> Cx<float> { return Cx<float>{eA[m], eB[m]}; };
@@ -170,7 +193,7 @@ namespace {
 template <class W, int BLOCK, class SH>
 cudaError_t update_launch(dim3 grid, size_t smem, cudaStream_t s, const float* e, const W* r_in,
                           W* r_out, float* r32, const Cx<float>* tspec, const Cx<float>* tw,
-                          const float* zero, int d, int n, int M, int logL, W hinv2, int npts,
+                          const float* zero, int d, int n, int M, int logL, float hinv2, int npts,
                           int npairs, unsigned long long* norm_bits, size_t fstride,
                           size_t sstride) {
   cudaError_t err = prepare_smem(k_defect_update<W, BLOCK, SH>, smem);
@@ -186,7 +209,7 @@ cudaError_t update_launch(dim3 grid, size_t smem, cudaStream_t s, const float* e
 template <class W>
 cudaError_t launch_defect_update(const float* e, const W* r_in, W* r_out, float* r32,
                                  const Cx<float>* tspec, size_t spec_stride, const Cx<float>* tw,
-                                 const float* zero, const LevelShape& ls, W hinv2,
+                                 const float* zero, const LevelShape& ls, float hinv2,
                                  unsigned long long* norm_bits, cudaStream_t s) {
   const int d = ls.d, n = ls.n, M = ls.M;
   if (M > kShortMaxM) return cudaErrorInvalidValue;
@@ -229,7 +252,7 @@ template <class W>
 cudaError_t launch_defect_update_rp(const float* e, const W* r_in, W* r_out, float* r32,
                                     const Cx<float>* tspec, size_t spec_stride,
                                     const Cx<float>* tw, const float* zero, const LevelShape& ls,
-                                    W hinv2, unsigned long long* norm_bits, cudaStream_t s) {
+                                    float hinv2, unsigned long long* norm_bits, cudaStream_t s) {
   const int d = ls.d, n = ls.n, M = ls.M;
   if (!radix_length(M)) return cudaErrorInvalidValue;
   const int npts = d == 1 ? n : n * n;
@@ -262,11 +285,11 @@ cudaError_t launch_defect_update_rp(const float* e, const W* r_in, W* r_out, flo
 
 template cudaError_t launch_defect_update<dd>(const float*, const dd*, dd*, float*,
                                              const Cx<float>*, size_t, const Cx<float>*,
-                                             const float*, const LevelShape&, dd,
+                                             const float*, const LevelShape&, float,
                                              unsigned long long*, cudaStream_t);
 template cudaError_t launch_defect_update_rp<dd>(const float*, const dd*, dd*, float*,
                                                 const Cx<float>*, size_t, const Cx<float>*,
-                                                const float*, const LevelShape&, dd,
+                                                const float*, const LevelShape&, float,
                                                 unsigned long long*, cudaStream_t);
 
 }  // namespace mgwr

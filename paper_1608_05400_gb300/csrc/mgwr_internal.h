@@ -219,13 +219,14 @@ cudaError_t launch_absmax_round(const double* x, float* out, size_t per, int bat
 // (FP32 spectra `tspec`, twiddles `tw`) and the stencil on e, widened, and the
 // subtraction in double-float (W = dd, the one instantiation); r_out also
 // rounded into r32, |r_out|_inf of instance b into norm_bits[b].  r_in and
-// r_out may be the same field.  Its error is that of one FP32 convolution of
-// e, about 1e-6 of |T_M e|.  Lines of M <= kShortMaxM only (else
+// r_out may be the same field.  hinv2 = 1/h^2 must be a power of 4 (exact in
+// FP32 and in every scaling by it), as every level of the solver's grids has.
+// Its error is that of one FP32 convolution of e, about 1e-6 of |T_M e|.  Lines of M <= kShortMaxM only (else
 // cudaErrorInvalidValue).  zero: M FP32 zeros.
 template <class W>
 cudaError_t launch_defect_update(const float* e, const W* r_in, W* r_out, float* r32,
                                  const Cx<float>* tspec, size_t spec_stride, const Cx<float>* tw,
-                                 const float* zero, const LevelShape& ls, W hinv2,
+                                 const float* zero, const LevelShape& ls, float hinv2,
                                  unsigned long long* norm_bits, cudaStream_t s);
 // The same on the register-pass engine (64 <= M <= kShortMaxM), tspec in its
 // spectral order (launch_spectra_rp).
@@ -233,7 +234,7 @@ template <class W>
 cudaError_t launch_defect_update_rp(const float* e, const W* r_in, W* r_out, float* r32,
                                     const Cx<float>* tspec, size_t spec_stride,
                                     const Cx<float>* tw, const float* zero, const LevelShape& ls,
-                                    W hinv2, unsigned long long* norm_bits, cudaStream_t s);
+                                    float hinv2, unsigned long long* norm_bits, cudaStream_t s);
 // Full outer defect of an FP64 iterate with T_M u by a double-float FFT
 // convolution of u split into double-float pairs (double-float spectra `tspec`,
 // twiddles `tw`) and the stencil, source and subtractions in FP64: r = f -

@@ -101,9 +101,12 @@ SWEEP64_DRAM_BYTES_PER_LINE_M1024 = 23758.0
 # DRAM bytes per line of further kernels from single-kernel ncu captures (see
 # profiles/), by kernel class and M
 # (k_defect<double, float>: 1059.1 MB read + 254.9 MB written for 16,129 lines of 4096,
-# profiles/k_defect_fp64_outer_2d_127x127_M4096.md; k_sweep_rp: 264.5 + 103.5 MB for 8065
-# lines of 4096, profiles/k_sweep_rp_fp32_2d_127x127_M4096.md)
-NCU_DRAM_BYTES_PER_LINE: dict = {"defect64": {4096: 81468.0}, "sweep32": {4096: 45629.0}}
+# profiles/k_defect_fp64_outer_2d_127x127_M4096.md; k_sweep_rp with the paired first pass:
+# 264.5 + 102.9 MB for 8065 lines of 4096, profiles/k_sweep_rp_fp32_2d_127x127_M4096.md;
+# k_defect_update_rp: 793.7 + 737.1 MB for 16,129 lines of 4096,
+# profiles/k_defect_outer_forms_2d_127x127_M4096.md)
+NCU_DRAM_BYTES_PER_LINE: dict = {"defect64": {4096: 81468.0}, "sweep32": {4096: 45546.0},
+                                 "defect32": {4096: 94908.0}}
 
 
 def parse():
@@ -330,8 +333,8 @@ def fp32_peak_tflops(pk: dict) -> float:
 CLASS_KERNELS = {
     "sweep64": ("k_sweep<double>", 8, "sweep"), "sweep32": ("k_sweep<float>", 4, "sweep"),
     "sweep_dd": ("k_sweep<dd>", 8, "sweep"), "defect64": ("k_defect<double>", 8, "defect"),
-    "defect32": ("k_defect<float> / k_defect_hybrid", 4, "defect"),
-    "defect_dd": ("k_defect<dd>", 8, "defect"),
+    "defect32": ("k_defect_update_rp<dd> (carried outer defect) / k_defect<float>", 4, "defect"),
+    "defect_dd": ("k_defect_anchor (MGWR_MIXED) / k_defect<dd> (MGWR_MIXED_DD)", 8, "defect"),
 }
 
 
@@ -349,8 +352,12 @@ def kernel_roofline(cls: str, p: dict, d: int, M: int, pk: dict) -> dict:
     flops = p["lines"] * per_line
     # algorithmic bytes: a sweep reads f and one line of the other colour and writes
     # its line; a defect reads u and f and writes r (the FP64 outer defect of the
-    # mixed form writes FP32); line kernels: three words per line value
-    if kind == "defect":
+    # mixed form writes FP32); the carried outer defect reads the FP32 correction and
+    # the double-float defect and writes it back and rounded (24 bytes per value);
+    # line kernels: three words per line value
+    if cls == "defect32":
+        bytes_per_line = 24 * M
+    elif kind == "defect":
         bytes_per_line = (2 * word + (4 if cls == "defect64" else word)) * M
     else:
         bytes_per_line = 3 * word * M

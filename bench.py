@@ -88,8 +88,9 @@ DTYPES = {"fp64": "f64", "mixed": "f32 cycles + f64 iterate/update/stencil, oute
           "auto": "f32 cycles + f32x2 (double-float) defect/update, f32x2 cycles on grids "
                   "with h <= 1/4096"}
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# FP64 issue rate of a GB300 SM: 2 FP64 FMA per clock (measured with an FMA
-# chain: 1.20 TFLOP/s at 1995 MHz on 152 SMs); peak at the maximum clock.
+# FP64 issue rate of a GB300 SM by unit count: 2 FP64 FMA per clock, peak at the
+# maximum clock (FMA chains sustain 1.68 per clock: `--probe-peaks`, mgwr_peak_probe,
+# 1.06 TFLOP/s at 2070 MHz on 152 SMs).
 FP64_FMA_PER_CLK_PER_SM = 2
 SMS = 152
 # FP32 lanes of a GB300 SM (4 partitions x 32)
@@ -142,6 +143,9 @@ def parse():
     p.add_argument("--shape", default=None,
                    help="d,n,M replacing the workload's grid (small cases for profiling)")
     p.add_argument("--batch", type=int, default=None, help="instances replacing the workload's batch")
+    p.add_argument("--probe-peaks", action="store_true",
+                   help="print the FP64 / FP32 FMA-chain peaks (mgwr_peak_probe) with the SM "
+                        "clocks sampled meanwhile, and exit")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     return p.parse_args()
@@ -374,7 +378,7 @@ def kernel_roofline(cls: str, p: dict, d: int, M: int, pk: dict) -> dict:
         out.update({"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak,
                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x max SM clock "
-                                   "(FMA-chain probe: 1.20 TFLOP/s at 1995 MHz)",
+                                   "(FMA-chain probe mgwr_peak_probe: 1.06 TFLOP/s at 2070 MHz)",
                     "hbm_view": {"achieved_gbs": hbm, "peak_gbs": hbm_peak, "frac": hbm / hbm_peak}})
     else:
         out.update({"bound": "hbm", "achieved": hbm, "peak": hbm_peak, "unit": "GB/s",
@@ -910,8 +914,30 @@ def measure_arm(args, torch, mgwr, wl: dict, precision: str, steps: int, warmup:
     return out
 
 
+def run_probe_peaks(args) -> None:
+    """The arithmetic denominators of the FP64 and FP32 rooflines, measured on this
+    GPU (dependent FMA chains, mgwr_peak_probe), with the clocks seen meanwhile and
+    the per-clock rates they imply (152 SMs)."""
+    import torch
+    from paper_1608_05400_gb300 import mgwr
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    mgwr.load()
+    mgwr.peak_probe()  # warm-up: module load, clocks up
+    with ClockSampler(local) as clk:
+        res = mgwr.peak_probe()
+    c = clk.summary()
+    mhz = c.get("sm_mhz") or float("nan")
+    res.update({"clocks": c,
+                "fp64_fma_per_clk_per_sm": res["fp64_tflops"] * 1e12 / 2 / (SMS * mhz * 1e6),
+                "fp32_fma_per_clk_per_sm": res["fp32_tflops"] * 1e12 / 2 / (SMS * mhz * 1e6)})
+    print(json.dumps(res))
+
+
 def main():
     args = parse()
+    if args.probe_peaks:
+        return run_probe_peaks(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "served":

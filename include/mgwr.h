@@ -468,6 +468,14 @@ int mgwr_server_stats(mgwr_server_t s, mgwr_server_info* info);
  * (process-wide; h may be NULL). */
 int mgwr_launch_count(mgwr_t h, long long* count);
 
+/* Arithmetic peaks of the current device, the denominators of the FP64- and
+ * FP32-issue rooflines: TFLOP/s of dependent-FMA chains, the best of 8 or 16
+ * independent chains per thread at 4 or 8 blocks of 256 threads per SM, FP64
+ * then FP32, each shape timed with CUDA events after an untimed launch (about
+ * 0.2 s a shape on a GB300).  Runs on a private stream and synchronises it;
+ * MGWR_E_INVAL for null outputs, MGWR_E_CUDA / MGWR_E_NOMEM on a CUDA failure. */
+int mgwr_peak_probe(double* fp64_tflops, double* fp32_tflops);
+
 /* ---- per-kernel-class timing ------------------------------------------- */
 /* Kernel classes for mgwr_profile_read. */
 #define MGWR_K_SWEEP64 0    /* FP64 colour half-sweeps (levels >= 1)          */

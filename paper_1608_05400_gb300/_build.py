@@ -18,7 +18,7 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libmgwr.so")
 SOURCES = ["mgwr_sweep.cu", "mgwr_sweep_rp.cu", "mgwr_sweep_staged.cu", "mgwr_sweep_tc.cu", "mgwr_defect_f64.cu", "mgwr_defect_f32.cu", "mgwr_defect_dd.cu", "mgwr_defect_ddd.cu",
            "mgwr_defect_update.cu", "mgwr_defect_anchor.cu", "mgwr_kernels.cu", "mgwr_long.cu", "mgwr_api.cu", "mgwr_noalloc.cu",
-           "mgwr_server.cu", "mgwr_fas.cu"]
+           "mgwr_server.cu", "mgwr_fas.cu", "mgwr_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]

@@ -117,6 +117,7 @@ _SIGS = {
     "mgwr_toeplitz_column": (C.c_int, [_h, _dp]),
     "mgwr_inverse_column": (C.c_int, [_h, C.c_int, _dp]),
     "mgwr_launch_count": (C.c_int, [_h, C.POINTER(C.c_longlong)]),
+    "mgwr_peak_probe": (C.c_int, [_dp, _dp]),
     "mgwr_inverse_column_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p]),
     "mgwr_footprint": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_size_t)]),
     "mgwr_auto_precision": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int)]),
@@ -588,6 +589,15 @@ def launch_count() -> int:
     v = C.c_longlong()
     load().mgwr_launch_count(None, C.byref(v))
     return v.value
+
+
+def peak_probe() -> dict:
+    """FP64 and FP32 FMA-chain throughput of the current device (TFLOP/s)."""
+    a, b = C.c_double(), C.c_double()
+    st = load().mgwr_peak_probe(C.byref(a), C.byref(b))
+    if st != MGWR_OK:
+        raise MGWRError(st, "mgwr_peak_probe")
+    return {"fp64_tflops": a.value, "fp32_tflops": b.value}
 
 
 class FAS:

@@ -186,3 +186,9 @@ def test_group_and_set_problem_reject_invalid_arguments_on_host(lib):
     st = (C.c_int * 1)()
     assert lib.mgwr_group_solve(None, 1, 1, 1, 1, 1e-10, 10, st, None) == mgwr.MGWR_E_INVAL
     assert lib.mgwr_set_problem(None, None, None) == mgwr.MGWR_E_INVAL
+
+
+def test_peak_probe_rejects_null_outputs_on_host(lib):
+    v = C.c_double()
+    assert lib.mgwr_peak_probe(None, None) == mgwr.MGWR_E_INVAL
+    assert lib.mgwr_peak_probe(C.byref(v), None) == mgwr.MGWR_E_INVAL

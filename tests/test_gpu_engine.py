@@ -358,3 +358,13 @@ def test_radix_paired_first_pass_matches_the_single_one(d, n, M, batch):
     assert (used_a, used_b) == (1 | G.MGWR_SPLIT_RADIX, 2 | G.MGWR_SPLIT_RADIX)
     for x, y in zip(a[:2], b[:2]):
         assert np.abs(x - y).max() <= 16 * 2.0 ** -24 * np.abs(x).max()
+
+
+def test_peak_probe_measures_both_pipes():
+    # the FP64 / FP32 FMA-chain peaks: positive, FP32 far above FP64 on this part
+    # (GB300: 1/64 of the rate), neither above the nominal per-clock rates at the
+    # highest SM clock (152 SMs: 2 FP64 and 128 FP32 FMA per clock, 2.2 GHz bound)
+    p = G.peak_probe()
+    assert 0.05 < p["fp64_tflops"] <= 152 * 2 * 2 * 2.2e9 / 1e12
+    assert 1.0 < p["fp32_tflops"] <= 152 * 128 * 2 * 2.2e9 / 1e12
+    assert p["fp32_tflops"] > 8 * p["fp64_tflops"]

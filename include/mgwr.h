@@ -252,6 +252,16 @@ int mgwr_autotune(mgwr_t h);
  * launches are issued one by one.  Results are identical either way.  The
  * capture uses thread-local capture mode on the handle's stream. */
 int mgwr_set_graphs(mgwr_t h, int enable);
+/* enable != 0 (default): an MGWR_FP64 solve with graphs runs its iterations
+ * after the first as one graph launch, a conditional (WHILE) node whose body is
+ * one iteration followed by a one-warp kernel that computes the relative
+ * defect from the iteration's norms and ends the loop on the device once it is
+ * at most tol, is not finite, or max_cycles is reached; the host then reads the
+ * iteration count and the norms once, and confirms a stop with the full defect
+ * as the host loop does.  Used when the iteration leaves the hierarchy's state
+ * as it found it (every V or W cycle from the second on).  Results are those of
+ * the host loop, bitwise.  0: one graph launch and one host wait per iteration. */
+int mgwr_set_device_loop(mgwr_t h, int enable);
 
 /* ---- problem data -------------------------------------------------------- */
 

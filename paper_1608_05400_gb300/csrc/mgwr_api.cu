@@ -68,6 +68,14 @@ struct Hier {
   bool full = false;              // every level's u, f, r, dl allocated
 };
 
+// The per-level defect states of a handle's three hierarchies.  Enqueuing an
+// iteration updates them as if it ran; a captured iteration graph keeps what
+// its capture left and a replay sets them to it, so that the next iteration's
+// key (and the launches it selects) follows the device's state.
+struct RsState {
+  std::vector<int> r64, r32, rdd;
+};
+
 }  // namespace
 
 struct mgwr_handle {
@@ -120,8 +128,24 @@ struct mgwr_handle {
     cudaGraphExec_t exec;
     bool exact;           // its norms come from the full defect in the working precision
     long long kernels;    // kernel launches recorded in the graph
+    RsState after;        // the defect states the iteration leaves
   };
   std::vector<IterGraph> graphs;
+  // the rest of an MGWR_FP64 solve as one graph launch: a WHILE node whose body
+  // is one iteration (its launches without the copy of the norms to the host)
+  // and k_loop_decide, which ends it on the device (run_device_loop)
+  struct LoopGraph {
+    long long key = -1;   // iteration_key of the body (-1: none)
+    cudaGraphExec_t exec = nullptr;
+    bool exact = true;    // the body's norms come from the full defect
+    long long kernels = 0;  // kernel launches of one body iteration
+    bool unusable = false;  // the body's iteration is not uniform for this key
+  } loop;
+  bool use_device_loop = true;              // mgwr_set_device_loop
+  mgwr::LoopState* loop_dev = nullptr;      // device state of the loop
+  mgwr::LoopState* loop_pin = nullptr;      // pinned copy read after it
+  double* r0_dev = nullptr;                 // per-instance reference norms (device)
+  double* r0_pin = nullptr;                 // pinned staging of r0
   // the finest iterate is zero (right-hand side just set without initial values)
   bool u_zero = false;
   // mixed modes: the form of the outer defect of the iteration being enqueued
@@ -218,9 +242,19 @@ int split_of(const mgwr_handle* h, int cls, int l) {
   return h->split[cls].empty() ? 0 : h->split[cls][l];
 }
 
+RsState save_rs(const mgwr_handle* h) { return RsState{h->h64.rs, h->h32.rs, h->hdd.rs}; }
+
+void load_rs(mgwr_t h, const RsState& s) {
+  h->h64.rs = s.r64;
+  h->h32.rs = s.r32;
+  h->hdd.rs = s.rdd;
+}
+
 void drop_graph(mgwr_t h) {
   for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
   h->graphs.clear();
+  if (h->loop.exec != nullptr) cudaGraphExecDestroy(h->loop.exec);
+  h->loop = mgwr_handle::LoopGraph{};
 }
 
 // The handle's partitioned-convolution scratch viewed as complex values of R
@@ -744,7 +778,7 @@ int enqueue_plain(mgwr_t h, Hier<R>& H, int cyc, int nu1, int nu2, bool* exact) 
 // false).  Mixed: `inner` FP32 cycles on the defect equation from e = 0, the
 // update, and the outer defect (double or double-float) with its norms.
 // MGWR_DD: the same with double-float inner cycles and outer defect.
-int enqueue_iteration(mgwr_t h, int cyc, int nu1, int nu2, bool* exact) {
+int enqueue_iteration(mgwr_t h, int cyc, int nu1, int nu2, bool* exact, bool copy_norms = true) {
   const int L = h->nlev - 1;
   const size_t cnt = level_count(h, L);
   if (h->precision == MGWR_FP64) {
@@ -800,8 +834,9 @@ int enqueue_iteration(mgwr_t h, int cyc, int nu1, int nu2, bool* exact) {
       *exact = true;
     }
   }
-  MGWR_CK(h, cudaMemcpyAsync(h->norm_host, h->norm_bits, sizeof(unsigned long long) * h->B,
-                             cudaMemcpyDeviceToHost, h->stream));
+  if (copy_norms)
+    MGWR_CK(h, cudaMemcpyAsync(h->norm_host, h->norm_bits, sizeof(unsigned long long) * h->B,
+                               cudaMemcpyDeviceToHost, h->stream));
   return MGWR_OK;
 }
 
@@ -846,9 +881,10 @@ int run_iteration(mgwr_t h, int cyc, int nu1, int nu2, std::vector<double>& norm
       const cudaError_t ei = cudaGraphInstantiate(&exec, g, 0);
       cudaGraphDestroy(g);
       MGWR_CK(h, ei);
-      h->graphs.push_back({key, exec, ex, captured});
+      h->graphs.push_back({key, exec, ex, captured, save_rs(h)});
       slot = &h->graphs.back();
     }
+    load_rs(h, slot->after);
     MGWR_CK(h, cudaGraphLaunch(slot->exec, h->stream));
     mgwr::add_launches(slot->kernels);
     *exact = slot->exact;
@@ -1259,6 +1295,9 @@ int mgwr_destroy(mgwr_t h) {
   for (void* p : h->allocs) cudaFreeAsync(p, h->stream);
   if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->norm_host) cudaFreeHost(h->norm_host);
+  if (h->loop_pin) cudaFreeHost(h->loop_pin);
+  if (h->r0_pin) cudaFreeHost(h->r0_pin);
+  if (h->loop.exec) cudaGraphExecDestroy(h->loop.exec);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
@@ -1387,6 +1426,12 @@ int mgwr_set_stream(mgwr_t h, void* stream) {
 int mgwr_set_graphs(mgwr_t h, int enable) {
   if (h == nullptr) return MGWR_E_INVAL;
   h->use_graphs = enable != 0;
+  return MGWR_OK;
+}
+
+int mgwr_set_device_loop(mgwr_t h, int enable) {
+  if (h == nullptr) return MGWR_E_INVAL;
+  h->use_device_loop = enable != 0;
   return MGWR_OK;
 }
 
@@ -1691,6 +1736,123 @@ int solve_after(mgwr_t h, SolveState& S, bool exact) {
   return MGWR_OK;
 }
 
+// Builds the device loop of the current iteration form: a WHILE node whose body
+// is one iteration without the copy of its norms and k_loop_decide.  The body's
+// iteration must leave the finest state as it found it (the same
+// iteration_key), so that every pass of the loop runs the launches of the host
+// loop's replayed iterations; otherwise the key is marked unusable.
+int build_device_loop(mgwr_t h, int cyc, int nu1, int nu2, long long key) {
+  if (h->loop.exec != nullptr) cudaGraphExecDestroy(h->loop.exec);
+  h->loop = mgwr_handle::LoopGraph{};
+  h->loop.key = key;
+  cudaGraph_t g = nullptr;
+  MGWR_CK(h, cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle cond;
+  cudaGraphNodeParams cp = {};
+  cudaGraphNode_t node;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) {
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp);
+  }
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    MGWR_CK(h, e);
+  }
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  e = cudaStreamBeginCaptureToGraph(h->stream, body, nullptr, nullptr, 0,
+                                    cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    MGWR_CK(h, e);
+  }
+  // the capture updates the hierarchies' defect states as if the iteration ran
+  const RsState pre = save_rs(h);
+  bool ex = true;
+  const long long before = mgwr::launch_counter();
+  int st = enqueue_iteration(h, cyc, nu1, nu2, &ex, false);
+  if (st == MGWR_OK)
+    st = mgwr::launch_loop_decide(h->norm_bits, h->r0_dev, h->B, h->loop_dev, cond, h->stream) ==
+                 cudaSuccess
+             ? MGWR_OK
+             : MGWR_E_CUDA;
+  cudaGraph_t captured = nullptr;
+  e = cudaStreamEndCapture(h->stream, &captured);
+  const long long kernels = mgwr::launch_counter() - before;
+  mgwr::add_launches(-kernels);  // captured launches run when the graph does
+  if (st != MGWR_OK || e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    if (st != MGWR_OK) return st;
+    MGWR_CK(h, e);
+  }
+  const bool uniform = iteration_key(h, cyc, nu1, nu2) == key && h->h64.rs == pre.r64 &&
+                       h->h32.rs == pre.r32 && h->hdd.rs == pre.rdd;
+  if (!uniform) {  // keep the host loop, and the states the capture changed
+    cudaGraphDestroy(g);
+    load_rs(h, pre);
+    h->loop.unusable = true;
+    return MGWR_OK;
+  }
+  e = cudaGraphInstantiate(&h->loop.exec, g, 0);
+  cudaGraphDestroy(g);
+  MGWR_CK(h, e);
+  h->loop.exact = ex;
+  h->loop.kernels = kernels;
+  return MGWR_OK;
+}
+
+// MGWR_FP64 with graphs: runs the remaining iterations of the solve as one
+// graph launch (the device decides when to stop, within max_cycles), then takes
+// in the last norms and the iteration count as solve_after would.  *ran =
+// false when the form has no device loop (the caller runs the host loop).
+int run_device_loop(mgwr_t h, SolveState& S, bool* ran) {
+  *ran = false;
+  const int left = S.max_cycles - S.cycles;
+  if (h->precision != MGWR_FP64 || !h->use_graphs || !h->use_device_loop || h->profiling ||
+      left < 2)
+    return MGWR_OK;
+  const long long key = iteration_key(h, S.cyc, S.nu1, S.nu2);
+  if (h->loop.key == key && h->loop.unusable) return MGWR_OK;
+  if (h->loop_dev == nullptr) {
+    MGWR_TRY(dev_alloc(h, &h->loop_dev, sizeof(mgwr::LoopState)));
+    MGWR_TRY(dev_alloc(h, &h->r0_dev, sizeof(double) * h->B));
+    if (cudaMallocHost(&h->loop_pin, sizeof(mgwr::LoopState)) != cudaSuccess ||
+        cudaMallocHost(&h->r0_pin, sizeof(double) * h->B) != cudaSuccess)
+      return fail(h, MGWR_E_NOMEM, "pinned loop state");
+  }
+  if (h->loop.key != key || h->loop.exec == nullptr) {
+    MGWR_TRY(build_device_loop(h, S.cyc, S.nu1, S.nu2, key));
+    if (h->loop.unusable) return MGWR_OK;
+  }
+  for (int b = 0; b < h->B; ++b) h->r0_pin[b] = h->r0[b];
+  MGWR_CK(h, cudaMemcpyAsync(h->r0_dev, h->r0_pin, sizeof(double) * h->B, cudaMemcpyHostToDevice,
+                             h->stream));
+  MGWR_CK(h, mgwr::launch_loop_init(h->loop_dev, S.tol, left, h->stream));
+  MGWR_CK(h, cudaGraphLaunch(h->loop.exec, h->stream));
+  MGWR_CK(h, cudaMemcpyAsync(h->loop_pin, h->loop_dev, sizeof(mgwr::LoopState),
+                             cudaMemcpyDeviceToHost, h->stream));
+  std::vector<double> norms;
+  MGWR_TRY(read_norms(h, norms));  // synchronises the stream
+  const int iters = h->loop_pin->iters;
+  mgwr::add_launches(h->loop.kernels * iters);
+  *ran = true;
+  S.norms = norms;
+  S.cycles += iters;
+  S.outer += iters;
+  S.rel = relative(h, S.norms, h->relres);
+  bool exact = h->loop.exact;
+  if (!exact && S.rel <= S.tol) {  // the stop is decided on the full defect
+    MGWR_TRY(solve_full_defect(h, S));
+    S.rel = relative(h, S.norms, h->relres);
+    exact = true;
+  }
+  S.rel_exact = exact;
+  return MGWR_OK;
+}
+
 // Ends a solve: the iterate back in FP64, the full defect when the last norms
 // were not, the timing and the statistics.
 int solve_end(mgwr_t h, SolveState& S, mgwr_stats* st) {
@@ -1733,6 +1895,11 @@ int mgwr_solve(mgwr_t h, int cyc, int nu1, int nu2, double tol, int max_cycles, 
   SolveState S;
   MGWR_TRY(solve_begin(h, S, cyc, nu1, nu2, tol, max_cycles));
   while (solve_plan(h, S)) {
+    if (S.cycles >= 1) {  // past the first iteration, whose start differs from u = 0
+      bool ran = false;
+      MGWR_TRY(run_device_loop(h, S, &ran));
+      if (ran) continue;
+    }
     bool exact = true;
     std::vector<double> unused;
     MGWR_TRY(run_iteration(h, cyc, nu1, nu2, unused, &exact));
@@ -1768,6 +1935,7 @@ struct mgwr_group {
     std::vector<std::pair<mgwr_t, long long>> key;
     cudaGraphExec_t exec = nullptr;
     std::vector<char> exact;
+    std::vector<RsState> after;  // per member: the defect states its iteration leaves
     long long kernels = 0;
     unsigned long long used = 0;
   };
@@ -1830,6 +1998,7 @@ int group_capture(mgwr_group* g, mgwr_group::Entry& e) {
     bool ex = true;
     st = enqueue_iteration(m.h, mm.S.cyc, mm.S.nu1, mm.S.nu2, &ex);
     e.exact[i] = ex ? 1 : 0;
+    e.after.push_back(save_rs(m.h));
     if (st == MGWR_OK && (cudaEventRecord(m.join, m.h->stream) != cudaSuccess ||
                           cudaStreamWaitEvent(g->stream, m.join, 0) != cudaSuccess))
       st = MGWR_E_CUDA;
@@ -1936,6 +2105,7 @@ int mgwr_group_step(mgwr_group_t g, int* running) {
     e = &g->graphs.back();
   }
   e->used = ++g->clock;
+  for (size_t i = 0; i < g->running.size(); ++i) load_rs(g->running[i].h, e->after[i]);
   cudaError_t ce = cudaGraphLaunch(e->exec, g->stream);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(g->stream);
   if (ce != cudaSuccess) {

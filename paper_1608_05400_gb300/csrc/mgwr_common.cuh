@@ -41,6 +41,34 @@ inline cudaError_t prepare_smem(K kernel, size_t smem) {
   return cudaSuccess;
 }
 
+// Number of SMs of the current device (queried once per process).
+inline int sm_count() {
+  static const int n = [] {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      v = 152;
+    }
+    return v > 0 ? v : 152;
+  }();
+  return n;
+}
+
+// Threads per block for line pairs of TL (< 256) threads each: 256, halved
+// (down to one warp, and not below TL) while the grid would give some SMs no
+// block at all.  Short lines on small grids (coarse levels, small 1-D
+// problems) then spread over the SMs instead of queueing up to 256 / TL pairs
+// on one; the arithmetic of each pair is the same in every block size.
+inline int spread_block(int TL, int npairs, int batch) {
+  int block = 256;
+  const long long sms = sm_count();
+  while (block > 32 && block > TL &&
+         (long long)((npairs + block / TL - 1) / (block / TL)) * batch < sms)
+    block /= 2;
+  return block;
+}
+
 inline unsigned elementwise_grid(size_t total) {
   size_t blocks = (total + 255) / 256;
   const size_t cap = 152 * 16;

@@ -141,7 +141,10 @@ cudaError_t launch_defect(const R* u, const R* f, RO* r, const Cx<R>* tspec, siz
   if (ls.batch == 0) return cudaSuccess;
   const size_t fstride = ls.field_stride();
   const int TL = L / (8 * E);
-  const int block = TL > 256 ? TL : 256;
+  int block = TL > 256 ? TL : 256;
+  if constexpr (sizeof(R) == 8) {
+    if (E == 1 && TL < 256) block = spread_block(TL, npairs, ls.batch);
+  }
   const int groups = block / TL;
   const size_t smem = (size_t)groups * Pad<R>::len(L) * sizeof(Cx<R>);
   const dim3 grid((unsigned)((npairs + groups - 1) / groups), (unsigned)ls.batch);
@@ -165,6 +168,9 @@ cudaError_t launch_defect(const R* u, const R* f, RO* r, const Cx<R>* tspec, siz
     }
   } else {
     switch (block * 8 + E) {
+      case 32 * 8 + 1: e = defect_launch<R, RO, 32, FftShape, 1>(MGWR_DEFECT_ARGS); break;
+      case 64 * 8 + 1: e = defect_launch<R, RO, 64, FftShape, 1>(MGWR_DEFECT_ARGS); break;
+      case 128 * 8 + 1: e = defect_launch<R, RO, 128, FftShape, 1>(MGWR_DEFECT_ARGS); break;
       case 256 * 8 + 1: e = defect_launch<R, RO, 256, FftShape, 1>(MGWR_DEFECT_ARGS); break;
       case 512 * 8 + 1: e = defect_launch<R, RO, 512, FftShape, 1>(MGWR_DEFECT_ARGS); break;
       case 1024 * 8 + 1: e = defect_launch<R, RO, 1024, FftShape, 1>(MGWR_DEFECT_ARGS); break;

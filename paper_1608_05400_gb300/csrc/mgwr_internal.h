@@ -210,6 +210,22 @@ cudaError_t launch_split_cx(Cx<dd>* dst, const Cx<double>* src, size_t count, cu
 cudaError_t launch_round(float* dst, const double* src, size_t count, cudaStream_t s);
 // Per instance b (x holds batch * per values): |x_b|_inf folded into
 // norm_bits[b]; out_b = (float) x_b when out != null.
+// State of a solve loop run on the device (a CUDA graph WHILE node whose body
+// is one iteration and k_loop_decide): the stopping tolerance and iteration
+// bound it was given, the iterations done and the last relative defect.
+struct LoopState {
+  double tol;
+  double rel;
+  int max_iter;
+  int iters;
+};
+cudaError_t launch_loop_init(LoopState* st, double tol, int max_iter, cudaStream_t s);
+// After an iteration: rel = max_b norm_b / r0_b (norm_bits as in the defect
+// kernels; r0_b = 0 takes the norm itself), iters += 1, and the loop's
+// condition set to continue while rel > tol, rel is finite and iters <
+// max_iter.
+cudaError_t launch_loop_decide(const unsigned long long* norm_bits, const double* r0, int batch,
+                               LoopState* st, cudaGraphConditionalHandle loop, cudaStream_t s);
 cudaError_t launch_absmax_round(const double* x, float* out, size_t per, int batch,
                                 unsigned long long* norm_bits, cudaStream_t s);
 

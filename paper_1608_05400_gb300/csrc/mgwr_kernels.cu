@@ -755,6 +755,49 @@ cudaError_t launch_round(float* dst, const double* src, size_t count, cudaStream
   return counted(cudaGetLastError());
 }
 
+namespace {
+
+__global__ void k_loop_init(LoopState* st, double tol, int max_iter) {
+  st->tol = tol;
+  st->rel = 0.0;
+  st->max_iter = max_iter;
+  st->iters = 0;
+}
+
+// One warp: the largest relative defect over the instances (NaN wins), then
+// the loop's condition.
+__global__ void k_loop_decide(const unsigned long long* __restrict__ norm_bits,
+                              const double* __restrict__ r0, int batch, LoopState* st,
+                              cudaGraphConditionalHandle loop) {
+  double worst = 0.0;
+  for (int b = threadIdx.x; b < batch; b += 32) {
+    const double nv = __longlong_as_double((long long)norm_bits[b]);
+    const double rel = r0[b] > 0.0 ? nv / r0[b] : (nv == 0.0 ? 0.0 : nv);
+    worst = absmax_nan(isinf(rel) ? (double)NAN : rel, worst);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) worst = absmax_nan(__shfl_xor_sync(0xffffffffu, worst, o), worst);
+  if (threadIdx.x == 0) {
+    st->iters += 1;
+    st->rel = worst;
+    const bool more = worst == worst && worst > st->tol && st->iters < st->max_iter;
+    cudaGraphSetConditional(loop, more ? 1u : 0u);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_loop_init(LoopState* st, double tol, int max_iter, cudaStream_t s) {
+  k_loop_init<<<1, 1, 0, s>>>(st, tol, max_iter);
+  return counted(cudaGetLastError());
+}
+
+cudaError_t launch_loop_decide(const unsigned long long* norm_bits, const double* r0, int batch,
+                               LoopState* st, cudaGraphConditionalHandle loop, cudaStream_t s) {
+  k_loop_decide<<<1, 32, 0, s>>>(norm_bits, r0, batch, st, loop);
+  return counted(cudaGetLastError());
+}
+
 cudaError_t launch_absmax_round(const double* x, float* out, size_t per, int batch,
                                 unsigned long long* norm_bits, cudaStream_t s) {
   if (per == 0 || batch == 0) return cudaSuccess;

@@ -124,7 +124,10 @@ cudaError_t launch_sweep(const R* f, R* u, R* delta, const Cx<R>* spec, size_t s
   if (npairs == 0 || ls.batch == 0) return cudaSuccess;
   const size_t fstride = ls.field_stride();
   const int TL = L / (8 * E);
-  const int block = TL > 256 ? TL : 256;
+  int block = TL > 256 ? TL : 256;
+  if constexpr (sizeof(R) == 8) {
+    if (E == 1 && TL < 256) block = spread_block(TL, npairs, ls.batch);
+  }
   const int groups = block / TL;
   const size_t smem = (size_t)groups * Pad<R>::len(L) * sizeof(Cx<R>);
   const dim3 grid((unsigned)((npairs + groups - 1) / groups), (unsigned)ls.batch);
@@ -149,6 +152,9 @@ cudaError_t launch_sweep(const R* f, R* u, R* delta, const Cx<R>* spec, size_t s
     }
   } else {
     switch (block * 8 + E) {
+      case 32 * 8 + 1: e = sweep_launch<R, 32, FftShape, 1>(MGWR_SWEEP_ARGS); break;
+      case 64 * 8 + 1: e = sweep_launch<R, 64, FftShape, 1>(MGWR_SWEEP_ARGS); break;
+      case 128 * 8 + 1: e = sweep_launch<R, 128, FftShape, 1>(MGWR_SWEEP_ARGS); break;
       case 256 * 8 + 1: e = sweep_launch<R, 256, FftShape, 1>(MGWR_SWEEP_ARGS); break;
       case 512 * 8 + 1: e = sweep_launch<R, 512, FftShape, 1>(MGWR_SWEEP_ARGS); break;
       case 1024 * 8 + 1: e = sweep_launch<R, 1024, FftShape, 1>(MGWR_SWEEP_ARGS); break;

@@ -95,6 +95,7 @@ _SIGS = {
     "mgwr_get_engine_split": (C.c_int, [_h, C.c_int, C.c_int, C.POINTER(C.c_int)]),
     "mgwr_autotune": (C.c_int, [_h]),
     "mgwr_set_graphs": (C.c_int, [_h, C.c_int]),
+    "mgwr_set_device_loop": (C.c_int, [_h, C.c_int]),
     "mgwr_set_rhs": (C.c_int, [_h, _dp, _dp]),
     "mgwr_set_rhs_dev": (C.c_int, [_h, C.c_void_p, C.c_void_p]),
     "mgwr_set_initial": (C.c_int, [_h, _dp]),
@@ -276,6 +277,9 @@ class Solver:
 
     def set_graphs(self, enable: bool):
         self._check(self.lib.mgwr_set_graphs(self.h, int(enable)), "mgwr_set_graphs")
+
+    def set_device_loop(self, enable: bool):
+        self._check(self.lib.mgwr_set_device_loop(self.h, int(enable)), "mgwr_set_device_loop")
 
     def set_inner_cycles(self, k: int):
         self._check(self.lib.mgwr_set_inner_cycles(self.h, k), "mgwr_set_inner_cycles")

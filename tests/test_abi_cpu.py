@@ -192,3 +192,7 @@ def test_peak_probe_rejects_null_outputs_on_host(lib):
     v = C.c_double()
     assert lib.mgwr_peak_probe(None, None) == mgwr.MGWR_E_INVAL
     assert lib.mgwr_peak_probe(C.byref(v), None) == mgwr.MGWR_E_INVAL
+
+
+def test_device_loop_switch_rejects_a_null_handle(lib):
+    assert lib.mgwr_set_device_loop(None, 1) == mgwr.MGWR_E_INVAL

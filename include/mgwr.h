@@ -332,6 +332,33 @@ int mgwr_residual(mgwr_t h, double* relres, double* r_host);
 int mgwr_get_solution(mgwr_t h, double* u_host);
 int mgwr_get_solution_dev(mgwr_t h, double* u_dev);
 
+/* Pipelined transfers, for a stream of problems through one handle: the next
+ * right-hand side travels to the device and the last solution to the host
+ * while a solve runs, so that only two device-to-device copies of one field
+ * (about 2.5 ms each at 2-D 511 x 511, M = 4096) stay between the solves.
+ * Each call returns at once; the copies run on two streams of the handle's
+ * own (created, with two device staging fields of N*M doubles, on first use).
+ * - mgwr_stage_rhs: starts copying f_host (N*M doubles, pinned for the copy
+ *   to overlap) into the input staging field.  f_host must stay unchanged
+ *   until the copy has landed: until mgwr_wait_staged, or the mgwr_solve
+ *   after the matching mgwr_take_rhs, returns.  MGWR_E_STATE while a staged
+ *   right-hand side is not taken yet.
+ * - mgwr_take_rhs: makes the staged right-hand side the handle's (as
+ *   mgwr_set_rhs(h, f, NULL) does, without a host wait): the handle's stream
+ *   waits for the copy, then copies it into place and zeroes the iterate.
+ *   MGWR_E_STATE when nothing is staged.
+ * - mgwr_stage_solution: copies the current solution into the output staging
+ *   field on the handle's stream (after the previous one has left it), then to
+ *   u_host (N*M doubles, pinned) on the output stream.  u_host holds it once
+ *   mgwr_wait_staged returns.
+ * - mgwr_wait_staged: waits for both transfer streams.
+ * A pipelined step: mgwr_take_rhs; mgwr_stage_rhs(next f); mgwr_solve;
+ * mgwr_stage_solution(u); and mgwr_wait_staged after the last. */
+int mgwr_stage_rhs(mgwr_t h, const double* f_host);
+int mgwr_take_rhs(mgwr_t h);
+int mgwr_stage_solution(mgwr_t h, double* u_host);
+int mgwr_wait_staged(mgwr_t h);
+
 /* ---- components (one step of Algorithm 1 on one level) ------------------ */
 /* hier is MGWR_H64 or MGWR_H32; level 0 is the one-point grid, level
  * num_levels-1 the finest.  Fields are exchanged as doubles in both

@@ -146,6 +146,17 @@ struct mgwr_handle {
   mgwr::LoopState* loop_pin = nullptr;      // pinned copy read after it
   double* r0_dev = nullptr;                 // per-instance reference norms (device)
   double* r0_pin = nullptr;                 // pinned staging of r0
+  // pipelined transfers (mgwr_stage_rhs / mgwr_take_rhs / mgwr_stage_solution):
+  // device staging of the next right-hand side and of the last solution, each
+  // copied to or from the host on a stream of its own
+  double* stage_in = nullptr;
+  double* stage_out = nullptr;
+  cudaStream_t copy_in = nullptr, copy_out = nullptr;
+  cudaEvent_t ev_in = nullptr;      // the staged right-hand side has landed
+  cudaEvent_t ev_taken = nullptr;   // stage_in copied into f: it may be refilled
+  cudaEvent_t ev_staged = nullptr;  // stage_out holds the solution to send
+  cudaEvent_t ev_sent = nullptr;    // stage_out sent to the host: it may be refilled
+  bool rhs_pending = false;
   // the finest iterate is zero (right-hand side just set without initial values)
   bool u_zero = false;
   // mixed modes: the form of the outer defect of the iteration being enqueued
@@ -1298,6 +1309,12 @@ int mgwr_destroy(mgwr_t h) {
   if (h->loop_pin) cudaFreeHost(h->loop_pin);
   if (h->r0_pin) cudaFreeHost(h->r0_pin);
   if (h->loop.exec) cudaGraphExecDestroy(h->loop.exec);
+  if (h->copy_in) cudaStreamSynchronize(h->copy_in);
+  if (h->copy_out) cudaStreamSynchronize(h->copy_out);
+  for (cudaEvent_t e : {h->ev_in, h->ev_taken, h->ev_staged, h->ev_sent})
+    if (e) cudaEventDestroy(e);
+  if (h->copy_in) cudaStreamDestroy(h->copy_in);
+  if (h->copy_out) cudaStreamDestroy(h->copy_out);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
@@ -2193,6 +2210,74 @@ int mgwr_residual(mgwr_t h, double* relres, double* r_host) {
                                cudaMemcpyDeviceToHost, h->stream));
     MGWR_CK(h, cudaStreamSynchronize(h->stream));
   }
+  return MGWR_OK;
+}
+
+// ---- pipelined transfers ---------------------------------------------------------
+
+static int ensure_staging(mgwr_t h) {
+  if (h->stage_in != nullptr) return MGWR_OK;
+  const size_t cnt = level_count(h, h->nlev - 1);
+  MGWR_TRY(dev_alloc(h, &h->stage_out, cnt * sizeof(double)));
+  MGWR_TRY(dev_alloc(h, &h->stage_in, cnt * sizeof(double)));
+  MGWR_CK(h, cudaStreamCreateWithFlags(&h->copy_in, cudaStreamNonBlocking));
+  MGWR_CK(h, cudaStreamCreateWithFlags(&h->copy_out, cudaStreamNonBlocking));
+  for (cudaEvent_t* e : {&h->ev_in, &h->ev_taken, &h->ev_staged, &h->ev_sent})
+    MGWR_CK(h, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+  // the staging buffers come from the handle's stream-ordered pool: the copy
+  // streams may use them once that allocation has completed
+  MGWR_CK(h, cudaStreamSynchronize(h->stream));
+  return MGWR_OK;
+}
+
+int mgwr_stage_rhs(mgwr_t h, const double* f_host) {
+  if (h == nullptr) return MGWR_E_INVAL;
+  if (f_host == nullptr) return fail(h, MGWR_E_INVAL, "f must not be null");
+  if (h->rhs_pending) return fail(h, MGWR_E_STATE, "a staged right-hand side is not taken yet");
+  MGWR_TRY(ensure_staging(h));
+  const size_t bytes = level_count(h, h->nlev - 1) * sizeof(double);
+  MGWR_CK(h, cudaStreamWaitEvent(h->copy_in, h->ev_taken, 0));
+  MGWR_CK(h, cudaMemcpyAsync(h->stage_in, f_host, bytes, cudaMemcpyHostToDevice, h->copy_in));
+  MGWR_CK(h, cudaEventRecord(h->ev_in, h->copy_in));
+  h->rhs_pending = true;
+  return MGWR_OK;
+}
+
+int mgwr_take_rhs(mgwr_t h) {
+  if (h == nullptr) return MGWR_E_INVAL;
+  if (!h->rhs_pending) return fail(h, MGWR_E_STATE, "no staged right-hand side");
+  const int L = h->nlev - 1;
+  const size_t bytes = level_count(h, L) * sizeof(double);
+  MGWR_CK(h, cudaStreamWaitEvent(h->stream, h->ev_in, 0));
+  MGWR_CK(h, cudaMemcpyAsync(h->h64.f[L], h->stage_in, bytes, cudaMemcpyDeviceToDevice, h->stream));
+  MGWR_CK(h, cudaEventRecord(h->ev_taken, h->stream));
+  MGWR_CK(h, cudaMemsetAsync(h->h64.u[L], 0, bytes, h->stream));
+  h->rhs_pending = false;
+  h->u_zero = true;
+  h->r0_valid = false;
+  h->h64.rs[L] = R_STALE;
+  return MGWR_OK;
+}
+
+int mgwr_stage_solution(mgwr_t h, double* u_host) {
+  if (h == nullptr) return MGWR_E_INVAL;
+  if (u_host == nullptr) return fail(h, MGWR_E_INVAL, "u must not be null");
+  MGWR_TRY(ensure_staging(h));
+  const int L = h->nlev - 1;
+  const size_t bytes = level_count(h, L) * sizeof(double);
+  MGWR_CK(h, cudaStreamWaitEvent(h->stream, h->ev_sent, 0));
+  MGWR_CK(h, cudaMemcpyAsync(h->stage_out, h->h64.u[L], bytes, cudaMemcpyDeviceToDevice, h->stream));
+  MGWR_CK(h, cudaEventRecord(h->ev_staged, h->stream));
+  MGWR_CK(h, cudaStreamWaitEvent(h->copy_out, h->ev_staged, 0));
+  MGWR_CK(h, cudaMemcpyAsync(u_host, h->stage_out, bytes, cudaMemcpyDeviceToHost, h->copy_out));
+  MGWR_CK(h, cudaEventRecord(h->ev_sent, h->copy_out));
+  return MGWR_OK;
+}
+
+int mgwr_wait_staged(mgwr_t h) {
+  if (h == nullptr) return MGWR_E_INVAL;
+  if (h->copy_in != nullptr) MGWR_CK(h, cudaStreamSynchronize(h->copy_in));
+  if (h->copy_out != nullptr) MGWR_CK(h, cudaStreamSynchronize(h->copy_out));
   return MGWR_OK;
 }
 

@@ -96,6 +96,10 @@ _SIGS = {
     "mgwr_autotune": (C.c_int, [_h]),
     "mgwr_set_graphs": (C.c_int, [_h, C.c_int]),
     "mgwr_set_device_loop": (C.c_int, [_h, C.c_int]),
+    "mgwr_stage_rhs": (C.c_int, [_h, _dp]),
+    "mgwr_take_rhs": (C.c_int, [_h]),
+    "mgwr_stage_solution": (C.c_int, [_h, _dp]),
+    "mgwr_wait_staged": (C.c_int, [_h]),
     "mgwr_set_rhs": (C.c_int, [_h, _dp, _dp]),
     "mgwr_set_rhs_dev": (C.c_int, [_h, C.c_void_p, C.c_void_p]),
     "mgwr_set_initial": (C.c_int, [_h, _dp]),
@@ -345,6 +349,22 @@ class Solver:
         u = np.empty(self._shape())
         self._check(self.lib.mgwr_get_solution(self.h, _ptr(u)), "mgwr_get_solution")
         return u
+
+    # -- pipelined transfers (mgwr_stage_rhs ...): the caller keeps the host arrays
+    #    alive and unchanged until wait_staged (pinned arrays let the copies overlap)
+    def stage_rhs(self, f: np.ndarray):
+        assert f.dtype == np.float64 and f.flags.c_contiguous and f.shape == self._shape()
+        self._check(self.lib.mgwr_stage_rhs(self.h, _ptr(f)), "mgwr_stage_rhs")
+
+    def take_rhs(self):
+        self._check(self.lib.mgwr_take_rhs(self.h), "mgwr_take_rhs")
+
+    def stage_solution(self, u: np.ndarray):
+        assert u.dtype == np.float64 and u.flags.c_contiguous and u.shape == self._shape()
+        self._check(self.lib.mgwr_stage_solution(self.h, _ptr(u)), "mgwr_stage_solution")
+
+    def wait_staged(self):
+        self._check(self.lib.mgwr_wait_staged(self.h), "mgwr_wait_staged")
 
     def solution_dev(self, u_ptr: int):
         self._check(self.lib.mgwr_get_solution_dev(self.h, C.c_void_p(u_ptr)), "mgwr_get_solution_dev")

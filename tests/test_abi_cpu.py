@@ -196,3 +196,10 @@ def test_peak_probe_rejects_null_outputs_on_host(lib):
 
 def test_device_loop_switch_rejects_a_null_handle(lib):
     assert lib.mgwr_set_device_loop(None, 1) == mgwr.MGWR_E_INVAL
+
+
+def test_pipelined_transfer_calls_reject_a_null_handle(lib):
+    assert lib.mgwr_stage_rhs(None, None) == mgwr.MGWR_E_INVAL
+    assert lib.mgwr_take_rhs(None) == mgwr.MGWR_E_INVAL
+    assert lib.mgwr_stage_solution(None, None) == mgwr.MGWR_E_INVAL
+    assert lib.mgwr_wait_staged(None) == mgwr.MGWR_E_INVAL

@@ -335,9 +335,10 @@ int ensure_h32(mgwr_t h) {
   if (mgwr::radix_length(h->M)) {
     MGWR_TRY(dev_alloc(h, &H.spec_rp, sizeof(Cx<float>) * nspec));
     MGWR_CK(h, mgwr::launch_spectra_rp(H.spec_rp, h->h64.spec, (size_t)h->B * h->nlev, h->M,
-                                       h->stream));
+                                       false, h->stream));
     MGWR_TRY(dev_alloc(h, &H.tspec_rp, sizeof(Cx<float>) * (size_t)h->B * h->L));
-    MGWR_CK(h, mgwr::launch_spectra_rp(H.tspec_rp, h->h64.tspec, (size_t)h->B, h->M, h->stream));
+    MGWR_CK(h, mgwr::launch_spectra_rp(H.tspec_rp, h->h64.tspec, (size_t)h->B, h->M, true,
+                                       h->stream));
   }
   if (mgwr::tensor_length(h->M)) {
     const size_t lines = (size_t)h->B * h->nlev;
@@ -1164,10 +1165,10 @@ int refresh_derived(mgwr_t h) {
     MGWR_CK(h, mgwr::launch_round_cx(h->h32.tspec, h->h64.tspec, (size_t)h->B * h->L, h->stream));
     if (h->h32.spec_rp != nullptr)
       MGWR_CK(h, mgwr::launch_spectra_rp(h->h32.spec_rp, h->h64.spec, (size_t)h->B * h->nlev,
-                                         h->M, h->stream));
+                                         h->M, false, h->stream));
     if (h->h32.tspec_rp != nullptr)
       MGWR_CK(h, mgwr::launch_spectra_rp(h->h32.tspec_rp, h->h64.tspec, (size_t)h->B, h->M,
-                                         h->stream));
+                                         true, h->stream));
     if (h->tc_band != nullptr)
       MGWR_CK(h, mgwr::launch_band_bf16x3(h->kcol, h->tc_band, h->M, (size_t)h->B * h->nlev,
                                           h->stream));

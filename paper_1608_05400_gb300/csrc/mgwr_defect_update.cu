@@ -141,17 +141,17 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<float>(BLOCK))
   if (norm_bits != nullptr) block_norm<BLOCK>((double)amax, red, norm_bits + blockIdx.y);
 }
 
-// The same on the register-pass engine (mgwr_fft_rp.cuh): tspec in that
-// engine's spectral order.
-template <class W, int LOGL, int R0, int R1, int R2, int T>
-__global__ void __launch_bounds__(kRpBlock, 2)
+// The same on the register-pass engine (mgwr_fft_rp.cuh, the carried defect's
+// plan table): tspec in that plan's spectral order.
+template <class W, int LOGL, int R0, int R1, int R2, int R3, int T>
+__global__ void __launch_bounds__(kRpBlock, (rp::Plan<LOGL, R0, R1, R2, R3, T>::MIN_BLOCKS))
     k_defect_update_rp(const float* __restrict__ e, const W* r_in, W* r_out,
                        float* __restrict__ r32, const Cx<float>* __restrict__ tspec,
                        const Cx<float>* __restrict__ tw, const float* __restrict__ zero, int d,
                        int n, int M, float hinv2, int npts, int npairs,
                        unsigned long long* __restrict__ norm_bits, size_t fstride,
                        size_t sstride) {
-  using P = rp::Plan<LOGL, R0, R1, R2, T>;
+  using P = rp::Plan<LOGL, R0, R1, R2, R3, T>;
   constexpr int PAIRS = kRpBlock / T;
   extern __shared__ unsigned char smem_raw[];
   __shared__ double red[kRpBlock / 32];
@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(kRpBlock, 2)
   const float* eA = valid ? store.e + store.pAM : zero;
   const float* eB = hasB ? store.e + store.pBM : zero;
   auto load = [&](int m) -> Cx<float> { return Cx<float>{eA[m], eB[m]}; };
-  rp::convolve<LOGL, R0, R1, R2, T, PAIRS>(buf, t, g, tspec, tw, load, store);
+  rp::convolve<LOGL, R0, R1, R2, R3, T, PAIRS>(buf, t, g, tspec, tw, load, store);
   if (norm_bits != nullptr) block_norm<kRpBlock>((double)amax, red, norm_bits + blockIdx.y);
 }
 
@@ -261,20 +261,20 @@ cudaError_t launch_defect_update_rp(const float* e, const W* r_in, W* r_out, flo
   const size_t fstride = ls.field_stride();
   cudaError_t err = cudaErrorInvalidValue;
   switch (ilog2(2 * M)) {
-#define MGWR_RP_UPDATE(LG, A, B, C, T)                                                          \
+#define MGWR_RP_UPDATE(LG, A, B, C, D, T)                                                        \
   case LG: {                                                                                    \
-    using P = rp::Plan<LG, A, B, C, T>;                                                         \
+    using P = rp::Plan<LG, A, B, C, D, T>;                                                         \
     const size_t smem = (size_t)(kRpBlock / T) * P::SMEM * sizeof(Cx<float>);                   \
-    err = prepare_smem(k_defect_update_rp<W, LG, A, B, C, T>, smem);                            \
+    err = prepare_smem(k_defect_update_rp<W, LG, A, B, C, D, T>, smem);                            \
     if (err != cudaSuccess) return err;                                                         \
     const dim3 grid((unsigned)((npairs + kRpBlock / T - 1) / (kRpBlock / T)),                   \
                     (unsigned)ls.batch);                                                        \
-    k_defect_update_rp<W, LG, A, B, C, T><<<grid, kRpBlock, smem, s>>>(                         \
+    k_defect_update_rp<W, LG, A, B, C, D, T><<<grid, kRpBlock, smem, s>>>(                         \
         e, r_in, r_out, r32, tspec, tw, zero, d, n, M, hinv2, npts, npairs, norm_bits, fstride, \
         spec_stride);                                                                           \
     break;                                                                                      \
   }
-    MGWR_RP_PLANS(MGWR_RP_UPDATE)
+    MGWR_RP_DEFECT_PLANS(MGWR_RP_UPDATE)
 #undef MGWR_RP_UPDATE
     default:
       break;

@@ -4,7 +4,7 @@
 // complex line of length L = 2M, zero upper half, spectrum product, first M
 // outputs of the inverse), organised for fewer instructions per value: each
 // pass of the decimation-in-frequency transform is one radix-R DFT of R <= 32
-// values held in registers (two or three passes instead of four or five
+// values held in registers (two to four passes instead of four or five
 // radix-8 stages), so every value crosses shared memory once per pass and the
 // inter-pass twiddles are applied only at pass boundaries.  The last pass
 // holds R contiguous positions per butterfly: the spectrum product and the
@@ -12,7 +12,7 @@
 // per R_last values, which makes every access of every pass conflict-free for
 // 8-byte elements (and its address a base plus an immediate offset).
 //
-// Plan (R0, R1[, R2]): pass p has radix R_p, stride S_p = G_p / R_p on groups of
+// Plan (R0, R1[, R2[, R3]]): pass p has radix R_p, stride S_p = G_p / R_p on groups of
 // G_p = L / (R_0 .. R_{p-1}) positions; butterfly j < S_p of a group reads
 // positions j + q S_p, applies the DFT and, except in the last pass, the
 // twiddles w_{G_p}^{j k}, and writes output k to j + k S_p.  Position
@@ -235,19 +235,24 @@ __device__ __forceinline__ void twiddle_apply(C (&v)[R], const TwBase<R>& tb) {
 }
 
 // Compile-time plan of a length-2^LOGL transform with radices R0, R1 and, when
-// R2 != 0, R2; T threads per line pair.
-template <int LOGL, int R0, int R1, int R2, int T>
+// not 0, R2 and R3; T threads per line pair.  Four-pass plans keep every radix
+// at most 16, so that a thread needs fewer registers and three blocks fit an
+// SM (MIN_BLOCKS), for one more pass through shared memory.
+template <int LOGL, int R0, int R1, int R2, int R3, int T>
 struct Plan {
   static constexpr int L = 1 << LOGL;
-  static constexpr int NP = R2 != 0 ? 3 : 2;
-  static constexpr int RL = R2 != 0 ? R2 : R1;  // radix of the last pass
+  static constexpr int NP = R3 != 0 ? 4 : R2 != 0 ? 3 : 2;
+  static constexpr int RL = NP == 4 ? R3 : NP == 3 ? R2 : R1;  // radix of the last pass
   static constexpr int LOG_RL = RL == 32 ? 5 : RL == 16 ? 4 : RL == 8 ? 3 : RL == 4 ? 2 : 1;
   static constexpr int S0 = L / R0;             // pass 0: one group of L
   static constexpr int G1 = S0, S1 = G1 / R1;   // pass 1
-  static constexpr int G2 = S1, S2 = G2 / (R2 != 0 ? R2 : 1);
+  static constexpr int G2 = S1, S2 = G2 / (R2 != 0 ? R2 : 1);  // pass 2
   static constexpr int SMEM = L + L / RL;       // padded complex slots per line pair
-  static_assert(R0 * R1 * (R2 != 0 ? R2 : 1) == L, "radices must multiply to L");
-  static_assert((L / R0) % T == 0 && (L / R1) % T == 0 && (L / RL) % T == 0,
+  static constexpr int MIN_BLOCKS = NP == 4 ? 3 : 2;
+  static_assert(R0 * R1 * (R2 != 0 ? R2 : 1) * (R3 != 0 ? R3 : 1) == L,
+                "radices must multiply to L");
+  static_assert((L / R0) % T == 0 && (L / R1) % T == 0 && (L / RL) % T == 0 &&
+                    (L / (R2 != 0 ? R2 : 1)) % T == 0,
                 "every pass must give each thread the same number of butterflies");
   static __device__ __forceinline__ int idx(int p) { return p + (p >> LOG_RL); }
 };
@@ -264,6 +269,50 @@ __device__ __forceinline__ void group_sync(int g) {
   }
 }
 
+// A middle pass (neither the first nor the last): radix R butterflies on
+// groups of G positions with stride S, twiddles w_G^{jk} = w_L^{j k TWS}
+// (TWS = L / G) after the forward DFT, before the inverse one; then the
+// group's barrier.
+template <class P, int R, int G, int S, int TWS, bool INV, int T, int PAIRS>
+__device__ __forceinline__ void mid_pass(C* buf, int t, int g, const C* __restrict__ tw) {
+  constexpr int NB = (P::L / R) / T;
+#pragma unroll 1
+  for (int i = 0; i < NB; ++i) {
+    const int beta = t + T * i;
+    const int grp = beta / S, j = beta - grp * S;
+    const int base = grp * G + j;
+    const TwBase<R> tb(tw, j * TWS);
+    C v[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) v[q] = buf[P::idx(base + q * S)];
+    if constexpr (INV) {
+      twiddle_apply<R, true>(v, tb);
+      Dft<R, true>::run(v);
+    } else {
+      Dft<R, false>::run(v);
+      twiddle_apply<R, false>(v, tb);
+    }
+#pragma unroll
+    for (int q = 0; q < R; ++q) buf[P::idx(base + q * S)] = v[q];
+  }
+  group_sync<T, PAIRS>(g);
+}
+
+// The forward middle passes of plan P (pass 1 of three- and four-pass plans,
+// pass 2 of four-pass ones), and their inverses in reverse order.
+template <class P, int R0, int R1, int R2, int T, int PAIRS>
+__device__ __forceinline__ void mid_passes_forward(C* buf, int t, int g, const C* __restrict__ tw) {
+  if constexpr (P::NP >= 3) mid_pass<P, R1, P::G1, P::S1, R0, false, T, PAIRS>(buf, t, g, tw);
+  if constexpr (P::NP == 4)
+    mid_pass<P, R2, P::G2, P::S2, R0 * R1, false, T, PAIRS>(buf, t, g, tw);
+}
+template <class P, int R0, int R1, int R2, int T, int PAIRS>
+__device__ __forceinline__ void mid_passes_inverse(C* buf, int t, int g, const C* __restrict__ tw) {
+  if constexpr (P::NP == 4)
+    mid_pass<P, R2, P::G2, P::S2, R0 * R1, true, T, PAIRS>(buf, t, g, tw);
+  if constexpr (P::NP >= 3) mid_pass<P, R1, P::G1, P::S1, R0, true, T, PAIRS>(buf, t, g, tw);
+}
+
 // One line pair's causal convolution by the T threads t of group g: the first
 // M = L/2 values of IFFT(FFT(x) * spec), x zero-padded to L.  load(m) gives
 // the pair's input at time m < M (both lines as one complex value; every call
@@ -271,10 +320,10 @@ __device__ __forceinline__ void group_sync(int g) {
 // store(m, y) receives output m < M.  spec: the kernel's spectrum in this
 // plan's spectral order, pre-scaled by 1/L; tw[e] = w_L^e.  buf: P::SMEM
 // complex values of shared memory for the group.
-template <int LOGL, int R0, int R1, int R2, int T, int PAIRS, class Load, class Store>
+template <int LOGL, int R0, int R1, int R2, int R3, int T, int PAIRS, class Load, class Store>
 __device__ __forceinline__ void convolve(C* buf, int t, int g, const C* __restrict__ spec,
                                          const C* __restrict__ tw, Load load, Store store) {
-  using P = Plan<LOGL, R0, R1, R2, T>;
+  using P = Plan<LOGL, R0, R1, R2, R3, T>;
   // ---- pass 0: every input of the thread, then half-input DFTs and twiddles
   constexpr int NB0 = P::S0 / T;
   C in[NB0][R0 / 2];
@@ -297,25 +346,8 @@ __device__ __forceinline__ void convolve(C* buf, int t, int g, const C* __restri
   }
   group_sync<T, PAIRS>(g);
 
-  // ---- pass 1 when there are three: radix R1 on groups of G1, twiddles w_G1^{jk}
-  if constexpr (P::NP == 3) {
-    constexpr int NB1 = (P::L / R1) / T;
-#pragma unroll 1
-    for (int i = 0; i < NB1; ++i) {
-      const int beta = t + T * i;
-      const int grp = beta / P::S1, j = beta - grp * P::S1;
-      const int base = grp * P::G1 + j;
-      const TwBase<R1> tb(tw, j * R0);
-      C v[R1];
-#pragma unroll
-      for (int q = 0; q < R1; ++q) v[q] = buf[P::idx(base + q * P::S1)];
-      Dft<R1, false>::run(v);
-      twiddle_apply<R1, false>(v, tb);
-#pragma unroll
-      for (int q = 0; q < R1; ++q) buf[P::idx(base + q * P::S1)] = v[q];
-    }
-    group_sync<T, PAIRS>(g);
-  }
+  // ---- the middle passes: radix R1 (and R2) on groups of G1 (G2), twiddles w_G^{jk}
+  mid_passes_forward<P, R0, R1, R2, T, PAIRS>(buf, t, g, tw);
 
   // ---- last pass (contiguous RL values), spectrum product, its inverse
   constexpr int RL = P::RL;
@@ -340,25 +372,8 @@ __device__ __forceinline__ void convolve(C* buf, int t, int g, const C* __restri
   }
   group_sync<T, PAIRS>(g);
 
-  // ---- inverse of pass 1
-  if constexpr (P::NP == 3) {
-    constexpr int NB1 = (P::L / R1) / T;
-#pragma unroll 1
-    for (int i = 0; i < NB1; ++i) {
-      const int beta = t + T * i;
-      const int grp = beta / P::S1, j = beta - grp * P::S1;
-      const int base = grp * P::G1 + j;
-      const TwBase<R1> tb(tw, j * R0);
-      C v[R1];
-#pragma unroll
-      for (int q = 0; q < R1; ++q) v[q] = buf[P::idx(base + q * P::S1)];
-      twiddle_apply<R1, true>(v, tb);
-      Dft<R1, true>::run(v);
-#pragma unroll
-      for (int q = 0; q < R1; ++q) buf[P::idx(base + q * P::S1)] = v[q];
-    }
-    group_sync<T, PAIRS>(g);
-  }
+  // ---- inverses of the middle passes
+  mid_passes_inverse<P, R0, R1, R2, T, PAIRS>(buf, t, g, tw);
 
   // ---- inverse of pass 0: the first M outputs
 #pragma unroll 1
@@ -389,10 +404,10 @@ struct Pair2 {
 // accesses.  spec: the kernel's spectrum in this
 // plan's spectral order, pre-scaled by 1/L; tw[e] = w_L^e.  buf: P::SMEM
 // complex values of shared memory for the group.
-template <int LOGL, int R0, int R1, int R2, int T, int PAIRS, class Load2, class Store2>
+template <int LOGL, int R0, int R1, int R2, int R3, int T, int PAIRS, class Load2, class Store2>
 __device__ __forceinline__ void convolve2(C* buf, int t, int g, const C* __restrict__ spec,
                                           const C* __restrict__ tw, Load2 load2, Store2 store2) {
-  using P = Plan<LOGL, R0, R1, R2, T>;
+  using P = Plan<LOGL, R0, R1, R2, R3, T>;
   // ---- pass 0: every input of the thread, then half-input DFTs and twiddles
   constexpr int NB0 = P::S0 / T;
   static_assert(NB0 % 2 == 0, "the first pass takes butterflies in adjacent pairs");
@@ -416,25 +431,8 @@ __device__ __forceinline__ void convolve2(C* buf, int t, int g, const C* __restr
   }
   group_sync<T, PAIRS>(g);
 
-  // ---- pass 1 when there are three: radix R1 on groups of G1, twiddles w_G1^{jk}
-  if constexpr (P::NP == 3) {
-    constexpr int NB1 = (P::L / R1) / T;
-#pragma unroll 1
-    for (int i = 0; i < NB1; ++i) {
-      const int beta = t + T * i;
-      const int grp = beta / P::S1, j = beta - grp * P::S1;
-      const int base = grp * P::G1 + j;
-      const TwBase<R1> tb(tw, j * R0);
-      C v[R1];
-#pragma unroll
-      for (int q = 0; q < R1; ++q) v[q] = buf[P::idx(base + q * P::S1)];
-      Dft<R1, false>::run(v);
-      twiddle_apply<R1, false>(v, tb);
-#pragma unroll
-      for (int q = 0; q < R1; ++q) buf[P::idx(base + q * P::S1)] = v[q];
-    }
-    group_sync<T, PAIRS>(g);
-  }
+  // ---- the middle passes: radix R1 (and R2) on groups of G1 (G2), twiddles w_G^{jk}
+  mid_passes_forward<P, R0, R1, R2, T, PAIRS>(buf, t, g, tw);
 
   // ---- last pass (contiguous RL values), spectrum product, its inverse
   constexpr int RL = P::RL;
@@ -459,25 +457,8 @@ __device__ __forceinline__ void convolve2(C* buf, int t, int g, const C* __restr
   }
   group_sync<T, PAIRS>(g);
 
-  // ---- inverse of pass 1
-  if constexpr (P::NP == 3) {
-    constexpr int NB1 = (P::L / R1) / T;
-#pragma unroll 1
-    for (int i = 0; i < NB1; ++i) {
-      const int beta = t + T * i;
-      const int grp = beta / P::S1, j = beta - grp * P::S1;
-      const int base = grp * P::G1 + j;
-      const TwBase<R1> tb(tw, j * R0);
-      C v[R1];
-#pragma unroll
-      for (int q = 0; q < R1; ++q) v[q] = buf[P::idx(base + q * P::S1)];
-      twiddle_apply<R1, true>(v, tb);
-      Dft<R1, true>::run(v);
-#pragma unroll
-      for (int q = 0; q < R1; ++q) buf[P::idx(base + q * P::S1)] = v[q];
-    }
-    group_sync<T, PAIRS>(g);
-  }
+  // ---- inverses of the middle passes
+  mid_passes_inverse<P, R0, R1, R2, T, PAIRS>(buf, t, g, tw);
 
   // ---- inverse of pass 0: the first M outputs, two adjacent butterflies at a time
 #pragma unroll 1
@@ -502,32 +483,55 @@ __device__ __forceinline__ void convolve2(C* buf, int t, int g, const C* __restr
 
 }  // namespace rp
 
-// Radix plans per transform length (L = 2^7 .. 2^13): two or three passes,
-// the last of radix 32; T threads per line pair, 256 threads per block.
-#define MGWR_RP_PLANS(X)      \
-  X(13, 16, 16, 32, 256)      \
-  X(12, 8, 16, 32, 128)       \
-  X(11, 8, 8, 32, 64)         \
-  X(10, 8, 4, 32, 32)         \
-  X(9, 16, 32, 0, 16)         \
-  X(8, 8, 32, 0, 8)           \
-  X(7, 4, 32, 0, 4)
+// Radix plans per transform length (L = 2^7 .. 2^13): two to four passes,
+// (LOGL, R0, R1, R2, R3, T), T threads per line pair, 256 threads per block.
+// The sweeps take two or three passes, the last of radix 32.  The carried
+// outer defect (launch_defect_update_rp), whose store phase is heavier, takes
+// four passes of radix <= 16 at L = 8192 (80 registers: three blocks per SM
+// instead of two; 12.8 against 17.2 ms on 2-D 511 x 511, M = 4096, where the
+// sweep measured 4.1 against 3.2 ms per half-sweep).
+#define MGWR_RP_PLANS(X)        \
+  X(13, 16, 16, 32, 0, 256)     \
+  X(12, 8, 16, 32, 0, 128)      \
+  X(11, 8, 8, 32, 0, 64)        \
+  X(10, 8, 4, 32, 0, 32)        \
+  X(9, 16, 32, 0, 0, 16)        \
+  X(8, 8, 32, 0, 0, 8)          \
+  X(7, 4, 32, 0, 0, 4)
+#define MGWR_RP_DEFECT_PLANS(X) \
+  X(13, 8, 8, 8, 16, 256)       \
+  X(12, 8, 16, 32, 0, 128)      \
+  X(11, 8, 8, 32, 0, 64)        \
+  X(10, 8, 4, 32, 0, 32)        \
+  X(9, 16, 32, 0, 0, 16)        \
+  X(8, 8, 32, 0, 0, 8)          \
+  X(7, 4, 32, 0, 0, 4)
 
 constexpr int kRpBlock = 256;  // threads per block of every register-pass kernel
 
-__host__ __device__ inline int rp_plan(int logL, int* r) {
+// Radices of the plan for length 2^logL into r[0..4) (the carried defect's
+// table when `defect`); returns their count, 0 for a length without a plan.
+__host__ __device__ inline int rp_plan(int logL, int* r, bool defect = false) {
+#define MGWR_RP_PLAN_CASE(LG, A, B, C, D, T) \
+  case LG:                                   \
+    r[0] = A;                                \
+    r[1] = B;                                \
+    r[2] = C;                                \
+    r[3] = D;                                \
+    return D != 0 ? 4 : C != 0 ? 3 : 2;
+  if (defect) {
+    switch (logL) {
+      MGWR_RP_DEFECT_PLANS(MGWR_RP_PLAN_CASE)
+      default:
+        return 0;
+    }
+  }
   switch (logL) {
-#define MGWR_RP_PLAN_CASE(LG, A, B, C, T) \
-  case LG:                                \
-    r[0] = A;                             \
-    r[1] = B;                             \
-    r[2] = C;                             \
-    return C != 0 ? 3 : 2;
     MGWR_RP_PLANS(MGWR_RP_PLAN_CASE)
-#undef MGWR_RP_PLAN_CASE
     default:
       return 0;
   }
+#undef MGWR_RP_PLAN_CASE
 }
 
 // Radices of the shared-memory engine of mgwr_fft.cuh for length 2^logL:

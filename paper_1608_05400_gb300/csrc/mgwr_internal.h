@@ -148,9 +148,10 @@ cudaError_t launch_sweep_rp(const float* f, float* u, float* delta, const Cx<flo
                             cudaStream_t s);
 // dst[c L ..] = the FP64 spectra src[c L ..] (length L = 2M, the shared-memory
 // engine's order) rounded to FP32 and permuted into the register-pass engine's
-// order, for `lines` lines.
+// order (the sweeps' plans, or the carried defect's when `defect`), for
+// `lines` lines.
 cudaError_t launch_spectra_rp(Cx<float>* dst, const Cx<double>* src, size_t lines, int M,
-                              cudaStream_t s);
+                              bool defect, cudaStream_t s);
 
 // Defect after a red-black step from the black half-sweep's delta: r = 0 on the
 // black points, r = hinv2 * sum of neighbour deltas on the red points

@@ -10,13 +10,13 @@ namespace {
 // PAIRED: the first pass takes adjacent butterflies two at a time, with 8-byte
 // gathers and stores (rp::convolve2), else one at a time (rp::convolve); the
 // tuner picks per level (faster for 256-step lines, slower for 1024 and 4096).
-template <int LOGL, int R0, int R1, int R2, int T, bool PAIRED>
-__global__ void __launch_bounds__(kRpBlock, 2)
+template <int LOGL, int R0, int R1, int R2, int R3, int T, bool PAIRED>
+__global__ void __launch_bounds__(kRpBlock, (rp::Plan<LOGL, R0, R1, R2, R3, T>::MIN_BLOCKS))
     k_sweep_rp(const float* __restrict__ f, float* __restrict__ u, float* __restrict__ delta,
                const Cx<float>* __restrict__ spec, const Cx<float>* __restrict__ tw,
                const float* __restrict__ zero, int d, int n, int M, int par, float hinv2,
                int npts, int npairs, size_t fstride, size_t sstride) {
-  using P = rp::Plan<LOGL, R0, R1, R2, T>;
+  using P = rp::Plan<LOGL, R0, R1, R2, R3, T>;
   using C = Cx<float>;
   constexpr int PAIRS = kRpBlock / T;
   extern __shared__ unsigned char smem_raw[];
@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(kRpBlock, 2)
         }
       }
     };
-    rp::convolve<LOGL, R0, R1, R2, T, PAIRS>(buf, t, g, spec, tw, load, store);
+    rp::convolve<LOGL, R0, R1, R2, R3, T, PAIRS>(buf, t, g, spec, tw, load, store);
     return;
   }
   // times m and m + 1 (m even) of a line as one 8-byte load
@@ -102,16 +102,17 @@ __global__ void __launch_bounds__(kRpBlock, 2)
       }
     }
   };
-  rp::convolve2<LOGL, R0, R1, R2, T, PAIRS>(buf, t, g, spec, tw, load2, store2);
+  rp::convolve2<LOGL, R0, R1, R2, R3, T, PAIRS>(buf, t, g, spec, tw, load2, store2);
 }
 
 // spec_rp[c L + rp position of k] = (float) spec64[c L + engine position of k]
+// (rp positions of the sweeps' plans, or of the carried defect's when `defect`)
 __global__ void k_spectra_rp(Cx<float>* __restrict__ dst, const Cx<double>* __restrict__ src,
-                             size_t lines, int logL) {
+                             size_t lines, int logL, bool defect) {
   const int L = 1 << logL;
-  int re[16], rr[3];
+  int re[16], rr[4];
   const int ne = engine_plan(logL, re);
-  const int nr = rp_plan(logL, rr);
+  const int nr = rp_plan(logL, rr, defect);
   const size_t total = lines * (size_t)L;
   for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < total;
        x += (size_t)gridDim.x * blockDim.x) {
@@ -122,16 +123,16 @@ __global__ void k_spectra_rp(Cx<float>* __restrict__ dst, const Cx<double>* __re
   }
 }
 
-template <int LOGL, int R0, int R1, int R2, int T, bool PAIRED>
+template <int LOGL, int R0, int R1, int R2, int R3, int T, bool PAIRED>
 cudaError_t sweep_rp_launch(dim3 grid, cudaStream_t s, const float* f, float* u, float* delta,
                             const Cx<float>* spec, const Cx<float>* tw, const float* zero, int d,
                             int n, int M, int par, float hinv2, int npts, int npairs,
                             size_t fstride, size_t sstride) {
-  using P = rp::Plan<LOGL, R0, R1, R2, T>;
+  using P = rp::Plan<LOGL, R0, R1, R2, R3, T>;
   const size_t smem = (size_t)(kRpBlock / T) * P::SMEM * sizeof(Cx<float>);
-  cudaError_t e = prepare_smem(k_sweep_rp<LOGL, R0, R1, R2, T, PAIRED>, smem);
+  cudaError_t e = prepare_smem(k_sweep_rp<LOGL, R0, R1, R2, R3, T, PAIRED>, smem);
   if (e != cudaSuccess) return e;
-  k_sweep_rp<LOGL, R0, R1, R2, T, PAIRED><<<grid, kRpBlock, smem, s>>>(
+  k_sweep_rp<LOGL, R0, R1, R2, R3, T, PAIRED><<<grid, kRpBlock, smem, s>>>(
       f, u, delta, spec, tw, zero, d, n, M, par, hinv2, npts, npairs, fstride, sstride);
   return cudaSuccess;
 }
@@ -151,15 +152,17 @@ cudaError_t launch_sweep_rp(const float* f, float* u, float* delta, const Cx<flo
   const size_t fstride = ls.field_stride();
   cudaError_t e = cudaErrorInvalidValue;
   switch (logL) {
-#define MGWR_RP_LAUNCH(LG, A, B, C, T)                                                       \
+#define MGWR_RP_LAUNCH(LG, A, B, C, D, T)                                                    \
   case LG: {                                                                                 \
     const dim3 grid((unsigned)((npairs + kRpBlock / T - 1) / (kRpBlock / T)), (unsigned)ls.batch); \
     if (paired)                                                                              \
-      e = sweep_rp_launch<LG, A, B, C, T, true>(grid, s, f, u, delta, spec, tw, zero, d, n, M,  \
-                                                par, hinv2, npts, npairs, fstride, spec_stride); \
+      e = sweep_rp_launch<LG, A, B, C, D, T, true>(grid, s, f, u, delta, spec, tw, zero, d, n,  \
+                                                   M, par, hinv2, npts, npairs, fstride,     \
+                                                   spec_stride);                             \
     else                                                                                     \
-      e = sweep_rp_launch<LG, A, B, C, T, false>(grid, s, f, u, delta, spec, tw, zero, d, n, M, \
-                                                 par, hinv2, npts, npairs, fstride, spec_stride); \
+      e = sweep_rp_launch<LG, A, B, C, D, T, false>(grid, s, f, u, delta, spec, tw, zero, d, n, \
+                                                    M, par, hinv2, npts, npairs, fstride,    \
+                                                    spec_stride);                            \
     break;                                                                                   \
   }
     MGWR_RP_PLANS(MGWR_RP_LAUNCH)
@@ -172,10 +175,10 @@ cudaError_t launch_sweep_rp(const float* f, float* u, float* delta, const Cx<flo
 }
 
 cudaError_t launch_spectra_rp(Cx<float>* dst, const Cx<double>* src, size_t lines, int M,
-                              cudaStream_t s) {
+                              bool defect, cudaStream_t s) {
   if (!radix_length(M)) return cudaErrorInvalidValue;
   const size_t total = lines * 2 * (size_t)M;
-  k_spectra_rp<<<elementwise_grid(total), 256, 0, s>>>(dst, src, lines, ilog2(2 * M));
+  k_spectra_rp<<<elementwise_grid(total), 256, 0, s>>>(dst, src, lines, ilog2(2 * M), defect);
   return counted(cudaGetLastError());
 }
 

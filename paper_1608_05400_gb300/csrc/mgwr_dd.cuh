@@ -44,6 +44,24 @@ __device__ __forceinline__ dd dd_split_fast(double x) {
   return dd(__double2float_rn(x), 0.f);
 }
 
+// The same pair with no FP64 arithmetic at all, for 2^-74 <= |x| < 2^128: hi as
+// in dd_split_fast, lo = the 29 cleared bits as an integer, converted to FP32
+// (rounded to 24 bits) and scaled by the exact power of two 2^(e - 1075), with
+// x's sign: x - (hi + lo) below 2^-48 |x| as there.  Other x take
+// dd_split_fast.
+__device__ __forceinline__ dd dd_split_int(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF);
+  if (e >= 949 && e <= 1150) {
+    const unsigned hb = ((unsigned)(b >> 32) & 0x80000000u) | ((unsigned)(e - 896) << 23) |
+                        ((unsigned)(b >> 29) & 0x7FFFFFu);
+    const float scale = __int_as_float((e - 1075 + 127) << 23);  // 2^(e - 1075), normal
+    const float mag = __fmul_rn(__uint2float_rn((unsigned)(b & 0x1FFFFFFFull)), scale);
+    return dd(__uint_as_float(hb), (b >> 63) ? -mag : mag);
+  }
+  return dd_split_fast(x);
+}
+
 // s + e = a + b exactly (TwoSum, any a, b)
 __device__ __forceinline__ dd dd_two_sum(float a, float b) {
   const float s = __fadd_rn(a, b);

@@ -14,11 +14,11 @@ namespace mgwr {
 // ---------------------------------------------------------------------------------
 
 // The defect's value in the output type: a conversion, or for an FP64 defect
-// kept in double-float the split that spends two FP64-pipe operations, not four.
+// kept in double-float the split without FP64 arithmetic (dd_split_int).
 template <class RO, class R>
 __device__ __forceinline__ RO out_value(R x) {
   if constexpr (std::is_same<RO, dd>::value && std::is_same<R, double>::value)
-    return dd_split_fast(x);
+    return dd_split_int(x);
   else
     return RO(x);
 }

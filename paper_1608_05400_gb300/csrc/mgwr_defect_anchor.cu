@@ -1,17 +1,18 @@
-// Full outer defect of MGWR_MIXED in a cheaper arithmetic, for the steps that
-// renew the anchor of the carried defects (launch_defect_update) rather than
-// decide the solve's stop: r = (f - A_h u) - T_M u of the FP64 iterate u, with
-// the stencil, the source and the subtractions in FP64 (exact differences
-// first, as in the FP64 defect) and T_M u by a double-float FFT convolution of
-// u split into double-float pairs (dd_split_fast).  The split drops u's last
-// five bits (2^-48 |u|, far below the convolution's own error) and only
-// reaches T_M u, not the stencil, so the defect errs by about 2^-44 of
-// |T_M u|: a few 1e-14 of the right-hand side's scale, on any grid.  GB300 runs
-// double-float butterflies (FP32 pipes) several times faster than FP64 ones
-// (1/64 of the FP32 rate); the FP64 work left is about twelve operations per
-// value (two splits, the stencil's seven sums, one fused multiply-add), and
-// the norm is taken on the FP32 leading part (it plans the next steps; no
-// stop is decided on it).
+// Full outer defect of MGWR_MIXED in a cheaper arithmetic, for solves to
+// tolerances of at least 1e-10: the anchors of the carried defects
+// (launch_defect_update) and the defects that decide the stop.
+// r = (f - A_h u) - T_M u of the FP64 iterate u, with the stencil, the source
+// and the subtractions in FP64 (exact differences first, as in the FP64
+// defect) and T_M u by a double-float FFT convolution of u split into
+// double-float pairs (dd_split_int).  The split drops u's last five bits
+// (2^-48 |u|, far below the convolution's own error) and only reaches T_M u,
+// not the stencil, so the defect errs by about 2^-44 of |T_M u|: a few 1e-14 of
+// the right-hand side's scale, on any grid.  GB300 runs double-float
+// butterflies (FP32 pipes) several times faster than FP64 ones (1/64 of the
+// FP32 rate); the FP64 work left is eight operations per value (the stencil's
+// seven sums and one fused multiply-add; the splits use integer and FP32
+// operations).  The norm is that of the FP32 leading words, within 2^-24 of
+// the defect's own.
 #include "mgwr_common.cuh"
 
 namespace mgwr {
@@ -47,7 +48,7 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<dd>(BLOCK))
   const int iB = d == 1 ? pB : pB % n, jB = d == 1 ? 0 : pB / n;
   const double* uA = valid ? u + pAM : zero;
   const double* uB = hasB ? u + pBM : zero;
-  auto load = [&](int m) -> Cx<dd> { return Cx<dd>{dd_split_fast(uA[m]), dd_split_fast(uB[m])}; };
+  auto load = [&](int m) -> Cx<dd> { return Cx<dd>{dd_split_int(uA[m]), dd_split_int(uB[m])}; };
   Cx<dd> v[1][8];
   fft_forward<1>(buf, t, sh, tw, load, v, sync);
 #pragma unroll
@@ -58,7 +59,7 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<dd>(BLOCK))
   // subtracted in double-float
   auto one = [&](size_t pM, int m, int i, int j, dd y, double up) {
     const double a = fma(-hinv2, stencil_differences(u, up, d, n, i, j, pM, M, m), f[pM + m]);
-    const dd rd = dd_add_accurate(dd_split_fast(a), -y);
+    const dd rd = dd_add_accurate(dd_split_int(a), -y);
     r[pM + m] = rd;
     r32[pM + m] = float(rd);
     amax = absmax_nan(fabsf(rd.hi), amax);

@@ -229,7 +229,11 @@ int mgwr_set_outer_switch(mgwr_t h, double rel);
  * per pass.  Results agree with the other engine's to FP32 rounding, not
  * bitwise.  2 | MGWR_SPLIT_RADIX takes the first pass's adjacent butterflies
  * two at a time, with 8-byte global loads and stores (the same arithmetic;
- * results agree to FP32 rounding).  Other lengths fall back to the FFT engine. */
+ * results agree to FP32 rounding).  4 | MGWR_SPLIT_RADIX runs that paired form
+ * with resident blocks (one 512-thread block per SM, looping over the line
+ * pairs) that keep the spectrum and the twiddle bases in shared memory; its
+ * results are bitwise those of 2 | MGWR_SPLIT_RADIX.  Other lengths fall back
+ * to the FFT engine. */
 #define MGWR_SPLIT_RADIX 64
 int mgwr_set_engine_split(mgwr_t h, int kernel_class, int level, int split);
 int mgwr_get_engine_split(mgwr_t h, int kernel_class, int level, int* split);

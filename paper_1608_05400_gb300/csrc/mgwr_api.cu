@@ -456,7 +456,7 @@ cudaError_t level_sweep(mgwr_t h, Hier<R>& H, int l, const R* f, R* u, R* delta,
     if ((eff & mgwr::kRadix) && H.spec_rp != nullptr)
       return mgwr::launch_sweep_rp(f, u, delta, H.spec_rp + (size_t)l * h->L,
                                    (size_t)h->nlev * h->L, H.tw, H.zero, ls, par,
-                                   (float)h->hinv2[l], (eff & ~mgwr::kRadix) == 2, h->stream);
+                                   (float)h->hinv2[l], eff & ~mgwr::kRadix, h->stream);
   }
   return mgwr::launch_sweep<R>(f, u, delta, H.spec + (size_t)l * h->L, (size_t)h->nlev * h->L,
                                H.tw, H.zero, scratch_for<R>(h), ls, par, false, R(h->hinv2[l]),
@@ -989,9 +989,9 @@ template <class F>
 int tune_class(mgwr_t h, int cls, int l, int word, F launch) {
   int best = 1;
   float best_ms = 0.f;
-  const int cands[9] = {1, 2, 4, 1 | mgwr::kStaged, 2 | mgwr::kStaged, 4 | mgwr::kStaged,
-                        1 | mgwr::kTensor, 1 | mgwr::kRadix, 2 | mgwr::kRadix};
-  const int ncand = cls == MGWR_K_SWEEP32 ? 9 : 3;
+  const int cands[10] = {1, 2, 4, 1 | mgwr::kStaged, 2 | mgwr::kStaged, 4 | mgwr::kStaged,
+                         1 | mgwr::kTensor, 1 | mgwr::kRadix, 2 | mgwr::kRadix, 4 | mgwr::kRadix};
+  const int ncand = cls == MGWR_K_SWEEP32 ? 10 : 3;
   for (int c = 0; c < ncand; ++c) {
     const int E = cands[c];
     if (mgwr::effective_split(h->M, word, E) != E) continue;  // same launch as a smaller E

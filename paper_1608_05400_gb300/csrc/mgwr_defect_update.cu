@@ -184,7 +184,8 @@ __global__ void __launch_bounds__(kRpBlock, (rp::Plan<LOGL, R0, R1, R2, R3, T>::
   const float* eA = valid ? store.e + store.pAM : zero;
   const float* eB = hasB ? store.e + store.pBM : zero;
   auto load = [&](int m) -> Cx<float> { return Cx<float>{eA[m], eB[m]}; };
-  rp::convolve<LOGL, R0, R1, R2, R3, T, PAIRS>(buf, t, g, tspec, tw, load, store);
+  rp::convolve<LOGL, R0, R1, R2, R3, T, PAIRS>(buf, t, g, rp::GlobalTables{tw, tspec}, load,
+                                               store);
   if (norm_bits != nullptr) block_norm<kRpBlock>((double)amax, red, norm_bits + blockIdx.y);
 }
 

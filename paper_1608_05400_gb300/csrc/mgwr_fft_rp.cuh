@@ -186,6 +186,12 @@ template <int R>
 struct TwBase {
   static constexpr int RA = R > 8 ? 8 : R;
   static constexpr int RB = R / RA;
+  // rows of a table of the bases (b = 1, 2, 4, RA, 2 RA, those present)
+  static constexpr int I_H1 = 1 + (RA >= 4) + (RA >= 8);
+  static constexpr int NB = I_H1 + (RB >= 2) + (RB >= 4);
+  static constexpr int exponent(int i) {
+    return i < I_H1 ? (1 << i) : (i == I_H1 ? RA : 2 * RA);
+  }
   C a1, a2, a4, h1, h2;
   __device__ __forceinline__ TwBase(const C* __restrict__ tw, int e1) {
     a1 = tw[e1];
@@ -193,6 +199,15 @@ struct TwBase {
     if constexpr (RA >= 8) a4 = tw[4 * e1];
     if constexpr (RB >= 2) h1 = tw[RA * e1];
     if constexpr (RB >= 4) h2 = tw[2 * RA * e1];
+  }
+  // The same values from a table whose row i holds base i for butterflies j < S.
+  struct FromRows {};
+  __device__ __forceinline__ TwBase(FromRows, const C* tab, int j, int S) {
+    a1 = tab[j];
+    if constexpr (RA >= 4) a2 = tab[S + j];
+    if constexpr (RA >= 8) a4 = tab[2 * S + j];
+    if constexpr (RB >= 2) h1 = tab[I_H1 * S + j];
+    if constexpr (RB >= 4) h2 = tab[(I_H1 + 1) * S + j];
   }
 };
 
@@ -257,6 +272,97 @@ struct Plan {
   static __device__ __forceinline__ int idx(int p) { return p + (p >> LOG_RL); }
 };
 
+// Where a convolution takes its twiddle bases and spectrum from.  Global
+// tables (tw[e] = w_L^e; spectrum in the plan's spectral order) are read
+// through the caches by every butterfly.
+struct GlobalTables {
+  const C* __restrict__ tw;
+  const C* __restrict__ spec;
+  // bases of butterfly j of twiddled pass PASS (exponent stride TWS)
+  template <int PASS, int R, int TWS>
+  __device__ __forceinline__ TwBase<R> base(int j) const {
+    return TwBase<R>(tw, j * TWS);
+  }
+  // spectrum values 2q, 2q + 1 of last-pass butterfly beta (RL values each)
+  template <int RL>
+  __device__ __forceinline__ float4 spec2(int beta, int q) const {
+    return __ldg(reinterpret_cast<const float4*>(spec + (size_t)beta * RL) + q);
+  }
+};
+
+// The same values copied into shared memory once per block, for kernels whose
+// blocks stay resident and convolve many line pairs.  Twiddled pass p (all but
+// the last) has a table of TwBase<R_p>::NB rows of S_p values, row i holding
+// w_L^{b_i TWS_p j} for its butterflies j < S_p (b_i the exponents of the
+// bases); the spectrum is kept per last-pass butterfly, RL values followed by
+// one unused 16-byte slot, so that the 16-byte reads of a warp's 32
+// butterflies fall on distinct banks in every wavefront.
+template <int LOGL, int R0, int R1, int R2, int R3>
+struct SharedTables {
+  static constexpr int L = 1 << LOGL;
+  static constexpr int NP = R3 != 0 ? 4 : R2 != 0 ? 3 : 2;
+  static constexpr int RL = NP == 4 ? R3 : NP == 3 ? R2 : R1;
+  // butterflies per group and exponent strides of the twiddled passes
+  static constexpr int S0 = L / R0, TWS0 = 1;
+  static constexpr int S1 = NP >= 3 ? L / (R0 * R1) : 0, TWS1 = R0;
+  static constexpr int S2 = NP == 4 ? L / (R0 * R1 * R2) : 0, TWS2 = R0 * R1;
+  static constexpr int N0 = TwBase<R0>::NB * S0;
+  static constexpr int N1 = NP >= 3 ? TwBase<R1>::NB * S1 : 0;
+  static constexpr int N2 = NP == 4 ? TwBase<R2 != 0 ? R2 : 2>::NB * S2 : 0;
+  static constexpr int SPEC_ROW = RL / 2 + 1;             // float4 slots per butterfly
+  static constexpr int SPEC_F4 = (L / RL) * SPEC_ROW;
+  // bytes: spectrum (16-byte slots) first, then the twiddle rows
+  static constexpr size_t BYTES = (size_t)SPEC_F4 * 16 + (size_t)(N0 + N1 + N2) * sizeof(C);
+
+  const float4* sp;
+  const C* t0;
+  const C* t1;
+  const C* t2;
+
+  __device__ __forceinline__ explicit SharedTables(unsigned char* mem) {
+    sp = reinterpret_cast<const float4*>(mem);
+    t0 = reinterpret_cast<const C*>(mem + (size_t)SPEC_F4 * 16);
+    t1 = t0 + N0;
+    t2 = t1 + N1;
+  }
+
+  template <int R, int S, int TWS>
+  static __device__ __forceinline__ void fill_rows(C* dst, const C* __restrict__ tw, int tid,
+                                                   int nthr) {
+    for (int x = tid; x < TwBase<R>::NB * S; x += nthr) {
+      const int i = x / S, j = x - i * S;
+      dst[x] = tw[TwBase<R>::exponent(i) * TWS * j];
+    }
+  }
+  // Copies the tables from global memory (all threads of the block; the
+  // caller synchronises the block before the first use).
+  static __device__ __forceinline__ void fill(unsigned char* mem, const C* __restrict__ tw,
+                                              const C* __restrict__ spec, int tid, int nthr) {
+    float4* sd = reinterpret_cast<float4*>(mem);
+    const float4* ss = reinterpret_cast<const float4*>(spec);
+    for (int x = tid; x < (L / RL) * (RL / 2); x += nthr) {
+      const int beta = x / (RL / 2), q = x - beta * (RL / 2);
+      sd[beta * SPEC_ROW + q] = __ldg(ss + x);
+    }
+    C* d0 = reinterpret_cast<C*>(mem + (size_t)SPEC_F4 * 16);
+    fill_rows<R0, S0, TWS0>(d0, tw, tid, nthr);
+    if constexpr (NP >= 3) fill_rows<R1, S1, TWS1>(d0 + N0, tw, tid, nthr);
+    if constexpr (NP == 4) fill_rows<R2, S2, TWS2>(d0 + N0 + N1, tw, tid, nthr);
+  }
+
+  template <int PASS, int R, int TWS>
+  __device__ __forceinline__ TwBase<R> base(int j) const {
+    using FR = typename TwBase<R>::FromRows;
+    if constexpr (PASS == 0) return TwBase<R>(FR{}, t0, j, S0);
+    else if constexpr (PASS == 1) return TwBase<R>(FR{}, t1, j, S1);
+    else return TwBase<R>(FR{}, t2, j, S2);
+  }
+  template <int RL_>
+  __device__ __forceinline__ float4 spec2(int beta, int q) const {
+    return sp[beta * SPEC_ROW + q];
+  }
+};
+
 // Barrier of the T threads of one line pair (PAIRS pairs per block).
 template <int T, int PAIRS>
 __device__ __forceinline__ void group_sync(int g) {
@@ -273,15 +379,15 @@ __device__ __forceinline__ void group_sync(int g) {
 // groups of G positions with stride S, twiddles w_G^{jk} = w_L^{j k TWS}
 // (TWS = L / G) after the forward DFT, before the inverse one; then the
 // group's barrier.
-template <class P, int R, int G, int S, int TWS, bool INV, int T, int PAIRS>
-__device__ __forceinline__ void mid_pass(C* buf, int t, int g, const C* __restrict__ tw) {
+template <class P, int PASS, int R, int G, int S, int TWS, bool INV, int T, int PAIRS, class Tab>
+__device__ __forceinline__ void mid_pass(C* buf, int t, int g, const Tab& tab) {
   constexpr int NB = (P::L / R) / T;
 #pragma unroll 1
   for (int i = 0; i < NB; ++i) {
     const int beta = t + T * i;
     const int grp = beta / S, j = beta - grp * S;
     const int base = grp * G + j;
-    const TwBase<R> tb(tw, j * TWS);
+    const TwBase<R> tb = tab.template base<PASS, R, TWS>(j);
     C v[R];
 #pragma unroll
     for (int q = 0; q < R; ++q) v[q] = buf[P::idx(base + q * S)];
@@ -300,29 +406,30 @@ __device__ __forceinline__ void mid_pass(C* buf, int t, int g, const C* __restri
 
 // The forward middle passes of plan P (pass 1 of three- and four-pass plans,
 // pass 2 of four-pass ones), and their inverses in reverse order.
-template <class P, int R0, int R1, int R2, int T, int PAIRS>
-__device__ __forceinline__ void mid_passes_forward(C* buf, int t, int g, const C* __restrict__ tw) {
-  if constexpr (P::NP >= 3) mid_pass<P, R1, P::G1, P::S1, R0, false, T, PAIRS>(buf, t, g, tw);
+template <class P, int R0, int R1, int R2, int T, int PAIRS, class Tab>
+__device__ __forceinline__ void mid_passes_forward(C* buf, int t, int g, const Tab& tab) {
+  if constexpr (P::NP >= 3) mid_pass<P, 1, R1, P::G1, P::S1, R0, false, T, PAIRS>(buf, t, g, tab);
   if constexpr (P::NP == 4)
-    mid_pass<P, R2, P::G2, P::S2, R0 * R1, false, T, PAIRS>(buf, t, g, tw);
+    mid_pass<P, 2, R2, P::G2, P::S2, R0 * R1, false, T, PAIRS>(buf, t, g, tab);
 }
-template <class P, int R0, int R1, int R2, int T, int PAIRS>
-__device__ __forceinline__ void mid_passes_inverse(C* buf, int t, int g, const C* __restrict__ tw) {
+template <class P, int R0, int R1, int R2, int T, int PAIRS, class Tab>
+__device__ __forceinline__ void mid_passes_inverse(C* buf, int t, int g, const Tab& tab) {
   if constexpr (P::NP == 4)
-    mid_pass<P, R2, P::G2, P::S2, R0 * R1, true, T, PAIRS>(buf, t, g, tw);
-  if constexpr (P::NP >= 3) mid_pass<P, R1, P::G1, P::S1, R0, true, T, PAIRS>(buf, t, g, tw);
+    mid_pass<P, 2, R2, P::G2, P::S2, R0 * R1, true, T, PAIRS>(buf, t, g, tab);
+  if constexpr (P::NP >= 3) mid_pass<P, 1, R1, P::G1, P::S1, R0, true, T, PAIRS>(buf, t, g, tab);
 }
 
 // One line pair's causal convolution by the T threads t of group g: the first
 // M = L/2 values of IFFT(FFT(x) * spec), x zero-padded to L.  load(m) gives
 // the pair's input at time m < M (both lines as one complex value; every call
 // of the thread is made before its first DFT, so the loads overlap);
-// store(m, y) receives output m < M.  spec: the kernel's spectrum in this
-// plan's spectral order, pre-scaled by 1/L; tw[e] = w_L^e.  buf: P::SMEM
-// complex values of shared memory for the group.
-template <int LOGL, int R0, int R1, int R2, int R3, int T, int PAIRS, class Load, class Store>
-__device__ __forceinline__ void convolve(C* buf, int t, int g, const C* __restrict__ spec,
-                                         const C* __restrict__ tw, Load load, Store store) {
+// store(m, y) receives output m < M.  tab: the twiddle bases and the kernel's
+// spectrum (in this plan's spectral order, pre-scaled by 1/L; GlobalTables or
+// SharedTables).  buf: P::SMEM complex values of shared memory for the group.
+template <int LOGL, int R0, int R1, int R2, int R3, int T, int PAIRS, class Tab, class Load,
+          class Store>
+__device__ __forceinline__ void convolve(C* buf, int t, int g, const Tab& tab, Load load,
+                                         Store store) {
   using P = Plan<LOGL, R0, R1, R2, R3, T>;
   // ---- pass 0: every input of the thread, then half-input DFTs and twiddles
   constexpr int NB0 = P::S0 / T;
@@ -335,7 +442,7 @@ __device__ __forceinline__ void convolve(C* buf, int t, int g, const C* __restri
 #pragma unroll
   for (int i = 0; i < NB0; ++i) {
     const int j = t + T * i;
-    const TwBase<R0> tb(tw, j);
+    const TwBase<R0> tb = tab.template base<0, R0, 1>(j);
     C v[R0];
 #pragma unroll
     for (int q = 0; q < R0 / 2; ++q) v[q] = in[i][q];
@@ -347,7 +454,7 @@ __device__ __forceinline__ void convolve(C* buf, int t, int g, const C* __restri
   group_sync<T, PAIRS>(g);
 
   // ---- the middle passes: radix R1 (and R2) on groups of G1 (G2), twiddles w_G^{jk}
-  mid_passes_forward<P, R0, R1, R2, T, PAIRS>(buf, t, g, tw);
+  mid_passes_forward<P, R0, R1, R2, T, PAIRS>(buf, t, g, tab);
 
   // ---- last pass (contiguous RL values), spectrum product, its inverse
   constexpr int RL = P::RL;
@@ -359,10 +466,9 @@ __device__ __forceinline__ void convolve(C* buf, int t, int g, const C* __restri
 #pragma unroll
     for (int q = 0; q < RL; ++q) v[q] = buf[P::idx(base + q)];
     Dft<RL, false>::run(v);
-    const float4* sp = reinterpret_cast<const float4*>(spec + base);
 #pragma unroll
     for (int q = 0; q < RL / 2; ++q) {
-      const float4 s2 = __ldg(sp + q);
+      const float4 s2 = tab.template spec2<RL>(t + T * i, q);
       v[2 * q] = cmul(v[2 * q], C{s2.x, s2.y});
       v[2 * q + 1] = cmul(v[2 * q + 1], C{s2.z, s2.w});
     }
@@ -373,13 +479,13 @@ __device__ __forceinline__ void convolve(C* buf, int t, int g, const C* __restri
   group_sync<T, PAIRS>(g);
 
   // ---- inverses of the middle passes
-  mid_passes_inverse<P, R0, R1, R2, T, PAIRS>(buf, t, g, tw);
+  mid_passes_inverse<P, R0, R1, R2, T, PAIRS>(buf, t, g, tab);
 
   // ---- inverse of pass 0: the first M outputs
 #pragma unroll 1
   for (int i = 0; i < NB0; ++i) {
     const int j = t + T * i;
-    const TwBase<R0> tb(tw, j);
+    const TwBase<R0> tb = tab.template base<0, R0, 1>(j);
     C v[R0];
 #pragma unroll
     for (int k = 0; k < R0; ++k) v[k] = buf[P::idx(j + k * P::S0)];
@@ -398,15 +504,16 @@ struct Pair2 {
 // The same convolution with the first pass's butterflies taken two adjacent at
 // a time (j = 2 (t + T i) and j + 1), so that the inputs and outputs of a
 // thread come as pairs of consecutive times: load2(m) gives the inputs at m and
-// m + 1 (Pair2), store2(m, y0, y1) receives the outputs at m and m + 1; the
-// global accesses are then 8-byte vectors (half the load and store
-// instructions), for 2-way bank conflicts on the first pass's shared-memory
-// accesses.  spec: the kernel's spectrum in this
-// plan's spectral order, pre-scaled by 1/L; tw[e] = w_L^e.  buf: P::SMEM
-// complex values of shared memory for the group.
-template <int LOGL, int R0, int R1, int R2, int R3, int T, int PAIRS, class Load2, class Store2>
-__device__ __forceinline__ void convolve2(C* buf, int t, int g, const C* __restrict__ spec,
-                                          const C* __restrict__ tw, Load2 load2, Store2 store2) {
+// m + 1 (Pair2), store_all(j, y) receives the outputs of the butterflies j and
+// j + 1, y[h][q] at time j + h + q L / R0 (q < R0 / 2); the global accesses are
+// then 8-byte vectors (half the load and store instructions), for 2-way bank
+// conflicts on the first pass's shared-memory accesses.  tab: the twiddle
+// bases and the kernel's spectrum (in this plan's spectral order, pre-scaled
+// by 1/L).  buf: P::SMEM complex values of shared memory for the group.
+template <int LOGL, int R0, int R1, int R2, int R3, int T, int PAIRS, class Tab, class Load2,
+          class StoreAll>
+__device__ __forceinline__ void convolve2(C* buf, int t, int g, const Tab& tab, Load2 load2,
+                                          StoreAll store_all) {
   using P = Plan<LOGL, R0, R1, R2, R3, T>;
   // ---- pass 0: every input of the thread, then half-input DFTs and twiddles
   constexpr int NB0 = P::S0 / T;
@@ -420,7 +527,7 @@ __device__ __forceinline__ void convolve2(C* buf, int t, int g, const C* __restr
 #pragma unroll
   for (int i = 0; i < NB0; ++i) {
     const int j = 2 * (t + T * (i >> 1)) + (i & 1);
-    const TwBase<R0> tb(tw, j);
+    const TwBase<R0> tb = tab.template base<0, R0, 1>(j);
     C v[R0];
 #pragma unroll
     for (int q = 0; q < R0 / 2; ++q) v[q] = (i & 1) ? in[i >> 1][q].b : in[i >> 1][q].a;
@@ -432,7 +539,7 @@ __device__ __forceinline__ void convolve2(C* buf, int t, int g, const C* __restr
   group_sync<T, PAIRS>(g);
 
   // ---- the middle passes: radix R1 (and R2) on groups of G1 (G2), twiddles w_G^{jk}
-  mid_passes_forward<P, R0, R1, R2, T, PAIRS>(buf, t, g, tw);
+  mid_passes_forward<P, R0, R1, R2, T, PAIRS>(buf, t, g, tab);
 
   // ---- last pass (contiguous RL values), spectrum product, its inverse
   constexpr int RL = P::RL;
@@ -444,10 +551,9 @@ __device__ __forceinline__ void convolve2(C* buf, int t, int g, const C* __restr
 #pragma unroll
     for (int q = 0; q < RL; ++q) v[q] = buf[P::idx(base + q)];
     Dft<RL, false>::run(v);
-    const float4* sp = reinterpret_cast<const float4*>(spec + base);
 #pragma unroll
     for (int q = 0; q < RL / 2; ++q) {
-      const float4 s2 = __ldg(sp + q);
+      const float4 s2 = tab.template spec2<RL>(t + T * i, q);
       v[2 * q] = cmul(v[2 * q], C{s2.x, s2.y});
       v[2 * q + 1] = cmul(v[2 * q + 1], C{s2.z, s2.w});
     }
@@ -458,7 +564,7 @@ __device__ __forceinline__ void convolve2(C* buf, int t, int g, const C* __restr
   group_sync<T, PAIRS>(g);
 
   // ---- inverses of the middle passes
-  mid_passes_inverse<P, R0, R1, R2, T, PAIRS>(buf, t, g, tw);
+  mid_passes_inverse<P, R0, R1, R2, T, PAIRS>(buf, t, g, tab);
 
   // ---- inverse of pass 0: the first M outputs, two adjacent butterflies at a time
 #pragma unroll 1
@@ -467,7 +573,7 @@ __device__ __forceinline__ void convolve2(C* buf, int t, int g, const C* __restr
     C y[2][R0 / 2];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const TwBase<R0> tb(tw, j + h);
+      const TwBase<R0> tb = tab.template base<0, R0, 1>(j + h);
       C v[R0];
 #pragma unroll
       for (int k = 0; k < R0; ++k) v[k] = buf[P::idx(j + h + k * P::S0)];
@@ -476,8 +582,7 @@ __device__ __forceinline__ void convolve2(C* buf, int t, int g, const C* __restr
 #pragma unroll
       for (int q = 0; q < R0 / 2; ++q) y[h][q] = v[q];
     }
-#pragma unroll
-    for (int q = 0; q < R0 / 2; ++q) store2(j + q * P::S0, y[0][q], y[1][q]);
+    store_all(j, y);
   }
 }
 
@@ -507,7 +612,8 @@ __device__ __forceinline__ void convolve2(C* buf, int t, int g, const C* __restr
   X(8, 8, 32, 0, 0, 8)          \
   X(7, 4, 32, 0, 0, 4)
 
-constexpr int kRpBlock = 256;  // threads per block of every register-pass kernel
+constexpr int kRpBlock = 256;     // threads per block of the register-pass kernels
+constexpr int kRpResBlock = 512;  // and of the resident sweep (one block per SM)
 
 // Radices of the plan for length 2^logL into r[0..4) (the carried defect's
 // table when `defect`); returns their count, 0 for a length without a plan.

@@ -72,7 +72,7 @@ inline int effective_split(int M, int word, int E) {
   const int L = 2 * M;
   E = engine_split(L, E);
   if (word == 4 && (L < 128 || L > 8192)) return 1;
-  if (word == 4 && radix && radix_length(M)) return (E == 1 ? 1 : 2) | kRadix;
+  if (word == 4 && radix && radix_length(M)) return E | kRadix;
   if (word == 4 && tensor && tensor_length(M)) return 1 | kTensor;
   return word == 4 ? (E | staged) : E;
 }
@@ -142,9 +142,13 @@ cudaError_t take_tc_timeout(bool* hit);
 // Results agree with the shared-memory engine's to FP32 rounding, not bitwise.
 // paired: the first pass's adjacent butterflies two at a time with 8-byte
 // global accesses (the split's E: 1 | kRadix single, 2 | kRadix paired).
+// Forms of the register-pass sweep: first-pass butterflies one at a time,
+// two adjacent at a time (8-byte gathers and stores), or paired with resident
+// blocks holding the spectrum and twiddle bases in shared memory.
+constexpr int kRpSingle = 1, kRpPaired = 2, kRpResident = 4;
 cudaError_t launch_sweep_rp(const float* f, float* u, float* delta, const Cx<float>* spec,
                             size_t spec_stride, const Cx<float>* tw, const float* zero,
-                            const LevelShape& ls, int par, float hinv2, bool paired,
+                            const LevelShape& ls, int par, float hinv2, int form,
                             cudaStream_t s);
 // dst[c L ..] = the FP64 spectra src[c L ..] (length L = 2M, the shared-memory
 // engine's order) rounded to FP32 and permuted into the register-pass engine's

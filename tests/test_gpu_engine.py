@@ -295,10 +295,11 @@ def test_radix_sweep_agrees_with_the_fft_sweep(d, n, M, batch):
         assert rel(a, b) <= 2e-6, rel(a, b)
 
 
+@pytest.mark.parametrize("form", [1, 4])
 @pytest.mark.parametrize("d,n,M", [(1, 63, 64), (2, 15, 512), (2, 31, 2048), (2, 7, 4096)])
-def test_radix_sweep_matches_the_oracle(d, n, M):
+def test_radix_sweep_matches_the_oracle(d, n, M, form):
     W = omg.WRMG(d, n, M, 1.0, 0.45)
-    got, _ = _sweep32(d, n, M, 1 | G.MGWR_SPLIT_RADIX)
+    got, _ = _sweep32(d, n, M, form | G.MGWR_SPLIT_RADIX)
     N = n ** d
     u = inputs.random_field(N, M, seed=3)
     f = inputs.random_field(N, M, seed=4, scale=2.0 * d * (n + 1) ** 2)
@@ -358,6 +359,25 @@ def test_radix_paired_first_pass_matches_the_single_one(d, n, M, batch):
     assert (used_a, used_b) == (1 | G.MGWR_SPLIT_RADIX, 2 | G.MGWR_SPLIT_RADIX)
     for x, y in zip(a[:2], b[:2]):
         assert np.abs(x - y).max() <= 16 * 2.0 ** -24 * np.abs(x).max()
+
+
+# resident blocks: grids whose pairs take several rounds of the blocks (2-D
+# 63 x 63 at M = 2048 and 4096, 1-D 4095 at M = 256) and batches of more
+# instances than SMs (one block per instance)
+RESIDENT_SHAPES = RADIX_SHAPES + [(2, 63, 2048, 1), (2, 63, 4096, 1), (1, 4095, 256, 1),
+                                  (2, 15, 512, 200), (2, 7, 4096, 3)]
+
+
+@pytest.mark.parametrize("d,n,M,batch", RESIDENT_SHAPES)
+def test_radix_resident_sweep_is_the_paired_sweep(d, n, M, batch):
+    # 4 | MGWR_SPLIT_RADIX: the paired arithmetic, with the spectrum and the
+    # twiddle bases read from shared memory by blocks that loop over the line
+    # pairs: the same values in the same order, so the same bits, changes included
+    a, used_a = _sweep32(d, n, M, 2 | G.MGWR_SPLIT_RADIX, batch, delta=True)
+    b, used_b = _sweep32(d, n, M, 4 | G.MGWR_SPLIT_RADIX, batch, delta=True)
+    assert (used_a, used_b) == (2 | G.MGWR_SPLIT_RADIX, 4 | G.MGWR_SPLIT_RADIX)
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x, y)
 
 
 def test_peak_probe_measures_both_pipes():

@@ -102,11 +102,13 @@ SWEEP64_DRAM_BYTES_PER_LINE_M1024 = 23758.0
 # DRAM bytes per line of further kernels from single-kernel ncu captures (see
 # profiles/), by kernel class and M
 # (k_defect<double, float>: 1059.1 MB read + 254.9 MB written for 16,129 lines of 4096,
-# profiles/k_defect_fp64_outer_2d_127x127_M4096.md; k_sweep_rp with the paired first pass:
-# 264.5 + 102.9 MB for 8065 lines of 4096, profiles/k_sweep_rp_fp32_2d_127x127_M4096.md;
+# profiles/k_defect_fp64_outer_2d_127x127_M4096.md; k_sweep_rp_res, the resident paired
+# sweep: 264.5 + 102.2 MB for 8065 red lines, 396.6 + 218.7 MB for 8064 black lines that
+# record their changes, weighted as a V(1,1) cycle runs them per level (two red, one
+# recording black, one plain black), profiles/k_sweep_rp_res_fp32_2d_127x127_M4096.md;
 # k_defect_update_rp: 793.7 + 737.1 MB for 16,129 lines of 4096,
 # profiles/k_defect_outer_forms_2d_127x127_M4096.md)
-NCU_DRAM_BYTES_PER_LINE: dict = {"defect64": {4096: 81468.0}, "sweep32": {4096: 45546.0},
+NCU_DRAM_BYTES_PER_LINE: dict = {"defect64": {4096: 81468.0}, "sweep32": {4096: 53174.0},
                                  "defect32": {4096: 94908.0}}
 
 
@@ -1055,7 +1057,9 @@ def main():
     # name the FP32 sweep by the engine the tuner chose for the finest level
     sp = (main_arm["engine_splits"] or {}).get("sweep32")
     if sp:
-        eng = ("k_sweep_rp<float> (register-pass engine)" if sp[-1] & 64 else
+        eng = ("k_sweep_rp_res<float> (resident register-pass engine)"
+               if sp[-1] & 64 and sp[-1] & 7 == 4 else
+               "k_sweep_rp<float> (register-pass engine)" if sp[-1] & 64 else
                "k_sweep_tc (tensor cores)" if sp[-1] & 32 else
                "k_sweep_staged<float>" if sp[-1] & 16 else f"k_sweep<float> (E={sp[-1]})")
         for key in ("roofline", "roofline_sweep32"):

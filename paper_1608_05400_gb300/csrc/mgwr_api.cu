@@ -485,15 +485,17 @@ int smooth_colour(mgwr_t h, Hier<R>& H, int l, int colour) {
   return MGWR_OK;
 }
 
-// `steps` red-black smoothing steps; the last black half-sweep records its
-// changes so that the defect that follows needs no convolution.
+// `steps` red-black smoothing steps; with `record`, the last black half-sweep
+// records its changes so that a defect that follows needs no convolution
+// (without, the level's defect state is stale).
 template <class R>
-int smooth(mgwr_t h, Hier<R>& H, int l, int steps) {
+int smooth(mgwr_t h, Hier<R>& H, int l, int steps, bool record = true) {
   for (int s = 0; s < steps; ++s) {
     MGWR_TRY(sweep_colour(h, H, l, MGWR_RED, (R*)nullptr));
-    MGWR_TRY(sweep_colour(h, H, l, MGWR_BLACK, s == steps - 1 ? H.dl[l] : (R*)nullptr));
+    MGWR_TRY(sweep_colour(h, H, l, MGWR_BLACK,
+                          record && s == steps - 1 ? H.dl[l] : (R*)nullptr));
   }
-  if (steps > 0) H.rs[l] = R_DELTA;
+  if (steps > 0) H.rs[l] = record ? R_DELTA : R_STALE;
   return MGWR_OK;
 }
 
@@ -587,14 +589,20 @@ int defect_restrict(mgwr_t h, Hier<R>& H, int l) {
   return restrict_into(h, H, l, r);
 }
 
+// One cycle from level l.  `keep`: the post-smoothing records its changes for
+// a defect of level l that follows before any other smoothing of it.  Below
+// the top that happens only in cycles without pre-smoothing that visit a
+// level more than once (the next visit restricts the defect the last one
+// left); every other visit starts from a restricted right-hand side.
 template <class R>
-int cycle(mgwr_t h, Hier<R>& H, int l, int gamma, int nu1, int nu2) {
+int cycle(mgwr_t h, Hier<R>& H, int l, int gamma, int nu1, int nu2, bool keep = true) {
   if (l == 0) return coarsest(h, H);
   MGWR_TRY(smooth(h, H, l, nu1));
   MGWR_TRY(defect_restrict(h, H, l));
-  for (int g = 0; g < gamma; ++g) MGWR_TRY(cycle(h, H, l - 1, gamma, nu1, nu2));
+  for (int g = 0; g < gamma; ++g)
+    MGWR_TRY(cycle(h, H, l - 1, gamma, nu1, nu2, gamma > 1 && nu1 == 0));
   MGWR_TRY(prolong_into(h, H, l));
-  MGWR_TRY(smooth(h, H, l, nu2));
+  MGWR_TRY(smooth(h, H, l, nu2, keep));
   return MGWR_OK;
 }
 
@@ -800,7 +808,10 @@ int enqueue_iteration(mgwr_t h, int cyc, int nu1, int nu2, bool* exact, bool cop
     // double-float iterate, its double-float defect as the next right-hand side
     MGWR_CK(h, cudaMemsetAsync(h->hdd.u[L], 0, cnt * sizeof(mgwr::dd), h->stream));
     h->hdd.rs[L] = R_ZERO_U;
-    for (int k = 0; k < step_cycles(h); ++k) MGWR_TRY(cycle(h, h->hdd, L, cyc, nu1, nu2));
+    // the next inner cycle restricts the post-smoothing's defect only without
+    // pre-smoothing; after the last one the outer defect is computed in full
+    for (int k = 0; k < step_cycles(h); ++k)
+      MGWR_TRY(cycle(h, h->hdd, L, cyc, nu1, nu2, nu1 == 0 && k + 1 < step_cycles(h)));
     const int pm = prof_begin(h, MGWR_K_REFINE, (double)(points(h, L) * h->B));
     MGWR_CK(h, mgwr::launch_refine_dd2(h->u_dd, h->hdd.u[L], cnt, h->stream));
     prof_end(h, pm);
@@ -811,7 +822,8 @@ int enqueue_iteration(mgwr_t h, int cyc, int nu1, int nu2, bool* exact, bool cop
     const bool ddef = h->precision == MGWR_MIXED_DD;
     MGWR_CK(h, cudaMemsetAsync(h->h32.u[L], 0, cnt * sizeof(float), h->stream));
     h->h32.rs[L] = R_ZERO_U;  // f32 holds the outer defect, e32 = 0
-    for (int k = 0; k < step_cycles(h); ++k) MGWR_TRY(cycle(h, h->h32, L, cyc, nu1, nu2));
+    for (int k = 0; k < step_cycles(h); ++k)
+      MGWR_TRY(cycle(h, h->h32, L, cyc, nu1, nu2, nu1 == 0 && k + 1 < step_cycles(h)));
     const int pm = prof_begin(h, MGWR_K_REFINE, (double)(points(h, L) * h->B));
     if (ddef)
       MGWR_CK(h, mgwr::launch_refine_dd(h->u_dd, h->h32.u[L], cnt, h->stream));

@@ -1641,13 +1641,18 @@ int solve_begin(mgwr_t h, SolveState& S, int cyc, int nu1, int nu2, double tol, 
   MGWR_CK(h, cudaEventRecord(h->ev0, h->stream));
   if (S.ddef) {
     MGWR_CK(h, mgwr::launch_split(h->u_dd, h->h64.u[L], cntL, h->stream));
-    MGWR_CK(h, mgwr::launch_split(h->f_dd, h->h64.f[L], cntL, h->stream));
+    if (!h->u_zero) MGWR_CK(h, mgwr::launch_split(h->f_dd, h->h64.f[L], cntL, h->stream));
   }
   if (h->u_zero) {
-    // the defect of u = 0 is f itself (Algorithm 1 from the zero iterate)
+    // the defect of u = 0 is f itself (Algorithm 1 from the zero iterate): its
+    // norm, its FP32 rounding for the first inner cycles and its double-float
+    // split (f_dd, or the outer defect MGWR_MIXED carries from) in one pass
     MGWR_TRY(clear_norms(h));
+    mgwr::dd* fdd = S.ddef ? h->f_dd
+                    : (S.mixed && !S.ddc && carries(h)) ? outer_field(h)
+                                                        : nullptr;
     MGWR_CK(h, mgwr::launch_absmax_round(h->h64.f[L], S.mixed && !S.ddc ? h->h32.f[L] : nullptr,
-                                         cntL / h->B, h->B, h->norm_bits, h->stream));
+                                         fdd, cntL / h->B, h->B, h->norm_bits, h->stream));
     if (S.ddc) {
       MGWR_CK(h, mgwr::launch_split(h->hdd.f[L], h->h64.f[L], cntL, h->stream));
       h->hdd.rs[L] = R_STALE;
@@ -1669,11 +1674,8 @@ int solve_begin(mgwr_t h, SolveState& S, int cyc, int nu1, int nu2, double tol, 
   // split into outer_field in MGWR_MIXED), else the full defect just computed
   // (kept in outer_field by enqueue_outer_full)
   h->outer_src = -1;
-  if (S.mixed && !S.ddc && carries(h)) {
-    h->outer_src = h->u_zero && S.ddef ? 0 : 1;
-    if (h->u_zero && !S.ddef)
-      MGWR_CK(h, mgwr::launch_split(outer_field(h), h->h64.f[L], cntL, h->stream));
-  }
+  if (S.mixed && !S.ddc && carries(h))
+    h->outer_src = h->u_zero && S.ddef ? 0 : 1;  // from u = 0: split above
   S.anchor = h->relres;
   return MGWR_OK;
 }

@@ -62,6 +62,33 @@ __device__ __forceinline__ dd dd_split_int(double x) {
   return dd_split_fast(x);
 }
 
+// The pair (RN32(x), RN32(x - RN32(x))) that FP64 arithmetic forms ((float)x,
+// then the exact FP64 difference rounded), here from integer and FP32
+// operations alone for 2^-74 <= |x| < 2^126 and for x = +-0; other x take the
+// FP64 forms.  Bitwise the same pair: hi is x's top 24 significand bits rounded
+// to nearest (ties to even) on the bits, the increment carrying into the
+// exponent; x - hi is the cleared 29-bit remainder, less 2^29 when hi rounded
+// up, times the power of two 2^(e - 1075), converted by one FP32 rounding and
+// an exact scaling.  GB300 runs the FP64 conversions and subtraction at 1/64
+// of the FP32 rate.
+__device__ __forceinline__ dd dd_split_rn(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  if (e >= 949 && e <= 1148) {
+    const unsigned r29 = (unsigned)(b & 0x1FFFFFFFull);
+    unsigned hb = sign | ((unsigned)(e - 896) << 23) | ((unsigned)(b >> 29) & 0x7FFFFFu);
+    const bool up = r29 > 0x10000000u || (r29 == 0x10000000u && (hb & 1u));
+    hb += up ? 1u : 0u;
+    const float scale = __int_as_float((e - 1075 + 127) << 23);  // 2^(e - 1075), normal
+    const float mag = __fmul_rn(__int2float_rn((int)r29 - (up ? 0x20000000 : 0)), scale);
+    return dd(__uint_as_float(hb), sign ? -mag : mag);
+  }
+  if ((b << 1) == 0) return dd(__uint_as_float(sign), 0.f);
+  const float hi = __double2float_rn(x);
+  return dd(hi, __double2float_rn(x - (double)hi));
+}
+
 // s + e = a + b exactly (TwoSum, any a, b)
 __device__ __forceinline__ dd dd_two_sum(float a, float b) {
   const float s = __fadd_rn(a, b);

@@ -231,7 +231,10 @@ cudaError_t launch_loop_init(LoopState* st, double tol, int max_iter, cudaStream
 // max_iter.
 cudaError_t launch_loop_decide(const unsigned long long* norm_bits, const double* r0, int batch,
                                LoopState* st, cudaGraphConditionalHandle loop, cudaStream_t s);
-cudaError_t launch_absmax_round(const double* x, float* out, size_t per, int batch,
+// Per instance (batch instances of `per` values): |x|_inf into norm_bits, and
+// in the same pass, where not null, out = (float) x and out_dd = x split as
+// launch_split does.
+cudaError_t launch_absmax_round(const double* x, float* out, dd* out_dd, size_t per, int batch,
                                 unsigned long long* norm_bits, cudaStream_t s);
 
 // Outer defect of the mixed modes carried by the correction of an outer step

@@ -363,13 +363,12 @@ __global__ void __launch_bounds__(kLineBlock)
 }
 
 // double <-> double-float conversions and the double-float update
+// dst = src as double-float pairs (RN32(x), RN32(x - RN32(x))), without FP64
+// arithmetic for the values a solve holds (dd_split_rn).
 __global__ void k_split(dd* __restrict__ dst, const double* __restrict__ src, size_t count) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
-       i += (size_t)gridDim.x * blockDim.x) {
-    const double x = src[i];
-    const float hi = (float)x;
-    dst[i] = dd(hi, (float)(x - (double)hi));
-  }
+       i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = dd_split_rn(src[i]);
 }
 
 __global__ void k_join(double* __restrict__ dst, const dd* __restrict__ src, size_t count) {
@@ -418,21 +417,32 @@ __global__ void k_round(float* __restrict__ dst, const double* __restrict__ src,
     dst[i] = (float)src[i];
 }
 
-// Per instance (blockIdx.y): |x|_inf folded into norm_bits[instance] and, when
-// out != null, out = (float) x.  The defect of u = 0 is f itself, so this is
-// the initial defect of a solve from zero.
+// Per instance (blockIdx.y), in one pass over x: |x|_inf folded into
+// norm_bits[instance], and where given out = (float) x and out_dd = x as
+// double-float pairs (k_split's).  The defect of u = 0 is f itself, so this
+// is the initial defect of a solve from zero, rounded for the first inner
+// cycles and split for the outer defect the first steps carry.  No FP64
+// arithmetic: the conversions by dd_split_rn, the norm as the largest
+// magnitude bit pattern (non-negative doubles order like their bits, a NaN
+// above infinity).
 __global__ void __launch_bounds__(128)
-    k_absmax_round(const double* __restrict__ x, float* __restrict__ out, size_t per,
-                   unsigned long long* __restrict__ norm_bits) {
+    k_absmax_round(const double* __restrict__ x, float* __restrict__ out, dd* __restrict__ out_dd,
+                   size_t per, unsigned long long* __restrict__ norm_bits) {
   x += blockIdx.y * per;
   if (out != nullptr) out += blockIdx.y * per;
-  double amax = 0.0;
+  if (out_dd != nullptr) out_dd += blockIdx.y * per;
+  unsigned long long amax = 0;
   for (size_t i = blockIdx.x * (size_t)128 + threadIdx.x; i < per; i += (size_t)gridDim.x * 128) {
     const double v = x[i];
-    if (out != nullptr) out[i] = (float)v;
-    amax = absmax_nan(fabs(v), amax);
+    if (out != nullptr || out_dd != nullptr) {
+      const dd p = dd_split_rn(v);
+      if (out != nullptr) out[i] = p.hi;
+      if (out_dd != nullptr) out_dd[i] = p;
+    }
+    const unsigned long long a = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+    amax = a > amax ? a : amax;
   }
-  block_absmax(amax, norm_bits + blockIdx.y);
+  block_absmax(__longlong_as_double((long long)amax), norm_bits + blockIdx.y);
 }
 
 // Initial value g of every instance (blockIdx.y): u = g along time (initial
@@ -798,12 +808,13 @@ cudaError_t launch_loop_decide(const unsigned long long* norm_bits, const double
   return counted(cudaGetLastError());
 }
 
-cudaError_t launch_absmax_round(const double* x, float* out, size_t per, int batch,
+cudaError_t launch_absmax_round(const double* x, float* out, dd* out_dd, size_t per, int batch,
                                 unsigned long long* norm_bits, cudaStream_t s) {
   if (per == 0 || batch == 0) return cudaSuccess;
   size_t bx = (per + 128 * 16 - 1) / (128 * 16);
   if (bx > 2432) bx = 2432;
-  k_absmax_round<<<dim3((unsigned)bx, (unsigned)batch), 128, 0, s>>>(x, out, per, norm_bits);
+  k_absmax_round<<<dim3((unsigned)bx, (unsigned)batch), 128, 0, s>>>(x, out, out_dd, per,
+                                                                     norm_bits);
   return counted(cudaGetLastError());
 }
 

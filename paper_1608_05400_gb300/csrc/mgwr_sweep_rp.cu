@@ -115,8 +115,9 @@ __global__ void __launch_bounds__(kRpBlock, (rp::Plan<LOGL, R0, R1, R2, R3, T>::
 // T line pairs at a time) per block and one block per SM, each block looping
 // over line pairs with the spectrum and the twiddle bases copied once into
 // shared memory (rp::SharedTables), where k_sweep_rp reads them through the
-// caches for every butterfly; the black half-sweep loads the old values of a
-// butterfly's outputs before its first store.  The same arithmetic as the
+// caches for every butterfly; the line between the two points of a pair is
+// loaded once; the black half-sweep loads the old values of a butterfly's
+// outputs before its first store.  The same arithmetic as the
 // paired k_sweep_rp: bitwise the same results.
 template <int LOGL, int R0, int R1, int R2, int R3, int T>
 __global__ void __launch_bounds__(kRpResBlock, 1)
@@ -162,9 +163,12 @@ __global__ void __launch_bounds__(kRpResBlock, 1)
     neighbour_lines(u, zero, d, n, iB, jB, pBM, M, qB);
     if (!valid) qA[0] = qA[1] = qA[2] = qA[3] = zero;
     if (!hasB) qB[0] = qB[1] = qB[2] = qB[3] = zero;
+    // the two points of a pair on one row share the line between them
+    const bool shared = qB[0] == qA[1] && hasB;
     auto load2 = [&](int m) -> rp::Pair2 {
       const float2 a = ld2(fA, m), b = ld2(fB, m);
-      const float2 a0 = ld2(qA[0], m), a1 = ld2(qA[1], m), b0 = ld2(qB[0], m), b1 = ld2(qB[1], m);
+      const float2 a0 = ld2(qA[0], m), a1 = ld2(qA[1], m), b1 = ld2(qB[1], m);
+      const float2 b0 = shared ? a1 : ld2(qB[0], m);
       float2 sa{a0.x + a1.x, a0.y + a1.y}, sb{b0.x + b1.x, b0.y + b1.y};
       if (d == 2) {
         const float2 a2 = ld2(qA[2], m), a3 = ld2(qA[3], m), b2 = ld2(qB[2], m),

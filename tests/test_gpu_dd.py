@@ -176,3 +176,35 @@ def test_auto_precision_resolves_on_the_handle_and_converges():
         assert st.outer <= 6, (d, n, st.outer)
         ref = separable.solution(d, n, M, 1.0, 0.3, prob.rhs_profile(), inputs.phi(d, n))
         assert rel(u, ref) <= 100 * tol
+
+
+def test_double_float_split_is_the_rounded_pair():
+    # A MGWR_MIXED_DD solve holds its iterate as double-float pairs split on the
+    # device and joins them back at its end; with a tolerance the first defect
+    # already meets (relative defect 1 <= 2) it stops before any cycle, so the
+    # solution is hi + lo of the split of every value: hi = RN32(x) (ties to
+    # even), lo = RN32(x - hi), formed by integer and FP32 operations on the
+    # device and here by IEEE conversions.  Values: rounding ties and their
+    # neighbours, signed zeros, the ends of the integer path's exponent range
+    # (2^-74) and beyond it (smaller, subnormal), random magnitudes 2^-80..2^60.
+    d, n, M = 1, 63, 64
+    rng = np.random.default_rng(11)
+    x = rng.standard_normal(n * M) * np.exp2(rng.integers(-80, 61, n * M).astype(float))
+    one = 1.0
+    special = [0.0, -0.0, one + 2.0 ** -24, one + 3 * 2.0 ** -24, -(one + 3 * 2.0 ** -24),
+               one + 2.0 ** -24 + 2.0 ** -52, one + 2.0 ** -24 - 2.0 ** -53, 3.0 - 2.0 ** -23,
+               (2.0 - 2.0 ** -24) * 2.0 ** 40, 2.0 ** -74, 1.5 * 2.0 ** -74, 2.0 ** -75,
+               -1.25 * 2.0 ** -75, 1e-30, 5e-324, -1e-310, 2.0 ** 59 * (1 + 2.0 ** -30)]
+    x[:len(special)] = special
+    u0 = x.reshape(n, M)
+    with G.Solver(d, n, M, 1.0, 0.5) as s:
+        s.set_precision(G.MGWR_MIXED_DD)
+        s.set_rhs(np.zeros((n, M)))
+        s.set_initial(u0)
+        st = s.solve(1, 1, 1, tol=2.0, max_cycles=4)
+        got = s.solution()
+    assert st.cycles == 0
+    hi = u0.astype(np.float32)
+    lo = (u0 - hi.astype(np.float64)).astype(np.float32)
+    want = hi.astype(np.float64) + lo.astype(np.float64)
+    np.testing.assert_array_equal(got.view(np.uint64), want.view(np.uint64))

@@ -128,9 +128,11 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=None,
                    help="timed steps of the end-to-end measurement (default min(steps, 5))")
     p.add_argument("--requests", type=int, default=2000, help="served: first R requests of the stream")
-    p.add_argument("--slots", type=int, default=4, help="served: server slots")
+    p.add_argument("--slots", type=int, default=8, help="served: server slots")
     p.add_argument("--rate", type=float, default=None,
                    help="served: Poisson arrival rate, requests/s (default 0.7 x the sustained rate)")
+    p.add_argument("--submit", default="buffer", choices=["buffer", "copy"],
+                   help="served: right-hand sides into server-lent page-locked buffers, or copied")
     p.add_argument("--policy", default="fifo", choices=["fifo", "smallest"],
                    help="served: server admission order")
     p.add_argument("--inner", type=int, default=None, help="mixed modes: FP32 cycles per outer defect")
@@ -690,8 +692,14 @@ def run_served(args):
     precision = args.precision or WORKLOADS["served"][6]
     prec = PREC_CODES[precision]
 
-    def rhs(rq):
-        return inputs.Problem(rq["d"], rq["n"], rq["M"], 1.0, rq["alpha"], rq["kind"]).rhs()
+    zero_copy = args.submit == "buffer"
+
+    def rhs(rq, srv):
+        prob = inputs.Problem(rq["d"], rq["n"], rq["M"], 1.0, rq["alpha"], rq["kind"])
+        if not zero_copy:
+            return prob.rhs()
+        # straight into a page-locked buffer lent by the server (no copy at submit)
+        return prob.rhs(out=srv.buffer(rq["n"] ** rq["d"], rq["M"]))
 
     def unknowns(rq):
         return rq["n"] ** rq["d"] * rq["M"]
@@ -725,7 +733,7 @@ def run_served(args):
                             if outstanding[0] and outstanding[0] + nbytes > host_cap:
                                 return
                             outstanding[0] += nbytes
-                        pending[nxt[0]] = pool.submit(rhs, reqs[nxt[0]])
+                        pending[nxt[0]] = pool.submit(rhs, reqs[nxt[0]], srv)
                         nxt[0] += 1
 
                 with cf.ThreadPoolExecutor(8) as pool:
@@ -741,8 +749,12 @@ def run_served(args):
                             time.sleep(wait)
                         # time a request waited for its data counts in its latency
                         delay[i] = max(0.0, time.perf_counter() - (t0 + arrivals[i]))
-                        tickets[i] = srv.submit(rq["d"], rq["n"], rq["M"], 1.0, rq["alpha"], f,
-                                                precision=prec, tol=tol)
+                        if zero_copy:
+                            tickets[i] = srv.submit_buffer(rq["d"], rq["n"], rq["M"], 1.0,
+                                                           rq["alpha"], f, precision=prec, tol=tol)
+                        else:
+                            tickets[i] = srv.submit(rq["d"], rq["n"], rq["M"], 1.0, rq["alpha"], f,
+                                                    precision=prec, tol=tol)
                         del f
 
             th = threading.Thread(target=submitter)
@@ -794,7 +806,14 @@ def run_served(args):
         "served": {"p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
                    "sustained_requests_per_s": rate, "offered_requests_per_s": offered,
                    "back_to_back_unknowns_per_s": total / span1, "completed_ok": ok,
-                   "requests": len(reqs), "total_unknowns": total, "peak_bytes": info["peak_bytes"]},
+                   "requests": len(reqs), "total_unknowns": total, "peak_bytes": info["peak_bytes"],
+                   "submit": ("zero-copy: f generated into page-locked buffers lent by the server "
+                              "(mgwr_server_buffer / mgwr_submit_buffer)" if zero_copy else
+                              "mgwr_submit (f copied into the server's page-locked pool)"),
+                   "host_seconds_pass2": {k: info[k] for k in ("submit_copy_s", "prepare_s",
+                                                               "finish_s", "pin_s")},
+                   "pinned_buffers_pass2": info["pinned_buffers"],
+                   "reused_handles_pass2": info["reused_handles"]},
     }
     print(json.dumps(out))
     return 0

@@ -440,7 +440,7 @@ int mgwr_footprint(int d, int n, int M, int batch, int precision, size_t* bytes)
  * at most `max_slots` at a time.  A worker thread per slot prepares each
  * admitted request's handle (an idle handle of the same d, n, M and resolved
  * precision, set up in place for the request's T and alpha by
- * mgwr_set_problem, else a new one; at most 8 idle handles are kept, the least
+ * mgwr_set_problem, else a new one; at most 32 idle handles are kept, the least
  * recently used evicted first, also when their memory keeps a request out) and
  * copies its data in; then the request joins the server's group
  * (mgwr_group_*): per size class (space-time unknowns n^d M below 2^22, below
@@ -483,6 +483,11 @@ typedef struct {
   long long group_launches;   /* graph launches of the group so far              */
   long long member_iterations;/* solve iterations those launches ran             */
   long long reused_handles;   /* requests served by an idle handle of their shape */
+  double submit_copy_s;       /* host seconds mgwr_submit spent copying f         */
+  double prepare_s;           /* slot seconds preparing handles, uploading data   */
+  double finish_s;            /* slot seconds downloading results                 */
+  double pin_s;               /* host seconds page-locking new pool buffers       */
+  long long pinned_buffers;   /* pool buffers page-locked so far                  */
 } mgwr_server_info;
 /* MGWR_E_INVAL (bad arguments), MGWR_E_CUDA (no device). */
 int mgwr_server_create(size_t hbm_budget, int max_slots, mgwr_server_t* out);
@@ -498,6 +503,21 @@ int mgwr_server_set_policy(mgwr_server_t s, int policy);
  * from a pool the server keeps (up to 32 GiB of released buffers are reused;
  * pageable memory when no page-locked memory can be had). */
 int mgwr_submit(mgwr_server_t s, const mgwr_request* rq, uint64_t* ticket);
+/* Zero-copy submission (no counterpart in the paper): a page-locked host
+ * buffer of at least `count` doubles from the server's pool, into which the
+ * caller writes a request's f (N*M doubles, time-contiguous as for
+ * mgwr_submit) and which mgwr_submit_buffer then queues without copying it.
+ * The buffer belongs to the caller until it is submitted or released;
+ * mgwr_server_destroy frees buffers still lent.  MGWR_E_INVAL (bad
+ * arguments), MGWR_E_NOMEM (no page-locked memory). */
+int mgwr_server_buffer(mgwr_server_t s, size_t count, double** buf);
+/* mgwr_submit with f in `buf` from mgwr_server_buffer (rq->f is ignored):
+ * on MGWR_OK the server owns the buffer (back to its pool once the data is on
+ * the device); on any error the caller still holds it.  Also MGWR_E_INVAL
+ * for a buffer the server did not lend or one smaller than N*M doubles. */
+int mgwr_submit_buffer(mgwr_server_t s, const mgwr_request* rq, double* buf, uint64_t* ticket);
+/* Gives a lent buffer back unsubmitted (MGWR_E_INVAL if it is not lent). */
+int mgwr_server_release(mgwr_server_t s, double* buf);
 /* Waits up to timeout_us (0: no wait) for the ticket.  MGWR_E_AGAIN (not
  * ready, timeout 0) or MGWR_E_TIMEOUT (not ready after the wait); MGWR_OK:
  * u_out (N*M doubles, may be NULL) and *res filled and the ticket released;

@@ -61,12 +61,24 @@ class PinnedPool {
       }
     }
     void* p = nullptr;
+    const auto t0 = std::chrono::steady_clock::now();
     if (cudaMallocHost(&p, count * sizeof(double)) != cudaSuccess) {
       cudaGetLastError();
       return nullptr;
     }
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      pin_s_ += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      pinned_++;
+    }
     *cap = count;
     return static_cast<double*>(p);
+  }
+  // seconds spent page-locking new buffers, and how many
+  void stats(double* pin_s, long long* pinned) {
+    std::lock_guard<std::mutex> lk(mu_);
+    *pin_s = pin_s_;
+    *pinned = pinned_;
   }
   void put(double* p, size_t cap) {
     {
@@ -84,6 +96,8 @@ class PinnedPool {
   std::mutex mu_;
   std::multimap<size_t, double*> free_;
   size_t kept_ = 0;
+  double pin_s_ = 0.0;
+  long long pinned_ = 0;
 };
 
 // `count` doubles of host memory: pinned from the pool when it has some, else
@@ -108,9 +122,18 @@ class HostBuf {
     n_ = count;
     return true;
   }
+  // takes over a pool buffer of capacity cap holding count values
+  void adopt(PinnedPool* pool, double* p, size_t cap, size_t count) {
+    release();
+    p_ = p;
+    pool_ = pool;
+    cap_ = cap;
+    n_ = count;
+  }
   double* data() const { return p_; }
   size_t size() const { return n_; }
   bool empty() const { return n_ == 0; }
+  void reset() { release(); }
 
  private:
   void release() {
@@ -185,6 +208,11 @@ struct mgwr_server {
   long long launches[kClasses] = {}, iterations[kClasses] = {};
   long long launches_seen[kClasses] = {}, iterations_seen[kClasses] = {};  // of the current group
   int most[kClasses] = {};
+  // pool buffers handed to callers (mgwr_server_buffer) and their capacities
+  std::unordered_map<double*, size_t> lent;
+  // host seconds: right-hand sides copied by mgwr_submit, handles prepared and
+  // data uploaded by the slots, results downloaded
+  double submit_copy_s = 0.0, prepare_s = 0.0, finish_s = 0.0;
 };
 
 namespace {
@@ -220,7 +248,7 @@ Ticket* pick(mgwr_server* s) {
   return t;
 }
 
-constexpr size_t kMaxIdle = 8;  // idle handles kept at most
+constexpr size_t kMaxIdle = 32;  // idle handles kept at most (and within the budget)
 
 std::tuple<int, int, int, int> shape_key(const mgwr_request& q) {
   int prec = q.precision;
@@ -335,7 +363,13 @@ void worker(mgwr_server* s) {
       s->admitted++;
     }
     for (mgwr_t h : drop) mgwr_destroy(h);
+    const auto tp = Clock::now();
     int st = prepare(s, t);
+    t->f.reset();  // uploaded (mgwr_set_rhs waits for its copy): back to the pool
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->prepare_s += std::chrono::duration<double>(Clock::now() - tp).count();
+    }
     if (st == MGWR_OK) {
       // the batcher adds it to the group at the next iteration boundary
       std::unique_lock<std::mutex> lk(s->mu);
@@ -345,7 +379,10 @@ void worker(mgwr_server* s) {
       st = t->res.status;
     }
     if (t->h != nullptr) {
+      const auto tf = Clock::now();
       st = finish(s, t, st);
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->finish_s += std::chrono::duration<double>(Clock::now() - tf).count();
     } else {
       std::lock_guard<std::mutex> lk(s->mu);
       s->in_use -= t->footprint;
@@ -452,6 +489,54 @@ int check_request(const mgwr_request* q) {
   return MGWR_OK;
 }
 
+// Queues a checked request.  Without `lent`, f is copied into a pool buffer;
+// with it, that buffer (from mgwr_server_buffer, holding f) is taken over
+// without a copy, on success only: on any error the caller still holds it.
+int submit_ticket(mgwr_server* s, const mgwr_request* rq, double* lent, uint64_t* ticket) {
+  size_t fp = 0;
+  if (mgwr_footprint(rq->d, rq->n, rq->M, 1, rq->precision, &fp) != MGWR_OK) return MGWR_E_INVAL;
+  if (fp > s->budget) return MGWR_E_TOOBIG;
+  auto t = std::unique_ptr<Ticket>(new (std::nothrow) Ticket);
+  if (!t) return MGWR_E_NOMEM;
+  t->rq = *rq;
+  t->N = rq->d == 1 ? (size_t)rq->n : (size_t)rq->n * rq->n;
+  const size_t count = t->N * rq->M;
+  try {
+    if (lent == nullptr) {
+      if (!t->f.alloc(&s->pool, count)) return MGWR_E_NOMEM;
+      const auto t0 = Clock::now();
+      std::memcpy(t->f.data(), rq->f, count * sizeof(double));
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->submit_copy_s += std::chrono::duration<double>(Clock::now() - t0).count();
+    }
+    t->pool = &s->pool;
+    if (rq->g != nullptr) t->g.assign(rq->g, rq->g + t->N);
+  } catch (const std::bad_alloc&) {
+    return MGWR_E_NOMEM;
+  }
+  t->rq.f = nullptr;
+  t->rq.g = nullptr;
+  t->footprint = fp;
+  t->t_submit = Clock::now();
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->stop) return MGWR_E_STATE;
+    if ((int)s->queue.size() >= s->max_queue) return MGWR_E_AGAIN;
+    if (lent != nullptr) {
+      auto it = s->lent.find(lent);
+      if (it == s->lent.end() || it->second < count) return MGWR_E_INVAL;
+      t->f.adopt(&s->pool, lent, it->second, count);
+      s->lent.erase(it);
+    }
+    t->id = s->next_id++;
+    *ticket = t->id;
+    s->queue.push_back(t.get());
+    s->tickets.emplace(t->id, std::move(t));
+  }
+  s->cv_work.notify_one();
+  return MGWR_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -511,6 +596,7 @@ int mgwr_server_destroy(mgwr_server_t s) {
   for (auto& b : s->batchers) b.join();
   for (auto& i : s->idle) mgwr_destroy(i.h);
   for (auto& g : s->group) mgwr_group_destroy(g);
+  for (auto& kv : s->lent) s->pool.put(kv.first, kv.second);  // freed with the pool
   delete s;
   return MGWR_OK;
 }
@@ -519,35 +605,48 @@ int mgwr_submit(mgwr_server_t s, const mgwr_request* rq, uint64_t* ticket) {
   if (s == nullptr || ticket == nullptr) return MGWR_E_INVAL;
   const int st = check_request(rq);
   if (st != MGWR_OK) return st;
-  size_t fp = 0;
-  if (mgwr_footprint(rq->d, rq->n, rq->M, 1, rq->precision, &fp) != MGWR_OK) return MGWR_E_INVAL;
-  if (fp > s->budget) return MGWR_E_TOOBIG;
-  auto t = std::unique_ptr<Ticket>(new (std::nothrow) Ticket);
-  if (!t) return MGWR_E_NOMEM;
-  t->rq = *rq;
-  t->N = rq->d == 1 ? (size_t)rq->n : (size_t)rq->n * rq->n;
-  try {
-    if (!t->f.alloc(&s->pool, t->N * rq->M)) return MGWR_E_NOMEM;
-    std::memcpy(t->f.data(), rq->f, t->N * rq->M * sizeof(double));
-    t->pool = &s->pool;
-    if (rq->g != nullptr) t->g.assign(rq->g, rq->g + t->N);
-  } catch (const std::bad_alloc&) {
-    return MGWR_E_NOMEM;
-  }
-  t->rq.f = nullptr;
-  t->rq.g = nullptr;
-  t->footprint = fp;
-  t->t_submit = Clock::now();
+  return submit_ticket(s, rq, nullptr, ticket);
+}
+
+int mgwr_server_buffer(mgwr_server_t s, size_t count, double** buf) {
+  if (s == nullptr || buf == nullptr || count == 0) return MGWR_E_INVAL;
+  *buf = nullptr;
+  size_t cap = 0;
+  double* p = s->pool.get(count, &cap);
+  if (p == nullptr) return MGWR_E_NOMEM;
   {
     std::lock_guard<std::mutex> lk(s->mu);
-    if (s->stop) return MGWR_E_STATE;
-    if ((int)s->queue.size() >= s->max_queue) return MGWR_E_AGAIN;
-    t->id = s->next_id++;
-    *ticket = t->id;
-    s->queue.push_back(t.get());
-    s->tickets.emplace(t->id, std::move(t));
+    try {
+      s->lent.emplace(p, cap);
+    } catch (const std::bad_alloc&) {
+      s->pool.put(p, cap);
+      return MGWR_E_NOMEM;
+    }
   }
-  s->cv_work.notify_one();
+  *buf = p;
+  return MGWR_OK;
+}
+
+int mgwr_submit_buffer(mgwr_server_t s, const mgwr_request* rq, double* buf, uint64_t* ticket) {
+  if (s == nullptr || ticket == nullptr || rq == nullptr || buf == nullptr) return MGWR_E_INVAL;
+  mgwr_request q = *rq;
+  q.f = buf;
+  const int st = check_request(&q);
+  if (st != MGWR_OK) return st;
+  return submit_ticket(s, &q, buf, ticket);
+}
+
+int mgwr_server_release(mgwr_server_t s, double* buf) {
+  if (s == nullptr || buf == nullptr) return MGWR_E_INVAL;
+  size_t cap = 0;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->lent.find(buf);
+    if (it == s->lent.end()) return MGWR_E_INVAL;
+    cap = it->second;
+    s->lent.erase(it);
+  }
+  s->pool.put(buf, cap);
   return MGWR_OK;
 }
 
@@ -580,6 +679,10 @@ int mgwr_server_stats(mgwr_server_t s, mgwr_server_info* info) {
   info->budget_bytes = s->budget;
   info->slots = s->slots;
   info->reused_handles = s->reused;
+  info->submit_copy_s = s->submit_copy_s;
+  info->prepare_s = s->prepare_s;
+  info->finish_s = s->finish_s;
+  s->pool.stats(&info->pin_s, &info->pinned_buffers);
   info->group_launches = 0;
   info->member_iterations = 0;
   info->max_group_members = 0;

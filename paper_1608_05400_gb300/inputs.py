@@ -117,8 +117,11 @@ class Problem:
         return caputo_of_profile(self.kind, self.alpha, t) + self.d * math.pi ** 2 * time_profile(
             self.kind, self.alpha, t)
 
-    def rhs(self) -> np.ndarray:
-        """Manufactured source f(x, t) on the grid, shape (N, M), float64."""
+    def rhs(self, out: np.ndarray | None = None) -> np.ndarray:
+        """Manufactured source f(x, t) on the grid, shape (N, M), float64 (into
+        `out` when given, a C-contiguous (N, M) float64 array)."""
+        if out is not None:
+            return np.outer(phi(self.d, self.n), self.rhs_profile(), out=out)
         return np.ascontiguousarray(np.outer(phi(self.d, self.n), self.rhs_profile()))
 
 

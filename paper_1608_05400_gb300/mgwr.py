@@ -61,7 +61,10 @@ class mgwr_server_info(C.Structure):
                 ("in_use_bytes", C.c_size_t), ("peak_bytes", C.c_size_t),
                 ("budget_bytes", C.c_size_t), ("slots", C.c_int),
                 ("max_group_members", C.c_int), ("group_launches", C.c_longlong),
-                ("member_iterations", C.c_longlong), ("reused_handles", C.c_longlong)]
+                ("member_iterations", C.c_longlong), ("reused_handles", C.c_longlong),
+                ("submit_copy_s", C.c_double), ("prepare_s", C.c_double),
+                ("finish_s", C.c_double), ("pin_s", C.c_double),
+                ("pinned_buffers", C.c_longlong)]
 
 
 _h = C.c_void_p
@@ -131,6 +134,10 @@ _SIGS = {
     "mgwr_server_destroy": (C.c_int, [C.c_void_p]),
     "mgwr_server_set_policy": (C.c_int, [C.c_void_p, C.c_int]),
     "mgwr_submit": (C.c_int, [C.c_void_p, C.POINTER(mgwr_request), C.POINTER(C.c_uint64)]),
+    "mgwr_server_buffer": (C.c_int, [C.c_void_p, C.c_size_t, C.POINTER(_dp)]),
+    "mgwr_submit_buffer": (C.c_int, [C.c_void_p, C.POINTER(mgwr_request), _dp,
+                                     C.POINTER(C.c_uint64)]),
+    "mgwr_server_release": (C.c_int, [C.c_void_p, _dp]),
     "mgwr_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int, _dp, C.POINTER(mgwr_result)]),
     "mgwr_server_stats": (C.c_int, [C.c_void_p, C.POINTER(mgwr_server_info)]),
     "mgwr_profile": (C.c_int, [_h, C.c_int]),
@@ -500,6 +507,39 @@ class Server:
             raise MGWRError(st, "mgwr_submit: " + self.lib.mgwr_status_string(st).decode())
         self._shapes[t.value] = (N, M)
         return t.value
+
+    def buffer(self, N: int, M: int) -> np.ndarray:
+        """A page-locked (N, M) float64 array lent from the server's pool
+        (mgwr_server_buffer): write f into it and hand it to submit_buffer, or
+        give it back with release.  The array must not be used after either."""
+        p = _dp()
+        st = self.lib.mgwr_server_buffer(self.h, N * M, C.byref(p))
+        if st != MGWR_OK:
+            raise MGWRError(st, "mgwr_server_buffer")
+        return np.ctypeslib.as_array(p, shape=(N, M))
+
+    def submit_buffer(self, d, n, M, T, alpha, buf: np.ndarray, g=None, precision=MGWR_MIXED,
+                      order=MGWR_ORDER_TEXT, cycle=1, nu1=1, nu2=1, tol=1e-8,
+                      max_cycles=100) -> int:
+        """submit() of f held in an array from buffer(), without a copy
+        (mgwr_submit_buffer); on success the server owns the array's memory."""
+        N = n ** d
+        assert buf.shape == (N, M) and buf.dtype == np.float64, (buf.shape, buf.dtype)
+        gg = None if g is None else _f64(g).reshape(N)
+        p = buf.ctypes.data_as(_dp)
+        rq = mgwr_request(d, n, M, T, alpha, p, _ptr(gg), precision, order, cycle, nu1, nu2, tol,
+                          max_cycles)
+        t = C.c_uint64()
+        st = self.lib.mgwr_submit_buffer(self.h, C.byref(rq), p, C.byref(t))
+        if st != MGWR_OK:
+            raise MGWRError(st, "mgwr_submit_buffer: " + self.lib.mgwr_status_string(st).decode())
+        self._shapes[t.value] = (N, M)
+        return t.value
+
+    def release(self, buf: np.ndarray):
+        st = self.lib.mgwr_server_release(self.h, buf.ctypes.data_as(_dp))
+        if st != MGWR_OK:
+            raise MGWRError(st, "mgwr_server_release")
 
     def poll(self, ticket: int, timeout_us: int = 0, copy_solution: bool = True) -> Result | None:
         N, M = self._shapes[ticket]

@@ -110,6 +110,10 @@ def test_server_calls_reject_null_and_bad_arguments(lib):
     assert lib.mgwr_server_create(0, 4, C.byref(h)) == mgwr.MGWR_E_INVAL
     assert lib.mgwr_server_set_policy(None, mgwr.MGWR_POLICY_SMALLEST) == mgwr.MGWR_E_INVAL
     assert lib.mgwr_server_create(1 << 30, 0, C.byref(h)) == mgwr.MGWR_E_INVAL
+    p = mgwr._dp()
+    assert lib.mgwr_server_buffer(None, 16, C.byref(p)) == mgwr.MGWR_E_INVAL
+    assert lib.mgwr_submit_buffer(None, C.byref(rq), p, C.byref(t)) == mgwr.MGWR_E_INVAL
+    assert lib.mgwr_server_release(None, p) == mgwr.MGWR_E_INVAL
 
 
 def test_auto_precision_follows_the_fp32_refinement_limit(lib):

@@ -54,6 +54,37 @@ def test_results_in_the_mix_equal_results_alone():
         assert res.stats.cycles == st.cycles and res.stats.relres == st.relres
 
 
+def test_zero_copy_submission_equals_copied_submission():
+    # f written into page-locked buffers lent by the server and handed over
+    # without a copy: the same results, bitwise, as mgwr_submit's copies; a
+    # buffer can be given back unsubmitted, and an array the server did not
+    # lend is refused
+    reqs = REQUESTS[:6]
+    fs = [inputs.Problem(d, n, M, 1.0, a, k).rhs() for d, n, M, a, k, _ in reqs]
+    with G.Server(hbm_budget=8 << 30, slots=3) as srv:
+        copied = [srv.submit(d, n, M, 1.0, a, f, precision=p, tol=1e-10)
+                  for (d, n, M, a, k, p), f in zip(reqs, fs)]
+        lent = []
+        for (d, n, M, a, k, p), f in zip(reqs, fs):
+            buf = srv.buffer(n ** d, M)
+            inputs.Problem(d, n, M, 1.0, a, k).rhs(out=buf)
+            lent.append(srv.submit_buffer(d, n, M, 1.0, a, buf, precision=p, tol=1e-10))
+        spare = srv.buffer(31, 64)
+        srv.release(spare)
+        with pytest.raises(G.MGWRError):
+            srv.release(spare)  # no longer lent
+        foreign = np.zeros((31, 64))
+        with pytest.raises(G.MGWRError):
+            srv.submit_buffer(1, 31, 64, 1.0, 0.5, foreign, precision=G.MGWR_FP64)
+        for a, b in zip(copied, lent):
+            ra, rb = srv.poll(a, timeout_us=120_000_000), srv.poll(b, timeout_us=120_000_000)
+            assert ra.status == rb.status == G.MGWR_OK
+            np.testing.assert_array_equal(ra.u, rb.u)
+            assert ra.stats.cycles == rb.stats.cycles and ra.stats.relres == rb.stats.relres
+        info = srv.info()
+    assert info["pinned_buffers"] >= 1 and info["prepare_s"] > 0.0
+
+
 def test_served_result_matches_oracle():
     d, n, M, a = 2, 31, 64, 0.4
     f = inputs.Problem(d, n, M, 1.0, a, "t2").rhs()

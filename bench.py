@@ -57,7 +57,7 @@ WORKLOADS = {
     "1d-63-m64": (1, 63, 64, 1, "t2", 1e-10, "fp64", "1-D plain MGWR 63 interior points, M=64, u=t^2 sin(pi x)"),
     "2d-511-m4096": (2, 511, 4096, 1, "talpha", 1e-8, "mixed",
            "2-D MGWR 511x511 interior, M=4096, u=t^alpha sin(pi x) sin(pi y)"),
-    "batch4096-2d-63-m256": (2, 63, 256, 4096, "t2", 1e-8, "mixed_dd",
+    "batch4096-2d-63-m256": (2, 63, 256, 4096, "t2", 1e-8, "mixed",
             "4096 independent 2-D 63x63, M=256 solves, alpha~U[0.1,0.9] (seed 1608), one batched handle"),
     "1d-4095-m65536": (1, 4095, 65536, 1, "talpha", 1e-8, "dd",
             "1-D MGWR 4095 interior points, M=65536 (long memory), u=t^alpha sin(pi x)"),

@@ -437,6 +437,85 @@ __global__ void __launch_bounds__(kLineBlock)
   }
 }
 
+// The 2-D k_prolong with each thread walking kProlongRun fine points of one fine
+// row for one vector of time values: a coarse column serves the three fine
+// columns around it, so each coarse value (one or two coarse rows) is loaded
+// once per walk and kept while the walk needs it, instead of once per fine
+// point that interpolates from it.  Every fine value takes the same taps in the
+// same order as in k_prolong: the same bits.
+constexpr int kProlongRun = 16;
+
+template <class R>
+__global__ void __launch_bounds__(kLineBlock)
+    k_prolong_rows(R* __restrict__ u, const R* __restrict__ uc, int n, int M, size_t fstride,
+                   size_t cstride) {
+  constexpr int W = Vec<R>::W;
+  u += blockIdx.y * fstride;
+  uc += blockIdx.y * cstride;
+  const int nc = (n - 1) / 2;
+  const int MV = M / W;
+  const int runs = (n + kProlongRun - 1) / kProlongRun;
+  const size_t items = (size_t)n * runs * MV;
+  for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < items;
+       x += (size_t)gridDim.x * blockDim.x) {
+    const int mv = (int)(x % MV);
+    const size_t rest = x / MV;
+    const int run = (int)(rest % runs);
+    const int j = (int)(rest / runs);
+    const int m = mv * W;
+    const Taps ty(j, nc);
+    const R* row0 = uc + (size_t)ty.i0 * nc * M + m;
+    const R* row1 = uc + (size_t)ty.i1 * nc * M + m;
+    // the last two coarse columns loaded (index, value in coarse rows i0 and i1)
+    int ca = -1, cb = -1;
+    Vec<R> a0, a1, b0, b1;
+    auto column = [&](int c, Vec<R>& v0, Vec<R>& v1) {
+      if (c == cb) {
+        v0 = b0;
+        v1 = b1;
+        return;
+      }
+      if (c == ca) {
+        v0 = a0;
+        v1 = a1;
+        return;
+      }
+      ca = cb;
+      a0 = b0;
+      a1 = b1;
+      cb = c;
+      b0 = vload(row0 + (size_t)c * M);
+      if (ty.count == 2) b1 = vload(row1 + (size_t)c * M);
+      v0 = b0;
+      v1 = b1;
+    };
+    const int i_end = (run + 1) * kProlongRun < n ? (run + 1) * kProlongRun : n;
+    for (int i = run * kProlongRun; i < i_end; ++i) {
+      const Taps tx(i, nc);
+      Vec<R> l0, l1, r0, r1;
+      column(tx.i0, l0, l1);  // a, c
+      column(tx.i1, r0, r1);  // b, e
+      const int taps = tx.count * ty.count;
+      Vec<R> sum = l0;
+      if (taps == 4) {
+#pragma unroll
+        for (int k = 0; k < W; ++k) sum.v[k] = (sum.v[k] + r0.v[k]) + (l1.v[k] + r1.v[k]);
+      } else if (taps == 2) {
+        const Vec<R>& second = ty.count == 2 ? l1 : r0;
+#pragma unroll
+        for (int k = 0; k < W; ++k) sum.v[k] = sum.v[k] + second.v[k];
+      }
+      const bool unit = !tx.half && !ty.half;
+      const R w = R((tx.half ? 0.5 : 1.0) * (ty.half ? 0.5 : 1.0));
+      R* up = u + ((size_t)i + (size_t)j * n) * M + m;
+      Vec<R> cur = vload_rw(up);
+#pragma unroll
+      for (int k = 0; k < W; ++k) cur.v[k] = unit ? cur.v[k] + sum.v[k] : cur.v[k] + w * sum.v[k];
+      vstore(up, cur);
+    }
+  }
+}
+
 // double <-> double-float conversions and the double-float update
 // dst = src as double-float pairs (RN32(x), RN32(x - RN32(x))), without FP64
 // arithmetic for the values a solve holds (dd_split_rn).
@@ -799,6 +878,17 @@ cudaError_t launch_prolong(R* u, const R* uc, const LevelShape& ls, cudaStream_t
   const int nc = (ls.n - 1) / 2;
   const size_t cstride = (size_t)(ls.d == 1 ? nc : nc * nc) * ls.M;
   if (ls.batch == 0) return cudaSuccess;
+  // short lines (at most 1 KB: one time vector per thread of the per-line kernel,
+  // whose index work per point then dominates) walk rows; longer ones keep the
+  // per-line kernel, near the HBM roof there (2-D 511 x 511, M = 4096: 21.9 ms per
+  // solve against 29.0 for the row walk; 4096 x 63 x 63, M = 256: 127 against 108)
+  if (ls.d == 2 && nc > 0 && (size_t)ls.M * sizeof(R) <= 1024) {
+    const size_t items =
+        (size_t)ls.n * ((ls.n + kProlongRun - 1) / kProlongRun) * (ls.M / Vec<R>::W);
+    k_prolong_rows<R><<<dim3(elementwise_grid(items), ls.batch), kLineBlock, 0, s>>>(
+        u, uc, ls.n, ls.M, ls.field_stride(), cstride);
+    return counted(cudaGetLastError());
+  }
   int log_tpl;
   unsigned blocks;
   line_grid<R>(ls.M, npts, &log_tpl, &blocks);

@@ -1025,7 +1025,9 @@ def main():
     unknowns = batch * n ** d * Mw
     wl = {"d": d, "n": n, "M": Mw, "batch": batch, "tol": tol, "unknowns": unknowns,
           "alpha": alpha if batch == 1 else alphas, "f_dev": f_dev, "phi_dev": ph}
-    e2e_steps = 0 if args.no_e2e else (args.e2e_steps or min(args.steps, 5))
+    # the pipelined loop exposes only the first upload and the last download: over
+    # ten steps they are a tenth of a step each
+    e2e_steps = 0 if args.no_e2e else (args.e2e_steps or min(args.steps, 10))
     if e2e_steps and batch == 1:
         wl["f_host"] = f_dev.cpu().numpy()
     cpu_leg = not args.no_cpu and world == 1
